@@ -1,0 +1,181 @@
+/*
+ * Test oracle for the Monte Carlo / Lorenz-Mie photon-transport engine.
+ *
+ * THIS IS TEST INFRASTRUCTURE. It is a plain, slow, double-precision CPU
+ * restatement of what the paper (arXiv 2507.23189) computes, written to check
+ * the CUDA path against. Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load it; the product library never does.
+ * It shares no code, header, table or constant generator with the product.
+ *
+ * Contents
+ *   mie.c     Mie coefficients a_n, b_n (Eq. 7-8, evaluated with the
+ *             logarithmic-derivative recurrences of Bohren & Huffman, the
+ *             paper's ref. [12] in Sec. 2.5), efficiencies (Eq. 13), amplitude
+ *             functions S1/S2 (Eq. 5-6), phase function (Eq. 9), asymmetry
+ *             parameter g (Eq. 12), cross section (Eq. 14), Eq. 17.
+ *   table.c   normalisation (Eq. 10), cumulative distribution and its inverse
+ *             on an equal-probability grid (Sec. 2.6, Sec. 3.1.2).
+ *   philox.c  Philox4x32-10 counter-based generator (Salmon et al., SC'11).
+ *   walk.c    the photon random walk of Sec. 3.1.3 (Eq. 15, Eq. 16) with a
+ *             next-event estimate for the 90-degree side camera (Sec. 4.3).
+ *
+ * Parity status: every function here is pinned by the -m "not gpu" tests
+ * (closed forms, invariants, an independent 50-digit evaluation of Eq. 7-8,
+ * a library Philox); none is "parity unpinned".
+ */
+#ifndef MC_ORACLE_H
+#define MC_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- mie.c */
+
+/* Wiscombe's series length: ceil(x + 4 x^(1/3) + 2). */
+int oracle_mie_nmax(double x);
+
+/* Size parameter x = pi d / lambda (Eq. 3) with lambda the wavelength in the
+ * medium, lambda0 / n_medium. d in micrometres, lambda0 in nanometres. */
+double oracle_size_parameter(double d_um, double n_medium, double lambda0_nm);
+
+/* a_n, b_n for n = 1..nmax, stored interleaved as (re, im) pairs at index
+ * 2*(n-1).  m = m_re + i m_im is the refractive index relative to the medium
+ * (m_im >= 0 absorbs).  Returns 0, or -1 on bad arguments. */
+int oracle_mie_ab(double m_re, double m_im, double x, int nmax,
+                  double *a_reim, double *b_reim);
+
+/* Efficiencies from the series: Eq. 13 for Q_ext, the matching sum of
+ * |a_n|^2 + |b_n|^2 for Q_sca, and g from the cross-term series. */
+int oracle_mie_efficiencies(double m_re, double m_im, double x,
+                            double *qext, double *qsca, double *g_series);
+
+/* S1 and S2 (Eq. 5-6) at n_mu cosines, (re, im) interleaved outputs. */
+int oracle_mie_s12(double m_re, double m_im, double x, const double *mu,
+                   int n_mu, double *s1_reim, double *s2_reim);
+
+/* Raw phase function |S1|^2 + |S2|^2 (Eq. 9 without the constant 1/k^2). */
+int oracle_mie_phase_raw(double m_re, double m_im, double x, const double *mu,
+                         int n_mu, double *p);
+
+/* Extinction cross section, Eq. 14: sigma = Q pi d^2 / 4, d in um, result
+ * in mm^2. */
+double oracle_cross_section_mm2(double q, double d_um);
+
+/* Eq. 17: optical depth from number density (per mm^3), cross section (mm^2)
+ * and path length (mm). */
+double oracle_optical_depth(double n_per_mm3, double sigma_mm2, double l_mm);
+
+/* --------------------------------------------------------------- table.c */
+
+/* Phase-function kinds understood by the table builder. */
+#define ORACLE_PHASE_MIE 0
+#define ORACLE_PHASE_HG  1
+
+/* Build the equal-probability inverse CDF of a phase function.
+ *   kind == ORACLE_PHASE_MIE: (m_re, m_im, x) select the Mie phase function.
+ *   kind == ORACLE_PHASE_HG : hg_g selects Eq. 11.
+ * n_fine (even) is the number of fine theta intervals on [0, pi].
+ * Outputs (each may be NULL):
+ *   icdf[n_bins+1]  cos(theta) at cumulative probability i / n_bins
+ *   omu [n_bins+1]  1 - icdf, computed without cancellation
+ *   pdf [n_bins]    density per unit cos(theta) of the piecewise-linear
+ *                   inverse CDF, (1/n_bins) / (icdf[j+1] - icdf[j])
+ *   diag[4]         {raw normalisation 1/2 int P dmu, g by quadrature,
+ *                    mean of the tabulated distribution, n_fine}
+ * Returns 0, or -1 on bad arguments. */
+int oracle_phase_table(int kind, double m_re, double m_im, double x,
+                       double hg_g, int n_bins, int n_fine, double *icdf,
+                       double *omu, double *pdf, double *diag);
+
+/* -------------------------------------------------------------- philox.c */
+
+/* Philox4x32 with 10 rounds: out = bijection(ctr) under key. */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                          uint32_t out[4]);
+
+/* Batch form for tests: n counters (4 words each), one key. */
+void oracle_philox4x32_10_n(const uint32_t *ctr, uint64_t n,
+                            uint64_t seed, uint32_t *out);
+
+/* The uniform in (0,1) the walk draws from one 32-bit output word. */
+double oracle_uniform(uint32_t r);
+
+/* ---------------------------------------------------------------- walk.c */
+
+typedef struct {
+    /* medium */
+    double mu_s, mu_a;          /* mm^-1 */
+    int phase_kind;             /* ORACLE_PHASE_MIE (table) or ORACLE_PHASE_HG */
+    double hg_g;
+    const double *icdf;         /* [n_bins+1] when phase_kind == MIE */
+    const double *omu;          /* [n_bins+1], 1 - icdf */
+    int n_bins;
+    /* geometry: x in [0,lx] (beam axis), y in [-ly/2,ly/2], z in [-lz/2,lz/2] */
+    double lx, ly, lz;
+    double beam_radius;         /* 0: pencil beam at (0,0,0) */
+    /* side camera on y = +ly/2, columns along x, rows along z */
+    int nx, nz;
+    int n_radial;               /* far-face radial profile bins */
+    double r_max;
+    /* run */
+    uint64_t n_photons, photon_offset, seed;
+    double rr_threshold, rr_survival;
+    uint32_t max_events;        /* flights per photon before truncation */
+    uint32_t max_scatter;       /* 0: unlimited; else stop after that many collisions */
+    double cone_cos;            /* > 0 enables the ORACLE_T_CONE tally */
+    int n_threads;
+} oracle_walk_cfg;
+
+/* Totals, in weight units (one photon carries weight 1). */
+enum {
+    ORACLE_T_REFLECT = 0,   /* left through x = 0 */
+    ORACLE_T_FAR = 1,       /* left through x = lx */
+    ORACLE_T_SIDE = 2,      /* left through a y or z face */
+    ORACLE_T_ABSORB = 3,    /* implicit capture, Eq. 16 */
+    ORACLE_T_ROULETTE = 4,  /* net weight removed by roulette */
+    ORACLE_T_TRUNC = 5,     /* weight left when max_events / max_scatter hit */
+    ORACLE_T_BALLISTIC = 6, /* far-face weight with no collision */
+    ORACLE_T_CONE = 7,      /* analog camera: weight leaving y = +ly/2 with
+                               d_y >= cone_cos (test of the camera estimate) */
+    ORACLE_N_TOTALS = 8
+};
+
+typedef struct {
+    double *image, *image_sq;     /* [nz*nx] sum and sum of per-photon squares */
+    double *radial, *radial_sq;   /* [n_radial] */
+    double totals[ORACLE_N_TOTALS];
+    double totals_sq[ORACLE_N_TOTALS];
+    uint64_t steps;               /* sampled free flights */
+    uint64_t capped;              /* photons stopped by max_events */
+} oracle_walk_out;
+
+/* Per-event trace record, double precision. */
+typedef struct {
+    double status;   /* 0 collided, 1 reflect, 2 far, 3 side, 4 roulette kill,
+                        5 truncated (max_scatter), 6 capped (max_events) */
+    double r[3];     /* position after the flight (collision or exit point) */
+    double d[3];     /* direction after the event */
+    double w;        /* weight after the event */
+    double nee;      /* camera contribution added at this event (0: none) */
+    double pix;      /* pixel index of that contribution, -1: none */
+    double nee_bin;  /* table bin used for the camera density, -1: none/HG */
+    double rad_bin;  /* radial bin for a far-face exit, -1 otherwise */
+    double margin;   /* smallest relative distance of any discrete decision
+                        taken at this event to its threshold */
+} oracle_trace_rec;
+
+/* Run photons [photon_offset, photon_offset + n_photons). Tallies are
+ * accumulated into out (caller zeroes them). If trace != NULL, the first
+ * n_trace photons of the range record their first n_trace_events events into
+ * trace[photon * n_trace_events + event] (unused records get status -1).
+ * Returns 0, or -1 on bad arguments. */
+int oracle_walk(const oracle_walk_cfg *cfg, oracle_walk_out *out,
+                oracle_trace_rec *trace, int n_trace, int n_trace_events);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,138 @@
+/*
+ * Oracle: phase-function normalisation and inverse-CDF table (test
+ * infrastructure only; see oracle.h).
+ *
+ * Sec. 3.1.2 precomputes the phase function on an angular grid and builds a
+ * cumulative distribution function that Sec. 2.6 inverts to sample the
+ * scattering angle. Steps, in that order:
+ *   1. P(cos theta) on a fine uniform theta grid (Eq. 9, or Eq. 11 for H-G).
+ *   2. Normalise so that (1/2) int_{-1}^{1} P dmu = 1, which is Eq. 10 for an
+ *      azimuthally symmetric P (dOmega = 2 pi dmu). Composite Simpson in theta
+ *      on the density F(theta) = (1/2) P(cos theta) sin theta.
+ *   3. CDF(mu) = (1/2) int_{-1}^{mu} P dmu', accumulated from theta = pi.
+ *   4. Invert at the equal-probability levels i / n_bins: inside the Simpson
+ *      panel that holds the level, the integral of the panel's interpolating
+ *      parabola is solved for theta by bisection.
+ * The sampled distribution is the piecewise-linear inverse CDF through those
+ * nodes, whose density on bin j is (1/n_bins) / (icdf[j+1] - icdf[j]); the
+ * walk's camera estimate uses that same density.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+
+/* Eq. 11 times 4 pi, in the cancellation-free form
+ * 1 + g^2 - 2 g cos(theta) = (1-g)^2 + 4 g sin^2(theta/2). */
+static double hg_phase(double g, double theta)
+{
+    double sh = sin(0.5 * theta);
+    double t = (1.0 - g) * (1.0 - g) + 4.0 * g * sh * sh;
+    return (1.0 - g * g) / (t * sqrt(t));
+}
+
+/* Integral over [0, s] of the parabola through (0,f0), (h,f1), (2h,f2). */
+static double panel_partial(double f0, double f1, double f2, double h, double s)
+{
+    double c1 = (-3.0 * f0 + 4.0 * f1 - f2) / (4.0 * h);
+    double c2 = (f0 - 2.0 * f1 + f2) / (6.0 * h * h);
+    return s * (f0 + s * (c1 + s * c2));
+}
+
+int oracle_phase_table(int kind, double m_re, double m_im, double x,
+                       double hg_g, int n_bins, int n_fine, double *icdf,
+                       double *omu, double *pdf, double *diag)
+{
+    if (n_bins < 2 || n_fine < 4 || (n_fine & 1))
+        return -1;
+    if (kind == ORACLE_PHASE_HG && !(hg_g > -1.0 && hg_g < 1.0))
+        return -1;
+    if (kind != ORACLE_PHASE_HG && kind != ORACLE_PHASE_MIE)
+        return -1;
+
+    const double h = M_PI / n_fine;
+    /* Node j sits at theta_j = pi - j h, so mu increases with j. */
+    double *F = malloc((size_t)(n_fine + 1) * sizeof *F);
+    double *mu = malloc((size_t)(n_fine + 1) * sizeof *mu);
+    double *cum = malloc((size_t)(n_fine / 2 + 1) * sizeof *cum);
+    double *t_icdf = malloc((size_t)(n_bins + 1) * sizeof *t_icdf);
+    double *t_omu = malloc((size_t)(n_bins + 1) * sizeof *t_omu);
+    if (!F || !mu || !cum || !t_icdf || !t_omu)
+        goto fail;
+
+    for (int j = 0; j <= n_fine; ++j)
+        mu[j] = cos((double)(n_fine - j) * h);
+    if (kind == ORACLE_PHASE_MIE) {
+        if (oracle_mie_phase_raw(m_re, m_im, x, mu, n_fine + 1, F))
+            goto fail;
+    } else {
+        for (int j = 0; j <= n_fine; ++j)
+            F[j] = hg_phase(hg_g, (double)(n_fine - j) * h);
+    }
+    /* F <- (1/2) P sin(theta) */
+    for (int j = 0; j <= n_fine; ++j)
+        F[j] *= 0.5 * sin((double)(n_fine - j) * h);
+
+    /* Step 2/3: Simpson panels, cumulated from theta = pi. */
+    cum[0] = 0.0;
+    double gnum = 0.0;
+    for (int p = 0; p < n_fine / 2; ++p) {
+        int j = 2 * p;
+        cum[p + 1] = cum[p] + h / 3.0 * (F[j] + 4.0 * F[j + 1] + F[j + 2]);
+        gnum += h / 3.0 * (F[j] * mu[j] + 4.0 * F[j + 1] * mu[j + 1] +
+                           F[j + 2] * mu[j + 2]);
+    }
+    const double Z = cum[n_fine / 2];
+    if (!(Z > 0.0))
+        goto fail;
+
+    /* Step 4: inversion at levels i / n_bins. */
+    t_icdf[0] = -1.0;
+    t_omu[0] = 2.0;
+    t_icdf[n_bins] = 1.0;
+    t_omu[n_bins] = 0.0;
+    int p = 0;
+    for (int i = 1; i < n_bins; ++i) {
+        double target = Z * ((double)i / n_bins);
+        while (p < n_fine / 2 - 1 && cum[p + 1] <= target)
+            ++p;
+        int j = 2 * p;
+        double want = target - cum[p];
+        double lo = 0.0, hi = 2.0 * h;
+        for (int it = 0; it < 200 && hi - lo > 1e-18 * h; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (panel_partial(F[j], F[j + 1], F[j + 2], h, mid) < want)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        double s = 0.5 * (lo + hi);
+        /* theta = pi - (2 p h + s), written from the near end of the grid */
+        double theta = (double)(n_fine - j) * h - s;
+        double sh = sin(0.5 * theta);
+        t_icdf[i] = cos(theta);
+        t_omu[i] = 2.0 * sh * sh;
+    }
+
+    if (icdf)
+        for (int i = 0; i <= n_bins; ++i) icdf[i] = t_icdf[i];
+    if (omu)
+        for (int i = 0; i <= n_bins; ++i) omu[i] = t_omu[i];
+    if (pdf)
+        for (int i = 0; i < n_bins; ++i)
+            pdf[i] = (1.0 / n_bins) / (t_omu[i] - t_omu[i + 1]);
+    if (diag) {
+        double mean = 0.0;
+        for (int i = 0; i < n_bins; ++i)
+            mean += 0.5 * (t_icdf[i] + t_icdf[i + 1]);
+        diag[0] = Z;
+        diag[1] = gnum / Z;
+        diag[2] = mean / n_bins;
+        diag[3] = (double)n_fine;
+    }
+    free(F); free(mu); free(cum); free(t_icdf); free(t_omu);
+    return 0;
+fail:
+    free(F); free(mu); free(cum); free(t_icdf); free(t_omu);
+    return -1;
+}
