@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""Throughput of the photon walk on the headline workload.
+
+Workload: the optical-depth sweep's tau = 5 Mie point -- 10x10x45 mm cuvette of
+water with 5 um polystyrene spheres at 532 nm, pencil beam along the 45 mm
+axis, 4096-bin Mie inverse-CDF table, roulette 1e-4 / 0.1, 1e8 photons per
+step, 256x256 side-camera image + 128-bin radial profile, Philox seed 1.
+A step is one mc_run over the 1e8 photons (the whole hot path). Metric:
+photon-steps (sampled free flights) per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
+
+Under torchrun each rank runs its own photon range (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "photon-steps/s at τ=5 Mie on 1 GB300; batched & adjoint vs plain at matched error"
+UNIT = "photon-steps/s"
+TAU = 5.0
+LX, LY, LZ = 45.0, 10.0, 10.0
+NX = NZ = 256
+N_RADIAL = 128
+R_MAX = 5.0 * 2 ** 0.5
+N_PHOTONS = 100_000_000
+SEED = 1
+
+# Roofline of the walk kernel: it is bound by single-precision / integer
+# issue, not by memory (photon state stays in registers, the table in shared
+# memory). Peak = SMs x 128 lanes x max SM clock (thread-instructions/s).
+# Work per photon-step = thread-instructions the kernel executes per sampled
+# flight on this workload, from ncu (smsp__thread_inst_executed.sum / steps);
+# DRAM bytes per launch from the same capture (None when stale).
+THREAD_INST_PER_STEP = None
+DRAM_BYTES_PER_LAUNCH = None
+LANES_PER_SM = 128
+
+
+def _workload_config():
+    return {
+        "workload": "tau=5 Mie point of the optical-depth sweep: 10x10x45 mm water cuvette, 5 um "
+                    "polystyrene (n=1.59) at 532 nm, pencil beam, 4096-bin Mie table, 1e8 photons, "
+                    "256x256 side image + 128-bin radial profile, roulette 1e-4/0.1, seed 1",
+        "n_photons": N_PHOTONS, "tau": TAU, "phase": "mie", "image": [NZ, NX], "n_radial": N_RADIAL,
+        "l2": "flushed between timed steps (512 MiB write)",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_sample(n_photons, n_threads=None):
+    """Time the oracle (test infrastructure) on n_photons of the workload."""
+    import oracle
+    x = oracle.size_parameter(5.0, 1.33, 532.0)
+    m = complex(1.59 / 1.33, 0.0)
+    t = oracle.phase_table(oracle.PHASE_MIE, m, x)
+    threads = n_threads or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.walk(mu_s=TAU / LX, table=t, n_photons=n_photons, nx=NX, nz=NZ, n_radial=N_RADIAL,
+                    r_max=R_MAX, seed=SEED, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return r["steps"], dt, threads
+
+
+def cpu_baseline(target_s=12.0):
+    """Oracle throughput on the host cores over a bounded sample."""
+    steps, dt, threads = oracle_sample(200_000)
+    rate = steps / dt
+    n = int(min(max(200_000 * target_s / max(dt, 1e-3), 200_000), N_PHOTONS))
+    steps, dt, threads = oracle_sample(n)
+    s1, d1, _ = oracle_sample(max(n // (4 * threads), 20_000), n_threads=1)
+    return {"value": steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d photons of the workload (%d photon-steps) in %.1f s on %d threads of %s; "
+                      "single thread: %.3g photon-steps/s" % (n, steps, dt, threads, _cpu_model(), s1 / d1),
+            "photons_per_s": n / dt}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    times, steps_total = [], 0
+    n = None
+    for i in range(args.warmup + args.steps):
+        if n is None:
+            s, dt, threads = oracle_sample(100_000)
+            n = int(min(max(100_000 * 5.0 / max(dt, 1e-3), 100_000), N_PHOTONS))
+        s, dt, threads = oracle_sample(n)
+        if i >= args.warmup:
+            times.append(dt)
+            steps_total += s
+    value = steps_total / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference", "config": _workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "each step: %d photons of the workload on %d threads of %s"
+                                       % (n, threads, _cpu_model())},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_engine(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2507_23189_gb300 import build as B
+    if rank == 0 or ws == 1:
+        B.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    import paper_2507_23189_gb300 as E
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    table = E.PhaseTable(5.0, 1.59, 1.33, 532.0, 4096)
+    med = E.Medium.from_optical_depth(table, TAU, LX)
+    cam = E.Camera(NX, NZ, N_RADIAL, R_MAX)
+    geo = E.Geometry(LX, LY, LZ, 0.0)
+    eng = E.Engine(cam, geo, dev)
+    offset = rank * N_PHOTONS
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        eng.run(med, N_PHOTONS, seed=SEED, photon_offset=offset, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    eng.check()
+    steps_per_run = eng.result()["steps"]
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(torch.cuda.current_device() if ws == 1 else local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    barrier()
+    clk = clocks.stop()
+    eng.check()
+    assert eng.result()["steps"] == steps_per_run
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_local = sum(ms) / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    st = torch.tensor([steps_per_run * args.steps], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(st, op=torch.distributed.ReduceOp.SUM)
+    t_max, total_steps = float(t.item()), float(st.item())
+    value = total_steps / t_max
+
+    # end to end through the host-buffer entry point: table in, tallies out
+    import numpy as np
+    work = torch.empty(E.host_workspace_bytes(med, cam), dtype=torch.uint8, device=dev)
+    pinned = lambda shape: torch.zeros(shape, dtype=torch.int64, pin_memory=True).numpy()
+    img, rad, tot = pinned((NZ, NX)), pinned(N_RADIAL), pinned(8)
+    blob = torch.from_numpy(table.blob).pin_memory().numpy()
+    E.run_host(med, geo, cam, N_PHOTONS, work, seed=SEED, photon_offset=offset, image=img, radial=rad,
+               totals=tot, table_host=blob)
+    barrier()
+    e2e_t = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        E.run_host(med, geo, cam, N_PHOTONS, work, seed=SEED, photon_offset=offset, image=img,
+                   radial=rad, totals=tot, table_host=blob)
+        e2e_t.append(time.perf_counter() - t0)
+    te = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = total_steps / float(te.item())
+    h2d = table.blob.nbytes
+    d2h = img.nbytes + rad.nbytes + tot.nbytes + 4
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * LANES_PER_SM * sm_max * 1e6 / 1e12   # T thread-instructions / s
+    kernel_s = t_local / args.steps
+    roof = None
+    if THREAD_INST_PER_STEP:
+        ach = THREAD_INST_PER_STEP * steps_per_run / kernel_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tinst/s", "frac": ach / peak,
+                "traffic": DRAM_BYTES_PER_LAUNCH,
+                "per_unit": "%g thread-instructions per photon-step (ncu), peak = %d SMs x %d lanes x "
+                            "%.0f MHz" % (THREAD_INST_PER_STEP, sms, LANES_PER_SM, sm_max)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _workload_config(),
+            "photons_per_s": ws * N_PHOTONS * args.steps / t_max,
+            "steps_per_photon": steps_per_run / N_PHOTONS,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps, "clocks": clk, "roofline": roof}
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)   # timing rule: at least three warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_engine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

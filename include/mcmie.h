@@ -1,0 +1,225 @@
+/*
+ * mcmie.h - C ABI of the GB300 Monte Carlo / Lorenz-Mie photon-transport
+ * engine (arXiv 2507.23189, "GPU-Accelerated Monte Carlo Simulation and
+ * Experimental Study of Radiative Transfer in Multiple Scattering Media").
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an mc_status and never aborts the process. Invalid
+ *    arguments are rejected (MC_ERR_ARG) before anything is launched.
+ *  - Lengths are in millimetres, coefficients in mm^-1, particle diameters in
+ *    micrometres, wavelengths in nanometres.
+ *  - Pointers named d_* are device pointers; all other pointers are host
+ *    pointers. All buffers are owned by the caller; the library never frees
+ *    or keeps a pointer after a call returns. Device pointers must be 16-byte
+ *    aligned (any cudaMalloc / torch allocation is).
+ *  - Device calls are asynchronous and ordered on the given stream (0: the
+ *    legacy default stream). Device-side problems (event cap reached, a
+ *    non-finite value, a table-staging timeout) are recorded as bits in the
+ *    caller's error word; mc_check() reads it back and maps it to a status.
+ *  - mc_run and mc_trace allocate nothing: scratch memory comes from the
+ *    caller's workspace (mc_workspace_bytes()).
+ *  - Photons [photon_offset, photon_offset + n_photons) are simulated; photon
+ *    p draws event e's random numbers from Philox4x32-10 with key = seed and
+ *    counter (p_lo, p_hi, e, 0), so splitting a photon range over calls,
+ *    streams or GPUs gives bit-identical integer tallies.
+ */
+#ifndef MCMIE_H
+#define MCMIE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MC_OK = 0,
+    MC_ERR_ARG = -1,      /* invalid argument; nothing was launched            */
+    MC_ERR_CUDA = -2,     /* a CUDA runtime call failed                        */
+    MC_ERR_NOMEM = -3,    /* workspace too small                               */
+    MC_ERR_TIMEOUT = -4,  /* a bounded device wait (table staging) gave up     */
+    MC_ERR_OVERFLOW = -5, /* a fixed-point contribution exceeded 2^62          */
+    MC_ERR_NUMERIC = -6,  /* a non-finite weight or contribution was seen      */
+    MC_ERR_EVENTS = -7,   /* at least one photon hit max_events (truncated)    */
+    MC_ERR_TABLE = -8     /* the device table blob failed its header check     */
+} mc_status;
+
+/* Device error-word bits (OR-ed by kernels into *d_error). */
+#define MC_EFLAG_EVENTS   0x1u
+#define MC_EFLAG_TIMEOUT  0x2u
+#define MC_EFLAG_NUMERIC  0x4u
+#define MC_EFLAG_OVERFLOW 0x8u
+#define MC_EFLAG_TABLE    0x10u
+
+/* ------------------------------------------------------------------------
+ * Phase table (Sec. 2.2 Eq. 3-9, Sec. 2.4 Eq. 12, Sec. 2.5 Eq. 13-14,
+ * Sec. 3.1.2): the Mie phase function is computed in double precision,
+ * normalised (Eq. 10) and inverted on n_bins equal-probability levels.
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+    double diameter_um;    /* sphere diameter d                                 */
+    double n_particle_re;  /* particle refractive index n + i k (Eq. 4)         */
+    double n_particle_im;  /*   k >= 0 absorbs                                  */
+    double n_medium;       /* refractive index of the surrounding medium        */
+    double wavelength_nm;  /* vacuum wavelength lambda0                         */
+    int n_bins;            /* equal-probability bins; power of two, 64..16384   */
+} mie_params;
+
+typedef struct {
+    double x;              /* size parameter pi d n_medium / lambda0 (Eq. 3)    */
+    double m_re, m_im;     /* relative refractive index m_particle / n_medium   */
+    double qext, qsca, qabs;        /* efficiencies (Eq. 13)                    */
+    double g;                       /* asymmetry parameter (Eq. 12), series     */
+    double g_table;                 /* mean cosine of the tabulated distribution */
+    double sigma_ext_mm2, sigma_sca_mm2, sigma_abs_mm2; /* Eq. 14               */
+    int nmax;                       /* terms kept in the Mie series             */
+} mie_info;
+
+/* Bytes of the packed table blob for n_bins bins (0 for an invalid n_bins). */
+size_t mc_table_bytes(int n_bins);
+
+/* Build the Mie phase table on the host.
+ *   params   in: particle and wavelength (see mie_params).
+ *   info     out: Mie quantities (may be NULL).
+ *   table    out: host buffer of mc_table_bytes(n_bins) bytes receiving the
+ *            packed single-precision table the kernels stage into shared
+ *            memory; copy it to a device buffer for mc_medium.d_table. May be
+ *            NULL.
+ *   omu64    out: double[n_bins+1], 1 - cos(theta) at the levels i / n_bins
+ *            (NULL to skip).
+ *   pdf64    out: double[n_bins], density per unit cos(theta) on each bin of
+ *            the piecewise-linear inverse CDF (NULL to skip).
+ * Returns MC_OK, or MC_ERR_ARG / MC_ERR_NUMERIC. Thread-safe. */
+mc_status mie_table_build(const mie_params *params, mie_info *info, void *table,
+                          double *omu64, double *pdf64);
+
+/* ------------------------------------------------------------------------
+ * Transport (Sec. 2.6, Sec. 3.1.3: Eq. 15 free path, Eq. 16 implicit
+ * capture, weight threshold; Sec. 4.3: 90-degree side camera).
+ * ------------------------------------------------------------------------ */
+
+#define MC_PHASE_TABLE 0   /* sample the staged inverse-CDF table           */
+#define MC_PHASE_HG    1   /* Henyey-Greenstein (Eq. 11) with parameter hg_g */
+
+typedef struct {
+    double mu_s, mu_a;      /* scattering / absorption coefficients, mm^-1     */
+    int phase_kind;         /* MC_PHASE_TABLE or MC_PHASE_HG                   */
+    double hg_g;            /* H-G asymmetry, -1 < g < 1 (MC_PHASE_HG only)    */
+    const void *d_table;    /* device copy of a mie_table_build() blob         */
+    int n_bins;             /* bins of that blob (checked against its header)  */
+} mc_medium;
+
+/* Eq. 17: number density (per mm^3) times the extinction cross section gives
+ * mu_ext; mu_s and mu_a follow from the Mie efficiencies, plus an absorption
+ * coefficient of the host medium. Writes mu_s and mu_a of *out. */
+mc_status mc_medium_from_density(const mie_info *info, double number_density_per_mm3,
+                                 double mu_a_medium, mc_medium *out);
+
+typedef struct {
+    double lx, ly, lz;      /* cuvette: x in [0,lx] (beam axis),
+                               y in [-ly/2,ly/2], z in [-lz/2,lz/2]            */
+    double beam_radius;     /* 0: pencil beam entering at (0,0,0) along +x;
+                               > 0: uniform disc of that radius at x = 0       */
+} mc_geometry;
+
+typedef struct {
+    int nx, nz;             /* side image on the y = +ly/2 face: columns span
+                               x in [0,lx], rows span z in [-lz/2,lz/2]        */
+    int n_radial;           /* far-face (x = lx) radial profile bins           */
+    double r_max;           /* radial profile range [0, r_max)                 */
+} mc_camera;
+
+typedef struct {
+    uint64_t n_photons;     /* photons to run                                  */
+    uint64_t photon_offset; /* index of the first photon                       */
+    uint64_t seed;          /* Philox key                                      */
+    double rr_threshold;    /* weight below which roulette is played           */
+    double rr_survival;     /* survival probability (0: plain cut)             */
+    uint32_t max_events;    /* free flights per photon before truncation       */
+    uint32_t max_scatter;   /* 0: unlimited; else end after that many collisions */
+    int image_frac_bits;    /* fixed-point fraction bits of the image (8..48)  */
+    int accumulate;         /* 0: zero the tallies first; 1: add to them       */
+    /* launch tuning; results do not depend on these (0 = automatic) */
+    int block_size;         /* threads per CTA: 0 or a multiple of 32, <= 256  */
+    int blocks_per_sm;      /* persistent CTAs per SM: 0 = occupancy maximum   */
+    int image_mode;         /* 0 auto, 1 image tile in shared memory (must
+                               fit), 2 image atomics straight to global memory */
+} mc_run_params;
+
+/* Totals tallied by mc_run, as int64 in the units noted. */
+enum {
+    MC_TOT_REFLECT = 0,     /* weight leaving x = 0            (2^-32 units)  */
+    MC_TOT_FAR = 1,         /* weight leaving x = lx           (2^-32)        */
+    MC_TOT_SIDE = 2,        /* weight leaving y/z faces        (2^-32)        */
+    MC_TOT_ABSORB = 3,      /* implicitly captured weight      (2^-32)        */
+    MC_TOT_ROULETTE = 4,    /* net weight removed by roulette  (2^-32, signed) */
+    MC_TOT_TRUNC = 5,       /* weight of truncated photons     (2^-32)        */
+    MC_TOT_BALLISTIC = 6,   /* far-face weight, no collision   (2^-32)        */
+    MC_TOT_STEPS = 7,       /* sampled free flights (photon-steps), count     */
+    MC_N_TOTALS = 8
+};
+#define MC_WEIGHT_FRAC_BITS 32
+
+typedef struct {
+    int64_t *d_image;       /* [nz][nx] camera image, 2^-image_frac_bits units */
+    int64_t *d_radial;      /* [n_radial] far-face weight by radius (2^-32)    */
+    int64_t *d_totals;      /* [MC_N_TOTALS]                                   */
+    uint32_t *d_error;      /* error word (MC_EFLAG_*), OR-ed; zero it first   */
+    void *d_work;           /* scratch, >= mc_workspace_bytes() bytes          */
+    size_t work_bytes;
+} mc_tallies;
+
+/* Scratch bytes mc_run / mc_trace need for this camera. */
+size_t mc_workspace_bytes(const mc_camera *camera);
+
+/* Run the photon walk on the GPU. Asynchronous on `stream`. */
+mc_status mc_run(const mc_medium *medium, const mc_geometry *geom,
+                 const mc_camera *camera, const mc_run_params *run,
+                 const mc_tallies *tallies, void *stream);
+
+/* Host-buffer form of mc_run, for callers whose inputs and outputs live in
+ * host memory. The table blob (mc_table_bytes(n_bins) bytes, or NULL for
+ * MC_PHASE_HG) is copied to the device, the walk runs, and image, radial
+ * profile and totals are copied back; the call returns when they are in
+ * host memory. d_work must hold mc_host_workspace_bytes() bytes of device
+ * memory (table, tallies and scratch are carved from it). */
+size_t mc_host_workspace_bytes(const mc_medium *medium, const mc_camera *camera);
+mc_status mc_run_host(const mc_medium *medium, const void *table,
+                      const mc_geometry *geom, const mc_camera *camera,
+                      const mc_run_params *run, int64_t *image, int64_t *radial,
+                      int64_t *totals, uint32_t *error, void *d_work,
+                      size_t work_bytes, void *stream);
+
+/* Per-event trace of the first n_trace photons of the range, first
+ * n_events events each (same arithmetic as mc_run, tallies included).
+ * d_trace receives n_trace * n_events records of 12 32-bit words:
+ *   [0] status (int32): -1 unused, 0 collided, 1 left x = 0, 2 left x = lx,
+ *       3 left a side face, 4 ended by roulette, 5 ended by max_scatter,
+ *       6 ended by max_events
+ *   [1..3] position after the flight (float), [4..6] direction after the
+ *   event (float), [7] weight after the event (float), [8] camera
+ *   contribution (float), [9] pixel (int32, -1 none), [10] table bin of the
+ *   camera density (int32, -1 none), [11] radial bin (int32, -1 none). */
+mc_status mc_trace(const mc_medium *medium, const mc_geometry *geom,
+                   const mc_camera *camera, const mc_run_params *run,
+                   const mc_tallies *tallies, void *d_trace, int n_trace,
+                   int n_events, void *stream);
+
+/* Synchronise `stream`, read *d_error and map its bits to a status
+ * (MC_OK when zero). */
+mc_status mc_check(const uint32_t *d_error, void *stream);
+
+/* Philox4x32-10 on the device: out[4i..4i+3] = Philox(key = seed,
+ * counter = ctr[4i..4i+3]) for i < n. For testing the generator. */
+mc_status mc_philox(const uint32_t *d_ctr, uint64_t n, uint64_t seed,
+                    uint32_t *d_out, void *stream);
+
+/* Short description of a status code (static string). */
+const char *mc_status_string(mc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCMIE_H */

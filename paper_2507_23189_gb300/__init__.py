@@ -1,0 +1,18 @@
+"""GB300 Monte Carlo / Lorenz-Mie photon-transport engine (arXiv 2507.23189).
+
+The per-photon random walk through a turbid suspension (free path, Mie or
+Henyey-Greenstein scattering, implicit capture with roulette, index-matched
+cuvette walls, side-camera next-event estimate) runs in hand-written sm_103a
+CUDA behind the C ABI in include/mcmie.h; this package is its binding.
+"""
+from . import _native
+from .engine import (Camera, Engine, Geometry, Medium, PhaseTable, decode_trace,
+                     host_workspace_bytes, philox, run_host, run_params)
+
+__all__ = ["Camera", "Engine", "Geometry", "Medium", "PhaseTable", "decode_trace",
+           "host_workspace_bytes", "philox", "run_host", "run_params", "lib"]
+
+
+def lib():
+    """The loaded engine library (build it with paper_2507_23189_gb300.build.build())."""
+    return _native.lib()

@@ -1,0 +1,122 @@
+"""ctypes declarations of the engine's C ABI (include/mcmie.h).
+
+Argument marshalling only: every computation happens in libmcmie.so. Loading
+fails loudly if the library has not been built; there is no fallback.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmcmie.so")
+
+MC_OK = 0
+STATUS = {0: "MC_OK", -1: "MC_ERR_ARG", -2: "MC_ERR_CUDA", -3: "MC_ERR_NOMEM", -4: "MC_ERR_TIMEOUT",
+          -5: "MC_ERR_OVERFLOW", -6: "MC_ERR_NUMERIC", -7: "MC_ERR_EVENTS", -8: "MC_ERR_TABLE"}
+EFLAG_EVENTS, EFLAG_TIMEOUT, EFLAG_NUMERIC, EFLAG_OVERFLOW, EFLAG_TABLE = 1, 2, 4, 8, 16
+PHASE_TABLE, PHASE_HG = 0, 1
+TOT_REFLECT, TOT_FAR, TOT_SIDE, TOT_ABSORB, TOT_ROULETTE, TOT_TRUNC, TOT_BALLISTIC, TOT_STEPS = range(8)
+N_TOTALS = 8
+WEIGHT_FRAC_BITS = 32
+TRACE_WORDS = 12
+
+# every symbol include/mcmie.h declares
+EXPORTS = ("mc_table_bytes", "mie_table_build", "mc_medium_from_density", "mc_workspace_bytes",
+           "mc_run", "mc_host_workspace_bytes", "mc_run_host", "mc_trace", "mc_check", "mc_philox",
+           "mc_status_string")
+
+
+class McError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (fn, STATUS.get(status, "?"), status))
+
+
+class MieParams(C.Structure):
+    _fields_ = [("diameter_um", C.c_double), ("n_particle_re", C.c_double),
+                ("n_particle_im", C.c_double), ("n_medium", C.c_double),
+                ("wavelength_nm", C.c_double), ("n_bins", C.c_int)]
+
+
+class MieInfo(C.Structure):
+    _fields_ = [("x", C.c_double), ("m_re", C.c_double), ("m_im", C.c_double),
+                ("qext", C.c_double), ("qsca", C.c_double), ("qabs", C.c_double),
+                ("g", C.c_double), ("g_table", C.c_double), ("sigma_ext_mm2", C.c_double),
+                ("sigma_sca_mm2", C.c_double), ("sigma_abs_mm2", C.c_double), ("nmax", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Medium(C.Structure):
+    _fields_ = [("mu_s", C.c_double), ("mu_a", C.c_double), ("phase_kind", C.c_int),
+                ("hg_g", C.c_double), ("d_table", C.c_void_p), ("n_bins", C.c_int)]
+
+
+class Geometry(C.Structure):
+    _fields_ = [("lx", C.c_double), ("ly", C.c_double), ("lz", C.c_double),
+                ("beam_radius", C.c_double)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("nx", C.c_int), ("nz", C.c_int), ("n_radial", C.c_int), ("r_max", C.c_double)]
+
+
+class RunParams(C.Structure):
+    _fields_ = [("n_photons", C.c_uint64), ("photon_offset", C.c_uint64), ("seed", C.c_uint64),
+                ("rr_threshold", C.c_double), ("rr_survival", C.c_double),
+                ("max_events", C.c_uint32), ("max_scatter", C.c_uint32),
+                ("image_frac_bits", C.c_int), ("accumulate", C.c_int),
+                ("block_size", C.c_int), ("blocks_per_sm", C.c_int), ("image_mode", C.c_int)]
+
+
+class Tallies(C.Structure):
+    _fields_ = [("d_image", C.c_void_p), ("d_radial", C.c_void_p), ("d_totals", C.c_void_p),
+                ("d_error", C.c_void_p), ("d_work", C.c_void_p), ("work_bytes", C.c_size_t)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded engine library. Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("engine library %s is missing: run paper_2507_23189_gb300.build.build() "
+                           "(or __graft_entry__.build()) first" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    vp = C.c_void_p
+    L.mc_table_bytes.restype = C.c_size_t
+    L.mc_table_bytes.argtypes = [C.c_int]
+    L.mie_table_build.restype = C.c_int
+    L.mie_table_build.argtypes = [P(MieParams), P(MieInfo), vp, P(C.c_double), P(C.c_double)]
+    L.mc_medium_from_density.restype = C.c_int
+    L.mc_medium_from_density.argtypes = [P(MieInfo), C.c_double, C.c_double, P(Medium)]
+    L.mc_workspace_bytes.restype = C.c_size_t
+    L.mc_workspace_bytes.argtypes = [P(Camera)]
+    L.mc_run.restype = C.c_int
+    L.mc_run.argtypes = [P(Medium), P(Geometry), P(Camera), P(RunParams), P(Tallies), vp]
+    L.mc_host_workspace_bytes.restype = C.c_size_t
+    L.mc_host_workspace_bytes.argtypes = [P(Medium), P(Camera)]
+    L.mc_run_host.restype = C.c_int
+    L.mc_run_host.argtypes = [P(Medium), vp, P(Geometry), P(Camera), P(RunParams), vp, vp, vp, vp,
+                              vp, C.c_size_t, vp]
+    L.mc_trace.restype = C.c_int
+    L.mc_trace.argtypes = [P(Medium), P(Geometry), P(Camera), P(RunParams), P(Tallies), vp, C.c_int,
+                           C.c_int, vp]
+    L.mc_check.restype = C.c_int
+    L.mc_check.argtypes = [vp, vp]
+    L.mc_philox.restype = C.c_int
+    L.mc_philox.argtypes = [vp, C.c_uint64, C.c_uint64, vp, vp]
+    L.mc_status_string.restype = C.c_char_p
+    L.mc_status_string.argtypes = [C.c_int]
+    _lib = L
+    return L
+
+
+def check(fn, status):
+    if status != MC_OK:
+        raise McError(fn, status)
+    return status

@@ -1,0 +1,58 @@
+// Internal interface between the C ABI layer (api.cu) and the kernels (walk.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mcmie.h"
+
+namespace mcx {
+
+// Everything a walk launch needs, already validated and converted to the
+// precision the kernels use. Passed by value as a __grid_constant__ argument.
+struct WalkArgs {
+    // medium
+    float mu_ext, inv_mu_ext;   // mm^-1, mm
+    float albedo;               // 1 - mu_a/mu_ext (Eq. 16 factor)
+    float absorb_frac;          // mu_a/mu_ext
+    int phase_kind;             // MC_PHASE_TABLE / MC_PHASE_HG
+    float hg_g, hg_one_m_g, hg_two_g;
+    float hg_A;                 // 2 (1-g)^2        (sampling)
+    float hg_a2;                // (1-g)^2           (density)
+    float hg_K;                 // (1-g^2) / (4 pi)  (density per sr)
+    const unsigned char *table; // packed blob in global memory (table_format.h)
+    uint32_t table_bytes;
+    int n_bins;
+    // geometry
+    float lx, hy, hz, beam_r;
+    // camera
+    int nx, nz, n_radial;
+    float sx, sz, sr;           // nx/lx, nz/lz, n_radial/r_max
+    // run
+    unsigned long long n_photons, photon_offset;
+    uint32_t key0, key1;
+    float rr_thr, rr_surv, inv_rr_surv;
+    uint32_t max_events, max_scatter;
+    float img_scale;            // 2^image_frac_bits
+    // outputs
+    unsigned long long *image, *radial, *totals;
+    uint32_t *error;
+    unsigned long long *counter;  // photon counter in the caller's workspace
+    // trace (trace kernels only)
+    int32_t *trace;
+    int n_trace, n_trace_events;
+};
+
+struct LaunchCfg {
+    int block = 256;
+    int blocks_per_sm = 0;  // 0: occupancy maximum
+    int image_mode = 0;     // 0 auto, 1 shared-memory tile, 2 global atomics
+};
+
+// Launch the walk (or its trace variant) on `stream`. Returns cudaSuccess or
+// the launch error.
+cudaError_t launch_walk(const WalkArgs &a, bool trace, const LaunchCfg &cfg, cudaStream_t stream);
+
+cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out,
+                          cudaStream_t stream);
+
+}  // namespace mcx

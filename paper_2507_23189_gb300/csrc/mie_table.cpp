@@ -1,0 +1,279 @@
+// Host-side Lorenz-Mie phase table (the engine's table builder).
+//
+// Sec. 3.1.2 precomputes the phase function and its cumulative distribution
+// so that the walk samples the scattering angle by table lookup (Sec. 2.6).
+// Everything here is double precision; only the packed output is rounded to
+// single precision for the kernels.
+//
+//  * Mie coefficients a_n, b_n (Eq. 7-8) in the logarithmic-derivative form of
+//    Bohren & Huffman (the paper's ref. [12], Sec. 2.5). D_N(mx) at the top of
+//    the series comes from the continued fraction for psi_N / psi_{N-1}
+//    (evaluated with the modified Lentz method), then D_n runs downward;
+//    psi_n(x), chi_n(x) run upward. Series length: Wiscombe (1980).
+//  * Efficiencies (Eq. 13), g (Eq. 12 via the cross-term series), cross
+//    sections (Eq. 14).
+//  * Phase function |S1|^2 + |S2|^2 (Eq. 5-6, 9) integrated over theta with
+//    8-point Gauss-Legendre panels; normalisation (Eq. 10) by the total.
+//  * Inverse CDF on n_bins equal-probability levels by safeguarded Newton
+//    iteration on the exact integrand inside the panel holding each level.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "../../include/mcmie.h"
+#include "table_format.h"
+
+namespace {
+
+using cplx = std::complex<double>;
+constexpr double kPi = 3.14159265358979323846;
+
+// Wiscombe's recommended number of terms.
+int series_length(double x)
+{
+    double n;
+    if (x < 0.02)
+        n = x + 4.0 * std::cbrt(x) + 1.0;
+    else if (x <= 8.0)
+        n = x + 4.0 * std::cbrt(x) + 1.0;
+    else if (x < 4200.0)
+        n = x + 4.05 * std::cbrt(x) + 2.0;
+    else
+        n = x + 4.0 * std::cbrt(x) + 2.0;
+    int k = (int)std::lround(n);
+    return k < 1 ? 1 : k;
+}
+
+// psi_N(z) / psi_{N-1}(z) = 1 / (b1 - 1 / (b2 - 1 / (b3 - ...))),
+// b_k = (2N + 2k - 1) / z; modified Lentz.
+cplx riccati_ratio(int N, cplx z)
+{
+    const double tiny = 1e-300, eps = 1e-17;
+    cplx f = tiny, C = f, D = 0.0;
+    for (int k = 1; k < 100000; ++k) {
+        cplx b = (2.0 * N + 2.0 * k - 1.0) / z;
+        double a = (k == 1) ? 1.0 : -1.0;
+        D = b + a * D;
+        if (std::abs(D) < tiny) D = tiny;
+        C = b + a / C;
+        if (std::abs(C) < tiny) C = tiny;
+        D = 1.0 / D;
+        cplx delta = C * D;
+        f *= delta;
+        if (std::abs(delta - 1.0) < eps) break;
+    }
+    return f;
+}
+
+struct MieSeries {
+    int nmax = 0;
+    std::vector<cplx> a, b;  // index 1..nmax
+};
+
+bool mie_series(cplx m, double x, MieSeries &S)
+{
+    int N = series_length(x);
+    S.nmax = N;
+    S.a.assign(N + 2, 0.0);
+    S.b.assign(N + 2, 0.0);
+    cplx z = m * x;
+    // D_n(z), n = 0..N+1, from the exact top value downward
+    int top = N + 1;
+    std::vector<cplx> D(top + 1);
+    D[top] = 1.0 / riccati_ratio(top, z) - (double)top / z;
+    for (int n = top; n >= 1; --n)
+        D[n - 1] = (double)n / z - 1.0 / (D[n] + (double)n / z);
+    double psi0 = std::cos(x), psi1 = std::sin(x);   // psi_{n-2}, psi_{n-1}
+    double chi0 = -std::sin(x), chi1 = std::cos(x);
+    for (int n = 1; n <= N; ++n) {
+        double fn = (2.0 * n - 1.0) / x;
+        double psi = fn * psi1 - psi0;
+        double chi = fn * chi1 - chi0;
+        cplx xi(psi, -chi), xi1(psi1, -chi1);
+        cplx ea = D[n] / m + (double)n / x;
+        cplx eb = m * D[n] + (double)n / x;
+        S.a[n] = (ea * psi - psi1) / (ea * xi - xi1);
+        S.b[n] = (eb * psi - psi1) / (eb * xi - xi1);
+        if (!std::isfinite(S.a[n].real()) || !std::isfinite(S.b[n].real())) return false;
+        psi0 = psi1; psi1 = psi;
+        chi0 = chi1; chi1 = chi;
+    }
+    return true;
+}
+
+// Unnormalised phase function |S1|^2 + |S2|^2 at cos(theta) = mu.
+double phase_raw(const MieSeries &S, double mu)
+{
+    cplx s1 = 0.0, s2 = 0.0;
+    double pm1 = 0.0, pm2 = 0.0;  // pi_{n-1}, pi_{n-2}
+    for (int n = 1; n <= S.nmax; ++n) {
+        double pn = (n == 1) ? 1.0 : ((2.0 * n - 1.0) * mu * pm1 - n * pm2) / (n - 1.0);
+        double tn = n * mu * pn - (n + 1.0) * pm1;
+        double w = (2.0 * n + 1.0) / (n * (n + 1.0));
+        s1 += w * (S.a[n] * pn + S.b[n] * tn);
+        s2 += w * (S.a[n] * tn + S.b[n] * pn);
+        pm2 = pm1;
+        pm1 = pn;
+    }
+    return std::norm(s1) + std::norm(s2);
+}
+
+// 8-point Gauss-Legendre on [-1, 1].
+const double GL_X[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290,
+                        -0.1834346424956498, 0.1834346424956498, 0.5255324099163290,
+                        0.7966664774136267, 0.9602898564975363};
+const double GL_W[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873,
+                        0.3626837833783620, 0.3626837833783620, 0.3137066458778873,
+                        0.2223810344533745, 0.1012285362903763};
+
+// Density in theta, (1/2) P(cos t) sin t (unnormalised).
+double dens_theta(const MieSeries &S, double t) { return 0.5 * phase_raw(S, std::cos(t)) * std::sin(t); }
+
+// Integral of the density over theta in [t0, t1].
+double integrate(const MieSeries &S, double t0, double t1)
+{
+    double c = 0.5 * (t0 + t1), h = 0.5 * (t1 - t0), s = 0.0;
+    for (int i = 0; i < 8; ++i) s += GL_W[i] * dens_theta(S, c + h * GL_X[i]);
+    return s * h;
+}
+
+}  // namespace
+
+extern "C" size_t mc_table_bytes(int n_bins) { return mc_table_layout(n_bins, nullptr); }
+
+extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *table,
+                                     double *omu64, double *pdf64)
+{
+    if (!P) return MC_ERR_ARG;
+    mc_table_header H;
+    size_t bytes = mc_table_layout(P->n_bins, &H);
+    if (!bytes) return MC_ERR_ARG;
+    if (!(P->diameter_um > 0.0) || !(P->n_medium > 0.0) || !(P->wavelength_nm > 0.0) ||
+        !(P->n_particle_re > 0.0) || !(P->n_particle_im >= 0.0) || !std::isfinite(P->diameter_um) ||
+        !std::isfinite(P->n_particle_re) || !std::isfinite(P->n_particle_im) ||
+        !std::isfinite(P->wavelength_nm) || !std::isfinite(P->n_medium))
+        return MC_ERR_ARG;
+    const double x = kPi * P->diameter_um * P->n_medium / (P->wavelength_nm * 1e-3);
+    if (!(x >= 1e-3) || x > 2000.0) return MC_ERR_ARG;
+    const cplx m(P->n_particle_re / P->n_medium, P->n_particle_im / P->n_medium);
+
+    MieSeries S;
+    if (!mie_series(m, x, S)) return MC_ERR_NUMERIC;
+
+    double se = 0.0, ss = 0.0, sg = 0.0;
+    for (int n = 1; n <= S.nmax; ++n) {
+        se += (2.0 * n + 1.0) * (S.a[n] + S.b[n]).real();
+        ss += (2.0 * n + 1.0) * (std::norm(S.a[n]) + std::norm(S.b[n]));
+        sg += n * (n + 2.0) / (n + 1.0) *
+                  (S.a[n] * std::conj(S.a[n + 1]) + S.b[n] * std::conj(S.b[n + 1])).real() +
+              (2.0 * n + 1.0) / (n * (n + 1.0)) * (S.a[n] * std::conj(S.b[n])).real();
+    }
+    const double qext = 2.0 / (x * x) * se, qsca = 2.0 / (x * x) * ss;
+    const double g = 4.0 / (x * x) * sg / qsca;
+
+    // Panels in theta, accumulated from theta = pi (mu = -1) toward 0.
+    const int n = P->n_bins;
+    const int M = std::max(4 * n, 96 * S.nmax);
+    const double h = kPi / M;
+    std::vector<double> cum(M + 1);
+    cum[0] = 0.0;
+    for (int k = 0; k < M; ++k) {
+        double t1 = kPi - k * h, t0 = kPi - (k + 1) * h;
+        cum[k + 1] = cum[k] + integrate(S, t0, t1);
+    }
+    const double Z = cum[M];
+    if (!(Z > 0.0) || !std::isfinite(Z)) return MC_ERR_NUMERIC;
+
+    std::vector<double> theta(n + 1);
+    theta[0] = kPi;
+    theta[n] = 0.0;
+    int k = 0;
+    for (int i = 1; i < n; ++i) {
+        double target = Z * ((double)i / n);
+        while (k < M - 1 && cum[k + 1] <= target) ++k;
+        // Panel k spans theta in [pi-(k+1)h, pi-kh]; cum rises as theta falls.
+        double hi = kPi - k * h, lo = kPi - (k + 1) * h;
+        if (k == M - 1) lo = 0.0;
+        double want = target - cum[k];
+        double a = lo, b = hi;  // C(b) = 0 <= want <= C(a)
+        double t = 0.5 * (a + b);
+        for (int it = 0; it < 60; ++it) {
+            double c = integrate(S, t, hi) - want;
+            if (c > 0) a = t; else b = t;   // too much mass: move toward hi
+            double f = dens_theta(S, t);
+            double tn = (f > 0.0) ? t + c / f : 0.5 * (a + b);
+            if (!(tn > a && tn < b)) tn = 0.5 * (a + b);
+            if (std::fabs(tn - t) <= 1e-16 * (1.0 + std::fabs(t))) { t = tn; break; }
+            t = tn;
+        }
+        theta[i] = t;
+    }
+
+    std::vector<double> omu(n + 1), pdf(n);
+    for (int i = 0; i <= n; ++i) {
+        double sh = std::sin(0.5 * theta[i]);
+        omu[i] = 2.0 * sh * sh;
+    }
+    omu[0] = 2.0;
+    omu[n] = 0.0;
+    double mean = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double w = omu[j] - omu[j + 1];
+        if (!(w > 0.0)) return MC_ERR_NUMERIC;
+        pdf[j] = (1.0 / n) / w;
+        mean += 1.0 - 0.5 * (omu[j] + omu[j + 1]);
+    }
+    mean /= n;
+
+    if (info) {
+        info->x = x;
+        info->m_re = m.real();
+        info->m_im = m.imag();
+        info->qext = qext;
+        info->qsca = qsca;
+        info->qabs = qext - qsca;
+        info->g = g;
+        info->g_table = mean;
+        double geo = kPi * (P->diameter_um * 1e-3) * (P->diameter_um * 1e-3) / 4.0;
+        info->sigma_ext_mm2 = qext * geo;
+        info->sigma_sca_mm2 = qsca * geo;
+        info->sigma_abs_mm2 = (qext - qsca) * geo;
+        info->nmax = S.nmax;
+    }
+    if (omu64) std::memcpy(omu64, omu.data(), sizeof(double) * (n + 1));
+    if (pdf64) std::memcpy(pdf64, pdf.data(), sizeof(double) * n);
+    if (table) {
+        unsigned char *blob = static_cast<unsigned char *>(table);
+        std::memset(blob, 0, bytes);
+        H.g_table = (float)mean;
+        std::memcpy(blob, &H, sizeof H);
+        float *fo = reinterpret_cast<float *>(blob + H.off_omu);
+        float *fp = reinterpret_cast<float *>(blob + H.off_pdf);
+        uint16_t *gd = reinterpret_cast<uint16_t *>(blob + H.off_guide);
+        for (int i = 0; i <= n; ++i) fo[i] = (float)omu[i];
+        for (int j = 0; j < n; ++j) fp[j] = (float)pdf[j];
+        // guide[c]: bin holding cos(theta) = -1 + 2c/G (largest j with
+        // 1 - omu[j] <= that cosine), c = 0..G.
+        const int G = H.n_guide;
+        int j = 0;
+        for (int c = 0; c <= G; ++c) {
+            double mu = -1.0 + 2.0 * c / G;
+            while (j < n - 1 && 1.0 - omu[j + 1] <= mu) ++j;
+            gd[c] = (uint16_t)j;
+        }
+    }
+    return MC_OK;
+}
+
+extern "C" mc_status mc_medium_from_density(const mie_info *info, double nd, double mu_a_medium,
+                                            mc_medium *out)
+{
+    if (!info || !out || !(nd >= 0.0) || !(mu_a_medium >= 0.0) || !std::isfinite(nd) ||
+        !std::isfinite(mu_a_medium))
+        return MC_ERR_ARG;
+    // Eq. 17 per unit length: mu = n sigma.
+    out->mu_s = nd * info->sigma_sca_mm2;
+    out->mu_a = nd * info->sigma_abs_mm2 + mu_a_medium;
+    return MC_OK;
+}

@@ -1,0 +1,446 @@
+// Photon random-walk kernels for sm_103a.
+//
+// One thread carries one photon at a time (Sec. 2.7); a warp refills lanes
+// whose photon ended from a per-warp pool of photon indices, taken in chunks
+// from a global counter, so lanes stay busy until the whole range is done.
+// Each event draws four uniforms from Philox4x32-10 keyed by
+// (seed; photon, event), so results do not depend on which thread ran which
+// photon. Per event (Sec. 2.6, Sec. 3.1.3):
+//   free path s = -ln(u0)/mu_ext (Eq. 15); a flight that reaches a wall
+//   leaves the index-matched cuvette there; otherwise the photon collides:
+//   implicit capture w <- w (1 - mu_a/mu_ext) (Eq. 16), a next-event estimate
+//   for the side camera (Sec. 4.3), a polar angle from the inverse-CDF table
+//   (Sec. 2.6, Sec. 3.1.2) or from H-G (Eq. 11), an azimuth uniform in
+//   [0, 2 pi), the direction update, and the weight threshold with roulette.
+// Tallies are 64-bit fixed point: each contribution is rounded once, and
+// integer sums do not depend on order, so images are bit-reproducible.
+// The table is staged into shared memory once per CTA by a bulk async copy
+// (cp.async.bulk + mbarrier, bounded wait).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "engine.h"
+#include "table_format.h"
+
+namespace mcx {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int CHUNK = 128;            // photons a warp takes from the counter at once
+constexpr float INV_2PI = 0.159154943091895335768883763372514f;
+constexpr float W_SCALE = 4294967296.0f;   // 2^32, weight tallies
+constexpr uint32_t WAIT_LIMIT = 1u << 22;  // mbarrier polls before giving up
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): per round
+//   (c0,c1,c2,c3) <- (hi(M1 c2)^c1^k0, lo(M1 c2), hi(M0 c0)^c3^k1, lo(M0 c0)),
+// then k += (0x9E3779B9, 0xBB67AE85).
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// (r >> 9) 2^-23 + 2^-24, exact: the float 1 + (r>>9) 2^-23 minus (1 - 2^-24).
+__device__ __forceinline__ float u01(uint32_t r)
+{
+    return __int_as_float(0x3F800000u | (r >> 9)) - 0.999999940395355224609375f;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ long long fix32(float w) { return __float2ll_rn(w * W_SCALE); }
+
+// Bulk-copy `bytes` (multiple of 16) from global to shared memory, bounded wait.
+__device__ bool stage_bulk(void *dst, const void *src, uint32_t bytes, unsigned long long *mbar,
+                           uint32_t *err)
+{
+    const uint32_t bar = smem_u32(mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(dst)),
+            "l"(src), "r"(bytes), "r"(bar)
+            : "memory");
+    }
+    __syncthreads();
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < WAIT_LIMIT && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+    }
+    if (!done && threadIdx.x == 0) atomicOr(err, MC_EFLAG_TIMEOUT);
+    return __syncthreads_and(done) != 0;
+}
+
+// Table bin j with omu[j] >= omu_c > omu[j+1], i.e. icdf[j] <= mu_c < icdf[j+1].
+__device__ __forceinline__ int table_bin(const float *omu, const uint16_t *guide, int n, float muc)
+{
+    muc = fminf(fmaxf(muc, -1.0f), 1.0f);
+    int cell = min(__float2int_rd((muc + 1.0f) * (0.5f * n)), n - 1);
+    int lo = max((int)guide[cell] - 1, 0);
+    int hi = min((int)guide[cell + 1] + 1, n - 1);
+    const float om = 1.0f - muc;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (omu[mid] >= om) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool TRACE>
+__device__ __forceinline__ void trace_write(const WalkArgs &A, unsigned long long rel, uint32_t ev,
+                                            int status, float rx, float ry, float rz, float dx,
+                                            float dy, float dz, float w, float nee, int pix, int nb,
+                                            int rb)
+{
+    if (!TRACE) return;
+    if (rel >= (unsigned long long)A.n_trace || ev >= (uint32_t)A.n_trace_events) return;
+    int32_t *t = A.trace + (rel * A.n_trace_events + ev) * 12;
+    t[0] = status;
+    t[1] = __float_as_int(rx); t[2] = __float_as_int(ry); t[3] = __float_as_int(rz);
+    t[4] = __float_as_int(dx); t[5] = __float_as_int(dy); t[6] = __float_as_int(dz);
+    t[7] = __float_as_int(w);
+    t[8] = __float_as_int(nee);
+    t[9] = pix; t[10] = nb; t[11] = rb;
+}
+
+// Shared-memory layout: [table blob][image tile][radial][totals][mbarrier]
+template <int PHASE, bool SMEM_IMAGE, bool TRACE>
+__global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ WalkArgs A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint32_t tb = (PHASE == MC_PHASE_TABLE) ? A.table_bytes : 0u;
+    const int npix = A.nx * A.nz;
+    unsigned long long *s_img = reinterpret_cast<unsigned long long *>(smem + tb);
+    unsigned long long *s_rad = s_img + (SMEM_IMAGE ? npix : 0);
+    unsigned long long *s_tot = s_rad + A.n_radial;
+    unsigned long long *s_bar = s_tot + MC_N_TOTALS;
+
+    for (int i = threadIdx.x; i < (SMEM_IMAGE ? npix : 0) + A.n_radial + MC_N_TOTALS; i += blockDim.x)
+        s_img[i] = 0ull;
+
+    const float *omu = nullptr, *pdf = nullptr;
+    const uint16_t *guide = nullptr;
+    if (PHASE == MC_PHASE_TABLE) {
+        if (!stage_bulk(smem, A.table, tb, s_bar, A.error)) return;
+        const mc_table_header *h = reinterpret_cast<const mc_table_header *>(smem);
+        if (h->magic != MC_TABLE_MAGIC || h->n_bins != A.n_bins || h->total_bytes != tb) {
+            if (threadIdx.x == 0) atomicOr(A.error, MC_EFLAG_TABLE);
+            return;
+        }
+        omu = reinterpret_cast<const float *>(smem + h->off_omu);
+        pdf = reinterpret_cast<const float *>(smem + h->off_pdf);
+        guide = reinterpret_cast<const uint16_t *>(smem + h->off_guide);
+    } else {
+        __syncthreads();
+    }
+
+    const int lane = threadIdx.x & 31;
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+    unsigned long long pool_next = 0, pool_end = 0;  // warp-uniform
+
+    // photon state
+    bool alive = false, done = false;
+    unsigned long long rel = 0;     // index within the range
+    uint32_t pk0 = 0, pk1 = 0;      // global photon index, lo/hi words
+    uint32_t ev = 0, ncoll = 0;
+    float rx = 0, ry = 0, rz = 0, dx = 1, dy = 0, dz = 0, w = 1;
+    unsigned long long my_steps = 0;
+    long long my_abs = 0;
+
+    while (true) {
+        // -------- refill lanes whose photon ended
+        const unsigned need = __ballot_sync(FULL, !alive && !done);
+        if (need) {
+            const unsigned n_need = __popc(need);
+            const unsigned rank = __popc(need & lanemask_lt);
+            const unsigned long long avail = pool_end - pool_next;
+            unsigned long long mine;
+            if (avail >= n_need) {
+                mine = pool_next + rank;
+                pool_next += n_need;
+            } else {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(A.counter, (unsigned long long)CHUNK);
+                base = __shfl_sync(FULL, base, 0);
+                mine = (rank < avail) ? pool_next + rank : base + (rank - avail);
+                pool_next = base + (n_need - avail);
+                pool_end = base + CHUNK;
+            }
+            if (!alive && !done) {
+                if (mine < A.n_photons) {
+                    rel = mine;
+                    const unsigned long long p = A.photon_offset + mine;
+                    pk0 = (uint32_t)p;
+                    pk1 = (uint32_t)(p >> 32);
+                    ev = 0;
+                    ncoll = 0;
+                    rx = 0.f; ry = 0.f; rz = 0.f;
+                    dx = 1.f; dy = 0.f; dz = 0.f;
+                    w = 1.f;
+                    if (A.beam_r > 0.f) {
+                        const uint4 b = philox10(make_uint4(pk0, pk1, 0xFFFFFFFFu, 0u), A.key0, A.key1);
+                        const float rho = A.beam_r * sqrtf(u01(b.x));
+                        float sp, cp;
+                        sincospif(2.0f * u01(b.y), &sp, &cp);
+                        ry = rho * cp;
+                        rz = rho * sp;
+                    }
+                    alive = true;
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, alive)) break;
+        if (!alive) continue;
+
+        // -------- one event
+        const uint32_t e_now = ev;
+        const uint4 rnd = philox10(make_uint4(pk0, pk1, e_now, 0u), A.key0, A.key1);
+        ++ev;
+        ++my_steps;
+        const float u0 = u01(rnd.x), u1 = u01(rnd.y), u2 = u01(rnd.z), u3 = u01(rnd.w);
+
+        const float s = -logf(u0) * A.inv_mu_ext;                 // Eq. 15
+        const float px = fmaf(s, dx, rx), py = fmaf(s, dy, ry), pz = fmaf(s, dz, rz);
+        const bool inside = (px > 0.f) & (px < A.lx) & (fabsf(py) < A.hy) & (fabsf(pz) < A.hz);
+
+        if (!inside) {
+            // leave through the first wall on the way (ties: lowest axis)
+            const float INF = __int_as_float(0x7f800000);
+            const float tx = dx > 0.f ? (A.lx - rx) / dx : (dx < 0.f ? (0.f - rx) / dx : INF);
+            const float ty = dy > 0.f ? (A.hy - ry) / dy : (dy < 0.f ? (-A.hy - ry) / dy : INF);
+            const float tz = dz > 0.f ? (A.hz - rz) / dz : (dz < 0.f ? (-A.hz - rz) / dz : INF);
+            int face;
+            float t;
+            if (tx <= ty && tx <= tz) { face = 0; t = tx; }
+            else if (ty <= tz) { face = 1; t = ty; }
+            else { face = 2; t = tz; }
+            const float ex = fmaf(t, dx, rx), ey = fmaf(t, dy, ry), ez = fmaf(t, dz, rz);
+            const long long wv = fix32(w);
+            int status, rb = -1;
+            if (face == 0 && dx < 0.f) {
+                atomicAdd(&s_tot[MC_TOT_REFLECT], (unsigned long long)wv);
+                status = 1;
+            } else if (face == 0) {
+                atomicAdd(&s_tot[MC_TOT_FAR], (unsigned long long)wv);
+                if (ncoll == 0) atomicAdd(&s_tot[MC_TOT_BALLISTIC], (unsigned long long)wv);
+                const float rho = sqrtf(fmaf(ey, ey, ez * ez));
+                rb = min(__float2int_rd(rho * A.sr), A.n_radial - 1);
+                atomicAdd(&s_rad[rb], (unsigned long long)wv);
+                status = 2;
+            } else {
+                atomicAdd(&s_tot[MC_TOT_SIDE], (unsigned long long)wv);
+                status = 3;
+            }
+            trace_write<TRACE>(A, rel, e_now, status, ex, ey, ez, dx, dy, dz, w, 0.f, -1, -1, rb);
+            alive = false;
+            continue;
+        }
+
+        // -------- collision
+        rx = px; ry = py; rz = pz;
+        ++ncoll;
+        if (A.absorb_frac > 0.f) my_abs += fix32(w * A.absorb_frac);
+        w = w * A.albedo;                                            // Eq. 16
+
+        // camera: next-event estimate toward +y
+        float psr;
+        int nb = -1;
+        if (PHASE == MC_PHASE_HG) {
+            const float t = fmaf(A.hg_two_g, 1.0f - dy, A.hg_a2);
+            psr = A.hg_K / (t * sqrtf(t));
+        } else {
+            nb = table_bin(omu, guide, A.n_bins, dy);
+            psr = pdf[nb] * INV_2PI;
+        }
+        const float nee = w * psr * expf(-A.mu_ext * (A.hy - ry));
+        const int ix = min(max(__float2int_rd(rx * A.sx), 0), A.nx - 1);
+        const int iz = min(max(__float2int_rd((rz + A.hz) * A.sz), 0), A.nz - 1);
+        const int pix = iz * A.nx + ix;
+        const float vf = nee * A.img_scale;
+        if (vf < 4.0e18f) {
+            const long long v = __float2ll_rn(vf);
+            if (SMEM_IMAGE) atomicAdd(&s_img[pix], (unsigned long long)v);
+            else atomicAdd(&A.image[pix], (unsigned long long)v);
+        } else {
+            atomicOr(A.error, (vf == vf) ? MC_EFLAG_OVERFLOW : MC_EFLAG_NUMERIC);
+        }
+
+        int status = 0;
+        if (A.max_scatter && ncoll >= A.max_scatter) {
+            atomicAdd(&s_tot[MC_TOT_TRUNC], (unsigned long long)fix32(w));
+            status = 5;
+            alive = false;
+        } else {
+            // polar angle as 1 - cos(theta), accurate near the forward peak
+            float om;
+            if (PHASE == MC_PHASE_HG) {
+                const float D = fmaf(A.hg_two_g, u1, A.hg_one_m_g);
+                om = A.hg_A * (1.0f - u1) * fmaf(A.hg_g, u1, 1.0f) / (D * D);
+            } else {
+                const float tt = u1 * (float)A.n_bins;
+                const int i = (int)tt;
+                const float f = tt - (float)i;
+                const float o0 = omu[i], o1 = omu[i + 1];
+                om = fmaf(f, o1 - o0, o0);
+            }
+            const float mu = 1.0f - om;
+            const float st = sqrtf(fmaxf(om * (2.0f - om), 0.0f));
+            float sp, cp;
+            sincospif(2.0f * u2, &sp, &cp);
+            // orthonormal basis around d (Duff et al. 2017)
+            const float sg = copysignf(1.0f, dz);
+            const float a = -__frcp_rn(sg + dz);
+            const float b = dx * dy * a;
+            const float e1x = fmaf(sg * dx * dx, a, 1.0f), e1y = sg * b, e1z = -sg * dx;
+            const float e2x = b, e2y = fmaf(dy * dy, a, sg), e2z = -dy;
+            const float qx = fmaf(cp, e1x, sp * e2x), qy = fmaf(cp, e1y, sp * e2y),
+                        qz = fmaf(cp, e1z, sp * e2z);
+            float nx = fmaf(mu, dx, st * qx), ny = fmaf(mu, dy, st * qy), nz = fmaf(mu, dz, st * qz);
+            const float inv = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+            dx = nx * inv; dy = ny * inv; dz = nz * inv;
+            // weight threshold / roulette (Sec. 3.1.3)
+            if (w < A.rr_thr) {
+                if (u3 < A.rr_surv) {
+                    const float wn = w * A.inv_rr_surv;
+                    atomicAdd(&s_tot[MC_TOT_ROULETTE], (unsigned long long)(fix32(w) - fix32(wn)));
+                    w = wn;
+                } else {
+                    atomicAdd(&s_tot[MC_TOT_ROULETTE], (unsigned long long)fix32(w));
+                    status = 4;
+                    alive = false;
+                }
+            }
+            if (!(w == w)) atomicOr(A.error, MC_EFLAG_NUMERIC);
+        }
+        trace_write<TRACE>(A, rel, e_now, status, rx, ry, rz, dx, dy, dz, status == 4 ? 0.f : w, nee,
+                           pix, nb, -1);
+        if (alive && ev >= A.max_events) {
+            atomicAdd(&s_tot[MC_TOT_TRUNC], (unsigned long long)fix32(w));
+            atomicOr(A.error, MC_EFLAG_EVENTS);
+            trace_write<TRACE>(A, rel, ev, 6, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1, -1);
+            alive = false;
+        }
+    }
+
+    // -------- per-thread counters -> shared -> global
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_steps += __shfl_xor_sync(FULL, my_steps, o);
+        my_abs += __shfl_xor_sync(FULL, my_abs, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&s_tot[MC_TOT_STEPS], my_steps);
+        if (my_abs) atomicAdd(&s_tot[MC_TOT_ABSORB], (unsigned long long)my_abs);
+    }
+    __syncthreads();
+    if (SMEM_IMAGE)
+        for (int i = threadIdx.x; i < npix; i += blockDim.x)
+            if (s_img[i]) atomicAdd(&A.image[i], s_img[i]);
+    for (int i = threadIdx.x; i < A.n_radial; i += blockDim.x)
+        if (s_rad[i]) atomicAdd(&A.radial[i], s_rad[i]);
+    for (int i = threadIdx.x; i < MC_N_TOTALS; i += blockDim.x)
+        if (s_tot[i]) atomicAdd(&A.totals[i], s_tot[i]);
+}
+
+__global__ void philox_kernel(const uint4 *ctr, uint64_t n, uint32_t k0, uint32_t k1, uint4 *out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = philox10(ctr[i], k0, k1);
+}
+
+template <int PHASE, bool SMEM_IMAGE, bool TRACE>
+cudaError_t launch_one(const WalkArgs &a, const LaunchCfg &cfg, size_t smem, cudaStream_t st)
+{
+    auto kern = walk_kernel<PHASE, SMEM_IMAGE, TRACE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, bps = cfg.blocks_per_sm;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (bps <= 0) {
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, cfg.block, smem)) != cudaSuccess)
+            return e;
+        if (bps < 1) return cudaErrorInvalidConfiguration;
+    }
+    unsigned long long blocks = (unsigned long long)sms * bps;
+    // no more warps than photons need (small runs)
+    unsigned long long warps_needed = (a.n_photons + CHUNK - 1) / CHUNK;
+    unsigned long long per_block = cfg.block / 32;
+    unsigned long long cap = (warps_needed + per_block - 1) / per_block;
+    if (cap < blocks) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, cfg.block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_walk(const WalkArgs &a, bool trace, const LaunchCfg &cfg, cudaStream_t st)
+{
+    const size_t tb = (a.phase_kind == MC_PHASE_TABLE) ? a.table_bytes : 0;
+    const size_t tail = sizeof(unsigned long long) * (a.n_radial + MC_N_TOTALS + 1);
+    const size_t img = sizeof(unsigned long long) * (size_t)a.nx * a.nz;
+    int dev = 0, optin = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return e;
+    // auto: the image tile lives in shared memory when two CTAs still fit per SM
+    bool smem_img;
+    if (cfg.image_mode == 1) {
+        smem_img = true;
+        if (tb + img + tail > (size_t)optin) return cudaErrorInvalidValue;
+    } else if (cfg.image_mode == 2) {
+        smem_img = false;
+    } else {
+        smem_img = (tb + img + tail) <= (size_t)optin / 2 - 1024;
+    }
+    const size_t smem = tb + tail + (smem_img ? img : 0);
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;
+    const bool table = a.phase_kind == MC_PHASE_TABLE;
+    if (trace) {
+        if (table) return smem_img ? launch_one<0, true, true>(a, cfg, smem, st)
+                                   : launch_one<0, false, true>(a, cfg, smem, st);
+        return smem_img ? launch_one<1, true, true>(a, cfg, smem, st)
+                        : launch_one<1, false, true>(a, cfg, smem, st);
+    }
+    if (table) return smem_img ? launch_one<0, true, false>(a, cfg, smem, st)
+                               : launch_one<0, false, false>(a, cfg, smem, st);
+    return smem_img ? launch_one<1, true, false>(a, cfg, smem, st)
+                    : launch_one<1, false, false>(a, cfg, smem, st);
+}
+
+cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    philox_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const uint4 *>(ctr), n, (uint32_t)seed,
+                                          (uint32_t)(seed >> 32), reinterpret_cast<uint4 *>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace mcx

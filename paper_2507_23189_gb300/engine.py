@@ -1,0 +1,268 @@
+"""Python face of the engine: PyTorch holds the device memory and streams;
+every step of the walk runs in libmcmie.so through the C ABI.
+
+    table = PhaseTable(diameter_um=5.0, n_particle=1.59, n_medium=1.33, wavelength_nm=532.0)
+    med = Medium.from_optical_depth(table, tau=5.0, length_mm=45.0)
+    eng = Engine(Camera(256, 256), Geometry())
+    eng.run(med, n_photons=10**8, seed=1)
+    out = eng.result()          # image/radial/totals as float64 weight units
+"""
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _native as N
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# --------------------------------------------------------------------- table
+
+
+class PhaseTable:
+    """Lorenz-Mie phase table built on the host in double precision
+    (mie_table_build), with a cached device copy of the packed blob."""
+
+    def __init__(self, diameter_um=5.0, n_particle=1.59 + 0j, n_medium=1.33, wavelength_nm=532.0,
+                 n_bins=4096):
+        L = N.lib()
+        n_particle = complex(n_particle)
+        p = N.MieParams(diameter_um, n_particle.real, n_particle.imag, n_medium, wavelength_nm, n_bins)
+        info = N.MieInfo()
+        nbytes = L.mc_table_bytes(n_bins)
+        if nbytes == 0:
+            raise N.McError("mc_table_bytes", -1)
+        self.blob = np.zeros(nbytes, dtype=np.uint8)
+        self.omu64 = np.zeros(n_bins + 1)
+        self.pdf64 = np.zeros(n_bins)
+        dp = C.POINTER(C.c_double)
+        N.check("mie_table_build", L.mie_table_build(
+            C.byref(p), C.byref(info), self.blob.ctypes.data_as(C.c_void_p),
+            self.omu64.ctypes.data_as(dp), self.pdf64.ctypes.data_as(dp)))
+        self.params = dict(diameter_um=diameter_um, n_particle=n_particle, n_medium=n_medium,
+                           wavelength_nm=wavelength_nm, n_bins=n_bins)
+        self.info = info.as_dict()
+        self.n_bins = n_bins
+        self._dev = {}
+
+    @property
+    def icdf64(self):
+        return 1.0 - self.omu64
+
+    def device_blob(self, device=None):
+        torch = _torch()
+        dev = torch.device(device if device is not None else "cuda")
+        key = str(dev)
+        if key not in self._dev:
+            self._dev[key] = torch.from_numpy(self.blob).to(dev)
+        return self._dev[key]
+
+
+# -------------------------------------------------------------------- medium
+
+
+@dataclass
+class Medium:
+    mu_s: float
+    mu_a: float = 0.0
+    phase: str = "table"   # "table" (Mie inverse CDF) or "hg"
+    hg_g: float = 0.0
+    table: PhaseTable = None
+
+    @classmethod
+    def from_density(cls, table, number_density_per_mm3, mu_a_medium=0.0, phase="table", hg_g=None):
+        """Eq. 17: coefficients from number density and the Mie cross sections."""
+        info = N.MieInfo(**{k: table.info[k] for k, _ in N.MieInfo._fields_})
+        m = N.Medium()
+        N.check("mc_medium_from_density", N.lib().mc_medium_from_density(
+            C.byref(info), number_density_per_mm3, mu_a_medium, C.byref(m)))
+        g = table.info["g"] if hg_g is None else hg_g
+        return cls(m.mu_s, m.mu_a, phase, g, table)
+
+    @classmethod
+    def from_optical_depth(cls, table, tau, length_mm=45.0, mu_a_medium=0.0, phase="table", hg_g=None):
+        """Number density giving optical depth tau over length_mm (Eq. 17)."""
+        n = tau / (table.info["sigma_ext_mm2"] * length_mm)
+        return cls.from_density(table, n, mu_a_medium, phase, hg_g)
+
+    def as_c(self, device=None):
+        m = N.Medium()
+        m.mu_s, m.mu_a = self.mu_s, self.mu_a
+        if self.phase == "table":
+            m.phase_kind = N.PHASE_TABLE
+            blob = self.table.device_blob(device)
+            m.d_table = blob.data_ptr()
+            m.n_bins = self.table.n_bins
+            return m, blob
+        if self.phase == "hg":
+            m.phase_kind = N.PHASE_HG
+            m.hg_g = self.hg_g
+            return m, None
+        raise ValueError("phase must be 'table' or 'hg'")
+
+
+@dataclass
+class Geometry:
+    lx: float = 45.0
+    ly: float = 10.0
+    lz: float = 10.0
+    beam_radius: float = 0.0
+
+    def as_c(self):
+        return N.Geometry(self.lx, self.ly, self.lz, self.beam_radius)
+
+
+@dataclass
+class Camera:
+    nx: int = 64
+    nz: int = 64
+    n_radial: int = 128
+    r_max: float = 5.0 * 2 ** 0.5
+
+    def as_c(self):
+        return N.Camera(self.nx, self.nz, self.n_radial, self.r_max)
+
+
+def run_params(n_photons, seed=1, photon_offset=0, rr_threshold=1e-4, rr_survival=0.1,
+               max_events=1_000_000, max_scatter=0, image_frac_bits=32, accumulate=False,
+               block_size=0, blocks_per_sm=0, image_mode=0):
+    return N.RunParams(int(n_photons), int(photon_offset), int(seed), rr_threshold, rr_survival,
+                       int(max_events), int(max_scatter), int(image_frac_bits), int(bool(accumulate)),
+                       int(block_size), int(blocks_per_sm), int(image_mode))
+
+
+# -------------------------------------------------------------------- engine
+
+
+class Engine:
+    """Device tallies for one camera/geometry; runs photon batches into them."""
+
+    def __init__(self, camera=None, geometry=None, device=None):
+        torch = _torch()
+        self.camera = camera or Camera()
+        self.geometry = geometry or Geometry()
+        self.device = torch.device(device if device is not None else "cuda")
+        cam = self.camera
+        L = N.lib()
+        wb = L.mc_workspace_bytes(C.byref(cam.as_c()))
+        if wb == 0:
+            raise N.McError("mc_workspace_bytes", -1)
+        dev = self.device
+        self.image = torch.zeros((cam.nz, cam.nx), dtype=torch.int64, device=dev)
+        self.radial = torch.zeros(cam.n_radial, dtype=torch.int64, device=dev)
+        self.totals = torch.zeros(N.N_TOTALS, dtype=torch.int64, device=dev)
+        self.error = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.work = torch.zeros(wb, dtype=torch.uint8, device=dev)
+        self.image_frac_bits = 32
+
+    def _tallies(self):
+        return N.Tallies(self.image.data_ptr(), self.radial.data_ptr(), self.totals.data_ptr(),
+                         self.error.data_ptr(), self.work.data_ptr(), self.work.numel())
+
+    def run(self, medium, n_photons, seed=1, stream=None, **kw):
+        """Queue photons on the stream (asynchronous)."""
+        rp = run_params(n_photons, seed, **kw)
+        self.image_frac_bits = rp.image_frac_bits
+        m, keep = medium.as_c(self.device)
+        g, c, t = self.geometry.as_c(), self.camera.as_c(), self._tallies()
+        N.check("mc_run", N.lib().mc_run(C.byref(m), C.byref(g), C.byref(c), C.byref(rp), C.byref(t),
+                                         _stream_handle(stream)))
+        self._keep = keep
+        return self
+
+    def trace(self, medium, n_photons, n_trace, n_events=32, seed=1, stream=None, **kw):
+        """Run with a per-event trace of the first n_trace photons; returns
+        an int32 tensor [n_trace, n_events, 12] (float fields bit-cast)."""
+        torch = _torch()
+        rp = run_params(n_photons, seed, **kw)
+        self.image_frac_bits = rp.image_frac_bits
+        m, keep = medium.as_c(self.device)
+        buf = torch.empty((n_trace, n_events, N.TRACE_WORDS), dtype=torch.int32, device=self.device)
+        g, c, t = self.geometry.as_c(), self.camera.as_c(), self._tallies()
+        N.check("mc_trace", N.lib().mc_trace(C.byref(m), C.byref(g), C.byref(c), C.byref(rp),
+                                             C.byref(t), C.c_void_p(buf.data_ptr()), n_trace, n_events,
+                                             _stream_handle(stream)))
+        self._keep = keep
+        return buf
+
+    def check(self, stream=None):
+        """Wait for the stream and raise if a kernel flagged an error."""
+        N.check("mc_check", N.lib().mc_check(C.c_void_p(self.error.data_ptr()), _stream_handle(stream)))
+
+    def result(self):
+        """Tallies as float64 numpy arrays in weight units (one photon = 1)."""
+        img = self.image.cpu().numpy().astype(np.float64) * 2.0 ** -self.image_frac_bits
+        rad = self.radial.cpu().numpy().astype(np.float64) * 2.0 ** -N.WEIGHT_FRAC_BITS
+        tot = self.totals.cpu().numpy()
+        w = tot[:7].astype(np.float64) * 2.0 ** -N.WEIGHT_FRAC_BITS
+        return dict(image=img, radial=rad, totals=w, steps=int(tot[N.TOT_STEPS]),
+                    raw_image=self.image.cpu().numpy(), raw_totals=tot,
+                    error=int(self.error.cpu().numpy()[0]))
+
+
+def decode_trace(buf):
+    """int32 [.., 12] trace -> dict of numpy arrays."""
+    a = buf.cpu().numpy() if hasattr(buf, "cpu") else np.asarray(buf)
+    f = a.view(np.float32)
+    return dict(status=a[..., 0], r=f[..., 1:4].astype(np.float64), d=f[..., 4:7].astype(np.float64),
+                w=f[..., 7].astype(np.float64), nee=f[..., 8].astype(np.float64), pix=a[..., 9],
+                nee_bin=a[..., 10], rad_bin=a[..., 11])
+
+
+def run_host(medium, geometry, camera, n_photons, d_work, seed=1, stream=None, image=None,
+             radial=None, totals=None, table_host=None, **kw):
+    """End-to-end call with host buffers (mc_run_host): table in, tallies out.
+    `d_work` is a device uint8 tensor of host_workspace_bytes() bytes; the
+    host outputs (numpy int64, pinned for speed) are allocated if not given;
+    `table_host` replaces the table's own host blob (e.g. a pinned copy)."""
+    L = N.lib()
+    m = N.Medium()
+    m.mu_s, m.mu_a = medium.mu_s, medium.mu_a
+    table_ptr = None
+    if medium.phase == "table":
+        m.phase_kind, m.n_bins = N.PHASE_TABLE, medium.table.n_bins
+        blob = medium.table.blob if table_host is None else table_host
+        if blob.nbytes != medium.table.blob.nbytes:
+            raise ValueError("table_host has the wrong size")
+        table_ptr = blob.ctypes.data_as(C.c_void_p)
+    else:
+        m.phase_kind, m.hg_g = N.PHASE_HG, medium.hg_g
+    image = image if image is not None else np.zeros((camera.nz, camera.nx), dtype=np.int64)
+    radial = radial if radial is not None else np.zeros(camera.n_radial, dtype=np.int64)
+    totals = totals if totals is not None else np.zeros(N.N_TOTALS, dtype=np.int64)
+    err = np.zeros(1, dtype=np.uint32)
+    rp = run_params(n_photons, seed, **kw)
+    g, c = geometry.as_c(), camera.as_c()
+    vp = C.c_void_p
+    st = L.mc_run_host(C.byref(m), table_ptr, C.byref(g), C.byref(c), C.byref(rp),
+                       image.ctypes.data_as(vp), radial.ctypes.data_as(vp), totals.ctypes.data_as(vp),
+                       err.ctypes.data_as(vp), vp(d_work.data_ptr()), d_work.numel(), _stream_handle(stream))
+    N.check("mc_run_host", st)
+    return image, radial, totals
+
+
+def host_workspace_bytes(medium, camera):
+    m = N.Medium()
+    m.phase_kind = N.PHASE_TABLE if medium.phase == "table" else N.PHASE_HG
+    m.n_bins = medium.table.n_bins if medium.phase == "table" else 0
+    return N.lib().mc_host_workspace_bytes(C.byref(m), C.byref(camera.as_c()))
+
+
+def philox(ctr, seed, stream=None):
+    """Device Philox4x32-10 of a uint32-valued int64/int32 tensor [n, 4]."""
+    torch = _torch()
+    c = ctr.to(torch.int32).contiguous()
+    out = torch.empty_like(c)
+    N.check("mc_philox", N.lib().mc_philox(C.c_void_p(c.data_ptr()), c.shape[0], int(seed),
+                                           C.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out

@@ -1,0 +1,70 @@
+"""Seeded synthetic workloads (inputs only; none of the method's arithmetic).
+
+They stand in for the paper's simulations of 5 um polystyrene spheres in
+water at 532 nm in a cuvette imaged by a 90-degree side camera (Sec. 4,
+Sec. 5.2: 3e8 photons at optical depths 5-12.5); the paper's experimental
+images are not used.
+
+  small       10x10x45 mm cuvette, tau = 1, 1e6 photons, 64x64 image, Mie and H-G
+  sweep       tau in {1, 2, 5, 10, 20}, Mie and H-G, 1e8 photons,
+              256x256 image + 128-bin radial profile (headline: tau = 5, Mie)
+  batched     64 media: d log-uniform in [1, 10] um, tau uniform in [0.5, 20],
+              photon budgets log-uniform in [1e6, 1e8], 128x128 images
+  adjoint     tau = 5, Mie, 1e7 photons, 128x128; target at 0.9 mu_s0, mu_a = 0.01
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+CUVETTE_MM = (45.0, 10.0, 10.0)   # beam axis x, then y (camera side), z
+N_MEDIUM = 1.33
+N_PARTICLE = complex(1.59, 0.0)
+DIAMETER_UM = 5.0
+WAVELENGTH_NM = 532.0
+N_BINS = 4096
+RR_THRESHOLD = 1e-4
+RR_SURVIVAL = 0.1
+R_MAX = 5.0 * 2 ** 0.5            # radial profile covers the far face's half-diagonal
+
+
+@dataclass
+class Case:
+    name: str
+    tau: float
+    phase: str                    # "mie" or "hg" (H-G with g from the Mie table)
+    n_photons: int
+    nx: int
+    nz: int
+    n_radial: int = 128
+    seed: int = 1
+    diameter_um: float = DIAMETER_UM
+    extra: dict = field(default_factory=dict)
+
+
+def small():
+    return [Case("small-%s" % p, 1.0, p, 1_000_000, 64, 64) for p in ("mie", "hg")]
+
+
+def sweep(taus=(1.0, 2.0, 5.0, 10.0, 20.0), n_photons=100_000_000):
+    return [Case("sweep-tau%g-%s" % (t, p), t, p, n_photons, 256, 256)
+            for t in taus for p in ("mie", "hg")]
+
+
+def headline(n_photons=100_000_000):
+    """The optical-depth sweep's tau = 5 Mie point."""
+    return Case("sweep-tau5-mie", 5.0, "mie", n_photons, 256, 256)
+
+
+def batched(n=64, seed=2026):
+    """Instance parameters from numpy's Philox (a 64-bit counter-based stream)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    d = np.exp(rng.uniform(np.log(1.0), np.log(10.0), n))
+    tau = rng.uniform(0.5, 20.0, n)
+    nph = np.exp(rng.uniform(np.log(1e6), np.log(1e8), n)).astype(np.int64)
+    return [Case("batched-%02d" % i, float(tau[i]), "mie", int(nph[i]), 128, 128, seed=1,
+                 diameter_um=float(d[i])) for i in range(n)]
+
+
+def adjoint():
+    return Case("adjoint-tau5-mie", 5.0, "mie", 10_000_000, 128, 128,
+                extra=dict(mu_s_factor=0.9, mu_a=0.01))

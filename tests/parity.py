@@ -1,0 +1,104 @@
+"""Comparison rules shared by the GPU parity tests.
+
+Trace rule: the first 32 events of every photon must agree with the
+double-precision oracle within 1e-5 relative (positions relative to the
+cuvette length, directions absolutely, weights and camera contributions
+relative). A discrete decision (wall hit, exit face, pixel, table bin,
+roulette) may differ only where the oracle's branch quantity lies within
+1e-5 of its threshold; that photon's later events are then excluded.
+At least 99.9 % of photons must match.
+
+Tally rule: every image bin within 3 sigma of the oracle's estimate, and a
+pooled chi-square over well-populated bins with p > 0.01.
+"""
+import math
+
+import numpy as np
+
+TOL = 1e-5
+
+
+def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL):
+    """g: decode_trace() dict of the GPU trace; o: oracle trace array
+    [n, ev, 13]. Returns dict(n, matched, flips, bad, worst...)."""
+    n, ev = o.shape[0], o.shape[1]
+    st_o = o[..., 0].astype(int)
+    worst = dict(pos=0.0, dir=0.0, w=0.0, nee=0.0)
+    bad, flips, checked_events = [], 0, 0
+    for p in range(n):
+        ok = True
+        for e in range(ev):
+            so, sg = st_o[p, e], int(g["status"][p, e])
+            if so < 0 and sg < 0:
+                break
+            rec = o[p, e]
+            margin = rec[12]
+            disc_o = (so, int(rec[9]), int(rec[10]), int(rec[11]))
+            disc_g = (sg, int(g["pix"][p, e]), int(g["nee_bin"][p, e]), int(g["rad_bin"][p, e]))
+            if disc_o != disc_g:
+                if margin < tol:
+                    flips += 1
+                    break
+                ok = False
+                break
+            if so == 6:
+                break
+            checked_events += 1
+            dpos = float(np.max(np.abs(g["r"][p, e] - rec[1:4])))
+            ddir = float(np.max(np.abs(g["d"][p, e] - rec[4:7])))
+            dw = abs(g["w"][p, e] - rec[7]) / max(abs(rec[7]), 1e-300) if rec[7] else abs(g["w"][p, e])
+            dnee_abs = abs(g["nee"][p, e] - rec[8])
+            # the camera term depends on r_y through exp(-mu_ext (ly/2 - r_y))
+            dnee = dnee_abs / rec[8] if rec[8] else dnee_abs
+            nee_tol = tol + mu_ext * dpos
+            worst["pos"] = max(worst["pos"], dpos / lx)
+            worst["dir"] = max(worst["dir"], ddir)
+            worst["w"] = max(worst["w"], dw)
+            worst["nee"] = max(worst["nee"], dnee)
+            if dpos > tol * lx or ddir > tol or dw > tol or dnee > nee_tol:
+                if margin < tol:
+                    flips += 1
+                    break
+                ok = False
+                break
+            if so != 0:
+                break
+        if not ok:
+            bad.append(p)
+    return dict(n=n, matched=n - len(bad), flips=flips, bad=bad[:20], worst=worst,
+                events=checked_events)
+
+
+def chi2_sf(x, k):
+    """Survival function of the chi-square distribution (Wilson-Hilferty
+    approximation for large k, exact series otherwise via scipy if present)."""
+    try:
+        from scipy.stats import chi2
+        return float(chi2.sf(x, k))
+    except Exception:  # pragma: no cover
+        z = ((x / k) ** (1 / 3) - (1 - 2 / (9 * k))) / math.sqrt(2 / (9 * k))
+        return 0.5 * math.erfc(z / math.sqrt(2))
+
+
+def tally_agreement(a, b, var, min_rel_sigma=0.3):
+    """a, b: images; var: variance of (a - b). Returns (max |z|, chi2, dof,
+    p) over bins whose relative standard error is below min_rel_sigma."""
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    var = np.asarray(var, dtype=np.float64).ravel()
+    sig = np.sqrt(np.maximum(var, 0))
+    pop = (sig > 0) & (sig < min_rel_sigma * np.maximum(np.abs(b), 1e-300))
+    z = np.zeros_like(a)
+    z[sig > 0] = (a - b)[sig > 0] / sig[sig > 0]
+    # bins the oracle never hit must be empty on the GPU too (up to rounding)
+    zmax = float(np.max(np.abs(z))) if z.size else 0.0
+    chi2 = float(np.sum(z[pop] ** 2))
+    dof = int(np.count_nonzero(pop))
+    return zmax, chi2, dof, chi2_sf(chi2, max(dof, 1))
+
+
+def oracle_var(res):
+    """Per-bin variance of an oracle image sum from its per-photon squares."""
+    n = res["n_photons"]
+    img, sq = res["image"], res["image_sq"]
+    return np.maximum(sq - img ** 2 / n, 0) * n / max(n - 1, 1)
