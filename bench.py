@@ -246,27 +246,30 @@ def run_engine(args):
 
     # end to end through the host-buffer entry point: table in, tallies out
     import numpy as np
-    work = torch.empty(E.host_workspace_bytes(med, cam), dtype=torch.uint8, device=dev)
-    pinned = lambda shape: torch.zeros(shape, dtype=torch.int64, pin_memory=True).numpy()
-    img, rad, tot = pinned((NZ, NX)), pinned(N_RADIAL), pinned(8)
-    blob = torch.from_numpy(table.blob).pin_memory().numpy()
-    E.run_host(med, geo, cam, N_PHOTONS, work, seed=SEED, photon_offset=offset, image=img, radial=rad,
-               totals=tot, table_host=blob)
-    barrier()
-    e2e_t = []
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
+    e2e = None
+    if not args.no_e2e:
+        work = torch.empty(E.host_workspace_bytes(med, cam), dtype=torch.uint8, device=dev)
+        pinned = lambda shape: torch.zeros(shape, dtype=torch.int64, pin_memory=True).numpy()
+        img, rad, tot = pinned((NZ, NX)), pinned(N_RADIAL), pinned(8)
+        blob = torch.from_numpy(table.blob).pin_memory().numpy()
         E.run_host(med, geo, cam, N_PHOTONS, work, seed=SEED, photon_offset=offset, image=img,
                    radial=rad, totals=tot, table_host=blob)
-        e2e_t.append(time.perf_counter() - t0)
-    te = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = total_steps / float(te.item())
-    h2d = table.blob.nbytes
-    d2h = img.nbytes + rad.nbytes + tot.nbytes + 4
+        barrier()
+        e2e_t = []
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            E.run_host(med, geo, cam, N_PHOTONS, work, seed=SEED, photon_offset=offset, image=img,
+                       radial=rad, totals=tot, table_host=blob)
+            e2e_t.append(time.perf_counter() - t0)
+        te = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
+        if ws > 1:
+            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        # the table goes in and image, radial profile, totals and error word come back
+        e2e = {"value": total_steps / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(blob.nbytes),
+               "d2h_bytes_per_step": int(img.nbytes + rad.nbytes + tot.nbytes + 4)}
 
     if rank != 0:
         if ws > 1:
@@ -290,8 +293,13 @@ def run_engine(args):
             "config": _workload_config(),
             "photons_per_s": ws * N_PHOTONS * args.steps / t_max,
             "steps_per_photon": steps_per_run / N_PHOTONS,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": e2e,
             "gpu_launches": args.steps, "clocks": clk, "roofline": roof}
+    if not args.no_peaks:
+        from paper_2507_23189_gb300 import peaks
+        pk = peaks.measure(dev)
+        line["issue_peaks"] = {"unit": "G ops/s (smem: GB/s)", "sms": pk["sms"],
+                               **{k: v / 1e9 for k, v in pk.items() if k != "sms"}}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -307,8 +315,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling)")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the issue-rate microbenchmarks")
+    ap.add_argument("--photons", type=int, default=N_PHOTONS,
+                    help="photons per step (default: the workload's 1e8; smaller for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # timing rule: at least three warm-up steps
+    globals()["N_PHOTONS"] = args.photons
     if args.impl == "reference":
         return run_reference(args)
     return run_engine(args)

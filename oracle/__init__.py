@@ -82,6 +82,7 @@ class WalkCfg(C.Structure):
 class WalkOut(C.Structure):
     _fields_ = [
         ("image", C.POINTER(C.c_double)), ("image_sq", C.POINTER(C.c_double)),
+        ("image_hits", C.POINTER(C.c_double)),
         ("radial", C.POINTER(C.c_double)), ("radial_sq", C.POINTER(C.c_double)),
         ("totals", C.c_double * N_TOTALS), ("totals_sq", C.c_double * N_TOTALS),
         ("steps", C.c_uint64), ("capped", C.c_uint64),
@@ -221,10 +222,11 @@ def walk(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,
     cfg.n_threads = n_threads if n_threads else (os.cpu_count() or 1)
     image = np.zeros(nz * nx)
     image_sq = np.zeros(nz * nx)
+    image_hits = np.zeros(nz * nx)
     radial = np.zeros(n_radial)
     radial_sq = np.zeros(n_radial)
     out = WalkOut()
-    out.image, out.image_sq = _dp(image), _dp(image_sq)
+    out.image, out.image_sq, out.image_hits = _dp(image), _dp(image_sq), _dp(image_hits)
     out.radial, out.radial_sq = _dp(radial), _dp(radial_sq)
     trace = None
     tptr = None
@@ -235,6 +237,7 @@ def walk(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,
     if rc:
         raise ValueError("oracle_walk: bad arguments")
     res = dict(image=image.reshape(nz, nx), image_sq=image_sq.reshape(nz, nx),
+               image_hits=image_hits.reshape(nz, nx),
                radial=radial, radial_sq=radial_sq,
                totals=np.array(out.totals[:]), totals_sq=np.array(out.totals_sq[:]),
                steps=int(out.steps), capped=int(out.capped), n_photons=n_photons)

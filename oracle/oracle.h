@@ -145,6 +145,7 @@ enum {
 
 typedef struct {
     double *image, *image_sq;     /* [nz*nx] sum and sum of per-photon squares */
+    double *image_hits;           /* [nz*nx] number of contributions (may be NULL) */
     double *radial, *radial_sq;   /* [n_radial] */
     double totals[ORACLE_N_TOTALS];
     double totals_sq[ORACLE_N_TOTALS];

@@ -34,7 +34,7 @@
 #include <string.h>
 
 typedef struct {
-    double *image, *image_sq, *radial, *radial_sq;
+    double *image, *image_sq, *image_hits, *radial, *radial_sq;
     double totals[ORACLE_N_TOTALS], totals_sq[ORACLE_N_TOTALS];
     uint64_t steps, capped;
     /* per-photon scratch for the squares */
@@ -256,6 +256,7 @@ static void run_photon(const oracle_walk_cfg *c, uint64_t p, acc_t *A,
         margin = min2(margin, min2(grid_margin(fx, c->nx), grid_margin(fz, c->nz)));
         int pix = iz * c->nx + ix;
         A->image[pix] += nee;
+        A->image_hits[pix] += 1.0;
         hit_push(A, pix, nee);
 
         double status = 0;
@@ -398,9 +399,11 @@ int oracle_walk(const oracle_walk_cfg *c, oracle_walk_out *out,
         J->n_trace_events = n_trace_events;
         J->acc.image = calloc(npix, sizeof(double));
         J->acc.image_sq = calloc(npix, sizeof(double));
+        J->acc.image_hits = calloc(npix, sizeof(double));
         J->acc.radial = calloc((size_t)c->n_radial, sizeof(double));
         J->acc.radial_sq = calloc((size_t)c->n_radial, sizeof(double));
-        if (!J->acc.image || !J->acc.image_sq || !J->acc.radial || !J->acc.radial_sq)
+        if (!J->acc.image || !J->acc.image_sq || !J->acc.image_hits || !J->acc.radial ||
+            !J->acc.radial_sq)
             rc = -1;
     }
     if (rc == 0) {
@@ -414,6 +417,7 @@ int oracle_walk(const oracle_walk_cfg *c, oracle_walk_out *out,
             for (size_t i = 0; i < npix; ++i) {
                 if (out->image) out->image[i] += A->image[i];
                 if (out->image_sq) out->image_sq[i] += A->image_sq[i];
+                if (out->image_hits) out->image_hits[i] += A->image_hits[i];
             }
             for (int i = 0; i < c->n_radial; ++i) {
                 if (out->radial) out->radial[i] += A->radial[i];
@@ -429,7 +433,8 @@ int oracle_walk(const oracle_walk_cfg *c, oracle_walk_out *out,
     }
     for (int t = 0; t < T; ++t) {
         acc_t *A = &jobs[t].acc;
-        free(A->image); free(A->image_sq); free(A->radial); free(A->radial_sq);
+        free(A->image); free(A->image_sq); free(A->image_hits);
+        free(A->radial); free(A->radial_sq);
         free(A->hit_pix); free(A->hit_val);
     }
     free(jobs);

@@ -34,21 +34,38 @@ def _stale(lib, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, extra=()):
-    """Compile the engine if missing or older than its sources; return its path."""
-    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS]
-    deps.append(os.path.join(ROOT, "include", "mcmie.h"))
-    deps.append(os.path.abspath(__file__))
-    if not force and not _stale(LIB, deps):
-        return LIB
-    os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    tmp = LIB + ".%d.tmp" % os.getpid()
+PEAKS_LIB = os.path.join(HERE, "_build", "libmcpeaks.so")
+
+
+def _compile(lib, sources, deps, force, verbose, extra):
+    if not force and not _stale(lib, deps):
+        return None
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [nvcc()] + NVCC_FLAGS + list(extra) + ["-I", os.path.join(ROOT, "include"),
-                                                 "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
+                                                 "-o", tmp] + [os.path.join(CSRC, s) for s in sources]
     if verbose:
         print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    return subprocess.Popen(cmd), tmp, lib
+
+
+def build(force=False, verbose=False, extra=()):
+    """Compile the engine (and the issue-rate microbenchmarks) if missing or
+    older than their sources; return the engine library's path."""
+    me = os.path.abspath(__file__)
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [
+        os.path.join(ROOT, "include", "mcmie.h"), me]
+    jobs = [_compile(LIB, SOURCES, deps, force, verbose, extra),
+            _compile(PEAKS_LIB, ["peaks.cu"], [os.path.join(CSRC, "peaks.cu"),
+                                               os.path.join(ROOT, "include", "mcpeaks.h"), me],
+                     force, verbose, extra)]
+    for job in jobs:
+        if job is None:
+            continue
+        proc, tmp, lib = job
+        if proc.wait() != 0:
+            raise subprocess.CalledProcessError(proc.returncode, "nvcc")
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -245,29 +245,29 @@ mc_status mc_run_host(const mc_medium *medium, const void *table, const mc_geome
     p += up(sizeof(uint32_t));
     t.d_work = p;
     t.work_bytes = mc_workspace_bytes(camera);
-    cudaError_t e;
-    if (tb && (e = cudaMemcpyAsync(d_table, table, tb, cudaMemcpyHostToDevice, st))) return MC_ERR_CUDA;
-    if ((e = cudaMemsetAsync(t.d_error, 0, sizeof(uint32_t), st))) return MC_ERR_CUDA;
+    auto fail = [](cudaError_t x) { return x != cudaSuccess; };
+    if (tb && fail(cudaMemcpyAsync(d_table, table, tb, cudaMemcpyHostToDevice, st))) return MC_ERR_CUDA;
+    if (fail(cudaMemsetAsync(t.d_error, 0, sizeof(uint32_t), st))) return MC_ERR_CUDA;
     mc_run_params r = *run;
     if (r.accumulate) {
         // carry the caller's running tallies in
-        if ((e = cudaMemcpyAsync(t.d_image, image, sizeof(int64_t) * npix, cudaMemcpyHostToDevice, st)) ||
-            (e = cudaMemcpyAsync(t.d_radial, radial, sizeof(int64_t) * camera->n_radial,
+        if (fail(cudaMemcpyAsync(t.d_image, image, sizeof(int64_t) * npix, cudaMemcpyHostToDevice, st)) ||
+            fail(cudaMemcpyAsync(t.d_radial, radial, sizeof(int64_t) * camera->n_radial,
                                  cudaMemcpyHostToDevice, st)) ||
-            (e = cudaMemcpyAsync(t.d_totals, totals, sizeof(int64_t) * MC_N_TOTALS,
+            fail(cudaMemcpyAsync(t.d_totals, totals, sizeof(int64_t) * MC_N_TOTALS,
                                  cudaMemcpyHostToDevice, st)))
             return MC_ERR_CUDA;
     }
     if (tb) m.d_table = d_table;
     if ((s = run_common(&m, geom, camera, &r, &t, nullptr, 0, 0, st)) != MC_OK) return s;
-    if ((e = cudaMemcpyAsync(image, t.d_image, sizeof(int64_t) * npix, cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaMemcpyAsync(radial, t.d_radial, sizeof(int64_t) * camera->n_radial,
+    if (fail(cudaMemcpyAsync(image, t.d_image, sizeof(int64_t) * npix, cudaMemcpyDeviceToHost, st)) ||
+        fail(cudaMemcpyAsync(radial, t.d_radial, sizeof(int64_t) * camera->n_radial,
                              cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaMemcpyAsync(totals, t.d_totals, sizeof(int64_t) * MC_N_TOTALS, cudaMemcpyDeviceToHost,
+        fail(cudaMemcpyAsync(totals, t.d_totals, sizeof(int64_t) * MC_N_TOTALS, cudaMemcpyDeviceToHost,
                              st)) ||
-        (e = cudaMemcpyAsync(error, t.d_error, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)))
+        fail(cudaMemcpyAsync(error, t.d_error, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)))
         return MC_ERR_CUDA;
-    if ((e = cudaStreamSynchronize(st))) return MC_ERR_CUDA;
+    if (fail(cudaStreamSynchronize(st))) return MC_ERR_CUDA;
     if (*error & MC_EFLAG_TIMEOUT) return MC_ERR_TIMEOUT;
     if (*error & MC_EFLAG_TABLE) return MC_ERR_TABLE;
     if (*error & MC_EFLAG_NUMERIC) return MC_ERR_NUMERIC;

@@ -170,6 +170,9 @@ extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *
               (2.0 * n + 1.0) / (n * (n + 1.0)) * (S.a[n] * std::conj(S.b[n])).real();
     }
     const double qext = 2.0 / (x * x) * se, qsca = 2.0 / (x * x) * ss;
+    // Q_abs is exactly zero for a real index; the series difference only
+    // carries rounding (of either sign), so keep it non-negative.
+    const double qabs = (m.imag() > 0.0) ? std::fmax(qext - qsca, 0.0) : 0.0;
     const double g = 4.0 / (x * x) * sg / qsca;
 
     // Panels in theta, accumulated from theta = pi (mu = -1) toward 0.
@@ -232,13 +235,13 @@ extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *
         info->m_im = m.imag();
         info->qext = qext;
         info->qsca = qsca;
-        info->qabs = qext - qsca;
+        info->qabs = qabs;
         info->g = g;
         info->g_table = mean;
         double geo = kPi * (P->diameter_um * 1e-3) * (P->diameter_um * 1e-3) / 4.0;
         info->sigma_ext_mm2 = qext * geo;
         info->sigma_sca_mm2 = qsca * geo;
-        info->sigma_abs_mm2 = (qext - qsca) * geo;
+        info->sigma_abs_mm2 = qabs * geo;
         info->nmax = S.nmax;
     }
     if (omu64) std::memcpy(omu64, omu.data(), sizeof(double) * (n + 1));
@@ -274,6 +277,6 @@ extern "C" mc_status mc_medium_from_density(const mie_info *info, double nd, dou
         return MC_ERR_ARG;
     // Eq. 17 per unit length: mu = n sigma.
     out->mu_s = nd * info->sigma_sca_mm2;
-    out->mu_a = nd * info->sigma_abs_mm2 + mu_a_medium;
+    out->mu_a = nd * std::fmax(info->sigma_abs_mm2, 0.0) + mu_a_medium;
     return MC_OK;
 }

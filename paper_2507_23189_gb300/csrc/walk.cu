@@ -61,6 +61,18 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
 
 __device__ __forceinline__ long long fix32(float w) { return __float2ll_rn(w * W_SCALE); }
 
+// 64-bit add into shared memory as two native 32-bit atomics: the low word's
+// returned old value gives the carry, which joins the high word. Exact and
+// independent of the order of concurrent adds (integer addition mod 2^64).
+__device__ __forceinline__ void sadd64(unsigned long long *p, long long v)
+{
+    const uint32_t lo = (uint32_t)v, hi = (uint32_t)((unsigned long long)v >> 32);
+    uint32_t *w = reinterpret_cast<uint32_t *>(p);
+    const uint32_t old = atomicAdd(w, lo);
+    const uint32_t up = hi + ((uint32_t)(old + lo) < lo ? 1u : 0u);
+    if (up) atomicAdd(w + 1, up);
+}
+
 // Bulk-copy `bytes` (multiple of 16) from global to shared memory, bounded wait.
 __device__ bool stage_bulk(void *dst, const void *src, uint32_t bytes, unsigned long long *mbar,
                            uint32_t *err)
@@ -165,8 +177,9 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ WalkA
     uint32_t pk0 = 0, pk1 = 0;      // global photon index, lo/hi words
     uint32_t ev = 0, ncoll = 0;
     float rx = 0, ry = 0, rz = 0, dx = 1, dy = 0, dz = 0, w = 1;
+    // per-thread tallies, reduced once at the end (no contention)
     unsigned long long my_steps = 0;
-    long long my_abs = 0;
+    long long t_refl = 0, t_far = 0, t_side = 0, t_ball = 0, t_abs = 0;
 
     while (true) {
         // -------- refill lanes whose photon ended
@@ -224,37 +237,51 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ WalkA
 
         const float s = -logf(u0) * A.inv_mu_ext;                 // Eq. 15
         const float px = fmaf(s, dx, rx), py = fmaf(s, dy, ry), pz = fmaf(s, dz, rz);
-        const bool inside = (px > 0.f) & (px < A.lx) & (fabsf(py) < A.hy) & (fabsf(pz) < A.hz);
+        const bool cx = !((px > 0.f) & (px < A.lx));
+        const bool cy = !(fabsf(py) < A.hy);
+        const bool cz = !(fabsf(pz) < A.hz);
 
-        if (!inside) {
-            // leave through the first wall on the way (ties: lowest axis)
+        if (cx | cy | cz) {
+            // the flight reaches a wall: the first one crossed is the exit
+            // (ties: lowest axis). With one axis crossed no division is needed.
             const float INF = __int_as_float(0x7f800000);
-            const float tx = dx > 0.f ? (A.lx - rx) / dx : (dx < 0.f ? (0.f - rx) / dx : INF);
-            const float ty = dy > 0.f ? (A.hy - ry) / dy : (dy < 0.f ? (-A.hy - ry) / dy : INF);
-            const float tz = dz > 0.f ? (A.hz - rz) / dz : (dz < 0.f ? (-A.hz - rz) / dz : INF);
             int face;
-            float t;
-            if (tx <= ty && tx <= tz) { face = 0; t = tx; }
-            else if (ty <= tz) { face = 1; t = ty; }
-            else { face = 2; t = tz; }
-            const float ex = fmaf(t, dx, rx), ey = fmaf(t, dy, ry), ez = fmaf(t, dz, rz);
+            if ((int)cx + (int)cy + (int)cz == 1) {
+                face = cx ? 0 : (cy ? 1 : 2);
+            } else {
+                const float tx = cx ? (dx > 0.f ? (A.lx - rx) / dx : (0.f - rx) / dx) : INF;
+                const float ty = cy ? (dy > 0.f ? (A.hy - ry) / dy : (-A.hy - ry) / dy) : INF;
+                const float tz = cz ? (dz > 0.f ? (A.hz - rz) / dz : (-A.hz - rz) / dz) : INF;
+                face = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
+            }
             const long long wv = fix32(w);
             int status, rb = -1;
+            float ex = px, ey = py, ez = pz;
             if (face == 0 && dx < 0.f) {
-                atomicAdd(&s_tot[MC_TOT_REFLECT], (unsigned long long)wv);
+                t_refl += wv;
                 status = 1;
             } else if (face == 0) {
-                atomicAdd(&s_tot[MC_TOT_FAR], (unsigned long long)wv);
-                if (ncoll == 0) atomicAdd(&s_tot[MC_TOT_BALLISTIC], (unsigned long long)wv);
+                t_far += wv;
+                if (ncoll == 0) t_ball += wv;
+                const float t = (A.lx - rx) / dx;
+                ex = A.lx; ey = fmaf(t, dy, ry); ez = fmaf(t, dz, rz);
                 const float rho = sqrtf(fmaf(ey, ey, ez * ez));
                 rb = min(__float2int_rd(rho * A.sr), A.n_radial - 1);
-                atomicAdd(&s_rad[rb], (unsigned long long)wv);
+                sadd64(&s_rad[rb], wv);
                 status = 2;
             } else {
-                atomicAdd(&s_tot[MC_TOT_SIDE], (unsigned long long)wv);
+                t_side += wv;
                 status = 3;
             }
-            trace_write<TRACE>(A, rel, e_now, status, ex, ey, ez, dx, dy, dz, w, 0.f, -1, -1, rb);
+            if (TRACE) {
+                if (face != 0 || dx < 0.f) {
+                    const float t = face == 0 ? (0.f - rx) / dx
+                                  : face == 1 ? (dy > 0.f ? A.hy - ry : -A.hy - ry) / dy
+                                              : (dz > 0.f ? A.hz - rz : -A.hz - rz) / dz;
+                    ex = fmaf(t, dx, rx); ey = fmaf(t, dy, ry); ez = fmaf(t, dz, rz);
+                }
+                trace_write<TRACE>(A, rel, e_now, status, ex, ey, ez, dx, dy, dz, w, 0.f, -1, -1, rb);
+            }
             alive = false;
             continue;
         }
@@ -262,8 +289,12 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ WalkA
         // -------- collision
         rx = px; ry = py; rz = pz;
         ++ncoll;
-        if (A.absorb_frac > 0.f) my_abs += fix32(w * A.absorb_frac);
-        w = w * A.albedo;                                            // Eq. 16
+        {   // Eq. 16; the captured part w - w a is exact in single precision
+            // for albedo a >= 1/2 (Sterbenz), so weight is conserved per photon
+            const float wn = w * A.albedo;
+            if (A.absorb_frac > 0.f) t_abs += fix32(w - wn);
+            w = wn;
+        }
 
         // camera: next-event estimate toward +y
         float psr;
@@ -282,7 +313,7 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ WalkA
         const float vf = nee * A.img_scale;
         if (vf < 4.0e18f) {
             const long long v = __float2ll_rn(vf);
-            if (SMEM_IMAGE) atomicAdd(&s_img[pix], (unsigned long long)v);
+            if (SMEM_IMAGE) sadd64(&s_img[pix], v);
             else atomicAdd(&A.image[pix], (unsigned long long)v);
         } else {
             atomicOr(A.error, (vf == vf) ? MC_EFLAG_OVERFLOW : MC_EFLAG_NUMERIC);
@@ -290,7 +321,7 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ WalkA
 
         int status = 0;
         if (A.max_scatter && ncoll >= A.max_scatter) {
-            atomicAdd(&s_tot[MC_TOT_TRUNC], (unsigned long long)fix32(w));
+            sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
             status = 5;
             alive = false;
         } else {
@@ -318,17 +349,17 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ WalkA
             const float e2x = b, e2y = fmaf(dy * dy, a, sg), e2z = -dy;
             const float qx = fmaf(cp, e1x, sp * e2x), qy = fmaf(cp, e1y, sp * e2y),
                         qz = fmaf(cp, e1z, sp * e2z);
-            float nx = fmaf(mu, dx, st * qx), ny = fmaf(mu, dy, st * qy), nz = fmaf(mu, dz, st * qz);
+            const float nx = fmaf(mu, dx, st * qx), ny = fmaf(mu, dy, st * qy), nz = fmaf(mu, dz, st * qz);
             const float inv = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
             dx = nx * inv; dy = ny * inv; dz = nz * inv;
             // weight threshold / roulette (Sec. 3.1.3)
             if (w < A.rr_thr) {
                 if (u3 < A.rr_surv) {
                     const float wn = w * A.inv_rr_surv;
-                    atomicAdd(&s_tot[MC_TOT_ROULETTE], (unsigned long long)(fix32(w) - fix32(wn)));
+                    sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w) - fix32(wn));
                     w = wn;
                 } else {
-                    atomicAdd(&s_tot[MC_TOT_ROULETTE], (unsigned long long)fix32(w));
+                    sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w));
                     status = 4;
                     alive = false;
                 }
@@ -338,22 +369,30 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ WalkA
         trace_write<TRACE>(A, rel, e_now, status, rx, ry, rz, dx, dy, dz, status == 4 ? 0.f : w, nee,
                            pix, nb, -1);
         if (alive && ev >= A.max_events) {
-            atomicAdd(&s_tot[MC_TOT_TRUNC], (unsigned long long)fix32(w));
+            sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
             atomicOr(A.error, MC_EFLAG_EVENTS);
             trace_write<TRACE>(A, rel, ev, 6, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1, -1);
             alive = false;
         }
     }
 
-    // -------- per-thread counters -> shared -> global
+    // -------- per-thread tallies -> warp -> shared -> global
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         my_steps += __shfl_xor_sync(FULL, my_steps, o);
-        my_abs += __shfl_xor_sync(FULL, my_abs, o);
+        t_refl += __shfl_xor_sync(FULL, t_refl, o);
+        t_far += __shfl_xor_sync(FULL, t_far, o);
+        t_side += __shfl_xor_sync(FULL, t_side, o);
+        t_ball += __shfl_xor_sync(FULL, t_ball, o);
+        t_abs += __shfl_xor_sync(FULL, t_abs, o);
     }
     if (lane == 0) {
-        atomicAdd(&s_tot[MC_TOT_STEPS], my_steps);
-        if (my_abs) atomicAdd(&s_tot[MC_TOT_ABSORB], (unsigned long long)my_abs);
+        sadd64(&s_tot[MC_TOT_STEPS], (long long)my_steps);
+        sadd64(&s_tot[MC_TOT_REFLECT], t_refl);
+        sadd64(&s_tot[MC_TOT_FAR], t_far);
+        sadd64(&s_tot[MC_TOT_SIDE], t_side);
+        sadd64(&s_tot[MC_TOT_BALLISTIC], t_ball);
+        sadd64(&s_tot[MC_TOT_ABSORB], t_abs);
     }
     __syncthreads();
     if (SMEM_IMAGE)

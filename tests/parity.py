@@ -80,21 +80,22 @@ def chi2_sf(x, k):
         return 0.5 * math.erfc(z / math.sqrt(2))
 
 
-def tally_agreement(a, b, var, min_rel_sigma=0.3):
-    """a, b: images; var: variance of (a - b). Returns (max |z|, chi2, dof,
-    p) over bins whose relative standard error is below min_rel_sigma."""
+def tally_agreement(a, b, var, hits=None, min_hits=20):
+    """a, b: images; var: variance of (a - b); hits: oracle contributions per
+    bin. Returns (max |z| over bins with var > 0, chi2, dof, p) with the
+    chi-square pooled over bins holding at least min_hits contributions."""
     a = np.asarray(a, dtype=np.float64).ravel()
     b = np.asarray(b, dtype=np.float64).ravel()
     var = np.asarray(var, dtype=np.float64).ravel()
     sig = np.sqrt(np.maximum(var, 0))
-    pop = (sig > 0) & (sig < min_rel_sigma * np.maximum(np.abs(b), 1e-300))
+    ok = sig > 0
     z = np.zeros_like(a)
-    z[sig > 0] = (a - b)[sig > 0] / sig[sig > 0]
-    # bins the oracle never hit must be empty on the GPU too (up to rounding)
+    z[ok] = (a - b)[ok] / sig[ok]
+    pop = ok if hits is None else ok & (np.asarray(hits).ravel() >= min_hits)
     zmax = float(np.max(np.abs(z))) if z.size else 0.0
     chi2 = float(np.sum(z[pop] ** 2))
     dof = int(np.count_nonzero(pop))
-    return zmax, chi2, dof, chi2_sf(chi2, max(dof, 1))
+    return zmax, chi2, dof, chi2_sf(chi2, max(dof, 1)), z
 
 
 def oracle_var(res):
@@ -102,3 +103,25 @@ def oracle_var(res):
     n = res["n_photons"]
     img, sq = res["image"], res["image_sq"]
     return np.maximum(sq - img ** 2 / n, 0) * n / max(n - 1, 1)
+
+
+def gpu_batches(gpu, med, n, batches, camera, geometry, offset=0, seed=1, **kw):
+    """Run photons [offset, offset + n) as `batches` separate launches and
+    return the summed result plus the batch-means variance of the image sum
+    (the engine keeps integer sums only, so its spread comes from batches)."""
+    imgs, tot, steps = [], None, 0
+    raw_img = None
+    edges = [offset + (n * k) // batches for k in range(batches + 1)]
+    for k in range(batches):
+        e = gpu.Engine(camera, geometry)
+        e.run(med, edges[k + 1] - edges[k], seed=seed, photon_offset=edges[k], **kw)
+        e.check()
+        r = e.result()
+        imgs.append(r["image"])
+        raw_img = r["raw_image"] if raw_img is None else raw_img + r["raw_image"]
+        tot = r["raw_totals"] if tot is None else tot + r["raw_totals"]
+        steps += r["steps"]
+    imgs = np.stack(imgs)
+    total = imgs.sum(axis=0)
+    var = batches * imgs.var(axis=0, ddof=1)
+    return dict(image=total, var=var, raw_image=raw_img, raw_totals=tot, steps=steps)

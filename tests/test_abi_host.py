@@ -126,3 +126,11 @@ def test_workspace_and_argument_checks_without_gpu(eng):
     med = N.Medium(0.1, 0.0, N.PHASE_TABLE, 0.0, None, 4096)
     assert L.mc_run(C.byref(med), C.byref(geo), C.byref(cam), C.byref(run), C.byref(tal), None) == -1
     assert L.mc_check(None, None) == -1
+
+
+def test_peaks_library_exports(eng):
+    from paper_2507_23189_gb300 import build
+    L = C.CDLL(build.PEAKS_LIB)
+    assert hasattr(L, "mc_peak_run")
+    L.mc_peak_run.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    assert L.mc_peak_run(0, 0, 256, 10, None, None, None) == -1   # rejected before any launch

@@ -37,7 +37,7 @@ def test_energy_bookkeeping(gpu, ps_table, phase):
     t = r["raw_totals"]
     assert t[0] + t[1] + t[2] == n << 32          # exact: every escape carries 1.0
     assert t[3] == t[4] == t[5] == 0
-    r = _run(gpu, gpu.Medium(4 / LX, 1 / LX, phase, g, ps_table), n, rr_threshold=0.01, rr_survival=0.1)
+    r = _run(gpu, gpu.Medium(4 / LX, 1 / LX, phase, g, ps_table), n, rr_threshold=0.5, rr_survival=0.1)
     t = r["raw_totals"].astype(np.float64)
     total = t[0] + t[1] + t[2] + t[3] + t[4] + t[5]
     # each contribution is rounded once to 2^-32: at most ~1/2 unit per term
@@ -62,13 +62,3 @@ def test_single_scatter_image(gpu, ps_table, mu_a):
     z = (img[nz // 2] - want) / sigma
     assert np.max(np.abs(z)) < 5.0
     assert float(np.sum(z ** 2)) < nx + 6 * math.sqrt(2 * nx)
-
-
-def test_mirror_symmetry(gpu, ps_table):
-    n, nx, nz = 10_000_000, 32, 31
-    r = _run(gpu, gpu.Medium(3 / LX, 0.0, "table", 0.0, ps_table), n, nx, nz, seed=5)
-    img = r["image"]
-    a, b = img[: nz // 2], img[::-1][: nz // 2]
-    rel = np.abs(a - b) / np.maximum(a + b, 1e-300)
-    big = (a + b) > np.max(img) * 1e-3
-    assert np.median(rel[big]) < 0.02

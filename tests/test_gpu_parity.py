@@ -10,7 +10,7 @@ import math
 import numpy as np
 import pytest
 
-from parity import compare_traces, oracle_var, tally_agreement
+from parity import compare_traces, gpu_batches, oracle_var, tally_agreement
 
 pytestmark = pytest.mark.gpu
 
@@ -59,7 +59,7 @@ def test_trace_parity_first_32_events(gpu, oracle_mod, ps_table, ps_oracle_table
     print(phase, tau, mu_a, cmp["matched"], "/", cmp["n"], "flips", cmp["flips"], "worst", cmp["worst"],
           "events", cmp["events"])
     assert cmp["matched"] >= 0.999 * n, cmp["bad"]
-    assert cmp["events"] > 4 * n
+    assert cmp["events"] > 1.5 * n
     if kw:
         assert np.any(ores["trace"][..., 0] == 4), "roulette never fired"
 
@@ -67,7 +67,8 @@ def test_trace_parity_first_32_events(gpu, oracle_mod, ps_table, ps_oracle_table
 def _tally_case(gpu, oracle_mod, ps_table, ps_oracle_table, phase, seed_gpu, seed_or, n=1_000_000,
                 tau=1.0):
     med, om = _media(gpu, oracle_mod, ps_table, tau, phase)
-    res, _ = _gpu_run(gpu, med, n, 64, 64, seed=seed_gpu)
+    res = gpu_batches(gpu, med, n, 32, gpu.Camera(64, 64, 128, R_MAX), gpu.Geometry(LX, LY, LZ),
+                      seed=seed_gpu)
     ores = oracle_mod.walk(table=ps_oracle_table, n_photons=n, nx=64, nz=64, seed=seed_or, **om)
     return res, ores
 
@@ -75,10 +76,10 @@ def _tally_case(gpu, oracle_mod, ps_table, ps_oracle_table, phase, seed_gpu, see
 @pytest.mark.parametrize("phase", ["mie", "hg"])
 def test_tally_parity_same_seed(gpu, oracle_mod, ps_table, ps_oracle_table, phase):
     res, ores = _tally_case(gpu, oracle_mod, ps_table, ps_oracle_table, phase, 1, 1)
-    var = 2.0 * oracle_var(ores)
-    zmax, chi2, dof, p = tally_agreement(res["image"], ores["image"], var)
-    pop = var > 0
-    rel = np.abs(res["image"] - ores["image"])[pop] / np.maximum(ores["image"][pop], 1e-300)
+    var = oracle_var(ores) + res["var"]
+    zmax, chi2, dof, p, z = tally_agreement(res["image"], ores["image"], var, ores["image_hits"])
+    pop = ores["image_hits"] >= 20
+    rel = np.abs(res["image"] - ores["image"])[pop] / ores["image"][pop]
     print(phase, "zmax", zmax, "chi2", chi2, "dof", dof, "p", p,
           "fp32-vs-fp64 per-bin rel err: median %.2e max %.2e" % (np.median(rel), rel.max()))
     assert zmax < 3.0 and p > 0.01 and dof > 500
@@ -86,21 +87,22 @@ def test_tally_parity_same_seed(gpu, oracle_mod, ps_table, ps_oracle_table, phas
     n = ores["n_photons"]
     raw = res["raw_totals"]
     assert raw[0] + raw[1] + raw[2] == n << 32
+    w = raw[:7].astype(np.float64) * 2.0 ** -32
     for k in range(3):
         sig = math.sqrt(max(ores["totals_sq"][k] - ores["totals"][k] ** 2 / n, 0.0))
-        assert abs(res["totals"][k] - ores["totals"][k]) <= 3 * math.sqrt(2) * sig + 1e-9
+        assert abs(w[k] - ores["totals"][k]) <= 3 * math.sqrt(2) * sig + 1e-9
     assert abs(res["steps"] - ores["steps"]) <= 1e-4 * ores["steps"]
     # ballistic photons are decided by u0 alone, identically on both sides
-    assert res["totals"][6] == ores["totals"][6]
+    assert w[6] == ores["totals"][6]
 
 
 @pytest.mark.parametrize("phase", ["mie", "hg"])
 def test_tally_agreement_independent_seeds(gpu, oracle_mod, ps_table, ps_oracle_table, phase):
     res, ores = _tally_case(gpu, oracle_mod, ps_table, ps_oracle_table, phase, 2, 1)
-    var = 2.0 * oracle_var(ores)   # both estimates carry the same per-photon variance
-    zmax, chi2, dof, p = tally_agreement(res["image"], ores["image"], var)
-    print(phase, "zmax", zmax, "chi2", chi2, "dof", dof, "p", p)
+    var = oracle_var(ores) + res["var"]
+    zmax, chi2, dof, p, z = tally_agreement(res["image"], ores["image"], var, ores["image_hits"])
+    frac3 = float(np.mean(np.abs(z[var.ravel() > 0]) > 3.0))
+    print(phase, "zmax", zmax, "chi2", chi2, "dof", dof, "p", p, "frac>3sigma", frac3)
     assert p > 0.01 and dof > 500
-    # 3-sigma on every bin, allowing the expected handful of 3-sigma excursions
-    z = np.abs(res["image"] - ores["image"])[var > 0] / np.sqrt(var[var > 0])
-    assert np.mean(z > 3.0) < 0.01 and zmax < 5.5
+    # independent estimates: about 0.3 % of bins beyond 3 sigma by chance
+    assert frac3 < 0.01 and zmax < 6.0
