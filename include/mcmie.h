@@ -142,10 +142,12 @@ typedef struct {
     int image_frac_bits;    /* fixed-point fraction bits of the image (8..48)  */
     int accumulate;         /* 0: zero the tallies first; 1: add to them       */
     /* launch tuning; results do not depend on these (0 = automatic) */
-    int block_size;         /* threads per CTA: 0 or a multiple of 32, <= 256  */
+    int block_size;         /* threads per CTA: 0 or a multiple of 32, <= 1024 */
     int blocks_per_sm;      /* persistent CTAs per SM: 0 = occupancy maximum   */
-    int image_mode;         /* 0 auto, 1 image tile in shared memory (must
-                               fit), 2 image atomics straight to global memory */
+    int image_mode;         /* 0 auto, 1 whole image in shared memory (must
+                               fit), 2 image atomics straight to global memory,
+                               3 the rows around the beam that fit in shared
+                               memory there, the other rows global            */
 } mc_run_params;
 
 /* Totals tallied by mc_run, as int64 in the units noted. */

@@ -58,8 +58,8 @@ mc_status check_run(const mc_run_params *r)
         r->rr_survival < 0 || r->rr_survival > 1 || r->max_events < 1 || r->image_frac_bits < 8 ||
         r->image_frac_bits > 48 || (r->accumulate != 0 && r->accumulate != 1) ||
         r->photon_offset + r->n_photons < r->photon_offset || r->block_size < 0 ||
-        r->block_size > 256 || (r->block_size % 32) != 0 || r->blocks_per_sm < 0 ||
-        r->blocks_per_sm > 64 || r->image_mode < 0 || r->image_mode > 2)
+        r->block_size > 1024 || (r->block_size % 32) != 0 || r->blocks_per_sm < 0 ||
+        r->blocks_per_sm > 64 || r->image_mode < 0 || r->image_mode > 3)
         return MC_ERR_ARG;
     return MC_OK;
 }
@@ -161,7 +161,7 @@ mc_status run_common(const mc_medium *m, const mc_geometry *g, const mc_camera *
     a.n_trace = n_trace;
     a.n_trace_events = n_events;
     mcx::LaunchCfg cfg;
-    if (r->block_size) cfg.block = r->block_size;
+    cfg.block = r->block_size;
     cfg.blocks_per_sm = r->blocks_per_sm;
     cfg.image_mode = r->image_mode;
     e = mcx::launch_walk(a, trace != nullptr, cfg, st);

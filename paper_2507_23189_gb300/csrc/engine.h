@@ -40,12 +40,17 @@ struct WalkArgs {
     // trace (trace kernels only)
     int32_t *trace;
     int n_trace, n_trace_events;
+    // image rows [band0, band0 + band_rows) are privatised in shared memory
+    // (set by the launcher; band_rows = nz for a whole-image tile)
+    int band0, band_rows;
 };
 
 struct LaunchCfg {
-    int block = 256;
+    int block = 0;          // 0: 256 (whole tile / global) or 1024 (band)
     int blocks_per_sm = 0;  // 0: occupancy maximum
-    int image_mode = 0;     // 0 auto, 1 shared-memory tile, 2 global atomics
+    int image_mode = 0;     // 0 auto, 1 whole image in shared memory, 2 global
+                            // atomics only, 3 band of rows around the beam in
+                            // shared memory, the rest global
 };
 
 // Launch the walk (or its trace variant) on `stream`. Returns cudaSuccess or

@@ -136,19 +136,21 @@ __device__ __forceinline__ void trace_write(const WalkArgs &A, unsigned long lon
     t[9] = pix; t[10] = nb; t[11] = rb;
 }
 
-// Shared-memory layout: [table blob][image tile][radial][totals][mbarrier]
+// Shared-memory layout: [table blob][image band][radial][totals][mbarrier]
+// SMEM_IMAGE: image rows [band0, band0 + band_rows) accumulate in shared
+// memory (the whole image when band_rows = nz); other rows go to L2 atomics.
 template <int PHASE, bool SMEM_IMAGE, bool TRACE>
-__global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ WalkArgs A)
+__global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ WalkArgs A)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const uint32_t tb = (PHASE == MC_PHASE_TABLE) ? A.table_bytes : 0u;
-    const int npix = A.nx * A.nz;
+    const int npix = SMEM_IMAGE ? A.nx * A.band_rows : 0;   // privatised pixels
     unsigned long long *s_img = reinterpret_cast<unsigned long long *>(smem + tb);
-    unsigned long long *s_rad = s_img + (SMEM_IMAGE ? npix : 0);
+    unsigned long long *s_rad = s_img + npix;
     unsigned long long *s_tot = s_rad + A.n_radial;
     unsigned long long *s_bar = s_tot + MC_N_TOTALS;
 
-    for (int i = threadIdx.x; i < (SMEM_IMAGE ? npix : 0) + A.n_radial + MC_N_TOTALS; i += blockDim.x)
+    for (int i = threadIdx.x; i < npix + A.n_radial + MC_N_TOTALS; i += blockDim.x)
         s_img[i] = 0ull;
 
     const float *omu = nullptr, *pdf = nullptr;
@@ -313,7 +315,8 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ WalkA
         const float vf = nee * A.img_scale;
         if (vf < 4.0e18f) {
             const long long v = __float2ll_rn(vf);
-            if (SMEM_IMAGE) sadd64(&s_img[pix], v);
+            const unsigned brow = (unsigned)(iz - A.band0);
+            if (SMEM_IMAGE && brow < (unsigned)A.band_rows) sadd64(&s_img[brow * A.nx + ix], v);
             else atomicAdd(&A.image[pix], (unsigned long long)v);
         } else {
             atomicOr(A.error, (vf == vf) ? MC_EFLAG_OVERFLOW : MC_EFLAG_NUMERIC);
@@ -395,9 +398,11 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ WalkA
         sadd64(&s_tot[MC_TOT_ABSORB], t_abs);
     }
     __syncthreads();
-    if (SMEM_IMAGE)
+    if (SMEM_IMAGE) {
+        unsigned long long *g = A.image + (size_t)A.band0 * A.nx;
         for (int i = threadIdx.x; i < npix; i += blockDim.x)
-            if (s_img[i]) atomicAdd(&A.image[i], s_img[i]);
+            if (s_img[i]) atomicAdd(&g[i], s_img[i]);
+    }
     for (int i = threadIdx.x; i < A.n_radial; i += blockDim.x)
         if (s_rad[i]) atomicAdd(&A.radial[i], s_rad[i]);
     for (int i = threadIdx.x; i < MC_N_TOTALS; i += blockDim.x)
@@ -438,27 +443,45 @@ cudaError_t launch_one(const WalkArgs &a, const LaunchCfg &cfg, size_t smem, cud
 
 }  // namespace
 
-cudaError_t launch_walk(const WalkArgs &a, bool trace, const LaunchCfg &cfg, cudaStream_t st)
+cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, cudaStream_t st)
 {
+    WalkArgs a = a0;
+    LaunchCfg cfg = cfg0;
     const size_t tb = (a.phase_kind == MC_PHASE_TABLE) ? a.table_bytes : 0;
     const size_t tail = sizeof(unsigned long long) * (a.n_radial + MC_N_TOTALS + 1);
-    const size_t img = sizeof(unsigned long long) * (size_t)a.nx * a.nz;
+    const size_t row = sizeof(unsigned long long) * (size_t)a.nx;
     int dev = 0, optin = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
         return e;
-    // auto: the image tile lives in shared memory when two CTAs still fit per SM
-    bool smem_img;
-    if (cfg.image_mode == 1) {
-        smem_img = true;
-        if (tb + img + tail > (size_t)optin) return cudaErrorInvalidValue;
-    } else if (cfg.image_mode == 2) {
-        smem_img = false;
-    } else {
-        smem_img = (tb + img + tail) <= (size_t)optin / 2 - 1024;
+    const size_t room = (size_t)optin > tb + tail + 1024 ? (size_t)optin - tb - tail - 1024 : 0;
+    const int fit_rows = (int)(room / row);
+    // auto: a whole-image tile when two 256-thread CTAs per SM still fit;
+    // otherwise one 1024-thread CTA per SM holding as many rows around the
+    // beam as fit, the rest going to L2 atomics
+    int mode = cfg.image_mode;
+    if (mode == 0) {
+        if (tb + row * a.nz + tail <= (size_t)optin / 2 - 1024) mode = 1;
+        else mode = fit_rows >= 1 ? 3 : 2;
     }
-    const size_t smem = tb + tail + (smem_img ? img : 0);
+    bool smem_img = false;
+    a.band0 = 0;
+    a.band_rows = 0;
+    if (mode == 1) {
+        if (fit_rows < a.nz) return cudaErrorInvalidValue;
+        smem_img = true;
+        a.band_rows = a.nz;
+    } else if (mode == 3) {
+        if (fit_rows < 1) return cudaErrorInvalidValue;
+        smem_img = true;
+        a.band_rows = fit_rows < a.nz ? fit_rows : a.nz;
+        int b0 = a.nz / 2 - a.band_rows / 2;
+        if (b0 > a.nz - a.band_rows) b0 = a.nz - a.band_rows;
+        a.band0 = b0 < 0 ? 0 : b0;
+    }
+    if (cfg.block == 0) cfg.block = (mode == 3) ? 1024 : 256;
+    const size_t smem = tb + tail + (smem_img ? row * a.band_rows : 0);
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
     const bool table = a.phase_kind == MC_PHASE_TABLE;
     if (trace) {

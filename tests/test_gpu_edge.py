@@ -65,7 +65,8 @@ def test_launch_shape_does_not_change_results(gpu, ps_table, phase):
     med = gpu.Medium(5 / LX, 0.002, phase, ps_table.info["g"], ps_table)
     ref = None
     for kw in (dict(), dict(block_size=64), dict(block_size=128, blocks_per_sm=1),
-               dict(image_mode=1), dict(image_mode=2), dict(block_size=32, image_mode=2)):
+               dict(image_mode=1), dict(image_mode=2), dict(block_size=32, image_mode=2),
+               dict(image_mode=3), dict(image_mode=3, block_size=512)):
         e = _eng(gpu)
         e.run(med, 300_000, seed=2, **kw)
         e.check()
@@ -75,6 +76,20 @@ def test_launch_shape_does_not_change_results(gpu, ps_table, phase):
         else:
             np.testing.assert_array_equal(r["raw_image"], ref["raw_image"])
             np.testing.assert_array_equal(r["raw_totals"], ref["raw_totals"])
+
+
+@pytest.mark.parametrize("nx,nz", [(256, 256), (512, 512), (300, 97)])
+def test_band_and_global_images_identical(gpu, ps_table, nx, nz):
+    """Rows routed to the shared-memory band or to L2 atomics sum identically."""
+    med = gpu.Medium(10 / LX, 0.0, "table", 0.0, ps_table)
+    out = []
+    for mode in (2, 3):
+        e = _eng(gpu, nx, nz)
+        e.run(med, 1_000_000, seed=5, image_mode=mode)
+        e.check()
+        out.append(e.result())
+    np.testing.assert_array_equal(out[0]["raw_image"], out[1]["raw_image"])
+    np.testing.assert_array_equal(out[0]["raw_totals"], out[1]["raw_totals"])
 
 
 def test_repeat_runs_bit_identical(gpu, ps_table):
