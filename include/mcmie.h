@@ -181,6 +181,24 @@ mc_status mc_run(const mc_medium *medium, const mc_geometry *geom,
                  const mc_camera *camera, const mc_run_params *run,
                  const mc_tallies *tallies, void *stream);
 
+/* mc_run for callers that cannot allocate device memory for a workspace (for
+ * example a host application that owns all device memory and hands a plug-in
+ * only the buffers it reads and writes). The paper has no counterpart: this is
+ * an interface convenience. The scratch the walk needs lives in a fixed
+ * MC_STATIC_SCRATCH_BYTES device array inside the library, held by every GPU
+ * that loads it until exit; cameras needing more workspace than that are
+ * rejected with MC_ERR_NOMEM. The first call on a device looks the array up
+ * (cudaGetSymbolAddress), so make it before any stream capture. All calls
+ * share the array: consecutive calls are independent (the counter is cleared
+ * on the stream first), but calls that overlap on the GPU race and must be
+ * serialised by the caller. Allocates nothing. Other arguments and errors as
+ * for mc_run. */
+#define MC_STATIC_SCRATCH_BYTES 4096
+mc_status mc_run_static(const mc_medium *medium, const mc_geometry *geom,
+                        const mc_camera *camera, const mc_run_params *run,
+                        int64_t *d_image, int64_t *d_radial, int64_t *d_totals,
+                        uint32_t *d_error, void *stream);
+
 /* Host-buffer form of mc_run, for callers whose inputs and outputs live in
  * host memory. The table blob (mc_table_bytes(n_bins) bytes, or NULL for
  * MC_PHASE_HG) is copied to the device, the walk runs, and image, radial

@@ -22,7 +22,7 @@ TRACE_WORDS = 12
 # every symbol include/mcmie.h declares
 EXPORTS = ("mc_table_bytes", "mie_table_build", "mc_medium_from_density", "mc_workspace_bytes",
            "mc_run", "mc_host_workspace_bytes", "mc_run_host", "mc_trace", "mc_check", "mc_philox",
-           "mc_status_string")
+           "mc_status_string", "mc_run_static")
 
 
 class McError(RuntimeError):
@@ -110,6 +110,8 @@ def lib():
     L.mc_check.argtypes = [vp, vp]
     L.mc_philox.restype = C.c_int
     L.mc_philox.argtypes = [vp, C.c_uint64, C.c_uint64, vp, vp]
+    L.mc_run_static.restype = C.c_int
+    L.mc_run_static.argtypes = [P(Medium), P(Geometry), P(Camera), P(RunParams), vp, vp, vp, vp, vp]
     L.mc_status_string.restype = C.c_char_p
     L.mc_status_string.argtypes = [C.c_int]
     _lib = L
