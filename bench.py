@@ -155,6 +155,74 @@ def cpu_baseline(target_s=12.0):
             "photons_per_s": n / dt}
 
 
+def batched_comparison(E, dev, steps, warmup, flush):
+    """64 media of uneven optical depth, particle size and photon budget
+    (workloads.batched): one graph-replayed mc_run_batch against 64
+    sequential mc_run launches over the same photons (identical tallies)."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2507_23189_gb300 import autotune, workloads
+    cases = workloads.batched()
+    with ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
+        tables = list(ex.map(lambda c: E.PhaseTable(diameter_um=c.diameter_um), cases))
+    media = [E.Medium.from_optical_depth(t, c.tau, LX) for t, c in zip(tables, cases)]
+    nph = [c.n_photons for c in cases]
+    cam, geo = E.Camera(128, 128, N_RADIAL, R_MAX), E.Geometry(LX, LY, LZ, 0.0)
+    batch = E.Batch(len(media), cam, geo, dev)
+    tune = autotune.tune_batch(batch, media, nph)
+    kw = dict(item_photons=tune["item_photons"], block_size=tune["block_size"])
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(warmup):
+        batch.run(media, nph, 1, 0, **kw)
+    batch.check()
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream(dev)
+    cs.wait_stream(stream)
+    with torch.cuda.stream(cs):
+        with torch.cuda.graph(g, stream=cs):
+            batch.run(media, nph, 1, 0, stream=cs, **kw)
+    stream.wait_stream(cs)
+    engines = [E.Engine(cam, geo, dev) for _ in media]
+
+    def plain():
+        for e, m, n in zip(engines, media, nph):
+            e.run(m, n, seed=1, stream=stream)
+
+    for _ in range(warmup):
+        plain()
+        g.replay()
+    torch.cuda.synchronize(dev)
+    batch.check()
+    for e in engines:
+        e.check()
+    same = all(bool(torch.equal(batch.totals[i], e.totals)) and bool(torch.equal(batch.image[i], e.image))
+               for i, e in enumerate(engines))
+    steps_per_run = int(batch.totals[:, 7].sum().item())
+
+    def timed(fn):
+        tot = 0.0
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b) / 1e3
+        return tot
+
+    t_batch = timed(g.replay)
+    t_plain = timed(plain)
+    return {"value": steps * steps_per_run / t_batch, "unit": UNIT,
+            "plain_sequential": steps * steps_per_run / t_plain, "speedup": t_plain / t_batch,
+            "ms_batched": 1e3 * t_batch / steps, "ms_plain": 1e3 * t_plain / steps,
+            "media": len(media), "photons": int(sum(nph)), "photon_steps": steps_per_run,
+            "identical_tallies": same, "tuned": {k: tune[k] for k in ("block_size", "item_photons")},
+            "workload": "64 media: d log-uniform 1-10 um, tau uniform 0.5-20, photons log-uniform 1e6-1e8 "
+                        "(numpy Philox seed 2026), 128x128 image, Mie tables, graph-captured batch vs "
+                        "64 sequential launches"}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -295,6 +363,8 @@ def run_engine(args):
             "steps_per_photon": steps_per_run / N_PHOTONS,
             "e2e": e2e,
             "gpu_launches": args.steps, "clocks": clk, "roofline": roof}
+    if not args.no_batched and ws == 1:
+        line["batched"] = batched_comparison(E, dev, args.steps, args.warmup, flush)
     if not args.no_peaks:
         from paper_2507_23189_gb300 import peaks
         pk = peaks.measure(dev)
@@ -317,6 +387,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling)")
     ap.add_argument("--no-peaks", action="store_true", help="skip the issue-rate microbenchmarks")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-launch comparison")
     ap.add_argument("--photons", type=int, default=N_PHOTONS,
                     help="photons per step (default: the workload's 1e8; smaller for profiling)")
     args = ap.parse_args()

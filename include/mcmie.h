@@ -199,6 +199,25 @@ mc_status mc_run_static(const mc_medium *medium, const mc_geometry *geom,
                         int64_t *d_image, int64_t *d_radial, int64_t *d_totals,
                         uint32_t *d_error, void *stream);
 
+/* Many media in one launch (work items: a medium and a chunk of its photons;
+ * each CTA takes items from a queue, largest estimated cost first, keeps the
+ * medium's table staged in shared memory while consecutive items share it).
+ * All instances share geometry, camera and run parameters (run->n_photons,
+ * photon_offset and seed are ignored; each instance has its own), and one
+ * phase kind and table size. item_photons: photons per work item (0: 2^17).
+ * Tallies per instance as for mc_run, bit-identical to running each instance
+ * with mc_run. d_work: mc_batch_workspace_bytes(n) bytes. At most 64 media. */
+typedef struct {
+    mc_medium medium;
+    uint64_t n_photons, photon_offset, seed;
+    int64_t *d_image, *d_radial, *d_totals;  /* device, [nz][nx], [n_radial], [MC_N_TOTALS] */
+} mc_instance;
+size_t mc_batch_workspace_bytes(int n_instances);
+mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom,
+                       const mc_camera *camera, const mc_run_params *run,
+                       uint64_t item_photons, uint32_t *d_error, void *d_work,
+                       size_t work_bytes, void *stream);
+
 /* Host-buffer form of mc_run, for callers whose inputs and outputs live in
  * host memory. The table blob (mc_table_bytes(n_bins) bytes, or NULL for
  * MC_PHASE_HG) is copied to the device, the walk runs, and image, radial

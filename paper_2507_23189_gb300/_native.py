@@ -22,7 +22,7 @@ TRACE_WORDS = 12
 # every symbol include/mcmie.h declares
 EXPORTS = ("mc_table_bytes", "mie_table_build", "mc_medium_from_density", "mc_workspace_bytes",
            "mc_run", "mc_host_workspace_bytes", "mc_run_host", "mc_trace", "mc_check", "mc_philox",
-           "mc_status_string", "mc_run_static")
+           "mc_status_string", "mc_run_static", "mc_batch_workspace_bytes", "mc_run_batch")
 
 
 class McError(RuntimeError):
@@ -69,6 +69,12 @@ class RunParams(C.Structure):
                 ("block_size", C.c_int), ("blocks_per_sm", C.c_int), ("image_mode", C.c_int)]
 
 
+class Instance(C.Structure):
+    _fields_ = [("medium", Medium), ("n_photons", C.c_uint64), ("photon_offset", C.c_uint64),
+                ("seed", C.c_uint64), ("d_image", C.c_void_p), ("d_radial", C.c_void_p),
+                ("d_totals", C.c_void_p)]
+
+
 class Tallies(C.Structure):
     _fields_ = [("d_image", C.c_void_p), ("d_radial", C.c_void_p), ("d_totals", C.c_void_p),
                 ("d_error", C.c_void_p), ("d_work", C.c_void_p), ("work_bytes", C.c_size_t)]
@@ -112,6 +118,11 @@ def lib():
     L.mc_philox.argtypes = [vp, C.c_uint64, C.c_uint64, vp, vp]
     L.mc_run_static.restype = C.c_int
     L.mc_run_static.argtypes = [P(Medium), P(Geometry), P(Camera), P(RunParams), vp, vp, vp, vp, vp]
+    L.mc_batch_workspace_bytes.restype = C.c_size_t
+    L.mc_batch_workspace_bytes.argtypes = [C.c_int]
+    L.mc_run_batch.restype = C.c_int
+    L.mc_run_batch.argtypes = [C.c_int, P(Instance), P(Geometry), P(Camera), P(RunParams), C.c_uint64,
+                               vp, vp, C.c_size_t, vp]
     L.mc_status_string.restype = C.c_char_p
     L.mc_status_string.argtypes = [C.c_int]
     _lib = L

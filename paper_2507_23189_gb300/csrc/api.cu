@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <new>
 
 #include "engine.h"
 #include "table_format.h"
@@ -74,55 +75,74 @@ mc_status check_tallies(const mc_tallies *t, const mc_camera *c)
     return MC_OK;
 }
 
+void fill_medium(mcx::MediumArgs &m, const mc_medium *med, uint64_t n_photons, uint64_t offset,
+                 uint64_t seed, int64_t *image, int64_t *radial, int64_t *totals)
+{
+    const double mu_ext = med->mu_s + med->mu_a;
+    m.mu_ext = (float)mu_ext;
+    m.inv_mu_ext = (float)(1.0 / mu_ext);
+    m.absorb_frac = (float)(med->mu_a / mu_ext);
+    m.albedo = (float)(1.0 - med->mu_a / mu_ext);
+    const double gg = (med->phase_kind == MC_PHASE_HG) ? med->hg_g : 0.0;
+    m.hg_g = (float)gg;
+    m.hg_one_m_g = (float)(1.0 - gg);
+    m.hg_two_g = (float)(2.0 * gg);
+    m.hg_A = (float)(2.0 * (1.0 - gg) * (1.0 - gg));
+    m.hg_a2 = (float)((1.0 - gg) * (1.0 - gg));
+    m.hg_K = (float)((1.0 - gg * gg) / (4.0 * kPi));
+    m.table = (med->phase_kind == MC_PHASE_TABLE) ? static_cast<const unsigned char *>(med->d_table) : nullptr;
+    m.key0 = (uint32_t)seed;
+    m.key1 = (uint32_t)(seed >> 32);
+    m.n_photons = n_photons;
+    m.photon_offset = offset;
+    m.image = reinterpret_cast<unsigned long long *>(image);
+    m.radial = reinterpret_cast<unsigned long long *>(radial);
+    m.totals = reinterpret_cast<unsigned long long *>(totals);
+}
+
+void fill_common(mcx::CommonArgs &c, const mc_medium *m, const mc_geometry *g, const mc_camera *cam,
+                 const mc_run_params *r, uint32_t *error)
+{
+    c.phase_kind = m->phase_kind;
+    c.table_bytes = (m->phase_kind == MC_PHASE_TABLE) ? (uint32_t)mc_table_layout(m->n_bins, nullptr) : 0u;
+    c.n_bins = (m->phase_kind == MC_PHASE_TABLE) ? m->n_bins : 0;
+    c.lx = (float)g->lx;
+    c.hy = (float)(0.5 * g->ly);
+    c.hz = (float)(0.5 * g->lz);
+    c.beam_r = (float)g->beam_radius;
+    c.nx = cam->nx;
+    c.nz = cam->nz;
+    c.n_radial = cam->n_radial;
+    c.sx = (float)(cam->nx / g->lx);
+    c.sz = (float)(cam->nz / g->lz);
+    c.sr = (float)(cam->n_radial / cam->r_max);
+    c.rr_thr = (float)r->rr_threshold;
+    c.rr_surv = (float)r->rr_survival;
+    c.inv_rr_surv = r->rr_survival > 0 ? (float)(1.0 / r->rr_survival) : 0.0f;
+    c.max_events = r->max_events;
+    c.max_scatter = r->max_scatter;
+    c.img_scale = std::ldexp(1.0f, r->image_frac_bits);
+    c.error = error;
+}
+
 mcx::WalkArgs make_args(const mc_medium *m, const mc_geometry *g, const mc_camera *c,
                         const mc_run_params *r, const mc_tallies *t)
 {
     mcx::WalkArgs a;
     std::memset(&a, 0, sizeof a);
-    const double mu_ext = m->mu_s + m->mu_a;
-    a.mu_ext = (float)mu_ext;
-    a.inv_mu_ext = (float)(1.0 / mu_ext);
-    a.absorb_frac = (float)(m->mu_a / mu_ext);
-    a.albedo = (float)(1.0 - m->mu_a / mu_ext);
-    a.phase_kind = m->phase_kind;
-    const double gg = (m->phase_kind == MC_PHASE_HG) ? m->hg_g : 0.0;
-    a.hg_g = (float)gg;
-    a.hg_one_m_g = (float)(1.0 - gg);
-    a.hg_two_g = (float)(2.0 * gg);
-    a.hg_A = (float)(2.0 * (1.0 - gg) * (1.0 - gg));
-    a.hg_a2 = (float)((1.0 - gg) * (1.0 - gg));
-    a.hg_K = (float)((1.0 - gg * gg) / (4.0 * kPi));
-    if (m->phase_kind == MC_PHASE_TABLE) {
-        a.table = static_cast<const unsigned char *>(m->d_table);
-        a.table_bytes = (uint32_t)mc_table_layout(m->n_bins, nullptr);
-        a.n_bins = m->n_bins;
-    }
-    a.lx = (float)g->lx;
-    a.hy = (float)(0.5 * g->ly);
-    a.hz = (float)(0.5 * g->lz);
-    a.beam_r = (float)g->beam_radius;
-    a.nx = c->nx;
-    a.nz = c->nz;
-    a.n_radial = c->n_radial;
-    a.sx = (float)(c->nx / g->lx);
-    a.sz = (float)(c->nz / g->lz);
-    a.sr = (float)(c->n_radial / c->r_max);
-    a.n_photons = r->n_photons;
-    a.photon_offset = r->photon_offset;
-    a.key0 = (uint32_t)r->seed;
-    a.key1 = (uint32_t)(r->seed >> 32);
-    a.rr_thr = (float)r->rr_threshold;
-    a.rr_surv = (float)r->rr_survival;
-    a.inv_rr_surv = r->rr_survival > 0 ? (float)(1.0 / r->rr_survival) : 0.0f;
-    a.max_events = r->max_events;
-    a.max_scatter = r->max_scatter;
-    a.img_scale = std::ldexp(1.0f, r->image_frac_bits);
-    a.image = reinterpret_cast<unsigned long long *>(t->d_image);
-    a.radial = reinterpret_cast<unsigned long long *>(t->d_radial);
-    a.totals = reinterpret_cast<unsigned long long *>(t->d_totals);
-    a.error = t->d_error;
+    fill_common(a.c, m, g, c, r, t->d_error);
+    fill_medium(a.m, m, r->n_photons, r->photon_offset, r->seed, t->d_image, t->d_radial, t->d_totals);
     a.counter = reinterpret_cast<unsigned long long *>(t->d_work);
     return a;
+}
+
+mcx::LaunchCfg launch_cfg(const mc_run_params *r)
+{
+    mcx::LaunchCfg cfg;
+    cfg.block = r->block_size;
+    cfg.blocks_per_sm = r->blocks_per_sm;
+    cfg.image_mode = r->image_mode;
+    return cfg;
 }
 
 mc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MC_OK : MC_ERR_CUDA; }
@@ -157,14 +177,10 @@ mc_status run_common(const mc_medium *m, const mc_geometry *g, const mc_camera *
     if ((e = cudaMemsetAsync(t->d_work, 0, sizeof(unsigned long long), st))) return cuda_status(e);
     if (r->n_photons == 0) return MC_OK;
     mcx::WalkArgs a = make_args(m, g, c, r, t);
-    a.trace = trace;
-    a.n_trace = n_trace;
-    a.n_trace_events = n_events;
-    mcx::LaunchCfg cfg;
-    cfg.block = r->block_size;
-    cfg.blocks_per_sm = r->blocks_per_sm;
-    cfg.image_mode = r->image_mode;
-    e = mcx::launch_walk(a, trace != nullptr, cfg, st);
+    a.c.trace = trace;
+    a.c.n_trace = n_trace;
+    a.c.n_trace_events = n_events;
+    e = mcx::launch_walk(a, trace != nullptr, launch_cfg(r), st);
     if (e == cudaErrorInvalidValue) return MC_ERR_ARG;  // requested image tile does not fit
     return cuda_status(e);
 }
@@ -274,6 +290,81 @@ mc_status mc_run_host(const mc_medium *medium, const void *table, const mc_geome
     if (*error & MC_EFLAG_OVERFLOW) return MC_ERR_OVERFLOW;
     if (*error & MC_EFLAG_EVENTS) return MC_ERR_EVENTS;
     return MC_OK;
+}
+
+size_t mc_batch_workspace_bytes(int n_instances)
+{
+    if (n_instances < 1 || n_instances > mcx::kMaxBatch) return 0;
+    return kAlign;  // the work-item queue counter
+}
+
+mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom, const mc_camera *camera,
+                       const mc_run_params *run, uint64_t item_photons, uint32_t *d_error, void *d_work,
+                       size_t work_bytes, void *stream)
+{
+    if (n < 1 || n > mcx::kMaxBatch || !inst || !d_error || !d_work || !aligned(d_work, 16) ||
+        !aligned(d_error, 4))
+        return MC_ERR_ARG;
+    if (work_bytes < mc_batch_workspace_bytes(n)) return MC_ERR_NOMEM;
+    mc_status s;
+    if ((s = check_geom(geom)) != MC_OK || (s = check_camera(camera)) != MC_OK ||
+        (s = check_run(run)) != MC_OK)
+        return s;
+    for (int i = 0; i < n; ++i) {
+        const mc_instance &I = inst[i];
+        if ((s = check_medium(&I.medium)) != MC_OK) return s;
+        if (I.medium.phase_kind != inst[0].medium.phase_kind ||
+            (I.medium.phase_kind == MC_PHASE_TABLE && I.medium.n_bins != inst[0].medium.n_bins))
+            return MC_ERR_ARG;   // one phase kind and table size per batch
+        if (!I.d_image || !I.d_radial || !I.d_totals || !aligned(I.d_image, 8) || !aligned(I.d_radial, 8) ||
+            !aligned(I.d_totals, 8) || I.photon_offset + I.n_photons < I.photon_offset)
+            return MC_ERR_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (!run->accumulate)
+        for (int i = 0; i < n; ++i) {
+            if ((e = cudaMemsetAsync(inst[i].d_image, 0, sizeof(int64_t) * (size_t)camera->nx * camera->nz, st)) ||
+                (e = cudaMemsetAsync(inst[i].d_radial, 0, sizeof(int64_t) * (size_t)camera->n_radial, st)) ||
+                (e = cudaMemsetAsync(inst[i].d_totals, 0, sizeof(int64_t) * MC_N_TOTALS, st)))
+                return MC_ERR_CUDA;
+        }
+    if ((e = cudaMemsetAsync(d_work, 0, sizeof(unsigned long long), st))) return MC_ERR_CUDA;
+
+    // largest estimated cost first: photons x (1 + optical depth along the beam)
+    int order[mcx::kMaxBatch];
+    double cost[mcx::kMaxBatch];
+    for (int i = 0; i < n; ++i) {
+        order[i] = i;
+        cost[i] = (double)inst[i].n_photons * (1.0 + (inst[i].medium.mu_s + inst[i].medium.mu_a) * geom->lx);
+    }
+    for (int i = 1; i < n; ++i)   // stable insertion sort, descending
+        for (int j = i; j > 0 && cost[order[j]] > cost[order[j - 1]]; --j) {
+            int t = order[j]; order[j] = order[j - 1]; order[j - 1] = t;
+        }
+    unsigned long long ip = item_photons;
+    if (ip == 0) ip = 1ull << 17;
+    mcx::BatchArgs *a = new (std::nothrow) mcx::BatchArgs;
+    if (!a) return MC_ERR_NOMEM;
+    std::memset(a, 0, sizeof *a);
+    fill_common(a->c, &inst[0].medium, geom, camera, run, d_error);
+    a->n_media = n;
+    a->item_photons = ip;
+    a->queue = static_cast<unsigned long long *>(d_work);
+    a->item_begin[0] = 0;
+    for (int k = 0; k < n; ++k) {
+        const mc_instance &I = inst[order[k]];
+        fill_medium(a->m[k], &I.medium, I.n_photons, I.photon_offset, I.seed, I.d_image, I.d_radial, I.d_totals);
+        a->item_begin[k + 1] = a->item_begin[k] + (I.n_photons + ip - 1) / ip;
+    }
+    if (a->item_begin[n] == 0) {
+        delete a;
+        return MC_OK;
+    }
+    e = mcx::launch_batch(*a, launch_cfg(run), st);
+    delete a;
+    if (e == cudaErrorInvalidValue) return MC_ERR_ARG;
+    return cuda_status(e);
 }
 
 mc_status mc_check(const uint32_t *d_error, void *stream)

@@ -7,19 +7,24 @@
 
 namespace mcx {
 
-// Everything a walk launch needs, already validated and converted to the
-// precision the kernels use. Passed by value as a __grid_constant__ argument.
-struct WalkArgs {
-    // medium
+// Per-medium parameters, already validated and in the kernels' precision.
+struct MediumArgs {
     float mu_ext, inv_mu_ext;   // mm^-1, mm
     float albedo;               // 1 - mu_a/mu_ext (Eq. 16 factor)
     float absorb_frac;          // mu_a/mu_ext
-    int phase_kind;             // MC_PHASE_TABLE / MC_PHASE_HG
     float hg_g, hg_one_m_g, hg_two_g;
     float hg_A;                 // 2 (1-g)^2        (sampling)
     float hg_a2;                // (1-g)^2           (density)
     float hg_K;                 // (1-g^2) / (4 pi)  (density per sr)
     const unsigned char *table; // packed blob in global memory (table_format.h)
+    uint32_t key0, key1;        // Philox key (seed)
+    unsigned long long n_photons, photon_offset;
+    unsigned long long *image, *radial, *totals;  // this medium's tallies
+};
+
+// Parameters shared by every medium of a launch.
+struct CommonArgs {
+    int phase_kind;             // MC_PHASE_TABLE / MC_PHASE_HG (one per launch)
     uint32_t table_bytes;
     int n_bins;
     // geometry
@@ -28,21 +33,36 @@ struct WalkArgs {
     int nx, nz, n_radial;
     float sx, sz, sr;           // nx/lx, nz/lz, n_radial/r_max
     // run
-    unsigned long long n_photons, photon_offset;
-    uint32_t key0, key1;
     float rr_thr, rr_surv, inv_rr_surv;
     uint32_t max_events, max_scatter;
     float img_scale;            // 2^image_frac_bits
-    // outputs
-    unsigned long long *image, *radial, *totals;
     uint32_t *error;
-    unsigned long long *counter;  // photon counter in the caller's workspace
-    // trace (trace kernels only)
-    int32_t *trace;
-    int n_trace, n_trace_events;
     // image rows [band0, band0 + band_rows) are privatised in shared memory
     // (set by the launcher; band_rows = nz for a whole-image tile)
     int band0, band_rows;
+    // trace (trace kernels only)
+    int32_t *trace;
+    int n_trace, n_trace_events;
+};
+
+// One medium, one photon range. Passed by value as a __grid_constant__.
+struct WalkArgs {
+    CommonArgs c;
+    MediumArgs m;
+    unsigned long long *counter;  // photon counter in the caller's workspace
+};
+
+// Many media in one launch: work items (medium, chunk of item_photons
+// photons) are numbered medium by medium in the order of m[]; medium i owns
+// items [item_begin[i], item_begin[i+1]).
+constexpr int kMaxBatch = 64;
+struct BatchArgs {
+    CommonArgs c;
+    int n_media;
+    unsigned long long item_photons;
+    unsigned long long *queue;    // work-item counter in the caller's workspace
+    unsigned long long item_begin[kMaxBatch + 1];
+    MediumArgs m[kMaxBatch];
 };
 
 struct LaunchCfg {
@@ -56,6 +76,9 @@ struct LaunchCfg {
 // Launch the walk (or its trace variant) on `stream`. Returns cudaSuccess or
 // the launch error.
 cudaError_t launch_walk(const WalkArgs &a, bool trace, const LaunchCfg &cfg, cudaStream_t stream);
+
+// Launch the batched walk (phase fixed by c.phase_kind) on `stream`.
+cudaError_t launch_batch(const BatchArgs &a, const LaunchCfg &cfg, cudaStream_t stream);
 
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out,
                           cudaStream_t stream);

@@ -256,15 +256,51 @@ extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *
         uint16_t *gd = reinterpret_cast<uint16_t *>(blob + H.off_guide);
         for (int i = 0; i <= n; ++i) fo[i] = (float)omu[i];
         for (int j = 0; j < n; ++j) fp[j] = (float)pdf[j];
-        // guide[c]: bin holding cos(theta) = -1 + 2c/G (largest j with
-        // 1 - omu[j] <= that cosine), c = 0..G.
+        // guide[c] brackets the camera-density lookup. The kernel finds the
+        // bin of a direction cosine m (float) as the largest j with
+        // fo[j] >= 1 - m (float subtraction), starting from the cell
+        // c = floor(fl(m + 1) * G/2). Both are monotone in m, so with lo(c) the
+        // smallest float whose cell is c, guide[c] = bin(lo(c)) and
+        // guide[c+1] bound the bins of every m in cell c. Computed here with
+        // the same single-precision operations the kernel performs.
         const int G = H.n_guide;
-        int j = 0;
-        for (int c = 0; c <= G; ++c) {
-            double mu = -1.0 + 2.0 * c / G;
-            while (j < n - 1 && 1.0 - omu[j + 1] <= mu) ++j;
-            gd[c] = (uint16_t)j;
+        const float half_g = 0.5f * (float)G;
+        auto cell_of = [&](float m) {
+            volatile float t = m + 1.0f;
+            return (int)std::floor((float)(t * half_g));
+        };
+        auto bin_of = [&](float m) {
+            volatile float om = 1.0f - m;
+            int lo = 0, hi = n - 1;   // fo[0] = 2 >= om always
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (fo[mid] >= om) lo = mid; else hi = mid - 1;
+            }
+            return lo;
+        };
+        // floats in increasing order <-> unsigned keys in increasing order
+        auto key_of = [](float f) {
+            uint32_t b;
+            std::memcpy(&b, &f, 4);
+            return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+        };
+        auto float_of = [](uint32_t k) {
+            uint32_t b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+            float f;
+            std::memcpy(&f, &b, 4);
+            return f;
+        };
+        gd[0] = (uint16_t)bin_of(-1.0f);
+        for (int c = 1; c < G; ++c) {
+            // smallest float m in [-1, 1] with cell_of(m) >= c, by bisection on keys
+            uint32_t lo = key_of(-1.0f), hi = key_of(1.0f);
+            while (lo < hi) {
+                uint32_t mid = lo + (hi - lo) / 2;
+                if (cell_of(float_of(mid)) >= c) hi = mid; else lo = mid + 1;
+            }
+            gd[c] = (uint16_t)bin_of(float_of(lo));
         }
+        gd[G] = (uint16_t)bin_of(1.0f);
     }
     return MC_OK;
 }

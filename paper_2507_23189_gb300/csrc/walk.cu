@@ -73,14 +73,23 @@ __device__ __forceinline__ void sadd64(unsigned long long *p, long long v)
     if (up) atomicAdd(w + 1, up);
 }
 
-// Bulk-copy `bytes` (multiple of 16) from global to shared memory, bounded wait.
-__device__ bool stage_bulk(void *dst, const void *src, uint32_t bytes, unsigned long long *mbar,
-                           uint32_t *err)
+// mbarrier for the table copies; initialised once per CTA by thread 0.
+__device__ __forceinline__ void mbar_init(unsigned long long *mbar)
 {
     const uint32_t bar = smem_u32(mbar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Bulk-copy `bytes` (multiple of 16) from global to shared memory and wait
+// (bounded) for the mbarrier phase `parity` to complete. Every thread of the
+// CTA must call it; the previous contents of dst must no longer be in use.
+__device__ bool stage_bulk(void *dst, const void *src, uint32_t bytes, unsigned long long *mbar,
+                           uint32_t parity, uint32_t *err)
+{
+    const uint32_t bar = smem_u32(mbar);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                      : "memory");
@@ -90,14 +99,13 @@ __device__ bool stage_bulk(void *dst, const void *src, uint32_t bytes, unsigned 
             "l"(src), "r"(bytes), "r"(bar)
             : "memory");
     }
-    __syncthreads();
     uint32_t done = 0;
     for (uint32_t it = 0; it < WAIT_LIMIT && !done; ++it) {
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             " selp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
-            : "r"(bar)
+            : "r"(bar), "r"(parity)
             : "memory");
     }
     if (!done && threadIdx.x == 0) atomicOr(err, MC_EFLAG_TIMEOUT);
@@ -108,9 +116,8 @@ __device__ bool stage_bulk(void *dst, const void *src, uint32_t bytes, unsigned 
 __device__ __forceinline__ int table_bin(const float *omu, const uint16_t *guide, int n, float muc)
 {
     muc = fminf(fmaxf(muc, -1.0f), 1.0f);
-    int cell = min(__float2int_rd((muc + 1.0f) * (0.5f * n)), n - 1);
-    int lo = max((int)guide[cell] - 1, 0);
-    int hi = min((int)guide[cell + 1] + 1, n - 1);
+    const int cell = min(__float2int_rd((muc + 1.0f) * (0.5f * n)), n - 1);
+    int lo = guide[cell], hi = guide[cell + 1];   // exact bracket (host-built)
     const float om = 1.0f - muc;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
@@ -120,14 +127,14 @@ __device__ __forceinline__ int table_bin(const float *omu, const uint16_t *guide
 }
 
 template <bool TRACE>
-__device__ __forceinline__ void trace_write(const WalkArgs &A, unsigned long long rel, uint32_t ev,
+__device__ __forceinline__ void trace_write(const CommonArgs &C, unsigned long long rel, uint32_t ev,
                                             int status, float rx, float ry, float rz, float dx,
                                             float dy, float dz, float w, float nee, int pix, int nb,
                                             int rb)
 {
     if (!TRACE) return;
-    if (rel >= (unsigned long long)A.n_trace || ev >= (uint32_t)A.n_trace_events) return;
-    int32_t *t = A.trace + (rel * A.n_trace_events + ev) * 12;
+    if (rel >= (unsigned long long)C.n_trace || ev >= (uint32_t)C.n_trace_events) return;
+    int32_t *t = C.trace + (rel * C.n_trace_events + ev) * 12;
     t[0] = status;
     t[1] = __float_as_int(rx); t[2] = __float_as_int(ry); t[3] = __float_as_int(rz);
     t[4] = __float_as_int(dx); t[5] = __float_as_int(dy); t[6] = __float_as_int(dz);
@@ -136,52 +143,116 @@ __device__ __forceinline__ void trace_write(const WalkArgs &A, unsigned long lon
     t[9] = pix; t[10] = nb; t[11] = rb;
 }
 
-// Shared-memory layout: [table blob][image band][radial][totals][mbarrier]
-// SMEM_IMAGE: image rows [band0, band0 + band_rows) accumulate in shared
-// memory (the whole image when band_rows = nz); other rows go to L2 atomics.
-template <int PHASE, bool SMEM_IMAGE, bool TRACE>
-__global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ WalkArgs A)
+// Shared memory of a walk CTA:
+//   [table blob][image band][radial][totals][mbarrier][item][pool]
+struct Smem {
+    unsigned char *table;
+    unsigned long long *img, *rad, *tot, *bar, *item, *pool;
+    int npix;                 // privatised image pixels (band rows x nx)
+    const float *omu, *pdf;
+    const uint16_t *guide;
+};
+
+template <int PHASE, bool SMEM_IMAGE>
+__device__ __forceinline__ Smem carve(unsigned char *smem, const CommonArgs &C)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const uint32_t tb = (PHASE == MC_PHASE_TABLE) ? A.table_bytes : 0u;
-    const int npix = SMEM_IMAGE ? A.nx * A.band_rows : 0;   // privatised pixels
-    unsigned long long *s_img = reinterpret_cast<unsigned long long *>(smem + tb);
-    unsigned long long *s_rad = s_img + npix;
-    unsigned long long *s_tot = s_rad + A.n_radial;
-    unsigned long long *s_bar = s_tot + MC_N_TOTALS;
+    Smem S;
+    const uint32_t tb = (PHASE == MC_PHASE_TABLE) ? C.table_bytes : 0u;
+    S.table = smem;
+    S.npix = SMEM_IMAGE ? C.nx * C.band_rows : 0;
+    S.img = reinterpret_cast<unsigned long long *>(smem + tb);
+    S.rad = S.img + S.npix;
+    S.tot = S.rad + C.n_radial;
+    S.bar = S.tot + MC_N_TOTALS;
+    S.item = S.bar + 1;
+    S.pool = S.item + 1;
+    S.omu = S.pdf = nullptr;
+    S.guide = nullptr;
+    return S;
+}
 
-    for (int i = threadIdx.x; i < npix + A.n_radial + MC_N_TOTALS; i += blockDim.x)
-        s_img[i] = 0ull;
+__device__ __forceinline__ void zero_tallies(const Smem &S, const CommonArgs &C)
+{
+    for (int i = threadIdx.x; i < S.npix + C.n_radial + MC_N_TOTALS; i += blockDim.x) S.img[i] = 0ull;
+}
 
-    const float *omu = nullptr, *pdf = nullptr;
-    const uint16_t *guide = nullptr;
-    if (PHASE == MC_PHASE_TABLE) {
-        if (!stage_bulk(smem, A.table, tb, s_bar, A.error)) return;
-        const mc_table_header *h = reinterpret_cast<const mc_table_header *>(smem);
-        if (h->magic != MC_TABLE_MAGIC || h->n_bins != A.n_bins || h->total_bytes != tb) {
-            if (threadIdx.x == 0) atomicOr(A.error, MC_EFLAG_TABLE);
-            return;
-        }
-        omu = reinterpret_cast<const float *>(smem + h->off_omu);
-        pdf = reinterpret_cast<const float *>(smem + h->off_pdf);
-        guide = reinterpret_cast<const uint16_t *>(smem + h->off_guide);
-    } else {
-        __syncthreads();
+// Table pointers into the staged blob; false (and the error flag) if its
+// header does not describe the expected table.
+__device__ __forceinline__ bool bind_table(Smem &S, const CommonArgs &C)
+{
+    const mc_table_header *h = reinterpret_cast<const mc_table_header *>(S.table);
+    if (h->magic != MC_TABLE_MAGIC || h->n_bins != C.n_bins || h->total_bytes != C.table_bytes) {
+        if (threadIdx.x == 0) atomicOr(C.error, MC_EFLAG_TABLE);
+        return false;
     }
+    S.omu = reinterpret_cast<const float *>(S.table + h->off_omu);
+    S.pdf = reinterpret_cast<const float *>(S.table + h->off_pdf);
+    S.guide = reinterpret_cast<const uint16_t *>(S.table + h->off_guide);
+    return true;
+}
 
+// Per-thread tallies, reduced when a CTA finishes a medium.
+struct Tally {
+    unsigned long long steps;
+    long long refl, far, side, ball, abs;
+};
+
+// Warp -> shared -> the medium's global tallies (one atomic per nonzero entry).
+template <bool SMEM_IMAGE>
+__device__ void flush(const CommonArgs &C, const MediumArgs &M, const Smem &S, Tally &T)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T.steps += __shfl_xor_sync(FULL, T.steps, o);
+        T.refl += __shfl_xor_sync(FULL, T.refl, o);
+        T.far += __shfl_xor_sync(FULL, T.far, o);
+        T.side += __shfl_xor_sync(FULL, T.side, o);
+        T.ball += __shfl_xor_sync(FULL, T.ball, o);
+        T.abs += __shfl_xor_sync(FULL, T.abs, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sadd64(&S.tot[MC_TOT_STEPS], (long long)T.steps);
+        sadd64(&S.tot[MC_TOT_REFLECT], T.refl);
+        sadd64(&S.tot[MC_TOT_FAR], T.far);
+        sadd64(&S.tot[MC_TOT_SIDE], T.side);
+        sadd64(&S.tot[MC_TOT_BALLISTIC], T.ball);
+        sadd64(&S.tot[MC_TOT_ABSORB], T.abs);
+    }
+    T = Tally{0ull, 0ll, 0ll, 0ll, 0ll, 0ll};
+    __syncthreads();
+    if (SMEM_IMAGE) {
+        unsigned long long *g = M.image + (size_t)C.band0 * C.nx;
+        for (int i = threadIdx.x; i < S.npix; i += blockDim.x)
+            if (S.img[i]) atomicAdd(&g[i], S.img[i]);
+    }
+    for (int i = threadIdx.x; i < C.n_radial; i += blockDim.x)
+        if (S.rad[i]) atomicAdd(&M.radial[i], S.rad[i]);
+    for (int i = threadIdx.x; i < MC_N_TOTALS; i += blockDim.x)
+        if (S.tot[i]) atomicAdd(&M.totals[i], S.tot[i]);
+    __syncthreads();
+}
+
+// The photon walk over indices [.., limit) of medium M: every warp refills
+// lanes whose photon ended from chunks of `chunk` indices obtained by
+// grab() (called by lane 0), until the range is exhausted.
+template <int PHASE, bool SMEM_IMAGE, bool TRACE, class Grab>
+__device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs &M, const Smem &S,
+                                          unsigned long long limit, unsigned chunk, Grab grab,
+                                          Tally &T)
+{
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
     unsigned long long pool_next = 0, pool_end = 0;  // warp-uniform
+    const float *omu = S.omu, *pdf = S.pdf;
+    const uint16_t *guide = S.guide;
+    unsigned long long *s_img = S.img, *s_rad = S.rad, *s_tot = S.tot;
 
     // photon state
     bool alive = false, done = false;
-    unsigned long long rel = 0;     // index within the range
+    unsigned long long rel = 0;     // index within the medium's range
     uint32_t pk0 = 0, pk1 = 0;      // global photon index, lo/hi words
     uint32_t ev = 0, ncoll = 0;
     float rx = 0, ry = 0, rz = 0, dx = 1, dy = 0, dz = 0, w = 1;
-    // per-thread tallies, reduced once at the end (no contention)
-    unsigned long long my_steps = 0;
-    long long t_refl = 0, t_far = 0, t_side = 0, t_ball = 0, t_abs = 0;
 
     while (true) {
         // -------- refill lanes whose photon ended
@@ -196,16 +267,16 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
                 pool_next += n_need;
             } else {
                 unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(A.counter, (unsigned long long)CHUNK);
+                if (lane == 0) base = grab();
                 base = __shfl_sync(FULL, base, 0);
                 mine = (rank < avail) ? pool_next + rank : base + (rank - avail);
                 pool_next = base + (n_need - avail);
-                pool_end = base + CHUNK;
+                pool_end = base + chunk;
             }
             if (!alive && !done) {
-                if (mine < A.n_photons) {
+                if (mine < limit) {
                     rel = mine;
-                    const unsigned long long p = A.photon_offset + mine;
+                    const unsigned long long p = M.photon_offset + mine;
                     pk0 = (uint32_t)p;
                     pk1 = (uint32_t)(p >> 32);
                     ev = 0;
@@ -213,9 +284,9 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
                     rx = 0.f; ry = 0.f; rz = 0.f;
                     dx = 1.f; dy = 0.f; dz = 0.f;
                     w = 1.f;
-                    if (A.beam_r > 0.f) {
-                        const uint4 b = philox10(make_uint4(pk0, pk1, 0xFFFFFFFFu, 0u), A.key0, A.key1);
-                        const float rho = A.beam_r * sqrtf(u01(b.x));
+                    if (C.beam_r > 0.f) {
+                        const uint4 b = philox10(make_uint4(pk0, pk1, 0xFFFFFFFFu, 0u), M.key0, M.key1);
+                        const float rho = C.beam_r * sqrtf(u01(b.x));
                         float sp, cp;
                         sincospif(2.0f * u01(b.y), &sp, &cp);
                         ry = rho * cp;
@@ -232,16 +303,16 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
 
         // -------- one event
         const uint32_t e_now = ev;
-        const uint4 rnd = philox10(make_uint4(pk0, pk1, e_now, 0u), A.key0, A.key1);
+        const uint4 rnd = philox10(make_uint4(pk0, pk1, e_now, 0u), M.key0, M.key1);
         ++ev;
-        ++my_steps;
+        ++T.steps;
         const float u0 = u01(rnd.x), u1 = u01(rnd.y), u2 = u01(rnd.z), u3 = u01(rnd.w);
 
-        const float s = -logf(u0) * A.inv_mu_ext;                 // Eq. 15
+        const float s = -logf(u0) * M.inv_mu_ext;                 // Eq. 15
         const float px = fmaf(s, dx, rx), py = fmaf(s, dy, ry), pz = fmaf(s, dz, rz);
-        const bool cx = !((px > 0.f) & (px < A.lx));
-        const bool cy = !(fabsf(py) < A.hy);
-        const bool cz = !(fabsf(pz) < A.hz);
+        const bool cx = !((px > 0.f) & (px < C.lx));
+        const bool cy = !(fabsf(py) < C.hy);
+        const bool cz = !(fabsf(pz) < C.hz);
 
         if (cx | cy | cz) {
             // the flight reaches a wall: the first one crossed is the exit
@@ -251,38 +322,38 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
             if ((int)cx + (int)cy + (int)cz == 1) {
                 face = cx ? 0 : (cy ? 1 : 2);
             } else {
-                const float tx = cx ? (dx > 0.f ? (A.lx - rx) / dx : (0.f - rx) / dx) : INF;
-                const float ty = cy ? (dy > 0.f ? (A.hy - ry) / dy : (-A.hy - ry) / dy) : INF;
-                const float tz = cz ? (dz > 0.f ? (A.hz - rz) / dz : (-A.hz - rz) / dz) : INF;
+                const float tx = cx ? (dx > 0.f ? (C.lx - rx) / dx : (0.f - rx) / dx) : INF;
+                const float ty = cy ? (dy > 0.f ? (C.hy - ry) / dy : (-C.hy - ry) / dy) : INF;
+                const float tz = cz ? (dz > 0.f ? (C.hz - rz) / dz : (-C.hz - rz) / dz) : INF;
                 face = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
             }
             const long long wv = fix32(w);
             int status, rb = -1;
             float ex = px, ey = py, ez = pz;
             if (face == 0 && dx < 0.f) {
-                t_refl += wv;
+                T.refl += wv;
                 status = 1;
             } else if (face == 0) {
-                t_far += wv;
-                if (ncoll == 0) t_ball += wv;
-                const float t = (A.lx - rx) / dx;
-                ex = A.lx; ey = fmaf(t, dy, ry); ez = fmaf(t, dz, rz);
+                T.far += wv;
+                if (ncoll == 0) T.ball += wv;
+                const float t = (C.lx - rx) / dx;
+                ex = C.lx; ey = fmaf(t, dy, ry); ez = fmaf(t, dz, rz);
                 const float rho = sqrtf(fmaf(ey, ey, ez * ez));
-                rb = min(__float2int_rd(rho * A.sr), A.n_radial - 1);
+                rb = min(__float2int_rd(rho * C.sr), C.n_radial - 1);
                 sadd64(&s_rad[rb], wv);
                 status = 2;
             } else {
-                t_side += wv;
+                T.side += wv;
                 status = 3;
             }
             if (TRACE) {
                 if (face != 0 || dx < 0.f) {
                     const float t = face == 0 ? (0.f - rx) / dx
-                                  : face == 1 ? (dy > 0.f ? A.hy - ry : -A.hy - ry) / dy
-                                              : (dz > 0.f ? A.hz - rz : -A.hz - rz) / dz;
+                                  : face == 1 ? (dy > 0.f ? C.hy - ry : -C.hy - ry) / dy
+                                              : (dz > 0.f ? C.hz - rz : -C.hz - rz) / dz;
                     ex = fmaf(t, dx, rx); ey = fmaf(t, dy, ry); ez = fmaf(t, dz, rz);
                 }
-                trace_write<TRACE>(A, rel, e_now, status, ex, ey, ez, dx, dy, dz, w, 0.f, -1, -1, rb);
+                trace_write<TRACE>(C, rel, e_now, status, ex, ey, ez, dx, dy, dz, w, 0.f, -1, -1, rb);
             }
             alive = false;
             continue;
@@ -293,8 +364,8 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
         ++ncoll;
         {   // Eq. 16; the captured part w - w a is exact in single precision
             // for albedo a >= 1/2 (Sterbenz), so weight is conserved per photon
-            const float wn = w * A.albedo;
-            if (A.absorb_frac > 0.f) t_abs += fix32(w - wn);
+            const float wn = w * M.albedo;
+            if (M.absorb_frac > 0.f) T.abs += fix32(w - wn);
             w = wn;
         }
 
@@ -302,28 +373,28 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
         float psr;
         int nb = -1;
         if (PHASE == MC_PHASE_HG) {
-            const float t = fmaf(A.hg_two_g, 1.0f - dy, A.hg_a2);
-            psr = A.hg_K / (t * sqrtf(t));
+            const float t = fmaf(M.hg_two_g, 1.0f - dy, M.hg_a2);
+            psr = M.hg_K / (t * sqrtf(t));
         } else {
-            nb = table_bin(omu, guide, A.n_bins, dy);
+            nb = table_bin(omu, guide, C.n_bins, dy);
             psr = pdf[nb] * INV_2PI;
         }
-        const float nee = w * psr * expf(-A.mu_ext * (A.hy - ry));
-        const int ix = min(max(__float2int_rd(rx * A.sx), 0), A.nx - 1);
-        const int iz = min(max(__float2int_rd((rz + A.hz) * A.sz), 0), A.nz - 1);
-        const int pix = iz * A.nx + ix;
-        const float vf = nee * A.img_scale;
+        const float nee = w * psr * expf(-M.mu_ext * (C.hy - ry));
+        const int ix = min(max(__float2int_rd(rx * C.sx), 0), C.nx - 1);
+        const int iz = min(max(__float2int_rd((rz + C.hz) * C.sz), 0), C.nz - 1);
+        const int pix = iz * C.nx + ix;
+        const float vf = nee * C.img_scale;
         if (vf < 4.0e18f) {
             const long long v = __float2ll_rn(vf);
-            const unsigned brow = (unsigned)(iz - A.band0);
-            if (SMEM_IMAGE && brow < (unsigned)A.band_rows) sadd64(&s_img[brow * A.nx + ix], v);
-            else atomicAdd(&A.image[pix], (unsigned long long)v);
+            const unsigned brow = (unsigned)(iz - C.band0);
+            if (SMEM_IMAGE && brow < (unsigned)C.band_rows) sadd64(&s_img[brow * C.nx + ix], v);
+            else atomicAdd(&M.image[pix], (unsigned long long)v);
         } else {
-            atomicOr(A.error, (vf == vf) ? MC_EFLAG_OVERFLOW : MC_EFLAG_NUMERIC);
+            atomicOr(C.error, (vf == vf) ? MC_EFLAG_OVERFLOW : MC_EFLAG_NUMERIC);
         }
 
         int status = 0;
-        if (A.max_scatter && ncoll >= A.max_scatter) {
+        if (C.max_scatter && ncoll >= C.max_scatter) {
             sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
             status = 5;
             alive = false;
@@ -331,10 +402,10 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
             // polar angle as 1 - cos(theta), accurate near the forward peak
             float om;
             if (PHASE == MC_PHASE_HG) {
-                const float D = fmaf(A.hg_two_g, u1, A.hg_one_m_g);
-                om = A.hg_A * (1.0f - u1) * fmaf(A.hg_g, u1, 1.0f) / (D * D);
+                const float D = fmaf(M.hg_two_g, u1, M.hg_one_m_g);
+                om = M.hg_A * (1.0f - u1) * fmaf(M.hg_g, u1, 1.0f) / (D * D);
             } else {
-                const float tt = u1 * (float)A.n_bins;
+                const float tt = u1 * (float)C.n_bins;
                 const int i = (int)tt;
                 const float f = tt - (float)i;
                 const float o0 = omu[i], o1 = omu[i + 1];
@@ -356,9 +427,9 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
             const float inv = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
             dx = nx * inv; dy = ny * inv; dz = nz * inv;
             // weight threshold / roulette (Sec. 3.1.3)
-            if (w < A.rr_thr) {
-                if (u3 < A.rr_surv) {
-                    const float wn = w * A.inv_rr_surv;
+            if (w < C.rr_thr) {
+                if (u3 < C.rr_surv) {
+                    const float wn = w * C.inv_rr_surv;
                     sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w) - fix32(wn));
                     w = wn;
                 } else {
@@ -367,46 +438,96 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
                     alive = false;
                 }
             }
-            if (!(w == w)) atomicOr(A.error, MC_EFLAG_NUMERIC);
+            if (!(w == w)) atomicOr(C.error, MC_EFLAG_NUMERIC);
         }
-        trace_write<TRACE>(A, rel, e_now, status, rx, ry, rz, dx, dy, dz, status == 4 ? 0.f : w, nee,
+        trace_write<TRACE>(C, rel, e_now, status, rx, ry, rz, dx, dy, dz, status == 4 ? 0.f : w, nee,
                            pix, nb, -1);
-        if (alive && ev >= A.max_events) {
+        if (alive && ev >= C.max_events) {
             sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
-            atomicOr(A.error, MC_EFLAG_EVENTS);
-            trace_write<TRACE>(A, rel, ev, 6, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1, -1);
+            atomicOr(C.error, MC_EFLAG_EVENTS);
+            trace_write<TRACE>(C, rel, ev, 6, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1, -1);
             alive = false;
         }
     }
+}
 
-    // -------- per-thread tallies -> warp -> shared -> global
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_steps += __shfl_xor_sync(FULL, my_steps, o);
-        t_refl += __shfl_xor_sync(FULL, t_refl, o);
-        t_far += __shfl_xor_sync(FULL, t_far, o);
-        t_side += __shfl_xor_sync(FULL, t_side, o);
-        t_ball += __shfl_xor_sync(FULL, t_ball, o);
-        t_abs += __shfl_xor_sync(FULL, t_abs, o);
+// One medium: the table staged once, the whole photon range from a global
+// counter, tallies flushed once.
+template <int PHASE, bool SMEM_IMAGE, bool TRACE>
+__global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ WalkArgs A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    Smem S = carve<PHASE, SMEM_IMAGE>(smem, A.c);
+    zero_tallies(S, A.c);
+    if (threadIdx.x == 0) mbar_init(S.bar);
+    if (PHASE == MC_PHASE_TABLE) {
+        if (!stage_bulk(S.table, A.m.table, A.c.table_bytes, S.bar, 0u, A.c.error)) return;
+        if (!bind_table(S, A.c)) return;
+    } else {
+        __syncthreads();
     }
-    if (lane == 0) {
-        sadd64(&s_tot[MC_TOT_STEPS], (long long)my_steps);
-        sadd64(&s_tot[MC_TOT_REFLECT], t_refl);
-        sadd64(&s_tot[MC_TOT_FAR], t_far);
-        sadd64(&s_tot[MC_TOT_SIDE], t_side);
-        sadd64(&s_tot[MC_TOT_BALLISTIC], t_ball);
-        sadd64(&s_tot[MC_TOT_ABSORB], t_abs);
-    }
+    Tally T{0ull, 0ll, 0ll, 0ll, 0ll, 0ll};
+    unsigned long long *counter = A.counter;
+    walk_loop<PHASE, SMEM_IMAGE, TRACE>(A.c, A.m, S, A.m.n_photons, CHUNK,
+                                        [counter]() { return atomicAdd(counter, (unsigned long long)CHUNK); },
+                                        T);
+    flush<SMEM_IMAGE>(A.c, A.m, S, T);
+}
+
+// Many media: each CTA takes work items (medium, chunk of photons) from a
+// global queue; consecutive items of one medium reuse the staged table and
+// the shared-memory tallies, a change of medium flushes them and stages the
+// next table. Within an item the CTA's warps share the photons through a
+// shared-memory counter.
+constexpr unsigned BATCH_CHUNK = 32;
+
+template <int PHASE, bool SMEM_IMAGE>
+__global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ BatchArgs B)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    Smem S = carve<PHASE, SMEM_IMAGE>(smem, B.c);
+    zero_tallies(S, B.c);
+    if (threadIdx.x == 0) mbar_init(S.bar);
     __syncthreads();
-    if (SMEM_IMAGE) {
-        unsigned long long *g = A.image + (size_t)A.band0 * A.nx;
-        for (int i = threadIdx.x; i < npix; i += blockDim.x)
-            if (s_img[i]) atomicAdd(&g[i], s_img[i]);
+    const unsigned long long n_items = B.item_begin[B.n_media];
+    Tally T{0ull, 0ll, 0ll, 0ll, 0ll, 0ll};
+    int cur = -1;
+    uint32_t parity = 0;
+    while (true) {
+        if (threadIdx.x == 0) *S.item = atomicAdd(B.queue, 1ull);
+        __syncthreads();
+        const unsigned long long item = *S.item;
+        if (item >= n_items) break;
+        int inst = 0, hi = B.n_media - 1;   // last medium whose first item <= item
+        while (inst < hi) {
+            const int mid = (inst + hi + 1) >> 1;
+            if (B.item_begin[mid] <= item) inst = mid; else hi = mid - 1;
+        }
+        if (inst != cur) {
+            if (cur >= 0) {
+                flush<SMEM_IMAGE>(B.c, B.m[cur], S, T);
+                zero_tallies(S, B.c);
+            }
+            if (PHASE == MC_PHASE_TABLE) {
+                if (!stage_bulk(S.table, B.m[inst].table, B.c.table_bytes, S.bar, parity, B.c.error))
+                    return;
+                parity ^= 1u;
+                if (!bind_table(S, B.c)) return;
+            }
+            cur = inst;
+        }
+        const MediumArgs &M = B.m[inst];
+        const unsigned long long start = (item - B.item_begin[inst]) * B.item_photons;
+        const unsigned long long end = min(start + B.item_photons, M.n_photons);
+        if (threadIdx.x == 0) *S.pool = start;
+        __syncthreads();
+        unsigned long long *pool = S.pool;
+        walk_loop<PHASE, SMEM_IMAGE, false>(
+            B.c, M, S, end, BATCH_CHUNK,
+            [pool]() { return atomicAdd(pool, (unsigned long long)BATCH_CHUNK); }, T);
+        __syncthreads();
     }
-    for (int i = threadIdx.x; i < A.n_radial; i += blockDim.x)
-        if (s_rad[i]) atomicAdd(&A.radial[i], s_rad[i]);
-    for (int i = threadIdx.x; i < MC_N_TOTALS; i += blockDim.x)
-        if (s_tot[i]) atomicAdd(&A.totals[i], s_tot[i]);
+    if (cur >= 0) flush<SMEM_IMAGE>(B.c, B.m[cur], S, T);
 }
 
 __global__ void philox_kernel(const uint4 *ctr, uint64_t n, uint32_t k0, uint32_t k1, uint4 *out)
@@ -416,10 +537,13 @@ __global__ void philox_kernel(const uint4 *ctr, uint64_t n, uint32_t k0, uint32_
         out[i] = philox10(ctr[i], k0, k1);
 }
 
-template <int PHASE, bool SMEM_IMAGE, bool TRACE>
-cudaError_t launch_one(const WalkArgs &a, const LaunchCfg &cfg, size_t smem, cudaStream_t st)
+// Persistent grid: SMs x CTAs per SM (occupancy, or the caller's choice),
+// capped at what `work_warps` warps of work can use.
+template <class Kern>
+cudaError_t launch_persistent(Kern kern, const void *args_unused, const LaunchCfg &cfg, size_t smem,
+                              unsigned long long work_warps, unsigned *grid)
 {
-    auto kern = walk_kernel<PHASE, SMEM_IMAGE, TRACE>;
+    (void)args_unused;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, bps = cfg.blocks_per_sm;
@@ -431,25 +555,19 @@ cudaError_t launch_one(const WalkArgs &a, const LaunchCfg &cfg, size_t smem, cud
         if (bps < 1) return cudaErrorInvalidConfiguration;
     }
     unsigned long long blocks = (unsigned long long)sms * bps;
-    // no more warps than photons need (small runs)
-    unsigned long long warps_needed = (a.n_photons + CHUNK - 1) / CHUNK;
-    unsigned long long per_block = cfg.block / 32;
-    unsigned long long cap = (warps_needed + per_block - 1) / per_block;
+    const unsigned long long per_block = cfg.block / 32;
+    const unsigned long long cap = (work_warps + per_block - 1) / per_block;
     if (cap < blocks) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, cfg.block, smem, st>>>(a);
-    return cudaGetLastError();
+    *grid = (unsigned)(blocks < 1 ? 1 : blocks);
+    return cudaSuccess;
 }
 
-}  // namespace
-
-cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, cudaStream_t st)
+// Where the image accumulates and how big the CTA is. Sets c.band0/band_rows.
+cudaError_t plan_image(CommonArgs &c, LaunchCfg &cfg, bool *smem_img, size_t *smem)
 {
-    WalkArgs a = a0;
-    LaunchCfg cfg = cfg0;
-    const size_t tb = (a.phase_kind == MC_PHASE_TABLE) ? a.table_bytes : 0;
-    const size_t tail = sizeof(unsigned long long) * (a.n_radial + MC_N_TOTALS + 1);
-    const size_t row = sizeof(unsigned long long) * (size_t)a.nx;
+    const size_t tb = (c.phase_kind == MC_PHASE_TABLE) ? c.table_bytes : 0;
+    const size_t tail = sizeof(unsigned long long) * (c.n_radial + MC_N_TOTALS + 3);
+    const size_t row = sizeof(unsigned long long) * (size_t)c.nx;
     int dev = 0, optin = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -462,28 +580,64 @@ cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, c
     // beam as fit, the rest going to L2 atomics
     int mode = cfg.image_mode;
     if (mode == 0) {
-        if (tb + row * a.nz + tail <= (size_t)optin / 2 - 1024) mode = 1;
+        if (tb + row * c.nz + tail <= (size_t)optin / 2 - 1024) mode = 1;
         else mode = fit_rows >= 1 ? 3 : 2;
     }
-    bool smem_img = false;
-    a.band0 = 0;
-    a.band_rows = 0;
+    *smem_img = false;
+    c.band0 = 0;
+    c.band_rows = 0;
     if (mode == 1) {
-        if (fit_rows < a.nz) return cudaErrorInvalidValue;
-        smem_img = true;
-        a.band_rows = a.nz;
+        if (fit_rows < c.nz) return cudaErrorInvalidValue;
+        *smem_img = true;
+        c.band_rows = c.nz;
     } else if (mode == 3) {
         if (fit_rows < 1) return cudaErrorInvalidValue;
-        smem_img = true;
-        a.band_rows = fit_rows < a.nz ? fit_rows : a.nz;
-        int b0 = a.nz / 2 - a.band_rows / 2;
-        if (b0 > a.nz - a.band_rows) b0 = a.nz - a.band_rows;
-        a.band0 = b0 < 0 ? 0 : b0;
+        *smem_img = true;
+        c.band_rows = fit_rows < c.nz ? fit_rows : c.nz;
+        int b0 = c.nz / 2 - c.band_rows / 2;
+        if (b0 > c.nz - c.band_rows) b0 = c.nz - c.band_rows;
+        c.band0 = b0 < 0 ? 0 : b0;
     }
     if (cfg.block == 0) cfg.block = (mode == 3) ? 1024 : 256;
-    const size_t smem = tb + tail + (smem_img ? row * a.band_rows : 0);
-    if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    const bool table = a.phase_kind == MC_PHASE_TABLE;
+    *smem = tb + tail + (*smem_img ? row * c.band_rows : 0);
+    if (*smem > (size_t)optin) return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+template <int PHASE, bool SMEM_IMAGE, bool TRACE>
+cudaError_t launch_one(const WalkArgs &a, const LaunchCfg &cfg, size_t smem, cudaStream_t st)
+{
+    auto kern = walk_kernel<PHASE, SMEM_IMAGE, TRACE>;
+    unsigned grid = 0;
+    cudaError_t e = launch_persistent(kern, &a, cfg, smem, (a.m.n_photons + CHUNK - 1) / CHUNK, &grid);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, cfg.block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int PHASE, bool SMEM_IMAGE>
+cudaError_t launch_batch_one(const BatchArgs &a, const LaunchCfg &cfg, size_t smem, cudaStream_t st)
+{
+    auto kern = batch_kernel<PHASE, SMEM_IMAGE>;
+    unsigned grid = 0;
+    const unsigned long long items = a.item_begin[a.n_media];
+    cudaError_t e = launch_persistent(kern, &a, cfg, smem, items * (cfg.block / 32), &grid);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, cfg.block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, cudaStream_t st)
+{
+    WalkArgs a = a0;
+    LaunchCfg cfg = cfg0;
+    bool smem_img = false;
+    size_t smem = 0;
+    cudaError_t e = plan_image(a.c, cfg, &smem_img, &smem);
+    if (e != cudaSuccess) return e;
+    const bool table = a.c.phase_kind == MC_PHASE_TABLE;
     if (trace) {
         if (table) return smem_img ? launch_one<0, true, true>(a, cfg, smem, st)
                                    : launch_one<0, false, true>(a, cfg, smem, st);
@@ -494,6 +648,19 @@ cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, c
                                : launch_one<0, false, false>(a, cfg, smem, st);
     return smem_img ? launch_one<1, true, false>(a, cfg, smem, st)
                     : launch_one<1, false, false>(a, cfg, smem, st);
+}
+
+cudaError_t launch_batch(const BatchArgs &a0, const LaunchCfg &cfg0, cudaStream_t st)
+{
+    BatchArgs a = a0;
+    LaunchCfg cfg = cfg0;
+    bool smem_img = false;
+    size_t smem = 0;
+    cudaError_t e = plan_image(a.c, cfg, &smem_img, &smem);
+    if (e != cudaSuccess) return e;
+    if (a.c.phase_kind == MC_PHASE_TABLE)
+        return smem_img ? launch_batch_one<0, true>(a, cfg, smem, st) : launch_batch_one<0, false>(a, cfg, smem, st);
+    return smem_img ? launch_batch_one<1, true>(a, cfg, smem, st) : launch_batch_one<1, false>(a, cfg, smem, st);
 }
 
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out, cudaStream_t st)

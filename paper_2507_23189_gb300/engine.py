@@ -210,6 +210,58 @@ class Engine:
                     error=int(self.error.cpu().numpy()[0]))
 
 
+class Batch:
+    """Device tallies for several media sharing camera and geometry, run in
+    one persistent launch (mc_run_batch)."""
+
+    def __init__(self, n, camera=None, geometry=None, device=None):
+        torch = _torch()
+        self.camera = camera or Camera()
+        self.geometry = geometry or Geometry()
+        self.device = torch.device(device if device is not None else "cuda")
+        cam, dev = self.camera, self.device
+        self.n = n
+        self.image = torch.zeros((n, cam.nz, cam.nx), dtype=torch.int64, device=dev)
+        self.radial = torch.zeros((n, cam.n_radial), dtype=torch.int64, device=dev)
+        self.totals = torch.zeros((n, N.N_TOTALS), dtype=torch.int64, device=dev)
+        self.error = torch.zeros(1, dtype=torch.int32, device=dev)
+        wb = N.lib().mc_batch_workspace_bytes(n)
+        if wb == 0:
+            raise N.McError("mc_batch_workspace_bytes", -1)
+        self.work = torch.zeros(wb, dtype=torch.uint8, device=dev)
+        self.image_frac_bits = 32
+
+    def run(self, media, n_photons, seeds=1, offsets=0, item_photons=0, stream=None, **kw):
+        """media: list of Medium; n_photons, seeds, offsets: scalars or lists."""
+        n = len(media)
+        if n != self.n:
+            raise ValueError("batch holds %d media, got %d" % (self.n, n))
+        as_list = lambda v: list(v) if isinstance(v, (list, tuple)) else [v] * n
+        nph, sd, off = as_list(n_photons), as_list(seeds), as_list(offsets)
+        rp = run_params(0, 0, **kw)
+        self.image_frac_bits = rp.image_frac_bits
+        arr = (N.Instance * n)()
+        keep = []
+        for i, med in enumerate(media):
+            m, k = med.as_c(self.device)
+            keep.append(k)
+            arr[i].medium = m
+            arr[i].n_photons, arr[i].photon_offset, arr[i].seed = int(nph[i]), int(off[i]), int(sd[i])
+            arr[i].d_image = self.image[i].data_ptr()
+            arr[i].d_radial = self.radial[i].data_ptr()
+            arr[i].d_totals = self.totals[i].data_ptr()
+        g, c = self.geometry.as_c(), self.camera.as_c()
+        N.check("mc_run_batch", N.lib().mc_run_batch(
+            n, arr, C.byref(g), C.byref(c), C.byref(rp), int(item_photons),
+            C.c_void_p(self.error.data_ptr()), C.c_void_p(self.work.data_ptr()), self.work.numel(),
+            _stream_handle(stream)))
+        self._keep = keep
+        return self
+
+    def check(self, stream=None):
+        N.check("mc_check", N.lib().mc_check(C.c_void_p(self.error.data_ptr()), _stream_handle(stream)))
+
+
 def decode_trace(buf):
     """int32 [.., 12] trace -> dict of numpy arrays."""
     a = buf.cpu().numpy() if hasattr(buf, "cpu") else np.asarray(buf)

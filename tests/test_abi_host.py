@@ -93,12 +93,20 @@ def test_packed_table_layout(eng):
     guide = np.frombuffer(b[off_guide:off_guide + 2 * (n + 1)].tobytes(), dtype=np.uint16)
     np.testing.assert_array_equal(omu, t.omu64.astype(np.float32))
     np.testing.assert_array_equal(pdf, t.pdf64.astype(np.float32))
-    # guide[c] is the bin that holds cos = -1 + 2c/n
-    icdf = 1.0 - t.omu64
-    for c in range(0, n + 1, 7):
-        mu = -1.0 + 2.0 * c / n
-        j = int(guide[c])
-        assert icdf[j] <= mu and (j == n - 1 or mu < icdf[j + 1])
+    # guide brackets the kernel's single-precision lookup: for a direction
+    # cosine m in cell c = floor(fl(m + 1) n/2), the largest j with
+    # omu[j] >= fl(1 - m) lies in [guide[c], guide[c + 1]]
+    rng = np.random.default_rng(3)
+    m = np.concatenate([rng.uniform(-1, 1, 20000), 1 - rng.uniform(0, 1e-3, 5000),
+                        np.linspace(-1, 1, 8193)]).astype(np.float32)
+    m = np.clip(m, np.float32(-1), np.float32(1))
+    cell = np.minimum(np.floor((m + np.float32(1)) * np.float32(n / 2)).astype(np.int64), n - 1)
+    om = np.float32(1) - m
+    j = np.searchsorted(-omu, -om, side="right") - 1
+    j = np.clip(j, 0, n - 1)
+    assert np.all(guide[cell] <= j) and np.all(j <= guide[cell + 1])
+    # and brackets are tight: most cells hold a single candidate bin
+    assert np.mean(guide[1:] == guide[:-1]) > 0.5
 
 
 def test_medium_from_density_eq17(eng):
