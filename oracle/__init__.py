@@ -40,6 +40,10 @@ def lib():
         L.oracle_phase_table.restype = C.c_int
         L.oracle_phase_table.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
                                          C.c_double, C.c_int, C.c_int, dp, dp, dp, dp]
+        L.oracle_phase_table_weighted.restype = C.c_int
+        L.oracle_phase_table_weighted.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
+                                                  C.c_double, C.c_int, dp, C.c_int, C.c_int, dp, dp,
+                                                  dp, dp]
         L.oracle_philox4x32_10_n.restype = None
         L.oracle_philox4x32_10_n.argtypes = [C.POINTER(C.c_uint32), C.c_uint64,
                                              C.c_uint64, C.POINTER(C.c_uint32)]
@@ -48,6 +52,12 @@ def lib():
         L.oracle_walk.restype = C.c_int
         L.oracle_walk.argtypes = [C.POINTER(WalkCfg), C.POINTER(WalkOut),
                                   C.POINTER(TraceRec), C.c_int, C.c_int]
+        L.oracle_hat.restype = C.c_double
+        L.oracle_hat.argtypes = [C.c_int, C.c_int, C.c_double]
+        L.oracle_hat_integrals.restype = None
+        L.oracle_hat_integrals.argtypes = [dp, C.c_int, C.c_int, dp]
+        L.oracle_adjoint.restype = C.c_int
+        L.oracle_adjoint.argtypes = [C.POINTER(WalkCfg), dp, C.c_int, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -172,6 +182,18 @@ def phase_table(kind, m=1.0 + 0j, x=1.0, hg_g=0.0, n_bins=4096, n_fine=1 << 18):
                 mean=diag[2], n_fine=int(diag[3]))
 
 
+def phase_table_weighted(m, x, w, n_bins=4096, n_fine=1 << 18):
+    """Mie table of p(mu) h_w(mu) / Z(w) with hat weights w (len n_w)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    icdf, omu, pdf, diag = np.zeros(n_bins + 1), np.zeros(n_bins + 1), np.zeros(n_bins), np.zeros(4)
+    rc = lib().oracle_phase_table_weighted(PHASE_MIE, m.real, m.imag, x, 0.0, w.size, _dp(w), n_bins,
+                                           n_fine, _dp(icdf), _dp(omu), _dp(pdf), _dp(diag))
+    if rc:
+        raise ValueError("oracle_phase_table_weighted: bad arguments")
+    return dict(icdf=icdf, omu=omu, pdf=pdf, norm=diag[0], g_quad=diag[1], mean=diag[2],
+                n_fine=int(diag[3]))
+
+
 # ------------------------------------------------------------------ philox
 
 
@@ -189,6 +211,66 @@ def uniform(r):
 
 
 # ------------------------------------------------------------------ walk
+
+
+def hat_integrals(table, n_w=64):
+    """Z_k = int p(mu) phi_k(mu) dmu for the tabulated density."""
+    omu = np.ascontiguousarray(table["omu"], dtype=np.float64)
+    z = np.zeros(n_w)
+    lib().oracle_hat_integrals(_dp(omu), omu.size - 1, n_w, _dp(z))
+    return z
+
+
+def hat(n_w, k, mu):
+    return lib().oracle_hat(n_w, k, mu)
+
+
+def adjoint(adj, n_w=64, **walk_kw):
+    """Gradient of sum(adj * image) w.r.t. (mu_s, mu_a, w_0..w_{n_w-1}) at
+    w = 1: dict(grad, grad_sq (per-photon squares), value). Same keywords as
+    walk()."""
+    cfg, keep = _walk_cfg(**walk_kw)
+    a = np.ascontiguousarray(adj, dtype=np.float64).ravel()
+    if a.size != cfg.nx * cfg.nz:
+        raise ValueError("adjoint image has the wrong size")
+    g = np.zeros(2 + n_w)
+    g2 = np.zeros(2 + n_w)
+    v = C.c_double(0.0)
+    if lib().oracle_adjoint(C.byref(cfg), _dp(a), n_w, _dp(g), _dp(g2), C.byref(v)):
+        raise ValueError("oracle_adjoint: bad arguments")
+    return dict(grad=g, grad_sq=g2, value=v.value, n_photons=cfg.n_photons)
+
+
+def _walk_cfg(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,
+              lx=45.0, ly=10.0, lz=10.0, beam_radius=0.0,
+              nx=64, nz=64, n_radial=128, r_max=5.0 * 2 ** 0.5,
+              n_photons=1000, photon_offset=0, seed=1,
+              rr_threshold=1e-4, rr_survival=0.1, max_events=1_000_000, max_scatter=0,
+              cone_cos=0.0, n_threads=None):
+    cfg = WalkCfg()
+    cfg.mu_s, cfg.mu_a = mu_s, mu_a
+    keep = []
+    if phase == "mie":
+        icdf = np.ascontiguousarray(table["icdf"], dtype=np.float64)
+        omu = np.ascontiguousarray(table["omu"], dtype=np.float64)
+        keep += [icdf, omu]
+        cfg.phase_kind = PHASE_MIE
+        cfg.icdf, cfg.omu = _dp(icdf), _dp(omu)
+        cfg.n_bins = icdf.size - 1
+    elif phase == "hg":
+        cfg.phase_kind = PHASE_HG
+        cfg.hg_g = hg_g
+    else:
+        raise ValueError(phase)
+    cfg.lx, cfg.ly, cfg.lz, cfg.beam_radius = lx, ly, lz, beam_radius
+    cfg.nx, cfg.nz, cfg.n_radial, cfg.r_max = nx, nz, n_radial, r_max
+    cfg.n_photons, cfg.photon_offset, cfg.seed = n_photons, photon_offset, seed
+    cfg.rr_threshold, cfg.rr_survival = rr_threshold, rr_survival
+    cfg.max_events, cfg.max_scatter = max_events, max_scatter
+    cfg.cone_cos = cone_cos
+    cfg.n_threads = n_threads if n_threads else (os.cpu_count() or 1)
+    cfg._keep = keep
+    return cfg, keep
 
 
 def walk(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,

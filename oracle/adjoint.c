@@ -1,0 +1,291 @@
+/*
+ * Oracle: gradients of a linear functional of the camera image by
+ * likelihood ratios along replayed paths (test infrastructure only; see
+ * oracle.h).
+ *
+ * The camera image of Sec. 3.1.3 / Sec. 4.3 is a sum over photons of
+ * next-event contributions c_j = W_j p_sr(mu_c,j) exp(-mu_ext l_j) at each
+ * collision j, W_j = a^j (a = mu_s/mu_ext, Eq. 16) times any roulette boosts.
+ * The path density is a product of flight densities mu_ext exp(-mu_ext s_i)
+ * (Eq. 15) and polar-angle densities p(mu_i). For a parameter theta,
+ *   dE[c_j]/dtheta = E[ c_j ( d log c_j/dtheta + sum over the flights and
+ *                               scatterings before j of d log density/dtheta ) ]
+ * with
+ *   flight i:  d/dmu_s = d/dmu_a = 1/mu_ext - s_i
+ *   W_j:       d/dmu_s = j (1/mu_s - 1/mu_ext),  d/dmu_a = -j/mu_ext
+ *   transport: d/dmu_s = d/dmu_a = -l_j
+ *   phase weights at w = 1: d log p_w(mu)/dw_k = phi_k(mu) - Z_k, both for the
+ *   sampled angles mu_i (i < j) and for the camera density at mu_c,j.
+ * Flights that leave the cuvette carry no camera term and later terms of
+ * the same photon do not depend on them. Each photon's path is simply
+ * stored and summed afterwards.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+double oracle_hat(int n_w, int k, double mu)
+{
+    double h = 2.0 / (n_w - 1);
+    double t = fabs(mu - (-1.0 + k * h)) / h;
+    return t < 1.0 ? 1.0 - t : 0.0;
+}
+
+/* integral of phi_k over [a, b] (a < b), exactly: phi_k is piecewise linear
+ * with breakpoints at the nodes, so integrate piece by piece. */
+static double hat_integral(int n_w, int k, double a, double b)
+{
+    double h = 2.0 / (n_w - 1);
+    double c = -1.0 + k * h;
+    double pts[4] = {c - h, c, c + h};
+    double s = 0.0, lo = a;
+    for (int i = 0; i < 3 && lo < b; ++i) {
+        double hi = fmin(b, pts[i]);
+        if (hi > lo) {
+            s += 0.5 * (oracle_hat(n_w, k, lo) + oracle_hat(n_w, k, hi)) * (hi - lo);
+            lo = hi;
+        }
+    }
+    if (b > lo)
+        s += 0.5 * (oracle_hat(n_w, k, lo) + oracle_hat(n_w, k, b)) * (b - lo);
+    return s;
+}
+
+void oracle_hat_integrals(const double *omu, int n_bins, int n_w, double *z)
+{
+    for (int k = 0; k < n_w; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < n_bins; ++j) {
+            double a = 1.0 - omu[j], b = 1.0 - omu[j + 1];
+            double pdf = (1.0 / n_bins) / (omu[j] - omu[j + 1]);
+            s += pdf * hat_integral(n_w, k, a, b);
+        }
+        z[k] = s;
+    }
+}
+
+/* One photon's record. */
+typedef struct {
+    int n;          /* collisions */
+    int cap;
+    double *A;      /* adj[pix_j] * c_j */
+    double *S;      /* prefix of flight scores up to flight j */
+    double *l;      /* distance to the camera face */
+    double *muc;    /* camera cosine d_y at collision j */
+    double *mus;    /* polar cosine sampled at collision j (NAN: none) */
+} rec_t;
+
+static void rec_push(rec_t *R, double A, double S, double l, double muc)
+{
+    if (R->n == R->cap) {
+        int nc = R->cap ? 2 * R->cap : 64;
+        R->A = realloc(R->A, nc * sizeof(double));
+        R->S = realloc(R->S, nc * sizeof(double));
+        R->l = realloc(R->l, nc * sizeof(double));
+        R->muc = realloc(R->muc, nc * sizeof(double));
+        R->mus = realloc(R->mus, nc * sizeof(double));
+        R->cap = nc;
+    }
+    R->A[R->n] = A;
+    R->S[R->n] = S;
+    R->l[R->n] = l;
+    R->muc[R->n] = muc;
+    R->mus[R->n] = NAN;
+    R->n++;
+}
+
+static double hg_per_sr(double g, double mu)
+{
+    double t = 1.0 + g * g - 2.0 * g * mu;
+    return (1.0 - g * g) / (4.0 * M_PI * t * sqrt(t));
+}
+
+static double hg_sample(double g, double xi)
+{
+    if (fabs(g) < 1e-6)
+        return 2.0 * xi - 1.0;
+    double q = (1.0 - g * g) / (1.0 - g + 2.0 * g * xi);
+    return (1.0 + g * g - q * q) / (2.0 * g);
+}
+
+static int table_bin(const double *icdf, int n, double mu)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (icdf[mid] <= mu) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/* Walk photon p exactly as oracle_walk does, recording the collisions. */
+static void replay(const oracle_walk_cfg *c, uint64_t p, const double *adj, rec_t *R)
+{
+    const uint32_t key[2] = {(uint32_t)c->seed, (uint32_t)(c->seed >> 32)};
+    const double mu_ext = c->mu_s + c->mu_a;
+    const double lo[3] = {0.0, -0.5 * c->ly, -0.5 * c->lz};
+    const double hi[3] = {c->lx, 0.5 * c->ly, 0.5 * c->lz};
+    double r[3] = {0.0, 0.0, 0.0}, d[3] = {1.0, 0.0, 0.0}, w = 1.0, S = 0.0;
+    uint32_t n_coll = 0;
+    R->n = 0;
+    if (c->beam_radius > 0.0) {
+        uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0xFFFFFFFFu, 0u}, o[4];
+        oracle_philox4x32_10(ctr, key, o);
+        double rho = c->beam_radius * sqrt(oracle_uniform(o[0]));
+        double psi = 2.0 * M_PI * oracle_uniform(o[1]);
+        r[1] = rho * cos(psi);
+        r[2] = rho * sin(psi);
+    }
+    for (uint32_t e = 0; e < c->max_events; ++e) {
+        uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), e, 0u}, o[4];
+        oracle_philox4x32_10(ctr, key, o);
+        double u0 = oracle_uniform(o[0]), u1 = oracle_uniform(o[1]);
+        double u2 = oracle_uniform(o[2]), u3 = oracle_uniform(o[3]);
+        double s = -log(u0) / mu_ext;
+        double sw = INFINITY;
+        for (int i = 0; i < 3; ++i) {
+            double t;
+            if (d[i] > 0.0) t = (hi[i] - r[i]) / d[i];
+            else if (d[i] < 0.0) t = (lo[i] - r[i]) / d[i];
+            else continue;
+            if (t < sw) sw = t;
+        }
+        if (s >= sw)
+            return;
+        for (int i = 0; i < 3; ++i) r[i] += s * d[i];
+        n_coll++;
+        S += 1.0 / mu_ext - s;
+        w = w * (1.0 - c->mu_a / mu_ext);
+        double muc = d[1], psr;
+        if (c->phase_kind == ORACLE_PHASE_HG) {
+            psr = hg_per_sr(c->hg_g, muc);
+        } else {
+            int nb = table_bin(c->icdf, c->n_bins, muc);
+            psr = (1.0 / c->n_bins) / (c->omu[nb] - c->omu[nb + 1]) / (2.0 * M_PI);
+        }
+        double l = hi[1] - r[1];
+        double nee = w * psr * exp(-mu_ext * l);
+        double fx = r[0] / c->lx * c->nx, fz = (r[2] - lo[2]) / c->lz * c->nz;
+        int ix = (int)floor(fx), iz = (int)floor(fz);
+        if (ix < 0) ix = 0;
+        if (ix > c->nx - 1) ix = c->nx - 1;
+        if (iz < 0) iz = 0;
+        if (iz > c->nz - 1) iz = c->nz - 1;
+        rec_push(R, adj[iz * c->nx + ix] * nee, S, l, muc);
+        if (c->max_scatter && n_coll >= c->max_scatter)
+            return;
+        double mu, omu;
+        if (c->phase_kind == ORACLE_PHASE_HG) {
+            mu = hg_sample(c->hg_g, u1);
+            omu = 1.0 - mu;
+        } else {
+            double t = u1 * c->n_bins;
+            int i = (int)floor(t);
+            omu = c->omu[i] + (t - i) * (c->omu[i + 1] - c->omu[i]);
+            mu = 1.0 - omu;
+        }
+        R->mus[R->n - 1] = mu;
+        double st = sqrt(fmax(0.0, omu * (2.0 - omu)));
+        double phi = 2.0 * M_PI * u2, cp = cos(phi), sp = sin(phi);
+        double sg = copysign(1.0, d[2]), a = -1.0 / (sg + d[2]), b = d[0] * d[1] * a;
+        double e1[3] = {1.0 + sg * d[0] * d[0] * a, sg * b, -sg * d[0]};
+        double e2[3] = {b, sg + d[1] * d[1] * a, -d[1]};
+        double nd[3];
+        for (int i = 0; i < 3; ++i) nd[i] = mu * d[i] + st * (cp * e1[i] + sp * e2[i]);
+        double nrm = sqrt(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]);
+        for (int i = 0; i < 3; ++i) d[i] = nd[i] / nrm;
+        if (w < c->rr_threshold) {
+            if (u3 < c->rr_survival) w = w / c->rr_survival;
+            else return;
+        }
+    }
+}
+
+typedef struct {
+    const oracle_walk_cfg *c;
+    const double *adj, *z;
+    int n_w;
+    uint64_t first, count;
+    double *g, *g2;   /* [2 + n_w] */
+    double value;
+} ajob_t;
+
+static void *adj_worker(void *arg)
+{
+    ajob_t *J = arg;
+    const oracle_walk_cfg *c = J->c;
+    const double mu_ext = c->mu_s + c->mu_a;
+    const int m = 2 + J->n_w;
+    double *pg = calloc((size_t)m, sizeof(double));
+    rec_t R = {0};
+    for (uint64_t k = 0; k < J->count; ++k) {
+        replay(c, c->photon_offset + J->first + k, J->adj, &R);
+        memset(pg, 0, (size_t)m * sizeof(double));
+        for (int j = 0; j < R.n; ++j) {
+            double jj = j + 1.0, A = R.A[j];
+            J->value += A;
+            pg[0] += A * (R.S[j] + jj * (1.0 / c->mu_s - 1.0 / mu_ext) - R.l[j]);
+            pg[1] += A * (R.S[j] - jj / mu_ext - R.l[j]);
+            for (int q = 0; q < J->n_w; ++q) {
+                double t = oracle_hat(J->n_w, q, R.muc[j]) - jj * J->z[q];
+                for (int i = 0; i < j; ++i)
+                    t += oracle_hat(J->n_w, q, R.mus[i]);
+                pg[2 + q] += A * t;
+            }
+        }
+        for (int q = 0; q < m; ++q) {
+            J->g[q] += pg[q];
+            J->g2[q] += pg[q] * pg[q];
+        }
+    }
+    free(pg);
+    free(R.A); free(R.S); free(R.l); free(R.muc); free(R.mus);
+    return NULL;
+}
+
+int oracle_adjoint(const oracle_walk_cfg *c, const double *adj, int n_w, double *grad, double *grad_sq,
+                   double *value)
+{
+    if (!c || !adj || !grad || !grad_sq || !value || n_w < 0 || n_w == 1 || !(c->mu_s > 0) || c->mu_a < 0)
+        return -1;
+    if (n_w > 0 && c->phase_kind != ORACLE_PHASE_MIE)
+        return -1;
+    if (c->phase_kind == ORACLE_PHASE_MIE && (!c->icdf || !c->omu))
+        return -1;
+    double *z = calloc((size_t)(n_w > 0 ? n_w : 1), sizeof(double));
+    if (n_w > 0)
+        oracle_hat_integrals(c->omu, c->n_bins, n_w, z);
+    int T = c->n_threads > 0 ? c->n_threads : 1;
+    if ((uint64_t)T > c->n_photons && c->n_photons > 0) T = (int)c->n_photons;
+    if (T < 1) T = 1;
+    ajob_t *jobs = calloc((size_t)T, sizeof *jobs);
+    pthread_t *th = calloc((size_t)T, sizeof *th);
+    for (int t = 0; t < T; ++t) {
+        jobs[t].c = c;
+        jobs[t].adj = adj;
+        jobs[t].z = z;
+        jobs[t].n_w = n_w;
+        jobs[t].first = c->n_photons * (uint64_t)t / (uint64_t)T;
+        jobs[t].count = c->n_photons * (uint64_t)(t + 1) / (uint64_t)T - jobs[t].first;
+        jobs[t].g = calloc((size_t)(2 + n_w), sizeof(double));
+        jobs[t].g2 = calloc((size_t)(2 + n_w), sizeof(double));
+        pthread_create(&th[t], NULL, adj_worker, &jobs[t]);
+    }
+    for (int t = 0; t < T; ++t) {
+        pthread_join(th[t], NULL);
+        for (int q = 0; q < 2 + n_w; ++q) {
+            grad[q] += jobs[t].g[q];
+            grad_sq[q] += jobs[t].g2[q];
+        }
+        *value += jobs[t].value;
+        free(jobs[t].g);
+        free(jobs[t].g2);
+    }
+    free(jobs);
+    free(th);
+    free(z);
+    return 0;
+}

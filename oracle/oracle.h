@@ -90,6 +90,13 @@ int oracle_phase_table(int kind, double m_re, double m_im, double x,
                        double hg_g, int n_bins, int n_fine, double *icdf,
                        double *omu, double *pdf, double *diag);
 
+/* The same for the weighted phase function p(mu) h_w(mu) / Z(w),
+ * h_w = sum_k w_k phi_k (hat functions of oracle_hat), n_w >= 2. */
+int oracle_phase_table_weighted(int kind, double m_re, double m_im, double x,
+                                double hg_g, int n_w, const double *w, int n_bins,
+                                int n_fine, double *icdf, double *omu, double *pdf,
+                                double *diag);
+
 /* -------------------------------------------------------------- philox.c */
 
 /* Philox4x32 with 10 rounds: out = bijection(ctr) under key. */
@@ -175,6 +182,30 @@ typedef struct {
  * Returns 0, or -1 on bad arguments. */
 int oracle_walk(const oracle_walk_cfg *cfg, oracle_walk_out *out,
                 oracle_trace_rec *trace, int n_trace, int n_trace_events);
+
+/* ---------------------------------------------------------- adjoint.c */
+
+/* Hat functions for the phase-weight gradient: n_w nodes at
+ * mu_k = -1 + 2k/(n_w-1); phi_k is 1 at mu_k and falls linearly to 0 at the
+ * neighbouring nodes. */
+double oracle_hat(int n_w, int k, double mu);
+
+/* Z_k = int_{-1}^{1} p(mu) phi_k(mu) dmu for the tabulated density
+ * (piecewise constant on the table bins), exactly. */
+void oracle_hat_integrals(const double *omu, int n_bins, int n_w, double *z);
+
+/* Gradient of L = sum_pix adj[pix] * image[pix] with respect to
+ * (mu_s, mu_a, w_0..w_{n_w-1}) at w = 1, where the phase function is
+ * p_w(mu) = p(mu) h_w(mu) / Z(w), h_w = sum_k w_k phi_k. Score-function
+ * (likelihood-ratio) terms for every sampled flight and polar angle plus
+ * direct terms of each camera contribution; roulette factors are held
+ * fixed. Same photons, random numbers and tallies as oracle_walk.
+ * grad[2 + n_w], grad_sq[2 + n_w] (sums of per-photon squares) and
+ * *value (the functional itself, from the replayed paths) are accumulated
+ * (caller zeroes). n_w = 0 skips the phase weights; n_w > 0
+ * needs the table phase. Returns 0 or -1. */
+int oracle_adjoint(const oracle_walk_cfg *cfg, const double *adj, int n_w, double *grad,
+                   double *grad_sq, double *value);
 
 #ifdef __cplusplus
 }

@@ -39,9 +39,30 @@ static double panel_partial(double f0, double f1, double f2, double h, double s)
     return s * (f0 + s * (c1 + s * c2));
 }
 
+static int build_table(int kind, double m_re, double m_im, double x, double hg_g, int n_w,
+                       const double *wts, int n_bins, int n_fine, double *icdf, double *omu,
+                       double *pdf, double *diag);
+
 int oracle_phase_table(int kind, double m_re, double m_im, double x,
                        double hg_g, int n_bins, int n_fine, double *icdf,
                        double *omu, double *pdf, double *diag)
+{
+    return build_table(kind, m_re, m_im, x, hg_g, 0, NULL, n_bins, n_fine, icdf, omu, pdf, diag);
+}
+
+int oracle_phase_table_weighted(int kind, double m_re, double m_im, double x,
+                                double hg_g, int n_w, const double *w, int n_bins,
+                                int n_fine, double *icdf, double *omu, double *pdf,
+                                double *diag)
+{
+    if (n_w < 2 || !w)
+        return -1;
+    return build_table(kind, m_re, m_im, x, hg_g, n_w, w, n_bins, n_fine, icdf, omu, pdf, diag);
+}
+
+static int build_table(int kind, double m_re, double m_im, double x, double hg_g, int n_w,
+                       const double *wts, int n_bins, int n_fine, double *icdf, double *omu,
+                       double *pdf, double *diag)
 {
     if (n_bins < 2 || n_fine < 4 || (n_fine & 1))
         return -1;
@@ -69,9 +90,16 @@ int oracle_phase_table(int kind, double m_re, double m_im, double x,
         for (int j = 0; j <= n_fine; ++j)
             F[j] = hg_phase(hg_g, (double)(n_fine - j) * h);
     }
-    /* F <- (1/2) P sin(theta) */
-    for (int j = 0; j <= n_fine; ++j)
+    /* F <- (1/2) P sin(theta), times the hat weights h_w(cos theta) if any */
+    for (int j = 0; j <= n_fine; ++j) {
         F[j] *= 0.5 * sin((double)(n_fine - j) * h);
+        if (n_w) {
+            double hw = 0.0;
+            for (int k = 0; k < n_w; ++k)
+                hw += wts[k] * oracle_hat(n_w, k, mu[j]);
+            F[j] *= hw;
+        }
+    }
 
     /* Step 2/3: Simpson panels, cumulated from theta = pi. */
     cum[0] = 0.0;
