@@ -223,6 +223,43 @@ def batched_comparison(E, dev, steps, warmup, flush):
                         "64 sequential launches"}
 
 
+def adjoint_comparison(E, dev, steps, flush):
+    """Adjoint cost against the forward pass on the tau = 5 Mie cuvette with
+    1e7 photons and a 128x128 image: mc_run vs mc_adjoint over the same
+    photons, with and without the 64 phase-weight gradients."""
+    import torch
+    table = E.PhaseTable(5.0, 1.59, 1.33, 532.0, 4096)
+    med = E.Medium.from_optical_depth(table, TAU, LX)
+    eng = E.Engine(E.Camera(128, 128, N_RADIAL, R_MAX), E.Geometry(LX, LY, LZ, 0.0), dev)
+    n = 10_000_000
+    adj = torch.rand((128, 128), generator=torch.Generator().manual_seed(1)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        tot = 0.0
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / steps
+
+    t_fwd = timed(lambda: eng.run(med, n, seed=1, stream=stream))
+    t_w = timed(lambda: eng.adjoint(med, adj, n, n_w=64, seed=1, stream=stream))
+    t_0 = timed(lambda: eng.adjoint(med, adj, n, n_w=0, seed=1, stream=stream))
+    eng.check()
+    return {"forward_ms": t_fwd, "adjoint_ms": t_w, "adjoint_mu_only_ms": t_0,
+            "cost_vs_forward": t_w / t_fwd, "cost_vs_forward_mu_only": t_0 / t_fwd,
+            "workload": "tau=5 Mie, 1e7 photons, 128x128 image; gradient w.r.t. mu_s, mu_a and 64 "
+                        "phase-table weights (two replays per photon) or mu_s, mu_a only (one replay)"}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -365,6 +402,7 @@ def run_engine(args):
             "gpu_launches": args.steps, "clocks": clk, "roofline": roof}
     if not args.no_batched and ws == 1:
         line["batched"] = batched_comparison(E, dev, args.steps, args.warmup, flush)
+        line["adjoint"] = adjoint_comparison(E, dev, args.steps, flush)
     if not args.no_peaks:
         from paper_2507_23189_gb300 import peaks
         pk = peaks.measure(dev)

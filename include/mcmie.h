@@ -218,6 +218,27 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom,
                        uint64_t item_photons, uint32_t *d_error, void *d_work,
                        size_t work_bytes, void *stream);
 
+/* Gradient of L = sum_pix adj[pix] * image[pix] (adj: d_adj_image, float,
+ * [nz][nx], in the image's weight units) with respect to mu_s, mu_a and
+ * n_phase_w hat-function weights of the phase function, p_w(mu) =
+ * p(mu) h_w(mu) / Z(w), h_w = sum_k w_k phi_k, evaluated at w = 1; phi_k has
+ * nodes at mu_k = -1 + 2k/(n_phase_w - 1). Likelihood ratios of every
+ * sampled flight (Eq. 15) and polar angle plus the direct terms of each
+ * camera contribution (Eq. 16 weight, transport, phase density), on the
+ * photons mc_run would simulate with the same arguments, replayed from
+ * their Philox counters (nothing about the paths is stored). Roulette
+ * factors are held fixed. d_out[3 + n_phase_w] receives (L, dL/dmu_s,
+ * dL/dmu_a, dL/dw_0, ..) in double precision, reduced in a fixed order.
+ * n_phase_w: 0 (no phase weights, one replay per photon) or 2..256 (table
+ * phase only; two replays per photon). Requires mu_s > 0.
+ * d_work: mc_adjoint_workspace_bytes(n_phase_w) bytes. The paper has no
+ * gradients; this serves fitting mu_s, mu_a and the phase function. */
+size_t mc_adjoint_workspace_bytes(int n_phase_w);
+mc_status mc_adjoint(const mc_medium *medium, const mc_geometry *geom,
+                     const mc_camera *camera, const mc_run_params *run,
+                     const float *d_adj_image, int n_phase_w, double *d_out,
+                     uint32_t *d_error, void *d_work, size_t work_bytes, void *stream);
+
 /* Host-buffer form of mc_run, for callers whose inputs and outputs live in
  * host memory. The table blob (mc_table_bytes(n_bins) bytes, or NULL for
  * MC_PHASE_HG) is copied to the device, the walk runs, and image, radial

@@ -22,7 +22,8 @@ TRACE_WORDS = 12
 # every symbol include/mcmie.h declares
 EXPORTS = ("mc_table_bytes", "mie_table_build", "mc_medium_from_density", "mc_workspace_bytes",
            "mc_run", "mc_host_workspace_bytes", "mc_run_host", "mc_trace", "mc_check", "mc_philox",
-           "mc_status_string", "mc_run_static", "mc_batch_workspace_bytes", "mc_run_batch")
+           "mc_status_string", "mc_run_static", "mc_batch_workspace_bytes", "mc_run_batch",
+           "mc_adjoint_workspace_bytes", "mc_adjoint")
 
 
 class McError(RuntimeError):
@@ -123,6 +124,11 @@ def lib():
     L.mc_run_batch.restype = C.c_int
     L.mc_run_batch.argtypes = [C.c_int, P(Instance), P(Geometry), P(Camera), P(RunParams), C.c_uint64,
                                vp, vp, C.c_size_t, vp]
+    L.mc_adjoint_workspace_bytes.restype = C.c_size_t
+    L.mc_adjoint_workspace_bytes.argtypes = [C.c_int]
+    L.mc_adjoint.restype = C.c_int
+    L.mc_adjoint.argtypes = [P(Medium), P(Geometry), P(Camera), P(RunParams), vp, C.c_int, vp, vp, vp,
+                             C.c_size_t, vp]
     L.mc_status_string.restype = C.c_char_p
     L.mc_status_string.argtypes = [C.c_int]
     _lib = L

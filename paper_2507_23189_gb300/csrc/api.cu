@@ -367,6 +367,47 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom, 
     return cuda_status(e);
 }
 
+size_t mc_adjoint_workspace_bytes(int n_phase_w)
+{
+    if (n_phase_w < 0 || n_phase_w == 1 || n_phase_w > 256) return 0;
+    const int rows = mcx::adjoint_max_grid();
+    if (rows < 1) return 0;
+    return kAlign + up(sizeof(double) * 256) + up(sizeof(double) * (size_t)rows * (3 + n_phase_w));
+}
+
+mc_status mc_adjoint(const mc_medium *medium, const mc_geometry *geom, const mc_camera *camera,
+                     const mc_run_params *run, const float *d_adj_image, int n_phase_w, double *d_out,
+                     uint32_t *d_error, void *d_work, size_t work_bytes, void *stream)
+{
+    mc_status s;
+    if ((s = validate_all(medium, geom, camera, run)) != MC_OK) return s;
+    if (!d_adj_image || !d_out || !d_error || !d_work || !aligned(d_adj_image, 4) || !aligned(d_out, 8) ||
+        !aligned(d_work, 16) || !(medium->mu_s > 0.0) || n_phase_w < 0 || n_phase_w == 1 || n_phase_w > 256 ||
+        (n_phase_w > 0 && medium->phase_kind != MC_PHASE_TABLE))
+        return MC_ERR_ARG;
+    const size_t need = mc_adjoint_workspace_bytes(n_phase_w);
+    if (!need) return MC_ERR_CUDA;
+    if (work_bytes < need) return MC_ERR_NOMEM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(d_out, 0, sizeof(double) * (3 + n_phase_w), st))) return MC_ERR_CUDA;
+    if ((e = cudaMemsetAsync(d_work, 0, sizeof(unsigned long long), st))) return MC_ERR_CUDA;
+    if (run->n_photons == 0) return MC_OK;
+    mcx::AdjArgs a;
+    std::memset(&a, 0, sizeof a);
+    fill_common(a.c, medium, geom, camera, run, d_error);
+    fill_medium(a.m, medium, run->n_photons, run->photon_offset, run->seed, nullptr, nullptr, nullptr);
+    a.adj = d_adj_image;
+    a.n_w = n_phase_w;
+    a.c_s = (float)(1.0 / medium->mu_s - 1.0 / (medium->mu_s + medium->mu_a));
+    a.counter = static_cast<unsigned long long *>(d_work);
+    a.z = reinterpret_cast<double *>(static_cast<unsigned char *>(d_work) + kAlign);
+    a.partials = reinterpret_cast<double *>(static_cast<unsigned char *>(d_work) + kAlign +
+                                            up(sizeof(double) * 256));
+    e = mcx::launch_adjoint(a, mcx::adjoint_max_grid(), d_out, st);
+    return cuda_status(e);
+}
+
 mc_status mc_check(const uint32_t *d_error, void *stream)
 {
     if (!d_error) return MC_ERR_ARG;

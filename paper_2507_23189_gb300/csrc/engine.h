@@ -65,6 +65,19 @@ struct BatchArgs {
     MediumArgs m[kMaxBatch];
 };
 
+// Gradient of L = sum_pix adj[pix] image[pix] for one medium (see adjoint
+// kernel); partials holds one row of 3 + n_w doubles per CTA.
+struct AdjArgs {
+    CommonArgs c;
+    MediumArgs m;
+    const float *adj;           // [nz][nx]
+    int n_w;                    // phase-weight hats (0: none)
+    float c_s;                  // 1/mu_s - 1/mu_ext
+    double *z;                  // [n_w] hat integrals of the table (workspace)
+    double *partials;           // [grid][3 + n_w]
+    unsigned long long *counter;
+};
+
 struct LaunchCfg {
     int block = 0;          // 0: 256 (whole tile / global) or 1024 (band)
     int blocks_per_sm = 0;  // 0: occupancy maximum
@@ -79,6 +92,13 @@ cudaError_t launch_walk(const WalkArgs &a, bool trace, const LaunchCfg &cfg, cud
 
 // Launch the batched walk (phase fixed by c.phase_kind) on `stream`.
 cudaError_t launch_batch(const BatchArgs &a, const LaunchCfg &cfg, cudaStream_t stream);
+
+// Launch the adjoint replay and the reduction into out[3 + n_w]
+// (value, dL/dmu_s, dL/dmu_a, dL/dw_k). partial_rows: capacity of partials.
+cudaError_t launch_adjoint(const AdjArgs &a, int partial_rows, double *out, cudaStream_t stream);
+
+// CTAs the adjoint launch may use on the current device (for workspace sizing).
+int adjoint_max_grid();
 
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out,
                           cudaStream_t stream);

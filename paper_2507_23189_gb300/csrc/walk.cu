@@ -143,6 +143,67 @@ __device__ __forceinline__ void trace_write(const CommonArgs &C, unsigned long l
     t[9] = pix; t[10] = nb; t[11] = rb;
 }
 
+// ---------------------------------------------------------------- physics
+// Shared by the forward walk and the adjoint replay so both compute the very
+// same single-precision values.
+
+// Phase density per steradian for the camera direction cosine d_y.
+template <int PHASE>
+__device__ __forceinline__ float camera_psr(const MediumArgs &M, const CommonArgs &C, const float *omu,
+                                            const float *pdf, const uint16_t *guide, float dy, int &nb)
+{
+    if (PHASE == MC_PHASE_HG) {
+        const float t = fmaf(M.hg_two_g, 1.0f - dy, M.hg_a2);
+        nb = -1;
+        return M.hg_K / (t * sqrtf(t));
+    }
+    nb = table_bin(omu, guide, C.n_bins, dy);
+    return pdf[nb] * INV_2PI;
+}
+
+// Camera pixel of a collision at (rx, rz).
+__device__ __forceinline__ int camera_pixel(const CommonArgs &C, float rx, float rz, int &ix, int &iz)
+{
+    ix = min(max(__float2int_rd(rx * C.sx), 0), C.nx - 1);
+    iz = min(max(__float2int_rd((rz + C.hz) * C.sz), 0), C.nz - 1);
+    return iz * C.nx + ix;
+}
+
+// Polar angle as 1 - cos(theta) (accurate near the forward peak).
+template <int PHASE>
+__device__ __forceinline__ float sample_omu(const MediumArgs &M, const CommonArgs &C, const float *omu,
+                                            float u1)
+{
+    if (PHASE == MC_PHASE_HG) {
+        const float D = fmaf(M.hg_two_g, u1, M.hg_one_m_g);
+        return M.hg_A * (1.0f - u1) * fmaf(M.hg_g, u1, 1.0f) / (D * D);
+    }
+    const float tt = u1 * (float)C.n_bins;
+    const int i = (int)tt;
+    const float f = tt - (float)i;
+    const float o0 = omu[i], o1 = omu[i + 1];
+    return fmaf(f, o1 - o0, o0);
+}
+
+// d <- mu d + sin(theta) (cos phi e1 + sin phi e2), (e1, e2) the orthonormal
+// basis of Duff et al. (2017) around d, phi = 2 pi u2; renormalised.
+__device__ __forceinline__ void rotate(float &dx, float &dy, float &dz, float om, float u2)
+{
+    const float mu = 1.0f - om;
+    const float st = sqrtf(fmaxf(om * (2.0f - om), 0.0f));
+    float sp, cp;
+    sincospif(2.0f * u2, &sp, &cp);
+    const float sg = copysignf(1.0f, dz);
+    const float a = -__frcp_rn(sg + dz);
+    const float b = dx * dy * a;
+    const float e1x = fmaf(sg * dx * dx, a, 1.0f), e1y = sg * b, e1z = -sg * dx;
+    const float e2x = b, e2y = fmaf(dy * dy, a, sg), e2z = -dy;
+    const float qx = fmaf(cp, e1x, sp * e2x), qy = fmaf(cp, e1y, sp * e2y), qz = fmaf(cp, e1z, sp * e2z);
+    const float nx = fmaf(mu, dx, st * qx), ny = fmaf(mu, dy, st * qy), nz = fmaf(mu, dz, st * qz);
+    const float inv = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+    dx = nx * inv; dy = ny * inv; dz = nz * inv;
+}
+
 // Shared memory of a walk CTA:
 //   [table blob][image band][radial][totals][mbarrier][item][pool]
 struct Smem {
@@ -370,19 +431,10 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
         }
 
         // camera: next-event estimate toward +y
-        float psr;
-        int nb = -1;
-        if (PHASE == MC_PHASE_HG) {
-            const float t = fmaf(M.hg_two_g, 1.0f - dy, M.hg_a2);
-            psr = M.hg_K / (t * sqrtf(t));
-        } else {
-            nb = table_bin(omu, guide, C.n_bins, dy);
-            psr = pdf[nb] * INV_2PI;
-        }
+        int nb, ix, iz;
+        const float psr = camera_psr<PHASE>(M, C, omu, pdf, guide, dy, nb);
         const float nee = w * psr * expf(-M.mu_ext * (C.hy - ry));
-        const int ix = min(max(__float2int_rd(rx * C.sx), 0), C.nx - 1);
-        const int iz = min(max(__float2int_rd((rz + C.hz) * C.sz), 0), C.nz - 1);
-        const int pix = iz * C.nx + ix;
+        const int pix = camera_pixel(C, rx, rz, ix, iz);
         const float vf = nee * C.img_scale;
         if (vf < 4.0e18f) {
             const long long v = __float2ll_rn(vf);
@@ -399,33 +451,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
             status = 5;
             alive = false;
         } else {
-            // polar angle as 1 - cos(theta), accurate near the forward peak
-            float om;
-            if (PHASE == MC_PHASE_HG) {
-                const float D = fmaf(M.hg_two_g, u1, M.hg_one_m_g);
-                om = M.hg_A * (1.0f - u1) * fmaf(M.hg_g, u1, 1.0f) / (D * D);
-            } else {
-                const float tt = u1 * (float)C.n_bins;
-                const int i = (int)tt;
-                const float f = tt - (float)i;
-                const float o0 = omu[i], o1 = omu[i + 1];
-                om = fmaf(f, o1 - o0, o0);
-            }
-            const float mu = 1.0f - om;
-            const float st = sqrtf(fmaxf(om * (2.0f - om), 0.0f));
-            float sp, cp;
-            sincospif(2.0f * u2, &sp, &cp);
-            // orthonormal basis around d (Duff et al. 2017)
-            const float sg = copysignf(1.0f, dz);
-            const float a = -__frcp_rn(sg + dz);
-            const float b = dx * dy * a;
-            const float e1x = fmaf(sg * dx * dx, a, 1.0f), e1y = sg * b, e1z = -sg * dx;
-            const float e2x = b, e2y = fmaf(dy * dy, a, sg), e2z = -dy;
-            const float qx = fmaf(cp, e1x, sp * e2x), qy = fmaf(cp, e1y, sp * e2y),
-                        qz = fmaf(cp, e1z, sp * e2z);
-            const float nx = fmaf(mu, dx, st * qx), ny = fmaf(mu, dy, st * qy), nz = fmaf(mu, dz, st * qz);
-            const float inv = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
-            dx = nx * inv; dy = ny * inv; dz = nz * inv;
+            rotate(dx, dy, dz, sample_omu<PHASE>(M, C, omu, u1), u2);
             // weight threshold / roulette (Sec. 3.1.3)
             if (w < C.rr_thr) {
                 if (u3 < C.rr_surv) {
@@ -528,6 +554,305 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ Bat
         __syncthreads();
     }
     if (cur >= 0) flush<SMEM_IMAGE>(B.c, B.m[cur], S, T);
+}
+
+// ------------------------------------------------------------------ adjoint
+// Gradient of L = sum_pix adj[pix] image[pix] with respect to (mu_s, mu_a)
+// and the hat-function phase weights w_k at w = 1 (p_w = p h_w / Z(w)), by
+// likelihood ratios along replayed paths (the photons, random numbers and
+// single-precision arithmetic of the forward walk). For a camera term
+// A_j = adj[pix_j] c_j at collision j of a photon:
+//   dL/dmu_s += A_j (S_j + j (1/mu_s - 1/mu_ext) - l_j)
+//   dL/dmu_a += A_j (S_j - j/mu_ext - l_j)
+//   dL/dw_k  += A_j (phi_k(mu_c,j) - j Z_k + sum_{i<j} phi_k(mu_i)),
+// S_j = sum over the flights up to j of (1/mu_ext - s_i) (Eq. 15 score),
+// l_j the distance to the camera face, mu_i the sampled polar cosines,
+// Z_k = int p phi_k. The last sum is rearranged as
+// sum_i phi_k(mu_i) (P_tot - P_i) with P_i = A_1 + .. + A_i, which needs the
+// photon's total P_tot: photons are replayed a second time (same counters)
+// when phase-weight gradients are wanted. Roulette factors are held fixed.
+
+// Hat functions: nodes mu_k = -1 + k h, h = 2/(n_w - 1); the two nonzero
+// weights at mu.
+__device__ __forceinline__ int hat_pair(int nw, float mu, float &f)
+{
+    const float t = (mu + 1.0f) * (0.5f * (float)(nw - 1));
+    int k = __float2int_rd(t);
+    k = min(max(k, 0), nw - 2);
+    f = fminf(fmaxf(t - (float)k, 0.0f), 1.0f);
+    return k;
+}
+
+// Z_k = int_{-1}^{1} p(mu) phi_k(mu) dmu over the table (bins of constant
+// density), exactly, in double precision: CTA k sums the bins of hat k's
+// support, each thread a strided subset in order, then a fixed-order tree.
+__global__ void hat_integrals_kernel(const unsigned char *table, int nw, double *z)
+{
+    __shared__ double part[256];
+    const mc_table_header *hd = reinterpret_cast<const mc_table_header *>(table);
+    const float *omu = reinterpret_cast<const float *>(table + hd->off_omu);
+    const float *pdf = reinterpret_cast<const float *>(table + hd->off_pdf);
+    const uint16_t *guide = reinterpret_cast<const uint16_t *>(table + hd->off_guide);
+    const int n = hd->n_bins, k = blockIdx.x;
+    const double h = 2.0 / (nw - 1), inv_h = (nw - 1) / 2.0, c = -1.0 + k * h;
+    const double lo = fmax(c - h, -1.0), hi = fmin(c + h, 1.0);
+    const int j0 = max(table_bin(omu, guide, n, (float)lo) - 1, 0);
+    const int j1 = min(table_bin(omu, guide, n, (float)hi) + 1, n - 1);
+    double acc = 0.0;
+    for (int j = j0 + (int)threadIdx.x; j <= j1; j += blockDim.x) {
+        const double a = fmax(1.0 - (double)omu[j], lo), b = fmin(1.0 - (double)omu[j + 1], hi);
+        if (!(b > a)) continue;
+        // phi_k is linear on each side of c: trapezoids are exact per piece
+        const double m = fmin(fmax(c, a), b);
+        const double pa = 1.0 - fabs(a - c) * inv_h, pm = 1.0 - fabs(m - c) * inv_h,
+                     pb = 1.0 - fabs(b - c) * inv_h;
+        acc += (double)pdf[j] * 0.5 * ((pa + pm) * (m - a) + (pm + pb) * (b - m));
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) z[k] = part[0];
+}
+
+constexpr int ADJ_BLOCK = 256;     // threads per CTA without phase weights
+constexpr int ADJ_BLOCK_W = 128;   // with phase weights (private accumulators)
+constexpr int ADJ_LIST = 8;        // sampled angles kept per photon before a replay is needed
+
+// Private single-precision accumulators: hat k of thread t at rows[k*B + t]
+// (consecutive threads in consecutive banks; no atomics, fixed order).
+__device__ __forceinline__ void hat_add(float *rows, int nw_stride, int k, float f, float v)
+{
+    rows[k * nw_stride + threadIdx.x] += v * (1.0f - f);
+    rows[(k + 1) * nw_stride + threadIdx.x] += v * f;
+}
+
+template <int PHASE, bool PHASEW>
+__global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constant__ AdjArgs A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const CommonArgs &C = A.c;
+    const MediumArgs &M = A.m;
+    const uint32_t tb = (PHASE == MC_PHASE_TABLE && !PHASEW) ? C.table_bytes : 0u;
+    const int nw = PHASEW ? A.n_w : 0;
+    const int B = blockDim.x, warps = B / 32, warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+    double *s_z = reinterpret_cast<double *>(smem + tb);   // [nw]
+    double *s_red = s_z + nw;                              // [warps][4]
+    unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(s_red + warps * 4);
+    float *rows = reinterpret_cast<float *>(s_bar + 2);    // [nw][B]
+    for (int i = threadIdx.x; i < nw * B; i += B) rows[i] = 0.0f;
+    if (threadIdx.x == 0) mbar_init(s_bar);
+    Smem S;
+    S.table = smem;
+    S.omu = S.pdf = nullptr;
+    S.guide = nullptr;
+    if (PHASE == MC_PHASE_TABLE) {
+        if (PHASEW) {
+            // shared memory holds the private accumulators; the table is read
+            // through L1 (41 KB, resident after the first touches)
+            S.table = const_cast<unsigned char *>(M.table);
+        } else if (!stage_bulk(smem, M.table, tb, s_bar, 0u, C.error)) {
+            return;
+        }
+        if (!bind_table(S, C)) return;
+    }
+    if (PHASEW)
+        for (int k = threadIdx.x; k < nw; k += B) s_z[k] = A.z[k];
+    __syncthreads();
+    const float *omu = S.omu, *pdf = S.pdf;
+    const uint16_t *guide = S.guide;
+    const float c_s = A.c_s;   // 1/mu_s - 1/mu_ext
+
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+    unsigned long long pool_next = 0, pool_end = 0;
+    bool alive = false, done = false;
+    int pass = 1, cnt = 0;
+    unsigned long long rel = 0;
+    uint32_t pk0 = 0, pk1 = 0, ev = 0, ncoll = 0;
+    float rx = 0, ry = 0, rz = 0, dx = 1, dy = 0, dz = 0, w = 1, Ssc = 0;
+    // the photon's running and total camera terms in single precision:
+    // P_tot - P_i is then accurate to ~1e-7 of the photon's total, far
+    // below the statistical error of any gradient
+    float P = 0.0f, Ptot = 0.0f;
+    double g_val = 0.0, g_s = 0.0, g_a = 0.0, g_z = 0.0;
+    // the photon's first ADJ_LIST sampled angles: hat index, fraction, P_i
+    // (indexed with compile-time constants only, so they stay in registers)
+    int lk[ADJ_LIST];
+    float lf[ADJ_LIST], lp[ADJ_LIST];
+#pragma unroll
+    for (int q = 0; q < ADJ_LIST; ++q) { lk[q] = 0; lf[q] = 0.0f; lp[q] = 0.0f; }
+
+    while (true) {
+        const unsigned need = __ballot_sync(FULL, !alive && !done);
+        if (need) {
+            const unsigned n_need = __popc(need), rank = __popc(need & lanemask_lt);
+            const unsigned long long avail = pool_end - pool_next;
+            unsigned long long mine;
+            if (avail >= n_need) {
+                mine = pool_next + rank;
+                pool_next += n_need;
+            } else {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(A.counter, (unsigned long long)CHUNK);
+                base = __shfl_sync(FULL, base, 0);
+                mine = (rank < avail) ? pool_next + rank : base + (rank - avail);
+                pool_next = base + (n_need - avail);
+                pool_end = base + CHUNK;
+            }
+            if (!alive && !done) {
+                if (mine < M.n_photons) {
+                    rel = mine;
+                    const unsigned long long p = M.photon_offset + mine;
+                    pk0 = (uint32_t)p;
+                    pk1 = (uint32_t)(p >> 32);
+                    pass = 1;
+                    alive = true;
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, alive)) break;
+        if (!alive) continue;
+        if (ev == 0) {
+            // (re)start of a pass: the photon enters as in the forward walk
+            rx = 0.f; ry = 0.f; rz = 0.f;
+            dx = 1.f; dy = 0.f; dz = 0.f;
+            w = 1.f;
+            P = 0.0f;
+            cnt = 0;
+            if (C.beam_r > 0.f) {
+                const uint4 b = philox10(make_uint4(pk0, pk1, 0xFFFFFFFFu, 0u), M.key0, M.key1);
+                const float rho = C.beam_r * sqrtf(u01(b.x));
+                float sp, cp;
+                sincospif(2.0f * u01(b.y), &sp, &cp);
+                ry = rho * cp;
+                rz = rho * sp;
+            }
+        }
+
+        const uint4 rnd = philox10(make_uint4(pk0, pk1, ev, 0u), M.key0, M.key1);
+        ++ev;
+        const float u0 = u01(rnd.x), u1 = u01(rnd.y), u2 = u01(rnd.z), u3 = u01(rnd.w);
+        const float s = -logf(u0) * M.inv_mu_ext;
+        const float px = fmaf(s, dx, rx), py = fmaf(s, dy, ry), pz = fmaf(s, dz, rz);
+        bool end = !((px > 0.f) & (px < C.lx) & (fabsf(py) < C.hy) & (fabsf(pz) < C.hz));
+        if (!end) {
+            rx = px; ry = py; rz = pz;
+            ++ncoll;
+            Ssc += M.inv_mu_ext - s;
+            w = w * M.albedo;
+            int nb, ix, iz;
+            const float psr = camera_psr<PHASE>(M, C, omu, pdf, guide, dy, nb);
+            const float l = C.hy - ry;
+            const float nee = w * psr * expf(-M.mu_ext * l);
+            const int pix = camera_pixel(C, rx, rz, ix, iz);
+            const float Aj = __ldg(&A.adj[pix]) * nee;
+            P += Aj;
+            if (pass == 1) {
+                const float jj = (float)ncoll;
+                g_val += (double)Aj;
+                g_s += (double)Aj * (double)(Ssc + jj * c_s - l);
+                g_a += (double)Aj * (double)(Ssc - jj * M.inv_mu_ext - l);
+                g_z += (double)jj * (double)Aj;
+                if (PHASEW && Aj != 0.0f) {
+                    float f;
+                    const int k = hat_pair(nw, dy, f);
+                    hat_add(rows, B, k, f, Aj);
+                }
+            }
+            if (C.max_scatter && ncoll >= C.max_scatter) {
+                end = true;
+            } else {
+                const float om = sample_omu<PHASE>(M, C, omu, u1);
+                if (PHASEW) {
+                    float f;
+                    const int k = hat_pair(nw, 1.0f - om, f);
+                    if (pass == 1) {
+#pragma unroll
+                        for (int q = 0; q < ADJ_LIST; ++q)
+                            if (q == cnt) { lk[q] = k; lf[q] = f; lp[q] = P; }
+                        ++cnt;
+                    } else {
+                        const float coef = Ptot - P;
+                        if (coef != 0.0f) hat_add(rows, B, k, f, coef);
+                    }
+                }
+                rotate(dx, dy, dz, om, u2);
+                if (w < C.rr_thr) {
+                    if (u3 < C.rr_surv) w = w * C.inv_rr_surv;
+                    else end = true;
+                }
+                if (!end && ev >= C.max_events) end = true;
+            }
+        }
+        if (end) {
+            bool replay = false;
+            if (PHASEW && pass == 1 && P != 0.0f) {
+                if (cnt <= ADJ_LIST) {
+                    // every sampled angle is in the list: sum_i phi(mu_i) (P_tot - P_i)
+#pragma unroll
+                    for (int q = 0; q < ADJ_LIST; ++q) {
+                        if (q < cnt) {
+                            const float coef = P - lp[q];
+                            if (coef != 0.0f) hat_add(rows, B, lk[q], lf[q], coef);
+                        }
+                    }
+                } else {
+                    Ptot = P;   // replay the same photon for its later angles
+                    pass = 2;
+                    replay = true;
+                }
+            }
+            if (!replay) alive = false;
+            ev = 0;
+            ncoll = 0;
+            Ssc = 0.0f;
+        }
+    }
+
+    // -------- reduce: lanes -> warp -> CTA row of partials (fixed order)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        g_val += __shfl_xor_sync(FULL, g_val, o);
+        g_s += __shfl_xor_sync(FULL, g_s, o);
+        g_a += __shfl_xor_sync(FULL, g_a, o);
+        g_z += __shfl_xor_sync(FULL, g_z, o);
+    }
+    if (lane == 0) {
+        s_red[warp * 4 + 0] = g_val;
+        s_red[warp * 4 + 1] = g_s;
+        s_red[warp * 4 + 2] = g_a;
+        s_red[warp * 4 + 3] = g_z;
+    }
+    __syncthreads();
+    double *row = A.partials + (size_t)blockIdx.x * (3 + A.n_w);
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int q = 0; q < warps; ++q) t += s_red[q * 4 + threadIdx.x];
+        row[threadIdx.x] = t;
+    }
+    if (PHASEW) {
+        double gzb = 0.0;
+        for (int q = 0; q < warps; ++q) gzb += s_red[q * 4 + 3];
+        for (int k = threadIdx.x; k < nw; k += B) {
+            double t = 0.0;
+            for (int q = 0; q < B; ++q) t += (double)rows[k * B + q];
+            row[3 + k] = t - s_z[k] * gzb;
+        }
+    }
+}
+
+// out[q] = sum over the grid's rows, in row order (deterministic).
+__global__ void adjoint_reduce(const double *partials, int rows, int width, double *out)
+{
+    for (int q = threadIdx.x; q < width; q += blockDim.x) {
+        double t = 0.0;
+        for (int r = 0; r < rows; ++r) t += partials[(size_t)r * width + q];
+        out[q] = t;
+    }
 }
 
 __global__ void philox_kernel(const uint4 *ctr, uint64_t n, uint32_t k0, uint32_t k1, uint4 *out)
@@ -661,6 +986,54 @@ cudaError_t launch_batch(const BatchArgs &a0, const LaunchCfg &cfg0, cudaStream_
     if (a.c.phase_kind == MC_PHASE_TABLE)
         return smem_img ? launch_batch_one<0, true>(a, cfg, smem, st) : launch_batch_one<0, false>(a, cfg, smem, st);
     return smem_img ? launch_batch_one<1, true>(a, cfg, smem, st) : launch_batch_one<1, false>(a, cfg, smem, st);
+}
+
+int adjoint_max_grid()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms * (2048 / ADJ_BLOCK_W);
+}
+
+namespace {
+template <int PHASE, bool PHASEW>
+cudaError_t launch_adjoint_one(const AdjArgs &a, int rows, double *out, cudaStream_t st)
+{
+    auto kern = adjoint_kernel<PHASE, PHASEW>;
+    const int nw = PHASEW ? a.n_w : 0;
+    const int block = PHASEW ? ADJ_BLOCK_W : ADJ_BLOCK;
+    const size_t smem = ((PHASE == MC_PHASE_TABLE && !PHASEW) ? a.c.table_bytes : 0) +
+                        sizeof(double) * (nw + (block / 32) * 4) + 16 + sizeof(float) * nw * block;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, bps = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, block, smem)) != cudaSuccess) return e;
+    if (bps < 1) return cudaErrorInvalidConfiguration;
+    long long grid = (long long)sms * bps;
+    const long long cap = (long long)((a.m.n_photons + CHUNK - 1) / CHUNK + block / 32 - 1) / (block / 32);
+    if (cap < grid) grid = cap < 1 ? 1 : cap;
+    if (grid > rows) grid = rows;
+    if (PHASEW) {
+        hat_integrals_kernel<<<a.n_w, 256, 0, st>>>(a.m.table, a.n_w, a.z);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    kern<<<(unsigned)grid, block, smem, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    adjoint_reduce<<<1, 128, 0, st>>>(a.partials, (int)grid, 3 + a.n_w, out);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_adjoint(const AdjArgs &a, int rows, double *out, cudaStream_t st)
+{
+    if (rows < 1) return cudaErrorInvalidValue;
+    if (a.c.phase_kind == MC_PHASE_TABLE)
+        return a.n_w ? launch_adjoint_one<0, true>(a, rows, out, st) : launch_adjoint_one<0, false>(a, rows, out, st);
+    if (a.n_w) return cudaErrorInvalidValue;
+    return launch_adjoint_one<1, false>(a, rows, out, st);
 }
 
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out, cudaStream_t st)

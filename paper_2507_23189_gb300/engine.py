@@ -195,6 +195,31 @@ class Engine:
         self._keep = keep
         return buf
 
+    def adjoint(self, medium, adj_image, n_photons, n_w=64, seed=1, stream=None, **kw):
+        """(L, dL/dmu_s, dL/dmu_a, dL/dw_0..) for L = sum(adj_image * image)
+        over the photons run(medium, n_photons, seed, **kw) simulates, as a
+        float64 device tensor (mc_adjoint). adj_image: [nz, nx] in weight
+        units per image unit."""
+        torch = _torch()
+        rp = run_params(n_photons, seed, **kw)
+        m, keep = medium.as_c(self.device)
+        adj = adj_image.to(device=self.device, dtype=torch.float32).contiguous()
+        if tuple(adj.shape) != (self.camera.nz, self.camera.nx):
+            raise ValueError("adjoint image must be [nz, nx]")
+        wb = N.lib().mc_adjoint_workspace_bytes(n_w)
+        if wb == 0:
+            raise N.McError("mc_adjoint_workspace_bytes", -1)
+        if getattr(self, "_adj_work", None) is None or self._adj_work.numel() < wb:
+            self._adj_work = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        out = torch.empty(3 + n_w, dtype=torch.float64, device=self.device)
+        g, c = self.geometry.as_c(), self.camera.as_c()
+        N.check("mc_adjoint", N.lib().mc_adjoint(
+            C.byref(m), C.byref(g), C.byref(c), C.byref(rp), C.c_void_p(adj.data_ptr()), n_w,
+            C.c_void_p(out.data_ptr()), C.c_void_p(self.error.data_ptr()),
+            C.c_void_p(self._adj_work.data_ptr()), self._adj_work.numel(), _stream_handle(stream)))
+        self._keep = (keep, adj)
+        return out
+
     def check(self, stream=None):
         """Wait for the stream and raise if a kernel flagged an error."""
         N.check("mc_check", N.lib().mc_check(C.c_void_p(self.error.data_ptr()), _stream_handle(stream)))
@@ -260,6 +285,64 @@ class Batch:
 
     def check(self, stream=None):
         N.check("mc_check", N.lib().mc_check(C.c_void_p(self.error.data_ptr()), _stream_handle(stream)))
+
+
+def camera_image(engine, table, mu_s, mu_a, phase_w=None, n_photons=10**6, seed=1, grad_seed=None, **kw):
+    """Differentiable side-camera image (float64 [nz, nx], weight units).
+
+    mu_s, mu_a: 0-d float64 tensors; phase_w: optional tensor of hat-function
+    phase weights, which must equal 1 (the image is evaluated at w = 1 and
+    only the gradient with respect to w is provided). Forward runs mc_run;
+    backward runs mc_adjoint with grad_output as the adjoint image, on the
+    same photons (grad_seed None: the exact derivative of the sampled image)
+    or on an independent photon set drawn with grad_seed (an unbiased
+    estimate of the derivative of the expected image, uncorrelated with the
+    forward sample; what a loss that is nonlinear in the image needs)."""
+    torch = _torch()
+    if phase_w is None:
+        phase_w = torch.ones(0, dtype=torch.float64, device=engine.device)
+    gs = seed if grad_seed is None else grad_seed
+    return _CameraImage.apply(mu_s, mu_a, phase_w, engine, table, n_photons, (seed, gs), kw)
+
+
+def _make_camera_image():
+    torch = _torch()
+
+    class CameraImageFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, mu_s, mu_a, phase_w, engine, table, n_photons, seed, kw):
+            if phase_w.numel() and not bool(torch.all(phase_w == 1)):
+                raise ValueError("the image is evaluated at phase weights w = 1")
+            seed, grad_seed = seed
+            med = Medium(float(mu_s), float(mu_a), "table", 0.0, table)
+            engine.run(med, n_photons, seed=seed, **kw)
+            engine.check()
+            img = engine.image.to(torch.float64) * 2.0 ** -engine.image_frac_bits
+            ctx.engine, ctx.med, ctx.n, ctx.seed, ctx.kw = engine, med, n_photons, grad_seed, kw
+            ctx.n_w = phase_w.numel()
+            ctx.devs = (mu_s.device, mu_a.device, phase_w.device)
+            return img
+
+        @staticmethod
+        def backward(ctx, grad_img):
+            out = ctx.engine.adjoint(ctx.med, grad_img, ctx.n, n_w=ctx.n_w, seed=ctx.seed, **ctx.kw)
+            ds, da, dw = ctx.devs
+            gw = out[3:].to(dw) if ctx.n_w else None
+            return out[1].to(ds), out[2].to(da), gw, None, None, None, None, None
+
+    return CameraImageFn
+
+
+class _Lazy:
+    fn = None
+
+    def apply(self, *a):
+        if _Lazy.fn is None:
+            _Lazy.fn = _make_camera_image()
+        return _Lazy.fn.apply(*a)
+
+
+_CameraImage = _Lazy()
 
 
 def decode_trace(buf):

@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol(eng):
     for name in declared:
         assert hasattr(L, name), name
     assert set(N.EXPORTS) <= set(declared)
-    assert set(declared) <= set(N.EXPORTS) | {"mc_run_batch", "mc_adjoint"}
+    assert set(declared) <= set(N.EXPORTS)
 
 
 def test_status_strings(eng):
