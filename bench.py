@@ -257,7 +257,8 @@ def adjoint_comparison(E, dev, steps, flush):
     return {"forward_ms": t_fwd, "adjoint_ms": t_w, "adjoint_mu_only_ms": t_0,
             "cost_vs_forward": t_w / t_fwd, "cost_vs_forward_mu_only": t_0 / t_fwd,
             "workload": "tau=5 Mie, 1e7 photons, 128x128 image; gradient w.r.t. mu_s, mu_a and 64 "
-                        "phase-table weights (two replays per photon) or mu_s, mu_a only (one replay)"}
+                        "phase-table weights (one pass; photons with more than 8 scatterings are replayed once) "
+                        "or mu_s, mu_a only (one pass)"}
 
 
 def run_reference(args):
