@@ -44,6 +44,9 @@ def lib():
         L.oracle_phase_table_weighted.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
                                                   C.c_double, C.c_int, dp, C.c_int, C.c_int, dp, dp,
                                                   dp, dp]
+        L.oracle_paper_cdf.restype = C.c_int
+        L.oracle_paper_cdf.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                       C.c_int, dp]
         L.oracle_philox4x32_10_n.restype = None
         L.oracle_philox4x32_10_n.argtypes = [C.POINTER(C.c_uint32), C.c_uint64,
                                              C.c_uint64, C.POINTER(C.c_uint32)]
@@ -68,6 +71,7 @@ def _dp(a):
 
 PHASE_MIE = 0
 PHASE_HG = 1
+PHASE_PAPER = 2
 N_TOTALS = 8
 TOTAL_NAMES = ("reflect", "far", "side", "absorb", "roulette", "trunc", "ballistic", "cone")
 
@@ -78,6 +82,7 @@ class WalkCfg(C.Structure):
         ("phase_kind", C.c_int), ("hg_g", C.c_double),
         ("icdf", C.POINTER(C.c_double)), ("omu", C.POINTER(C.c_double)),
         ("n_bins", C.c_int),
+        ("cdf", C.POINTER(C.c_double)), ("n_theta", C.c_int),
         ("lx", C.c_double), ("ly", C.c_double), ("lz", C.c_double),
         ("beam_radius", C.c_double),
         ("nx", C.c_int), ("nz", C.c_int), ("n_radial", C.c_int), ("r_max", C.c_double),
@@ -194,6 +199,15 @@ def phase_table_weighted(m, x, w, n_bins=4096, n_fine=1 << 18):
                 n_fine=int(diag[3]))
 
 
+def paper_cdf(kind, m=1.0 + 0j, x=1.0, hg_g=0.0, n_theta=3000):
+    """The paper's sampling table (Sec. 3.1.2): cumulative probability at the
+    angles theta_i = i pi / (n_theta - 1). Returns dict(cdf, theta)."""
+    cdf = np.zeros(n_theta)
+    if lib().oracle_paper_cdf(kind, m.real, m.imag, x, hg_g, n_theta, _dp(cdf)):
+        raise ValueError("oracle_paper_cdf: bad arguments")
+    return dict(cdf=cdf, theta=np.arange(n_theta) * (np.pi / (n_theta - 1)))
+
+
 # ------------------------------------------------------------------ philox
 
 
@@ -260,6 +274,11 @@ def _walk_cfg(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,
     elif phase == "hg":
         cfg.phase_kind = PHASE_HG
         cfg.hg_g = hg_g
+    elif phase == "paper":
+        cdf = np.ascontiguousarray(table["cdf"], dtype=np.float64)
+        keep += [cdf]
+        cfg.phase_kind = PHASE_PAPER
+        cfg.cdf, cfg.n_theta = _dp(cdf), cdf.size
     else:
         raise ValueError(phase)
     cfg.lx, cfg.ly, cfg.lz, cfg.beam_radius = lx, ly, lz, beam_radius
@@ -279,29 +298,12 @@ def walk(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,
          n_photons=1000, photon_offset=0, seed=1,
          rr_threshold=1e-4, rr_survival=0.1, max_events=1_000_000, max_scatter=0,
          cone_cos=0.0, n_threads=None, n_trace=0, n_trace_events=32):
-    """Run the double-precision walk; returns a dict of tallies (and trace)."""
-    cfg = WalkCfg()
-    cfg.mu_s, cfg.mu_a = mu_s, mu_a
-    keep = []
-    if phase == "mie":
-        icdf = np.ascontiguousarray(table["icdf"], dtype=np.float64)
-        omu = np.ascontiguousarray(table["omu"], dtype=np.float64)
-        keep += [icdf, omu]
-        cfg.phase_kind = PHASE_MIE
-        cfg.icdf, cfg.omu = _dp(icdf), _dp(omu)
-        cfg.n_bins = icdf.size - 1
-    elif phase == "hg":
-        cfg.phase_kind = PHASE_HG
-        cfg.hg_g = hg_g
-    else:
-        raise ValueError(phase)
-    cfg.lx, cfg.ly, cfg.lz, cfg.beam_radius = lx, ly, lz, beam_radius
-    cfg.nx, cfg.nz, cfg.n_radial, cfg.r_max = nx, nz, n_radial, r_max
-    cfg.n_photons, cfg.photon_offset, cfg.seed = n_photons, photon_offset, seed
-    cfg.rr_threshold, cfg.rr_survival = rr_threshold, rr_survival
-    cfg.max_events, cfg.max_scatter = max_events, max_scatter
-    cfg.cone_cos = cone_cos
-    cfg.n_threads = n_threads if n_threads else (os.cpu_count() or 1)
+    """Run the double-precision walk; returns a dict of tallies (and trace).
+    phase: "mie" (equal-probability table), "hg" or "paper" (the table of
+    paper_cdf, sampled by binary search)."""
+    cfg, keep = _walk_cfg(mu_s, mu_a, phase, table, hg_g, lx, ly, lz, beam_radius, nx, nz, n_radial,
+                          r_max, n_photons, photon_offset, seed, rr_threshold, rr_survival, max_events,
+                          max_scatter, cone_cos, n_threads)
     image = np.zeros(nz * nx)
     image_sq = np.zeros(nz * nx)
     image_hits = np.zeros(nz * nx)

@@ -14,7 +14,8 @@
  *             functions S1/S2 (Eq. 5-6), phase function (Eq. 9), asymmetry
  *             parameter g (Eq. 12), cross section (Eq. 14), Eq. 17.
  *   table.c   normalisation (Eq. 10), cumulative distribution and its inverse
- *             on an equal-probability grid (Sec. 2.6, Sec. 3.1.2).
+ *             on an equal-probability grid (Sec. 2.6, Sec. 3.1.2), and the
+ *             paper's own 3000-angle cumulative distribution (Sec. 3.1.2).
  *   philox.c  Philox4x32-10 counter-based generator (Salmon et al., SC'11).
  *   walk.c    the photon random walk of Sec. 3.1.3 (Eq. 15, Eq. 16) with a
  *             next-event estimate for the 90-degree side camera (Sec. 4.3).
@@ -73,6 +74,7 @@ double oracle_optical_depth(double n_per_mm3, double sigma_mm2, double l_mm);
 /* Phase-function kinds understood by the table builder. */
 #define ORACLE_PHASE_MIE 0
 #define ORACLE_PHASE_HG  1
+#define ORACLE_PHASE_PAPER 2   /* walk only: the cdf of oracle_paper_cdf */
 
 /* Build the equal-probability inverse CDF of a phase function.
  *   kind == ORACLE_PHASE_MIE: (m_re, m_im, x) select the Mie phase function.
@@ -97,6 +99,14 @@ int oracle_phase_table_weighted(int kind, double m_re, double m_im, double x,
                                 int n_fine, double *icdf, double *omu, double *pdf,
                                 double *diag);
 
+/* The paper's own sampling table (Sec. 3.1.2): cdf[i], i < n_theta, the
+ * cumulative probability of scattering angles up to theta_i = i pi /
+ * (n_theta - 1) (trapezoidal rule on (1/2) P(cos theta) sin theta, normalised
+ * so that cdf[0] = 0 and cdf[n_theta - 1] = 1). The walk samples it by binary
+ * search and linear interpolation in theta (ORACLE_PHASE_PAPER). */
+int oracle_paper_cdf(int kind, double m_re, double m_im, double x, double hg_g,
+                     int n_theta, double *cdf);
+
 /* -------------------------------------------------------------- philox.c */
 
 /* Philox4x32 with 10 rounds: out = bijection(ctr) under key. */
@@ -115,11 +125,13 @@ double oracle_uniform(uint32_t r);
 typedef struct {
     /* medium */
     double mu_s, mu_a;          /* mm^-1 */
-    int phase_kind;             /* ORACLE_PHASE_MIE (table) or ORACLE_PHASE_HG */
+    int phase_kind;             /* ORACLE_PHASE_MIE (table), _HG or _PAPER */
     double hg_g;
     const double *icdf;         /* [n_bins+1] when phase_kind == MIE */
     const double *omu;          /* [n_bins+1], 1 - icdf */
     int n_bins;
+    const double *cdf;          /* [n_theta] when phase_kind == PAPER */
+    int n_theta;
     /* geometry: x in [0,lx] (beam axis), y in [-ly/2,ly/2], z in [-lz/2,lz/2] */
     double lx, ly, lz;
     double beam_radius;         /* 0: pencil beam at (0,0,0) */

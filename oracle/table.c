@@ -164,3 +164,56 @@ fail:
     free(F); free(mu); free(cum); free(t_icdf); free(t_omu);
     return -1;
 }
+
+/*
+ * The sampling scheme of Sec. 3.1.2 as printed: the phase function at
+ * n_theta equally spaced scattering angles theta_i = i pi / (n_theta - 1),
+ * i = 0 (forward) .. n_theta - 1 (backward), a cumulative distribution over
+ * them, and a binary search of that distribution for each sample. The paper
+ * does not say how the cumulative sum is formed; here it is the trapezoidal
+ * rule on the density in theta, (1/2) P(cos theta) sin theta (Eq. 10 with
+ * dOmega = 2 pi sin theta dtheta), divided by its total so that cdf[0] = 0
+ * and cdf[n_theta - 1] = 1.
+ */
+int oracle_paper_cdf(int kind, double m_re, double m_im, double x, double hg_g,
+                     int n_theta, double *cdf)
+{
+    if (n_theta < 3 || !cdf)
+        return -1;
+    if (kind == ORACLE_PHASE_HG && !(hg_g > -1.0 && hg_g < 1.0))
+        return -1;
+    if (kind != ORACLE_PHASE_HG && kind != ORACLE_PHASE_MIE)
+        return -1;
+    const int n = n_theta - 1;
+    const double h = M_PI / n;
+    double *F = malloc((size_t)n_theta * sizeof *F);
+    double *mu = malloc((size_t)n_theta * sizeof *mu);
+    if (!F || !mu) {
+        free(F); free(mu);
+        return -1;
+    }
+    for (int i = 0; i < n_theta; ++i)
+        mu[i] = cos(i * h);
+    if (kind == ORACLE_PHASE_MIE) {
+        if (oracle_mie_phase_raw(m_re, m_im, x, mu, n_theta, F)) {
+            free(F); free(mu);
+            return -1;
+        }
+    } else {
+        for (int i = 0; i < n_theta; ++i)
+            F[i] = hg_phase(hg_g, i * h);
+    }
+    for (int i = 0; i < n_theta; ++i)
+        F[i] *= 0.5 * sin(i * h);
+    cdf[0] = 0.0;
+    for (int i = 0; i < n; ++i)
+        cdf[i + 1] = cdf[i] + 0.5 * h * (F[i] + F[i + 1]);
+    const double Z = cdf[n];
+    free(F); free(mu);
+    if (!(Z > 0.0))
+        return -1;
+    for (int i = 1; i < n; ++i)
+        cdf[i] /= Z;
+    cdf[n] = 1.0;
+    return 0;
+}

@@ -13,8 +13,10 @@
  *       c = w p_sr(d_y) exp(-mu_ext (ly/2 - r_y)),
  *     p_sr the phase function per steradian, here the density of the same
  *     discretised table the walk samples (or Eq. 11 for H-G)
- *   scattering angle from the inverse-CDF table (Sec. 2.6) or from H-G
- *     with the same g (Sec. 3.1.3); azimuth phi uniform on [0, 2 pi)
+ *   scattering angle from the inverse-CDF table (Sec. 2.6), from the
+ *     paper's 3000-angle cumulative distribution by binary search
+ *     (Sec. 3.1.2), or from H-G with the same g (Sec. 3.1.3); azimuth phi
+ *     uniform on [0, 2 pi)
  *   direction update in the orthonormal basis of Duff et al. (JCGT 6(1),
  *     2017), d' = mu d + sqrt(1 - mu^2) (cos phi e1 + sin phi e2)
  *   weight threshold (Sec. 3.1.3): below rr_threshold a photon survives with
@@ -107,6 +109,20 @@ static int table_bin(const double *icdf, int n, double mu)
     while (hi - lo > 1) {
         int mid = (lo + hi) / 2;
         if (icdf[mid] <= mu)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+/* Largest i in [0, n-1] with cdf[i] <= u (plain bisection; cdf[0] = 0). */
+static int cdf_interval(const double *cdf, int n, double u)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (cdf[mid] <= u)
             lo = mid;
         else
             hi = mid;
@@ -239,6 +255,19 @@ static void run_photon(const oracle_walk_cfg *c, uint64_t p, acc_t *A,
         int nbin = -1;
         if (c->phase_kind == ORACLE_PHASE_HG) {
             psr = hg_per_sr(c->hg_g, muc);
+        } else if (c->phase_kind == ORACLE_PHASE_PAPER) {
+            /* the sampled distribution is uniform in theta on each interval,
+             * density (cdf[j+1] - cdf[j]) / dtheta per radian, hence that
+             * divided by sin(theta) per unit cos(theta) */
+            const int n = c->n_theta - 1;
+            const double dth = M_PI / n;
+            double thc = acos(fmax(-1.0, fmin(1.0, muc)));
+            nbin = (int)floor(thc / dth);
+            if (nbin > n - 1) nbin = n - 1;
+            double stc = sin(thc);
+            double pth = (c->cdf[nbin + 1] - c->cdf[nbin]) / dth;
+            psr = stc > 0.0 ? pth / stc / (2.0 * M_PI) : 0.0;
+            margin = min2(margin, min2(cos(nbin * dth) - muc, muc - cos((nbin + 1) * dth)));
         } else {
             nbin = table_bin(c->icdf, c->n_bins, muc);
             double pdf = (1.0 / c->n_bins) / (c->omu[nbin] - c->omu[nbin + 1]);
@@ -269,6 +298,17 @@ static void run_photon(const oracle_walk_cfg *c, uint64_t p, acc_t *A,
             if (c->phase_kind == ORACLE_PHASE_HG) {
                 mu = hg_sample(c->hg_g, u1);
                 omu = 1.0 - mu;
+            } else if (c->phase_kind == ORACLE_PHASE_PAPER) {
+                /* binary search of the cumulative distribution, then linear
+                 * interpolation in theta inside the interval (Sec. 3.1.2) */
+                const int n = c->n_theta - 1;
+                int i = cdf_interval(c->cdf, n, u1);
+                double f = (u1 - c->cdf[i]) / (c->cdf[i + 1] - c->cdf[i]);
+                margin = min2(margin, min2(u1 - c->cdf[i], c->cdf[i + 1] - u1));
+                double th = (i + f) * (M_PI / n);
+                double sh = sin(0.5 * th);
+                omu = 2.0 * sh * sh;
+                mu = cos(th);
             } else {
                 double t = u1 * c->n_bins;
                 int i = (int)floor(t);
@@ -364,6 +404,10 @@ int oracle_walk(const oracle_walk_cfg *c, oracle_walk_out *out,
         c->mu_a < 0 || !(c->r_max > 0) || c->beam_radius < 0)
         return -1;
     if (c->phase_kind == ORACLE_PHASE_MIE && (!c->icdf || !c->omu || c->n_bins < 2))
+        return -1;
+    if (c->phase_kind == ORACLE_PHASE_PAPER && (!c->cdf || c->n_theta < 3))
+        return -1;
+    if (c->phase_kind < 0 || c->phase_kind > ORACLE_PHASE_PAPER)
         return -1;
     if (c->phase_kind == ORACLE_PHASE_HG && !(c->hg_g > -1.0 && c->hg_g < 1.0))
         return -1;
