@@ -95,6 +95,25 @@ size_t mc_table_bytes(int n_bins);
 mc_status mie_table_build(const mie_params *params, mie_info *info, void *table,
                           double *omu64, double *pdf64);
 
+/* The paper's own sampling table (Sec. 3.1.2): the phase function at
+ * n_theta equally spaced scattering angles theta_i = i pi / (n_theta - 1),
+ * its cumulative distribution by the trapezoidal rule on (1/2) P sin(theta),
+ * normalised to end at 1; the walk samples it by bisection and linear
+ * interpolation in theta (MC_PHASE_PAPER). The paper uses n_theta = 3000.
+ * mc_paper_table_bytes: bytes of the packed blob (0 unless 16 <= n_theta <=
+ * 16384). mie_paper_table_build:
+ *   params   in: particle and wavelength (n_bins is ignored).
+ *   info     out (may be NULL): as mie_table_build; g_table is the mean
+ *            cosine of the sampled distribution.
+ *   table    out (may be NULL): host buffer of mc_paper_table_bytes(n_theta)
+ *            bytes; copy it to a 16-byte-aligned device buffer for
+ *            mc_medium.d_table.
+ *   cdf64    out (may be NULL): double[n_theta], the cumulative distribution.
+ * Returns MC_OK, MC_ERR_ARG or MC_ERR_NUMERIC. Thread-safe. */
+size_t mc_paper_table_bytes(int n_theta);
+mc_status mie_paper_table_build(const mie_params *params, int n_theta, mie_info *info,
+                                void *table, double *cdf64);
+
 /* ------------------------------------------------------------------------
  * Transport (Sec. 2.6, Sec. 3.1.3: Eq. 15 free path, Eq. 16 implicit
  * capture, weight threshold; Sec. 4.3: 90-degree side camera).
@@ -102,13 +121,16 @@ mc_status mie_table_build(const mie_params *params, mie_info *info, void *table,
 
 #define MC_PHASE_TABLE 0   /* sample the staged inverse-CDF table           */
 #define MC_PHASE_HG    1   /* Henyey-Greenstein (Eq. 11) with parameter hg_g */
+#define MC_PHASE_PAPER 2   /* the paper's CDF table, bisection (Sec. 3.1.2) */
 
 typedef struct {
     double mu_s, mu_a;      /* scattering / absorption coefficients, mm^-1     */
-    int phase_kind;         /* MC_PHASE_TABLE or MC_PHASE_HG                   */
+    int phase_kind;         /* MC_PHASE_TABLE, MC_PHASE_HG or MC_PHASE_PAPER   */
     double hg_g;            /* H-G asymmetry, -1 < g < 1 (MC_PHASE_HG only)    */
-    const void *d_table;    /* device copy of a mie_table_build() blob         */
-    int n_bins;             /* bins of that blob (checked against its header)  */
+    const void *d_table;    /* device copy of a mie_table_build() blob, or of
+                               a mie_paper_table_build() blob (PAPER)          */
+    int n_bins;             /* bins of that blob, or its n_theta for PAPER
+                               (checked against the blob's header)             */
 } mc_medium;
 
 /* Eq. 17: number density (per mm^3) times the extinction cross section gives
@@ -229,8 +251,10 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom,
  * their Philox counters (nothing about the paths is stored). Roulette
  * factors are held fixed. d_out[3 + n_phase_w] receives (L, dL/dmu_s,
  * dL/dmu_a, dL/dw_0, ..) in double precision, reduced in a fixed order.
- * n_phase_w: 0 (no phase weights, one replay per photon) or 2..256 (table
- * phase only; two replays per photon). Requires mu_s > 0.
+ * n_phase_w: 0 (no phase weights) or 2..256 (MC_PHASE_TABLE only). One pass
+ * per photon; with phase weights, photons with more than 8 collisions are
+ * replayed once more. MC_PHASE_PAPER is not supported (MC_ERR_ARG).
+ * Requires mu_s > 0.
  * d_work: mc_adjoint_workspace_bytes(n_phase_w) bytes. The paper has no
  * gradients; this serves fitting mu_s, mu_a and the phase function. */
 size_t mc_adjoint_workspace_bytes(int n_phase_w);
@@ -238,6 +262,28 @@ mc_status mc_adjoint(const mc_medium *medium, const mc_geometry *geom,
                      const mc_camera *camera, const mc_run_params *run,
                      const float *d_adj_image, int n_phase_w, double *d_out,
                      uint32_t *d_error, void *d_work, size_t work_bytes, void *stream);
+
+/* Image comparison (Sec. 3.1.4: every image normalised the same way, here
+ * min-max to [0, 1]; Table 3: RMSE and Pearson r over the pixels; Table 4:
+ * radial profiles, i.e. means over n_r equal-width rings about the image
+ * centre out to the half-diagonal, compared zone by zone, ring b standing for
+ * the angle 180 deg (b + 1/2) / n_r: forward < 30 deg, intermediate 30-120
+ * deg, edge > 120 deg). Images: device int64 [nz][nx] (the camera images of
+ * mc_run; the unit cancels in the normalisation). d_b may be NULL.
+ * d_out: mc_metrics_out_len(n_r) doubles, device:
+ *   [0..5]   a vs ref: RMSE, r, zone RMSE (forward, intermediate, edge),
+ *            correlation of the radial profiles
+ *   [6..11]  the same for b (zeros without b)
+ *   [12]     share of rings where a's profile is closer to ref's than b's
+ *   [13 ..]  the radial profiles of ref, a and b (n_r each)
+ * Rings that hold no pixel are left out of the profile statistics. Sums are
+ * double precision in a fixed order (bit-reproducible). 1 <= n_r <= 4096,
+ * nx, nz >= 1, nx * nz <= 2^26. d_work: mc_metrics_workspace_bytes(n_r). */
+int mc_metrics_out_len(int n_r);
+size_t mc_metrics_workspace_bytes(int n_r);
+mc_status mc_image_metrics(const int64_t *d_ref, const int64_t *d_a, const int64_t *d_b,
+                           int nx, int nz, int n_r, double *d_out, void *d_work,
+                           size_t work_bytes, void *stream);
 
 /* Host-buffer form of mc_run, for callers whose inputs and outputs live in
  * host memory. The table blob (mc_table_bytes(n_bins) bytes, or NULL for

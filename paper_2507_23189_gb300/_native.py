@@ -13,7 +13,7 @@ MC_OK = 0
 STATUS = {0: "MC_OK", -1: "MC_ERR_ARG", -2: "MC_ERR_CUDA", -3: "MC_ERR_NOMEM", -4: "MC_ERR_TIMEOUT",
           -5: "MC_ERR_OVERFLOW", -6: "MC_ERR_NUMERIC", -7: "MC_ERR_EVENTS", -8: "MC_ERR_TABLE"}
 EFLAG_EVENTS, EFLAG_TIMEOUT, EFLAG_NUMERIC, EFLAG_OVERFLOW, EFLAG_TABLE = 1, 2, 4, 8, 16
-PHASE_TABLE, PHASE_HG = 0, 1
+PHASE_TABLE, PHASE_HG, PHASE_PAPER = 0, 1, 2
 TOT_REFLECT, TOT_FAR, TOT_SIDE, TOT_ABSORB, TOT_ROULETTE, TOT_TRUNC, TOT_BALLISTIC, TOT_STEPS = range(8)
 N_TOTALS = 8
 WEIGHT_FRAC_BITS = 32
@@ -23,7 +23,8 @@ TRACE_WORDS = 12
 EXPORTS = ("mc_table_bytes", "mie_table_build", "mc_medium_from_density", "mc_workspace_bytes",
            "mc_run", "mc_host_workspace_bytes", "mc_run_host", "mc_trace", "mc_check", "mc_philox",
            "mc_status_string", "mc_run_static", "mc_batch_workspace_bytes", "mc_run_batch",
-           "mc_adjoint_workspace_bytes", "mc_adjoint")
+           "mc_adjoint_workspace_bytes", "mc_adjoint", "mc_paper_table_bytes", "mie_paper_table_build",
+           "mc_metrics_out_len", "mc_metrics_workspace_bytes", "mc_image_metrics")
 
 
 class McError(RuntimeError):
@@ -129,6 +130,16 @@ def lib():
     L.mc_adjoint.restype = C.c_int
     L.mc_adjoint.argtypes = [P(Medium), P(Geometry), P(Camera), P(RunParams), vp, C.c_int, vp, vp, vp,
                              C.c_size_t, vp]
+    L.mc_paper_table_bytes.restype = C.c_size_t
+    L.mc_paper_table_bytes.argtypes = [C.c_int]
+    L.mie_paper_table_build.restype = C.c_int
+    L.mie_paper_table_build.argtypes = [P(MieParams), C.c_int, P(MieInfo), vp, P(C.c_double)]
+    L.mc_metrics_out_len.restype = C.c_int
+    L.mc_metrics_out_len.argtypes = [C.c_int]
+    L.mc_metrics_workspace_bytes.restype = C.c_size_t
+    L.mc_metrics_workspace_bytes.argtypes = [C.c_int]
+    L.mc_image_metrics.restype = C.c_int
+    L.mc_image_metrics.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, vp, vp, C.c_size_t, vp]
     L.mc_status_string.restype = C.c_char_p
     L.mc_status_string.argtypes = [C.c_int]
     _lib = L

@@ -30,10 +30,21 @@ mc_status check_medium(const mc_medium *m)
     } else if (m->phase_kind == MC_PHASE_TABLE) {
         if (!m->d_table || !aligned(m->d_table, 16) || !mc_table_layout(m->n_bins, nullptr))
             return MC_ERR_ARG;
+    } else if (m->phase_kind == MC_PHASE_PAPER) {
+        if (!m->d_table || !aligned(m->d_table, 16) || !mc_paper_layout(m->n_bins, nullptr))
+            return MC_ERR_ARG;
     } else {
         return MC_ERR_ARG;
     }
     return MC_OK;
+}
+
+// Bytes of the medium's table blob (0 for H-G).
+size_t table_bytes_of(const mc_medium *m)
+{
+    if (m->phase_kind == MC_PHASE_TABLE) return mc_table_layout(m->n_bins, nullptr);
+    if (m->phase_kind == MC_PHASE_PAPER) return mc_paper_layout(m->n_bins, nullptr);
+    return 0;
 }
 
 mc_status check_geom(const mc_geometry *g)
@@ -90,7 +101,7 @@ void fill_medium(mcx::MediumArgs &m, const mc_medium *med, uint64_t n_photons, u
     m.hg_A = (float)(2.0 * (1.0 - gg) * (1.0 - gg));
     m.hg_a2 = (float)((1.0 - gg) * (1.0 - gg));
     m.hg_K = (float)((1.0 - gg * gg) / (4.0 * kPi));
-    m.table = (med->phase_kind == MC_PHASE_TABLE) ? static_cast<const unsigned char *>(med->d_table) : nullptr;
+    m.table = (med->phase_kind != MC_PHASE_HG) ? static_cast<const unsigned char *>(med->d_table) : nullptr;
     m.key0 = (uint32_t)seed;
     m.key1 = (uint32_t)(seed >> 32);
     m.n_photons = n_photons;
@@ -104,8 +115,8 @@ void fill_common(mcx::CommonArgs &c, const mc_medium *m, const mc_geometry *g, c
                  const mc_run_params *r, uint32_t *error)
 {
     c.phase_kind = m->phase_kind;
-    c.table_bytes = (m->phase_kind == MC_PHASE_TABLE) ? (uint32_t)mc_table_layout(m->n_bins, nullptr) : 0u;
-    c.n_bins = (m->phase_kind == MC_PHASE_TABLE) ? m->n_bins : 0;
+    c.table_bytes = (uint32_t)table_bytes_of(m);
+    c.n_bins = (m->phase_kind != MC_PHASE_HG) ? m->n_bins : 0;
     c.lx = (float)g->lx;
     c.hy = (float)(0.5 * g->ly);
     c.hz = (float)(0.5 * g->lz);
@@ -219,11 +230,8 @@ mc_status mc_trace(const mc_medium *medium, const mc_geometry *geom, const mc_ca
 size_t mc_host_workspace_bytes(const mc_medium *medium, const mc_camera *camera)
 {
     if (check_camera(camera) != MC_OK || !medium) return 0;
-    size_t tb = 0;
-    if (medium->phase_kind == MC_PHASE_TABLE) {
-        tb = mc_table_layout(medium->n_bins, nullptr);
-        if (!tb) return 0;
-    }
+    const size_t tb = table_bytes_of(medium);
+    if (medium->phase_kind != MC_PHASE_HG && !tb) return 0;
     return up(tb) + up(sizeof(int64_t) * (size_t)camera->nx * camera->nz) +
            up(sizeof(int64_t) * (size_t)camera->n_radial) + up(sizeof(int64_t) * MC_N_TOTALS) +
            up(sizeof(uint32_t)) + up(mc_workspace_bytes(camera));
@@ -236,9 +244,9 @@ mc_status mc_run_host(const mc_medium *medium, const void *table, const mc_geome
 {
     if (!medium || !image || !radial || !totals || !error || !d_work || !aligned(d_work, 256))
         return MC_ERR_ARG;
-    if (medium->phase_kind == MC_PHASE_TABLE && !table) return MC_ERR_ARG;
+    if (medium->phase_kind != MC_PHASE_HG && !table) return MC_ERR_ARG;
     mc_medium m = *medium;
-    if (m.phase_kind == MC_PHASE_TABLE) m.d_table = d_work;  // placeholder for validation
+    if (m.phase_kind != MC_PHASE_HG) m.d_table = d_work;  // placeholder for validation
     mc_status s;
     if ((s = validate_all(&m, geom, camera, run)) != MC_OK) return s;
     const size_t need = mc_host_workspace_bytes(medium, camera);
@@ -246,7 +254,7 @@ mc_status mc_run_host(const mc_medium *medium, const void *table, const mc_geome
     if (work_bytes < need) return MC_ERR_NOMEM;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char *p = static_cast<unsigned char *>(d_work);
-    size_t tb = m.phase_kind == MC_PHASE_TABLE ? mc_table_layout(m.n_bins, nullptr) : 0;
+    const size_t tb = table_bytes_of(&m);
     const size_t npix = (size_t)camera->nx * camera->nz;
     mc_tallies t;
     unsigned char *d_table = p;
@@ -314,7 +322,7 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom, 
         const mc_instance &I = inst[i];
         if ((s = check_medium(&I.medium)) != MC_OK) return s;
         if (I.medium.phase_kind != inst[0].medium.phase_kind ||
-            (I.medium.phase_kind == MC_PHASE_TABLE && I.medium.n_bins != inst[0].medium.n_bins))
+            (I.medium.phase_kind != MC_PHASE_HG && I.medium.n_bins != inst[0].medium.n_bins))
             return MC_ERR_ARG;   // one phase kind and table size per batch
         if (!I.d_image || !I.d_radial || !I.d_totals || !aligned(I.d_image, 8) || !aligned(I.d_radial, 8) ||
             !aligned(I.d_totals, 8) || I.photon_offset + I.n_photons < I.photon_offset)
@@ -383,7 +391,7 @@ mc_status mc_adjoint(const mc_medium *medium, const mc_geometry *geom, const mc_
     if ((s = validate_all(medium, geom, camera, run)) != MC_OK) return s;
     if (!d_adj_image || !d_out || !d_error || !d_work || !aligned(d_adj_image, 4) || !aligned(d_out, 8) ||
         !aligned(d_work, 16) || !(medium->mu_s > 0.0) || n_phase_w < 0 || n_phase_w == 1 || n_phase_w > 256 ||
-        (n_phase_w > 0 && medium->phase_kind != MC_PHASE_TABLE))
+        (n_phase_w > 0 && medium->phase_kind != MC_PHASE_TABLE) || medium->phase_kind == MC_PHASE_PAPER)
         return MC_ERR_ARG;
     const size_t need = mc_adjoint_workspace_bytes(n_phase_w);
     if (!need) return MC_ERR_CUDA;

@@ -138,17 +138,10 @@ double integrate(const MieSeries &S, double t0, double t1)
     return s * h;
 }
 
-}  // namespace
-
-extern "C" size_t mc_table_bytes(int n_bins) { return mc_table_layout(n_bins, nullptr); }
-
-extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *table,
-                                     double *omu64, double *pdf64)
+// The particle's Mie series and the quantities of mie_info (all but
+// g_table). Returns MC_ERR_ARG for parameters out of range.
+mc_status prepare(const mie_params *P, MieSeries &S, mie_info &I)
 {
-    if (!P) return MC_ERR_ARG;
-    mc_table_header H;
-    size_t bytes = mc_table_layout(P->n_bins, &H);
-    if (!bytes) return MC_ERR_ARG;
     if (!(P->diameter_um > 0.0) || !(P->n_medium > 0.0) || !(P->wavelength_nm > 0.0) ||
         !(P->n_particle_re > 0.0) || !(P->n_particle_im >= 0.0) || !std::isfinite(P->diameter_um) ||
         !std::isfinite(P->n_particle_re) || !std::isfinite(P->n_particle_im) ||
@@ -157,8 +150,6 @@ extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *
     const double x = kPi * P->diameter_um * P->n_medium / (P->wavelength_nm * 1e-3);
     if (!(x >= 1e-3) || x > 2000.0) return MC_ERR_ARG;
     const cplx m(P->n_particle_re / P->n_medium, P->n_particle_im / P->n_medium);
-
-    MieSeries S;
     if (!mie_series(m, x, S)) return MC_ERR_NUMERIC;
 
     double se = 0.0, ss = 0.0, sg = 0.0;
@@ -173,7 +164,37 @@ extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *
     // Q_abs is exactly zero for a real index; the series difference only
     // carries rounding (of either sign), so keep it non-negative.
     const double qabs = (m.imag() > 0.0) ? std::fmax(qext - qsca, 0.0) : 0.0;
-    const double g = 4.0 / (x * x) * sg / qsca;
+    I.x = x;
+    I.m_re = m.real();
+    I.m_im = m.imag();
+    I.qext = qext;
+    I.qsca = qsca;
+    I.qabs = qabs;
+    I.g = 4.0 / (x * x) * sg / qsca;
+    I.g_table = 0.0;
+    const double geo = kPi * (P->diameter_um * 1e-3) * (P->diameter_um * 1e-3) / 4.0;
+    I.sigma_ext_mm2 = qext * geo;
+    I.sigma_sca_mm2 = qsca * geo;
+    I.sigma_abs_mm2 = qabs * geo;
+    I.nmax = S.nmax;
+    return MC_OK;
+}
+
+}  // namespace
+
+extern "C" size_t mc_table_bytes(int n_bins) { return mc_table_layout(n_bins, nullptr); }
+
+extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *table,
+                                     double *omu64, double *pdf64)
+{
+    if (!P) return MC_ERR_ARG;
+    mc_table_header H;
+    size_t bytes = mc_table_layout(P->n_bins, &H);
+    if (!bytes) return MC_ERR_ARG;
+    MieSeries S;
+    mie_info I;
+    const mc_status st = prepare(P, S, I);
+    if (st != MC_OK) return st;
 
     // Panels in theta, accumulated from theta = pi (mu = -1) toward 0.
     const int n = P->n_bins;
@@ -230,19 +251,8 @@ extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *
     mean /= n;
 
     if (info) {
-        info->x = x;
-        info->m_re = m.real();
-        info->m_im = m.imag();
-        info->qext = qext;
-        info->qsca = qsca;
-        info->qabs = qabs;
-        info->g = g;
+        *info = I;
         info->g_table = mean;
-        double geo = kPi * (P->diameter_um * 1e-3) * (P->diameter_um * 1e-3) / 4.0;
-        info->sigma_ext_mm2 = qext * geo;
-        info->sigma_sca_mm2 = qsca * geo;
-        info->sigma_abs_mm2 = qabs * geo;
-        info->nmax = S.nmax;
     }
     if (omu64) std::memcpy(omu64, omu.data(), sizeof(double) * (n + 1));
     if (pdf64) std::memcpy(pdf64, pdf.data(), sizeof(double) * n);
@@ -314,5 +324,84 @@ extern "C" mc_status mc_medium_from_density(const mie_info *info, double nd, dou
     // Eq. 17 per unit length: mu = n sigma.
     out->mu_s = nd * info->sigma_sca_mm2;
     out->mu_a = nd * std::fmax(info->sigma_abs_mm2, 0.0) + mu_a_medium;
+    return MC_OK;
+}
+
+extern "C" size_t mc_paper_table_bytes(int n_theta) { return mc_paper_layout(n_theta, nullptr); }
+
+// Sec. 3.1.2 as printed: the phase function at n_theta equally spaced angles,
+// its cumulative distribution by the trapezoidal rule on (1/2) P sin(theta)
+// (Eq. 10's measure), normalised by the total, and the search aids the
+// kernel needs to sample it by bisection exactly as a double-precision
+// search would decide.
+extern "C" mc_status mie_paper_table_build(const mie_params *P, int n_theta, mie_info *info,
+                                           void *table, double *cdf64)
+{
+    if (!P) return MC_ERR_ARG;
+    mc_paper_header H;
+    const size_t bytes = mc_paper_layout(n_theta, &H);
+    if (!bytes) return MC_ERR_ARG;
+    MieSeries S;
+    mie_info I;
+    const mc_status st = prepare(P, S, I);
+    if (st != MC_OK) return st;
+
+    const int n = n_theta - 1;
+    const double dth = kPi / n;
+    std::vector<double> F(n_theta), cdf(n_theta);
+    for (int i = 0; i < n_theta; ++i) {
+        const double t = i * dth;
+        F[i] = 0.5 * phase_raw(S, std::cos(t)) * std::sin(t);
+    }
+    cdf[0] = 0.0;
+    for (int i = 0; i < n; ++i) cdf[i + 1] = cdf[i] + 0.5 * dth * (F[i] + F[i + 1]);
+    const double Z = cdf[n];
+    if (!(Z > 0.0) || !std::isfinite(Z)) return MC_ERR_NUMERIC;
+    for (int i = 1; i < n; ++i) cdf[i] /= Z;
+    cdf[n] = 1.0;
+
+    // mean cosine of the distribution that is uniform in theta on each interval
+    double mean = 0.0;
+    for (int i = 0; i < n; ++i)
+        mean += (cdf[i + 1] - cdf[i]) * (std::sin((i + 1) * dth) - std::sin(i * dth)) / dth;
+    if (info) {
+        *info = I;
+        info->g_table = mean;
+    }
+    if (cdf64) std::memcpy(cdf64, cdf.data(), sizeof(double) * n_theta);
+    if (table) {
+        unsigned char *blob = static_cast<unsigned char *>(table);
+        std::memset(blob, 0, bytes);
+        H.dtheta = (float)dth;
+        H.g_table = (float)mean;
+        std::memcpy(blob, &H, sizeof H);
+        uint32_t *K = reinterpret_cast<uint32_t *>(blob + H.off_k);
+        float *dl = reinterpret_cast<float *>(blob + H.off_dl);
+        float *ri = reinterpret_cast<float *>(blob + H.off_ri);
+        float *om = reinterpret_cast<float *>(blob + H.off_omu);
+        float *pth = reinterpret_cast<float *>(blob + H.off_pth);
+        const double q = 8388608.0;   // 2^23 uniform indices; u(k) = (k + 1/2) / q
+        for (int i = 0; i <= n; ++i) {
+            double kk = (i == n) ? q : std::ceil(cdf[i] * q - 0.5);
+            if (kk < 0.0) kk = 0.0;
+            if (kk > q) kk = q;
+            K[i] = (uint32_t)kk;
+            if (i < n) {
+                // K[i] is the first index whose uniform reaches cdf_i
+                const double u = (kk + 0.5) / q;
+                if (!(u >= cdf[i]) || (kk > 0.0 && !((kk - 0.5) / q < cdf[i]))) return MC_ERR_NUMERIC;
+                dl[i] = (float)(u - cdf[i]);
+                const double w = cdf[i + 1] - cdf[i];
+                ri[i] = w > 0.0 ? (float)(1.0 / w) : 0.0f;
+                pth[i] = (float)(w / dth);
+            }
+        }
+        for (int i = 0; i < n_theta; ++i) {
+            const double sh = std::sin(0.5 * i * dth);
+            om[i] = (float)(2.0 * sh * sh);
+        }
+        om[0] = 0.0f;
+        om[n] = 2.0f;
+    }
     return MC_OK;
 }

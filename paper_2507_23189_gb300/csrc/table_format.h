@@ -56,3 +56,67 @@ static inline size_t mc_table_layout(int n_bins, mc_table_header *h)
     }
     return off;
 }
+
+// The paper's own sampling table (Sec. 3.1.2): the cumulative distribution
+// of the scattering angle at n_theta equally spaced angles theta_i =
+// i pi / n_int (n_int = n_theta - 1), searched by bisection. Layout:
+//   [0, 64)   mc_paper_header
+//   off_k     uint32 k[n_int + 1]  k[i] = smallest 23-bit uniform index q with
+//                                  (q + 1/2) 2^-23 >= cdf_i (k[n_int] = 2^23),
+//                                  so the search compares integers exactly
+//   off_dl    float dl[n_int]      (k[i] + 1/2) 2^-23 - cdf_i, in [0, 2^-23)
+//   off_ri    float ri[n_int]      1 / (cdf_{i+1} - cdf_i)  (0 if empty)
+//   off_omu   float omu[n_theta]   1 - cos(theta_i)
+//   off_pth   float pth[n_int]     (cdf_{i+1} - cdf_i) / dtheta, per radian
+#define MC_PAPER_MAGIC 0x504D434Du  // "MCMP"
+#define MC_PAPER_VERSION 1u
+
+struct mc_paper_header {
+    uint32_t magic;
+    uint32_t version;
+    int32_t n_theta;
+    int32_t n_int;
+    uint32_t off_k, off_dl, off_ri, off_omu, off_pth;
+    uint32_t total_bytes;
+    float dtheta;
+    int32_t top;            // largest power of two <= n_int - 1
+    float g_table;          // mean cosine of the sampled distribution
+    float pad[3];
+};
+static_assert(sizeof(mc_paper_header) == 64, "header must be 64 bytes");
+
+static inline size_t mc_paper_layout(int n_theta, mc_paper_header *h)
+{
+    if (n_theta < 16 || n_theta > 16384) return 0;
+    const int n = n_theta - 1;
+    size_t off = sizeof(mc_paper_header);
+    const size_t k = off;
+    off += mc_pad16(sizeof(uint32_t) * (size_t)(n + 1));
+    const size_t dl = off;
+    off += mc_pad16(sizeof(float) * (size_t)n);
+    const size_t ri = off;
+    off += mc_pad16(sizeof(float) * (size_t)n);
+    const size_t om = off;
+    off += mc_pad16(sizeof(float) * (size_t)n_theta);
+    const size_t pth = off;
+    off += mc_pad16(sizeof(float) * (size_t)n);
+    if (h) {
+        int top = 1;
+        while (2 * top <= n - 1) top *= 2;
+        h->magic = MC_PAPER_MAGIC;
+        h->version = MC_PAPER_VERSION;
+        h->n_theta = n_theta;
+        h->n_int = n;
+        h->off_k = (uint32_t)k;
+        h->off_dl = (uint32_t)dl;
+        h->off_ri = (uint32_t)ri;
+        h->off_omu = (uint32_t)om;
+        h->off_pth = (uint32_t)pth;
+        h->total_bytes = (uint32_t)off;
+        h->dtheta = 0.0f;
+        h->top = top;
+        h->g_table = 0.0f;
+        for (int i = 0; i < 3; ++i) h->pad[i] = 0.0f;
+    }
+    return off;
+}

@@ -143,22 +143,60 @@ __device__ __forceinline__ void trace_write(const CommonArgs &C, unsigned long l
     t[9] = pix; t[10] = nb; t[11] = rb;
 }
 
+// Shared memory of a walk CTA:
+//   [table blob][image band][radial][totals][mbarrier][item][pool]
+// and the views of the staged table: omu / pdf / guide of the inverse-CDF
+// table, or, for the paper's table, omu (node 1 - cos theta), pdf (density
+// per radian), pk / pdl / pri (search thresholds and interpolation aids).
+struct Smem {
+    unsigned char *table;
+    unsigned long long *img, *rad, *tot, *bar, *item, *pool;
+    int npix;                 // privatised image pixels (band rows x nx)
+    const float *omu, *pdf;
+    const uint16_t *guide;
+    const uint32_t *pk;
+    const float *pdl, *pri;
+    int pn, ptop;             // intervals of the paper table, search start
+    float pinv;               // 1 / intervals
+};
+
 // ---------------------------------------------------------------- physics
 // Shared by the forward walk and the adjoint replay so both compute the very
 // same single-precision values.
 
 // Phase density per steradian for the camera direction cosine d_y.
+// Largest i in [0, n-1] with a[i] <= v for nondecreasing a: binary lifting
+// from the largest power of two top <= n-1 (a fixed, warp-uniform number of
+// steps, no divergent loop).
+template <class T>
+__device__ __forceinline__ int lift_search(const T *a, int n, int top, T v)
+{
+    int i = 0;
+    for (int step = top; step > 0; step >>= 1) {
+        const int t = i + step;
+        if (t < n && a[t] <= v) i = t;
+    }
+    return i;
+}
+
 template <int PHASE>
-__device__ __forceinline__ float camera_psr(const MediumArgs &M, const CommonArgs &C, const float *omu,
-                                            const float *pdf, const uint16_t *guide, float dy, int &nb)
+__device__ __forceinline__ float camera_psr(const MediumArgs &M, const CommonArgs &C, const Smem &S,
+                                            float dy, int &nb)
 {
     if (PHASE == MC_PHASE_HG) {
         const float t = fmaf(M.hg_two_g, 1.0f - dy, M.hg_a2);
         nb = -1;
         return M.hg_K / (t * sqrtf(t));
     }
-    nb = table_bin(omu, guide, C.n_bins, dy);
-    return pdf[nb] * INV_2PI;
+    if (PHASE == MC_PHASE_PAPER) {
+        // uniform in theta on each interval: density per radian / sin(theta)
+        const float om = 1.0f - fminf(fmaxf(dy, -1.0f), 1.0f);
+        nb = lift_search(S.omu, S.pn, S.ptop, om);
+        const float st2 = om * (2.0f - om);
+        return st2 > 0.0f ? S.pdf[nb] * rsqrtf(st2) * INV_2PI : 0.0f;
+    }
+    nb = table_bin(S.omu, S.guide, C.n_bins, dy);
+    return S.pdf[nb] * INV_2PI;
 }
 
 // Camera pixel of a collision at (rx, rz).
@@ -171,17 +209,28 @@ __device__ __forceinline__ int camera_pixel(const CommonArgs &C, float rx, float
 
 // Polar angle as 1 - cos(theta) (accurate near the forward peak).
 template <int PHASE>
-__device__ __forceinline__ float sample_omu(const MediumArgs &M, const CommonArgs &C, const float *omu,
+__device__ __forceinline__ float sample_omu(const MediumArgs &M, const CommonArgs &C, const Smem &S,
                                             float u1)
 {
     if (PHASE == MC_PHASE_HG) {
         const float D = fmaf(M.hg_two_g, u1, M.hg_one_m_g);
         return M.hg_A * (1.0f - u1) * fmaf(M.hg_g, u1, 1.0f) / (D * D);
     }
+    if (PHASE == MC_PHASE_PAPER) {
+        // bisection of the cumulative distribution on the uniform's integer
+        // index q (u1 = (q + 1/2) 2^-23 exactly), then linear interpolation
+        // in theta: u1 - cdf_i = (q - k_i) 2^-23 + dl_i, fraction = that / w_i
+        const int q = __float2int_rd(u1 * 8388608.0f);
+        const int i = lift_search(S.pk, S.pn, S.ptop, (uint32_t)q);
+        const float fr = fminf(fmaxf(fmaf((float)(q - (int)S.pk[i]), 1.1920928955078125e-7f, S.pdl[i]) *
+                                         S.pri[i], 0.0f), 1.0f);
+        const float sh = sinpif(0.5f * ((float)i + fr) * S.pinv);   // sin(theta / 2)
+        return 2.0f * sh * sh;
+    }
     const float tt = u1 * (float)C.n_bins;
     const int i = (int)tt;
     const float f = tt - (float)i;
-    const float o0 = omu[i], o1 = omu[i + 1];
+    const float o0 = S.omu[i], o1 = S.omu[i + 1];
     return fmaf(f, o1 - o0, o0);
 }
 
@@ -204,21 +253,11 @@ __device__ __forceinline__ void rotate(float &dx, float &dy, float &dz, float om
     dx = nx * inv; dy = ny * inv; dz = nz * inv;
 }
 
-// Shared memory of a walk CTA:
-//   [table blob][image band][radial][totals][mbarrier][item][pool]
-struct Smem {
-    unsigned char *table;
-    unsigned long long *img, *rad, *tot, *bar, *item, *pool;
-    int npix;                 // privatised image pixels (band rows x nx)
-    const float *omu, *pdf;
-    const uint16_t *guide;
-};
-
 template <int PHASE, bool SMEM_IMAGE>
 __device__ __forceinline__ Smem carve(unsigned char *smem, const CommonArgs &C)
 {
     Smem S;
-    const uint32_t tb = (PHASE == MC_PHASE_TABLE) ? C.table_bytes : 0u;
+    const uint32_t tb = (PHASE != MC_PHASE_HG) ? C.table_bytes : 0u;
     S.table = smem;
     S.npix = SMEM_IMAGE ? C.nx * C.band_rows : 0;
     S.img = reinterpret_cast<unsigned long long *>(smem + tb);
@@ -227,8 +266,11 @@ __device__ __forceinline__ Smem carve(unsigned char *smem, const CommonArgs &C)
     S.bar = S.tot + MC_N_TOTALS;
     S.item = S.bar + 1;
     S.pool = S.item + 1;
-    S.omu = S.pdf = nullptr;
+    S.omu = S.pdf = S.pdl = S.pri = nullptr;
     S.guide = nullptr;
+    S.pk = nullptr;
+    S.pn = S.ptop = 0;
+    S.pinv = 0.0f;
     return S;
 }
 
@@ -239,8 +281,25 @@ __device__ __forceinline__ void zero_tallies(const Smem &S, const CommonArgs &C)
 
 // Table pointers into the staged blob; false (and the error flag) if its
 // header does not describe the expected table.
+template <int PHASE>
 __device__ __forceinline__ bool bind_table(Smem &S, const CommonArgs &C)
 {
+    if (PHASE == MC_PHASE_PAPER) {
+        const mc_paper_header *h = reinterpret_cast<const mc_paper_header *>(S.table);
+        if (h->magic != MC_PAPER_MAGIC || h->n_theta != C.n_bins || h->total_bytes != C.table_bytes) {
+            if (threadIdx.x == 0) atomicOr(C.error, MC_EFLAG_TABLE);
+            return false;
+        }
+        S.pk = reinterpret_cast<const uint32_t *>(S.table + h->off_k);
+        S.pdl = reinterpret_cast<const float *>(S.table + h->off_dl);
+        S.pri = reinterpret_cast<const float *>(S.table + h->off_ri);
+        S.omu = reinterpret_cast<const float *>(S.table + h->off_omu);
+        S.pdf = reinterpret_cast<const float *>(S.table + h->off_pth);
+        S.pn = h->n_int;
+        S.ptop = h->top;
+        S.pinv = 1.0f / (float)h->n_int;
+        return true;
+    }
     const mc_table_header *h = reinterpret_cast<const mc_table_header *>(S.table);
     if (h->magic != MC_TABLE_MAGIC || h->n_bins != C.n_bins || h->total_bytes != C.table_bytes) {
         if (threadIdx.x == 0) atomicOr(C.error, MC_EFLAG_TABLE);
@@ -304,8 +363,6 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
     unsigned long long pool_next = 0, pool_end = 0;  // warp-uniform
-    const float *omu = S.omu, *pdf = S.pdf;
-    const uint16_t *guide = S.guide;
     unsigned long long *s_img = S.img, *s_rad = S.rad, *s_tot = S.tot;
 
     // photon state
@@ -432,7 +489,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
 
         // camera: next-event estimate toward +y
         int nb, ix, iz;
-        const float psr = camera_psr<PHASE>(M, C, omu, pdf, guide, dy, nb);
+        const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
         const float nee = w * psr * expf(-M.mu_ext * (C.hy - ry));
         const int pix = camera_pixel(C, rx, rz, ix, iz);
         const float vf = nee * C.img_scale;
@@ -451,7 +508,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
             status = 5;
             alive = false;
         } else {
-            rotate(dx, dy, dz, sample_omu<PHASE>(M, C, omu, u1), u2);
+            rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
             // weight threshold / roulette (Sec. 3.1.3)
             if (w < C.rr_thr) {
                 if (u3 < C.rr_surv) {
@@ -486,9 +543,9 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
     Smem S = carve<PHASE, SMEM_IMAGE>(smem, A.c);
     zero_tallies(S, A.c);
     if (threadIdx.x == 0) mbar_init(S.bar);
-    if (PHASE == MC_PHASE_TABLE) {
+    if (PHASE != MC_PHASE_HG) {
         if (!stage_bulk(S.table, A.m.table, A.c.table_bytes, S.bar, 0u, A.c.error)) return;
-        if (!bind_table(S, A.c)) return;
+        if (!bind_table<PHASE>(S, A.c)) return;
     } else {
         __syncthreads();
     }
@@ -534,11 +591,11 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ Bat
                 flush<SMEM_IMAGE>(B.c, B.m[cur], S, T);
                 zero_tallies(S, B.c);
             }
-            if (PHASE == MC_PHASE_TABLE) {
+            if (PHASE != MC_PHASE_HG) {
                 if (!stage_bulk(S.table, B.m[inst].table, B.c.table_bytes, S.bar, parity, B.c.error))
                     return;
                 parity ^= 1u;
-                if (!bind_table(S, B.c)) return;
+                if (!bind_table<PHASE>(S, B.c)) return;
             }
             cur = inst;
         }
@@ -644,10 +701,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
     float *rows = reinterpret_cast<float *>(s_bar + 2);    // [nw][B]
     for (int i = threadIdx.x; i < nw * B; i += B) rows[i] = 0.0f;
     if (threadIdx.x == 0) mbar_init(s_bar);
-    Smem S;
+    Smem S = carve<MC_PHASE_HG, false>(smem, C);
     S.table = smem;
-    S.omu = S.pdf = nullptr;
-    S.guide = nullptr;
     if (PHASE == MC_PHASE_TABLE) {
         if (PHASEW) {
             // shared memory holds the private accumulators; the table is read
@@ -656,13 +711,11 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
         } else if (!stage_bulk(smem, M.table, tb, s_bar, 0u, C.error)) {
             return;
         }
-        if (!bind_table(S, C)) return;
+        if (!bind_table<PHASE>(S, C)) return;
     }
     if (PHASEW)
         for (int k = threadIdx.x; k < nw; k += B) s_z[k] = A.z[k];
     __syncthreads();
-    const float *omu = S.omu, *pdf = S.pdf;
-    const uint16_t *guide = S.guide;
     const float c_s = A.c_s;   // 1/mu_s - 1/mu_ext
 
     const unsigned lanemask_lt = (1u << lane) - 1u;
@@ -745,7 +798,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
             Ssc += M.inv_mu_ext - s;
             w = w * M.albedo;
             int nb, ix, iz;
-            const float psr = camera_psr<PHASE>(M, C, omu, pdf, guide, dy, nb);
+            const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
             const float l = C.hy - ry;
             const float nee = w * psr * expf(-M.mu_ext * l);
             const int pix = camera_pixel(C, rx, rz, ix, iz);
@@ -766,7 +819,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
             if (C.max_scatter && ncoll >= C.max_scatter) {
                 end = true;
             } else {
-                const float om = sample_omu<PHASE>(M, C, omu, u1);
+                const float om = sample_omu<PHASE>(M, C, S, u1);
                 if (PHASEW) {
                     float f;
                     const int k = hat_pair(nw, 1.0f - om, f);
@@ -890,7 +943,7 @@ cudaError_t launch_persistent(Kern kern, const void *args_unused, const LaunchCf
 // Where the image accumulates and how big the CTA is. Sets c.band0/band_rows.
 cudaError_t plan_image(CommonArgs &c, LaunchCfg &cfg, bool *smem_img, size_t *smem)
 {
-    const size_t tb = (c.phase_kind == MC_PHASE_TABLE) ? c.table_bytes : 0;
+    const size_t tb = (c.phase_kind != MC_PHASE_HG) ? c.table_bytes : 0;
     const size_t tail = sizeof(unsigned long long) * (c.n_radial + MC_N_TOTALS + 3);
     const size_t row = sizeof(unsigned long long) * (size_t)c.nx;
     int dev = 0, optin = 0;
@@ -962,17 +1015,21 @@ cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, c
     size_t smem = 0;
     cudaError_t e = plan_image(a.c, cfg, &smem_img, &smem);
     if (e != cudaSuccess) return e;
-    const bool table = a.c.phase_kind == MC_PHASE_TABLE;
-    if (trace) {
-        if (table) return smem_img ? launch_one<0, true, true>(a, cfg, smem, st)
-                                   : launch_one<0, false, true>(a, cfg, smem, st);
-        return smem_img ? launch_one<1, true, true>(a, cfg, smem, st)
-                        : launch_one<1, false, true>(a, cfg, smem, st);
+    switch (a.c.phase_kind * 4 + (smem_img ? 2 : 0) + (trace ? 1 : 0)) {
+    case 0: return launch_one<MC_PHASE_TABLE, false, false>(a, cfg, smem, st);
+    case 1: return launch_one<MC_PHASE_TABLE, false, true>(a, cfg, smem, st);
+    case 2: return launch_one<MC_PHASE_TABLE, true, false>(a, cfg, smem, st);
+    case 3: return launch_one<MC_PHASE_TABLE, true, true>(a, cfg, smem, st);
+    case 4: return launch_one<MC_PHASE_HG, false, false>(a, cfg, smem, st);
+    case 5: return launch_one<MC_PHASE_HG, false, true>(a, cfg, smem, st);
+    case 6: return launch_one<MC_PHASE_HG, true, false>(a, cfg, smem, st);
+    case 7: return launch_one<MC_PHASE_HG, true, true>(a, cfg, smem, st);
+    case 8: return launch_one<MC_PHASE_PAPER, false, false>(a, cfg, smem, st);
+    case 9: return launch_one<MC_PHASE_PAPER, false, true>(a, cfg, smem, st);
+    case 10: return launch_one<MC_PHASE_PAPER, true, false>(a, cfg, smem, st);
+    case 11: return launch_one<MC_PHASE_PAPER, true, true>(a, cfg, smem, st);
+    default: return cudaErrorInvalidValue;
     }
-    if (table) return smem_img ? launch_one<0, true, false>(a, cfg, smem, st)
-                               : launch_one<0, false, false>(a, cfg, smem, st);
-    return smem_img ? launch_one<1, true, false>(a, cfg, smem, st)
-                    : launch_one<1, false, false>(a, cfg, smem, st);
 }
 
 cudaError_t launch_batch(const BatchArgs &a0, const LaunchCfg &cfg0, cudaStream_t st)
@@ -983,9 +1040,15 @@ cudaError_t launch_batch(const BatchArgs &a0, const LaunchCfg &cfg0, cudaStream_
     size_t smem = 0;
     cudaError_t e = plan_image(a.c, cfg, &smem_img, &smem);
     if (e != cudaSuccess) return e;
-    if (a.c.phase_kind == MC_PHASE_TABLE)
-        return smem_img ? launch_batch_one<0, true>(a, cfg, smem, st) : launch_batch_one<0, false>(a, cfg, smem, st);
-    return smem_img ? launch_batch_one<1, true>(a, cfg, smem, st) : launch_batch_one<1, false>(a, cfg, smem, st);
+    switch (a.c.phase_kind * 2 + (smem_img ? 1 : 0)) {
+    case 0: return launch_batch_one<MC_PHASE_TABLE, false>(a, cfg, smem, st);
+    case 1: return launch_batch_one<MC_PHASE_TABLE, true>(a, cfg, smem, st);
+    case 2: return launch_batch_one<MC_PHASE_HG, false>(a, cfg, smem, st);
+    case 3: return launch_batch_one<MC_PHASE_HG, true>(a, cfg, smem, st);
+    case 4: return launch_batch_one<MC_PHASE_PAPER, false>(a, cfg, smem, st);
+    case 5: return launch_batch_one<MC_PHASE_PAPER, true>(a, cfg, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 int adjoint_max_grid()
@@ -1029,7 +1092,7 @@ cudaError_t launch_adjoint_one(const AdjArgs &a, int rows, double *out, cudaStre
 
 cudaError_t launch_adjoint(const AdjArgs &a, int rows, double *out, cudaStream_t st)
 {
-    if (rows < 1) return cudaErrorInvalidValue;
+    if (rows < 1 || a.c.phase_kind == MC_PHASE_PAPER) return cudaErrorInvalidValue;
     if (a.c.phase_kind == MC_PHASE_TABLE)
         return a.n_w ? launch_adjoint_one<0, true>(a, rows, out, st) : launch_adjoint_one<0, false>(a, rows, out, st);
     if (a.n_w) return cudaErrorInvalidValue;

@@ -68,6 +68,34 @@ class PhaseTable:
         return self._dev[key]
 
 
+class PaperTable:
+    """The paper's own sampling table (Sec. 3.1.2, mie_paper_table_build):
+    the Mie phase function at n_theta equally spaced angles, its cumulative
+    distribution, sampled by bisection; with a cached device copy."""
+
+    def __init__(self, diameter_um=5.0, n_particle=1.59 + 0j, n_medium=1.33, wavelength_nm=532.0,
+                 n_theta=3000):
+        L = N.lib()
+        n_particle = complex(n_particle)
+        p = N.MieParams(diameter_um, n_particle.real, n_particle.imag, n_medium, wavelength_nm, 0)
+        info = N.MieInfo()
+        nbytes = L.mc_paper_table_bytes(n_theta)
+        if nbytes == 0:
+            raise N.McError("mc_paper_table_bytes", -1)
+        self.blob = np.zeros(nbytes, dtype=np.uint8)
+        self.cdf64 = np.zeros(n_theta)
+        N.check("mie_paper_table_build", L.mie_paper_table_build(
+            C.byref(p), n_theta, C.byref(info), self.blob.ctypes.data_as(C.c_void_p),
+            self.cdf64.ctypes.data_as(C.POINTER(C.c_double))))
+        self.params = dict(diameter_um=diameter_um, n_particle=n_particle, n_medium=n_medium,
+                           wavelength_nm=wavelength_nm, n_theta=n_theta)
+        self.info = info.as_dict()
+        self.n_bins = n_theta        # the medium's n_bins field carries n_theta
+        self._dev = {}
+
+    device_blob = PhaseTable.device_blob
+
+
 # -------------------------------------------------------------------- medium
 
 
@@ -75,7 +103,7 @@ class PhaseTable:
 class Medium:
     mu_s: float
     mu_a: float = 0.0
-    phase: str = "table"   # "table" (Mie inverse CDF) or "hg"
+    phase: str = "table"   # "table" (Mie inverse CDF), "hg" or "paper" (PaperTable)
     hg_g: float = 0.0
     table: PhaseTable = None
 
@@ -108,7 +136,15 @@ class Medium:
             m.phase_kind = N.PHASE_HG
             m.hg_g = self.hg_g
             return m, None
-        raise ValueError("phase must be 'table' or 'hg'")
+        if self.phase == "paper":
+            if not isinstance(self.table, PaperTable):
+                raise ValueError("phase 'paper' needs a PaperTable")
+            m.phase_kind = N.PHASE_PAPER
+            blob = self.table.device_blob(device)
+            m.d_table = blob.data_ptr()
+            m.n_bins = self.table.n_bins
+            return m, blob
+        raise ValueError("phase must be 'table', 'hg' or 'paper'")
 
 
 @dataclass
@@ -364,8 +400,9 @@ def run_host(medium, geometry, camera, n_photons, d_work, seed=1, stream=None, i
     m = N.Medium()
     m.mu_s, m.mu_a = medium.mu_s, medium.mu_a
     table_ptr = None
-    if medium.phase == "table":
-        m.phase_kind, m.n_bins = N.PHASE_TABLE, medium.table.n_bins
+    if medium.phase in ("table", "paper"):
+        m.phase_kind = N.PHASE_TABLE if medium.phase == "table" else N.PHASE_PAPER
+        m.n_bins = medium.table.n_bins
         blob = medium.table.blob if table_host is None else table_host
         if blob.nbytes != medium.table.blob.nbytes:
             raise ValueError("table_host has the wrong size")
@@ -388,9 +425,36 @@ def run_host(medium, geometry, camera, n_photons, d_work, seed=1, stream=None, i
 
 def host_workspace_bytes(medium, camera):
     m = N.Medium()
-    m.phase_kind = N.PHASE_TABLE if medium.phase == "table" else N.PHASE_HG
-    m.n_bins = medium.table.n_bins if medium.phase == "table" else 0
+    m.phase_kind = {"table": N.PHASE_TABLE, "hg": N.PHASE_HG, "paper": N.PHASE_PAPER}[medium.phase]
+    m.n_bins = medium.table.n_bins if medium.phase != "hg" else 0
     return N.lib().mc_host_workspace_bytes(C.byref(m), C.byref(camera.as_c()))
+
+
+def image_metrics(ref, a, b=None, n_r=32, stream=None):
+    """Sec. 3.1.4 / Tables 3-4 comparison of device int64 images [nz, nx]
+    (mc_image_metrics). Returns a float64 numpy array: a vs ref (RMSE, r,
+    zone RMSE x3, profile r), the same for b, the share of rings where a is
+    closer than b, then the radial profiles of ref, a, b."""
+    torch = _torch()
+    L = N.lib()
+    nz, nx = ref.shape
+    for t in (a, b):
+        if t is not None and tuple(t.shape) != (nz, nx):
+            raise ValueError("images differ in shape")
+    imgs = [t.contiguous() if t is not None else None for t in (ref, a, b)]
+    for t in imgs:
+        if t is not None and (t.dtype != torch.int64 or not t.is_cuda):
+            raise ValueError("images must be int64 CUDA tensors")
+    n_out = L.mc_metrics_out_len(n_r)
+    if n_out == 0:
+        raise ValueError("n_r out of range")
+    out = torch.empty(n_out, dtype=torch.float64, device=ref.device)
+    work = torch.empty(L.mc_metrics_workspace_bytes(n_r), dtype=torch.uint8, device=ref.device)
+    vp = C.c_void_p
+    N.check("mc_image_metrics", L.mc_image_metrics(
+        vp(imgs[0].data_ptr()), vp(imgs[1].data_ptr()), vp(imgs[2].data_ptr()) if b is not None else None,
+        nx, nz, n_r, vp(out.data_ptr()), vp(work.data_ptr()), work.numel(), _stream_handle(stream)))
+    return out.cpu().numpy()
 
 
 def philox(ctr, seed, stream=None):

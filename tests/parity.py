@@ -18,15 +18,19 @@ import numpy as np
 TOL = 1e-5
 
 
-def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL):
+def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL, nee_slope=None):
     """g: decode_trace() dict of the GPU trace; o: oracle trace array
-    [n, ev, 13]. Returns dict(n, matched, flips, bad, worst...)."""
+    [n, ev, 13]. nee_slope(mu_c): |d log p_sr / d mu_c| of a camera density
+    that varies continuously with the direction (the paper's table); the
+    camera term then also carries the direction difference of the previous
+    event times that slope. Returns dict(n, matched, flips, bad, worst...)."""
     n, ev = o.shape[0], o.shape[1]
     st_o = o[..., 0].astype(int)
     worst = dict(pos=0.0, dir=0.0, w=0.0, nee=0.0)
     bad, flips, checked_events = [], 0, 0
     for p in range(n):
         ok = True
+        muc, ddir_prev = 0.0, 0.0     # direction before the first collision is +x
         for e in range(ev):
             so, sg = st_o[p, e], int(g["status"][p, e])
             if so < 0 and sg < 0:
@@ -51,6 +55,8 @@ def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL):
             # the camera term depends on r_y through exp(-mu_ext (ly/2 - r_y))
             dnee = dnee_abs / rec[8] if rec[8] else dnee_abs
             nee_tol = tol + mu_ext * dpos
+            if nee_slope is not None:
+                nee_tol += nee_slope(muc) * ddir_prev
             worst["pos"] = max(worst["pos"], dpos / lx)
             worst["dir"] = max(worst["dir"], ddir)
             worst["w"] = max(worst["w"], dw)
@@ -63,6 +69,7 @@ def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL):
                 break
             if so != 0:
                 break
+            muc, ddir_prev = float(rec[5]), ddir
         if not ok:
             bad.append(p)
     return dict(n=n, matched=n - len(bad), flips=flips, bad=bad[:20], worst=worst,

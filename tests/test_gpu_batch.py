@@ -15,7 +15,7 @@ def _media(gpu, spec, phase="table"):
     out = []
     for d, tau, _ in spec:
         if d not in tables:
-            tables[d] = gpu.PhaseTable(diameter_um=d)
+            tables[d] = gpu.PaperTable(diameter_um=d) if phase == "paper" else gpu.PhaseTable(diameter_um=d)
         t = tables[d]
         out.append(gpu.Medium.from_optical_depth(t, tau, LX, phase=phase))
     return out
@@ -33,7 +33,7 @@ SPEC = [(5.0, 5.0, 300_000), (1.0, 0.5, 40_000), (10.0, 20.0, 120_000), (2.5, 2.
         (5.0, 12.0, 250_000), (7.0, 8.0, 0), (3.0, 1.0, 77_777)]
 
 
-@pytest.mark.parametrize("phase", ["table", "hg"])
+@pytest.mark.parametrize("phase", ["table", "hg", "paper"])
 @pytest.mark.parametrize("item_photons", [0, 4096, 65_536])
 def test_batch_equals_plain_runs(gpu, phase, item_photons):
     media = _media(gpu, SPEC, phase)

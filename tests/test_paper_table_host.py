@@ -1,0 +1,60 @@
+"""The engine's paper-faithful table (mie_paper_table_build, host code; no
+GPU needed): its cumulative distribution against the oracle's, and the
+integer search thresholds against a double-precision search."""
+import numpy as np
+import pytest
+
+M_PS = complex(1.59 / 1.33, 0.0)
+
+
+@pytest.fixture(scope="module")
+def eng_paper():
+    from paper_2507_23189_gb300 import build
+    build.build()
+    import paper_2507_23189_gb300 as g
+    return g.PaperTable(n_theta=3000)
+
+
+def _header(blob):
+    h = np.frombuffer(blob[:64].tobytes(), dtype=np.uint32)
+    return dict(magic=int(h[0]), n_theta=int(h[2]), n_int=int(h[3]), off_k=int(h[4]), off_dl=int(h[5]),
+                off_ri=int(h[6]), off_omu=int(h[7]), off_pth=int(h[8]), total=int(h[9]),
+                top=int(np.frombuffer(blob[44:48].tobytes(), dtype=np.int32)[0]))
+
+
+def test_cdf_matches_oracle(eng_paper, oracle_mod):
+    x = oracle_mod.size_parameter(5.0, 1.33, 532.0)
+    o = oracle_mod.paper_cdf(oracle_mod.PHASE_MIE, M_PS, x, n_theta=3000)
+    np.testing.assert_allclose(eng_paper.cdf64, o["cdf"], rtol=0, atol=1e-12)
+    assert eng_paper.info["g_table"] == pytest.approx(
+        np.sum(np.diff(o["cdf"]) * np.diff(np.sin(o["theta"])) / (np.pi / 2999)), abs=1e-12)
+
+
+def test_integer_thresholds_reproduce_the_double_search(eng_paper):
+    b = eng_paper.blob
+    h = _header(b)
+    n = h["n_int"]
+    assert h["magic"] == 0x504D434D and h["n_theta"] == 3000 and h["total"] == b.size
+    assert h["top"] == 2048
+    K = np.frombuffer(b[h["off_k"]:h["off_k"] + 4 * (n + 1)].tobytes(), dtype=np.uint32).astype(np.int64)
+    dl = np.frombuffer(b[h["off_dl"]:h["off_dl"] + 4 * n].tobytes(), dtype=np.float32).astype(np.float64)
+    ri = np.frombuffer(b[h["off_ri"]:h["off_ri"] + 4 * n].tobytes(), dtype=np.float32).astype(np.float64)
+    cdf = eng_paper.cdf64
+    assert K[0] == 0 and K[n] == 1 << 23 and np.all(np.diff(K) >= 0)
+    q = np.concatenate([np.arange(0, 1 << 23, 997), [0, (1 << 23) - 1], K[:n], np.maximum(K[:n] - 1, 0)])
+    u = (q + 0.5) * 2.0 ** -23
+    want = np.searchsorted(cdf[:n], u, side="right") - 1      # largest i with cdf[i] <= u
+    got = np.searchsorted(K[:n], q, side="right") - 1         # largest i with K[i] <= q
+    np.testing.assert_array_equal(got, want)
+    # the interpolation aids give the fraction (u - cdf_i) / (cdf_{i+1} - cdf_i)
+    i = got
+    frac = ((q - K[i]) * 2.0 ** -23 + dl[i]) * ri[i]
+    exact = (u - cdf[i]) / (cdf[i + 1] - cdf[i])
+    np.testing.assert_allclose(frac, exact, rtol=0, atol=2e-6)
+
+
+def test_bad_sizes_rejected(eng_paper):
+    import paper_2507_23189_gb300 as g
+    for n in (0, 15, 16385):
+        with pytest.raises(Exception):
+            g.PaperTable(n_theta=n)
