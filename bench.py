@@ -15,6 +15,7 @@ collective on the data path); rank 0 prints one JSON line.
 """
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -223,6 +224,59 @@ def batched_comparison(E, dev, steps, warmup, flush):
                         "64 sequential launches"}
 
 
+def paper_comparison(E, dev, steps, flush):
+    """The paper's own set-up (Sec. 4.1, 4.3, 5.2): 30 x 10 x 45 mm cuvette with
+    the beam through the 30 mm side, 2.5 mm beam, tau = 8 over 30 mm, plain
+    cut at w < 0.001, 1e8 photons, 60 x 90 image: the paper's 3000-angle CDF
+    sampled by bisection against the 4096-level equal-probability table, same
+    photons; then the Sec. 3.1.4 / Tables 3-4 comparison of the two images and
+    of H-G (g from Mie) against the table image."""
+    import torch
+    table = E.PhaseTable(5.0, 1.59, 1.33, 532.0, 4096)
+    paper = E.PaperTable(5.0, 1.59, 1.33, 532.0, 3000)
+    lx, tau, n = 30.0, 8.0, 100_000_000
+    mu_s = tau / lx * table.info["qsca"] / table.info["qext"]
+    cam = E.Camera(60, 90, 64, math.hypot(5.0, 22.5))
+    geo = E.Geometry(lx, 10.0, 45.0, 1.25)
+    kw = dict(rr_threshold=1e-3, rr_survival=0.0)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    imgs = {}
+    for name, med in (("table", E.Medium(mu_s, 0.0, "table", 0.0, table)),
+                      ("paper", E.Medium(mu_s, 0.0, "paper", 0.0, paper)),
+                      ("hg", E.Medium(mu_s, 0.0, "hg", table.info["g"], table))):
+        eng = E.Engine(cam, geo, dev)
+        for _ in range(3):
+            eng.run(med, n, seed=1, stream=stream, **kw)
+        torch.cuda.synchronize(dev)
+        tot = 0.0
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            eng.run(med, n, seed=1, stream=stream, **kw)
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        eng.check()
+        ms = tot / steps
+        steps_run = int(eng.totals[7].item())
+        out[name] = {"ms": ms, "photons_per_s": n / (ms * 1e-3), "photon_steps_per_s": steps_run / (ms * 1e-3)}
+        imgs[name] = eng.image.clone()
+    m = E.image_metrics(imgs["table"], imgs["paper"], imgs["hg"], n_r=32)
+    out["paper_vs_table_speed"] = out["table"]["ms"] / out["paper"]["ms"]
+    # context only: the paper reports 4.56e6 photons/s on an RTX 3050 (Sec. 3.1.3)
+    out["paper_reported_photons_per_s"] = 4.56e6
+    out["metrics_vs_table"] = {
+        "paper": {"rmse": m[0], "r": m[1], "zone_rmse": list(m[2:5]), "radial_r": m[5]},
+        "hg": {"rmse": m[6], "r": m[7], "zone_rmse": list(m[8:11]), "radial_r": m[11]},
+        "paper_closer_rings": m[12]}
+    out["workload"] = ("30x10x45 mm cuvette, beam along the 30 mm side, 2.5 mm beam, 5 um PS in water, "
+                       "tau=8 over 30 mm, w<0.001 cut, 1e8 photons, 60x90 image; 3000-angle CDF + bisection "
+                       "vs 4096-level equal-probability table vs H-G; metrics: min-max normalised, 32 rings")
+    return out
+
+
 def adjoint_comparison(E, dev, steps, flush):
     """Adjoint cost against the forward pass on the tau = 5 Mie cuvette with
     1e7 photons and a 128x128 image: mc_run vs mc_adjoint over the same
@@ -404,6 +458,7 @@ def run_engine(args):
     if not args.no_batched and ws == 1:
         line["batched"] = batched_comparison(E, dev, args.steps, args.warmup, flush)
         line["adjoint"] = adjoint_comparison(E, dev, args.steps, flush)
+        line["paper_mode"] = paper_comparison(E, dev, args.steps, flush)
     if not args.no_peaks:
         from paper_2507_23189_gb300 import peaks
         pk = peaks.measure(dev)
