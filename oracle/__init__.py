@@ -44,6 +44,9 @@ def lib():
         L.oracle_phase_table_weighted.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
                                                   C.c_double, C.c_int, dp, C.c_int, C.c_int, dp, dp,
                                                   dp, dp]
+        L.oracle_phase_table_mixture.restype = C.c_int
+        L.oracle_phase_table_mixture.argtypes = [C.c_int, C.POINTER(C.c_int), dp, dp, dp, dp, dp, C.c_int,
+                                                 C.c_int, dp, dp, dp, dp]
         L.oracle_paper_cdf.restype = C.c_int
         L.oracle_paper_cdf.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                        C.c_int, dp]
@@ -91,6 +94,10 @@ class WalkCfg(C.Structure):
         ("max_events", C.c_uint32), ("max_scatter", C.c_uint32),
         ("cone_cos", C.c_double),
         ("n_threads", C.c_int),
+        ("density", C.POINTER(C.c_double)),
+        ("gx", C.c_int), ("gy", C.c_int), ("gz", C.c_int),
+        ("k_ext", C.c_double), ("k_sca", C.c_double),
+        ("bx", C.c_int), ("by", C.c_int), ("bz", C.c_int),
     ]
 
 
@@ -199,6 +206,29 @@ def phase_table_weighted(m, x, w, n_bins=4096, n_fine=1 << 18):
                 n_fine=int(diag[3]))
 
 
+def phase_table_mixture(components, weights, n_bins=4096, n_fine=1 << 18):
+    """Table of a phase-function mixture. components: list of ("mie", m, x)
+    or ("hg", g); weights: each component's share of the scattering
+    coefficient. Returns the dict of phase_table."""
+    n = len(components)
+    kind = (C.c_int * n)()
+    mre, mim, xs, gs, w = (np.zeros(n) for _ in range(5))
+    for i, comp in enumerate(components):
+        if comp[0] == "mie":
+            kind[i] = PHASE_MIE
+            mre[i], mim[i], xs[i] = comp[1].real, comp[1].imag, comp[2]
+        else:
+            kind[i] = PHASE_HG
+            gs[i] = comp[1]
+        w[i] = weights[i]
+    icdf, omu, pdf, diag = np.zeros(n_bins + 1), np.zeros(n_bins + 1), np.zeros(n_bins), np.zeros(4)
+    if lib().oracle_phase_table_mixture(n, kind, _dp(mre), _dp(mim), _dp(xs), _dp(gs), _dp(w), n_bins,
+                                        n_fine, _dp(icdf), _dp(omu), _dp(pdf), _dp(diag)):
+        raise ValueError("oracle_phase_table_mixture: bad arguments")
+    return dict(icdf=icdf, omu=omu, pdf=pdf, norm=diag[0], g_quad=diag[1], mean=diag[2],
+                n_fine=int(diag[3]))
+
+
 def paper_cdf(kind, m=1.0 + 0j, x=1.0, hg_g=0.0, n_theta=3000):
     """The paper's sampling table (Sec. 3.1.2): cumulative probability at the
     angles theta_i = i pi / (n_theta - 1). Returns dict(cdf, theta)."""
@@ -260,7 +290,7 @@ def _walk_cfg(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,
               nx=64, nz=64, n_radial=128, r_max=5.0 * 2 ** 0.5,
               n_photons=1000, photon_offset=0, seed=1,
               rr_threshold=1e-4, rr_survival=0.1, max_events=1_000_000, max_scatter=0,
-              cone_cos=0.0, n_threads=None):
+              cone_cos=0.0, n_threads=None, grid=None):
     cfg = WalkCfg()
     cfg.mu_s, cfg.mu_a = mu_s, mu_a
     keep = []
@@ -288,6 +318,15 @@ def _walk_cfg(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,
     cfg.max_events, cfg.max_scatter = max_events, max_scatter
     cfg.cone_cos = cone_cos
     cfg.n_threads = n_threads if n_threads else (os.cpu_count() or 1)
+    if grid is not None:
+        # dict(density [gz, gy, gx] per mm^3, k_ext, k_sca, block=(bx, by, bz));
+        # mu_a is then a uniform background absorption and mu_s is unused
+        dens = np.ascontiguousarray(grid["density"], dtype=np.float64)
+        keep.append(dens)
+        cfg.density = _dp(dens)
+        cfg.gz, cfg.gy, cfg.gx = dens.shape
+        cfg.k_ext, cfg.k_sca = grid["k_ext"], grid["k_sca"]
+        cfg.bx, cfg.by, cfg.bz = grid.get("block", (1, 1, 1))
     cfg._keep = keep
     return cfg, keep
 
@@ -297,13 +336,13 @@ def walk(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,
          nx=64, nz=64, n_radial=128, r_max=5.0 * 2 ** 0.5,
          n_photons=1000, photon_offset=0, seed=1,
          rr_threshold=1e-4, rr_survival=0.1, max_events=1_000_000, max_scatter=0,
-         cone_cos=0.0, n_threads=None, n_trace=0, n_trace_events=32):
+         cone_cos=0.0, n_threads=None, n_trace=0, n_trace_events=32, grid=None):
     """Run the double-precision walk; returns a dict of tallies (and trace).
     phase: "mie" (equal-probability table), "hg" or "paper" (the table of
     paper_cdf, sampled by binary search)."""
     cfg, keep = _walk_cfg(mu_s, mu_a, phase, table, hg_g, lx, ly, lz, beam_radius, nx, nz, n_radial,
                           r_max, n_photons, photon_offset, seed, rr_threshold, rr_survival, max_events,
-                          max_scatter, cone_cos, n_threads)
+                          max_scatter, cone_cos, n_threads, grid)
     image = np.zeros(nz * nx)
     image_sq = np.zeros(nz * nx)
     image_hits = np.zeros(nz * nx)

@@ -18,7 +18,9 @@
  *             paper's own 3000-angle cumulative distribution (Sec. 3.1.2).
  *   philox.c  Philox4x32-10 counter-based generator (Salmon et al., SC'11).
  *   walk.c    the photon random walk of Sec. 3.1.3 (Eq. 15, Eq. 16) with a
- *             next-event estimate for the 90-degree side camera (Sec. 4.3).
+ *             next-event estimate for the 90-degree side camera (Sec. 4.3);
+ *             optionally through a voxel density grid by delta tracking
+ *             (the complex media the paper leaves to future work, Sec. 6).
  *
  * Parity status: every function here is pinned by the -m "not gpu" tests
  * (closed forms, invariants, an independent 50-digit evaluation of Eq. 7-8,
@@ -99,6 +101,15 @@ int oracle_phase_table_weighted(int kind, double m_re, double m_im, double x,
                                 int n_fine, double *icdf, double *omu, double *pdf,
                                 double *diag);
 
+/* Table of a mixture of n_comp phase functions (kind[i], m[i], x[i] or
+ * hg_g[i]), component i weighted by w[i] >= 0 (its share n_i sigma_sca,i of
+ * the scattering coefficient) after each is normalised (Eq. 10). Outputs
+ * as oracle_phase_table. */
+int oracle_phase_table_mixture(int n_comp, const int *kind, const double *m_re,
+                               const double *m_im, const double *x, const double *hg_g,
+                               const double *w, int n_bins, int n_fine, double *icdf,
+                               double *omu, double *pdf, double *diag);
+
 /* The paper's own sampling table (Sec. 3.1.2): cdf[i], i < n_theta, the
  * cumulative probability of scattering angles up to theta_i = i pi /
  * (n_theta - 1) (trapezoidal rule on (1/2) P(cos theta) sin theta, normalised
@@ -146,6 +157,15 @@ typedef struct {
     uint32_t max_scatter;       /* 0: unlimited; else stop after that many collisions */
     double cone_cos;            /* > 0 enables the ORACLE_T_CONE tally */
     int n_threads;
+    /* heterogeneous medium, delta tracking (density NULL: homogeneous).
+     * density[gz][gy][gx]: particles per mm^3, constant on each voxel of the
+     * cuvette; mu_ext = k_ext n + mu_a, mu_s = k_sca n (mu_s above unused);
+     * majorants constant on cells of bx x by x bz voxels. Traces then record
+     * real collisions and the exit only; max_events counts tentative ones. */
+    const double *density;
+    int gx, gy, gz;
+    double k_ext, k_sca;
+    int bx, by, bz;
 } oracle_walk_cfg;
 
 /* Totals, in weight units (one photon carries weight 1). */

@@ -42,6 +42,8 @@ static double panel_partial(double f0, double f1, double f2, double h, double s)
 static int build_table(int kind, double m_re, double m_im, double x, double hg_g, int n_w,
                        const double *wts, int n_bins, int n_fine, double *icdf, double *omu,
                        double *pdf, double *diag);
+static int invert_density(double *F, const double *mu, int n_fine, int n_bins, double *icdf,
+                          double *omu, double *pdf, double *diag);
 
 int oracle_phase_table(int kind, double m_re, double m_im, double x,
                        double hg_g, int n_bins, int n_fine, double *icdf,
@@ -75,10 +77,7 @@ static int build_table(int kind, double m_re, double m_im, double x, double hg_g
     /* Node j sits at theta_j = pi - j h, so mu increases with j. */
     double *F = malloc((size_t)(n_fine + 1) * sizeof *F);
     double *mu = malloc((size_t)(n_fine + 1) * sizeof *mu);
-    double *cum = malloc((size_t)(n_fine / 2 + 1) * sizeof *cum);
-    double *t_icdf = malloc((size_t)(n_bins + 1) * sizeof *t_icdf);
-    double *t_omu = malloc((size_t)(n_bins + 1) * sizeof *t_omu);
-    if (!F || !mu || !cum || !t_icdf || !t_omu)
+    if (!F || !mu)
         goto fail;
 
     for (int j = 0; j <= n_fine; ++j)
@@ -100,6 +99,25 @@ static int build_table(int kind, double m_re, double m_im, double x, double hg_g
             F[j] *= hw;
         }
     }
+    int rc = invert_density(F, mu, n_fine, n_bins, icdf, omu, pdf, diag);
+    free(F); free(mu);
+    return rc;
+fail:
+    free(F); free(mu);
+    return -1;
+}
+
+/* Steps 2-4 for a density F(theta_j) = (1/2) P(cos theta_j) sin theta_j on the
+ * grid theta_j = pi - j pi / n_fine (mu[j] = cos theta_j). */
+static int invert_density(double *F, const double *mu, int n_fine, int n_bins, double *icdf,
+                          double *omu, double *pdf, double *diag)
+{
+    const double h = M_PI / n_fine;
+    double *cum = malloc((size_t)(n_fine / 2 + 1) * sizeof *cum);
+    double *t_icdf = malloc((size_t)(n_bins + 1) * sizeof *t_icdf);
+    double *t_omu = malloc((size_t)(n_bins + 1) * sizeof *t_omu);
+    if (!cum || !t_icdf || !t_omu)
+        goto fail;
 
     /* Step 2/3: Simpson panels, cumulated from theta = pi. */
     cum[0] = 0.0;
@@ -158,11 +176,71 @@ static int build_table(int kind, double m_re, double m_im, double x, double hg_g
         diag[2] = mean / n_bins;
         diag[3] = (double)n_fine;
     }
-    free(F); free(mu); free(cum); free(t_icdf); free(t_omu);
+    free(cum); free(t_icdf); free(t_omu);
     return 0;
 fail:
-    free(F); free(mu); free(cum); free(t_icdf); free(t_omu);
+    free(cum); free(t_icdf); free(t_omu);
     return -1;
+}
+
+/*
+ * A suspension of several particle kinds (for example the size bins of a
+ * polydisperse sample) scatters with the mixture of their phase functions,
+ * each weighted by its share of the scattering coefficient, n_i sigma_sca,i:
+ * p = sum_i w_i p_i / sum_i w_i with every p_i normalised by Eq. 10. The
+ * components are normalised on the same Simpson grid, summed, and the
+ * mixture is tabulated by the same steps 2-4.
+ */
+int oracle_phase_table_mixture(int n_comp, const int *kind, const double *m_re,
+                               const double *m_im, const double *x, const double *hg_g,
+                               const double *w, int n_bins, int n_fine, double *icdf,
+                               double *omu, double *pdf, double *diag)
+{
+    if (n_comp < 1 || n_bins < 2 || n_fine < 4 || (n_fine & 1))
+        return -1;
+    double wsum = 0.0;
+    for (int i = 0; i < n_comp; ++i) {
+        if (!(w[i] >= 0.0))
+            return -1;
+        if (kind[i] == ORACLE_PHASE_HG && !(hg_g[i] > -1.0 && hg_g[i] < 1.0))
+            return -1;
+        if (kind[i] != ORACLE_PHASE_HG && kind[i] != ORACLE_PHASE_MIE)
+            return -1;
+        wsum += w[i];
+    }
+    if (!(wsum > 0.0))
+        return -1;
+    const double h = M_PI / n_fine;
+    double *F = calloc((size_t)(n_fine + 1), sizeof *F);
+    double *G = malloc((size_t)(n_fine + 1) * sizeof *G);
+    double *mu = malloc((size_t)(n_fine + 1) * sizeof *mu);
+    int rc = -1;
+    if (!F || !G || !mu)
+        goto out;
+    for (int j = 0; j <= n_fine; ++j)
+        mu[j] = cos((double)(n_fine - j) * h);
+    for (int i = 0; i < n_comp; ++i) {
+        if (kind[i] == ORACLE_PHASE_MIE) {
+            if (oracle_mie_phase_raw(m_re[i], m_im[i], x[i], mu, n_fine + 1, G))
+                goto out;
+        } else {
+            for (int j = 0; j <= n_fine; ++j)
+                G[j] = hg_phase(hg_g[i], (double)(n_fine - j) * h);
+        }
+        double Z = 0.0;
+        for (int j = 0; j <= n_fine; ++j)
+            G[j] *= 0.5 * sin((double)(n_fine - j) * h);
+        for (int p = 0; p < n_fine / 2; ++p)
+            Z += h / 3.0 * (G[2 * p] + 4.0 * G[2 * p + 1] + G[2 * p + 2]);
+        if (!(Z > 0.0))
+            goto out;
+        for (int j = 0; j <= n_fine; ++j)
+            F[j] += (w[i] / wsum) * G[j] / Z;
+    }
+    rc = invert_density(F, mu, n_fine, n_bins, icdf, omu, pdf, diag);
+out:
+    free(F); free(G); free(mu);
+    return rc;
 }
 
 /*

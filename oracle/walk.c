@@ -130,7 +130,116 @@ static int cdf_interval(const double *cdf, int n, double u)
     return lo;
 }
 
-static void run_photon(const oracle_walk_cfg *c, uint64_t p, acc_t *A,
+/* ---- heterogeneous medium (delta tracking) ------------------------------
+ * The number density n is piecewise constant on a gx x gy x gz voxel grid
+ * spanning the cuvette; mu_ext = k_ext n + mu_a and mu_s = k_sca n (Eq. 17
+ * per voxel, mu_a a uniform background absorption). Free flights are sampled
+ * by delta (Woodcock) tracking against a majorant that is constant on cells
+ * of bx x by x bz voxels: the flight's optical depth tau = -ln u0 is spent
+ * cell by cell at the cell's majorant; where it runs out, a tentative
+ * collision is real with probability mu_ext / majorant (u3 decides), else
+ * null (the photon goes on in the same direction with the next event's
+ * numbers). A real collision reuses u3 for roulette as u3 * majorant /
+ * mu_ext, uniform on [0, 1) given acceptance. The camera transmittance is
+ * the exact optical depth of the voxel column above the collision. */
+
+/* Voxel of r and mu_ext there; margin: distance to a voxel face. */
+static double grid_mu(const oracle_walk_cfg *c, const double lo[3], const double r[3], int *ix,
+                      int *iy, int *iz, double *margin)
+{
+    const double f[3] = {(r[0] - lo[0]) / c->lx * c->gx, (r[1] - lo[1]) / c->ly * c->gy,
+                         (r[2] - lo[2]) / c->lz * c->gz};
+    const int g[3] = {c->gx, c->gy, c->gz};
+    int v[3];
+    for (int i = 0; i < 3; ++i) {
+        v[i] = (int)floor(f[i]);
+        if (v[i] < 0) v[i] = 0;
+        if (v[i] > g[i] - 1) v[i] = g[i] - 1;
+        *margin = min2(*margin, grid_margin(f[i], g[i]));
+    }
+    *ix = v[0]; *iy = v[1]; *iz = v[2];
+    return c->k_ext * c->density[((size_t)v[2] * c->gy + v[1]) * c->gx + v[0]] + c->mu_a;
+}
+
+/* One tentative flight spending tau. Returns 0 at a tentative collision (r
+ * moved there, *mubar = the cell's majorant) or 1 when the flight reaches a
+ * wall first (r on the wall, *face = its axis). */
+static int delta_flight(const oracle_walk_cfg *c, const double *maj, const double lo[3],
+                        const double hi[3], double r[3], const double d[3], double tau,
+                        double *mubar, int *face, double *margin)
+{
+    const int g[3] = {c->gx, c->gy, c->gz};
+    const int b[3] = {c->bx, c->by, c->bz};
+    const double L[3] = {c->lx, c->ly, c->lz};
+    int m[3], cell[3];
+    for (int i = 0; i < 3; ++i) {
+        m[i] = (g[i] + b[i] - 1) / b[i];
+        double f = (r[i] - lo[i]) / L[i] * g[i] / b[i];
+        cell[i] = (int)floor(f);
+        if (cell[i] < 0) cell[i] = 0;
+        if (cell[i] > m[i] - 1) cell[i] = m[i] - 1;
+        if (d[i] != 0.0)
+            *margin = min2(*margin, grid_margin(f, m[i]));
+    }
+    for (;;) {
+        const double mb = maj[((size_t)cell[2] * m[1] + cell[1]) * m[0] + cell[0]];
+        double t = INFINITY, t2 = INFINITY;
+        int ax = -1;
+        for (int i = 0; i < 3; ++i) {
+            double plane, ti;
+            if (d[i] > 0.0)
+                plane = (cell[i] == m[i] - 1) ? hi[i] : lo[i] + (double)(cell[i] + 1) * b[i] * L[i] / g[i];
+            else if (d[i] < 0.0)
+                plane = (cell[i] == 0) ? lo[i] : lo[i] + (double)cell[i] * b[i] * L[i] / g[i];
+            else
+                continue;
+            ti = (plane - r[i]) / d[i];
+            if (ti < t) {
+                t2 = t;
+                t = ti;
+                ax = i;
+            } else if (ti < t2) {
+                t2 = ti;
+            }
+        }
+        if (mb * t > tau) {
+            *margin = min2(*margin, (mb * t - tau) / tau);
+            const double s = tau / mb;
+            for (int i = 0; i < 3; ++i)
+                r[i] += s * d[i];
+            *mubar = mb;
+            return 0;
+        }
+        if (tau > 0.0)
+            *margin = min2(*margin, (tau - mb * t) / tau);
+        if (isfinite(t2) && t > 0.0)
+            *margin = min2(*margin, (t2 - t) / t);
+        tau -= mb * t;
+        for (int i = 0; i < 3; ++i)
+            r[i] += t * d[i];
+        cell[ax] += d[ax] > 0.0 ? 1 : -1;
+        if (cell[ax] < 0 || cell[ax] >= m[ax]) {
+            r[ax] = d[ax] > 0.0 ? hi[ax] : lo[ax];
+            *face = ax;
+            return 1;
+        }
+    }
+}
+
+/* Optical depth from r (in voxel ix, iy, iz) to the camera face y = +ly/2. */
+static double column_depth(const oracle_walk_cfg *c, const double lo[3], const double hi[3],
+                           const double r[3], int ix, int iy, int iz)
+{
+    const double vy = c->ly / c->gy;
+    const double top = (iy == c->gy - 1) ? hi[1] : lo[1] + (iy + 1) * vy;
+    const size_t row = (size_t)iz * c->gy;
+    double od = (c->k_ext * c->density[(row + iy) * c->gx + ix] + c->mu_a) * (top - r[1]);
+    for (int j = iy + 1; j < c->gy; ++j)
+        od += (c->k_ext * c->density[(row + j) * c->gx + ix] + c->mu_a) * vy;
+    return od;
+}
+
+static void run_photon(const oracle_walk_cfg *c, const double *maj, uint64_t p, acc_t *A,
                        oracle_trace_rec *tr, int n_tr_ev)
 {
     const uint32_t key[2] = {(uint32_t)c->seed, (uint32_t)(c->seed >> 32)};
@@ -153,8 +262,12 @@ static void run_photon(const oracle_walk_cfg *c, uint64_t p, acc_t *A,
         r[2] = rho * sin(psi);
     }
 
+    const int het = c->density != NULL;
     for (uint32_t e = 0;; ++e) {
-        oracle_trace_rec *rec = (tr && e < (uint32_t)n_tr_ev) ? &tr[e] : NULL;
+        /* traces record the real events: every flight, or with delta
+         * tracking every real collision and the exit */
+        const uint32_t ri = het ? n_coll : e;
+        oracle_trace_rec *rec = (tr && ri < (uint32_t)n_tr_ev) ? &tr[ri] : NULL;
         if (e >= c->max_events) {
             pt[ORACLE_T_TRUNC] += w;
             A->capped++;
@@ -173,34 +286,56 @@ static void run_photon(const oracle_walk_cfg *c, uint64_t p, acc_t *A,
         double u2 = oracle_uniform(o[2]), u3 = oracle_uniform(o[3]);
         A->steps++;
 
-        /* Eq. 15 */
-        double s = mu_ext > 0.0 ? -log(u0) / mu_ext : INFINITY;
-        /* boundary: distance to the first wall along d */
-        double sw = INFINITY, sw2 = INFINITY;
-        int face = -1;
-        for (int i = 0; i < 3; ++i) {
-            double t;
-            if (d[i] > 0.0)
-                t = (hi[i] - r[i]) / d[i];
-            else if (d[i] < 0.0)
-                t = (lo[i] - r[i]) / d[i];
-            else
-                continue;
-            if (t < sw) {
-                sw2 = sw;
-                sw = t;
-                face = i;
-            } else if (t < sw2) {
-                sw2 = t;
+        int face = -1, escaped;
+        double margin, mu_here = mu_ext, mubar = mu_ext, mua_here = c->mu_a;
+        int vx = 0, vy = 0, vz = 0;
+        if (het) {
+            margin = INFINITY;
+            escaped = delta_flight(c, maj, lo, hi, r, d, -log(u0), &mubar, &face, &margin);
+            if (!escaped) {
+                mu_here = grid_mu(c, lo, r, &vx, &vy, &vz, &margin);
+                mua_here = mu_here - c->k_sca * c->density[((size_t)vz * c->gy + vy) * c->gx + vx];
+                const double acc = mu_here / mubar;
+                margin = min2(margin, fabs(u3 - acc));
+                if (!(u3 < acc))
+                    continue;   /* null collision */
+                u3 = u3 / acc;  /* uniform on [0, 1) given acceptance */
+            }
+        } else {
+            /* Eq. 15 */
+            double s = mu_ext > 0.0 ? -log(u0) / mu_ext : INFINITY;
+            /* boundary: distance to the first wall along d */
+            double sw = INFINITY, sw2 = INFINITY;
+            for (int i = 0; i < 3; ++i) {
+                double t;
+                if (d[i] > 0.0)
+                    t = (hi[i] - r[i]) / d[i];
+                else if (d[i] < 0.0)
+                    t = (lo[i] - r[i]) / d[i];
+                else
+                    continue;
+                if (t < sw) {
+                    sw2 = sw;
+                    sw = t;
+                    face = i;
+                } else if (t < sw2) {
+                    sw2 = t;
+                }
+            }
+            margin = fabs(s - sw) / (sw > 0.0 ? sw : 1e-300);
+            escaped = s >= sw;
+            if (escaped) {
+                for (int i = 0; i < 3; ++i)
+                    r[i] += sw * d[i];
+                if (isfinite(sw2))
+                    margin = min2(margin, (sw2 - sw) / (sw > 0.0 ? sw : 1e-300));
+            } else {
+                for (int i = 0; i < 3; ++i)
+                    r[i] += s * d[i];
             }
         }
-        double margin = fabs(s - sw) / (sw > 0.0 ? sw : 1e-300);
 
-        if (s >= sw) {
-            for (int i = 0; i < 3; ++i)
-                r[i] += sw * d[i];
-            if (isfinite(sw2))
-                margin = min2(margin, (sw2 - sw) / (sw > 0.0 ? sw : 1e-300));
+        if (escaped) {
             double status;
             int rbin = -1;
             if (face == 0 && d[0] < 0.0) {
@@ -241,13 +376,11 @@ static void run_photon(const oracle_walk_cfg *c, uint64_t p, acc_t *A,
             break;
         }
 
-        for (int i = 0; i < 3; ++i)
-            r[i] += s * d[i];
         n_coll++;
 
         /* Eq. 16 */
-        pt[ORACLE_T_ABSORB] += w * (c->mu_a / mu_ext);
-        w = w * (1.0 - c->mu_a / mu_ext);
+        pt[ORACLE_T_ABSORB] += w * (mua_here / mu_here);
+        w = w * (1.0 - mua_here / mu_here);
 
         /* camera: next-event estimate toward +y */
         double muc = d[1];
@@ -274,7 +407,8 @@ static void run_photon(const oracle_walk_cfg *c, uint64_t p, acc_t *A,
             psr = pdf / (2.0 * M_PI);
             margin = min2(margin, min2(muc - c->icdf[nbin], c->icdf[nbin + 1] - muc));
         }
-        double nee = w * psr * exp(-mu_ext * (hi[1] - r[1]));
+        double od = het ? column_depth(c, lo, hi, r, vx, vy, vz) : mu_ext * (hi[1] - r[1]);
+        double nee = w * psr * exp(-od);
         double fx = r[0] / c->lx * c->nx;
         double fz = (r[2] - lo[2]) / c->lz * c->nz;
         int ix = (int)floor(fx), iz = (int)floor(fz);
@@ -335,6 +469,8 @@ static void run_photon(const oracle_walk_cfg *c, uint64_t p, acc_t *A,
             /* weight threshold */
             if (w < c->rr_threshold) {
                 margin = min2(margin, fabs(w - c->rr_threshold) / c->rr_threshold);
+                if (het)
+                    margin = min2(margin, fabs(u3 - c->rr_survival));
                 if (u3 < c->rr_survival) {
                     double wn = w / c->rr_survival;
                     pt[ORACLE_T_ROULETTE] += w - wn;
@@ -375,6 +511,7 @@ static void run_photon(const oracle_walk_cfg *c, uint64_t p, acc_t *A,
 
 typedef struct {
     const oracle_walk_cfg *c;
+    const double *maj;
     acc_t acc;
     uint64_t first, count;
     oracle_trace_rec *trace;
@@ -391,7 +528,7 @@ static void *worker(void *arg)
         oracle_trace_rec *tr = NULL;
         if (J->trace && rel < (uint64_t)J->n_trace)
             tr = J->trace + rel * (uint64_t)J->n_trace_events;
-        run_photon(c, c->photon_offset + rel, &J->acc, tr, J->n_trace_events);
+        run_photon(c, J->maj, c->photon_offset + rel, &J->acc, tr, J->n_trace_events);
     }
     return NULL;
 }
@@ -409,9 +546,33 @@ int oracle_walk(const oracle_walk_cfg *c, oracle_walk_out *out,
         return -1;
     if (c->phase_kind < 0 || c->phase_kind > ORACLE_PHASE_PAPER)
         return -1;
-    if (c->phase_kind == ORACLE_PHASE_HG && !(c->hg_g > -1.0 && c->hg_g < 1.0))
+    double *maj = NULL;
+    if (c->density) {
+        if (c->gx < 1 || c->gy < 1 || c->gz < 1 || c->bx < 1 || c->by < 1 || c->bz < 1 ||
+            !(c->k_ext >= c->k_sca) || !(c->k_sca >= 0.0))
+            return -1;
+        const size_t nv = (size_t)c->gx * c->gy * c->gz;
+        for (size_t i = 0; i < nv; ++i)
+            if (!(c->density[i] >= 0.0) || !isfinite(c->density[i]))
+                return -1;
+        /* majorant of each cell: mu_ext at the densest voxel it holds */
+        const int mx = (c->gx + c->bx - 1) / c->bx, my = (c->gy + c->by - 1) / c->by,
+                  mz = (c->gz + c->bz - 1) / c->bz;
+        maj = calloc((size_t)mx * my * mz, sizeof *maj);
+        if (!maj)
+            return -1;
+        for (int z = 0; z < c->gz; ++z)
+            for (int y = 0; y < c->gy; ++y)
+                for (int x = 0; x < c->gx; ++x) {
+                    double mu = c->k_ext * c->density[((size_t)z * c->gy + y) * c->gx + x] + c->mu_a;
+                    double *q = &maj[((size_t)(z / c->bz) * my + y / c->by) * mx + x / c->bx];
+                    if (mu > *q)
+                        *q = mu;
+                }
+    } else if (!(c->mu_s + c->mu_a > 0.0)) {
         return -1;
-    if (!(c->mu_s + c->mu_a > 0.0))
+    }
+    if (c->phase_kind == ORACLE_PHASE_HG && !(c->hg_g > -1.0 && c->hg_g < 1.0))
         return -1;
     if (trace) {
         for (size_t i = 0; i < (size_t)n_trace * (size_t)n_trace_events; ++i) {
@@ -430,12 +591,14 @@ int oracle_walk(const oracle_walk_cfg *c, oracle_walk_out *out,
     if (!jobs || !th) {
         free(jobs);
         free(th);
+        free(maj);
         return -1;
     }
     int rc = 0;
     for (int t = 0; t < T; ++t) {
         job_t *J = &jobs[t];
         J->c = c;
+        J->maj = maj;
         J->first = c->n_photons * (uint64_t)t / (uint64_t)T;
         J->count = c->n_photons * (uint64_t)(t + 1) / (uint64_t)T - J->first;
         J->trace = trace;
@@ -483,5 +646,6 @@ int oracle_walk(const oracle_walk_cfg *c, oracle_walk_out *out,
     }
     free(jobs);
     free(th);
+    free(maj);
     return rc;
 }
