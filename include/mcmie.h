@@ -95,6 +95,18 @@ size_t mc_table_bytes(int n_bins);
 mc_status mie_table_build(const mie_params *params, mie_info *info, void *table,
                           double *omu64, double *pdf64);
 
+/* Phase table of a particle mixture, e.g. the size bins of a polydisperse
+ * sample: n_comp particle kinds (params[k], all with the same n_bins) present
+ * with number fractions number_frac[k] >= 0 (normalised here). The mixture
+ * phase function weights each kind's normalised phase function (Eq. 9-10) by
+ * its share f_k sigma_sca,k of the scattering cross section (Eq. 14). info
+ * receives the number-averaged cross sections sigma_* (so that Eq. 17 with
+ * the total number density gives mu_s, mu_a), efficiencies relative to the
+ * mean geometric cross section, the mixture's g, and x, m of params[0].
+ * Outputs otherwise as mie_table_build. 1 <= n_comp <= 256. */
+mc_status mie_mixture_table_build(const mie_params *params, const double *number_frac, int n_comp,
+                                  mie_info *info, void *table, double *omu64, double *pdf64);
+
 /* The paper's own sampling table (Sec. 3.1.2): the phase function at
  * n_theta equally spaced scattering angles theta_i = i pi / (n_theta - 1),
  * its cumulative distribution by the trapezoidal rule on (1/2) P sin(theta),
@@ -262,6 +274,48 @@ mc_status mc_adjoint(const mc_medium *medium, const mc_geometry *geom,
                      const mc_camera *camera, const mc_run_params *run,
                      const float *d_adj_image, int n_phase_w, double *d_out,
                      uint32_t *d_error, void *d_work, size_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Heterogeneous media: the number density of the particles on a voxel grid
+ * spanning the cuvette (the paper's walls and camera; the complex media its
+ * Sec. 6 leaves to future work). In voxel v, mu_ext = k_ext n_v + mu_a and
+ * mu_s = k_sca n_v (Eq. 17 per voxel; k_* are the cross sections per
+ * particle, e.g. the mixture averages of mie_mixture_table_build). Flights
+ * are sampled by delta (Woodcock) tracking against a majorant constant on
+ * cells of bx x by x bz voxels; the camera transmittance of a collision is
+ * the exact optical depth of its voxel column. Event e of photon p draws
+ * Philox (p_lo, p_hi, e, 0) for every tentative collision: u0 optical depth
+ * of the flight, u1 polar angle, u2 azimuth, u3 acceptance (real if u3 <
+ * mu_ext / majorant), then u3 / (mu_ext / majorant) for roulette.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    const float *d_density;   /* device, [gz][gy][gx] particles per mm^3 (>= 0, finite) */
+    int gx, gy, gz;           /* voxels along x, y, z: 1..4096 each, product <= 2^28 */
+    double k_ext, k_sca;      /* mm^2, k_ext >= k_sca >= 0, k_ext > 0 */
+    double mu_a;              /* uniform background absorption, mm^-1 (>= 0) */
+    int bx, by, bz;           /* majorant cells in voxels (>= 1); at most 16384 cells */
+} mc_grid;
+
+/* Device bytes of a prepared grid (per voxel mu_ext and the optical depth
+ * above it as two floats, then the cell majorants); 0 if *grid is invalid. */
+size_t mc_grid_workspace_bytes(const mc_grid *grid);
+
+/* Prepare d_work (mc_grid_workspace_bytes bytes, 16-byte aligned) from the
+ * density: per voxel (mu_ext, optical depth from the voxel's top face to y =
+ * +ly/2, summed in double) and per cell the largest mu_ext. Asynchronous on
+ * `stream`; redo after the density changes. */
+mc_status mc_grid_prepare(const mc_grid *grid, const mc_geometry *geom, void *d_work, size_t work_bytes,
+                          void *stream);
+
+/* The walk through a prepared grid. phase: its phase_kind, hg_g, d_table and
+ * n_bins give the phase function (a table of the mixture for a polydisperse
+ * suspension); its mu_s, mu_a are ignored. max_events bounds the tentative
+ * collisions of a photon. d_trace (may be NULL): n_trace * n_events records
+ * as mc_trace's, one per real collision and one for the exit. Other
+ * arguments and errors as mc_run. */
+mc_status mc_run_grid(const mc_grid *grid, const void *d_grid_work, const mc_medium *phase,
+                      const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
+                      const mc_tallies *tallies, void *d_trace, int n_trace, int n_events, void *stream);
 
 /* Image comparison (Sec. 3.1.4: every image normalised the same way, here
  * min-max to [0, 1]; Table 3: RMSE and Pearson r over the pixels; Table 4:

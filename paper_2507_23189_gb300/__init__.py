@@ -6,10 +6,12 @@ cuvette walls, side-camera next-event estimate) runs in hand-written sm_103a
 CUDA behind the C ABI in include/mcmie.h; this package is its binding.
 """
 from . import _native
-from .engine import (Batch, Camera, Engine, Geometry, Medium, PaperTable, PhaseTable, camera_image,
-                     decode_trace, host_workspace_bytes, image_metrics, philox, run_host, run_params)
+from .engine import (Batch, Camera, Engine, Geometry, Grid, Medium, MixtureTable, PaperTable, PhaseTable,
+                     camera_image, decode_trace, host_workspace_bytes, image_metrics, philox, run_host,
+                     run_params)
 
-__all__ = ["Batch", "Camera", "Engine", "Geometry", "Medium", "PaperTable", "PhaseTable", "camera_image",
+__all__ = ["Batch", "Camera", "Engine", "Geometry", "Grid", "Medium", "MixtureTable", "PaperTable", "PhaseTable",
+           "camera_image",
            "decode_trace", "host_workspace_bytes", "image_metrics", "philox", "run_host", "run_params", "lib"]
 
 

@@ -24,7 +24,8 @@ EXPORTS = ("mc_table_bytes", "mie_table_build", "mc_medium_from_density", "mc_wo
            "mc_run", "mc_host_workspace_bytes", "mc_run_host", "mc_trace", "mc_check", "mc_philox",
            "mc_status_string", "mc_run_static", "mc_batch_workspace_bytes", "mc_run_batch",
            "mc_adjoint_workspace_bytes", "mc_adjoint", "mc_paper_table_bytes", "mie_paper_table_build",
-           "mc_metrics_out_len", "mc_metrics_workspace_bytes", "mc_image_metrics")
+           "mc_metrics_out_len", "mc_metrics_workspace_bytes", "mc_image_metrics", "mie_mixture_table_build",
+           "mc_grid_workspace_bytes", "mc_grid_prepare", "mc_run_grid")
 
 
 class McError(RuntimeError):
@@ -47,6 +48,12 @@ class MieInfo(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Grid(C.Structure):
+    _fields_ = [("d_density", C.c_void_p), ("gx", C.c_int), ("gy", C.c_int), ("gz", C.c_int),
+                ("k_ext", C.c_double), ("k_sca", C.c_double), ("mu_a", C.c_double),
+                ("bx", C.c_int), ("by", C.c_int), ("bz", C.c_int)]
 
 
 class Medium(C.Structure):
@@ -140,6 +147,16 @@ def lib():
     L.mc_metrics_workspace_bytes.argtypes = [C.c_int]
     L.mc_image_metrics.restype = C.c_int
     L.mc_image_metrics.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, vp, vp, C.c_size_t, vp]
+    L.mie_mixture_table_build.restype = C.c_int
+    L.mie_mixture_table_build.argtypes = [P(MieParams), P(C.c_double), C.c_int, P(MieInfo), vp, P(C.c_double),
+                                          P(C.c_double)]
+    L.mc_grid_workspace_bytes.restype = C.c_size_t
+    L.mc_grid_workspace_bytes.argtypes = [P(Grid)]
+    L.mc_grid_prepare.restype = C.c_int
+    L.mc_grid_prepare.argtypes = [P(Grid), P(Geometry), vp, C.c_size_t, vp]
+    L.mc_run_grid.restype = C.c_int
+    L.mc_run_grid.argtypes = [P(Grid), vp, P(Medium), P(Geometry), P(Camera), P(RunParams), P(Tallies), vp,
+                              C.c_int, C.c_int, vp]
     L.mc_status_string.restype = C.c_char_p
     L.mc_status_string.argtypes = [C.c_int]
     _lib = L

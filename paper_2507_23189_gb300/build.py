@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "_build", "libmcmie.so")
-SOURCES = ["walk.cu", "api.cu", "mie_table.cpp", "noalloc.cu", "metrics.cu"]
+SOURCES = ["walk.cu", "api.cu", "mie_table.cpp", "noalloc.cu", "metrics.cu", "grid.cu"]
 HEADERS = ["engine.h", "table_format.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true",

@@ -134,6 +134,7 @@ void fill_common(mcx::CommonArgs &c, const mc_medium *m, const mc_geometry *g, c
     c.max_scatter = r->max_scatter;
     c.img_scale = std::ldexp(1.0f, r->image_frac_bits);
     c.error = error;
+    c.extra_bytes = 0;
 }
 
 mcx::WalkArgs make_args(const mc_medium *m, const mc_geometry *g, const mc_camera *c,
@@ -455,3 +456,113 @@ const char *mc_status_string(mc_status s)
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ voxel grids
+
+namespace {
+
+constexpr int kMaxCells = 16384;
+
+size_t pad16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+bool grid_dims(const mc_grid *g, int *mx, int *my, int *mz)
+{
+    if (!g || g->gx < 1 || g->gy < 1 || g->gz < 1 || g->gx > 4096 || g->gy > 4096 || g->gz > 4096 ||
+        (long long)g->gx * g->gy * g->gz > (1ll << 28) || g->bx < 1 || g->by < 1 || g->bz < 1 ||
+        !fin(g->k_ext) || !fin(g->k_sca) || !fin(g->mu_a) || !(g->k_ext > 0.0) || g->k_sca < 0.0 ||
+        g->k_sca > g->k_ext || g->mu_a < 0.0)
+        return false;
+    *mx = (g->gx + g->bx - 1) / g->bx;
+    *my = (g->gy + g->by - 1) / g->by;
+    *mz = (g->gz + g->bz - 1) / g->bz;
+    return (long long)*mx * *my * *mz <= kMaxCells;
+}
+
+}  // namespace
+
+size_t mc_grid_workspace_bytes(const mc_grid *g)
+{
+    int mx, my, mz;
+    if (!grid_dims(g, &mx, &my, &mz)) return 0;
+    return pad16(sizeof(float) * 2 * (size_t)g->gx * g->gy * g->gz) + pad16(sizeof(float) * (size_t)mx * my * mz);
+}
+
+mc_status mc_grid_prepare(const mc_grid *g, const mc_geometry *geom, void *d_work, size_t work_bytes,
+                          void *stream)
+{
+    int mx, my, mz;
+    mc_status s;
+    if (!grid_dims(g, &mx, &my, &mz) || !g->d_density || !aligned(g->d_density, 4) || !d_work ||
+        !aligned(d_work, 16))
+        return MC_ERR_ARG;
+    if ((s = check_geom(geom)) != MC_OK) return s;
+    if (work_bytes < mc_grid_workspace_bytes(g)) return MC_ERR_NOMEM;
+    unsigned char *w = static_cast<unsigned char *>(d_work);
+    float2 *cells = reinterpret_cast<float2 *>(w);
+    float *maj = reinterpret_cast<float *>(w + pad16(sizeof(float) * 2 * (size_t)g->gx * g->gy * g->gz));
+    const cudaError_t e = mcx::launch_grid_prepare(g->d_density, g->gx, g->gy, g->gz, g->bx, g->by, g->bz,
+                                                   (float)g->k_ext, (float)g->mu_a, geom->ly / g->gy, cells,
+                                                   maj, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MC_OK : MC_ERR_CUDA;
+}
+
+mc_status mc_run_grid(const mc_grid *g, const void *d_grid_work, const mc_medium *phase,
+                      const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
+                      const mc_tallies *tallies, void *d_trace, int n_trace, int n_events, void *stream)
+{
+    int mx, my, mz;
+    mc_status s;
+    if (!grid_dims(g, &mx, &my, &mz) || !d_grid_work || !aligned(d_grid_work, 16) || !phase) return MC_ERR_ARG;
+    // the phase part of the medium; its coefficients are placeholders
+    mc_medium m = *phase;
+    m.mu_s = 1.0;
+    m.mu_a = 0.0;
+    if ((s = validate_all(&m, geom, camera, run)) != MC_OK) return s;
+    if ((s = check_tallies(tallies, camera)) != MC_OK) return s;
+    if (d_trace && (n_trace < 1 || n_events < 1 || n_events > 1 << 20 || !aligned(d_trace, 4) ||
+                    (uint64_t)n_trace > run->n_photons))
+        return MC_ERR_ARG;
+    mcx::GridArgs a;
+    std::memset(&a, 0, sizeof a);
+    fill_common(a.c, &m, geom, camera, run, tallies->d_error);
+    fill_medium(a.m, &m, run->n_photons, run->photon_offset, run->seed, tallies->d_image, tallies->d_radial,
+                tallies->d_totals);
+    const unsigned char *w = static_cast<const unsigned char *>(d_grid_work);
+    a.cells = reinterpret_cast<const float2 *>(w);
+    a.maj = reinterpret_cast<const float *>(w + pad16(sizeof(float) * 2 * (size_t)g->gx * g->gy * g->gz));
+    a.c.extra_bytes = (uint32_t)pad16(sizeof(float) * (size_t)mx * my * mz);
+    a.gx = g->gx; a.gy = g->gy; a.gz = g->gz;
+    a.mx = mx; a.my = my; a.mz = mz;
+    a.inv_vx = (float)(g->gx / geom->lx);
+    a.inv_vy = (float)(g->gy / geom->ly);
+    a.inv_vz = (float)(g->gz / geom->lz);
+    a.vy = (float)(geom->ly / g->gy);
+    a.csx = (float)(g->bx * geom->lx / g->gx);
+    a.csy = (float)(g->by * geom->ly / g->gy);
+    a.csz = (float)(g->bz * geom->lz / g->gz);
+    a.inv_csx = (float)(g->gx / (g->bx * geom->lx));
+    a.inv_csy = (float)(g->gy / (g->by * geom->ly));
+    a.inv_csz = (float)(g->gz / (g->bz * geom->lz));
+    a.ks_over_ke = (float)(g->k_sca / g->k_ext);
+    a.mu_a = (float)g->mu_a;
+    a.counter = reinterpret_cast<unsigned long long *>(tallies->d_work);
+    a.c.trace = static_cast<int32_t *>(d_trace);
+    a.c.n_trace = d_trace ? n_trace : 0;
+    a.c.n_trace_events = d_trace ? n_events : 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t npix = (size_t)camera->nx * camera->nz;
+    auto fail = [](cudaError_t x) { return x != cudaSuccess; };
+    if (fail(cudaMemsetAsync(tallies->d_work, 0, sizeof(unsigned long long), st))) return MC_ERR_CUDA;
+    if (!run->accumulate) {
+        if (fail(cudaMemsetAsync(tallies->d_image, 0, sizeof(int64_t) * npix, st)) ||
+            fail(cudaMemsetAsync(tallies->d_radial, 0, sizeof(int64_t) * camera->n_radial, st)) ||
+            fail(cudaMemsetAsync(tallies->d_totals, 0, sizeof(int64_t) * MC_N_TOTALS, st)))
+            return MC_ERR_CUDA;
+    }
+    if (d_trace && fail(cudaMemsetAsync(d_trace, 0xFF, sizeof(int32_t) * 12 * (size_t)n_trace * n_events, st)))
+        return MC_ERR_CUDA;
+    if (run->n_photons == 0) return MC_OK;
+    const cudaError_t e = mcx::launch_grid(a, d_trace != nullptr, launch_cfg(run), st);
+    if (e == cudaErrorInvalidValue) return MC_ERR_ARG;  // the shared-memory plan does not fit
+    return cuda_status(e);
+}

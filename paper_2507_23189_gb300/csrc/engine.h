@@ -43,6 +43,8 @@ struct CommonArgs {
     // trace (trace kernels only)
     int32_t *trace;
     int n_trace, n_trace_events;
+    // bytes staged after the table (the majorant cells of a grid walk)
+    uint32_t extra_bytes;
 };
 
 // One medium, one photon range. Passed by value as a __grid_constant__.
@@ -78,6 +80,23 @@ struct AdjArgs {
     unsigned long long *counter;
 };
 
+// A heterogeneous medium on a voxel grid (mc_run_grid): per voxel
+// (mu_ext, optical depth from the voxel's top face to the camera face), the
+// majorant of each cell of bx x by x bz voxels, and the geometry of both.
+struct GridArgs {
+    CommonArgs c;
+    MediumArgs m;                 // phase, Philox key, photon range, tallies
+    const float2 *cells;          // [gz][gy][gx]
+    const float *maj;             // [mz][my][mx], staged into shared memory
+    int gx, gy, gz, mx, my, mz;
+    float inv_vx, inv_vy, inv_vz; // voxels per mm
+    float vy;                     // voxel height, mm
+    float csx, csy, csz;          // cell sizes, mm
+    float inv_csx, inv_csy, inv_csz;
+    float ks_over_ke, mu_a;       // albedo = ks_over_ke (1 - mu_a / mu_ext)
+    unsigned long long *counter;
+};
+
 struct LaunchCfg {
     int block = 0;          // 0: 256 (whole tile / global) or 1024 (band)
     int blocks_per_sm = 0;  // 0: occupancy maximum
@@ -96,6 +115,15 @@ cudaError_t launch_batch(const BatchArgs &a, const LaunchCfg &cfg, cudaStream_t 
 // Launch the adjoint replay and the reduction into out[3 + n_w]
 // (value, dL/dmu_s, dL/dmu_a, dL/dw_k). partial_rows: capacity of partials.
 cudaError_t launch_adjoint(const AdjArgs &a, int partial_rows, double *out, cudaStream_t stream);
+
+// Launch the delta-tracking walk through a prepared grid (trace: records of
+// real events in c.trace).
+cudaError_t launch_grid(const GridArgs &a, bool trace, const LaunchCfg &cfg, cudaStream_t stream);
+
+// Per-voxel (mu_ext, optical depth above) and per-cell majorants of a grid.
+cudaError_t launch_grid_prepare(const float *density, int gx, int gy, int gz, int bx, int by, int bz,
+                                float k_ext, float mu_a, double vy, float2 *cells, float *maj,
+                                cudaStream_t stream);
 
 // CTAs the adjoint launch may use on the current device (for workspace sizing).
 int adjoint_max_grid();

@@ -1,0 +1,74 @@
+// Preparation of a heterogeneous medium for the delta-tracking walk
+// (mc_grid_prepare): per voxel mu_ext = k_ext n + mu_a (Eq. 17 per voxel)
+// and the optical depth from the voxel's top face to the camera face
+// y = +ly/2, which makes the camera transmittance of any collision exact
+// with one gather; and the majorant of every cell of bx x by x bz voxels.
+#include <cuda_runtime.h>
+
+#include "engine.h"
+
+namespace mcx {
+namespace {
+
+// One thread per (x, z) column, walking down from the camera face: writes
+// (mu_ext, depth above) per voxel; consecutive threads touch consecutive x,
+// so every row access is coalesced. The depth is summed in double.
+__global__ void column_kernel(const float *__restrict__ density, int gx, int gy, int gz, float k_ext,
+                              float mu_a, double vy, float2 *__restrict__ cells)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)gx * gz) return;
+    const int iz = (int)(t / gx), ix = (int)(t - (long long)iz * gx);
+    double od = 0.0;
+    for (int iy = gy - 1; iy >= 0; --iy) {
+        const size_t v = ((size_t)iz * gy + iy) * gx + ix;
+        const float mu = fmaf(k_ext, density[v], mu_a);
+        cells[v] = make_float2(mu, (float)od);
+        od += (double)mu * vy;
+    }
+}
+
+// One CTA per majorant cell: the largest density of its voxels, as mu_ext
+// with the same single-precision operation as the voxels (so no voxel
+// exceeds its cell's majorant).
+__global__ void __launch_bounds__(256) majorant_kernel(const float *__restrict__ density, int gx, int gy,
+                                                       int gz, int bx, int by, int bz, int mx, int my,
+                                                       float k_ext, float mu_a, float *__restrict__ maj)
+{
+    __shared__ float red[256];
+    const int c = blockIdx.x;
+    const int cz = c / (mx * my), cy = (c / mx) % my, cx = c % mx;
+    const int x0 = cx * bx, y0 = cy * by, z0 = cz * bz;
+    const int nxb = min(bx, gx - x0), nyb = min(by, gy - y0), nzb = min(bz, gz - z0);
+    const long long nv = (long long)nxb * nyb * nzb;
+    float m = 0.0f;
+    for (long long i = threadIdx.x; i < nv; i += blockDim.x) {
+        const int xi = (int)(i % nxb), yi = (int)((i / nxb) % nyb), zi = (int)(i / ((long long)nxb * nyb));
+        m = fmaxf(m, density[((size_t)(z0 + zi) * gy + (y0 + yi)) * gx + (x0 + xi)]);
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) maj[c] = fmaf(k_ext, red[0], mu_a);
+}
+
+}  // namespace
+
+cudaError_t launch_grid_prepare(const float *density, int gx, int gy, int gz, int bx, int by, int bz,
+                                float k_ext, float mu_a, double vy, float2 *cells, float *maj,
+                                cudaStream_t st)
+{
+    const long long cols = (long long)gx * gz;
+    column_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(density, gx, gy, gz, k_ext, mu_a,
+                                                                  vy, cells);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int mx = (gx + bx - 1) / bx, my = (gy + by - 1) / by, mz = (gz + bz - 1) / bz;
+    majorant_kernel<<<mx * my * mz, 256, 0, st>>>(density, gx, gy, gz, bx, by, bz, mx, my, k_ext, mu_a, maj);
+    return cudaGetLastError();
+}
+
+}  // namespace mcx

@@ -16,6 +16,7 @@
 //    8-point Gauss-Legendre panels; normalisation (Eq. 10) by the total.
 //  * Inverse CDF on n_bins equal-probability levels by safeguarded Newton
 //    iteration on the exact integrand inside the panel holding each level.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -127,16 +128,27 @@ const double GL_W[8] = {0.1012285362903763, 0.2223810344533745, 0.31370664587788
                         0.3626837833783620, 0.3626837833783620, 0.3137066458778873,
                         0.2223810344533745, 0.1012285362903763};
 
-// Density in theta, (1/2) P(cos t) sin t (unnormalised).
-double dens_theta(const MieSeries &S, double t) { return 0.5 * phase_raw(S, std::cos(t)) * std::sin(t); }
-
-// Integral of the density over theta in [t0, t1].
-double integrate(const MieSeries &S, double t0, double t1)
-{
-    double c = 0.5 * (t0 + t1), h = 0.5 * (t1 - t0), s = 0.0;
-    for (int i = 0; i < 8; ++i) s += GL_W[i] * dens_theta(S, c + h * GL_X[i]);
-    return s * h;
-}
+// A phase function as a weighted sum of Mie components: density in theta
+// sum_k c_k (1/2) P_k(cos t) sin t (a single particle is one component).
+struct Mix {
+    std::vector<const MieSeries *> S;
+    std::vector<double> c;
+    double dens(double t) const
+    {
+        const double mu = std::cos(t), st = std::sin(t);
+        double v = 0.0;
+        for (size_t k = 0; k < S.size(); ++k)
+            if (c[k] != 0.0) v += c[k] * phase_raw(*S[k], mu);
+        return 0.5 * v * st;
+    }
+    // Integral of the density over theta in [t0, t1].
+    double integrate(double t0, double t1) const
+    {
+        double m = 0.5 * (t0 + t1), h = 0.5 * (t1 - t0), s = 0.0;
+        for (int i = 0; i < 8; ++i) s += GL_W[i] * dens(m + h * GL_X[i]);
+        return s * h;
+    }
+};
 
 // The particle's Mie series and the quantities of mie_info (all but
 // g_table). Returns MC_ERR_ARG for parameters out of range.
@@ -180,31 +192,23 @@ mc_status prepare(const mie_params *P, MieSeries &S, mie_info &I)
     return MC_OK;
 }
 
-}  // namespace
 
-extern "C" size_t mc_table_bytes(int n_bins) { return mc_table_layout(n_bins, nullptr); }
-
-extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *table,
-                                     double *omu64, double *pdf64)
+// Steps 2-4 for the density D: cumulative integral over theta on panels of
+// 8-point Gauss-Legendre (enough panels for the oscillations of a series of
+// nmax terms), the equal-probability levels by safeguarded Newton iteration,
+// the packed single-precision blob and its camera-density guide.
+mc_status build_levels(const Mix &D, int nmax, int n_bins, size_t bytes, mc_table_header &H, void *table,
+                       double *omu64, double *pdf64, double *mean_out)
 {
-    if (!P) return MC_ERR_ARG;
-    mc_table_header H;
-    size_t bytes = mc_table_layout(P->n_bins, &H);
-    if (!bytes) return MC_ERR_ARG;
-    MieSeries S;
-    mie_info I;
-    const mc_status st = prepare(P, S, I);
-    if (st != MC_OK) return st;
-
+    const int n = n_bins;
     // Panels in theta, accumulated from theta = pi (mu = -1) toward 0.
-    const int n = P->n_bins;
-    const int M = std::max(4 * n, 96 * S.nmax);
+    const int M = std::max(4 * n, 96 * nmax);
     const double h = kPi / M;
     std::vector<double> cum(M + 1);
     cum[0] = 0.0;
     for (int k = 0; k < M; ++k) {
         double t1 = kPi - k * h, t0 = kPi - (k + 1) * h;
-        cum[k + 1] = cum[k] + integrate(S, t0, t1);
+        cum[k + 1] = cum[k] + D.integrate(t0, t1);
     }
     const double Z = cum[M];
     if (!(Z > 0.0) || !std::isfinite(Z)) return MC_ERR_NUMERIC;
@@ -223,9 +227,9 @@ extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *
         double a = lo, b = hi;  // C(b) = 0 <= want <= C(a)
         double t = 0.5 * (a + b);
         for (int it = 0; it < 60; ++it) {
-            double c = integrate(S, t, hi) - want;
+            double c = D.integrate(t, hi) - want;
             if (c > 0) a = t; else b = t;   // too much mass: move toward hi
-            double f = dens_theta(S, t);
+            double f = D.dens(t);
             double tn = (f > 0.0) ? t + c / f : 0.5 * (a + b);
             if (!(tn > a && tn < b)) tn = 0.5 * (a + b);
             if (std::fabs(tn - t) <= 1e-16 * (1.0 + std::fabs(t))) { t = tn; break; }
@@ -249,11 +253,8 @@ extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *
         mean += 1.0 - 0.5 * (omu[j] + omu[j + 1]);
     }
     mean /= n;
+    *mean_out = mean;
 
-    if (info) {
-        *info = I;
-        info->g_table = mean;
-    }
     if (omu64) std::memcpy(omu64, omu.data(), sizeof(double) * (n + 1));
     if (pdf64) std::memcpy(pdf64, pdf.data(), sizeof(double) * n);
     if (table) {
@@ -315,6 +316,35 @@ extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *
     return MC_OK;
 }
 
+}  // namespace
+
+extern "C" size_t mc_table_bytes(int n_bins) { return mc_table_layout(n_bins, nullptr); }
+
+extern "C" mc_status mie_table_build(const mie_params *P, mie_info *info, void *table,
+                                     double *omu64, double *pdf64)
+{
+    if (!P) return MC_ERR_ARG;
+    mc_table_header H;
+    size_t bytes = mc_table_layout(P->n_bins, &H);
+    if (!bytes) return MC_ERR_ARG;
+    MieSeries S;
+    mie_info I;
+    const mc_status st = prepare(P, S, I);
+    if (st != MC_OK) return st;
+
+    Mix D;
+    D.S.push_back(&S);
+    D.c.push_back(1.0);
+    double mean = 0.0;
+    const mc_status bs = build_levels(D, S.nmax, P->n_bins, bytes, H, table, omu64, pdf64, &mean);
+    if (bs != MC_OK) return bs;
+    if (info) {
+        *info = I;
+        info->g_table = mean;
+    }
+    return MC_OK;
+}
+
 extern "C" mc_status mc_medium_from_density(const mie_info *info, double nd, double mu_a_medium,
                                             mc_medium *out)
 {
@@ -324,6 +354,66 @@ extern "C" mc_status mc_medium_from_density(const mie_info *info, double nd, dou
     // Eq. 17 per unit length: mu = n sigma.
     out->mu_s = nd * info->sigma_sca_mm2;
     out->mu_a = nd * std::fmax(info->sigma_abs_mm2, 0.0) + mu_a_medium;
+    return MC_OK;
+}
+
+// A suspension of several particle kinds (the size bins of a polydisperse
+// sample, number fractions f_k) scatters with the mixture of their phase
+// functions weighted by f_k sigma_sca,k (Eq. 14 per kind); each raw
+// |S1|^2 + |S2|^2 integrates to x_k^2 Q_sca,k (its Eq. 10 normalisation).
+extern "C" mc_status mie_mixture_table_build(const mie_params *P, const double *number_frac, int n_comp,
+                                             mie_info *info, void *table, double *omu64, double *pdf64)
+{
+    if (!P || !number_frac || n_comp < 1 || n_comp > 256) return MC_ERR_ARG;
+    const int n_bins = P[0].n_bins;
+    mc_table_header H;
+    const size_t bytes = mc_table_layout(n_bins, &H);
+    if (!bytes) return MC_ERR_ARG;
+    std::vector<MieSeries> S(n_comp);
+    std::vector<mie_info> I(n_comp);
+    double fsum = 0.0;
+    for (int k = 0; k < n_comp; ++k) {
+        if (P[k].n_bins != n_bins || !(number_frac[k] >= 0.0) || !std::isfinite(number_frac[k]))
+            return MC_ERR_ARG;
+        const mc_status st = prepare(&P[k], S[k], I[k]);
+        if (st != MC_OK) return st;
+        fsum += number_frac[k];
+    }
+    if (!(fsum > 0.0)) return MC_ERR_ARG;
+    mie_info M = I[0];
+    double se = 0.0, ss = 0.0, sa = 0.0, geo = 0.0, gs = 0.0;
+    int nmax = 0;
+    Mix D;
+    for (int k = 0; k < n_comp; ++k) {
+        const double f = number_frac[k] / fsum;
+        se += f * I[k].sigma_ext_mm2;
+        ss += f * I[k].sigma_sca_mm2;
+        sa += f * I[k].sigma_abs_mm2;
+        geo += f * kPi * (P[k].diameter_um * 1e-3) * (P[k].diameter_um * 1e-3) / 4.0;
+        gs += f * I[k].sigma_sca_mm2 * I[k].g;
+        nmax = std::max(nmax, S[k].nmax);
+    }
+    if (!(ss > 0.0)) return MC_ERR_NUMERIC;
+    for (int k = 0; k < n_comp; ++k) {
+        const double w = (number_frac[k] / fsum) * I[k].sigma_sca_mm2 / ss;
+        D.S.push_back(&S[k]);
+        D.c.push_back(w * 2.0 / (I[k].x * I[k].x * I[k].qsca));
+    }
+    double mean = 0.0;
+    const mc_status bs = build_levels(D, nmax, n_bins, bytes, H, table, omu64, pdf64, &mean);
+    if (bs != MC_OK) return bs;
+    if (info) {
+        M.sigma_ext_mm2 = se;
+        M.sigma_sca_mm2 = ss;
+        M.sigma_abs_mm2 = sa;
+        M.qext = se / geo;
+        M.qsca = ss / geo;
+        M.qabs = sa / geo;
+        M.g = gs / ss;
+        M.g_table = mean;
+        M.nmax = nmax;
+        *info = M;
+    }
     return MC_OK;
 }
 

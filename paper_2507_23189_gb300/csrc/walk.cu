@@ -260,7 +260,7 @@ __device__ __forceinline__ Smem carve(unsigned char *smem, const CommonArgs &C)
     const uint32_t tb = (PHASE != MC_PHASE_HG) ? C.table_bytes : 0u;
     S.table = smem;
     S.npix = SMEM_IMAGE ? C.nx * C.band_rows : 0;
-    S.img = reinterpret_cast<unsigned long long *>(smem + tb);
+    S.img = reinterpret_cast<unsigned long long *>(smem + tb + C.extra_bytes);
     S.rad = S.img + S.npix;
     S.tot = S.rad + C.n_radial;
     S.bar = S.tot + MC_N_TOTALS;
@@ -613,6 +613,244 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ Bat
     if (cur >= 0) flush<SMEM_IMAGE>(B.c, B.m[cur], S, T);
 }
 
+
+// ------------------------------------------------------- heterogeneous medium
+// Delta (Woodcock) tracking through a voxel grid (the complex media of
+// Sec. 6's outlook). A tentative flight spends tau = -ln u0 of optical depth
+// cell by cell at each cell's majorant (a DDA over the cells, majorants in
+// shared memory); where tau runs out, the collision is real with probability
+// mu_ext / majorant (u3), else null and the photon goes on with the next
+// event's numbers. A real collision reuses u3 / (mu_ext / majorant), uniform
+// on [0, 1) given acceptance, for roulette, and weights its camera term with
+// the exact column transmittance exp(-(depth above the voxel + mu_ext times
+// the distance to the voxel's top face)). One Philox call per tentative
+// collision; the voxel's (mu_ext, depth) pair is one 8-byte gather from the
+// L2-resident grid. Traces record real events only.
+template <int PHASE, bool SMEM_IMAGE, bool TRACE>
+__device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, const float *s_maj, Tally &T)
+{
+    const CommonArgs &C = G.c;
+    const MediumArgs &M = G.m;
+    const int lane = threadIdx.x & 31;
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+    unsigned long long pool_next = 0, pool_end = 0;
+    unsigned long long *s_img = S.img, *s_rad = S.rad, *s_tot = S.tot;
+    const int max_cross = G.mx + G.my + G.mz + 4;
+    const float INF = __int_as_float(0x7f800000);
+
+    bool alive = false, done = false;
+    unsigned long long rel = 0;
+    uint32_t pk0 = 0, pk1 = 0, ev = 0, ncoll = 0;
+    float rx = 0, ry = 0, rz = 0, dx = 1, dy = 0, dz = 0, w = 1;
+    float idx = 1, idy = INF, idz = INF;   // 1 / d (infinite along an axis d does not move on)
+
+    while (true) {
+        const unsigned need = __ballot_sync(FULL, !alive && !done);
+        if (need) {
+            const unsigned n_need = __popc(need), rank = __popc(need & lanemask_lt);
+            const unsigned long long avail = pool_end - pool_next;
+            unsigned long long mine;
+            if (avail >= n_need) {
+                mine = pool_next + rank;
+                pool_next += n_need;
+            } else {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(G.counter, (unsigned long long)CHUNK);
+                base = __shfl_sync(FULL, base, 0);
+                mine = (rank < avail) ? pool_next + rank : base + (rank - avail);
+                pool_next = base + (n_need - avail);
+                pool_end = base + CHUNK;
+            }
+            if (!alive && !done) {
+                if (mine < M.n_photons) {
+                    rel = mine;
+                    const unsigned long long p = M.photon_offset + mine;
+                    pk0 = (uint32_t)p;
+                    pk1 = (uint32_t)(p >> 32);
+                    ev = 0;
+                    ncoll = 0;
+                    rx = 0.f; ry = 0.f; rz = 0.f;
+                    dx = 1.f; dy = 0.f; dz = 0.f;
+                    idx = 1.f; idy = INF; idz = INF;
+                    w = 1.f;
+                    if (C.beam_r > 0.f) {
+                        const uint4 b = philox10(make_uint4(pk0, pk1, 0xFFFFFFFFu, 0u), M.key0, M.key1);
+                        const float rho = C.beam_r * sqrtf(u01(b.x));
+                        float sp, cp;
+                        sincospif(2.0f * u01(b.y), &sp, &cp);
+                        ry = rho * cp;
+                        rz = rho * sp;
+                    }
+                    alive = true;
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, alive)) break;
+        if (!alive) continue;
+
+        if (ev >= C.max_events) {
+            sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
+            atomicOr(C.error, MC_EFLAG_EVENTS);
+            trace_write<TRACE>(C, rel, ncoll, 6, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1, -1);
+            alive = false;
+            continue;
+        }
+        const uint4 rnd = philox10(make_uint4(pk0, pk1, ev, 0u), M.key0, M.key1);
+        ++ev;
+        ++T.steps;
+        const float u1 = u01(rnd.y), u2 = u01(rnd.z);
+        float u3 = u01(rnd.w);
+
+        // -------- one tentative flight
+        float tau = -logf(u01(rnd.x));
+        int cx = min(max(__float2int_rd(rx * G.inv_csx), 0), G.mx - 1);
+        int cy = min(max(__float2int_rd((ry + C.hy) * G.inv_csy), 0), G.my - 1);
+        int cz = min(max(__float2int_rd((rz + C.hz) * G.inv_csz), 0), G.mz - 1);
+        int face = -1;
+        float mb = 0.f;
+        bool hit = false;
+        for (int it = 0; it < max_cross; ++it) {
+            mb = s_maj[(cz * G.my + cy) * G.mx + cx];
+            float tx = INF, ty = INF, tz = INF;
+            if (dx > 0.f) tx = ((cx == G.mx - 1) ? C.lx : (float)(cx + 1) * G.csx) - rx;
+            else if (dx < 0.f) tx = ((cx == 0) ? 0.f : (float)cx * G.csx) - rx;
+            if (dy > 0.f) ty = ((cy == G.my - 1) ? C.hy : fmaf((float)(cy + 1), G.csy, -C.hy)) - ry;
+            else if (dy < 0.f) ty = ((cy == 0) ? -C.hy : fmaf((float)cy, G.csy, -C.hy)) - ry;
+            if (dz > 0.f) tz = ((cz == G.mz - 1) ? C.hz : fmaf((float)(cz + 1), G.csz, -C.hz)) - rz;
+            else if (dz < 0.f) tz = ((cz == 0) ? -C.hz : fmaf((float)cz, G.csz, -C.hz)) - rz;
+            tx = (dx != 0.f) ? fmaxf(tx * idx, 0.f) : INF;
+            ty = (dy != 0.f) ? fmaxf(ty * idy, 0.f) : INF;
+            tz = (dz != 0.f) ? fmaxf(tz * idz, 0.f) : INF;
+            const int ax = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
+            const float t = ax == 0 ? tx : (ax == 1 ? ty : tz);
+            if (mb * t > tau) {
+                const float s = tau / mb;
+                rx = fmaf(s, dx, rx); ry = fmaf(s, dy, ry); rz = fmaf(s, dz, rz);
+                hit = true;
+                break;
+            }
+            if (!(t < INF)) { face = -2; break; }   // no exit plane: not a direction
+            tau = fmaf(-mb, t, tau);
+            rx = fmaf(t, dx, rx); ry = fmaf(t, dy, ry); rz = fmaf(t, dz, rz);
+            if (ax == 0) {
+                cx += dx > 0.f ? 1 : -1;
+                if (cx < 0 || cx >= G.mx) { rx = dx > 0.f ? C.lx : 0.f; face = 0; break; }
+            } else if (ax == 1) {
+                cy += dy > 0.f ? 1 : -1;
+                if (cy < 0 || cy >= G.my) { ry = dy > 0.f ? C.hy : -C.hy; face = 1; break; }
+            } else {
+                cz += dz > 0.f ? 1 : -1;
+                if (cz < 0 || cz >= G.mz) { rz = dz > 0.f ? C.hz : -C.hz; face = 2; break; }
+            }
+        }
+        if (!hit && face < 0) {
+            // a non-finite direction or more crossings than cells: give up on
+            // the photon and say so
+            atomicOr(C.error, MC_EFLAG_NUMERIC);
+            sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
+            alive = false;
+            continue;
+        }
+        if (!hit) {
+            const long long wv = fix32(w);
+            int status, rb = -1;
+            if (face == 0 && dx < 0.f) {
+                T.refl += wv;
+                status = 1;
+            } else if (face == 0) {
+                T.far += wv;
+                if (ncoll == 0) T.ball += wv;
+                const float rho = sqrtf(fmaf(ry, ry, rz * rz));
+                rb = min(__float2int_rd(rho * C.sr), C.n_radial - 1);
+                sadd64(&s_rad[rb], wv);
+                status = 2;
+            } else {
+                T.side += wv;
+                status = 3;
+            }
+            trace_write<TRACE>(C, rel, ncoll, status, rx, ry, rz, dx, dy, dz, w, 0.f, -1, -1, rb);
+            alive = false;
+            continue;
+        }
+
+        // -------- tentative collision: real with probability mu_ext / majorant
+        const int ix = min(max(__float2int_rd(rx * G.inv_vx), 0), G.gx - 1);
+        const int iy = min(max(__float2int_rd((ry + C.hy) * G.inv_vy), 0), G.gy - 1);
+        const int iz = min(max(__float2int_rd((rz + C.hz) * G.inv_vz), 0), G.gz - 1);
+        const float2 cell = __ldg(&G.cells[((size_t)iz * G.gy + iy) * G.gx + ix]);
+        const float acc = cell.x / mb;
+        if (!(u3 < acc)) continue;   // null collision
+        u3 = u3 / acc;
+        ++ncoll;
+        {   // Eq. 16 with the voxel's albedo
+            const float a = G.mu_a > 0.f ? G.ks_over_ke * (1.0f - G.mu_a / cell.x) : G.ks_over_ke;
+            const float wn = w * a;
+            if (a < 1.0f) T.abs += fix32(w - wn);
+            w = wn;
+        }
+        int nb, pix_x, pix_z;
+        const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
+        const float top = (iy == G.gy - 1) ? C.hy : fmaf((float)(iy + 1), G.vy, -C.hy);
+        const float nee = w * psr * expf(-fmaf(cell.x, top - ry, cell.y));
+        const int pix = camera_pixel(C, rx, rz, pix_x, pix_z);
+        const float vf = nee * C.img_scale;
+        if (vf < 4.0e18f) {
+            const long long v = __float2ll_rn(vf);
+            const unsigned brow = (unsigned)(pix_z - C.band0);
+            if (SMEM_IMAGE && brow < (unsigned)C.band_rows) sadd64(&s_img[brow * C.nx + pix_x], v);
+            else atomicAdd(&M.image[pix], (unsigned long long)v);
+        } else {
+            atomicOr(C.error, (vf == vf) ? MC_EFLAG_OVERFLOW : MC_EFLAG_NUMERIC);
+        }
+        int status = 0;
+        if (C.max_scatter && ncoll >= C.max_scatter) {
+            sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
+            status = 5;
+            alive = false;
+        } else {
+            rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
+            idx = __frcp_rn(dx); idy = __frcp_rn(dy); idz = __frcp_rn(dz);
+            if (w < C.rr_thr) {
+                if (u3 < C.rr_surv) {
+                    const float wn = w * C.inv_rr_surv;
+                    sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w) - fix32(wn));
+                    w = wn;
+                } else {
+                    sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w));
+                    status = 4;
+                    alive = false;
+                }
+            }
+            if (!(w == w)) atomicOr(C.error, MC_EFLAG_NUMERIC);
+        }
+        trace_write<TRACE>(C, rel, ncoll - 1, status, rx, ry, rz, dx, dy, dz, status == 4 ? 0.f : w, nee,
+                           pix, nb, -1);
+    }
+}
+
+template <int PHASE, bool SMEM_IMAGE, bool TRACE>
+__global__ void __launch_bounds__(1024) grid_kernel(const __grid_constant__ GridArgs A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    Smem S = carve<PHASE, SMEM_IMAGE>(smem, A.c);
+    zero_tallies(S, A.c);
+    if (threadIdx.x == 0) mbar_init(S.bar);
+    const uint32_t tb = (PHASE != MC_PHASE_HG) ? A.c.table_bytes : 0u;
+    float *s_maj = reinterpret_cast<float *>(smem + tb);
+    uint32_t parity = 0u;
+    if (PHASE != MC_PHASE_HG) {
+        if (!stage_bulk(S.table, A.m.table, A.c.table_bytes, S.bar, parity, A.c.error)) return;
+        parity ^= 1u;
+        if (!bind_table<PHASE>(S, A.c)) return;
+    }
+    if (!stage_bulk(s_maj, A.maj, A.c.extra_bytes, S.bar, parity, A.c.error)) return;
+    Tally T{0ull, 0ll, 0ll, 0ll, 0ll, 0ll};
+    grid_loop<PHASE, SMEM_IMAGE, TRACE>(A, S, s_maj, T);
+    flush<SMEM_IMAGE>(A.c, A.m, S, T);
+}
+
 // ------------------------------------------------------------------ adjoint
 // Gradient of L = sum_pix adj[pix] image[pix] with respect to (mu_s, mu_a)
 // and the hat-function phase weights w_k at w = 1 (p_w = p h_w / Z(w)), by
@@ -943,7 +1181,7 @@ cudaError_t launch_persistent(Kern kern, const void *args_unused, const LaunchCf
 // Where the image accumulates and how big the CTA is. Sets c.band0/band_rows.
 cudaError_t plan_image(CommonArgs &c, LaunchCfg &cfg, bool *smem_img, size_t *smem)
 {
-    const size_t tb = (c.phase_kind != MC_PHASE_HG) ? c.table_bytes : 0;
+    const size_t tb = ((c.phase_kind != MC_PHASE_HG) ? c.table_bytes : 0) + c.extra_bytes;
     const size_t tail = sizeof(unsigned long long) * (c.n_radial + MC_N_TOTALS + 3);
     const size_t row = sizeof(unsigned long long) * (size_t)c.nx;
     int dev = 0, optin = 0;
@@ -1005,6 +1243,17 @@ cudaError_t launch_batch_one(const BatchArgs &a, const LaunchCfg &cfg, size_t sm
     return cudaGetLastError();
 }
 
+
+template <int PHASE, bool SMEM_IMAGE, bool TRACE>
+cudaError_t launch_grid_one(const GridArgs &a, const LaunchCfg &cfg, size_t smem, cudaStream_t st)
+{
+    auto kern = grid_kernel<PHASE, SMEM_IMAGE, TRACE>;
+    unsigned grid = 0;
+    cudaError_t e = launch_persistent(kern, &a, cfg, smem, (a.m.n_photons + CHUNK - 1) / CHUNK, &grid);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, cfg.block, smem, st>>>(a);
+    return cudaGetLastError();
+}
 }  // namespace
 
 cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, cudaStream_t st)
@@ -1028,6 +1277,31 @@ cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, c
     case 9: return launch_one<MC_PHASE_PAPER, false, true>(a, cfg, smem, st);
     case 10: return launch_one<MC_PHASE_PAPER, true, false>(a, cfg, smem, st);
     case 11: return launch_one<MC_PHASE_PAPER, true, true>(a, cfg, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_grid(const GridArgs &a0, bool trace, const LaunchCfg &cfg0, cudaStream_t st)
+{
+    GridArgs a = a0;
+    LaunchCfg cfg = cfg0;
+    bool smem_img = false;
+    size_t smem = 0;
+    cudaError_t e = plan_image(a.c, cfg, &smem_img, &smem);
+    if (e != cudaSuccess) return e;
+    switch (a.c.phase_kind * 4 + (smem_img ? 2 : 0) + (trace ? 1 : 0)) {
+    case 0: return launch_grid_one<MC_PHASE_TABLE, false, false>(a, cfg, smem, st);
+    case 1: return launch_grid_one<MC_PHASE_TABLE, false, true>(a, cfg, smem, st);
+    case 2: return launch_grid_one<MC_PHASE_TABLE, true, false>(a, cfg, smem, st);
+    case 3: return launch_grid_one<MC_PHASE_TABLE, true, true>(a, cfg, smem, st);
+    case 4: return launch_grid_one<MC_PHASE_HG, false, false>(a, cfg, smem, st);
+    case 5: return launch_grid_one<MC_PHASE_HG, false, true>(a, cfg, smem, st);
+    case 6: return launch_grid_one<MC_PHASE_HG, true, false>(a, cfg, smem, st);
+    case 7: return launch_grid_one<MC_PHASE_HG, true, true>(a, cfg, smem, st);
+    case 8: return launch_grid_one<MC_PHASE_PAPER, false, false>(a, cfg, smem, st);
+    case 9: return launch_grid_one<MC_PHASE_PAPER, false, true>(a, cfg, smem, st);
+    case 10: return launch_grid_one<MC_PHASE_PAPER, true, false>(a, cfg, smem, st);
+    case 11: return launch_grid_one<MC_PHASE_PAPER, true, true>(a, cfg, smem, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -68,6 +68,40 @@ class PhaseTable:
         return self._dev[key]
 
 
+class MixtureTable(PhaseTable):
+    """Phase table of a particle mixture (mie_mixture_table_build), e.g. the
+    size bins of a polydisperse sample with number fractions; info holds the
+    number-averaged cross sections (sigma_ext_mm2, ...) of one particle."""
+
+    def __init__(self, diameters_um, number_frac, n_particle=1.59 + 0j, n_medium=1.33, wavelength_nm=532.0,
+                 n_bins=4096):
+        L = N.lib()
+        n_particle = complex(n_particle)
+        d = [float(v) for v in diameters_um]
+        k = len(d)
+        ps = (N.MieParams * k)(*[N.MieParams(di, n_particle.real, n_particle.imag, n_medium, wavelength_nm,
+                                             n_bins) for di in d])
+        f = np.ascontiguousarray(number_frac, dtype=np.float64)
+        if f.size != k:
+            raise ValueError("one number fraction per diameter")
+        info = N.MieInfo()
+        nbytes = L.mc_table_bytes(n_bins)
+        if nbytes == 0:
+            raise N.McError("mc_table_bytes", -1)
+        self.blob = np.zeros(nbytes, dtype=np.uint8)
+        self.omu64 = np.zeros(n_bins + 1)
+        self.pdf64 = np.zeros(n_bins)
+        dp = C.POINTER(C.c_double)
+        N.check("mie_mixture_table_build", L.mie_mixture_table_build(
+            ps, f.ctypes.data_as(dp), k, C.byref(info), self.blob.ctypes.data_as(C.c_void_p),
+            self.omu64.ctypes.data_as(dp), self.pdf64.ctypes.data_as(dp)))
+        self.params = dict(diameters_um=d, number_frac=list(f), n_particle=n_particle, n_medium=n_medium,
+                           wavelength_nm=wavelength_nm, n_bins=n_bins, diameter_um=d[0])
+        self.info = info.as_dict()
+        self.n_bins = n_bins
+        self._dev = {}
+
+
 class PaperTable:
     """The paper's own sampling table (Sec. 3.1.2, mie_paper_table_build):
     the Mie phase function at n_theta equally spaced angles, its cumulative
@@ -177,6 +211,38 @@ def run_params(n_photons, seed=1, photon_offset=0, rr_threshold=1e-4, rr_surviva
                        int(block_size), int(blocks_per_sm), int(image_mode))
 
 
+class Grid:
+    """A heterogeneous medium: particle number density per voxel (float32
+    CUDA tensor [gz, gy, gx], per mm^3) with per-particle cross sections
+    k_ext, k_sca (mm^2), a uniform background absorption mu_a and majorant
+    cells of block = (bx, by, bz) voxels. prepare() builds the device
+    workspace mc_run_grid reads (redo it after changing the density)."""
+
+    def __init__(self, density, k_ext, k_sca, mu_a=0.0, block=(8, 16, 16)):
+        torch = _torch()
+        if density.dtype != torch.float32 or not density.is_cuda or density.dim() != 3:
+            raise ValueError("density must be a 3-d float32 CUDA tensor [gz, gy, gx]")
+        self.density = density.contiguous()
+        self.k_ext, self.k_sca, self.mu_a = float(k_ext), float(k_sca), float(mu_a)
+        self.block = tuple(int(b) for b in block)
+        g = self.as_c()
+        nbytes = N.lib().mc_grid_workspace_bytes(C.byref(g))
+        if nbytes == 0:
+            raise ValueError("invalid grid (sizes, cross sections or more than 16384 majorant cells)")
+        self.work = torch.empty(nbytes, dtype=torch.uint8, device=self.density.device)
+
+    def as_c(self):
+        gz, gy, gx = self.density.shape
+        return N.Grid(self.density.data_ptr(), gx, gy, gz, self.k_ext, self.k_sca, self.mu_a, *self.block)
+
+    def prepare(self, geometry, stream=None):
+        g, geo = self.as_c(), geometry.as_c()
+        N.check("mc_grid_prepare", N.lib().mc_grid_prepare(C.byref(g), C.byref(geo),
+                                                           C.c_void_p(self.work.data_ptr()), self.work.numel(),
+                                                           _stream_handle(stream)))
+        return self
+
+
 # -------------------------------------------------------------------- engine
 
 
@@ -255,6 +321,28 @@ class Engine:
             C.c_void_p(self._adj_work.data_ptr()), self._adj_work.numel(), _stream_handle(stream)))
         self._keep = (keep, adj)
         return out
+
+    def run_grid(self, grid, phase, n_photons, seed=1, stream=None, n_trace=0, n_events=32, **kw):
+        """Delta-tracking walk through a prepared Grid; `phase` is a Medium
+        whose phase function is used (its mu_s, mu_a are ignored). With
+        n_trace > 0 returns the raw trace of real events (decode_trace)."""
+        torch = _torch()
+        rp = run_params(n_photons, seed, **kw)
+        self.image_frac_bits = rp.image_frac_bits
+        m, keep = phase.as_c(self.device)
+        m.mu_s, m.mu_a = 1.0, 0.0
+        g, geo, c, t = grid.as_c(), self.geometry.as_c(), self.camera.as_c(), self._tallies()
+        tr = None
+        if n_trace:
+            tr = torch.empty(n_trace * n_events * N.TRACE_WORDS, dtype=torch.int32, device=self.device)
+        N.check("mc_run_grid", N.lib().mc_run_grid(
+            C.byref(g), C.c_void_p(grid.work.data_ptr()), C.byref(m), C.byref(geo), C.byref(c), C.byref(rp),
+            C.byref(t), C.c_void_p(tr.data_ptr()) if tr is not None else None, n_trace, n_events,
+            _stream_handle(stream)))
+        self._keep = (keep, grid)
+        if tr is not None:
+            return tr.view(n_trace, n_events, N.TRACE_WORDS)
+        return self
 
     def check(self, stream=None):
         """Wait for the stream and raise if a kernel flagged an error."""

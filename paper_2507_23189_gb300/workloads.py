@@ -11,6 +11,11 @@ images are not used.
   batched     64 media: d log-uniform in [1, 10] um, tau uniform in [0.5, 20],
               photon budgets log-uniform in [1e6, 1e8], 128x128 images
   adjoint     tau = 5, Mie, 1e7 photons, 128x128; target at 0.9 mu_s0, mu_a = 0.01
+  plume       256^3 voxel grid over the cuvette: a Gaussian plume (sigma 5 mm,
+              centred at x = 22.5 mm on the beam axis) of polystyrene spheres
+              with log-normal diameters (median 5 um, sigma_ln 0.3) in 16
+              equal-number quantile bins; peak optical depth 30 along the
+              beam; 1e9 photons, 512x512 image
 """
 from dataclasses import dataclass, field
 
@@ -68,3 +73,49 @@ def batched(n=64, seed=2026):
 def adjoint():
     return Case("adjoint-tau5-mie", 5.0, "mie", 10_000_000, 128, 128,
                 extra=dict(mu_s_factor=0.9, mu_a=0.01))
+
+
+@dataclass
+class Plume:
+    shape: tuple = (256, 256, 256)          # (gz, gy, gx)
+    sigma_mm: float = 5.0
+    center_x_mm: float = 22.5
+    tau_peak: float = 30.0                  # optical depth along the beam through the plume
+    median_um: float = 5.0
+    sigma_ln: float = 0.3
+    n_size_bins: int = 16
+    n_photons: int = 1_000_000_000
+    nx: int = 512
+    nz: int = 512
+    block: tuple = (8, 16, 16)              # majorant cells, voxels (bx, by, bz)
+    seed: int = 1
+
+
+def plume():
+    return Plume()
+
+
+def size_bins(median_um=5.0, sigma_ln=0.3, n=16):
+    """Diameters at the centres (in probability) of n equal-number quantile
+    bins of a log-normal distribution, with their number fractions."""
+    from scipy.special import ndtri
+    q = (np.arange(n) + 0.5) / n
+    return median_um * np.exp(sigma_ln * ndtri(q)), np.full(n, 1.0 / n)
+
+
+def plume_shape(shape=(256, 256, 256), cuvette=CUVETTE_MM, sigma_mm=5.0, center_x_mm=22.5):
+    """Relative density (peak 1) of a Gaussian plume at the voxel centres,
+    float32 [gz, gy, gx], the beam axis at y = z = 0."""
+    gz, gy, gx = shape
+    lx, ly, lz = cuvette
+    x = (np.arange(gx) + 0.5) * lx / gx - center_x_mm
+    y = (np.arange(gy) + 0.5) * ly / gy - ly / 2
+    z = (np.arange(gz) + 0.5) * lz / gz - lz / 2
+    e = lambda v: np.exp(-0.5 * (v / sigma_mm) ** 2)
+    return (e(z)[:, None, None] * e(y)[None, :, None] * e(x)[None, None, :]).astype(np.float32)
+
+
+def rough_grid(shape, seed, mean=1.0, spread=0.6):
+    """Seeded log-normal voxel field (a test input without structure)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    return (mean * np.exp(spread * rng.standard_normal(shape))).astype(np.float32)
