@@ -277,6 +277,64 @@ def paper_comparison(E, dev, steps, flush):
     return out
 
 
+def plume_leg(E, dev, steps, flush, n_photons=None):
+    """Heterogeneous medium at full size: a 256^3 Gaussian plume (sigma 5 mm,
+    centred at x = 22.5 mm) of polystyrene spheres with log-normal diameters
+    (median 5 um, sigma_ln 0.3, 16 quantile bins, one mixture table), peak
+    optical depth 30 along the beam, 512x512 image, 1e9 photons, delta
+    tracking with 8x16x16-voxel majorant cells. Times mc_grid_prepare and
+    mc_run_grid separately."""
+    import numpy as np
+    import torch
+    from paper_2507_23189_gb300 import workloads as W
+    P = W.plume()
+    n = int(n_photons or P.n_photons)
+    d, f = W.size_bins(P.median_um, P.sigma_ln, P.n_size_bins)
+    t0 = time.time()
+    tab = E.MixtureTable(d, f)
+    t_table = time.time() - t0
+    k_ext, k_sca = tab.info["sigma_ext_mm2"], tab.info["sigma_sca_mm2"]
+    shape = W.plume_shape(P.shape, (LX, LY, LZ), P.sigma_mm, P.center_x_mm)
+    gz, gy, gx = P.shape
+    rho0 = P.tau_peak / (k_ext * float(np.sum(shape[gz // 2, gy // 2, :].astype(np.float64))) * LX / gx)
+    dens = torch.from_numpy(shape).to(dev).mul_(rho0)
+    geo = E.Geometry(LX, LY, LZ, 0.0)
+    grid = E.Grid(dens, k_ext, k_sca, 0.0, P.block)
+    eng = E.Engine(E.Camera(P.nx, P.nz, N_RADIAL, R_MAX), geo, dev)
+    med = E.Medium(1.0, 0.0, "table", 0.0, tab)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        tot = 0.0
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps
+
+    t_prep = timed(lambda: grid.prepare(geo, stream), steps)
+    grid.prepare(geo, stream)
+    t_walk = timed(lambda: eng.run_grid(grid, med, n, seed=1, stream=stream), max(1, min(steps, 3)))
+    eng.check()
+    tentative = int(eng.totals[7].item())
+    res = eng.result()
+    return {"prepare_ms": t_prep, "walk_ms": t_walk, "photons_per_s": n / (t_walk * 1e-3),
+            "tentative_steps_per_s": tentative / (t_walk * 1e-3), "tentative_steps_per_photon": tentative / n,
+            "ballistic_fraction": float(res["totals"][6] / n), "expected_ballistic": math.exp(-P.tau_peak),
+            "mixture_table_build_s": t_table, "k_ext_mm2": k_ext, "k_sca_mm2": k_sca, "g": tab.info["g"],
+            "grid_bytes": grid.work.numel(),
+            "workload": "256^3 Gaussian plume (sigma 5 mm at x=22.5), 16 log-normal size bins (median 5 um, "
+                        "sigma_ln 0.3), peak tau 30 on the beam, %d photons, %dx%d image, cells %s" %
+                        (n, P.nx, P.nz, "x".join(map(str, P.block)))}
+
+
 def adjoint_comparison(E, dev, steps, flush):
     """Adjoint cost against the forward pass on the tau = 5 Mie cuvette with
     1e7 photons and a 128x128 image: mc_run vs mc_adjoint over the same
@@ -459,6 +517,7 @@ def run_engine(args):
         line["batched"] = batched_comparison(E, dev, args.steps, args.warmup, flush)
         line["adjoint"] = adjoint_comparison(E, dev, args.steps, flush)
         line["paper_mode"] = paper_comparison(E, dev, args.steps, flush)
+        line["plume"] = plume_leg(E, dev, args.steps, flush)
     if not args.no_peaks:
         from paper_2507_23189_gb300 import peaks
         pk = peaks.measure(dev)
