@@ -47,6 +47,8 @@ def lib():
         L.oracle_phase_table_mixture.restype = C.c_int
         L.oracle_phase_table_mixture.argtypes = [C.c_int, C.POINTER(C.c_int), dp, dp, dp, dp, dp, C.c_int,
                                                  C.c_int, dp, dp, dp, dp]
+        L.oracle_grid_adjoint.restype = C.c_int
+        L.oracle_grid_adjoint.argtypes = [C.POINTER(WalkCfg), dp, C.c_int, dp, dp]
         L.oracle_paper_cdf.restype = C.c_int
         L.oracle_paper_cdf.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                        C.c_int, dp]
@@ -283,6 +285,21 @@ def adjoint(adj, n_w=64, **walk_kw):
     if lib().oracle_adjoint(C.byref(cfg), _dp(a), n_w, _dp(g), _dp(g2), C.byref(v)):
         raise ValueError("oracle_adjoint: bad arguments")
     return dict(grad=g, grad_sq=g2, value=v.value, n_photons=cfg.n_photons)
+
+
+def grid_adjoint(adj, max_events=512, **walk_kw):
+    """Gradient of sum(adj * image) w.r.t. the voxel densities of
+    walk_kw["grid"]["density"]: dict(grad [gz, gy, gx], value)."""
+    cfg, keep = _walk_cfg(**walk_kw)
+    a = np.ascontiguousarray(adj, dtype=np.float64).ravel()
+    if a.size != cfg.nx * cfg.nz or not cfg.density:
+        raise ValueError("adjoint image size or grid missing")
+    g = np.zeros(cfg.gz * cfg.gy * cfg.gx)
+    v = C.c_double(0.0)
+    if lib().oracle_grid_adjoint(C.byref(cfg), _dp(a), max_events, _dp(g), C.byref(v)):
+        raise ValueError("oracle_grid_adjoint failed (arguments, or a photon with more real events than "
+                         "max_events)")
+    return dict(grad=g.reshape(cfg.gz, cfg.gy, cfg.gx), value=v.value)
 
 
 def _walk_cfg(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,

@@ -289,3 +289,181 @@ int oracle_adjoint(const oracle_walk_cfg *c, const double *adj, int n_w, double 
     free(z);
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Gradient of L = sum adj * image with respect to the voxel densities n_v of
+ * a heterogeneous medium (oracle_walk_cfg.density; delta tracking in
+ * walk.c). The paths are the oracle walk's own, read from its traces of real
+ * events. For a photon with real collisions at r_1..r_J (entry point r_0),
+ * camera terms c_j and A_j = adj[pix_j] c_j, P_i = A_1 + .. + A_i:
+ *   flight i (r_{i-1} -> r_i) has density mu_s(r_i) exp(-int mu_ext) times
+ *   the scattering share, so d log / d n_v = [r_i in v] / n_v - k_ext l_i(v)
+ *   (l_i(v): length of the flight inside voxel v), and it multiplies every
+ *   later camera term: coefficient P_J - P_{i-1};
+ *   camera term j: d log c_j / d n_v = -k_ext lc_j(v), lc_j(v) the length of
+ *   the column from r_j up to y = +ly/2 inside v.
+ * (With mu_a = 0 the point term 1/n_v equals k_ext / mu_ext; with mu_a > 0 it
+ * is k_ext / mu_ext from the flight plus 1/n_v - k_ext / mu_ext from the
+ * albedo k_sca n_v / mu_ext.) Roulette is held fixed. The escaping flight
+ * precedes no camera term.
+ * ------------------------------------------------------------------------ */
+
+static int cmp_dbl(const void *x, const void *y)
+{
+    double a = *(const double *)x, b = *(const double *)y;
+    return (a > b) - (a < b);
+}
+
+static void voxel_of(const oracle_walk_cfg *c, const double lo[3], const double r[3], int v[3])
+{
+    const double L[3] = {c->lx, c->ly, c->lz};
+    const int g[3] = {c->gx, c->gy, c->gz};
+    for (int i = 0; i < 3; ++i) {
+        v[i] = (int)floor((r[i] - lo[i]) / L[i] * g[i]);
+        if (v[i] < 0) v[i] = 0;
+        if (v[i] > g[i] - 1) v[i] = g[i] - 1;
+    }
+}
+
+/* grad[v] += coef * (length of the segment a -> b inside v), every v: the
+ * segment is cut at every voxel plane it crosses and each piece is given to
+ * the voxel holding its midpoint. */
+static void segment_voxels(const oracle_walk_cfg *c, const double lo[3], const double a[3],
+                           const double b[3], double coef, double *grad, double *ts, size_t ts_cap)
+{
+    const double L[3] = {c->lx, c->ly, c->lz};
+    const int g[3] = {c->gx, c->gy, c->gz};
+    double d[3], len = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        d[i] = b[i] - a[i];
+        len += d[i] * d[i];
+    }
+    len = sqrt(len);
+    if (!(len > 0.0))
+        return;
+    size_t n = 0;
+    ts[n++] = 0.0;
+    ts[n++] = 1.0;
+    for (int i = 0; i < 3; ++i) {
+        if (d[i] == 0.0)
+            continue;
+        const double h = L[i] / g[i];
+        double fa = (a[i] - lo[i]) / h, fb = (b[i] - lo[i]) / h;
+        int k0 = (int)floor(fmin(fa, fb)) + 1, k1 = (int)ceil(fmax(fa, fb)) - 1;
+        for (int k = k0; k <= k1 && n < ts_cap; ++k)
+            ts[n++] = (lo[i] + k * h - a[i]) / d[i];
+    }
+    qsort(ts, n, sizeof *ts, cmp_dbl);
+    for (size_t q = 0; q + 1 < n; ++q) {
+        const double t0 = fmax(ts[q], 0.0), t1 = fmin(ts[q + 1], 1.0);
+        if (!(t1 > t0))
+            continue;
+        double m[3];
+        for (int i = 0; i < 3; ++i)
+            m[i] = a[i] + 0.5 * (t0 + t1) * d[i];
+        int v[3];
+        voxel_of(c, lo, m, v);
+        grad[((size_t)v[2] * c->gy + v[1]) * c->gx + v[0]] += coef * (t1 - t0) * len;
+    }
+}
+
+int oracle_grid_adjoint(const oracle_walk_cfg *c, const double *adj, int max_events, double *grad,
+                        double *value)
+{
+    if (!c || !c->density || !adj || !grad || !value || max_events < 2)
+        return -1;
+    const size_t nv = (size_t)c->gx * c->gy * c->gz;
+    const double lo[3] = {0.0, -0.5 * c->ly, -0.5 * c->lz};
+    const double hi1 = 0.5 * c->ly;
+    const double vy = c->ly / c->gy;
+    const uint32_t key[2] = {(uint32_t)c->seed, (uint32_t)(c->seed >> 32)};
+    const uint64_t batch = 2048;
+    oracle_trace_rec *tr = malloc(batch * (size_t)max_events * sizeof *tr);
+    double *A = malloc((size_t)max_events * sizeof *A);
+    const size_t ts_cap = (size_t)c->gx + c->gy + c->gz + 8;
+    double *ts = malloc(ts_cap * sizeof *ts);
+    if (!tr || !A || !ts) {
+        free(tr); free(A); free(ts);
+        return -1;
+    }
+    memset(grad, 0, nv * sizeof *grad);
+    double val = 0.0;
+    int rc = 0;
+    for (uint64_t first = 0; first < c->n_photons && rc == 0; first += batch) {
+        const uint64_t cnt = (c->n_photons - first < batch) ? c->n_photons - first : batch;
+        oracle_walk_cfg cb = *c;
+        cb.photon_offset = c->photon_offset + first;
+        cb.n_photons = cnt;
+        cb.nx = c->nx;
+        oracle_walk_out out;
+        memset(&out, 0, sizeof out);
+        if (oracle_walk(&cb, &out, tr, (int)cnt, max_events)) {
+            rc = -1;
+            break;
+        }
+        for (uint64_t q = 0; q < cnt; ++q) {
+            const oracle_trace_rec *R = tr + q * (size_t)max_events;
+            const uint64_t p = cb.photon_offset + q;
+            /* real collisions of the photon, and its camera terms */
+            int J = 0, ended = 0;
+            for (int e = 0; e < max_events; ++e) {
+                const int st = (int)R[e].status;
+                if (st < 0) { ended = 1; break; }
+                if (st == 0 || st == 4 || st == 5) {
+                    A[J++] = adj[(int)R[e].pix] * R[e].nee;
+                    if (st != 0) { ended = 1; break; }
+                } else {
+                    ended = 1;   /* left the cuvette or truncated */
+                    break;
+                }
+            }
+            if (!ended) {
+                rc = -1;   /* more real events than max_events */
+                break;
+            }
+            double P = 0.0;
+            for (int j = 0; j < J; ++j)
+                P += A[j];
+            val += P;
+            double r0[3] = {0.0, 0.0, 0.0};
+            if (c->beam_radius > 0.0) {
+                uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0xFFFFFFFFu, 0u}, o[4];
+                oracle_philox4x32_10(ctr, key, o);
+                double rho = c->beam_radius * sqrt(oracle_uniform(o[0]));
+                double psi = 2.0 * M_PI * oracle_uniform(o[1]);
+                r0[1] = rho * cos(psi);
+                r0[2] = rho * sin(psi);
+            }
+            double prev[3] = {r0[0], r0[1], r0[2]}, Pb = 0.0;
+            for (int i = 0; i < J; ++i) {
+                const double *ri = R[i].r;
+                const double B = P - Pb;   /* camera terms from collision i on */
+                int v[3];
+                voxel_of(c, lo, ri, v);
+                const size_t vi = ((size_t)v[2] * c->gy + v[1]) * c->gx + v[0];
+                const double n_v = c->density[vi];
+                const double mu = c->k_ext * n_v + c->mu_a;
+                if (B != 0.0) {
+                    /* flight: point term and transmission along the flight */
+                    grad[vi] += B * c->k_ext / mu;
+                    if (c->mu_a > 0.0 && n_v > 0.0)
+                        grad[vi] += B * (1.0 / n_v - c->k_ext / mu);
+                    segment_voxels(c, lo, prev, ri, -B * c->k_ext, grad, ts, ts_cap);
+                }
+                /* camera term i: its column up to the camera face */
+                if (A[i] != 0.0) {
+                    const double top = (v[1] == c->gy - 1) ? hi1 : lo[1] + (v[1] + 1) * vy;
+                    grad[vi] -= A[i] * c->k_ext * (top - ri[1]);
+                    for (int j = v[1] + 1; j < c->gy; ++j)
+                        grad[((size_t)v[2] * c->gy + j) * c->gx + v[0]] -= A[i] * c->k_ext * vy;
+                }
+                Pb += A[i];
+                for (int k = 0; k < 3; ++k)
+                    prev[k] = ri[k];
+            }
+        }
+    }
+    free(tr); free(A); free(ts);
+    *value = val;
+    return rc;
+}

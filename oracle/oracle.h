@@ -239,6 +239,13 @@ void oracle_hat_integrals(const double *omu, int n_bins, int n_w, double *z);
 int oracle_adjoint(const oracle_walk_cfg *cfg, const double *adj, int n_w, double *grad,
                    double *grad_sq, double *value);
 
+/* Gradient of L = sum_pix adj[pix] image[pix] with respect to the voxel
+ * densities of c->density (delta-tracking walk), from the oracle walk's own
+ * paths; grad[gz*gy*gx] (overwritten), *value = L. max_events: trace room
+ * per photon (real events); -1 if a photon needs more. Roulette held fixed. */
+int oracle_grid_adjoint(const oracle_walk_cfg *c, const double *adj, int max_events, double *grad,
+                        double *value);
+
 #ifdef __cplusplus
 }
 #endif
