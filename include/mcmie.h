@@ -317,6 +317,26 @@ mc_status mc_run_grid(const mc_grid *grid, const void *d_grid_work, const mc_med
                       const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
                       const mc_tallies *tallies, void *d_trace, int n_trace, int n_events, void *stream);
 
+/* Gradient of L = sum_pix adj[pix] image[pix] (adj: d_adj_image, float
+ * [nz][nx], in the image's weight units) with respect to every voxel density
+ * n_v, on the photons mc_run_grid would run with the same arguments. Each
+ * photon runs twice on its Philox counters (the first pass sums its camera
+ * terms); every real flight i contributes B_i / n_v at its collision voxel
+ * (the scattering density k_sca n exp(-int mu_ext)) and -B_i k_ext times its
+ * length inside each voxel it crosses, B_i the camera terms from collision i
+ * on; every camera term contributes -A k_ext times the length of its column
+ * inside each voxel above the collision. Roulette factors are held fixed.
+ * d_grad: float [gz][gy][gx], overwritten (sums of double-precision atomics,
+ * rounded once; their last bits depend on scheduling); *d_value = L
+ * (double, fixed order).
+ * d_work: mc_grid_adjoint_workspace_bytes(grid) bytes. The paper has no
+ * gradients; this serves fitting the density of a heterogeneous medium. */
+size_t mc_grid_adjoint_workspace_bytes(const mc_grid *grid);
+mc_status mc_grid_adjoint(const mc_grid *grid, const void *d_grid_work, const mc_medium *phase,
+                          const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
+                          const float *d_adj_image, float *d_grad, double *d_value, uint32_t *d_error,
+                          void *d_work, size_t work_bytes, void *stream);
+
 /* Image comparison (Sec. 3.1.4: every image normalised the same way, here
  * min-max to [0, 1]; Table 3: RMSE and Pearson r over the pixels; Table 4:
  * radial profiles, i.e. means over n_r equal-width rings about the image

@@ -25,7 +25,8 @@ EXPORTS = ("mc_table_bytes", "mie_table_build", "mc_medium_from_density", "mc_wo
            "mc_status_string", "mc_run_static", "mc_batch_workspace_bytes", "mc_run_batch",
            "mc_adjoint_workspace_bytes", "mc_adjoint", "mc_paper_table_bytes", "mie_paper_table_build",
            "mc_metrics_out_len", "mc_metrics_workspace_bytes", "mc_image_metrics", "mie_mixture_table_build",
-           "mc_grid_workspace_bytes", "mc_grid_prepare", "mc_run_grid")
+           "mc_grid_workspace_bytes", "mc_grid_prepare", "mc_run_grid", "mc_grid_adjoint_workspace_bytes",
+           "mc_grid_adjoint")
 
 
 class McError(RuntimeError):
@@ -157,6 +158,11 @@ def lib():
     L.mc_run_grid.restype = C.c_int
     L.mc_run_grid.argtypes = [P(Grid), vp, P(Medium), P(Geometry), P(Camera), P(RunParams), P(Tallies), vp,
                               C.c_int, C.c_int, vp]
+    L.mc_grid_adjoint_workspace_bytes.restype = C.c_size_t
+    L.mc_grid_adjoint_workspace_bytes.argtypes = [P(Grid)]
+    L.mc_grid_adjoint.restype = C.c_int
+    L.mc_grid_adjoint.argtypes = [P(Grid), vp, P(Medium), P(Geometry), P(Camera), P(RunParams), vp, vp, vp, vp,
+                                  vp, C.c_size_t, vp]
     L.mc_status_string.restype = C.c_char_p
     L.mc_status_string.argtypes = [C.c_int]
     _lib = L

@@ -478,6 +478,35 @@ bool grid_dims(const mc_grid *g, int *mx, int *my, int *mz)
     return (long long)*mx * *my * *mz <= kMaxCells;
 }
 
+void fill_grid(mcx::GridArgs &a, const mc_grid *g, int mx, int my, int mz, const void *d_grid_work,
+               const mc_medium *m, const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
+               uint32_t *d_error, int64_t *image, int64_t *radial, int64_t *totals)
+{
+    std::memset(&a, 0, sizeof a);
+    fill_common(a.c, m, geom, camera, run, d_error);
+    fill_medium(a.m, m, run->n_photons, run->photon_offset, run->seed, image, radial, totals);
+    const unsigned char *w = static_cast<const unsigned char *>(d_grid_work);
+    a.cells = reinterpret_cast<const float2 *>(w);
+    a.maj = reinterpret_cast<const float *>(w + pad16(sizeof(float) * 2 * (size_t)g->gx * g->gy * g->gz));
+    a.c.extra_bytes = (uint32_t)pad16(sizeof(float) * (size_t)mx * my * mz);
+    a.gx = g->gx; a.gy = g->gy; a.gz = g->gz;
+    a.mx = mx; a.my = my; a.mz = mz;
+    a.inv_vx = (float)(g->gx / geom->lx);
+    a.inv_vy = (float)(g->gy / geom->ly);
+    a.inv_vz = (float)(g->gz / geom->lz);
+    a.vx = (float)(geom->lx / g->gx);
+    a.vy = (float)(geom->ly / g->gy);
+    a.vz = (float)(geom->lz / g->gz);
+    a.csx = (float)(g->bx * geom->lx / g->gx);
+    a.csy = (float)(g->by * geom->ly / g->gy);
+    a.csz = (float)(g->bz * geom->lz / g->gz);
+    a.inv_csx = (float)(g->gx / (g->bx * geom->lx));
+    a.inv_csy = (float)(g->gy / (g->by * geom->ly));
+    a.inv_csz = (float)(g->gz / (g->bz * geom->lz));
+    a.ks_over_ke = (float)(g->k_sca / g->k_ext);
+    a.mu_a = (float)g->mu_a;
+}
+
 }  // namespace
 
 size_t mc_grid_workspace_bytes(const mc_grid *g)
@@ -523,28 +552,8 @@ mc_status mc_run_grid(const mc_grid *g, const void *d_grid_work, const mc_medium
                     (uint64_t)n_trace > run->n_photons))
         return MC_ERR_ARG;
     mcx::GridArgs a;
-    std::memset(&a, 0, sizeof a);
-    fill_common(a.c, &m, geom, camera, run, tallies->d_error);
-    fill_medium(a.m, &m, run->n_photons, run->photon_offset, run->seed, tallies->d_image, tallies->d_radial,
-                tallies->d_totals);
-    const unsigned char *w = static_cast<const unsigned char *>(d_grid_work);
-    a.cells = reinterpret_cast<const float2 *>(w);
-    a.maj = reinterpret_cast<const float *>(w + pad16(sizeof(float) * 2 * (size_t)g->gx * g->gy * g->gz));
-    a.c.extra_bytes = (uint32_t)pad16(sizeof(float) * (size_t)mx * my * mz);
-    a.gx = g->gx; a.gy = g->gy; a.gz = g->gz;
-    a.mx = mx; a.my = my; a.mz = mz;
-    a.inv_vx = (float)(g->gx / geom->lx);
-    a.inv_vy = (float)(g->gy / geom->ly);
-    a.inv_vz = (float)(g->gz / geom->lz);
-    a.vy = (float)(geom->ly / g->gy);
-    a.csx = (float)(g->bx * geom->lx / g->gx);
-    a.csy = (float)(g->by * geom->ly / g->gy);
-    a.csz = (float)(g->bz * geom->lz / g->gz);
-    a.inv_csx = (float)(g->gx / (g->bx * geom->lx));
-    a.inv_csy = (float)(g->gy / (g->by * geom->ly));
-    a.inv_csz = (float)(g->gz / (g->bz * geom->lz));
-    a.ks_over_ke = (float)(g->k_sca / g->k_ext);
-    a.mu_a = (float)g->mu_a;
+    fill_grid(a, g, mx, my, mz, d_grid_work, &m, geom, camera, run, tallies->d_error, tallies->d_image,
+              tallies->d_radial, tallies->d_totals);
     a.counter = reinterpret_cast<unsigned long long *>(tallies->d_work);
     a.c.trace = static_cast<int32_t *>(d_trace);
     a.c.n_trace = d_trace ? n_trace : 0;
@@ -565,4 +574,56 @@ mc_status mc_run_grid(const mc_grid *g, const void *d_grid_work, const mc_medium
     const cudaError_t e = mcx::launch_grid(a, d_trace != nullptr, launch_cfg(run), st);
     if (e == cudaErrorInvalidValue) return MC_ERR_ARG;  // the shared-memory plan does not fit
     return cuda_status(e);
+}
+
+size_t mc_grid_adjoint_workspace_bytes(const mc_grid *g)
+{
+    int mx, my, mz;
+    if (!grid_dims(g, &mx, &my, &mz)) return 0;
+    const int rows = mcx::grid_adjoint_max_grid();
+    if (rows < 1) return 0;
+    const size_t n = (size_t)g->gx * g->gy * g->gz;
+    return kAlign + 3 * up(sizeof(double) * n) + up(sizeof(double) * (size_t)rows);
+}
+
+mc_status mc_grid_adjoint(const mc_grid *g, const void *d_grid_work, const mc_medium *phase,
+                          const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
+                          const float *d_adj_image, float *d_grad, double *d_value, uint32_t *d_error,
+                          void *d_work, size_t work_bytes, void *stream)
+{
+    int mx, my, mz;
+    mc_status s;
+    if (!grid_dims(g, &mx, &my, &mz) || !d_grid_work || !aligned(d_grid_work, 16) || !phase || !d_adj_image ||
+        !d_grad || !d_value || !d_error || !d_work || !aligned(d_adj_image, 4) || !aligned(d_grad, 4) ||
+        !aligned(d_value, 8) || !aligned(d_work, 16))
+        return MC_ERR_ARG;
+    mc_medium m = *phase;
+    m.mu_s = 1.0;
+    m.mu_a = 0.0;
+    if ((s = validate_all(&m, geom, camera, run)) != MC_OK) return s;
+    const size_t need = mc_grid_adjoint_workspace_bytes(g);
+    if (!need) return MC_ERR_CUDA;
+    if (work_bytes < need) return MC_ERR_NOMEM;
+    const size_t n = (size_t)g->gx * g->gy * g->gz;
+    unsigned char *w = static_cast<unsigned char *>(d_work);
+    mcx::GridAdjArgs a;
+    std::memset(&a, 0, sizeof a);
+    fill_grid(a.g, g, mx, my, mz, d_grid_work, &m, geom, camera, run, d_error, nullptr, nullptr, nullptr);
+    const size_t nb = up(sizeof(double) * n);
+    a.g.counter = reinterpret_cast<unsigned long long *>(w);
+    a.gsum = reinterpret_cast<double *>(w + kAlign);
+    a.s1 = reinterpret_cast<double *>(w + kAlign + nb);
+    a.s2 = reinterpret_cast<double *>(w + kAlign + 2 * nb);
+    a.partials = reinterpret_cast<double *>(w + kAlign + 3 * nb);
+    a.adj = d_adj_image;
+    a.grad = d_grad;
+    a.k_ext = (float)g->k_ext;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto fail = [](cudaError_t x) { return x != cudaSuccess; };
+    if (fail(cudaMemsetAsync(w, 0, kAlign + 3 * nb, st)) ||
+        fail(cudaMemsetAsync(d_grad, 0, sizeof(float) * n, st)) ||
+        fail(cudaMemsetAsync(d_value, 0, sizeof(double), st)))
+        return MC_ERR_CUDA;
+    if (run->n_photons == 0) return MC_OK;
+    return cuda_status(mcx::launch_grid_adjoint(a, mcx::grid_adjoint_max_grid(), d_value, st));
 }

@@ -90,11 +90,24 @@ struct GridArgs {
     const float *maj;             // [mz][my][mx], staged into shared memory
     int gx, gy, gz, mx, my, mz;
     float inv_vx, inv_vy, inv_vz; // voxels per mm
-    float vy;                     // voxel height, mm
+    float vx, vy, vz;             // voxel sizes, mm
     float csx, csy, csz;          // cell sizes, mm
     float inv_csx, inv_csy, inv_csz;
     float ks_over_ke, mu_a;       // albedo = ks_over_ke (1 - mu_a / mu_ext)
     unsigned long long *counter;
+};
+
+// Gradient of L = sum_pix adj[pix] image[pix] with respect to the voxel
+// densities (mc_grid_adjoint): flight terms straight into grad, camera
+// column terms as per-voxel sources s1 (A) and s2 (A times the distance to
+// the voxel's top) folded into grad by a column scan afterwards.
+struct GridAdjArgs {
+    GridArgs g;
+    const float *adj;             // [nz][nx]
+    double *gsum, *s1, *s2;       // [gz][gy][gx], double-precision atomic sums
+    float *grad;                  // [gz][gy][gx] output (written by the fold)
+    float k_ext;
+    double *partials;             // [grid] value per CTA
 };
 
 struct LaunchCfg {
@@ -124,6 +137,16 @@ cudaError_t launch_grid(const GridArgs &a, bool trace, const LaunchCfg &cfg, cud
 cudaError_t launch_grid_prepare(const float *density, int gx, int gy, int gz, int bx, int by, int bz,
                                 float k_ext, float mu_a, double vy, float2 *cells, float *maj,
                                 cudaStream_t stream);
+
+// Launch the density-gradient replay, the column fold and the value reduction.
+cudaError_t launch_grid_adjoint(const GridAdjArgs &a, int partial_rows, double *value, cudaStream_t stream);
+
+// grad[v] = gsum[v] - k_ext (s2[v] + vy * sum of s1 below v in its column).
+cudaError_t launch_column_fold(const double *gsum, const double *s1, const double *s2, float *grad, int gx,
+                               int gy, int gz, double k_ext, double vy, cudaStream_t stream);
+
+// CTAs the grid adjoint may use on the current device (for workspace sizing).
+int grid_adjoint_max_grid();
 
 // CTAs the adjoint launch may use on the current device (for workspace sizing).
 int adjoint_max_grid();

@@ -55,7 +55,33 @@ __global__ void __launch_bounds__(256) majorant_kernel(const float *__restrict__
     if (threadIdx.x == 0) maj[c] = fmaf(k_ext, red[0], mu_a);
 }
 
+// One thread per (x, z) column, upward: a collision in voxel iy adds A times
+// the distance to its voxel's top (s2) and A times a full voxel height to
+// every voxel above it (s1, summed below); the flight terms are in gsum.
+__global__ void fold_kernel(const double *__restrict__ gsum, const double *__restrict__ s1,
+                            const double *__restrict__ s2, float *__restrict__ grad, int gx, int gy, int gz,
+                            double k_ext, double vy)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)gx * gz) return;
+    const int iz = (int)(t / gx), ix = (int)(t - (long long)iz * gx);
+    double run = 0.0;
+    for (int iy = 0; iy < gy; ++iy) {
+        const size_t v = ((size_t)iz * gy + iy) * gx + ix;
+        grad[v] = (float)(gsum[v] - k_ext * (s2[v] + vy * run));
+        run += s1[v];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_column_fold(const double *gsum, const double *s1, const double *s2, float *grad, int gx,
+                               int gy, int gz, double k_ext, double vy, cudaStream_t st)
+{
+    const long long cols = (long long)gx * gz;
+    fold_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(gsum, s1, s2, grad, gx, gy, gz, k_ext, vy);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_grid_prepare(const float *density, int gx, int gy, int gz, int bx, int by, int bz,
                                 float k_ext, float mu_a, double vy, float2 *cells, float *maj,

@@ -626,6 +626,59 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ Bat
 // the distance to the voxel's top face)). One Philox call per tentative
 // collision; the voxel's (mu_ext, depth) pair is one 8-byte gather from the
 // L2-resident grid. Traces record real events only.
+
+// One tentative flight of delta tracking: spends optical depth tau cell by
+// cell at the cells' majorants (a DDA over the majorant cells in s_maj) from
+// r along d (id = 1/d per axis). Returns 3 at a tentative collision (r moved
+// there, mb = that cell's majorant), 0/1/2 when the flight leaves through an
+// x/y/z wall first (r on the wall), -1 if no exit plane exists or more cells
+// than the grid has were crossed (a non-finite direction).
+__device__ __forceinline__ int grid_flight(const GridArgs &G, const float *s_maj, float tau, float &rx,
+                                           float &ry, float &rz, float dx, float dy, float dz, float idx,
+                                           float idy, float idz, float &mb)
+{
+    const CommonArgs &C = G.c;
+    const float INF = __int_as_float(0x7f800000);
+    int cx = min(max(__float2int_rd(rx * G.inv_csx), 0), G.mx - 1);
+    int cy = min(max(__float2int_rd((ry + C.hy) * G.inv_csy), 0), G.my - 1);
+    int cz = min(max(__float2int_rd((rz + C.hz) * G.inv_csz), 0), G.mz - 1);
+    const int max_cross = G.mx + G.my + G.mz + 4;
+    for (int it = 0; it < max_cross; ++it) {
+        mb = s_maj[(cz * G.my + cy) * G.mx + cx];
+        float tx = INF, ty = INF, tz = INF;
+        if (dx > 0.f) tx = ((cx == G.mx - 1) ? C.lx : (float)(cx + 1) * G.csx) - rx;
+        else if (dx < 0.f) tx = ((cx == 0) ? 0.f : (float)cx * G.csx) - rx;
+        if (dy > 0.f) ty = ((cy == G.my - 1) ? C.hy : fmaf((float)(cy + 1), G.csy, -C.hy)) - ry;
+        else if (dy < 0.f) ty = ((cy == 0) ? -C.hy : fmaf((float)cy, G.csy, -C.hy)) - ry;
+        if (dz > 0.f) tz = ((cz == G.mz - 1) ? C.hz : fmaf((float)(cz + 1), G.csz, -C.hz)) - rz;
+        else if (dz < 0.f) tz = ((cz == 0) ? -C.hz : fmaf((float)cz, G.csz, -C.hz)) - rz;
+        tx = (dx != 0.f) ? fmaxf(tx * idx, 0.f) : INF;
+        ty = (dy != 0.f) ? fmaxf(ty * idy, 0.f) : INF;
+        tz = (dz != 0.f) ? fmaxf(tz * idz, 0.f) : INF;
+        const int ax = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
+        const float t = ax == 0 ? tx : (ax == 1 ? ty : tz);
+        if (mb * t > tau) {
+            const float sl = tau / mb;
+            rx = fmaf(sl, dx, rx); ry = fmaf(sl, dy, ry); rz = fmaf(sl, dz, rz);
+            return 3;
+        }
+        if (!(t < INF)) return -1;
+        tau = fmaf(-mb, t, tau);
+        rx = fmaf(t, dx, rx); ry = fmaf(t, dy, ry); rz = fmaf(t, dz, rz);
+        if (ax == 0) {
+            cx += dx > 0.f ? 1 : -1;
+            if (cx < 0 || cx >= G.mx) { rx = dx > 0.f ? C.lx : 0.f; return 0; }
+        } else if (ax == 1) {
+            cy += dy > 0.f ? 1 : -1;
+            if (cy < 0 || cy >= G.my) { ry = dy > 0.f ? C.hy : -C.hy; return 1; }
+        } else {
+            cz += dz > 0.f ? 1 : -1;
+            if (cz < 0 || cz >= G.mz) { rz = dz > 0.f ? C.hz : -C.hz; return 2; }
+        }
+    }
+    return -1;
+}
+
 template <int PHASE, bool SMEM_IMAGE, bool TRACE>
 __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, const float *s_maj, Tally &T)
 {
@@ -635,7 +688,6 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
     const unsigned lanemask_lt = (1u << lane) - 1u;
     unsigned long long pool_next = 0, pool_end = 0;
     unsigned long long *s_img = S.img, *s_rad = S.rad, *s_tot = S.tot;
-    const int max_cross = G.mx + G.my + G.mz + 4;
     const float INF = __int_as_float(0x7f800000);
 
     bool alive = false, done = false;
@@ -704,48 +756,10 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
         float u3 = u01(rnd.w);
 
         // -------- one tentative flight
-        float tau = -logf(u01(rnd.x));
-        int cx = min(max(__float2int_rd(rx * G.inv_csx), 0), G.mx - 1);
-        int cy = min(max(__float2int_rd((ry + C.hy) * G.inv_csy), 0), G.my - 1);
-        int cz = min(max(__float2int_rd((rz + C.hz) * G.inv_csz), 0), G.mz - 1);
-        int face = -1;
         float mb = 0.f;
-        bool hit = false;
-        for (int it = 0; it < max_cross; ++it) {
-            mb = s_maj[(cz * G.my + cy) * G.mx + cx];
-            float tx = INF, ty = INF, tz = INF;
-            if (dx > 0.f) tx = ((cx == G.mx - 1) ? C.lx : (float)(cx + 1) * G.csx) - rx;
-            else if (dx < 0.f) tx = ((cx == 0) ? 0.f : (float)cx * G.csx) - rx;
-            if (dy > 0.f) ty = ((cy == G.my - 1) ? C.hy : fmaf((float)(cy + 1), G.csy, -C.hy)) - ry;
-            else if (dy < 0.f) ty = ((cy == 0) ? -C.hy : fmaf((float)cy, G.csy, -C.hy)) - ry;
-            if (dz > 0.f) tz = ((cz == G.mz - 1) ? C.hz : fmaf((float)(cz + 1), G.csz, -C.hz)) - rz;
-            else if (dz < 0.f) tz = ((cz == 0) ? -C.hz : fmaf((float)cz, G.csz, -C.hz)) - rz;
-            tx = (dx != 0.f) ? fmaxf(tx * idx, 0.f) : INF;
-            ty = (dy != 0.f) ? fmaxf(ty * idy, 0.f) : INF;
-            tz = (dz != 0.f) ? fmaxf(tz * idz, 0.f) : INF;
-            const int ax = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
-            const float t = ax == 0 ? tx : (ax == 1 ? ty : tz);
-            if (mb * t > tau) {
-                const float s = tau / mb;
-                rx = fmaf(s, dx, rx); ry = fmaf(s, dy, ry); rz = fmaf(s, dz, rz);
-                hit = true;
-                break;
-            }
-            if (!(t < INF)) { face = -2; break; }   // no exit plane: not a direction
-            tau = fmaf(-mb, t, tau);
-            rx = fmaf(t, dx, rx); ry = fmaf(t, dy, ry); rz = fmaf(t, dz, rz);
-            if (ax == 0) {
-                cx += dx > 0.f ? 1 : -1;
-                if (cx < 0 || cx >= G.mx) { rx = dx > 0.f ? C.lx : 0.f; face = 0; break; }
-            } else if (ax == 1) {
-                cy += dy > 0.f ? 1 : -1;
-                if (cy < 0 || cy >= G.my) { ry = dy > 0.f ? C.hy : -C.hy; face = 1; break; }
-            } else {
-                cz += dz > 0.f ? 1 : -1;
-                if (cz < 0 || cz >= G.mz) { rz = dz > 0.f ? C.hz : -C.hz; face = 2; break; }
-            }
-        }
-        if (!hit && face < 0) {
+        const int face = grid_flight(G, s_maj, -logf(u01(rnd.x)), rx, ry, rz, dx, dy, dz, idx, idy, idz, mb);
+        const bool hit = face == 3;
+        if (face < 0) {
             // a non-finite direction or more crossings than cells: give up on
             // the photon and say so
             atomicOr(C.error, MC_EFLAG_NUMERIC);
@@ -849,6 +863,233 @@ __global__ void __launch_bounds__(1024) grid_kernel(const __grid_constant__ Grid
     Tally T{0ull, 0ll, 0ll, 0ll, 0ll, 0ll};
     grid_loop<PHASE, SMEM_IMAGE, TRACE>(A, S, s_maj, T);
     flush<SMEM_IMAGE>(A.c, A.m, S, T);
+}
+
+
+// ------------------------------------------------ gradient w.r.t. densities
+// For a photon with real collisions r_1..r_J (entry r_0), camera terms
+// A_i = adj[pix_i] c_i and B_i = A_i + .. + A_J (the terms that flight i and
+// collision i precede): flight i adds B_i / n(r_i) at r_i's voxel (scattering
+// density k_sca n exp(-int mu)) and -B_i k_ext times its length inside every
+// voxel it crosses; camera term i adds -A_i k_ext times the length of its
+// column inside every voxel above r_i, gathered here as the sources s1 / s2
+// and folded by a column scan. A photon runs twice on its Philox counters:
+// the first pass sums its camera terms, the second replays it and scatters
+// the terms. Roulette factors are held fixed.
+constexpr int GADJ_BLOCK = 256;
+
+// grad[v] += coef * (length of the segment from p along d, of length len,
+// inside voxel v), by a DDA over the voxels.
+__device__ __forceinline__ void segment_scatter(const GridArgs &G, double *grad, float px, float py, float pz,
+                                                float dx, float dy, float dz, float idx, float idy, float idz,
+                                                float len, float coef)
+{
+    const CommonArgs &C = G.c;
+    const float INF = __int_as_float(0x7f800000);
+    int ix = min(max(__float2int_rd(px * G.inv_vx), 0), G.gx - 1);
+    int iy = min(max(__float2int_rd((py + C.hy) * G.inv_vy), 0), G.gy - 1);
+    int iz = min(max(__float2int_rd((pz + C.hz) * G.inv_vz), 0), G.gz - 1);
+    float t = 0.f;
+    const int max_cross = G.gx + G.gy + G.gz + 4;
+    for (int it = 0; it < max_cross; ++it) {
+        float tx = INF, ty = INF, tz = INF;
+        if (dx > 0.f) tx = ((float)(ix + 1) * G.vx - px) * idx;
+        else if (dx < 0.f) tx = ((float)ix * G.vx - px) * idx;
+        if (dy > 0.f) ty = (fmaf((float)(iy + 1), G.vy, -C.hy) - py) * idy;
+        else if (dy < 0.f) ty = (fmaf((float)iy, G.vy, -C.hy) - py) * idy;
+        if (dz > 0.f) tz = (fmaf((float)(iz + 1), G.vz, -C.hz) - pz) * idz;
+        else if (dz < 0.f) tz = (fmaf((float)iz, G.vz, -C.hz) - pz) * idz;
+        const int ax = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
+        const float tn = fminf(fmaxf(ax == 0 ? tx : (ax == 1 ? ty : tz), t), len);
+        if (tn > t) atomicAdd(&grad[((size_t)iz * G.gy + iy) * G.gx + ix], (double)coef * (double)(tn - t));
+        t = tn;
+        if (!(t < len)) return;
+        if (ax == 0) { ix += dx > 0.f ? 1 : -1; if (ix < 0 || ix >= G.gx) return; }
+        else if (ax == 1) { iy += dy > 0.f ? 1 : -1; if (iy < 0 || iy >= G.gy) return; }
+        else { iz += dz > 0.f ? 1 : -1; if (iz < 0 || iz >= G.gz) return; }
+    }
+}
+
+template <int PHASE>
+__global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_constant__ GridAdjArgs A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const GridArgs &G = A.g;
+    const CommonArgs &C = G.c;
+    const MediumArgs &M = G.m;
+    const uint32_t tb = (PHASE != MC_PHASE_HG) ? C.table_bytes : 0u;
+    float *s_maj = reinterpret_cast<float *>(smem + tb);
+    unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(smem + tb + C.extra_bytes);
+    double *s_red = reinterpret_cast<double *>(s_bar + 2);
+    Smem S = carve<MC_PHASE_HG, false>(smem, C);
+    S.table = smem;
+    if (threadIdx.x == 0) mbar_init(s_bar);
+    uint32_t parity = 0u;
+    if (PHASE != MC_PHASE_HG) {
+        if (!stage_bulk(smem, M.table, C.table_bytes, s_bar, parity, C.error)) return;
+        parity ^= 1u;
+        if (!bind_table<PHASE>(S, C)) return;
+    }
+    if (!stage_bulk(s_maj, G.maj, C.extra_bytes, s_bar, parity, C.error)) return;
+
+    const int lane = threadIdx.x & 31;
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+    const float INF = __int_as_float(0x7f800000);
+    unsigned long long pool_next = 0, pool_end = 0;
+    bool alive = false, done = false;
+    int pass = 0;
+    uint32_t pk0 = 0, pk1 = 0, ev = 0, ncoll = 0;
+    float rx = 0, ry = 0, rz = 0, dx = 1, dy = 0, dz = 0, w = 1;
+    float idx = 1, idy = INF, idz = INF;
+    float px = 0, py = 0, pz = 0;          // previous real collision (or the entry point)
+    float P = 0.f, Ptot = 0.f;             // running / total camera terms of the photon
+    double val = 0.0;
+
+    while (true) {
+        const unsigned need = __ballot_sync(FULL, !alive && !done);
+        if (need) {
+            const unsigned n_need = __popc(need), rank = __popc(need & lanemask_lt);
+            const unsigned long long avail = pool_end - pool_next;
+            unsigned long long mine;
+            if (avail >= n_need) {
+                mine = pool_next + rank;
+                pool_next += n_need;
+            } else {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(G.counter, (unsigned long long)CHUNK);
+                base = __shfl_sync(FULL, base, 0);
+                mine = (rank < avail) ? pool_next + rank : base + (rank - avail);
+                pool_next = base + (n_need - avail);
+                pool_end = base + CHUNK;
+            }
+            if (!alive && !done) {
+                if (mine < M.n_photons) {
+                    const unsigned long long p = M.photon_offset + mine;
+                    pk0 = (uint32_t)p;
+                    pk1 = (uint32_t)(p >> 32);
+                    pass = 0;
+                    alive = true;
+                    ev = 0;   // the state itself is set below (start of a pass)
+                    ncoll = 0xFFFFFFFFu;
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, alive)) break;
+        if (!alive) continue;
+
+        if (ncoll == 0xFFFFFFFFu) {
+            // start (or restart) the photon's pass at the entry point
+            ev = 0;
+            ncoll = 0;
+            rx = 0.f; ry = 0.f; rz = 0.f;
+            dx = 1.f; dy = 0.f; dz = 0.f;
+            idx = 1.f; idy = INF; idz = INF;
+            w = 1.f;
+            P = 0.f;
+            if (C.beam_r > 0.f) {
+                const uint4 b = philox10(make_uint4(pk0, pk1, 0xFFFFFFFFu, 0u), M.key0, M.key1);
+                const float rho = C.beam_r * sqrtf(u01(b.x));
+                float sp, cp;
+                sincospif(2.0f * u01(b.y), &sp, &cp);
+                ry = rho * cp;
+                rz = rho * sp;
+            }
+            px = rx; py = ry; pz = rz;
+        }
+
+        bool end = false;
+        if (ev >= C.max_events) {
+            if (pass == 0) atomicOr(C.error, MC_EFLAG_EVENTS);
+            end = true;
+        } else {
+            const uint4 rnd = philox10(make_uint4(pk0, pk1, ev, 0u), M.key0, M.key1);
+            ++ev;
+            const float u1 = u01(rnd.y), u2 = u01(rnd.z);
+            float u3 = u01(rnd.w);
+            float mb = 0.f;
+            const int face = grid_flight(G, s_maj, -logf(u01(rnd.x)), rx, ry, rz, dx, dy, dz, idx, idy, idz, mb);
+            if (face < 0) {
+                atomicOr(C.error, MC_EFLAG_NUMERIC);
+                end = true;
+            } else if (face < 3) {
+                end = true;   // left the cuvette: no camera term follows
+            } else {
+                const int ix = min(max(__float2int_rd(rx * G.inv_vx), 0), G.gx - 1);
+                const int iy = min(max(__float2int_rd((ry + C.hy) * G.inv_vy), 0), G.gy - 1);
+                const int iz = min(max(__float2int_rd((rz + C.hz) * G.inv_vz), 0), G.gz - 1);
+                const size_t v = ((size_t)iz * G.gy + iy) * G.gx + ix;
+                const float2 cell = __ldg(&G.cells[v]);
+                const float acc = cell.x / mb;
+                if (u3 < acc) {
+                    u3 = u3 / acc;
+                    ++ncoll;
+                    const float a = G.mu_a > 0.f ? G.ks_over_ke * (1.0f - G.mu_a / cell.x) : G.ks_over_ke;
+                    w = w * a;
+                    int nb, pix_x, pix_z;
+                    const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
+                    const float top = (iy == G.gy - 1) ? C.hy : fmaf((float)(iy + 1), G.vy, -C.hy);
+                    const float nee = w * psr * expf(-fmaf(cell.x, top - ry, cell.y));
+                    const int pix = camera_pixel(C, rx, rz, pix_x, pix_z);
+                    const float Aj = __ldg(&A.adj[pix]) * nee;
+                    if (pass == 1) {
+                        const float B = Ptot - P;
+                        const float dens = cell.x - G.mu_a;   // k_ext n_v
+                        if (B != 0.f) {
+                            if (dens > 0.f) atomicAdd(&A.gsum[v], (double)B * (double)A.k_ext / (double)dens);
+                            const float ex = rx - px, ey = ry - py, ez = rz - pz;
+                            const float len = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+                            segment_scatter(G, A.gsum, px, py, pz, dx, dy, dz, idx, idy, idz, len, -B * A.k_ext);
+                        }
+                        if (Aj != 0.f) {
+                            atomicAdd(&A.s1[v], (double)Aj);
+                            atomicAdd(&A.s2[v], (double)Aj * (double)(top - ry));
+                        }
+                    }
+                    P += Aj;
+                    px = rx; py = ry; pz = rz;
+                    if (C.max_scatter && ncoll >= C.max_scatter) {
+                        end = true;
+                    } else {
+                        rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
+                        idx = __frcp_rn(dx); idy = __frcp_rn(dy); idz = __frcp_rn(dz);
+                        if (w < C.rr_thr) {
+                            if (u3 < C.rr_surv) w = w * C.inv_rr_surv;
+                            else end = true;
+                        }
+                    }
+                }
+            }
+        }
+        if (end) {
+            if (pass == 0) {
+                Ptot = P;
+                val += (double)P;
+                if (P != 0.f) {
+                    pass = 1;
+                    ncoll = 0xFFFFFFFFu;   // replay
+                } else {
+                    alive = false;
+                }
+            } else {
+                alive = false;
+            }
+        }
+    }
+    // fixed-order block reduction of the value
+    val += __shfl_xor_sync(FULL, val, 16);
+    val += __shfl_xor_sync(FULL, val, 8);
+    val += __shfl_xor_sync(FULL, val, 4);
+    val += __shfl_xor_sync(FULL, val, 2);
+    val += __shfl_xor_sync(FULL, val, 1);
+    if (lane == 0) s_red[threadIdx.x / 32] = val;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x / 32); ++k) t += s_red[k];
+        A.partials[blockIdx.x] = t;
+    }
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -1254,6 +1495,31 @@ cudaError_t launch_grid_one(const GridArgs &a, const LaunchCfg &cfg, size_t smem
     kern<<<grid, cfg.block, smem, st>>>(a);
     return cudaGetLastError();
 }
+
+template <int PHASE>
+cudaError_t launch_grid_adjoint_one(const GridAdjArgs &a, int rows, double *value, cudaStream_t st)
+{
+    auto kern = grid_adjoint_kernel<PHASE>;
+    const size_t tb = (PHASE != MC_PHASE_HG) ? a.g.c.table_bytes : 0;
+    const size_t smem = tb + a.g.c.extra_bytes + 16 + sizeof(double) * (GADJ_BLOCK / 32);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, bps = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, GADJ_BLOCK, smem)) != cudaSuccess) return e;
+    if (bps < 1) return cudaErrorInvalidConfiguration;
+    long long grid = (long long)sms * bps;
+    const long long cap = (long long)((a.g.m.n_photons + CHUNK - 1) / CHUNK + GADJ_BLOCK / 32 - 1) / (GADJ_BLOCK / 32);
+    if (cap < grid) grid = cap < 1 ? 1 : cap;
+    if (grid > rows) grid = rows;
+    kern<<<(unsigned)grid, GADJ_BLOCK, smem, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_column_fold(a.gsum, a.s1, a.s2, a.grad, a.g.gx, a.g.gy, a.g.gz, (double)a.k_ext, (double)a.g.vy, st);
+    if (e != cudaSuccess) return e;
+    adjoint_reduce<<<1, 128, 0, st>>>(a.partials, (int)grid, 1, value);
+    return cudaGetLastError();
+}
 }  // namespace
 
 cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, cudaStream_t st)
@@ -1302,6 +1568,25 @@ cudaError_t launch_grid(const GridArgs &a0, bool trace, const LaunchCfg &cfg0, c
     case 9: return launch_grid_one<MC_PHASE_PAPER, false, true>(a, cfg, smem, st);
     case 10: return launch_grid_one<MC_PHASE_PAPER, true, false>(a, cfg, smem, st);
     case 11: return launch_grid_one<MC_PHASE_PAPER, true, true>(a, cfg, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int grid_adjoint_max_grid()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms * (2048 / GADJ_BLOCK);
+}
+
+cudaError_t launch_grid_adjoint(const GridAdjArgs &a, int rows, double *value, cudaStream_t st)
+{
+    if (rows < 1) return cudaErrorInvalidValue;
+    switch (a.g.c.phase_kind) {
+    case MC_PHASE_TABLE: return launch_grid_adjoint_one<MC_PHASE_TABLE>(a, rows, value, st);
+    case MC_PHASE_HG: return launch_grid_adjoint_one<MC_PHASE_HG>(a, rows, value, st);
+    case MC_PHASE_PAPER: return launch_grid_adjoint_one<MC_PHASE_PAPER>(a, rows, value, st);
     default: return cudaErrorInvalidValue;
     }
 }

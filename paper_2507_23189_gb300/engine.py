@@ -344,6 +344,32 @@ class Engine:
             return tr.view(n_trace, n_events, N.TRACE_WORDS)
         return self
 
+    def grid_adjoint(self, grid, phase, adj_image, n_photons, seed=1, stream=None, **kw):
+        """Gradient of sum(adj_image * image) w.r.t. the voxel densities of a
+        prepared Grid (mc_grid_adjoint) on the photons run_grid would use.
+        Returns (value tensor [1] float64, grad tensor [gz, gy, gx] float32),
+        both on the device; check() afterwards for device errors."""
+        torch = _torch()
+        rp = run_params(n_photons, seed, **kw)
+        m, keep = phase.as_c(self.device)
+        m.mu_s, m.mu_a = 1.0, 0.0
+        adj = adj_image.to(device=self.device, dtype=torch.float32).contiguous()
+        if tuple(adj.shape) != (self.camera.nz, self.camera.nx):
+            raise ValueError("adjoint image must be [nz, nx]")
+        g, geo, c = grid.as_c(), self.geometry.as_c(), self.camera.as_c()
+        nbytes = N.lib().mc_grid_adjoint_workspace_bytes(C.byref(g))
+        work = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        grad = torch.empty(tuple(grid.density.shape), dtype=torch.float32, device=self.device)
+        value = torch.empty(1, dtype=torch.float64, device=self.device)
+        self.error.zero_()
+        vp = C.c_void_p
+        N.check("mc_grid_adjoint", N.lib().mc_grid_adjoint(
+            C.byref(g), vp(grid.work.data_ptr()), C.byref(m), C.byref(geo), C.byref(c), C.byref(rp),
+            vp(adj.data_ptr()), vp(grad.data_ptr()), vp(value.data_ptr()), vp(self.error.data_ptr()),
+            vp(work.data_ptr()), work.numel(), _stream_handle(stream)))
+        self._keep = (keep, grid, adj, work)
+        return value, grad
+
     def check(self, stream=None):
         """Wait for the stream and raise if a kernel flagged an error."""
         N.check("mc_check", N.lib().mc_check(C.c_void_p(self.error.data_ptr()), _stream_handle(stream)))
