@@ -325,7 +325,15 @@ def plume_leg(E, dev, steps, flush, n_photons=None):
     eng.check()
     tentative = int(eng.totals[7].item())
     res = eng.result()
+    # gradient w.r.t. all 256^3 densities against the forward walk, 1e7 photons
+    n_adj = 10_000_000
+    adj = torch.rand((P.nz, P.nx), generator=torch.Generator().manual_seed(1)).to(dev)
+    t_fwd_adj = timed(lambda: eng.run_grid(grid, med, n_adj, seed=2, stream=stream), max(1, min(steps, 3)))
+    t_adj = timed(lambda: eng.grid_adjoint(grid, med, adj, n_adj, seed=2, stream=stream), max(1, min(steps, 3)))
+    eng.check()
     return {"prepare_ms": t_prep, "walk_ms": t_walk, "photons_per_s": n / (t_walk * 1e-3),
+            "density_gradient": {"photons": n_adj, "forward_ms": t_fwd_adj, "gradient_ms": t_adj,
+                                 "cost_vs_forward": t_adj / t_fwd_adj},
             "tentative_steps_per_s": tentative / (t_walk * 1e-3), "tentative_steps_per_photon": tentative / n,
             "ballistic_fraction": float(res["totals"][6] / n), "expected_ballistic": math.exp(-P.tau_peak),
             "mixture_table_build_s": t_table, "k_ext_mm2": k_ext, "k_sca_mm2": k_sca, "g": tab.info["g"],
