@@ -104,6 +104,10 @@ void fill_medium(mcx::MediumArgs &m, const mc_medium *med, uint64_t n_photons, u
     m.table = (med->phase_kind != MC_PHASE_HG) ? static_cast<const unsigned char *>(med->d_table) : nullptr;
     m.key0 = (uint32_t)seed;
     m.key1 = (uint32_t)(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        m.rk[2 * i] = m.key0 + (uint32_t)i * 0x9E3779B9u;
+        m.rk[2 * i + 1] = m.key1 + (uint32_t)i * 0xBB67AE85u;
+    }
     m.n_photons = n_photons;
     m.photon_offset = offset;
     m.image = reinterpret_cast<unsigned long long *>(image);

@@ -18,6 +18,7 @@ struct MediumArgs {
     float hg_K;                 // (1-g^2) / (4 pi)  (density per sr)
     const unsigned char *table; // packed blob in global memory (table_format.h)
     uint32_t key0, key1;        // Philox key (seed)
+    uint32_t rk[20];            // Philox round keys: rk[2i] = key0 + i W0, rk[2i+1] = key1 + i W1
     unsigned long long n_photons, photon_offset;
     unsigned long long *image, *radial, *totals;  // this medium's tallies
 };

@@ -48,6 +48,19 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
+// The same with the round keys precomputed (rk[2i], rk[2i+1]); when rk lives
+// in the kernel's parameter space the key XORs take it as an operand.
+__device__ __forceinline__ uint4 philox10(uint4 c, const uint32_t (&rk)[20])
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * i], lo1, hi0 ^ c.w ^ rk[2 * i + 1], lo0);
+    }
+    return c;
+}
+
 // (r >> 9) 2^-23 + 2^-24, exact: the float 1 + (r>>9) 2^-23 minus (1 - 2^-24).
 __device__ __forceinline__ float u01(uint32_t r)
 {
@@ -239,11 +252,16 @@ __device__ __forceinline__ float sample_omu(const MediumArgs &M, const CommonArg
 __device__ __forceinline__ void rotate(float &dx, float &dy, float &dz, float om, float u2)
 {
     const float mu = 1.0f - om;
-    const float st = sqrtf(fmaxf(om * (2.0f - om), 0.0f));
+    const float st2 = om * (2.0f - om);
+    const float st = st2 > 0.0f ? st2 * rsqrtf(st2) : 0.0f;
+    // phi = 2 pi u2 through the hardware sine / cosine, evaluated at
+    // phi - pi in [-pi, pi) where they are most accurate
     float sp, cp;
-    sincospif(2.0f * u2, &sp, &cp);
+    __sincosf(fmaf(6.28318530717958647692f, u2, -3.14159265358979323846f), &sp, &cp);
+    sp = -sp;
+    cp = -cp;
     const float sg = copysignf(1.0f, dz);
-    const float a = -__frcp_rn(sg + dz);
+    const float a = __fdividef(-1.0f, sg + dz);
     const float b = dx * dy * a;
     const float e1x = fmaf(sg * dx * dx, a, 1.0f), e1y = sg * b, e1z = -sg * dx;
     const float e2x = b, e2y = fmaf(dy * dy, a, sg), e2z = -dy;
@@ -355,7 +373,7 @@ __device__ void flush(const CommonArgs &C, const MediumArgs &M, const Smem &S, T
 // The photon walk over indices [.., limit) of medium M: every warp refills
 // lanes whose photon ended from chunks of `chunk` indices obtained by
 // grab() (called by lane 0), until the range is exhausted.
-template <int PHASE, bool SMEM_IMAGE, bool TRACE, class Grab>
+template <int PHASE, bool SMEM_IMAGE, bool TRACE, bool RK, class Grab>
 __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs &M, const Smem &S,
                                           unsigned long long limit, unsigned chunk, Grab grab,
                                           Tally &T)
@@ -421,12 +439,13 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
 
         // -------- one event
         const uint32_t e_now = ev;
-        const uint4 rnd = philox10(make_uint4(pk0, pk1, e_now, 0u), M.key0, M.key1);
+        const uint4 rnd = RK ? philox10(make_uint4(pk0, pk1, e_now, 0u), M.rk)
+                             : philox10(make_uint4(pk0, pk1, e_now, 0u), M.key0, M.key1);
         ++ev;
         ++T.steps;
         const float u0 = u01(rnd.x), u1 = u01(rnd.y), u2 = u01(rnd.z), u3 = u01(rnd.w);
 
-        const float s = -logf(u0) * M.inv_mu_ext;                 // Eq. 15
+        const float s = -__logf(u0) * M.inv_mu_ext;                 // Eq. 15
         const float px = fmaf(s, dx, rx), py = fmaf(s, dy, ry), pz = fmaf(s, dz, rz);
         const bool cx = !((px > 0.f) & (px < C.lx));
         const bool cy = !(fabsf(py) < C.hy);
@@ -490,7 +509,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
         // camera: next-event estimate toward +y
         int nb, ix, iz;
         const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
-        const float nee = w * psr * expf(-M.mu_ext * (C.hy - ry));
+        const float nee = w * psr * __expf(-M.mu_ext * (C.hy - ry));
         const int pix = camera_pixel(C, rx, rz, ix, iz);
         const float vf = nee * C.img_scale;
         if (vf < 4.0e18f) {
@@ -551,7 +570,7 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
     }
     Tally T{0ull, 0ll, 0ll, 0ll, 0ll, 0ll};
     unsigned long long *counter = A.counter;
-    walk_loop<PHASE, SMEM_IMAGE, TRACE>(A.c, A.m, S, A.m.n_photons, CHUNK,
+    walk_loop<PHASE, SMEM_IMAGE, TRACE, true>(A.c, A.m, S, A.m.n_photons, CHUNK,
                                         [counter]() { return atomicAdd(counter, (unsigned long long)CHUNK); },
                                         T);
     flush<SMEM_IMAGE>(A.c, A.m, S, T);
@@ -605,7 +624,7 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ Bat
         if (threadIdx.x == 0) *S.pool = start;
         __syncthreads();
         unsigned long long *pool = S.pool;
-        walk_loop<PHASE, SMEM_IMAGE, false>(
+        walk_loop<PHASE, SMEM_IMAGE, false, false>(
             B.c, M, S, end, BATCH_CHUNK,
             [pool]() { return atomicAdd(pool, (unsigned long long)BATCH_CHUNK); }, T);
         __syncthreads();
@@ -749,7 +768,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
             alive = false;
             continue;
         }
-        const uint4 rnd = philox10(make_uint4(pk0, pk1, ev, 0u), M.key0, M.key1);
+        const uint4 rnd = philox10(make_uint4(pk0, pk1, ev, 0u), M.rk);
         ++ev;
         ++T.steps;
         const float u1 = u01(rnd.y), u2 = u01(rnd.z);
@@ -757,7 +776,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
 
         // -------- one tentative flight
         float mb = 0.f;
-        const int face = grid_flight(G, s_maj, -logf(u01(rnd.x)), rx, ry, rz, dx, dy, dz, idx, idy, idz, mb);
+        const int face = grid_flight(G, s_maj, -__logf(u01(rnd.x)), rx, ry, rz, dx, dy, dz, idx, idy, idz, mb);
         const bool hit = face == 3;
         if (face < 0) {
             // a non-finite direction or more crossings than cells: give up on
@@ -807,7 +826,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
         int nb, pix_x, pix_z;
         const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
         const float top = (iy == G.gy - 1) ? C.hy : fmaf((float)(iy + 1), G.vy, -C.hy);
-        const float nee = w * psr * expf(-fmaf(cell.x, top - ry, cell.y));
+        const float nee = w * psr * __expf(-fmaf(cell.x, top - ry, cell.y));
         const int pix = camera_pixel(C, rx, rz, pix_x, pix_z);
         const float vf = nee * C.img_scale;
         if (vf < 4.0e18f) {
@@ -1004,12 +1023,12 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
             if (pass == 0) atomicOr(C.error, MC_EFLAG_EVENTS);
             end = true;
         } else {
-            const uint4 rnd = philox10(make_uint4(pk0, pk1, ev, 0u), M.key0, M.key1);
+            const uint4 rnd = philox10(make_uint4(pk0, pk1, ev, 0u), M.rk);
             ++ev;
             const float u1 = u01(rnd.y), u2 = u01(rnd.z);
             float u3 = u01(rnd.w);
             float mb = 0.f;
-            const int face = grid_flight(G, s_maj, -logf(u01(rnd.x)), rx, ry, rz, dx, dy, dz, idx, idy, idz, mb);
+            const int face = grid_flight(G, s_maj, -__logf(u01(rnd.x)), rx, ry, rz, dx, dy, dz, idx, idy, idz, mb);
             if (face < 0) {
                 atomicOr(C.error, MC_EFLAG_NUMERIC);
                 end = true;
@@ -1030,7 +1049,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                     int nb, pix_x, pix_z;
                     const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
                     const float top = (iy == G.gy - 1) ? C.hy : fmaf((float)(iy + 1), G.vy, -C.hy);
-                    const float nee = w * psr * expf(-fmaf(cell.x, top - ry, cell.y));
+                    const float nee = w * psr * __expf(-fmaf(cell.x, top - ry, cell.y));
                     const int pix = camera_pixel(C, rx, rz, pix_x, pix_z);
                     const float Aj = __ldg(&A.adj[pix]) * nee;
                     if (pass == 1) {
@@ -1265,10 +1284,10 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
             }
         }
 
-        const uint4 rnd = philox10(make_uint4(pk0, pk1, ev, 0u), M.key0, M.key1);
+        const uint4 rnd = philox10(make_uint4(pk0, pk1, ev, 0u), M.rk);
         ++ev;
         const float u0 = u01(rnd.x), u1 = u01(rnd.y), u2 = u01(rnd.z), u3 = u01(rnd.w);
-        const float s = -logf(u0) * M.inv_mu_ext;
+        const float s = -__logf(u0) * M.inv_mu_ext;
         const float px = fmaf(s, dx, rx), py = fmaf(s, dy, ry), pz = fmaf(s, dz, rz);
         bool end = !((px > 0.f) & (px < C.lx) & (fabsf(py) < C.hy) & (fabsf(pz) < C.hz));
         if (!end) {
@@ -1279,7 +1298,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
             int nb, ix, iz;
             const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
             const float l = C.hy - ry;
-            const float nee = w * psr * expf(-M.mu_ext * l);
+            const float nee = w * psr * __expf(-M.mu_ext * l);
             const int pix = camera_pixel(C, rx, rz, ix, iz);
             const float Aj = __ldg(&A.adj[pix]) * nee;
             P += Aj;
