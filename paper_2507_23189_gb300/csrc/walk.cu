@@ -197,9 +197,11 @@ __device__ __forceinline__ float camera_psr(const MediumArgs &M, const CommonArg
                                             float dy, int &nb)
 {
     if (PHASE == MC_PHASE_HG) {
+        // Eq. 11 per steradian, K t^(-3/2) with t = (1-g)^2 + 2g(1 - mu)
         const float t = fmaf(M.hg_two_g, 1.0f - dy, M.hg_a2);
+        const float r = rsqrtf(t);
         nb = -1;
-        return M.hg_K / (t * sqrtf(t));
+        return M.hg_K * (r * r * r);
     }
     if (PHASE == MC_PHASE_PAPER) {
         // uniform in theta on each interval: density per radian / sin(theta)
@@ -227,7 +229,7 @@ __device__ __forceinline__ float sample_omu(const MediumArgs &M, const CommonArg
 {
     if (PHASE == MC_PHASE_HG) {
         const float D = fmaf(M.hg_two_g, u1, M.hg_one_m_g);
-        return M.hg_A * (1.0f - u1) * fmaf(M.hg_g, u1, 1.0f) / (D * D);
+        return __fdividef(M.hg_A * (1.0f - u1) * fmaf(M.hg_g, u1, 1.0f), D * D);
     }
     if (PHASE == MC_PHASE_PAPER) {
         // bisection of the cumulative distribution on the uniform's integer
@@ -331,7 +333,7 @@ __device__ __forceinline__ bool bind_table(Smem &S, const CommonArgs &C)
 
 // Per-thread tallies, reduced when a CTA finishes a medium.
 struct Tally {
-    unsigned long long steps;
+    unsigned long long steps;   // flushed per medium; a thread's count per flush fits 32 bits
     long long refl, far, side, ball, abs;
 };
 
@@ -459,9 +461,11 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
             if ((int)cx + (int)cy + (int)cz == 1) {
                 face = cx ? 0 : (cy ? 1 : 2);
             } else {
-                const float tx = cx ? (dx > 0.f ? (C.lx - rx) / dx : (0.f - rx) / dx) : INF;
-                const float ty = cy ? (dy > 0.f ? (C.hy - ry) / dy : (-C.hy - ry) / dy) : INF;
-                const float tz = cz ? (dz > 0.f ? (C.hz - rz) / dz : (-C.hz - rz) / dz) : INF;
+                // several walls crossed: the nearest decides (approximate
+                // divisions; a different answer needs a near tie)
+                const float tx = cx ? __fdividef(dx > 0.f ? C.lx - rx : 0.f - rx, dx) : INF;
+                const float ty = cy ? __fdividef(dy > 0.f ? C.hy - ry : -C.hy - ry, dy) : INF;
+                const float tz = cz ? __fdividef(dz > 0.f ? C.hz - rz : -C.hz - rz, dz) : INF;
                 face = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
             }
             const long long wv = fix32(w);
@@ -473,9 +477,10 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
             } else if (face == 0) {
                 T.far += wv;
                 if (ncoll == 0) T.ball += wv;
-                const float t = (C.lx - rx) / dx;
+                const float t = __fdividef(C.lx - rx, dx);
                 ex = C.lx; ey = fmaf(t, dy, ry); ez = fmaf(t, dz, rz);
-                const float rho = sqrtf(fmaf(ey, ey, ez * ez));
+                const float r2 = fmaf(ey, ey, ez * ez);
+                const float rho = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
                 rb = min(__float2int_rd(rho * C.sr), C.n_radial - 1);
                 sadd64(&s_rad[rb], wv);
                 status = 2;
