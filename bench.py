@@ -41,16 +41,16 @@ SEED = 1
 # Work per photon-step = thread-instructions the kernel executes per sampled
 # flight on this workload, from ncu (smsp__thread_inst_executed.sum / steps);
 # DRAM bytes per launch from the same capture (None when stale).
-THREAD_INST_PER_STEP = 328.4          # ncu, 1e7-photon launch of this workload
-DRAM_BYTES_PER_LAUNCH = 601856        # same capture; fixed per launch (L2-resident tallies)
+THREAD_INST_PER_STEP = 255.6          # ncu, 1e7-photon launch of this workload
+DRAM_BYTES_PER_LAUNCH = 595712        # same capture; fixed per launch (L2-resident tallies)
 LANES_PER_SM = 128
 
 
 def _workload_config():
     return {
         "workload": "tau=5 Mie point of the optical-depth sweep: 10x10x45 mm water cuvette, 5 um "
-                    "polystyrene (n=1.59) at 532 nm, pencil beam, 4096-bin Mie table, 1e8 photons, "
-                    "256x256 side image + 128-bin radial profile, roulette 1e-4/0.1, seed 1",
+                    "polystyrene (n=1.59) at 532 nm, pencil beam, 4096-bin Mie table, %.0e photons, "
+                    "256x256 side image + 128-bin radial profile, roulette 1e-4/0.1, seed 1" % N_PHOTONS,
         "n_photons": N_PHOTONS, "tau": TAU, "phase": "mie", "image": [NZ, NX], "n_radial": N_RADIAL,
         "l2": "flushed between timed steps (512 MiB write)",
     }
