@@ -170,7 +170,10 @@ def batched_comparison(E, dev, steps, warmup, flush):
     nph = [c.n_photons for c in cases]
     cam, geo = E.Camera(128, 128, N_RADIAL, R_MAX), E.Geometry(LX, LY, LZ, 0.0)
     batch = E.Batch(len(media), cam, geo, dev)
-    tune = autotune.tune_batch(batch, media, nph)
+    if globals().get("NO_TUNE"):
+        tune = dict(item_photons=0, block_size=0, skipped=True)
+    else:
+        tune = autotune.tune_batch(batch, media, nph)
     kw = dict(item_photons=tune["item_photons"], block_size=tune["block_size"])
     stream = torch.cuda.current_stream(dev)
     for _ in range(warmup):
@@ -326,7 +329,7 @@ def plume_leg(E, dev, steps, flush, n_photons=None):
     tentative = int(eng.totals[7].item())
     res = eng.result()
     # gradient w.r.t. all 256^3 densities against the forward walk, 1e7 photons
-    n_adj = 10_000_000
+    n_adj = min(10_000_000, n)
     adj = torch.rand((P.nz, P.nx), generator=torch.Generator().manual_seed(1)).to(dev)
     t_fwd_adj = timed(lambda: eng.run_grid(grid, med, n_adj, seed=2, stream=stream), max(1, min(steps, 3)))
     t_adj = timed(lambda: eng.grid_adjoint(grid, med, adj, n_adj, seed=2, stream=stream), max(1, min(steps, 3)))
@@ -551,12 +554,40 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-launch comparison")
     ap.add_argument("--photons", type=int, default=N_PHOTONS,
                     help="photons per step (default: the workload's 1e8; smaller for profiling)")
+    ap.add_argument("--leg", choices=["batched", "adjoint", "paper", "plume"],
+                    help="run only this comparison leg and print its JSON (profiling aid)")
+    ap.add_argument("--no-tune", action="store_true", help="batched leg: default launch shape, no autotuning")
+    ap.add_argument("--plume-photons", type=int, default=None, help="plume leg: photons per walk")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # timing rule: at least three warm-up steps
     globals()["N_PHOTONS"] = args.photons
+    globals()["NO_TUNE"] = args.no_tune
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg:
+        return run_leg(args)
     return run_engine(args)
+
+
+def run_leg(args):
+    """One comparison leg on its own, for profiling its kernels."""
+    import torch
+    from paper_2507_23189_gb300 import build as B
+    B.build()
+    import paper_2507_23189_gb300 as E
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    if args.leg == "batched":
+        out = batched_comparison(E, dev, args.steps, args.warmup, flush)
+    elif args.leg == "adjoint":
+        out = adjoint_comparison(E, dev, args.steps, flush)
+    elif args.leg == "paper":
+        out = paper_comparison(E, dev, args.steps, flush)
+    else:
+        out = plume_leg(E, dev, args.steps, flush, n_photons=args.plume_photons)
+    print(json.dumps({"leg": args.leg, **out}))
+    return 0
 
 
 if __name__ == "__main__":
