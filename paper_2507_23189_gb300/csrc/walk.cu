@@ -661,43 +661,58 @@ __device__ __forceinline__ int grid_flight(const GridArgs &G, const float *s_maj
                                            float &ry, float &rz, float dx, float dy, float dz, float idx,
                                            float idy, float idz, float &mb)
 {
+    // Incremental DDA: distances along the flight (from its start r) to the
+    // next cell plane on each axis, t0 the distance travelled so far; each
+    // crossing recomputes only the crossed axis's next plane, from r. Signs
+    // are selects, not branches, so lanes flying different ways stay together.
     const CommonArgs &C = G.c;
     const float INF = __int_as_float(0x7f800000);
     int cx = min(max(__float2int_rd(rx * G.inv_csx), 0), G.mx - 1);
     int cy = min(max(__float2int_rd((ry + C.hy) * G.inv_csy), 0), G.my - 1);
     int cz = min(max(__float2int_rd((rz + C.hz) * G.inv_csz), 0), G.mz - 1);
+    const bool px = dx > 0.f, py = dy > 0.f, pz = dz > 0.f;
+    // next plane of cell c on an axis of cell size cs, lower wall lo, upper wall hi
+    auto plane = [](int c, int m, bool up, float cs, float lo, float hi) {
+        return up ? (c == m - 1 ? hi : fmaf((float)(c + 1), cs, lo)) : (c == 0 ? lo : fmaf((float)c, cs, lo));
+    };
+    float tx = dx != 0.f ? fmaxf((plane(cx, G.mx, px, G.csx, 0.f, C.lx) - rx) * idx, 0.f) : INF;
+    float ty = dy != 0.f ? fmaxf((plane(cy, G.my, py, G.csy, -C.hy, C.hy) - ry) * idy, 0.f) : INF;
+    float tz = dz != 0.f ? fmaxf((plane(cz, G.mz, pz, G.csz, -C.hz, C.hz) - rz) * idz, 0.f) : INF;
+    float t0 = 0.f;
     const int max_cross = G.mx + G.my + G.mz + 4;
     for (int it = 0; it < max_cross; ++it) {
         mb = s_maj[(cz * G.my + cy) * G.mx + cx];
-        float tx = INF, ty = INF, tz = INF;
-        if (dx > 0.f) tx = ((cx == G.mx - 1) ? C.lx : (float)(cx + 1) * G.csx) - rx;
-        else if (dx < 0.f) tx = ((cx == 0) ? 0.f : (float)cx * G.csx) - rx;
-        if (dy > 0.f) ty = ((cy == G.my - 1) ? C.hy : fmaf((float)(cy + 1), G.csy, -C.hy)) - ry;
-        else if (dy < 0.f) ty = ((cy == 0) ? -C.hy : fmaf((float)cy, G.csy, -C.hy)) - ry;
-        if (dz > 0.f) tz = ((cz == G.mz - 1) ? C.hz : fmaf((float)(cz + 1), G.csz, -C.hz)) - rz;
-        else if (dz < 0.f) tz = ((cz == 0) ? -C.hz : fmaf((float)cz, G.csz, -C.hz)) - rz;
-        tx = (dx != 0.f) ? fmaxf(tx * idx, 0.f) : INF;
-        ty = (dy != 0.f) ? fmaxf(ty * idy, 0.f) : INF;
-        tz = (dz != 0.f) ? fmaxf(tz * idz, 0.f) : INF;
         const int ax = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
-        const float t = ax == 0 ? tx : (ax == 1 ? ty : tz);
-        if (mb * t > tau) {
-            const float sl = tau / mb;
+        const float t1 = fmaxf(ax == 0 ? tx : (ax == 1 ? ty : tz), t0);
+        if (mb * (t1 - t0) > tau) {
+            const float sl = t0 + tau / mb;
             rx = fmaf(sl, dx, rx); ry = fmaf(sl, dy, ry); rz = fmaf(sl, dz, rz);
             return 3;
         }
-        if (!(t < INF)) return -1;
-        tau = fmaf(-mb, t, tau);
-        rx = fmaf(t, dx, rx); ry = fmaf(t, dy, ry); rz = fmaf(t, dz, rz);
+        if (!(t1 < INF)) return -1;
+        tau = fmaf(-mb, t1 - t0, tau);
+        t0 = t1;
         if (ax == 0) {
-            cx += dx > 0.f ? 1 : -1;
-            if (cx < 0 || cx >= G.mx) { rx = dx > 0.f ? C.lx : 0.f; return 0; }
+            cx += px ? 1 : -1;
+            if (cx < 0 || cx >= G.mx) {
+                ry = fmaf(t1, dy, ry); rz = fmaf(t1, dz, rz); rx = px ? C.lx : 0.f;
+                return 0;
+            }
+            tx = fmaxf((plane(cx, G.mx, px, G.csx, 0.f, C.lx) - rx) * idx, t1);
         } else if (ax == 1) {
-            cy += dy > 0.f ? 1 : -1;
-            if (cy < 0 || cy >= G.my) { ry = dy > 0.f ? C.hy : -C.hy; return 1; }
+            cy += py ? 1 : -1;
+            if (cy < 0 || cy >= G.my) {
+                rx = fmaf(t1, dx, rx); rz = fmaf(t1, dz, rz); ry = py ? C.hy : -C.hy;
+                return 1;
+            }
+            ty = fmaxf((plane(cy, G.my, py, G.csy, -C.hy, C.hy) - ry) * idy, t1);
         } else {
-            cz += dz > 0.f ? 1 : -1;
-            if (cz < 0 || cz >= G.mz) { rz = dz > 0.f ? C.hz : -C.hz; return 2; }
+            cz += pz ? 1 : -1;
+            if (cz < 0 || cz >= G.mz) {
+                rx = fmaf(t1, dx, rx); ry = fmaf(t1, dy, ry); rz = pz ? C.hz : -C.hz;
+                return 2;
+            }
+            tz = fmaxf((plane(cz, G.mz, pz, G.csz, -C.hz, C.hz) - rz) * idz, t1);
         }
     }
     return -1;
