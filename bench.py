@@ -118,6 +118,27 @@ def _dist():
     return ws, rank, local
 
 
+def photon_range(rank, n_per_rank):
+    """Weak scaling: rank r runs photons [r n, (r + 1) n). Photons are keyed by
+    their global index in the Philox counter, so ranks draw disjoint streams
+    and the union is exactly the single-GPU run of ws * n photons."""
+    return rank * n_per_rank, n_per_rank
+
+
+def job_rate(t_local_s, steps_local, ws, device):
+    """Whole-job rate: photon-steps summed over ranks divided by the slowest
+    rank's time (max over ranks). Returns (rate, t_max, total_steps)."""
+    import torch
+    t = torch.tensor([t_local_s], dtype=torch.float64, device=device)
+    st = torch.tensor([float(steps_local)], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(st, op=dist.ReduceOp.SUM)
+    t_max, total = float(t.item()), float(st.item())
+    return total / t_max, t_max, total
+
+
 def _cpu_model():
     try:
         for ln in open("/proc/cpuinfo"):
@@ -431,7 +452,7 @@ def run_engine(args):
     cam = E.Camera(NX, NZ, N_RADIAL, R_MAX)
     geo = E.Geometry(LX, LY, LZ, 0.0)
     eng = E.Engine(cam, geo, dev)
-    offset = rank * N_PHOTONS
+    offset, _ = photon_range(rank, N_PHOTONS)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -465,13 +486,7 @@ def run_engine(args):
     assert eng.result()["steps"] == steps_per_run
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_local = sum(ms) / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    st = torch.tensor([steps_per_run * args.steps], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(st, op=torch.distributed.ReduceOp.SUM)
-    t_max, total_steps = float(t.item()), float(st.item())
-    value = total_steps / t_max
+    value, t_max, total_steps = job_rate(t_local, steps_per_run * args.steps, ws, dev)
 
     # end to end through the host-buffer entry point: table in, tallies out
     import numpy as np
