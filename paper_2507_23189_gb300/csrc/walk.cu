@@ -86,6 +86,18 @@ __device__ __forceinline__ void sadd64(unsigned long long *p, long long v)
     if (up) atomicAdd(w + 1, up);
 }
 
+// Image pixel add: the shared-memory band keeps only the low 32 bits of each
+// pixel; the contribution's high word and any wrap of the low word go to the
+// pixel in global memory at once, the low words at the flush. Exact and
+// order-independent (integer addition mod 2^64).
+__device__ __forceinline__ void band_add(uint32_t *cell, unsigned long long *gpix, long long v)
+{
+    const uint32_t lo = (uint32_t)v, hi = (uint32_t)((unsigned long long)v >> 32);
+    const uint32_t old = atomicAdd(cell, lo);
+    const uint32_t up = hi + ((uint32_t)(old + lo) < lo ? 1u : 0u);
+    if (up) atomicAdd(gpix, (unsigned long long)up << 32);
+}
+
 // mbarrier for the table copies; initialised once per CTA by thread 0.
 __device__ __forceinline__ void mbar_init(unsigned long long *mbar)
 {
@@ -163,7 +175,8 @@ __device__ __forceinline__ void trace_write(const CommonArgs &C, unsigned long l
 // per radian), pk / pdl / pri (search thresholds and interpolation aids).
 struct Smem {
     unsigned char *table;
-    unsigned long long *img, *rad, *tot, *bar, *item, *pool;
+    uint32_t *img;            // low 32 bits of the privatised image pixels
+    unsigned long long *rad, *tot, *bar, *item, *pool;
     int npix;                 // privatised image pixels (band rows x nx)
     const float *omu, *pdf;
     const uint16_t *guide;
@@ -280,8 +293,9 @@ __device__ __forceinline__ Smem carve(unsigned char *smem, const CommonArgs &C)
     const uint32_t tb = (PHASE != MC_PHASE_HG) ? C.table_bytes : 0u;
     S.table = smem;
     S.npix = SMEM_IMAGE ? C.nx * C.band_rows : 0;
-    S.img = reinterpret_cast<unsigned long long *>(smem + tb + C.extra_bytes);
-    S.rad = S.img + S.npix;
+    S.img = reinterpret_cast<uint32_t *>(smem + tb + C.extra_bytes);
+    S.rad = reinterpret_cast<unsigned long long *>(smem + tb + C.extra_bytes +
+                                                   ((sizeof(uint32_t) * (size_t)S.npix + 15) & ~(size_t)15));
     S.tot = S.rad + C.n_radial;
     S.bar = S.tot + MC_N_TOTALS;
     S.item = S.bar + 1;
@@ -296,7 +310,8 @@ __device__ __forceinline__ Smem carve(unsigned char *smem, const CommonArgs &C)
 
 __device__ __forceinline__ void zero_tallies(const Smem &S, const CommonArgs &C)
 {
-    for (int i = threadIdx.x; i < S.npix + C.n_radial + MC_N_TOTALS; i += blockDim.x) S.img[i] = 0ull;
+    for (int i = threadIdx.x; i < S.npix; i += blockDim.x) S.img[i] = 0u;
+    for (int i = threadIdx.x; i < C.n_radial + MC_N_TOTALS; i += blockDim.x) S.rad[i] = 0ull;
 }
 
 // Table pointers into the staged blob; false (and the error flag) if its
@@ -363,7 +378,7 @@ __device__ void flush(const CommonArgs &C, const MediumArgs &M, const Smem &S, T
     if (SMEM_IMAGE) {
         unsigned long long *g = M.image + (size_t)C.band0 * C.nx;
         for (int i = threadIdx.x; i < S.npix; i += blockDim.x)
-            if (S.img[i]) atomicAdd(&g[i], S.img[i]);
+            if (S.img[i]) atomicAdd(&g[i], (unsigned long long)S.img[i]);
     }
     for (int i = threadIdx.x; i < C.n_radial; i += blockDim.x)
         if (S.rad[i]) atomicAdd(&M.radial[i], S.rad[i]);
@@ -383,7 +398,8 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
     unsigned long long pool_next = 0, pool_end = 0;  // warp-uniform
-    unsigned long long *s_img = S.img, *s_rad = S.rad, *s_tot = S.tot;
+    uint32_t *s_img = S.img;
+    unsigned long long *s_rad = S.rad, *s_tot = S.tot;
 
     // photon state
     bool alive = false, done = false;
@@ -520,7 +536,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
         if (vf < 4.0e18f) {
             const long long v = __float2ll_rn(vf);
             const unsigned brow = (unsigned)(iz - C.band0);
-            if (SMEM_IMAGE && brow < (unsigned)C.band_rows) sadd64(&s_img[brow * C.nx + ix], v);
+            if (SMEM_IMAGE && brow < (unsigned)C.band_rows) band_add(&s_img[brow * C.nx + ix], &M.image[pix], v);
             else atomicAdd(&M.image[pix], (unsigned long long)v);
         } else {
             atomicOr(C.error, (vf == vf) ? MC_EFLAG_OVERFLOW : MC_EFLAG_NUMERIC);
@@ -726,7 +742,8 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
     unsigned long long pool_next = 0, pool_end = 0;
-    unsigned long long *s_img = S.img, *s_rad = S.rad, *s_tot = S.tot;
+    uint32_t *s_img = S.img;
+    unsigned long long *s_rad = S.rad, *s_tot = S.tot;
     const float INF = __int_as_float(0x7f800000);
 
     bool alive = false, done = false;
@@ -852,7 +869,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
         if (vf < 4.0e18f) {
             const long long v = __float2ll_rn(vf);
             const unsigned brow = (unsigned)(pix_z - C.band0);
-            if (SMEM_IMAGE && brow < (unsigned)C.band_rows) sadd64(&s_img[brow * C.nx + pix_x], v);
+            if (SMEM_IMAGE && brow < (unsigned)C.band_rows) band_add(&s_img[brow * C.nx + pix_x], &M.image[pix], v);
             else atomicAdd(&M.image[pix], (unsigned long long)v);
         } else {
             atomicOr(C.error, (vf == vf) ? MC_EFLAG_OVERFLOW : MC_EFLAG_NUMERIC);
@@ -1462,8 +1479,8 @@ cudaError_t launch_persistent(Kern kern, const void *args_unused, const LaunchCf
 cudaError_t plan_image(CommonArgs &c, LaunchCfg &cfg, bool *smem_img, size_t *smem)
 {
     const size_t tb = ((c.phase_kind != MC_PHASE_HG) ? c.table_bytes : 0) + c.extra_bytes;
-    const size_t tail = sizeof(unsigned long long) * (c.n_radial + MC_N_TOTALS + 3);
-    const size_t row = sizeof(unsigned long long) * (size_t)c.nx;
+    const size_t tail = sizeof(unsigned long long) * (c.n_radial + MC_N_TOTALS + 3) + 16;
+    const size_t row = sizeof(uint32_t) * (size_t)c.nx;
     int dev = 0, optin = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -1471,14 +1488,11 @@ cudaError_t plan_image(CommonArgs &c, LaunchCfg &cfg, bool *smem_img, size_t *sm
         return e;
     const size_t room = (size_t)optin > tb + tail + 1024 ? (size_t)optin - tb - tail - 1024 : 0;
     const int fit_rows = (int)(room / row);
-    // auto: a whole-image tile when two 256-thread CTAs per SM still fit;
-    // otherwise one 1024-thread CTA per SM holding as many rows around the
-    // beam as fit, the rest going to L2 atomics
+    // auto: one 1024-thread CTA per SM (32 warps) holding as many image rows
+    // around the beam as fit (the whole image when it fits), the rest going
+    // to L2 atomics
     int mode = cfg.image_mode;
-    if (mode == 0) {
-        if (tb + row * c.nz + tail <= (size_t)optin / 2 - 1024) mode = 1;
-        else mode = fit_rows >= 1 ? 3 : 2;
-    }
+    if (mode == 0) mode = fit_rows >= 1 ? 3 : 2;
     *smem_img = false;
     c.band0 = 0;
     c.band_rows = 0;
