@@ -61,6 +61,14 @@ __device__ __forceinline__ uint4 philox10(uint4 c, const uint32_t (&rk)[20])
     return c;
 }
 
+// 2^x by the hardware approximation (relative error a few 1e-7).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // (r >> 9) 2^-23 + 2^-24, exact: the float 1 + (r>>9) 2^-23 minus (1 - 2^-24).
 __device__ __forceinline__ float u01(uint32_t r)
 {
@@ -348,7 +356,7 @@ __device__ __forceinline__ bool bind_table(Smem &S, const CommonArgs &C)
 
 // Per-thread tallies, reduced when a CTA finishes a medium.
 struct Tally {
-    unsigned long long steps;   // flushed per medium; a thread's count per flush fits 32 bits
+    uint32_t steps;             // flushed per medium; a thread's count per flush fits 32 bits
     long long refl, far, side, ball, abs;
 };
 
@@ -356,9 +364,10 @@ struct Tally {
 template <bool SMEM_IMAGE>
 __device__ void flush(const CommonArgs &C, const MediumArgs &M, const Smem &S, Tally &T)
 {
+    unsigned long long steps = T.steps;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        T.steps += __shfl_xor_sync(FULL, T.steps, o);
+        steps += __shfl_xor_sync(FULL, steps, o);
         T.refl += __shfl_xor_sync(FULL, T.refl, o);
         T.far += __shfl_xor_sync(FULL, T.far, o);
         T.side += __shfl_xor_sync(FULL, T.side, o);
@@ -366,14 +375,14 @@ __device__ void flush(const CommonArgs &C, const MediumArgs &M, const Smem &S, T
         T.abs += __shfl_xor_sync(FULL, T.abs, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        sadd64(&S.tot[MC_TOT_STEPS], (long long)T.steps);
+        sadd64(&S.tot[MC_TOT_STEPS], (long long)steps);
         sadd64(&S.tot[MC_TOT_REFLECT], T.refl);
         sadd64(&S.tot[MC_TOT_FAR], T.far);
         sadd64(&S.tot[MC_TOT_SIDE], T.side);
         sadd64(&S.tot[MC_TOT_BALLISTIC], T.ball);
         sadd64(&S.tot[MC_TOT_ABSORB], T.abs);
     }
-    T = Tally{0ull, 0ll, 0ll, 0ll, 0ll, 0ll};
+    T = Tally{0u, 0ll, 0ll, 0ll, 0ll, 0ll};
     __syncthreads();
     if (SMEM_IMAGE) {
         unsigned long long *g = M.image + (size_t)C.band0 * C.nx;
@@ -398,6 +407,8 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
     unsigned long long pool_next = 0, pool_end = 0;  // warp-uniform
+    // camera transmittance exp(-mu_ext (ly/2 - r_y)) = 2^(cam_a r_y + cam_b)
+    const float cam_a = M.mu_ext * 1.44269504088896340736f, cam_b = -cam_a * C.hy;
     uint32_t *s_img = S.img;
     unsigned long long *s_rad = S.rad, *s_tot = S.tot;
 
@@ -530,7 +541,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
         // camera: next-event estimate toward +y
         int nb, ix, iz;
         const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
-        const float nee = w * psr * __expf(-M.mu_ext * (C.hy - ry));
+        const float nee = w * psr * ex2_approx(fmaf(cam_a, ry, cam_b));
         const int pix = camera_pixel(C, rx, rz, ix, iz);
         const float vf = nee * C.img_scale;
         if (vf < 4.0e18f) {
@@ -589,7 +600,7 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
     } else {
         __syncthreads();
     }
-    Tally T{0ull, 0ll, 0ll, 0ll, 0ll, 0ll};
+    Tally T{0u, 0ll, 0ll, 0ll, 0ll, 0ll};
     unsigned long long *counter = A.counter;
     walk_loop<PHASE, SMEM_IMAGE, TRACE, true>(A.c, A.m, S, A.m.n_photons, CHUNK,
                                         [counter]() { return atomicAdd(counter, (unsigned long long)CHUNK); },
@@ -613,7 +624,7 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ Bat
     if (threadIdx.x == 0) mbar_init(S.bar);
     __syncthreads();
     const unsigned long long n_items = B.item_begin[B.n_media];
-    Tally T{0ull, 0ll, 0ll, 0ll, 0ll, 0ll};
+    Tally T{0u, 0ll, 0ll, 0ll, 0ll, 0ll};
     int cur = -1;
     uint32_t parity = 0;
     while (true) {
@@ -916,7 +927,7 @@ __global__ void __launch_bounds__(1024) grid_kernel(const __grid_constant__ Grid
         if (!bind_table<PHASE>(S, A.c)) return;
     }
     if (!stage_bulk(s_maj, A.maj, A.c.extra_bytes, S.bar, parity, A.c.error)) return;
-    Tally T{0ull, 0ll, 0ll, 0ll, 0ll, 0ll};
+    Tally T{0u, 0ll, 0ll, 0ll, 0ll, 0ll};
     grid_loop<PHASE, SMEM_IMAGE, TRACE>(A, S, s_maj, T);
     flush<SMEM_IMAGE>(A.c, A.m, S, T);
 }
