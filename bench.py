@@ -177,18 +177,11 @@ def cpu_baseline(target_s=12.0):
             "photons_per_s": n / dt}
 
 
-def batched_comparison(E, dev, steps, warmup, flush):
-    """64 media of uneven optical depth, particle size and photon budget
-    (workloads.batched): one graph-replayed mc_run_batch against 64
-    sequential mc_run launches over the same photons (identical tallies)."""
+def _batch_vs_plain(E, dev, media, nph, steps, warmup, flush):
+    """One graph-replayed mc_run_batch against sequential mc_run launches over
+    the same photons (identical tallies required)."""
     import torch
-    from concurrent.futures import ThreadPoolExecutor
-    from paper_2507_23189_gb300 import autotune, workloads
-    cases = workloads.batched()
-    with ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
-        tables = list(ex.map(lambda c: E.PhaseTable(diameter_um=c.diameter_um), cases))
-    media = [E.Medium.from_optical_depth(t, c.tau, LX) for t, c in zip(tables, cases)]
-    nph = [c.n_photons for c in cases]
+    from paper_2507_23189_gb300 import autotune
     cam, geo = E.Camera(128, 128, N_RADIAL, R_MAX), E.Geometry(LX, LY, LZ, 0.0)
     batch = E.Batch(len(media), cam, geo, dev)
     if globals().get("NO_TUNE"):
@@ -242,10 +235,27 @@ def batched_comparison(E, dev, steps, warmup, flush):
             "plain_sequential": steps * steps_per_run / t_plain, "speedup": t_plain / t_batch,
             "ms_batched": 1e3 * t_batch / steps, "ms_plain": 1e3 * t_plain / steps,
             "media": len(media), "photons": int(sum(nph)), "photon_steps": steps_per_run,
-            "identical_tallies": same, "tuned": {k: tune[k] for k in ("block_size", "item_photons")},
-            "workload": "64 media: d log-uniform 1-10 um, tau uniform 0.5-20, photons log-uniform 1e6-1e8 "
-                        "(numpy Philox seed 2026), 128x128 image, Mie tables, graph-captured batch vs "
-                        "64 sequential launches"}
+            "identical_tallies": same, "tuned": {k: tune[k] for k in ("block_size", "item_photons")}}
+
+
+def batched_comparison(E, dev, steps, warmup, flush):
+    """64 media of uneven optical depth, particle size and photon budget
+    (workloads.batched): the batched launch against 64 sequential launches;
+    and the same 64 media at 2e5 photons each, where launches are short."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2507_23189_gb300 import workloads
+    cases = workloads.batched()
+    with ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
+        tables = list(ex.map(lambda c: E.PhaseTable(diameter_um=c.diameter_um), cases))
+    media = [E.Medium.from_optical_depth(t, c.tau, LX) for t, c in zip(tables, cases)]
+    out = _batch_vs_plain(E, dev, media, [c.n_photons for c in cases], steps, warmup, flush)
+    out["workload"] = ("64 media: d log-uniform 1-10 um, tau uniform 0.5-20, photons log-uniform 1e6-1e8 "
+                       "(numpy Philox seed 2026), 128x128 image, Mie tables, graph-captured batch vs "
+                       "64 sequential launches")
+    small = _batch_vs_plain(E, dev, media, [200_000] * len(media), steps, warmup, flush)
+    small["workload"] = "the same 64 media at 2e5 photons each"
+    out["small_budgets"] = small
+    return out
 
 
 def paper_comparison(E, dev, steps, flush):
