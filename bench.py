@@ -168,7 +168,7 @@ def cpu_baseline(target_s=12.0):
     """Oracle throughput on the host cores over a bounded sample."""
     steps, dt, threads = oracle_sample(200_000)
     rate = steps / dt
-    n = int(min(max(200_000 * target_s / max(dt, 1e-3), 200_000), N_PHOTONS))
+    n = int(min(max(200_000 * target_s / max(dt, 1e-3), 200_000), 10 * N_PHOTONS))
     steps, dt, threads = oracle_sample(n)
     s1, d1, _ = oracle_sample(max(n // (4 * threads), 20_000), n_threads=1)
     return {"value": steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
