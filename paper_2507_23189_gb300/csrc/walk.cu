@@ -1497,6 +1497,15 @@ cudaError_t plan_image(CommonArgs &c, LaunchCfg &cfg, bool *smem_img, size_t *sm
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
         return e;
+    // shared memory per CTA: all of it for one CTA per SM, an equal share
+    // (less the per-CTA reservation) when several are requested
+    int per_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+        return e;
+    if (cfg.blocks_per_sm > 1) {
+        const int share = per_sm / cfg.blocks_per_sm - 1024;
+        if (share < optin) optin = share;
+    }
     const size_t room = (size_t)optin > tb + tail + 1024 ? (size_t)optin - tb - tail - 1024 : 0;
     const int fit_rows = (int)(room / row);
     // auto: one 1024-thread CTA per SM (32 warps) holding as many image rows
