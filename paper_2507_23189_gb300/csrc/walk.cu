@@ -944,6 +944,7 @@ __global__ void __launch_bounds__(1024) grid_kernel(const __grid_constant__ Grid
 // the first pass sums its camera terms, the second replays it and scatters
 // the terms. Roulette factors are held fixed.
 constexpr int GADJ_BLOCK = 256;
+constexpr int GADJ_SEG = 11;     // floats per queued flight segment
 
 // grad[v] += coef * (length of the segment from p along d, of length len,
 // inside voxel v), by a DDA over the voxels.
@@ -988,6 +989,8 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
     float *s_maj = reinterpret_cast<float *>(smem + tb);
     unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(smem + tb + C.extra_bytes);
     double *s_red = reinterpret_cast<double *>(s_bar + 2);
+    // per-warp queue of flight segments to rasterise: (p, d, 1/d, length, coef)
+    float *s_seg = reinterpret_cast<float *>(s_red + GADJ_BLOCK / 32) + (threadIdx.x & ~31u) * GADJ_SEG;
     Smem S = carve<MC_PHASE_HG, false>(smem, C);
     S.table = smem;
     if (threadIdx.x == 0) mbar_init(s_bar);
@@ -1044,9 +1047,9 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
             }
         }
         if (!__any_sync(FULL, alive)) break;
-        if (!alive) continue;
+        bool seg = false;      // this lane queued a flight segment this round
 
-        if (ncoll == 0xFFFFFFFFu) {
+        if (alive && ncoll == 0xFFFFFFFFu) {
             // start (or restart) the photon's pass at the entry point
             ev = 0;
             ncoll = 0;
@@ -1067,7 +1070,9 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
         }
 
         bool end = false;
-        if (ev >= C.max_events) {
+        if (!alive) {
+            // nothing to walk; still takes part in the warp's rasterisation below
+        } else if (ev >= C.max_events) {
             if (pass == 0) atomicOr(C.error, MC_EFLAG_EVENTS);
             end = true;
         } else {
@@ -1106,8 +1111,12 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                         if (B != 0.f) {
                             if (dens > 0.f) atomicAdd(&A.gsum[v], (double)B * (double)A.k_ext / (double)dens);
                             const float ex = rx - px, ey = ry - py, ez = rz - pz;
-                            const float len = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-                            segment_scatter(G, A.gsum, px, py, pz, dx, dy, dz, idx, idy, idz, len, -B * A.k_ext);
+                            float *q = s_seg + lane * GADJ_SEG;
+                            q[0] = px; q[1] = py; q[2] = pz; q[3] = dx; q[4] = dy; q[5] = dz;
+                            q[6] = idx; q[7] = idy; q[8] = idz;
+                            q[9] = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+                            q[10] = -B * A.k_ext;
+                            seg = true;
                         }
                         if (Aj != 0.f) {
                             atomicAdd(&A.s1[v], (double)Aj);
@@ -1129,7 +1138,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                 }
             }
         }
-        if (end) {
+        if (alive && end) {
             if (pass == 0) {
                 Ptot = P;
                 val += (double)P;
@@ -1143,6 +1152,21 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                 alive = false;
             }
         }
+        // the warp rasterises each queued flight together: lane i takes the
+        // i-th of 32 equal pieces of it, so lanes with short or no flights
+        // do not idle while one lane walks a long one
+        __syncwarp();
+        unsigned pend = __ballot_sync(FULL, seg);
+        while (pend) {
+            const int q = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const float *e = s_seg + q * GADJ_SEG;
+            const float len = e[9];
+            const float a = len * (float)lane * (1.0f / 32.0f), b = len * (float)(lane + 1) * (1.0f / 32.0f);
+            segment_scatter(G, A.gsum, fmaf(a, e[3], e[0]), fmaf(a, e[4], e[1]), fmaf(a, e[5], e[2]), e[3], e[4],
+                            e[5], e[6], e[7], e[8], b - a, e[10]);
+        }
+        __syncwarp();
     }
     // fixed-order block reduction of the value
     val += __shfl_xor_sync(FULL, val, 16);
@@ -1574,7 +1598,8 @@ cudaError_t launch_grid_adjoint_one(const GridAdjArgs &a, int rows, double *valu
 {
     auto kern = grid_adjoint_kernel<PHASE>;
     const size_t tb = (PHASE != MC_PHASE_HG) ? a.g.c.table_bytes : 0;
-    const size_t smem = tb + a.g.c.extra_bytes + 16 + sizeof(double) * (GADJ_BLOCK / 32);
+    const size_t smem = tb + a.g.c.extra_bytes + 16 + sizeof(double) * (GADJ_BLOCK / 32) +
+                        sizeof(float) * GADJ_BLOCK * GADJ_SEG;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, bps = 0;
