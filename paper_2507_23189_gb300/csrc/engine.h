@@ -109,6 +109,9 @@ struct GridAdjArgs {
     float *grad;                  // [gz][gy][gx] output (written by the fold)
     float k_ext;
     double *partials;             // [grid] value per CTA
+    // the voxel row (beam_iy, beam_iz) along x holding the beam's entry point
+    // is summed in shared memory first (-1: not privatised)
+    int beam_iy, beam_iz;
 };
 
 struct LaunchCfg {

@@ -945,12 +945,14 @@ __global__ void __launch_bounds__(1024) grid_kernel(const __grid_constant__ Grid
 // the terms. Roulette factors are held fixed.
 constexpr int GADJ_BLOCK = 256;
 constexpr int GADJ_SEG = 11;     // floats per queued flight segment
+constexpr int GADJ_ROWR = 0;     // rows within this many voxels of the beam's (in y and z) live in shared memory
+constexpr int GADJ_ROWS = (2 * GADJ_ROWR + 1) * (2 * GADJ_ROWR + 1);
 
 // grad[v] += coef * (length of the segment from p along d, of length len,
 // inside voxel v), by a DDA over the voxels.
-__device__ __forceinline__ void segment_scatter(const GridArgs &G, double *grad, float px, float py, float pz,
-                                                float dx, float dy, float dz, float idx, float idy, float idz,
-                                                float len, float coef)
+__device__ __forceinline__ void segment_scatter(const GridArgs &G, double *grad, double *row, int row_y,
+                                                int row_z, float px, float py, float pz, float dx, float dy,
+                                                float dz, float idx, float idy, float idz, float len, float coef)
 {
     const CommonArgs &C = G.c;
     const float INF = __int_as_float(0x7f800000);
@@ -969,7 +971,14 @@ __device__ __forceinline__ void segment_scatter(const GridArgs &G, double *grad,
         else if (dz < 0.f) tz = (fmaf((float)iz, G.vz, -C.hz) - pz) * idz;
         const int ax = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
         const float tn = fminf(fmaxf(ax == 0 ? tx : (ax == 1 ? ty : tz), t), len);
-        if (tn > t) atomicAdd(&grad[((size_t)iz * G.gy + iy) * G.gx + ix], (double)coef * (double)(tn - t));
+        if (tn > t) {
+            const double val = (double)coef * (double)(tn - t);
+            const int ry = iy - row_y + GADJ_ROWR, rz = iz - row_z + GADJ_ROWR;
+            if (row_y >= 0 && (unsigned)ry <= 2u * GADJ_ROWR && (unsigned)rz <= 2u * GADJ_ROWR)
+                atomicAdd(&row[(rz * (2 * GADJ_ROWR + 1) + ry) * G.gx + ix], val);   // near the beam: shared
+            else
+                atomicAdd(&grad[((size_t)iz * G.gy + iy) * G.gx + ix], val);
+        }
         t = tn;
         if (!(t < len)) return;
         if (ax == 0) { ix += dx > 0.f ? 1 : -1; if (ix < 0 || ix >= G.gx) return; }
@@ -991,6 +1000,11 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
     double *s_red = reinterpret_cast<double *>(s_bar + 2);
     // per-warp queue of flight segments to rasterise: (p, d, 1/d, length, coef)
     float *s_seg = reinterpret_cast<float *>(s_red + GADJ_BLOCK / 32) + (threadIdx.x & ~31u) * GADJ_SEG;
+    // the beam row's sums: flight and point terms, column sources A and A (top - y)
+    double *s_row = reinterpret_cast<double *>(reinterpret_cast<float *>(s_red + GADJ_BLOCK / 32) +
+                                               GADJ_BLOCK * GADJ_SEG);
+    const int nrow = A.beam_iy >= 0 ? GADJ_ROWS * G.gx : 0;   // per sum
+    for (int i = threadIdx.x; i < 3 * nrow; i += blockDim.x) s_row[i] = 0.0;
     Smem S = carve<MC_PHASE_HG, false>(smem, C);
     S.table = smem;
     if (threadIdx.x == 0) mbar_init(s_bar);
@@ -1108,8 +1122,16 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                     if (pass == 1) {
                         const float B = Ptot - P;
                         const float dens = cell.x - G.mu_a;   // k_ext n_v
+                        const int ryo = iy - A.beam_iy + GADJ_ROWR, rzo = iz - A.beam_iz + GADJ_ROWR;
+                        const bool on_row = A.beam_iy >= 0 && (unsigned)ryo <= 2u * GADJ_ROWR &&
+                                            (unsigned)rzo <= 2u * GADJ_ROWR;
+                        const int ri = (rzo * (2 * GADJ_ROWR + 1) + ryo) * G.gx + ix;
                         if (B != 0.f) {
-                            if (dens > 0.f) atomicAdd(&A.gsum[v], (double)B * (double)A.k_ext / (double)dens);
+                            if (dens > 0.f) {
+                                const double pt = (double)B * (double)A.k_ext / (double)dens;
+                                if (on_row) atomicAdd(&s_row[ri], pt);
+                                else atomicAdd(&A.gsum[v], pt);
+                            }
                             const float ex = rx - px, ey = ry - py, ez = rz - pz;
                             float *q = s_seg + lane * GADJ_SEG;
                             q[0] = px; q[1] = py; q[2] = pz; q[3] = dx; q[4] = dy; q[5] = dz;
@@ -1119,8 +1141,13 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                             seg = true;
                         }
                         if (Aj != 0.f) {
-                            atomicAdd(&A.s1[v], (double)Aj);
-                            atomicAdd(&A.s2[v], (double)Aj * (double)(top - ry));
+                            if (on_row) {
+                                atomicAdd(&s_row[nrow + ri], (double)Aj);
+                                atomicAdd(&s_row[2 * nrow + ri], (double)Aj * (double)(top - ry));
+                            } else {
+                                atomicAdd(&A.s1[v], (double)Aj);
+                                atomicAdd(&A.s2[v], (double)Aj * (double)(top - ry));
+                            }
                         }
                     }
                     P += Aj;
@@ -1163,10 +1190,24 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
             const float *e = s_seg + q * GADJ_SEG;
             const float len = e[9];
             const float a = len * (float)lane * (1.0f / 32.0f), b = len * (float)(lane + 1) * (1.0f / 32.0f);
-            segment_scatter(G, A.gsum, fmaf(a, e[3], e[0]), fmaf(a, e[4], e[1]), fmaf(a, e[5], e[2]), e[3], e[4],
-                            e[5], e[6], e[7], e[8], b - a, e[10]);
+            segment_scatter(G, A.gsum, s_row, A.beam_iy, A.beam_iz, fmaf(a, e[3], e[0]), fmaf(a, e[4], e[1]),
+                            fmaf(a, e[5], e[2]), e[3], e[4], e[5], e[6], e[7], e[8], b - a, e[10]);
         }
         __syncwarp();
+    }
+    // the beam row's shared sums into the global ones
+    __syncthreads();
+    if (nrow) {
+        for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
+            const int ix = i % G.gx, r = i / G.gx;
+            const int iy = A.beam_iy + r % (2 * GADJ_ROWR + 1) - GADJ_ROWR;
+            const int iz = A.beam_iz + r / (2 * GADJ_ROWR + 1) - GADJ_ROWR;
+            if (iy < 0 || iy >= G.gy || iz < 0 || iz >= G.gz) continue;   // rows beyond the grid stay 0
+            const size_t v = ((size_t)iz * G.gy + iy) * G.gx + ix;
+            if (s_row[i] != 0.0) atomicAdd(&A.gsum[v], s_row[i]);
+            if (s_row[nrow + i] != 0.0) atomicAdd(&A.s1[v], s_row[nrow + i]);
+            if (s_row[2 * nrow + i] != 0.0) atomicAdd(&A.s2[v], s_row[2 * nrow + i]);
+        }
     }
     // fixed-order block reduction of the value
     val += __shfl_xor_sync(FULL, val, 16);
@@ -1599,7 +1640,8 @@ cudaError_t launch_grid_adjoint_one(const GridAdjArgs &a, int rows, double *valu
     auto kern = grid_adjoint_kernel<PHASE>;
     const size_t tb = (PHASE != MC_PHASE_HG) ? a.g.c.table_bytes : 0;
     const size_t smem = tb + a.g.c.extra_bytes + 16 + sizeof(double) * (GADJ_BLOCK / 32) +
-                        sizeof(float) * GADJ_BLOCK * GADJ_SEG;
+                        sizeof(float) * GADJ_BLOCK * GADJ_SEG +
+                        (a.beam_iy >= 0 ? sizeof(double) * 3 * GADJ_ROWS * a.g.gx : 0);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, bps = 0;
