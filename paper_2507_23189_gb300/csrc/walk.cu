@@ -553,34 +553,65 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
             atomicOr(C.error, (vf == vf) ? MC_EFLAG_OVERFLOW : MC_EFLAG_NUMERIC);
         }
 
-        int status = 0;
-        if (C.max_scatter && ncoll >= C.max_scatter) {
-            sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
-            status = 5;
-            alive = false;
+        if (TRACE) {
+            int status = 0;
+            if (C.max_scatter && ncoll >= C.max_scatter) {
+                sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
+                status = 5;
+                alive = false;
+            } else {
+                rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
+                // weight threshold / roulette (Sec. 3.1.3)
+                if (w < C.rr_thr) {
+                    if (u3 < C.rr_surv) {
+                        const float wn = w * C.inv_rr_surv;
+                        sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w) - fix32(wn));
+                        w = wn;
+                    } else {
+                        sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w));
+                        status = 4;
+                        alive = false;
+                    }
+                }
+                if (!(w == w)) atomicOr(C.error, MC_EFLAG_NUMERIC);
+            }
+            trace_write<TRACE>(C, rel, e_now, status, rx, ry, rz, dx, dy, dz, status == 4 ? 0.f : w, nee,
+                               pix, nb, -1);
+            if (alive && ev >= C.max_events) {
+                sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
+                atomicOr(C.error, MC_EFLAG_EVENTS);
+                trace_write<TRACE>(C, rel, ev, 6, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1, -1);
+                alive = false;
+            }
         } else {
+            // the same decisions with one branch for the rare cases: the new
+            // direction is computed for every photon (a photon truncated by
+            // max_scatter ends here and never uses it)
+            const bool cap = C.max_scatter && ncoll >= C.max_scatter;
             rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
-            // weight threshold / roulette (Sec. 3.1.3)
-            if (w < C.rr_thr) {
-                if (u3 < C.rr_surv) {
-                    const float wn = w * C.inv_rr_surv;
-                    sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w) - fix32(wn));
-                    w = wn;
-                } else {
-                    sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w));
-                    status = 4;
+            if (cap | (w < C.rr_thr) | (ev >= C.max_events) | !(w == w)) {
+                if (cap) {
+                    sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
                     alive = false;
+                } else {
+                    if (w < C.rr_thr) {   // weight threshold / roulette (Sec. 3.1.3)
+                        if (u3 < C.rr_surv) {
+                            const float wn = w * C.inv_rr_surv;
+                            sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w) - fix32(wn));
+                            w = wn;
+                        } else {
+                            sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w));
+                            alive = false;
+                        }
+                    }
+                    if (!(w == w)) atomicOr(C.error, MC_EFLAG_NUMERIC);
+                    if (alive && ev >= C.max_events) {
+                        sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
+                        atomicOr(C.error, MC_EFLAG_EVENTS);
+                        alive = false;
+                    }
                 }
             }
-            if (!(w == w)) atomicOr(C.error, MC_EFLAG_NUMERIC);
-        }
-        trace_write<TRACE>(C, rel, e_now, status, rx, ry, rz, dx, dy, dz, status == 4 ? 0.f : w, nee,
-                           pix, nb, -1);
-        if (alive && ev >= C.max_events) {
-            sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
-            atomicOr(C.error, MC_EFLAG_EVENTS);
-            trace_write<TRACE>(C, rel, ev, 6, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1, -1);
-            alive = false;
         }
     }
 }
