@@ -28,23 +28,29 @@ __global__ void column_kernel(const float *__restrict__ density, int gx, int gy,
     }
 }
 
-// One CTA per majorant cell: the largest density of its voxels, as mu_ext
-// with the same single-precision operation as the voxels (so no voxel
-// exceeds its cell's majorant).
+// Majorants: blockIdx.y picks the cell, blockIdx.x a piece of MAJ_CHUNK of
+// its voxels; each CTA reduces its piece to the largest mu_ext (the same
+// single-precision fmaf as the voxels, so no voxel exceeds its majorant) and
+// merges it with atomicMax on the float's bits, which order like the
+// non-negative floats they are (maj starts at 0).
+constexpr int MAJ_CHUNK = 8192;
+
 __global__ void __launch_bounds__(256) majorant_kernel(const float *__restrict__ density, int gx, int gy,
                                                        int gz, int bx, int by, int bz, int mx, int my,
                                                        float k_ext, float mu_a, float *__restrict__ maj)
 {
     __shared__ float red[256];
-    const int c = blockIdx.x;
+    const int c = blockIdx.y;
     const int cz = c / (mx * my), cy = (c / mx) % my, cx = c % mx;
     const int x0 = cx * bx, y0 = cy * by, z0 = cz * bz;
     const int nxb = min(bx, gx - x0), nyb = min(by, gy - y0), nzb = min(bz, gz - z0);
     const long long nv = (long long)nxb * nyb * nzb;
+    const long long i0 = (long long)blockIdx.x * MAJ_CHUNK;
+    const long long i1 = min(nv, i0 + MAJ_CHUNK);
     float m = 0.0f;
-    for (long long i = threadIdx.x; i < nv; i += blockDim.x) {
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int xi = (int)(i % nxb), yi = (int)((i / nxb) % nyb), zi = (int)(i / ((long long)nxb * nyb));
-        m = fmaxf(m, density[((size_t)(z0 + zi) * gy + (y0 + yi)) * gx + (x0 + xi)]);
+        m = fmaxf(m, fmaf(k_ext, density[((size_t)(z0 + zi) * gy + (y0 + yi)) * gx + (x0 + xi)], mu_a));
     }
     red[threadIdx.x] = m;
     __syncthreads();
@@ -52,7 +58,7 @@ __global__ void __launch_bounds__(256) majorant_kernel(const float *__restrict__
         if (threadIdx.x < s) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + s]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) maj[c] = fmaf(k_ext, red[0], mu_a);
+    if (threadIdx.x == 0) atomicMax(reinterpret_cast<int *>(&maj[c]), __float_as_int(fmaxf(red[0], 0.0f)));
 }
 
 // One thread per (x, z) column, upward: a collision in voxel iy adds A times
@@ -93,7 +99,10 @@ cudaError_t launch_grid_prepare(const float *density, int gx, int gy, int gz, in
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int mx = (gx + bx - 1) / bx, my = (gy + by - 1) / by, mz = (gz + bz - 1) / bz;
-    majorant_kernel<<<mx * my * mz, 256, 0, st>>>(density, gx, gy, gz, bx, by, bz, mx, my, k_ext, mu_a, maj);
+    if ((e = cudaMemsetAsync(maj, 0, sizeof(float) * (size_t)mx * my * mz, st)) != cudaSuccess) return e;
+    const long long per_cell = (long long)bx * by * bz;
+    const dim3 grid((unsigned)((per_cell + MAJ_CHUNK - 1) / MAJ_CHUNK), (unsigned)(mx * my * mz));
+    majorant_kernel<<<grid, 256, 0, st>>>(density, gx, gy, gz, bx, by, bz, mx, my, k_ext, mu_a, maj);
     return cudaGetLastError();
 }
 

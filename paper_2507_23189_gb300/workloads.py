@@ -87,7 +87,7 @@ class Plume:
     n_photons: int = 1_000_000_000
     nx: int = 512
     nz: int = 512
-    block: tuple = (16, 32, 32)             # majorant cells, voxels (bx, by, bz): 16 x 8 x 8 cells
+    block: tuple = (32, 256, 256)           # majorant cells, voxels (bx, by, bz): 8 slabs along the beam
     seed: int = 1
 
 
