@@ -916,29 +916,54 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
         } else {
             atomicOr(C.error, (vf == vf) ? MC_EFLAG_OVERFLOW : MC_EFLAG_NUMERIC);
         }
-        int status = 0;
-        if (C.max_scatter && ncoll >= C.max_scatter) {
-            sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
-            status = 5;
-            alive = false;
+        if (TRACE) {
+            int status = 0;
+            if (C.max_scatter && ncoll >= C.max_scatter) {
+                sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
+                status = 5;
+                alive = false;
+            } else {
+                rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
+                idx = __frcp_rn(dx); idy = __frcp_rn(dy); idz = __frcp_rn(dz);
+                if (w < C.rr_thr) {
+                    if (u3 < C.rr_surv) {
+                        const float wn = w * C.inv_rr_surv;
+                        sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w) - fix32(wn));
+                        w = wn;
+                    } else {
+                        sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w));
+                        status = 4;
+                        alive = false;
+                    }
+                }
+                if (!(w == w)) atomicOr(C.error, MC_EFLAG_NUMERIC);
+            }
+            trace_write<TRACE>(C, rel, ncoll - 1, status, rx, ry, rz, dx, dy, dz, status == 4 ? 0.f : w, nee,
+                               pix, nb, -1);
         } else {
+            // one branch for the rare cases, as in walk_loop
+            const bool cap = C.max_scatter && ncoll >= C.max_scatter;
             rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
             idx = __frcp_rn(dx); idy = __frcp_rn(dy); idz = __frcp_rn(dz);
-            if (w < C.rr_thr) {
-                if (u3 < C.rr_surv) {
-                    const float wn = w * C.inv_rr_surv;
-                    sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w) - fix32(wn));
-                    w = wn;
-                } else {
-                    sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w));
-                    status = 4;
+            if (cap | (w < C.rr_thr) | !(w == w)) {
+                if (cap) {
+                    sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
                     alive = false;
+                } else {
+                    if (w < C.rr_thr) {
+                        if (u3 < C.rr_surv) {
+                            const float wn = w * C.inv_rr_surv;
+                            sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w) - fix32(wn));
+                            w = wn;
+                        } else {
+                            sadd64(&s_tot[MC_TOT_ROULETTE], fix32(w));
+                            alive = false;
+                        }
+                    }
+                    if (!(w == w)) atomicOr(C.error, MC_EFLAG_NUMERIC);
                 }
             }
-            if (!(w == w)) atomicOr(C.error, MC_EFLAG_NUMERIC);
         }
-        trace_write<TRACE>(C, rel, ncoll - 1, status, rx, ry, rz, dx, dy, dz, status == 4 ? 0.f : w, nee,
-                           pix, nb, -1);
     }
 }
 
