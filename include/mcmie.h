@@ -326,8 +326,9 @@ mc_status mc_run_grid(const mc_grid *grid, const void *d_grid_work, const mc_med
  * length inside each voxel it crosses, B_i the camera terms from collision i
  * on; every camera term contributes -A k_ext times the length of its column
  * inside each voxel above the collision. Roulette factors are held fixed.
- * d_grad: float [gz][gy][gx], overwritten (sums of double-precision atomics,
- * rounded once; their last bits depend on scheduling); *d_value = L
+ * d_grad: float [gz][gy][gx], overwritten (terms formed in single precision,
+ * summed by double-precision atomics and rounded once; the sums' last bits
+ * depend on scheduling); *d_value = L
  * (double, fixed order).
  * d_work: mc_grid_adjoint_workspace_bytes(grid) bytes. The paper has no
  * gradients; this serves fitting the density of a heterogeneous medium. */

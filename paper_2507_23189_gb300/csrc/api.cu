@@ -618,18 +618,11 @@ mc_status mc_grid_adjoint(const mc_grid *g, const void *d_grid_work, const mc_me
     a.g.counter = reinterpret_cast<unsigned long long *>(w);
     a.gsum = reinterpret_cast<double *>(w + kAlign);
     a.s1 = reinterpret_cast<double *>(w + kAlign + nb);
-    a.s2 = reinterpret_cast<double *>(w + kAlign + 2 * nb);
+    a.ex = reinterpret_cast<double *>(w + kAlign + 2 * nb);
     a.partials = reinterpret_cast<double *>(w + kAlign + 3 * nb);
     a.adj = d_adj_image;
     a.grad = d_grad;
     a.k_ext = (float)g->k_ext;
-    // privatise the voxel row of the beam's entry point (every photon's first
-    // flight of a pencil beam runs along it) when it fits in shared memory
-    a.beam_iy = a.beam_iz = -1;
-    if (g->gx <= 2048) {
-        a.beam_iy = std::min(std::max((int)std::floor(0.5 * g->gy), 0), g->gy - 1);
-        a.beam_iz = std::min(std::max((int)std::floor(0.5 * g->gz), 0), g->gz - 1);
-    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto fail = [](cudaError_t x) { return x != cudaSuccess; };
     if (fail(cudaMemsetAsync(w, 0, kAlign + 3 * nb, st)) ||

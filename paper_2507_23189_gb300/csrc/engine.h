@@ -99,19 +99,18 @@ struct GridArgs {
 };
 
 // Gradient of L = sum_pix adj[pix] image[pix] with respect to the voxel
-// densities (mc_grid_adjoint): flight terms straight into grad, camera
-// column terms as per-voxel sources s1 (A) and s2 (A times the distance to
-// the voxel's top) folded into grad by a column scan afterwards.
+// densities (mc_grid_adjoint): point, flight and own-voxel column terms into
+// gsum, the rest of each camera column as the per-voxel source s1 and each
+// first flight as one row-suffix entry ex, both folded in afterwards.
 struct GridAdjArgs {
     GridArgs g;
     const float *adj;             // [nz][nx]
-    double *gsum, *s1, *s2;       // [gz][gy][gx], double-precision atomic sums
+    // [gz][gy][gx] double-precision atomic sums: point, flight and own-voxel
+    // column terms; column sources above a collision; first-flight row suffix
+    double *gsum, *s1, *ex;
     float *grad;                  // [gz][gy][gx] output (written by the fold)
     float k_ext;
     double *partials;             // [grid] value per CTA
-    // the voxel row (beam_iy, beam_iz) along x holding the beam's entry point
-    // is summed in shared memory first (-1: not privatised)
-    int beam_iy, beam_iz;
 };
 
 struct LaunchCfg {
@@ -145,9 +144,11 @@ cudaError_t launch_grid_prepare(const float *density, int gx, int gy, int gz, in
 // Launch the density-gradient replay, the column fold and the value reduction.
 cudaError_t launch_grid_adjoint(const GridAdjArgs &a, int partial_rows, double *value, cudaStream_t stream);
 
-// grad[v] = gsum[v] - k_ext (s2[v] + vy * sum of s1 below v in its column).
-cudaError_t launch_column_fold(const double *gsum, const double *s1, const double *s2, float *grad, int gx,
-                               int gy, int gz, double k_ext, double vy, cudaStream_t stream);
+// grad[v] = gsum[v] + vx * (sum of ex after v in its row along x)
+//           - k_ext vy * (sum of s1 below v in its column along y); gsum is
+// updated in place by the row sums.
+cudaError_t launch_gradient_fold(double *gsum, const double *s1, const double *ex, float *grad, int gx, int gy,
+                                 int gz, double k_ext, double vx, double vy, cudaStream_t stream);
 
 // CTAs the grid adjoint may use on the current device (for workspace sizing).
 int grid_adjoint_max_grid();

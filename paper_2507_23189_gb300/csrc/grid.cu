@@ -61,12 +61,43 @@ __global__ void __launch_bounds__(256) majorant_kernel(const float *__restrict__
     if (threadIdx.x == 0) atomicMax(reinterpret_cast<int *>(&maj[c]), __float_as_int(fmaxf(red[0], 0.0f)));
 }
 
-// One thread per (x, z) column, upward: a collision in voxel iy adds A times
-// the distance to its voxel's top (s2) and A times a full voxel height to
-// every voxel above it (s1, summed below); the flight terms are in gsum.
+// One warp per voxel row along x, from its far end: every voxel before the
+// one where a first flight ended takes the full voxel length vx of that
+// flight's coefficient, gsum[ix] += vx * sum_{j > ix} ex[j]. Chunks of 32
+// voxels with a warp suffix scan; rows with no entries cost their loads.
+__global__ void row_suffix_kernel(double *__restrict__ gsum, const double *__restrict__ ex, int gx,
+                                  long long rows, double vx)
+{
+    const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (r >= rows) return;   // whole warps leave together
+    const int lane = threadIdx.x & 31;
+    const size_t base = (size_t)r * gx;
+    double carry = 0.0;      // sum of ex beyond the current chunk
+    for (int c = ((gx - 1) >> 5) << 5; c >= 0; c -= 32) {
+        const int ix = c + lane;
+        const double e = ix < gx ? ex[base + ix] : 0.0;
+        if (__any_sync(0xFFFFFFFFu, e != 0.0)) {
+            double s = e;    // inclusive suffix within the chunk
+            for (int o = 1; o < 32; o <<= 1) {
+                const double t = __shfl_down_sync(0xFFFFFFFFu, s, o);
+                if (lane + o < 32) s += t;
+            }
+            const double after = __shfl_down_sync(0xFFFFFFFFu, s, 1);
+            const double total = __shfl_sync(0xFFFFFFFFu, s, 0);
+            const double add = carry + (lane < 31 ? after : 0.0);
+            if (ix < gx && add != 0.0) gsum[base + ix] += vx * add;
+            carry += total;
+        } else if (carry != 0.0 && ix < gx) {
+            gsum[base + ix] += vx * carry;
+        }
+    }
+}
+
+// One thread per (x, z) column, upward: a camera term A at a collision in
+// voxel iy takes A times a full voxel height in every voxel above it (s1,
+// summed below); its part in its own voxel is already in gsum.
 __global__ void fold_kernel(const double *__restrict__ gsum, const double *__restrict__ s1,
-                            const double *__restrict__ s2, float *__restrict__ grad, int gx, int gy, int gz,
-                            double k_ext, double vy)
+                            float *__restrict__ grad, int gx, int gy, int gz, double k_vy)
 {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)gx * gz) return;
@@ -74,18 +105,22 @@ __global__ void fold_kernel(const double *__restrict__ gsum, const double *__res
     double run = 0.0;
     for (int iy = 0; iy < gy; ++iy) {
         const size_t v = ((size_t)iz * gy + iy) * gx + ix;
-        grad[v] = (float)(gsum[v] - k_ext * (s2[v] + vy * run));
+        grad[v] = (float)(gsum[v] - k_vy * run);
         run += s1[v];
     }
 }
 
 }  // namespace
 
-cudaError_t launch_column_fold(const double *gsum, const double *s1, const double *s2, float *grad, int gx,
-                               int gy, int gz, double k_ext, double vy, cudaStream_t st)
+cudaError_t launch_gradient_fold(double *gsum, const double *s1, const double *ex, float *grad, int gx, int gy,
+                                 int gz, double k_ext, double vx, double vy, cudaStream_t st)
 {
+    const long long rows = (long long)gy * gz;
+    row_suffix_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(gsum, ex, gx, rows, vx);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const long long cols = (long long)gx * gz;
-    fold_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(gsum, s1, s2, grad, gx, gy, gz, k_ext, vy);
+    fold_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(gsum, s1, grad, gx, gy, gz, k_ext * vy);
     return cudaGetLastError();
 }
 

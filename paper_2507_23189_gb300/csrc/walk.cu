@@ -995,51 +995,137 @@ __global__ void __launch_bounds__(1024) grid_kernel(const __grid_constant__ Grid
 // collision i precede): flight i adds B_i / n(r_i) at r_i's voxel (scattering
 // density k_sca n exp(-int mu)) and -B_i k_ext times its length inside every
 // voxel it crosses; camera term i adds -A_i k_ext times the length of its
-// column inside every voxel above r_i, gathered here as the sources s1 / s2
-// and folded by a column scan. A photon runs twice on its Philox counters:
-// the first pass sums its camera terms, the second replays it and scatters
-// the terms. Roulette factors are held fixed.
+// column inside every voxel above r_i: the part in r_i's own voxel directly,
+// the rest gathered as the source s1 and folded by a column scan. The first
+// flight runs from the entry point along +x inside one voxel row, so it is
+// one entry of a row-suffix array (every voxel before the collision's takes
+// the full voxel length). A photon runs twice on its Philox counters: the
+// first pass sums its camera terms, the second replays it and scatters the
+// terms. Roulette factors are held fixed. Every term is formed in single
+// precision and summed by double-precision atomics in L2; the SM's own
+// double-precision pipe, a small fraction of the single-precision rate,
+// is not used on this path.
 constexpr int GADJ_BLOCK = 256;
-constexpr int GADJ_SEG = 11;     // floats per queued flight segment
-constexpr int GADJ_ROWR = 0;     // rows within this many voxels of the beam's (in y and z) live in shared memory
-constexpr int GADJ_ROWS = (2 * GADJ_ROWR + 1) * (2 * GADJ_ROWR + 1);
+// per-warp queue of flights to rasterise, one column per lane: for the three
+// axes in partition order, the first crossing distance and the spacing of
+// the plane crossings, and the count with the axis code; then the length,
+// the coefficient and the start voxel
+constexpr int GADJ_SEG = 12;
 
-// grad[v] += coef * (length of the segment from p along d, of length len,
-// inside voxel v), by a DDA over the voxels.
-__device__ __forceinline__ void segment_scatter(const GridArgs &G, double *grad, double *row, int row_y,
-                                                int row_z, float px, float py, float pz, float dx, float dy,
-                                                float dz, float idx, float idy, float idz, float len, float coef)
+// float -> double by moving the bit fields: exact for normal numbers and
+// infinities; subnormals (far below any term summed here) become zero.
+__device__ __forceinline__ double widen(float f)
 {
-    const CommonArgs &C = G.c;
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const uint32_t s = u & 0x80000000u;
+    const uint32_t ex = e == 0xFFu ? 0x7FFu : e + 896u;     // rebias 127 -> 1023
+    const uint32_t hi = e == 0u ? s : (s | (ex << 20) | ((u & 0x7FFFFFu) >> 3));
+    const uint32_t lo = e == 0u ? 0u : (u << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Distance along a flight to its j-th crossing of one axis's voxel planes,
+// affine in j (planes are evenly spaced) and 0 for a plane the start lies on
+// or past. Every use shares this one formula, so the segments between
+// consecutive crossings tile the flight exactly.
+__device__ __forceinline__ float cross_at(float t0, float dl, int j)
+{
+    return fmaxf(fmaf((float)j, dl, t0), 0.f);
+}
+
+// One axis of a flight of length len from p along d (1/d = id): start voxel
+// i0, first crossing t0, spacing dl, and n, the interior planes crossed at
+// distances below len.
+struct Cross {
+    float t0, dl;
+    int i0, n;
+    bool up;
+};
+
+__device__ __forceinline__ Cross axis_cross(float p, float d, float id, float lo, float v, float iv, int g,
+                                            float len)
+{
+    Cross c;
+    c.i0 = min(max(__float2int_rd((p - lo) * iv), 0), g - 1);
+    c.up = d > 0.f;
+    c.t0 = 0.f;
+    c.dl = 1.f;
+    c.n = 0;
+    if (!(fabsf(id) < __int_as_float(0x7f800000))) return c;   // no motion along this axis
+    c.t0 = (fmaf((float)(c.up ? c.i0 + 1 : c.i0), v, lo) - p) * id;
+    c.dl = v * fabsf(id);
+    const int lim = c.up ? g - 1 - c.i0 : c.i0;
+    int n = min(max(__float2int_ru((len - c.t0) * (fabsf(d) * iv)), 0), lim);
+    while (n > 0 && !(cross_at(c.t0, c.dl, n - 1) < len)) --n;
+    while (n < lim && cross_at(c.t0, c.dl, n) < len) ++n;
+    c.n = n;
+    return c;
+}
+
+// crossings of an axis at distances <= t, and the distance of the next one
+__device__ __forceinline__ int count_le(float t0, float dl, int n, float t, float &next)
+{
+    int c = 0;
+    if (n > 0) {
+        c = min(max(__float2int_rd((t - t0) * rcp_approx(dl)) + 1, 0), n);
+        while (c > 0 && cross_at(t0, dl, c - 1) > t) --c;
+        while (c < n && cross_at(t0, dl, c) <= t) ++c;
+    }
+    next = c < n ? cross_at(t0, dl, c) : __int_as_float(0x7f800000);
+    return c;
+}
+
+// Unit u of queued flight q: the stretch between crossings u-1 and u of its
+// partition axis A (the axis it crosses most; the flight's start and end
+// close the first and last stretch), walked across the crossings of the
+// other two axes B and C inside it; grad[voxel] += coef * length of each
+// piece.
+__device__ __forceinline__ void raster_unit(const GridArgs &G, double *grad, const float *s_seg, int q, int u)
+{
     const float INF = __int_as_float(0x7f800000);
-    int ix = min(max(__float2int_rd(px * G.inv_vx), 0), G.gx - 1);
-    int iy = min(max(__float2int_rd((py + C.hy) * G.inv_vy), 0), G.gy - 1);
-    int iz = min(max(__float2int_rd((pz + C.hz) * G.inv_vz), 0), G.gz - 1);
-    float t = 0.f;
-    const int max_cross = G.gx + G.gy + G.gz + 4;
-    for (int it = 0; it < max_cross; ++it) {
-        float tx = INF, ty = INF, tz = INF;
-        if (dx > 0.f) tx = ((float)(ix + 1) * G.vx - px) * idx;
-        else if (dx < 0.f) tx = ((float)ix * G.vx - px) * idx;
-        if (dy > 0.f) ty = (fmaf((float)(iy + 1), G.vy, -C.hy) - py) * idy;
-        else if (dy < 0.f) ty = (fmaf((float)iy, G.vy, -C.hy) - py) * idy;
-        if (dz > 0.f) tz = (fmaf((float)(iz + 1), G.vz, -C.hz) - pz) * idz;
-        else if (dz < 0.f) tz = (fmaf((float)iz, G.vz, -C.hz) - pz) * idz;
-        const int ax = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
-        const float tn = fminf(fmaxf(ax == 0 ? tx : (ax == 1 ? ty : tz), t), len);
-        if (tn > t) {
-            const double val = (double)coef * (double)(tn - t);
-            const int ry = iy - row_y + GADJ_ROWR, rz = iz - row_z + GADJ_ROWR;
-            if (row_y >= 0 && (unsigned)ry <= 2u * GADJ_ROWR && (unsigned)rz <= 2u * GADJ_ROWR)
-                atomicAdd(&row[(rz * (2 * GADJ_ROWR + 1) + ry) * G.gx + ix], val);   // near the beam: shared
-            else
-                atomicAdd(&grad[((size_t)iz * G.gy + iy) * G.gx + ix], val);
+    const float *f = s_seg + q;
+    const int *fi = reinterpret_cast<const int *>(f);
+    const int wA = fi[192], wB = fi[224], wC = fi[256];
+    const int nA = wA & 0xFFFF, nB = wB & 0xFFFF, nC = wC & 0xFFFF;
+    auto stride = [&](int w) {
+        const int ax = (w >> 16) & 3;
+        const int st = ax == 0 ? 1 : (ax == 1 ? G.gx : G.gx * G.gy);
+        return (w >> 18) & 1 ? -st : st;
+    };
+    const float len = f[288], coef = f[320];
+    const float tB0 = f[32], dB = f[128], tC0 = f[64], dC = f[160];
+    const float t0 = u == 0 ? 0.f : cross_at(f[0], f[96], u - 1);
+    const float t1 = u == nA ? len : cross_at(f[0], f[96], u);
+    float nextB, nextC;
+    int cB = count_le(tB0, dB, nB, t0, nextB);
+    int cC = count_le(tC0, dC, nC, t0, nextC);
+    const int sB = stride(wB), sC = stride(wC);
+    int v = fi[352] + u * stride(wA) + cB * sB + cC * sC;
+    float t = t0;
+    for (int it = 0; it <= nB + nC; ++it) {
+        const bool bfirst = nextB <= nextC;
+        const float m = fminf(nextB, nextC);
+        const float e = fminf(m, t1);
+        if (e > t) atomicAdd(&grad[v], widen(coef * (e - t)));
+        t = e;
+        if (!(m < t1)) break;
+        if (bfirst) {
+            v += sB;
+            ++cB;
+            nextB = cB < nB ? cross_at(tB0, dB, cB) : INF;
+        } else {
+            v += sC;
+            ++cC;
+            nextC = cC < nC ? cross_at(tC0, dC, cC) : INF;
         }
-        t = tn;
-        if (!(t < len)) return;
-        if (ax == 0) { ix += dx > 0.f ? 1 : -1; if (ix < 0 || ix >= G.gx) return; }
-        else if (ax == 1) { iy += dy > 0.f ? 1 : -1; if (iy < 0 || iy >= G.gy) return; }
-        else { iz += dz > 0.f ? 1 : -1; if (iz < 0 || iz >= G.gz) return; }
     }
 }
 
@@ -1056,11 +1142,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
     double *s_red = reinterpret_cast<double *>(s_bar + 2);
     // per-warp queue of flight segments to rasterise: (p, d, 1/d, length, coef)
     float *s_seg = reinterpret_cast<float *>(s_red + GADJ_BLOCK / 32) + (threadIdx.x & ~31u) * GADJ_SEG;
-    // the beam row's sums: flight and point terms, column sources A and A (top - y)
-    double *s_row = reinterpret_cast<double *>(reinterpret_cast<float *>(s_red + GADJ_BLOCK / 32) +
-                                               GADJ_BLOCK * GADJ_SEG);
-    const int nrow = A.beam_iy >= 0 ? GADJ_ROWS * G.gx : 0;   // per sum
-    for (int i = threadIdx.x; i < 3 * nrow; i += blockDim.x) s_row[i] = 0.0;
+    // (column f of lane q at s_seg[32 f + q])
     Smem S = carve<MC_PHASE_HG, false>(smem, C);
     S.table = smem;
     if (threadIdx.x == 0) mbar_init(s_bar);
@@ -1117,7 +1199,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
             }
         }
         if (!__any_sync(FULL, alive)) break;
-        bool seg = false;      // this lane queued a flight segment this round
+        int nseg = 0;          // stretches of the flight this lane queued this round
 
         if (alive && ncoll == 0xFFFFFFFFu) {
             // start (or restart) the photon's pass at the entry point
@@ -1177,34 +1259,43 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                     const float Aj = __ldg(&A.adj[pix]) * nee;
                     if (pass == 1) {
                         const float B = Ptot - P;
-                        const float dens = cell.x - G.mu_a;   // k_ext n_v
-                        const int ryo = iy - A.beam_iy + GADJ_ROWR, rzo = iz - A.beam_iz + GADJ_ROWR;
-                        const bool on_row = A.beam_iy >= 0 && (unsigned)ryo <= 2u * GADJ_ROWR &&
-                                            (unsigned)rzo <= 2u * GADJ_ROWR;
-                        const int ri = (rzo * (2 * GADJ_ROWR + 1) + ryo) * G.gx + ix;
+                        // column source: this voxel's part directly, the rest by the fold
+                        float gv = -A.k_ext * Aj * (top - ry);
                         if (B != 0.f) {
-                            if (dens > 0.f) {
-                                const double pt = (double)B * (double)A.k_ext / (double)dens;
-                                if (on_row) atomicAdd(&s_row[ri], pt);
-                                else atomicAdd(&A.gsum[v], pt);
-                            }
-                            const float ex = rx - px, ey = ry - py, ez = rz - pz;
-                            float *q = s_seg + lane * GADJ_SEG;
-                            q[0] = px; q[1] = py; q[2] = pz; q[3] = dx; q[4] = dy; q[5] = dz;
-                            q[6] = idx; q[7] = idy; q[8] = idz;
-                            q[9] = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-                            q[10] = -B * A.k_ext;
-                            seg = true;
-                        }
-                        if (Aj != 0.f) {
-                            if (on_row) {
-                                atomicAdd(&s_row[nrow + ri], (double)Aj);
-                                atomicAdd(&s_row[2 * nrow + ri], (double)Aj * (double)(top - ry));
+                            const float dens = cell.x - G.mu_a;   // k_ext n_v
+                            if (dens > 0.f) gv = fmaf(B, __fdividef(A.k_ext, dens), gv);
+                            const float coef = -B * A.k_ext;
+                            if (ncoll == 1) {
+                                // first flight, along +x from the entry point in this
+                                // voxel row: the voxels before ix by the row suffix
+                                gv = fmaf(coef, fmaxf(fmaf(-(float)ix, G.vx, rx), 0.f), gv);
+                                atomicAdd(&A.ex[v], widen(coef));
                             } else {
-                                atomicAdd(&A.s1[v], (double)Aj);
-                                atomicAdd(&A.s2[v], (double)Aj * (double)(top - ry));
+                                const float ex = rx - px, ey = ry - py, ez = rz - pz;
+                                const float len = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+                                const Cross X = axis_cross(px, dx, idx, 0.f, G.vx, G.inv_vx, G.gx, len);
+                                const Cross Y = axis_cross(py, dy, idy, -C.hy, G.vy, G.inv_vy, G.gy, len);
+                                const Cross Z = axis_cross(pz, dz, idz, -C.hz, G.vz, G.inv_vz, G.gz, len);
+                                // partition axis: the one crossed most; then the other two
+                                const int pa = (X.n >= Y.n && X.n >= Z.n) ? 0 : (Y.n >= Z.n ? 1 : 2);
+                                const Cross &A0 = pa == 0 ? X : (pa == 1 ? Y : Z);
+                                const Cross &B0 = pa == 0 ? Y : X;
+                                const Cross &C0 = pa == 2 ? Y : Z;
+                                const int ab = pa == 0 ? 1 : 0, ac = pa == 2 ? 1 : 2;
+                                float *q = s_seg + lane;
+                                int *qi = reinterpret_cast<int *>(q);
+                                q[0] = A0.t0; q[32] = B0.t0; q[64] = C0.t0;
+                                q[96] = A0.dl; q[128] = B0.dl; q[160] = C0.dl;
+                                qi[192] = A0.n | (pa << 16) | ((A0.up ? 0 : 1) << 18);
+                                qi[224] = B0.n | (ab << 16) | ((B0.up ? 0 : 1) << 18);
+                                qi[256] = C0.n | (ac << 16) | ((C0.up ? 0 : 1) << 18);
+                                q[288] = len; q[320] = coef;
+                                qi[352] = (Z.i0 * G.gy + Y.i0) * G.gx + X.i0;
+                                nseg = A0.n + 1;
                             }
                         }
+                        if (gv != 0.f) atomicAdd(&A.gsum[v], widen(gv));
+                        if (Aj != 0.f) atomicAdd(&A.s1[v], widen(Aj));
                     }
                     P += Aj;
                     px = rx; py = ry; pz = rz;
@@ -1235,34 +1326,29 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                 alive = false;
             }
         }
-        // the warp rasterises each queued flight together: lane i takes the
-        // i-th of 32 equal pieces of it, so lanes with short or no flights
-        // do not idle while one lane walks a long one
-        __syncwarp();
-        unsigned pend = __ballot_sync(FULL, seg);
-        while (pend) {
-            const int q = __ffs(pend) - 1;
-            pend &= pend - 1;
-            const float *e = s_seg + q * GADJ_SEG;
-            const float len = e[9];
-            const float a = len * (float)lane * (1.0f / 32.0f), b = len * (float)(lane + 1) * (1.0f / 32.0f);
-            segment_scatter(G, A.gsum, s_row, A.beam_iy, A.beam_iz, fmaf(a, e[3], e[0]), fmaf(a, e[4], e[1]),
-                            fmaf(a, e[5], e[2]), e[3], e[4], e[5], e[6], e[7], e[8], b - a, e[10]);
-        }
-        __syncwarp();
-    }
-    // the beam row's shared sums into the global ones
-    __syncthreads();
-    if (nrow) {
-        for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
-            const int ix = i % G.gx, r = i / G.gx;
-            const int iy = A.beam_iy + r % (2 * GADJ_ROWR + 1) - GADJ_ROWR;
-            const int iz = A.beam_iz + r / (2 * GADJ_ROWR + 1) - GADJ_ROWR;
-            if (iy < 0 || iy >= G.gy || iz < 0 || iz >= G.gz) continue;   // rows beyond the grid stay 0
-            const size_t v = ((size_t)iz * G.gy + iy) * G.gx + ix;
-            if (s_row[i] != 0.0) atomicAdd(&A.gsum[v], s_row[i]);
-            if (s_row[nrow + i] != 0.0) atomicAdd(&A.s1[v], s_row[nrow + i]);
-            if (s_row[2 * nrow + i] != 0.0) atomicAdd(&A.s2[v], s_row[2 * nrow + i]);
+        // the warp rasterises its queued flights together, one stretch between
+        // partition-axis crossings per lane: the stretches of all flights are
+        // numbered in lane order and handed out 32 at a time, each lane
+        // finding its flight by a search over the exclusive prefix sums
+        if (__any_sync(FULL, nseg != 0)) {
+            __syncwarp();
+            int incl = nseg;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int excl = incl - nseg;
+            const int total = __shfl_sync(FULL, incl, 31);
+            for (int base = 0; base < total; base += 32) {
+                const int g = base + lane;
+                int q = 0, eq = 0;    // last lane whose flight starts at or before g
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int e = __shfl_sync(FULL, excl, q + st);
+                    if (e <= g) { q += st; eq = e; }
+                }
+                if (g < total) raster_unit(G, A.gsum, s_seg, q, g - eq);
+            }
+            __syncwarp();
         }
     }
     // fixed-order block reduction of the value
@@ -1696,8 +1782,7 @@ cudaError_t launch_grid_adjoint_one(const GridAdjArgs &a, int rows, double *valu
     auto kern = grid_adjoint_kernel<PHASE>;
     const size_t tb = (PHASE != MC_PHASE_HG) ? a.g.c.table_bytes : 0;
     const size_t smem = tb + a.g.c.extra_bytes + 16 + sizeof(double) * (GADJ_BLOCK / 32) +
-                        sizeof(float) * GADJ_BLOCK * GADJ_SEG +
-                        (a.beam_iy >= 0 ? sizeof(double) * 3 * GADJ_ROWS * a.g.gx : 0);
+                        sizeof(float) * GADJ_BLOCK * GADJ_SEG;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, bps = 0;
@@ -1711,7 +1796,8 @@ cudaError_t launch_grid_adjoint_one(const GridAdjArgs &a, int rows, double *valu
     if (grid > rows) grid = rows;
     kern<<<(unsigned)grid, GADJ_BLOCK, smem, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = launch_column_fold(a.gsum, a.s1, a.s2, a.grad, a.g.gx, a.g.gy, a.g.gz, (double)a.k_ext, (double)a.g.vy, st);
+    e = launch_gradient_fold(a.gsum, a.s1, a.ex, a.grad, a.g.gx, a.g.gy, a.g.gz, (double)a.k_ext, (double)a.g.vx,
+                             (double)a.g.vy, st);
     if (e != cudaSuccess) return e;
     adjoint_reduce<<<1, 128, 0, st>>>(a.partials, (int)grid, 1, value);
     return cudaGetLastError();
