@@ -152,3 +152,44 @@ def test_fit_plume_scale_with_adam(gpu):
     s = math.exp(log_s.item())
     print("recovered scale %.4f (true 0.8)" % s)
     assert abs(s / 0.8 - 1) < 0.03
+
+
+def test_disc_beam_gradient_matches_oracle(gpu, oracle_mod, ps_table, ps_oracle_table):
+    """A 2.5 mm disc beam: first flights start in many voxel rows (each one
+    entry of the row-suffix sums), single and multiple scattering against the
+    oracle on the same photons."""
+    import torch
+    dens = _rough((16, 16, 32), 13, 2000.0)
+    k_ext, k_sca = 4e-5, 3.2e-5
+    nx = nz = 32
+    adj = np.random.default_rng(6).uniform(0.2, 1.0, (nz, nx)).astype(np.float32)
+    geo = gpu.Geometry(LX, LY, LZ, beam_radius=1.25)
+    g = gpu.Grid(torch.from_numpy(np.ascontiguousarray(dens, dtype=np.float32)).cuda(), k_ext, k_sca, 0.0,
+                 (8, 4, 4)).prepare(geo)
+    e = gpu.Engine(gpu.Camera(nx, nz, 64, R_MAX), geo)
+    n = 200_000
+    grid = dict(density=dens.astype(np.float64), k_ext=k_ext, k_sca=k_sca, block=(8, 4, 4))
+    val, grad = e.grid_adjoint(g, gpu.Medium(1.0, 0.0, "hg", 0.7, None), torch.from_numpy(adj), n, seed=8,
+                               max_scatter=1)
+    e.check()
+    o = oracle_mod.grid_adjoint(adj.astype(np.float64), phase="hg", hg_g=0.7, mu_s=0.0, n_photons=n, nx=nx, nz=nz,
+                                max_scatter=1, seed=8, beam_radius=1.25, grid=grid)
+    gg_ = grad.cpu().numpy().astype(np.float64)
+    rows = np.any(o["grad"] != 0.0, axis=2)
+    assert rows.sum() >= 12                       # first flights in many rows
+    assert val.item() == pytest.approx(o["value"], rel=1e-5)
+    scale = np.max(np.abs(o["grad"]))
+    ok = np.abs(gg_ - o["grad"]) <= 1e-4 * np.abs(o["grad"]) + 1e-5 * scale
+    print("disc beam, single scattering: voxels within tolerance %d / %d" % (ok.sum(), ok.size))
+    assert ok.mean() >= 0.995
+    val, grad = e.grid_adjoint(g, gpu.Medium(1.0, 0.0, "table", 0.0, ps_table), torch.from_numpy(adj), n, seed=9,
+                               rr_threshold=1e-2)
+    e.check()
+    o = oracle_mod.grid_adjoint(adj.astype(np.float64), phase="mie", table=ps_oracle_table, mu_s=0.0, n_photons=n,
+                                nx=nx, nz=nz, seed=9, rr_threshold=1e-2, beam_radius=1.25, grid=grid)
+    gg_ = grad.cpu().numpy().astype(np.float64)
+    assert val.item() == pytest.approx(o["value"], rel=2e-4)
+    blk = lambda t: t.reshape(4, 4, 4, 4, 4, 8).sum(axis=(1, 3, 5))
+    bg, bo = blk(gg_), blk(o["grad"])
+    print("disc beam, multiple scattering: worst block %.2e of max" % (np.max(np.abs(bg - bo)) / np.max(np.abs(bo))))
+    assert np.max(np.abs(bg - bo)) <= 1e-2 * np.max(np.abs(bo))
