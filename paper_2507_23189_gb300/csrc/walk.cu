@@ -1431,6 +1431,17 @@ constexpr int ADJ_BLOCK = 256;     // threads per CTA without phase weights
 constexpr int ADJ_BLOCK_W = 128;   // with phase weights (private accumulators)
 constexpr int ADJ_LIST = 8;        // sampled angles kept per photon before a replay is needed
 
+// Compensated (Kahan) sum in single precision: s + c carries the running
+// total to about 2^-46 of the summed magnitudes, on the full-rate float pipe
+// (GB300's double-precision pipe runs at a small fraction of it).
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 // Private single-precision accumulators: hat k of thread t at rows[k*B + t]
 // (consecutive threads in consecutive banks; no atomics, fixed order).
 __device__ __forceinline__ void hat_add(float *rows, int nw_stride, int k, float f, float v)
@@ -1482,7 +1493,9 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
     // P_tot - P_i is then accurate to ~1e-7 of the photon's total, far
     // below the statistical error of any gradient
     float P = 0.0f, Ptot = 0.0f;
-    double g_val = 0.0, g_s = 0.0, g_a = 0.0, g_z = 0.0;
+    // per-thread sums of A_j, A_j dlog/dmu_s, A_j dlog/dmu_a and j A_j as
+    // compensated single-precision pairs
+    float gs_val = 0.f, gc_val = 0.f, gs_s = 0.f, gc_s = 0.f, gs_a = 0.f, gc_a = 0.f, gs_z = 0.f, gc_z = 0.f;
     // the photon's first ADJ_LIST sampled angles: hat index, fraction, P_i
     // (indexed with compile-time constants only, so they stay in registers)
     int lk[ADJ_LIST];
@@ -1559,10 +1572,10 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
             P += Aj;
             if (pass == 1) {
                 const float jj = (float)ncoll;
-                g_val += (double)Aj;
-                g_s += (double)Aj * (double)(Ssc + jj * c_s - l);
-                g_a += (double)Aj * (double)(Ssc - jj * M.inv_mu_ext - l);
-                g_z += (double)jj * (double)Aj;
+                kahan_add(gs_val, gc_val, Aj);
+                kahan_add(gs_s, gc_s, Aj * (Ssc + jj * c_s - l));
+                kahan_add(gs_a, gc_a, Aj * (Ssc - jj * M.inv_mu_ext - l));
+                kahan_add(gs_z, gc_z, jj * Aj);
                 if (PHASEW && Aj != 0.0f) {
                     float f;
                     const int k = hat_pair(nw, dy, f);
@@ -1620,6 +1633,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
     }
 
     // -------- reduce: lanes -> warp -> CTA row of partials (fixed order)
+    double g_val = (double)gs_val - (double)gc_val, g_s = (double)gs_s - (double)gc_s;
+    double g_a = (double)gs_a - (double)gc_a, g_z = (double)gs_z - (double)gc_z;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         g_val += __shfl_xor_sync(FULL, g_val, o);
