@@ -1666,14 +1666,23 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
     }
 }
 
-// out[q] = sum over the grid's rows, in row order (deterministic).
-__global__ void adjoint_reduce(const double *partials, int rows, int width, double *out)
+// out[q] = sum over the grid's rows of partials[row][q]: one CTA per column,
+// each thread a fixed stride of rows, then a fixed tree (deterministic).
+constexpr int RED_BLOCK = 256;
+__global__ void __launch_bounds__(RED_BLOCK) adjoint_reduce(const double *partials, int rows, int width,
+                                                            double *out)
 {
-    for (int q = threadIdx.x; q < width; q += blockDim.x) {
-        double t = 0.0;
-        for (int r = 0; r < rows; ++r) t += partials[(size_t)r * width + q];
-        out[q] = t;
+    __shared__ double part[RED_BLOCK];
+    const int q = blockIdx.x;
+    double t = 0.0;
+    for (int r = threadIdx.x; r < rows; r += RED_BLOCK) t += partials[(size_t)r * width + q];
+    part[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = RED_BLOCK / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) out[q] = part[0];
 }
 
 __global__ void philox_kernel(const uint4 *ctr, uint64_t n, uint32_t k0, uint32_t k1, uint4 *out)
@@ -1814,7 +1823,7 @@ cudaError_t launch_grid_adjoint_one(const GridAdjArgs &a, int rows, double *valu
     e = launch_gradient_fold(a.gsum, a.s1, a.ex, a.grad, a.g.gx, a.g.gy, a.g.gz, (double)a.k_ext, (double)a.g.vx,
                              (double)a.g.vy, st);
     if (e != cudaSuccess) return e;
-    adjoint_reduce<<<1, 128, 0, st>>>(a.partials, (int)grid, 1, value);
+    adjoint_reduce<<<1, RED_BLOCK, 0, st>>>(a.partials, (int)grid, 1, value);
     return cudaGetLastError();
 }
 }  // namespace
@@ -1941,7 +1950,7 @@ cudaError_t launch_adjoint_one(const AdjArgs &a, int rows, double *out, cudaStre
     }
     kern<<<(unsigned)grid, block, smem, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    adjoint_reduce<<<1, 128, 0, st>>>(a.partials, (int)grid, 3 + a.n_w, out);
+    adjoint_reduce<<<3 + a.n_w, RED_BLOCK, 0, st>>>(a.partials, (int)grid, 3 + a.n_w, out);
     return cudaGetLastError();
 }
 }  // namespace
