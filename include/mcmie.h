@@ -34,6 +34,7 @@ extern "C" {
 #endif
 
 typedef enum {
+    MC_NOT_READY = 1,     /* mc_check_within: the stream's work still runs     */
     MC_OK = 0,
     MC_ERR_ARG = -1,      /* invalid argument; nothing was launched            */
     MC_ERR_CUDA = -2,     /* a CUDA runtime call failed                        */
@@ -391,6 +392,19 @@ mc_status mc_trace(const mc_medium *medium, const mc_geometry *geom,
 /* Synchronise `stream`, read *d_error and map its bits to a status
  * (MC_OK when zero). */
 mc_status mc_check(const uint32_t *d_error, void *stream);
+
+/* mc_check with a host-side watchdog: polls the stream (cudaStreamQuery)
+ * for at most timeout_ms milliseconds. MC_NOT_READY when the work is still
+ * running then (it goes on; call again or mc_check later); otherwise as
+ * mc_check. timeout_ms >= 0, d_error non-NULL, else MC_ERR_ARG. */
+mc_status mc_check_within(const uint32_t *d_error, void *stream, double timeout_ms);
+
+/* Self-test of the kernels' bounded waits: one CTA waits on an mbarrier
+ * phase that can never complete (it expects bytes no copy delivers), gives
+ * up after `tries` polls (1 .. 2^22) and sets MC_EFLAG_TIMEOUT in *d_error,
+ * so that mc_check then returns MC_ERR_TIMEOUT and the context stays
+ * usable. The same wait guards every table staging. */
+mc_status mc_wait_selftest(uint32_t *d_error, uint32_t tries, void *stream);
 
 /* Philox4x32-10 on the device: out[4i..4i+3] = Philox(key = seed,
  * counter = ctr[4i..4i+3]) for i < n. For testing the generator. */

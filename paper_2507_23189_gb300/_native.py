@@ -9,8 +9,8 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libmcmie.so")
 
-MC_OK = 0
-STATUS = {0: "MC_OK", -1: "MC_ERR_ARG", -2: "MC_ERR_CUDA", -3: "MC_ERR_NOMEM", -4: "MC_ERR_TIMEOUT",
+MC_OK, MC_NOT_READY = 0, 1
+STATUS = {1: "MC_NOT_READY", 0: "MC_OK", -1: "MC_ERR_ARG", -2: "MC_ERR_CUDA", -3: "MC_ERR_NOMEM", -4: "MC_ERR_TIMEOUT",
           -5: "MC_ERR_OVERFLOW", -6: "MC_ERR_NUMERIC", -7: "MC_ERR_EVENTS", -8: "MC_ERR_TABLE"}
 EFLAG_EVENTS, EFLAG_TIMEOUT, EFLAG_NUMERIC, EFLAG_OVERFLOW, EFLAG_TABLE = 1, 2, 4, 8, 16
 PHASE_TABLE, PHASE_HG, PHASE_PAPER = 0, 1, 2
@@ -26,7 +26,7 @@ EXPORTS = ("mc_table_bytes", "mie_table_build", "mc_medium_from_density", "mc_wo
            "mc_adjoint_workspace_bytes", "mc_adjoint", "mc_paper_table_bytes", "mie_paper_table_build",
            "mc_metrics_out_len", "mc_metrics_workspace_bytes", "mc_image_metrics", "mie_mixture_table_build",
            "mc_grid_workspace_bytes", "mc_grid_prepare", "mc_run_grid", "mc_grid_adjoint_workspace_bytes",
-           "mc_grid_adjoint")
+           "mc_grid_adjoint", "mc_check_within", "mc_wait_selftest")
 
 
 class McError(RuntimeError):
@@ -124,6 +124,10 @@ def lib():
                            C.c_int, vp]
     L.mc_check.restype = C.c_int
     L.mc_check.argtypes = [vp, vp]
+    L.mc_check_within.restype = C.c_int
+    L.mc_check_within.argtypes = [vp, vp, C.c_double]
+    L.mc_wait_selftest.restype = C.c_int
+    L.mc_wait_selftest.argtypes = [vp, C.c_uint32, vp]
     L.mc_philox.restype = C.c_int
     L.mc_philox.argtypes = [vp, C.c_uint64, C.c_uint64, vp, vp]
     L.mc_run_static.restype = C.c_int

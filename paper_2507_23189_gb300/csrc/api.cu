@@ -6,7 +6,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <chrono>
 #include <cstring>
+#include <thread>
 #include <new>
 
 #include "engine.h"
@@ -422,6 +424,16 @@ mc_status mc_adjoint(const mc_medium *medium, const mc_geometry *geom, const mc_
     return cuda_status(e);
 }
 
+static mc_status flags_status(uint32_t h)
+{
+    if (h & MC_EFLAG_TIMEOUT) return MC_ERR_TIMEOUT;
+    if (h & MC_EFLAG_TABLE) return MC_ERR_TABLE;
+    if (h & MC_EFLAG_NUMERIC) return MC_ERR_NUMERIC;
+    if (h & MC_EFLAG_OVERFLOW) return MC_ERR_OVERFLOW;
+    if (h & MC_EFLAG_EVENTS) return MC_ERR_EVENTS;
+    return MC_OK;
+}
+
 mc_status mc_check(const uint32_t *d_error, void *stream)
 {
     if (!d_error) return MC_ERR_ARG;
@@ -429,12 +441,31 @@ mc_status mc_check(const uint32_t *d_error, void *stream)
     if (cudaStreamSynchronize(st) != cudaSuccess) return MC_ERR_CUDA;
     uint32_t h = 0;
     if (cudaMemcpy(&h, d_error, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return MC_ERR_CUDA;
-    if (h & MC_EFLAG_TIMEOUT) return MC_ERR_TIMEOUT;
-    if (h & MC_EFLAG_TABLE) return MC_ERR_TABLE;
-    if (h & MC_EFLAG_NUMERIC) return MC_ERR_NUMERIC;
-    if (h & MC_EFLAG_OVERFLOW) return MC_ERR_OVERFLOW;
-    if (h & MC_EFLAG_EVENTS) return MC_ERR_EVENTS;
-    return MC_OK;
+    return flags_status(h);
+}
+
+mc_status mc_check_within(const uint32_t *d_error, void *stream, double timeout_ms)
+{
+    if (!d_error || !(timeout_ms >= 0.0)) return MC_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+        const cudaError_t q = cudaStreamQuery(st);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return MC_ERR_CUDA;
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ms >= timeout_ms) return MC_NOT_READY;   // the work goes on; check again later
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    uint32_t h = 0;
+    if (cudaMemcpy(&h, d_error, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return MC_ERR_CUDA;
+    return flags_status(h);
+}
+
+mc_status mc_wait_selftest(uint32_t *d_error, uint32_t tries, void *stream)
+{
+    if (!d_error || tries == 0 || tries > (1u << 22)) return MC_ERR_ARG;
+    return cuda_status(mcx::launch_wait_selftest(d_error, tries, static_cast<cudaStream_t>(stream)));
 }
 
 mc_status mc_philox(const uint32_t *d_ctr, uint64_t n, uint64_t seed, uint32_t *d_out, void *stream)
@@ -447,6 +478,7 @@ mc_status mc_philox(const uint32_t *d_ctr, uint64_t n, uint64_t seed, uint32_t *
 const char *mc_status_string(mc_status s)
 {
     switch (s) {
+    case MC_NOT_READY: return "work still running";
     case MC_OK: return "ok";
     case MC_ERR_ARG: return "invalid argument";
     case MC_ERR_CUDA: return "CUDA runtime error";

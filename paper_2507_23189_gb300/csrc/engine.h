@@ -159,4 +159,7 @@ int adjoint_max_grid();
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out,
                           cudaStream_t stream);
 
+// The bounded mbarrier wait on a phase that cannot complete (self-test).
+cudaError_t launch_wait_selftest(uint32_t *err, uint32_t tries, cudaStream_t stream);
+
 }  // namespace mcx

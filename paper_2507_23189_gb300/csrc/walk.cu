@@ -114,6 +114,23 @@ __device__ __forceinline__ void mbar_init(unsigned long long *mbar)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Wait for mbarrier phase `parity` to complete, giving up after `tries`
+// polls (each may suspend the thread for a bounded, hardware-defined time).
+// Returns 1 when the phase completed.
+__device__ __forceinline__ uint32_t mbar_wait(uint32_t bar, uint32_t parity, uint32_t tries)
+{
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < tries && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+    }
+    return done;
+}
+
 // Bulk-copy `bytes` (multiple of 16) from global to shared memory and wait
 // (bounded) for the mbarrier phase `parity` to complete. Every thread of the
 // CTA must call it; the previous contents of dst must no longer be in use.
@@ -132,15 +149,7 @@ __device__ bool stage_bulk(void *dst, const void *src, uint32_t bytes, unsigned 
             "l"(src), "r"(bytes), "r"(bar)
             : "memory");
     }
-    uint32_t done = 0;
-    for (uint32_t it = 0; it < WAIT_LIMIT && !done; ++it) {
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-    }
+    const uint32_t done = mbar_wait(bar, parity, WAIT_LIMIT);
     if (!done && threadIdx.x == 0) atomicOr(err, MC_EFLAG_TIMEOUT);
     return __syncthreads_and(done) != 0;
 }
@@ -1685,6 +1694,22 @@ __global__ void __launch_bounds__(RED_BLOCK) adjoint_reduce(const double *partia
     if (threadIdx.x == 0) out[q] = part[0];
 }
 
+// Self-test of the bounded wait: a phase that expects 16 bytes of a copy
+// that is never issued, so it cannot complete; the wait must give up after
+// `tries` polls and flag MC_EFLAG_TIMEOUT. No copy is in flight at exit.
+__global__ void wait_selftest_kernel(uint32_t *err, uint32_t tries)
+{
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)), "r"(16u)
+                     : "memory");
+    }
+    __syncthreads();
+    const uint32_t done = mbar_wait(smem_u32(&bar), 0u, tries);
+    if (!done && threadIdx.x == 0) atomicOr(err, MC_EFLAG_TIMEOUT);
+}
+
 __global__ void philox_kernel(const uint4 *ctr, uint64_t n, uint32_t k0, uint32_t k1, uint4 *out)
 {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
@@ -1970,6 +1995,12 @@ cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32
     unsigned blocks = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     philox_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const uint4 *>(ctr), n, (uint32_t)seed,
                                           (uint32_t)(seed >> 32), reinterpret_cast<uint4 *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(uint32_t *err, uint32_t tries, cudaStream_t st)
+{
+    wait_selftest_kernel<<<1, 32, 0, st>>>(err, tries);
     return cudaGetLastError();
 }
 

@@ -203,6 +203,17 @@ class Camera:
         return N.Camera(self.nx, self.nz, self.n_radial, self.r_max)
 
 
+def wait_selftest(tries=4096, device=None, stream=None):
+    """The kernels' bounded wait on an mbarrier phase that cannot complete
+    (mc_wait_selftest); returns mc_check's status afterwards, which is
+    MC_ERR_TIMEOUT (-4) when the wait gave up as it must."""
+    torch = _torch()
+    err = torch.zeros(1, dtype=torch.int32, device=device if device is not None else "cuda")
+    N.check("mc_wait_selftest", N.lib().mc_wait_selftest(C.c_void_p(err.data_ptr()), int(tries),
+                                                         _stream_handle(stream)))
+    return N.lib().mc_check(C.c_void_p(err.data_ptr()), _stream_handle(stream))
+
+
 def run_params(n_photons, seed=1, photon_offset=0, rr_threshold=1e-4, rr_survival=0.1,
                max_events=1_000_000, max_scatter=0, image_frac_bits=32, accumulate=False,
                block_size=0, blocks_per_sm=0, image_mode=0):
@@ -373,6 +384,17 @@ class Engine:
     def check(self, stream=None):
         """Wait for the stream and raise if a kernel flagged an error."""
         N.check("mc_check", N.lib().mc_check(C.c_void_p(self.error.data_ptr()), _stream_handle(stream)))
+
+    def check_within(self, timeout_ms, stream=None):
+        """check() with a host-side watchdog: True when the stream finished
+        within timeout_ms (raises on a flagged error), False when it is still
+        running (it goes on; call again or check())."""
+        st = N.lib().mc_check_within(C.c_void_p(self.error.data_ptr()), _stream_handle(stream),
+                                     float(timeout_ms))
+        if st == N.MC_NOT_READY:
+            return False
+        N.check("mc_check_within", st)
+        return True
 
     def result(self):
         """Tallies as float64 numpy arrays in weight units (one photon = 1)."""
