@@ -30,7 +30,6 @@ constexpr int CHUNK = 128;            // photons a warp takes from the counter a
 constexpr float INV_2PI = 0.159154943091895335768883763372514f;
 constexpr float W_SCALE = 4294967296.0f;   // 2^32, weight tallies
 constexpr uint32_t WAIT_LIMIT = 1u << 22;  // mbarrier polls before giving up
-constexpr int EXIT_BATCH = 16;             // pending exits that start a warp's batch of exit tallies
 
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon et al., SC'11): per round
@@ -409,35 +408,6 @@ __device__ void flush(const CommonArgs &C, const MediumArgs &M, const Smem &S, T
 // The photon walk over indices [.., limit) of medium M: every warp refills
 // lanes whose photon ended from chunks of `chunk` indices obtained by
 // grab() (called by lane 0), until the range is exhausted.
-// Exit tally of a photon that left the cuvette on a flight from r along d
-// with weight w; code: walls crossed (bits 0-2: x, y, z), bit 3 no collision
-// before (ballistic). The first wall crossed is the exit (ties: lowest axis).
-// Branch-free but for the radial atomic: a warp tallies its exits in
-// batches, and a batch holds every kind of exit.
-__device__ __forceinline__ void exit_tally(const CommonArgs &C, const Smem &S, Tally &T, float rx, float ry,
-                                           float rz, float dx, float dy, float dz, float w, uint32_t code)
-{
-    // the x wall comes first when its distance |n_x / d_x| is at most that
-    // of every other crossed wall: |n_x| |d_b| <= |n_b| |d_x|, no division
-    const float ax = dx > 0.f ? C.lx - rx : rx, ay = dy > 0.f ? C.hy - ry : C.hy + ry;
-    const float az = dz > 0.f ? C.hz - rz : C.hz + rz;
-    const float bx = fabsf(dx), by = fabsf(dy), bz = fabsf(dz);
-    const bool xface = (code & 1u) && (!(code & 2u) || ax * by <= ay * bx) && (!(code & 4u) || ax * bz <= az * bx);
-    const bool refl = xface && dx < 0.f, far = xface && !(dx < 0.f);
-    const long long wv = fix32(w);
-    T.refl += refl ? wv : 0ll;
-    T.far += far ? wv : 0ll;
-    T.side += xface ? 0ll : wv;
-    T.ball += (far && (code & 8u)) ? wv : 0ll;
-    // radial bin of the far-face exit point
-    const float t = __fdividef(C.lx - rx, dx);
-    const float ey = fmaf(t, dy, ry), ez = fmaf(t, dz, rz);
-    const float r2 = fmaf(ey, ey, ez * ez);
-    const float rho = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-    const int rb = min(max(__float2int_rd(rho * C.sr), 0), C.n_radial - 1);
-    if (far) sadd64(&S.rad[rb], wv);
-}
-
 template <int PHASE, bool SMEM_IMAGE, bool TRACE, bool RK, class Grab>
 __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs &M, const Smem &S,
                                           unsigned long long limit, unsigned chunk, Grab grab,
@@ -457,13 +427,6 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
     uint32_t pk0 = 0, pk1 = 0;      // global photon index, lo/hi words
     uint32_t ev = 0, ncoll = 0;
     float rx = 0, ry = 0, rz = 0, dx = 1, dy = 0, dz = 0, w = 1;
-    // An exit waiting for the warp's batch of exit tallies: position and
-    // direction before the flight, weight, walls crossed (bits 0-2) and no
-    // collision before (bit 3). The exit branch then costs a few moves; the
-    // tallies run for many lanes at once.
-    bool pend = false;
-    float qx = 0, qy = 0, qz = 0, qdx = 0, qdy = 0, qdz = 0, qw = 0;
-    uint32_t qcode = 0;
 
     while (true) {
         // -------- refill lanes whose photon ended
@@ -509,15 +472,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
                 }
             }
         }
-        const bool any_alive = __any_sync(FULL, alive);
-        if (!TRACE) {
-            const unsigned pm = __ballot_sync(FULL, pend);
-            if (pm && (__popc(pm) >= EXIT_BATCH || !any_alive)) {
-                if (pend) exit_tally(C, S, T, qx, qy, qz, qdx, qdy, qdz, qw, qcode);
-                pend = false;
-            }
-        }
-        if (!any_alive) break;
+        if (!__any_sync(FULL, alive)) break;
         if (!alive) continue;
 
         // -------- one event
@@ -535,41 +490,41 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
         const bool cz = !(fabsf(pz) < C.hz);
 
         if (cx | cy | cz) {
+            // the flight reaches a wall: the first one crossed is the exit
+            // (ties: lowest axis). With one axis crossed no division is needed.
+            const float INF = __int_as_float(0x7f800000);
+            int face;
+            if ((int)cx + (int)cy + (int)cz == 1) {
+                face = cx ? 0 : (cy ? 1 : 2);
+            } else {
+                // several walls crossed: the nearest decides (approximate
+                // divisions; a different answer needs a near tie)
+                const float tx = cx ? __fdividef(dx > 0.f ? C.lx - rx : 0.f - rx, dx) : INF;
+                const float ty = cy ? __fdividef(dy > 0.f ? C.hy - ry : -C.hy - ry, dy) : INF;
+                const float tz = cz ? __fdividef(dz > 0.f ? C.hz - rz : -C.hz - rz, dz) : INF;
+                face = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
+            }
+            const long long wv = fix32(w);
+            int status, rb = -1;
+            float ex = px, ey = py, ez = pz;
+            if (face == 0 && dx < 0.f) {
+                T.refl += wv;
+                status = 1;
+            } else if (face == 0) {
+                T.far += wv;
+                if (ncoll == 0) T.ball += wv;
+                const float t = __fdividef(C.lx - rx, dx);
+                ex = C.lx; ey = fmaf(t, dy, ry); ez = fmaf(t, dz, rz);
+                const float r2 = fmaf(ey, ey, ez * ez);
+                const float rho = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+                rb = min(__float2int_rd(rho * C.sr), C.n_radial - 1);
+                sadd64(&s_rad[rb], wv);
+                status = 2;
+            } else {
+                T.side += wv;
+                status = 3;
+            }
             if (TRACE) {
-                // the flight reaches a wall: the first one crossed is the exit
-                // (ties: lowest axis). With one axis crossed no division is needed.
-                const float INF = __int_as_float(0x7f800000);
-                int face;
-                if ((int)cx + (int)cy + (int)cz == 1) {
-                    face = cx ? 0 : (cy ? 1 : 2);
-                } else {
-                    // several walls crossed: the nearest decides (approximate
-                    // divisions; a different answer needs a near tie)
-                    const float tx = cx ? __fdividef(dx > 0.f ? C.lx - rx : 0.f - rx, dx) : INF;
-                    const float ty = cy ? __fdividef(dy > 0.f ? C.hy - ry : -C.hy - ry, dy) : INF;
-                    const float tz = cz ? __fdividef(dz > 0.f ? C.hz - rz : -C.hz - rz, dz) : INF;
-                    face = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
-                }
-                const long long wv = fix32(w);
-                int status, rb = -1;
-                float ex = px, ey = py, ez = pz;
-                if (face == 0 && dx < 0.f) {
-                    T.refl += wv;
-                    status = 1;
-                } else if (face == 0) {
-                    T.far += wv;
-                    if (ncoll == 0) T.ball += wv;
-                    const float t = __fdividef(C.lx - rx, dx);
-                    ex = C.lx; ey = fmaf(t, dy, ry); ez = fmaf(t, dz, rz);
-                    const float r2 = fmaf(ey, ey, ez * ez);
-                    const float rho = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-                    rb = min(__float2int_rd(rho * C.sr), C.n_radial - 1);
-                    sadd64(&s_rad[rb], wv);
-                    status = 2;
-                } else {
-                    T.side += wv;
-                    status = 3;
-                }
                 if (face != 0 || dx < 0.f) {
                     const float t = face == 0 ? (0.f - rx) / dx
                                   : face == 1 ? (dy > 0.f ? C.hy - ry : -C.hy - ry) / dy
@@ -577,13 +532,6 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
                     ex = fmaf(t, dx, rx); ey = fmaf(t, dy, ry); ez = fmaf(t, dz, rz);
                 }
                 trace_write<TRACE>(C, rel, e_now, status, ex, ey, ez, dx, dy, dz, w, 0.f, -1, -1, rb);
-            } else {
-                // hand the exit to the warp's next batch of exit tallies (a
-                // second exit of this lane before that batch is tallied now)
-                if (pend) exit_tally(C, S, T, qx, qy, qz, qdx, qdy, qdz, qw, qcode);
-                qx = rx; qy = ry; qz = rz; qdx = dx; qdy = dy; qdz = dz; qw = w;
-                qcode = (cx ? 1u : 0u) | (cy ? 2u : 0u) | (cz ? 4u : 0u) | (ncoll == 0 ? 8u : 0u);
-                pend = true;
             }
             alive = false;
             continue;
