@@ -41,8 +41,8 @@ SEED = 1
 # Work per photon-step = thread-instructions the kernel executes per sampled
 # flight on this workload, from ncu (smsp__thread_inst_executed.sum / steps);
 # DRAM bytes per launch from the same capture (None when stale).
-THREAD_INST_PER_STEP = 244.0          # ncu, 1e7-photon launch of this workload
-DRAM_BYTES_PER_LAUNCH = 596480        # same capture; fixed per launch (L2-resident tallies)
+THREAD_INST_PER_STEP = 241.3          # ncu, 1e7-photon launch of this workload
+DRAM_BYTES_PER_LAUNCH = 596736        # same capture; fixed per launch (L2-resident tallies)
 LANES_PER_SM = 128
 
 

@@ -491,23 +491,17 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
 
         if (cx | cy | cz) {
             // the flight reaches a wall: the first one crossed is the exit
-            // (ties: lowest axis)
-            int face;
-            if ((int)cx + (int)cy + (int)cz == 1) {
-                face = cx ? 0 : (cy ? 1 : 2);
-            } else {
-                // several walls crossed: the nearest decides. Wall a comes
-                // before wall b when |n_a / d_a| <= |n_b / d_b| (n: distance to
-                // the wall along the axis), tested as |n_a| |d_b| <= |n_b| |d_a|
-                // without divisions; a different answer than exact arithmetic
-                // needs a near tie
-                const float ax = dx > 0.f ? C.lx - rx : rx, ay = dy > 0.f ? C.hy - ry : C.hy + ry;
-                const float az = dz > 0.f ? C.hz - rz : C.hz + rz;
-                const float bx = fabsf(dx), by = fabsf(dy), bz = fabsf(dz);
-                const bool xf = cx && (!cy || ax * by <= ay * bx) && (!cz || ax * bz <= az * bx);
-                const bool yf = !xf && cy && (!cz || ay * bz <= az * by);
-                face = xf ? 0 : (yf ? 1 : 2);
-            }
+            // (ties: lowest axis). Wall a comes before wall b when
+            // |n_a / d_a| <= |n_b / d_b| (n: distance to the wall along the
+            // axis), tested as |n_a| |d_b| <= |n_b| |d_a| without divisions (a
+            // different answer than exact arithmetic needs a near tie); with one
+            // wall crossed the test picks it
+            const float ax = dx > 0.f ? C.lx - rx : rx, ay = dy > 0.f ? C.hy - ry : C.hy + ry;
+            const float az = dz > 0.f ? C.hz - rz : C.hz + rz;
+            const float bx = fabsf(dx), by = fabsf(dy), bz = fabsf(dz);
+            const bool xf = cx && (!cy || ax * by <= ay * bx) && (!cz || ax * bz <= az * bx);
+            const bool yf = !xf && cy && (!cz || ay * bz <= az * by);
+            const int face = xf ? 0 : (yf ? 1 : 2);
             const long long wv = fix32(w);
             int status, rb = -1;
             float ex = px, ey = py, ez = pz;
