@@ -750,7 +750,7 @@ __device__ __forceinline__ int grid_flight(const GridArgs &G, const float *s_maj
         const int ax = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
         const float t1 = fmaxf(ax == 0 ? tx : (ax == 1 ? ty : tz), t0);
         if (mb * (t1 - t0) > tau) {
-            const float sl = t0 + tau / mb;
+            const float sl = t0 + __fdividef(tau, mb);
             rx = fmaf(sl, dx, rx); ry = fmaf(sl, dy, ry); rz = fmaf(sl, dz, rz);
             return 3;
         }
@@ -881,7 +881,8 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
             } else if (face == 0) {
                 T.far += wv;
                 if (ncoll == 0) T.ball += wv;
-                const float rho = sqrtf(fmaf(ry, ry, rz * rz));
+                const float r2 = fmaf(ry, ry, rz * rz);
+                const float rho = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
                 rb = min(__float2int_rd(rho * C.sr), C.n_radial - 1);
                 sadd64(&s_rad[rb], wv);
                 status = 2;
@@ -899,9 +900,9 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
         const int iy = min(max(__float2int_rd((ry + C.hy) * G.inv_vy), 0), G.gy - 1);
         const int iz = min(max(__float2int_rd((rz + C.hz) * G.inv_vz), 0), G.gz - 1);
         const float2 cell = __ldg(&G.cells[((size_t)iz * G.gy + iy) * G.gx + ix]);
-        const float acc = cell.x / mb;
+        const float acc = __fdividef(cell.x, mb);   // hardware reciprocal: a few ulp
         if (!(u3 < acc)) continue;   // null collision
-        u3 = u3 / acc;
+        u3 = __fdividef(u3, acc);
         ++ncoll;
         {   // Eq. 16 with the voxel's albedo
             const float a = G.mu_a > 0.f ? G.ks_over_ke * (1.0f - G.mu_a / cell.x) : G.ks_over_ke;
@@ -1252,9 +1253,9 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                 const int iz = min(max(__float2int_rd((rz + C.hz) * G.inv_vz), 0), G.gz - 1);
                 const size_t v = ((size_t)iz * G.gy + iy) * G.gx + ix;
                 const float2 cell = __ldg(&G.cells[v]);
-                const float acc = cell.x / mb;
+                const float acc = __fdividef(cell.x, mb);   // hardware reciprocal: a few ulp
                 if (u3 < acc) {
-                    u3 = u3 / acc;
+                    u3 = __fdividef(u3, acc);
                     ++ncoll;
                     const float a = G.mu_a > 0.f ? G.ks_over_ke * (1.0f - G.mu_a / cell.x) : G.ks_over_ke;
                     w = w * a;
