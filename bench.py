@@ -252,6 +252,7 @@ def batched_comparison(E, dev, steps, warmup, flush):
     out["workload"] = ("64 media: d log-uniform 1-10 um, tau uniform 0.5-20, photons log-uniform 1e6-1e8 "
                        "(numpy Philox seed 2026), 128x128 image, Mie tables, graph-captured batch vs "
                        "64 sequential launches")
+    out["media_list"] = [[round(c.diameter_um, 4), round(c.tau, 4), c.n_photons] for c in cases]  # d um, tau, N
     small = _batch_vs_plain(E, dev, media, [200_000] * len(media), steps, warmup, flush)
     small["workload"] = "the same 64 media at 2e5 photons each"
     out["small_budgets"] = small
