@@ -932,7 +932,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
                 alive = false;
             } else {
                 rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
-                idx = __frcp_rn(dx); idy = __frcp_rn(dy); idz = __frcp_rn(dz);
+                idx = __fdividef(1.0f, dx); idy = __fdividef(1.0f, dy); idz = __fdividef(1.0f, dz);
                 if (w < C.rr_thr) {
                     if (u3 < C.rr_surv) {
                         const float wn = w * C.inv_rr_surv;
@@ -952,7 +952,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
             // one branch for the rare cases, as in walk_loop
             const bool cap = C.max_scatter && ncoll >= C.max_scatter;
             rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
-            idx = __frcp_rn(dx); idy = __frcp_rn(dy); idz = __frcp_rn(dz);
+            idx = __fdividef(1.0f, dx); idy = __fdividef(1.0f, dy); idz = __fdividef(1.0f, dz);
             if (cap | (w < C.rr_thr) | !(w == w)) {
                 if (cap) {
                     sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
@@ -1311,7 +1311,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                         end = true;
                     } else {
                         rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
-                        idx = __frcp_rn(dx); idy = __frcp_rn(dy); idz = __frcp_rn(dz);
+                        idx = __fdividef(1.0f, dx); idy = __fdividef(1.0f, dy); idz = __fdividef(1.0f, dz);
                         if (w < C.rr_thr) {
                             if (u3 < C.rr_surv) w = w * C.inv_rr_surv;
                             else end = true;
