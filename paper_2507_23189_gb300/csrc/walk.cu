@@ -905,7 +905,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
         u3 = __fdividef(u3, acc);
         ++ncoll;
         {   // Eq. 16 with the voxel's albedo
-            const float a = G.mu_a > 0.f ? G.ks_over_ke * (1.0f - G.mu_a / cell.x) : G.ks_over_ke;
+            const float a = G.mu_a > 0.f ? G.ks_over_ke * (1.0f - __fdividef(G.mu_a, cell.x)) : G.ks_over_ke;
             const float wn = w * a;
             if (a < 1.0f) T.abs += fix32(w - wn);
             w = wn;
@@ -1257,7 +1257,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                 if (u3 < acc) {
                     u3 = __fdividef(u3, acc);
                     ++ncoll;
-                    const float a = G.mu_a > 0.f ? G.ks_over_ke * (1.0f - G.mu_a / cell.x) : G.ks_over_ke;
+                    const float a = G.mu_a > 0.f ? G.ks_over_ke * (1.0f - __fdividef(G.mu_a, cell.x)) : G.ks_over_ke;
                     w = w * a;
                     int nb, pix_x, pix_z;
                     const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
