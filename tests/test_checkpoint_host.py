@@ -36,7 +36,8 @@ class FakeEngine:
 
     def result(self):
         return dict(raw_image=self.image.numpy().copy(), raw_totals=self.totals.numpy().copy(),
-                    radial=self.radial.numpy().copy())
+                    radial=self.radial.numpy().copy(),
+                    image=self.image.numpy().astype(np.float64) * 2.0 ** -self.image_frac_bits)
 
 
 @pytest.fixture
@@ -95,3 +96,29 @@ def test_watchdog_and_selftest_reject_bad_arguments(gpu_mod):
     assert L.mc_wait_selftest(C.cast(err, C.c_void_p), 0, None) == -1
     assert L.mc_wait_selftest(C.cast(err, C.c_void_p), (1 << 22) + 1, None) == -1
     assert L.mc_status_string(1) == b"work still running"
+
+
+def test_image_sigma_is_the_batch_means_error(gpu_mod, tmp_path):
+    """Equal chunks: sigma(image) = n sqrt(k) * sample std of the chunks'
+    per-photon images, computed here from the chunk images directly."""
+    from paper_2507_23189_gb300.checkpoint import run_resumable
+    med = gpu_mod.Medium(0.1, 0.0, "hg", 0.8, None)
+    n, k = 2500, 4
+    e = FakeEngine(gpu_mod)
+    r = run_resumable(e, med, n * k, str(tmp_path / "s.npz"), chunk=n, seed=5)
+    chunks = []
+    for c in range(k):
+        f = FakeEngine(gpu_mod)
+        f.run(med, n, seed=5, photon_offset=c * n, accumulate=True)
+        chunks.append(f.image.numpy().astype(np.float64) * 2.0 ** -32 / n)
+    chunks = np.stack(chunks)
+    want = n * np.sqrt(k) * chunks.std(axis=0, ddof=1)
+    np.testing.assert_allclose(r["image_sigma"], want, rtol=1e-9, atol=1e-12 * want.max())
+    # resumed after two chunks: the same errors
+    p2 = str(tmp_path / "s2.npz")
+    run_resumable(FakeEngine(gpu_mod), med, n * k, p2, chunk=n, seed=5, stop_after=2)
+    r2 = run_resumable(FakeEngine(gpu_mod), med, n * k, p2, chunk=n, seed=5)
+    np.testing.assert_allclose(r2["image_sigma"], r["image_sigma"], rtol=1e-12)
+    one = run_resumable(FakeEngine(gpu_mod), med, n, str(tmp_path / "one.npz"), chunk=n, seed=5)
+    assert one["image_sigma"] is None
+
