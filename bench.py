@@ -44,6 +44,8 @@ SEED = 1
 THREAD_INST_PER_STEP = 241.3          # ncu, 1e7-photon launch of this workload
 DRAM_BYTES_PER_LAUNCH = 596736        # same capture; fixed per launch (L2-resident tallies)
 LANES_PER_SM = 128
+SMEM_WAVEFRONTS_PER_STEP = 0.650       # same capture: shared-memory wavefronts (128 B each) per photon-step
+SMEM_BYTES_PER_CLK_SM = 128
 
 
 def _workload_config():
@@ -560,6 +562,14 @@ def run_engine(args):
         pk = peaks.measure(dev)
         line["issue_peaks"] = {"unit": "G ops/s (smem: GB/s)", "sms": pk["sms"],
                                **{k: v / 1e9 for k, v in pk.items() if k != "sms"}}
+    # the shared-memory pipe: wavefronts per step (ncu) x 128 B at the measured rate
+    smem_peak = (pk["smem_bytes"] / 1e12 if not args.no_peaks
+                 else sms * SMEM_BYTES_PER_CLK_SM * sm_max * 1e6 / 1e12)
+    smem_ach = SMEM_WAVEFRONTS_PER_STEP * SMEM_BYTES_PER_CLK_SM * steps_per_run / kernel_s / 1e12
+    line["smem_roofline"] = {"achieved": smem_ach, "peak": smem_peak, "unit": "TB/s", "frac": smem_ach / smem_peak,
+                             "peak_kind": "measured" if not args.no_peaks else "nominal",
+                             "per_unit": "%g shared-memory wavefronts of 128 B per photon-step (ncu)"
+                                         % SMEM_WAVEFRONTS_PER_STEP}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
