@@ -43,7 +43,8 @@ typedef enum {
     MC_ERR_OVERFLOW = -5, /* a fixed-point contribution exceeded 2^62          */
     MC_ERR_NUMERIC = -6,  /* a non-finite weight or contribution was seen      */
     MC_ERR_EVENTS = -7,   /* at least one photon hit max_events (truncated)    */
-    MC_ERR_TABLE = -8     /* the device table blob failed its header check     */
+    MC_ERR_TABLE = -8,    /* the device table blob failed its header check     */
+    MC_ERR_BOUNDS = -9    /* checked build only: an index check failed         */
 } mc_status;
 
 /* Device error-word bits (OR-ed by kernels into *d_error). */
@@ -52,6 +53,8 @@ typedef enum {
 #define MC_EFLAG_NUMERIC  0x4u
 #define MC_EFLAG_OVERFLOW 0x8u
 #define MC_EFLAG_TABLE    0x10u
+#define MC_EFLAG_BOUNDS   0x20u  /* checked build (MC_CHECKED) only: an index fell outside
+                                    its array; the access was clamped instead of made */
 
 /* ------------------------------------------------------------------------
  * Phase table (Sec. 2.2 Eq. 3-9, Sec. 2.4 Eq. 12, Sec. 2.5 Eq. 13-14,

@@ -11,8 +11,9 @@ LIB_PATH = os.path.join(HERE, "_build", "libmcmie.so")
 
 MC_OK, MC_NOT_READY = 0, 1
 STATUS = {1: "MC_NOT_READY", 0: "MC_OK", -1: "MC_ERR_ARG", -2: "MC_ERR_CUDA", -3: "MC_ERR_NOMEM", -4: "MC_ERR_TIMEOUT",
-          -5: "MC_ERR_OVERFLOW", -6: "MC_ERR_NUMERIC", -7: "MC_ERR_EVENTS", -8: "MC_ERR_TABLE"}
-EFLAG_EVENTS, EFLAG_TIMEOUT, EFLAG_NUMERIC, EFLAG_OVERFLOW, EFLAG_TABLE = 1, 2, 4, 8, 16
+          -5: "MC_ERR_OVERFLOW", -6: "MC_ERR_NUMERIC", -7: "MC_ERR_EVENTS", -8: "MC_ERR_TABLE",
+          -9: "MC_ERR_BOUNDS"}
+EFLAG_EVENTS, EFLAG_TIMEOUT, EFLAG_NUMERIC, EFLAG_OVERFLOW, EFLAG_TABLE, EFLAG_BOUNDS = 1, 2, 4, 8, 16, 32
 PHASE_TABLE, PHASE_HG, PHASE_PAPER = 0, 1, 2
 TOT_REFLECT, TOT_FAR, TOT_SIDE, TOT_ABSORB, TOT_ROULETTE, TOT_TRUNC, TOT_BALLISTIC, TOT_STEPS = range(8)
 N_TOTALS = 8
@@ -98,10 +99,14 @@ def lib():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
+    path = LIB_PATH
+    if os.environ.get("MC_CHECKED") == "1":
+        # the index-checked build (paper_2507_23189_gb300.build.build_checked())
+        path = os.path.join(HERE, "_build", "libmcmie_checked.so")
+    if not os.path.exists(path):
         raise RuntimeError("engine library %s is missing: run paper_2507_23189_gb300.build.build() "
-                           "(or __graft_entry__.build()) first" % LIB_PATH)
-    L = C.CDLL(LIB_PATH)
+                           "(or __graft_entry__.build()) first" % path)
+    L = C.CDLL(path)
     P = C.POINTER
     vp = C.c_void_p
     L.mc_table_bytes.restype = C.c_size_t

@@ -12,6 +12,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "_build", "libmcmie.so")
+# the same engine with every table, pixel, bin and voxel index checked at run
+# time (MC_CHECKED: an out-of-range index sets MC_EFLAG_BOUNDS and is clamped);
+# for tests, built only on request
+LIB_CHECKED = os.path.join(HERE, "_build", "libmcmie_checked.so")
 SOURCES = ["walk.cu", "api.cu", "mie_table.cpp", "noalloc.cu", "metrics.cu", "grid.cu"]
 HEADERS = ["engine.h", "table_format.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -47,6 +51,21 @@ def _compile(lib, sources, deps, force, verbose, extra):
     if verbose:
         print(" ".join(cmd))
     return subprocess.Popen(cmd), tmp, lib
+
+
+def build_checked(force=False, verbose=False):
+    """Compile the checked engine (-DMC_CHECKED) if missing or stale; return
+    its path. Loaded instead of the normal one when MC_CHECKED=1."""
+    me = os.path.abspath(__file__)
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [
+        os.path.join(ROOT, "include", "mcmie.h"), me]
+    job = _compile(LIB_CHECKED, SOURCES, deps, force, verbose, ["-DMC_CHECKED"])
+    if job is not None:
+        proc, tmp, lib = job
+        if proc.wait() != 0:
+            raise subprocess.CalledProcessError(proc.returncode, "nvcc")
+        os.replace(tmp, lib)
+    return LIB_CHECKED
 
 
 def build(force=False, verbose=False, extra=()):

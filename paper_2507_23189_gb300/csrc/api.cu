@@ -245,6 +245,17 @@ size_t mc_host_workspace_bytes(const mc_medium *medium, const mc_camera *camera)
            up(sizeof(uint32_t)) + up(mc_workspace_bytes(camera));
 }
 
+static mc_status flags_status(uint32_t h)
+{
+    if (h & MC_EFLAG_TIMEOUT) return MC_ERR_TIMEOUT;
+    if (h & MC_EFLAG_TABLE) return MC_ERR_TABLE;
+    if (h & MC_EFLAG_BOUNDS) return MC_ERR_BOUNDS;
+    if (h & MC_EFLAG_NUMERIC) return MC_ERR_NUMERIC;
+    if (h & MC_EFLAG_OVERFLOW) return MC_ERR_OVERFLOW;
+    if (h & MC_EFLAG_EVENTS) return MC_ERR_EVENTS;
+    return MC_OK;
+}
+
 mc_status mc_run_host(const mc_medium *medium, const void *table, const mc_geometry *geom,
                       const mc_camera *camera, const mc_run_params *run, int64_t *image,
                       int64_t *radial, int64_t *totals, uint32_t *error, void *d_work,
@@ -300,12 +311,7 @@ mc_status mc_run_host(const mc_medium *medium, const void *table, const mc_geome
         fail(cudaMemcpyAsync(error, t.d_error, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)))
         return MC_ERR_CUDA;
     if (fail(cudaStreamSynchronize(st))) return MC_ERR_CUDA;
-    if (*error & MC_EFLAG_TIMEOUT) return MC_ERR_TIMEOUT;
-    if (*error & MC_EFLAG_TABLE) return MC_ERR_TABLE;
-    if (*error & MC_EFLAG_NUMERIC) return MC_ERR_NUMERIC;
-    if (*error & MC_EFLAG_OVERFLOW) return MC_ERR_OVERFLOW;
-    if (*error & MC_EFLAG_EVENTS) return MC_ERR_EVENTS;
-    return MC_OK;
+    return flags_status(*error);
 }
 
 size_t mc_batch_workspace_bytes(int n_instances)
@@ -424,16 +430,6 @@ mc_status mc_adjoint(const mc_medium *medium, const mc_geometry *geom, const mc_
     return cuda_status(e);
 }
 
-static mc_status flags_status(uint32_t h)
-{
-    if (h & MC_EFLAG_TIMEOUT) return MC_ERR_TIMEOUT;
-    if (h & MC_EFLAG_TABLE) return MC_ERR_TABLE;
-    if (h & MC_EFLAG_NUMERIC) return MC_ERR_NUMERIC;
-    if (h & MC_EFLAG_OVERFLOW) return MC_ERR_OVERFLOW;
-    if (h & MC_EFLAG_EVENTS) return MC_ERR_EVENTS;
-    return MC_OK;
-}
-
 mc_status mc_check(const uint32_t *d_error, void *stream)
 {
     if (!d_error) return MC_ERR_ARG;
@@ -488,6 +484,7 @@ const char *mc_status_string(mc_status s)
     case MC_ERR_NUMERIC: return "non-finite value";
     case MC_ERR_EVENTS: return "photon reached max_events";
     case MC_ERR_TABLE: return "phase table header mismatch";
+    case MC_ERR_BOUNDS: return "index check failed (checked build)";
     }
     return "unknown status";
 }

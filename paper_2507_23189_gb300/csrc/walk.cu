@@ -31,6 +31,24 @@ constexpr float INV_2PI = 0.159154943091895335768883763372514f;
 constexpr float W_SCALE = 4294967296.0f;   // 2^32, weight tallies
 constexpr uint32_t WAIT_LIMIT = 1u << 22;  // mbarrier polls before giving up
 
+// Index check of the checked build (compiled with MC_CHECKED): an index
+// outside [0, n) sets MC_EFLAG_BOUNDS and is clamped into range, so a wrong
+// index is reported instead of read or written. The normal build returns
+// the index unchanged (n and err unused, their computation dropped).
+__device__ __forceinline__ int chk(int i, int n, uint32_t *err)
+{
+#ifdef MC_CHECKED
+    if ((unsigned)i >= (unsigned)n) {
+        atomicOr(err, MC_EFLAG_BOUNDS);
+        return i < 0 ? 0 : n - 1;
+    }
+#else
+    (void)n;
+    (void)err;
+#endif
+    return i;
+}
+
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon et al., SC'11): per round
 //   (c0,c1,c2,c3) <- (hi(M1 c2)^c1^k0, lo(M1 c2), hi(M0 c0)^c3^k1, lo(M0 c0)),
@@ -236,11 +254,11 @@ __device__ __forceinline__ float camera_psr(const MediumArgs &M, const CommonArg
     if (PHASE == MC_PHASE_PAPER) {
         // uniform in theta on each interval: density per radian / sin(theta)
         const float om = 1.0f - fminf(fmaxf(dy, -1.0f), 1.0f);
-        nb = lift_search(S.omu, S.pn, S.ptop, om);
+        nb = chk(lift_search(S.omu, S.pn, S.ptop, om), S.pn, C.error);
         const float st2 = om * (2.0f - om);
         return st2 > 0.0f ? S.pdf[nb] * rsqrtf(st2) * INV_2PI : 0.0f;
     }
-    nb = table_bin(S.omu, S.guide, C.n_bins, dy);
+    nb = chk(table_bin(S.omu, S.guide, C.n_bins, dy), C.n_bins, C.error);
     return S.pdf[nb] * INV_2PI;
 }
 
@@ -249,7 +267,7 @@ __device__ __forceinline__ int camera_pixel(const CommonArgs &C, float rx, float
 {
     ix = min(max(__float2int_rd(rx * C.sx), 0), C.nx - 1);
     iz = min(max(__float2int_rd((rz + C.hz) * C.sz), 0), C.nz - 1);
-    return iz * C.nx + ix;
+    return chk(iz * C.nx + ix, C.nx * C.nz, C.error);
 }
 
 // Polar angle as 1 - cos(theta) (accurate near the forward peak).
@@ -266,14 +284,14 @@ __device__ __forceinline__ float sample_omu(const MediumArgs &M, const CommonArg
         // index q (u1 = (q + 1/2) 2^-23 exactly), then linear interpolation
         // in theta: u1 - cdf_i = (q - k_i) 2^-23 + dl_i, fraction = that / w_i
         const int q = __float2int_rd(u1 * 8388608.0f);
-        const int i = lift_search(S.pk, S.pn, S.ptop, (uint32_t)q);
+        const int i = chk(lift_search(S.pk, S.pn, S.ptop, (uint32_t)q), S.pn, C.error);
         const float fr = fminf(fmaxf(fmaf((float)(q - (int)S.pk[i]), 1.1920928955078125e-7f, S.pdl[i]) *
                                          S.pri[i], 0.0f), 1.0f);
         const float sh = sinpif(0.5f * ((float)i + fr) * S.pinv);   // sin(theta / 2)
         return 2.0f * sh * sh;
     }
     const float tt = u1 * (float)C.n_bins;
-    const int i = (int)tt;
+    const int i = chk((int)tt, C.n_bins, C.error);
     const float f = tt - (float)i;
     const float o0 = S.omu[i], o1 = S.omu[i + 1];
     return fmaf(f, o1 - o0, o0);
@@ -515,7 +533,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
                 ex = C.lx; ey = fmaf(t, dy, ry); ez = fmaf(t, dz, rz);
                 const float r2 = fmaf(ey, ey, ez * ez);
                 const float rho = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-                rb = min(__float2int_rd(rho * C.sr), C.n_radial - 1);
+                rb = chk(min(__float2int_rd(rho * C.sr), C.n_radial - 1), C.n_radial, C.error);
                 sadd64(&s_rad[rb], wv);
                 status = 2;
             } else {
@@ -746,7 +764,7 @@ __device__ __forceinline__ int grid_flight(const GridArgs &G, const float *s_maj
     float t0 = 0.f;
     const int max_cross = G.mx + G.my + G.mz + 4;
     for (int it = 0; it < max_cross; ++it) {
-        mb = s_maj[(cz * G.my + cy) * G.mx + cx];
+        mb = s_maj[chk((cz * G.my + cy) * G.mx + cx, G.mx * G.my * G.mz, C.error)];
         const int ax = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
         const float t1 = fmaxf(ax == 0 ? tx : (ax == 1 ? ty : tz), t0);
         if (mb * (t1 - t0) > tau) {
@@ -883,7 +901,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
                 if (ncoll == 0) T.ball += wv;
                 const float r2 = fmaf(ry, ry, rz * rz);
                 const float rho = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-                rb = min(__float2int_rd(rho * C.sr), C.n_radial - 1);
+                rb = chk(min(__float2int_rd(rho * C.sr), C.n_radial - 1), C.n_radial, C.error);
                 sadd64(&s_rad[rb], wv);
                 status = 2;
             } else {
@@ -899,7 +917,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
         const int ix = min(max(__float2int_rd(rx * G.inv_vx), 0), G.gx - 1);
         const int iy = min(max(__float2int_rd((ry + C.hy) * G.inv_vy), 0), G.gy - 1);
         const int iz = min(max(__float2int_rd((rz + C.hz) * G.inv_vz), 0), G.gz - 1);
-        const float2 cell = __ldg(&G.cells[((size_t)iz * G.gy + iy) * G.gx + ix]);
+        const float2 cell = __ldg(&G.cells[chk((iz * G.gy + iy) * G.gx + ix, G.gx * G.gy * G.gz, C.error)]);
         const float acc = __fdividef(cell.x, mb);   // hardware reciprocal: a few ulp
         if (!(u3 < acc)) continue;   // null collision
         u3 = __fdividef(u3, acc);
@@ -1122,7 +1140,7 @@ __device__ __forceinline__ void raster_unit(const GridArgs &G, double *grad, con
         const bool bfirst = nextB <= nextC;
         const float m = fminf(nextB, nextC);
         const float e = fminf(m, t1);
-        if (e > t) atomicAdd(&grad[v], widen(coef * (e - t)));
+        if (e > t) atomicAdd(&grad[chk(v, G.gx * G.gy * G.gz, G.c.error)], widen(coef * (e - t)));
         t = e;
         if (!(m < t1)) break;
         if (bfirst) {
@@ -1251,7 +1269,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                 const int ix = min(max(__float2int_rd(rx * G.inv_vx), 0), G.gx - 1);
                 const int iy = min(max(__float2int_rd((ry + C.hy) * G.inv_vy), 0), G.gy - 1);
                 const int iz = min(max(__float2int_rd((rz + C.hz) * G.inv_vz), 0), G.gz - 1);
-                const size_t v = ((size_t)iz * G.gy + iy) * G.gx + ix;
+                const size_t v = chk((iz * G.gy + iy) * G.gx + ix, G.gx * G.gy * G.gz, C.error);
                 const float2 cell = __ldg(&G.cells[v]);
                 const float acc = __fdividef(cell.x, mb);   // hardware reciprocal: a few ulp
                 if (u3 < acc) {
@@ -1586,7 +1604,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
                 kahan_add(gs_z, gc_z, jj * Aj);
                 if (PHASEW && Aj != 0.0f) {
                     float f;
-                    const int k = hat_pair(nw, dy, f);
+                    const int k = chk(hat_pair(nw, dy, f), nw - 1, C.error);
                     hat_add(rows, B, k, f, Aj);
                 }
             }
@@ -1596,7 +1614,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
                 const float om = sample_omu<PHASE>(M, C, S, u1);
                 if (PHASEW) {
                     float f;
-                    const int k = hat_pair(nw, 1.0f - om, f);
+                    const int k = chk(hat_pair(nw, 1.0f - om, f), nw - 1, C.error);
                     if (pass == 1) {
 #pragma unroll
                         for (int q = 0; q < ADJ_LIST; ++q)
