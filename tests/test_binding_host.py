@@ -1,0 +1,49 @@
+"""Host-side pieces of the Python binding that need no GPU: the trace record
+decoder (the layout include/mcmie.h documents for mc_trace) and the medium
+argument checks."""
+import numpy as np
+import pytest
+
+import paper_2507_23189_gb300 as gpu
+
+
+def test_decode_trace_reads_the_documented_record():
+    rec = np.zeros((2, 3, 12), dtype=np.int32)
+    f = rec.view(np.float32)
+    rec[0, 0, 0] = 0                                   # collision
+    f[0, 0, 1:4] = (1.5, -2.25, 3.0)                   # position after the flight
+    f[0, 0, 4:7] = (0.6, 0.0, -0.8)                    # direction after the event
+    f[0, 0, 7] = 0.875                                 # weight
+    f[0, 0, 8] = 1.25e-3                               # camera contribution
+    rec[0, 0, 9:12] = (4099, 17, -1)                   # pixel, camera table bin, radial bin
+    rec[0, 1, 0] = 2                                   # far-face exit
+    rec[0, 1, 11] = 63
+    rec[1, :, 0] = -1                                  # no event recorded
+    t = gpu.decode_trace(rec)
+    assert t["status"].tolist() == [[0, 2, 0], [-1, -1, -1]]
+    np.testing.assert_array_equal(t["r"][0, 0], [1.5, -2.25, 3.0])
+    np.testing.assert_array_equal(t["d"][0, 0], [0.6000000238418579, 0.0, -0.800000011920929])
+    assert t["w"][0, 0] == 0.875 and t["nee"][0, 0] == np.float32(1.25e-3)
+    assert (t["pix"][0, 0], t["nee_bin"][0, 0], t["rad_bin"][0, 0]) == (4099, 17, -1)
+    assert t["rad_bin"][0, 1] == 63
+    assert t["r"].dtype == np.float64 and t["pix"].dtype == np.int32
+
+
+def test_medium_phase_checks():
+    m = gpu.Medium(0.1, 0.0, "paper", 0.0, None)
+    with pytest.raises(ValueError):
+        m.as_c()                                       # the paper scheme needs a PaperTable
+    with pytest.raises(ValueError):
+        gpu.Medium(0.1, 0.0, "isotropic", 0.0, None).as_c()
+    c, keep = gpu.Medium(0.2, 0.01, "hg", 0.85, None).as_c()
+    assert keep is None and (c.mu_s, c.mu_a, c.hg_g) == pytest.approx((0.2, 0.01, 0.85))
+
+
+def test_run_params_carry_every_field():
+    rp = gpu.run_params(123, seed=7, photon_offset=5, rr_threshold=1e-3, rr_survival=0.0, max_events=99,
+                        max_scatter=2, image_frac_bits=24, accumulate=True, block_size=512, blocks_per_sm=1,
+                        image_mode=2)
+    assert (rp.n_photons, rp.photon_offset, rp.seed, rp.max_events, rp.max_scatter, rp.image_frac_bits,
+            rp.accumulate, rp.block_size, rp.blocks_per_sm, rp.image_mode) == (123, 5, 7, 99, 2, 24, 1, 512,
+                                                                              1, 2)
+    assert (rp.rr_threshold, rp.rr_survival) == (1e-3, 0.0)
