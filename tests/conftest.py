@@ -1,5 +1,6 @@
 import os
 import sys
+import tempfile
 
 import pytest
 
@@ -7,14 +8,18 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# Everything the tests write (pytest's tmp_path, tempfile, the rendezvous files
+# of torchrun children) stays inside the working tree, under .tmp/.
+TMP = os.path.join(ROOT, ".tmp")
+os.makedirs(TMP, exist_ok=True)
+os.environ["TMPDIR"] = TMP
+tempfile.tempdir = TMP
+
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built engine")
-
-
-def pytest_collection_modifyitems(config, items):
-    # A file whose name sorts last runs last; keep pytest's file order otherwise.
-    pass
+    if config.option.basetemp is None:
+        config.option.basetemp = os.path.join(TMP, "pytest")
 
 
 @pytest.fixture(scope="session")

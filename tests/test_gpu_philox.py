@@ -2,7 +2,6 @@
 import ctypes as C
 import os
 import subprocess
-import tempfile
 
 import numpy as np
 import pytest
@@ -41,11 +40,10 @@ def test_device_philox_matches_oracle(gpu, oracle_mod, seed):
     np.testing.assert_array_equal(out, oracle_mod.philox4x32_10(c, seed))
 
 
-def test_device_philox_matches_curand(gpu):
+def test_device_philox_matches_curand(gpu, tmp_path):
     import torch
-    d = tempfile.mkdtemp()
-    src = os.path.join(d, "ref.cu")
-    so = os.path.join(d, "libref.so")
+    src = os.path.join(tmp_path, "ref.cu")
+    so = os.path.join(tmp_path, "libref.so")
     open(src, "w").write(_CURAND_REF)
     subprocess.run(["nvcc", "-gencode=arch=compute_103a,code=sm_103a", "-shared", "-Xcompiler",
                     "-fPIC", "-o", so, src], check=True)
