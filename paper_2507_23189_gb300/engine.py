@@ -26,6 +26,16 @@ def _stream_handle(stream):
     return C.c_void_p(s.cuda_stream)
 
 
+def _fresh_error(error, stream, accumulate):
+    """A run that starts its tallies afresh starts its error word afresh, on
+    the launch stream; an accumulating run keeps the flags of the tallies it
+    adds to."""
+    if not accumulate:
+        torch = _torch()
+        with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream(error.device)):
+            error.zero_()
+
+
 # --------------------------------------------------------------------- table
 
 
@@ -283,11 +293,14 @@ class Engine:
                          self.error.data_ptr(), self.work.data_ptr(), self.work.numel())
 
     def run(self, medium, n_photons, seed=1, stream=None, **kw):
-        """Queue photons on the stream (asynchronous)."""
+        """Queue photons on the stream (asynchronous). Without accumulate=True
+        the tallies and the error word start afresh; check() reports the
+        flags of everything run into the tallies since."""
         rp = run_params(n_photons, seed, **kw)
         self.image_frac_bits = rp.image_frac_bits
         m, keep = medium.as_c(self.device)
         g, c, t = self.geometry.as_c(), self.camera.as_c(), self._tallies()
+        _fresh_error(self.error, stream, rp.accumulate)
         N.check("mc_run", N.lib().mc_run(C.byref(m), C.byref(g), C.byref(c), C.byref(rp), C.byref(t),
                                          _stream_handle(stream)))
         self._keep = keep
@@ -302,6 +315,7 @@ class Engine:
         m, keep = medium.as_c(self.device)
         buf = torch.empty((n_trace, n_events, N.TRACE_WORDS), dtype=torch.int32, device=self.device)
         g, c, t = self.geometry.as_c(), self.camera.as_c(), self._tallies()
+        _fresh_error(self.error, stream, rp.accumulate)
         N.check("mc_trace", N.lib().mc_trace(C.byref(m), C.byref(g), C.byref(c), C.byref(rp),
                                              C.byref(t), C.c_void_p(buf.data_ptr()), n_trace, n_events,
                                              _stream_handle(stream)))
@@ -346,6 +360,7 @@ class Engine:
         tr = None
         if n_trace:
             tr = torch.empty(n_trace * n_events * N.TRACE_WORDS, dtype=torch.int32, device=self.device)
+        _fresh_error(self.error, stream, rp.accumulate)
         N.check("mc_run_grid", N.lib().mc_run_grid(
             C.byref(g), C.c_void_p(grid.work.data_ptr()), C.byref(m), C.byref(geo), C.byref(c), C.byref(rp),
             C.byref(t), C.c_void_p(tr.data_ptr()) if tr is not None else None, n_trace, n_events,
@@ -369,10 +384,12 @@ class Engine:
             raise ValueError("adjoint image must be [nz, nx]")
         g, geo, c = grid.as_c(), self.geometry.as_c(), self.camera.as_c()
         nbytes = N.lib().mc_grid_adjoint_workspace_bytes(C.byref(g))
+        if nbytes == 0:
+            raise N.McError("mc_grid_adjoint_workspace_bytes", -1)
         work = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         grad = torch.empty(tuple(grid.density.shape), dtype=torch.float32, device=self.device)
         value = torch.empty(1, dtype=torch.float64, device=self.device)
-        self.error.zero_()
+        _fresh_error(self.error, stream, False)
         vp = C.c_void_p
         N.check("mc_grid_adjoint", N.lib().mc_grid_adjoint(
             C.byref(g), vp(grid.work.data_ptr()), C.byref(m), C.byref(geo), C.byref(c), C.byref(rp),
@@ -448,6 +465,7 @@ class Batch:
             arr[i].d_radial = self.radial[i].data_ptr()
             arr[i].d_totals = self.totals[i].data_ptr()
         g, c = self.geometry.as_c(), self.camera.as_c()
+        _fresh_error(self.error, stream, rp.accumulate)
         N.check("mc_run_batch", N.lib().mc_run_batch(
             n, arr, C.byref(g), C.byref(c), C.byref(rp), int(item_photons),
             C.c_void_p(self.error.data_ptr()), C.c_void_p(self.work.data_ptr()), self.work.numel(),
@@ -498,6 +516,7 @@ def _make_camera_image():
         @staticmethod
         def backward(ctx, grad_img):
             out = ctx.engine.adjoint(ctx.med, grad_img, ctx.n, n_w=ctx.n_w, seed=ctx.seed, **ctx.kw)
+            ctx.engine.check()
             ds, da, dw = ctx.devs
             gw = out[3:].to(dw) if ctx.n_w else None
             return out[1].to(ds), out[2].to(da), gw, None, None, None, None, None

@@ -47,3 +47,42 @@ def test_run_params_carry_every_field():
             rp.accumulate, rp.block_size, rp.blocks_per_sm, rp.image_mode) == (123, 5, 7, 99, 2, 24, 1, 512,
                                                                               1, 2)
     assert (rp.rr_threshold, rp.rr_survival) == (1e-3, 0.0)
+
+
+def test_fresh_error_resets_on_the_launch_stream_only_for_fresh_tallies(monkeypatch):
+    import contextlib
+    import types
+
+    import torch
+
+    from paper_2507_23189_gb300 import engine as eng_mod
+    log = []
+
+    @contextlib.contextmanager
+    def stream_ctx(s):
+        log.append(("enter", s))
+        yield
+        log.append(("exit", s))
+
+    fake = types.SimpleNamespace(cuda=types.SimpleNamespace(
+        stream=stream_ctx, current_stream=lambda dev=None: ("current", str(dev))))
+    monkeypatch.setattr(eng_mod, "_torch", lambda: fake)
+
+    class Word:
+        device = torch.device("cpu")
+
+        def __init__(self):
+            self.v = 0x7
+
+        def zero_(self):
+            log.append(("zero",))
+            self.v = 0
+
+    w = Word()
+    eng_mod._fresh_error(w, "s1", True)                # accumulating: flags stay
+    assert w.v == 0x7 and log == []
+    eng_mod._fresh_error(w, "s1", False)               # fresh tallies: zeroed inside the launch stream
+    assert w.v == 0 and log == [("enter", "s1"), ("zero",), ("exit", "s1")]
+    log.clear()
+    eng_mod._fresh_error(w, None, 0)                   # no stream given: the device's current stream
+    assert log[0] == ("enter", ("current", "cpu")) and log[1] == ("zero",)
