@@ -37,10 +37,22 @@ def test_library_exports_every_declared_symbol(eng):
     assert set(declared) <= set(N.EXPORTS)
 
 
+def test_checked_build_compiles_and_exports_every_declared_symbol(eng):
+    # the index-checked variant (MC_CHECKED) is the same entry points with
+    # bounds checks compiled into the kernels
+    from paper_2507_23189_gb300 import build
+    L = C.CDLL(build.build_checked())
+    for name in _declared_functions():
+        assert hasattr(L, name), name
+    L.mc_status_string.restype = C.c_char_p
+    assert b"checked" in L.mc_status_string(-9)
+
+
 def test_status_strings(eng):
     L = eng.lib()
-    for s in range(-8, 1):
-        assert L.mc_status_string(s)
+    for s in range(-9, 2):
+        assert L.mc_status_string(s) and L.mc_status_string(s) != b"unknown status"
+    assert L.mc_status_string(-10) == b"unknown status"
 
 
 def test_table_bytes(eng):
