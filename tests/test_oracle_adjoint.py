@@ -97,6 +97,20 @@ def test_gradient_matches_common_random_number_difference(oracle_mod, table):
         assert abs(g[i] - fd) < 5 * sig[i] * math.sqrt(2), (i, g[i], fd, sig[i])
 
 
+@pytest.mark.parametrize("n_w", [2, 7, 64])
+def test_phase_weight_gradient_is_scale_invariant(oracle_mod, table, n_w):
+    """The hats sum to one at every cosine, so w -> c w leaves the
+    normalised phase function p h_w / Z(w) unchanged: on every path the
+    weight derivatives sum to zero (to rounding), whatever the number of
+    collisions; and the normalisation integrals Z_k sum to one."""
+    assert oracle_mod.hat_integrals(table, n_w).sum() == pytest.approx(1.0, abs=1e-14)
+    adj = np.random.default_rng(3).uniform(0, 1, (16, 16))
+    r = oracle_mod.adjoint(adj, n_w, table=table, mu_s=10 / LX, mu_a=0.01, n_photons=20_000, nx=16, nz=16,
+                           seed=5)
+    g = r["grad"][2:]
+    assert abs(g.sum()) < 1e-12 * np.abs(g).sum() + 1e-300 and np.abs(g).sum() > 0
+
+
 def test_phase_weight_gradient_matches_weighted_tables(oracle_mod, table):
     """Multiple scattering: d/dw_k against a central difference of E[L]
     over tables built for p h_w / Z(w) with w_k = 1 +- eps, each side

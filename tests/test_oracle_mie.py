@@ -142,6 +142,33 @@ def test_paper_worked_values(oracle_mod):
     assert abs(x - t["x"]) <= t["abs_tol"]
 
 
+def test_size_parameter_is_the_wavelength_in_the_medium(oracle_mod):
+    """A sphere in a medium of index n at vacuum wavelength lambda0 scatters
+    as the same sphere (index relative to the medium) in vacuum at
+    lambda0 / n: the size parameter may depend on n and lambda0 only through
+    lambda0 / n, and in vacuum it is the circumference over the wavelength."""
+    for d, n, lam in ((5.0, 1.33, 532.0), (1.0, 1.5, 633.0), (10.0, 1.0, 400.0)):
+        x = oracle_mod.size_parameter(d, n, lam)
+        assert x == pytest.approx(oracle_mod.size_parameter(d, 1.0, lam / n), rel=1e-14)
+        assert oracle_mod.size_parameter(d, 1.0, lam / n) == pytest.approx(
+            oracle_mod.size_parameter(2 * d, 1.0, 2 * lam / n), rel=1e-14)
+    assert oracle_mod.size_parameter(1.0, 1.0, 1000.0 * np.pi) == pytest.approx(1.0, rel=1e-14)
+
+
+@pytest.mark.parametrize("m,x", [(M_PS, 10.0), (M_PS, 39.26990816987241), (complex(1.5, 0.1), 39.26990816987241)])
+def test_series_is_summed_to_convergence(oracle_mod, m, x):
+    """The oracle stops the Mie series after nmax terms; with 40 more terms of
+    the 50-digit coefficients (Eq. 7-8) the Eq. 13 sums must not move."""
+    n = oracle_mod.nmax(x) + 40
+    a, b = _mp_ab(m, x, n)
+    k = np.arange(1, n + 1)
+    qe_ref = 2.0 / x ** 2 * np.sum((2 * k + 1) * np.real(a + b))
+    qs_ref = 2.0 / x ** 2 * np.sum((2 * k + 1) * (np.abs(a) ** 2 + np.abs(b) ** 2))
+    qe, qs, _ = oracle_mod.mie_efficiencies(m, x)
+    assert qe == pytest.approx(qe_ref, rel=1e-9)
+    assert qs == pytest.approx(qs_ref, rel=1e-9)
+
+
 def test_eq17_optical_depth_roundtrip(oracle_mod):
     qe, _, _ = oracle_mod.mie_efficiencies(M_PS, oracle_mod.size_parameter(5.0, 1.33, 532.0))
     sig = oracle_mod.cross_section_mm2(qe, 5.0)

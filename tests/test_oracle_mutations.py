@@ -1,0 +1,184 @@
+"""Planted mistakes in the oracle: each entry changes one expression of a
+copy of oracle/ the way a plausible slip would (a dropped term, a wrong sign,
+index, factor or constant) and runs the oracle's pins against that copy. Every
+mistake must make a pin fail, and the unchanged copy must pass the same pins,
+so the pins are shown to fix the oracle rather than only to agree with it.
+Nothing here touches the oracle in the tree; copies live in pytest's tmp_path."""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+WALK = ["test_oracle_walk.py"]
+MIE = ["test_oracle_mie.py"]
+TABLE = ["test_oracle_table.py"]
+PHILOX = ["test_oracle_philox.py"]
+ADJ = ["test_oracle_adjoint.py"]
+GRID = ["test_oracle_grid.py"]
+GADJ = ["test_oracle_grid_adjoint.py"]
+PAPER = ["test_oracle_paper.py"]
+
+# (file, text, replacement, pin files, the mistake)
+MUTATIONS = [
+    # Mie series (Sec. 2.2 Eq. 3-9)
+    ("mie.c", "double complex ta = D[n] / m + (double)n / x;", "double complex ta = D[n] * m + (double)n / x;",
+     MIE, "a_n built with m D_n (a_n and b_n confused)"),
+    ("mie.c", "double tau_n = n * mu * pi_n - (n + 1.0) * pi_nm1;", "double tau_n = n * mu * pi_n - n * pi_nm1;",
+     MIE, "tau_n recurrence off by one"),
+    ("mie.c", "se += (2.0 * n + 1.0) * creal(a[n] + b[n]);", "se += (2.0 * n + 1.0) * creal(a[n] - b[n]);",
+     MIE, "sign of b_n in Q_ext"),
+    ("mie.c", "        sg += (2.0 * n + 1.0) / ((double)n * (n + 1.0)) * creal(a[n] * conj(b[n]));\n", "",
+     MIE, "g series without its a_n b_n* term"),
+    ("mie.c", "double lambda_um = (lambda0_nm * 1e-3) / n_medium;", "double lambda_um = (lambda0_nm * 1e-3);",
+     MIE, "size parameter with the vacuum wavelength"),
+    ("mie.c", "return (int)ceil(x + 4.0 * cbrt(x) + 2.0);", "return (int)ceil(x + 2.0);",
+     MIE, "Mie series truncated early"),
+    # phase table (Sec. 3.1.2, Eq. 10)
+    ("table.c", "cum[p + 1] = cum[p] + h / 3.0 * (F[j] + 4.0 * F[j + 1] + F[j + 2]);",
+     "cum[p + 1] = cum[p] + h / 3.0 * (F[j] + 2.0 * F[j + 1] + F[j + 2]);", TABLE, "Simpson weights"),
+    ("table.c", "F[j] *= 0.5 * sin((double)(n_fine - j) * h);", "F[j] *= 0.5;", TABLE,
+     "solid-angle factor sin(theta) dropped"),
+    ("table.c", "double theta = (double)(n_fine - j) * h - s;", "double theta = (double)(n_fine - j) * h + s;",
+     TABLE, "panel inversion measured from the wrong end"),
+    ("table.c", "pdf[i] = (1.0 / n_bins) / (t_omu[i] - t_omu[i + 1]);", "pdf[i] = (1.0 / n_bins) / (t_omu[i] + t_omu[i + 1]);",
+     TABLE, "bin density"),
+    ("table.c", "double target = Z * ((double)i / n_bins);", "double target = Z * ((double)(i - 1) / n_bins);",
+     TABLE, "inversion levels shifted by one"),
+    # Philox4x32-10 and the uniforms
+    ("philox.c", "k1 += 0xBB67AE85u;", "k1 += 0xBB67AE84u;", PHILOX, "Weyl constant"),
+    ("philox.c", "uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;", "uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k1;",
+     PHILOX, "round key word"),
+    ("philox.c", "return (double)(r >> 9) * 0x1p-23 + 0x1p-24;", "return (double)(r >> 9) * 0x1p-23;", PHILOX,
+     "uniform not centred (can be 0)"),
+    # the walk (Sec. 3.1.3 Eq. 15-16, the camera of Sec. 4.3)
+    ("walk.c", "double s = mu_ext > 0.0 ? -log(u0) / mu_ext : INFINITY;",
+     "double s = mu_ext > 0.0 ? -log(u0) * mu_ext : INFINITY;", WALK, "free path in the wrong units (Eq. 15)"),
+    ("walk.c", "w = w * (1.0 - mua_here / mu_here);", "w = w * (1.0 - 0.5 * mua_here / mu_here);", WALK,
+     "albedo (Eq. 16)"),
+    ("walk.c", "double nee = w * psr * exp(-od);", "double nee = w * psr * exp(-0.5 * od);", WALK,
+     "camera transmittance"),
+    ("walk.c", "psr = pdf / (2.0 * M_PI);", "psr = pdf / (4.0 * M_PI);", WALK, "table density per steradian"),
+    ("walk.c", "return (1.0 - g * g) / (4.0 * M_PI * t * sqrt(t));", "return (1.0 - g * g) / (4.0 * M_PI * t);",
+     WALK, "H-G density (Eq. 11)"),
+    ("walk.c", "double fz = (r[2] - lo[2]) / c->lz * c->nz;", "double fz = (r[2] + lo[2]) / c->lz * c->nz;", WALK,
+     "image row sign"),
+    ("walk.c", "double phi = 2.0 * M_PI * u2;", "double phi = M_PI * u2;", WALK, "azimuth on [0, pi)"),
+    ("walk.c", "    double b = d[0] * d[1] * a;\n            double e1[3]",
+     "    double b = d[0] * d[2] * a;\n            double e1[3]", WALK, "basis vector index"),
+    ("walk.c", "double wn = w / c->rr_survival;", "double wn = w;", WALK, "roulette survivor not reweighted"),
+    ("walk.c", "if (face == 0 && d[0] < 0.0) {", "if (face == 0 && d[0] > 0.0) {", WALK,
+     "reflection and transmission faces swapped"),
+    ("walk.c", "omu = c->omu[i] + f * (c->omu[i + 1] - c->omu[i]);", "omu = c->omu[i];", WALK,
+     "table sample without interpolation"),
+    ("walk.c", "nbin = table_bin(c->icdf, c->n_bins, muc);", "nbin = table_bin(c->icdf, c->n_bins, -muc);", WALK,
+     "camera cosine sign"),
+    # delta tracking (heterogeneous media)
+    ("walk.c", "const double s = tau / mb;", "const double s = tau * mb;", GRID, "tentative flight length"),
+    ("walk.c", "tau -= mb * t;", "tau -= t;", GRID, "optical depth spent in a cell"),
+    ("walk.c", "for (int j = iy + 1; j < c->gy; ++j)\n        od +=", "for (int j = iy; j < c->gy; ++j)\n        od +=",
+     GRID, "camera column counts its own voxel twice"),
+    ("walk.c", "const double acc = mu_here / mubar;", "const double acc = 0.5 * (1.0 + mu_here / mubar);", GRID,
+     "acceptance probability"),
+    ("walk.c", "u3 = u3 / acc;  /* uniform", "u3 = u3;  /* uniform", GRID, "roulette number not rescaled"),
+    # the paper's sampler (Sec. 3.1.2)
+    ("walk.c", "double th = (i + f) * (M_PI / n);", "double th = (i + 0.5) * (M_PI / n);", PAPER,
+     "no interpolation inside the angle interval"),
+    ("walk.c", "psr = stc > 0.0 ? pth / stc / (2.0 * M_PI) : 0.0;", "psr = pth / (2.0 * M_PI);", PAPER,
+     "camera density per radian, not per unit cosine"),
+    # the adjoint (gradients of Eq. 15-16)
+    ("adjoint.c", "S += 1.0 / mu_ext - s;", "S += 1.0 / mu_ext + s;", ADJ, "sign of the flight score"),
+    ("adjoint.c", "pg[0] += A * (R.S[j] + jj * (1.0 / c->mu_s - 1.0 / mu_ext) - R.l[j]);",
+     "pg[0] += A * (R.S[j] + jj * (1.0 / c->mu_s - 1.0 / mu_ext));", ADJ, "transport term dropped"),
+    ("adjoint.c", "pg[1] += A * (R.S[j] - jj / mu_ext - R.l[j]);", "pg[1] += A * (R.S[j] + jj / mu_ext - R.l[j]);",
+     ADJ, "sign of the albedo term"),
+    ("adjoint.c", "double t = oracle_hat(J->n_w, q, R.muc[j]) - jj * J->z[q];",
+     "double t = oracle_hat(J->n_w, q, R.muc[j]) - J->z[q];", ADJ, "normalisation counted once"),
+    ("adjoint.c", "for (int i = 0; i < j; ++i)\n                    t +=", "for (int i = 1; i < j; ++i)\n                    t +=",
+     ADJ, "range of the sampled-angle sum"),
+    ("adjoint.c", "grad[vi] += B * c->k_ext / mu;", "grad[vi] += B / mu;", GADJ, "collision point term"),
+    ("adjoint.c", "grad[vi] -= A[i] * c->k_ext * (top - ri[1]);", "grad[vi] -= A[i] * c->k_ext * (top + ri[1]);",
+     GADJ, "camera column inside the collision voxel"),
+    ("adjoint.c", "segment_voxels(c, lo, prev, ri, -B * c->k_ext, grad, ts, ts_cap);",
+     "segment_voxels(c, lo, prev, ri, B * c->k_ext, grad, ts, ts_cap);", GADJ, "sign of the flight transmission"),
+]
+
+
+def _copy(dst):
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"),
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+
+
+def _pins(root, files, basetemp):
+    """Run the pin files against the oracle copy under `root` (it comes first
+    on the import path: the working directory of the child)."""
+    env = dict(os.environ, PYTHONPATH=root + os.pathsep + ROOT)
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
+           "--basetemp", basetemp] + [os.path.join(ROOT, "tests", f) for f in files]
+    p = subprocess.run(cmd, cwd=root, env=env, capture_output=True, text=True, timeout=900)
+    return p.returncode, p.stdout[-1500:] + p.stderr[-1500:]
+
+
+def _compiles(root):
+    src = [os.path.join(root, "oracle", s) for s in ("mie.c", "table.c", "philox.c", "walk.c", "adjoint.c")]
+    p = subprocess.run(["gcc", "-std=c11", "-D_GNU_SOURCE", "-fsyntax-only", "-Wall"] + src,
+                       capture_output=True, text=True)
+    return p.returncode == 0, p.stderr[-800:]
+
+
+@pytest.fixture(scope="module")
+def workdir(tmp_path_factory):
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    return tmp_path_factory.mktemp("mut")
+
+
+def test_every_planted_mistake_applies_once():
+    for fname, old, new, _, what in MUTATIONS:
+        text = open(os.path.join(ROOT, "oracle", fname)).read()
+        assert text.count(old) == 1, (fname, what)
+        assert old != new
+
+
+def _pool():
+    return ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1)))
+
+
+def test_unchanged_copy_passes_the_pins(workdir):
+    root = str(workdir / "control")
+    _copy(root)
+    files = sorted({f for m in MUTATIONS for f in m[3]})
+    subprocess.run([sys.executable, os.path.join(root, "oracle", "build.py")], check=True, capture_output=True)
+    # a child started like the pin runs imports the copy, not the oracle in the tree
+    p = subprocess.run([sys.executable, "-c", "import oracle; print(oracle.__file__)"], cwd=root,
+                       env=dict(os.environ, PYTHONPATH=root + os.pathsep + ROOT), capture_output=True, text=True)
+    assert os.path.dirname(p.stdout.strip()) == os.path.join(root, "oracle"), p.stdout + p.stderr
+    with _pool() as ex:   # one child per pin file, all on the copy built above
+        results = list(ex.map(lambda f: (f, _pins(root, [f], str(workdir / ("control_bt_" + f[:-3])))), files))
+    for f, (rc, out) in results:
+        assert rc == 0, (f, out)
+
+
+def test_every_planted_mistake_fails_a_pin(workdir):
+    def one(k):
+        fname, old, new, files, what = MUTATIONS[k]
+        root = str(workdir / ("m%02d" % k))
+        _copy(root)
+        path = os.path.join(root, "oracle", fname)
+        text = open(path).read()
+        open(path, "w").write(text.replace(old, new, 1))
+        ok, err = _compiles(root)
+        if not ok:
+            return k, "does not compile: " + err
+        rc, out = _pins(root, files, str(workdir / ("m%02d_bt" % k)))
+        # exit status 1: tests ran and at least one failed
+        return k, None if rc == 1 and "failed" in out else "not caught (exit %d): %s" % (rc, out[-600:])
+
+    with _pool() as ex:
+        results = list(ex.map(one, range(len(MUTATIONS))))
+    missed = ["%s: %s -> %s" % (MUTATIONS[k][0], MUTATIONS[k][4], why) for k, why in results if why]
+    assert not missed, "\n".join(missed)

@@ -125,6 +125,28 @@ def test_deterministic_weight_cut(oracle_mod):
     assert r["steps"] == int(np.sum(st >= 0))
 
 
+def test_roulette_is_unbiased(oracle_mod):
+    """Roulette changes the spread of the estimates, not their expectation:
+    with absorption and a threshold most photons reach, the net weight it
+    removes averages to zero, and every weight total agrees with the walk
+    without roulette (independent seeds, 4 standard errors)."""
+    mu_ext, a, n = 5.0 / LX, 0.7, 1_000_000
+    kw = dict(mu_s=a * mu_ext, mu_a=(1 - a) * mu_ext, phase="hg", hg_g=0.5, n_photons=n, nx=8, nz=8)
+    plain = oracle_mod.walk(rr_threshold=0.0, rr_survival=1.0, seed=3, **kw)
+    rr = oracle_mod.walk(rr_threshold=0.3, rr_survival=0.25, seed=4, **kw)
+    assert rr["steps"] < 0.97 * plain["steps"]        # roulette ends many walks early
+
+    def mean_se(r, k):
+        m = r["totals"][k] / n
+        return m, math.sqrt(max(r["totals_sq"][k] / n - m * m, 0.0) / n)
+
+    m, se = mean_se(rr, 4)
+    assert se > 0 and abs(m) < 4 * se
+    for k in (0, 1, 2, 3):                            # R, T far, T side, absorbed
+        (m0, s0), (m1, s1) = mean_se(plain, k), mean_se(rr, k)
+        assert abs(m1 - m0) < 4 * math.hypot(s0, s1), (k, m0, m1)
+
+
 def test_mean_free_path(oracle_mod):
     mu_ext, n = 0.25, 4000
     big = 1e9
