@@ -74,3 +74,16 @@ def test_compare_identical_and_better_share():
     np.testing.assert_array_equal(out[13:21], out[21:29])
     single = M.compare(ref, ref, None, n_r=8)
     assert np.all(single[6:13] == 0.0) and np.all(single[29:] == 0.0)
+
+
+def test_better_share_counts_only_rings_with_pixels():
+    """Hand-worked 2 x 2 case: every pixel centre lies at half the
+    half-diagonal, so with 4 rings only ring 2 holds pixels. Normalised, ref
+    and a average 1/2 there and b averages 3/4: a is closer on the one ring
+    that has pixels, a share of 1 (not 1/4), and the empty rings stay 0."""
+    ref = np.array([[0, 1], [1, 0]])
+    b = np.array([[0, 1], [1, 1]])
+    out = M.compare(ref, ref.copy(), b, n_r=4)
+    assert out[12] == 1.0
+    np.testing.assert_array_equal(out[13:17], [0.0, 0.0, 0.5, 0.0])       # profile of ref
+    np.testing.assert_array_equal(out[21:25], [0.0, 0.0, 0.75, 0.0])      # profile of b

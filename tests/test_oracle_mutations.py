@@ -22,6 +22,7 @@ ADJ = ["test_oracle_adjoint.py"]
 GRID = ["test_oracle_grid.py"]
 GADJ = ["test_oracle_grid_adjoint.py"]
 PAPER = ["test_oracle_paper.py"]
+METRICS = ["test_oracle_metrics.py"]
 
 # (file, text, replacement, pin files, the mistake)
 MUTATIONS = [
@@ -90,6 +91,17 @@ MUTATIONS = [
      "no interpolation inside the angle interval"),
     ("walk.c", "psr = stc > 0.0 ? pth / stc / (2.0 * M_PI) : 0.0;", "psr = pth / (2.0 * M_PI);", PAPER,
      "camera density per radian, not per unit cosine"),
+    # image comparison (Sec. 3.1.4, Tables 3-4)
+    ("metrics.py", "return (a - mn) / (mx - mn)", "return (a - mn) / mx", METRICS, "min-max normalisation"),
+    ("metrics.py", "return float(np.sqrt(np.mean((a - b) ** 2)))", "return float(np.mean(np.abs(a - b)))", METRICS,
+     "mean absolute instead of root-mean-square error"),
+    ("metrics.py", "return float(np.sum(da * db) / np.sqrt(saa * sbb))", "return float(np.sum(da * db) / (saa * sbb))",
+     METRICS, "correlation not normalised"),
+    ("metrics.py", "dx = ix + 0.5 - nx / 2.0", "dx = ix - nx / 2.0", METRICS, "ring centre off by half a pixel"),
+    ("metrics.py", "rho_max = np.sqrt((nx / 2.0) ** 2 + (nz / 2.0) ** 2)", "rho_max = max(nx, nz) / 2.0", METRICS,
+     "ring range"),
+    ("metrics.py", "return np.where(ang < 30.0, 0,", "return np.where(ang < 60.0, 0,", METRICS, "forward zone limit"),
+    ("metrics.py", "/ max(int(ok.sum()), 1))", "/ n_r)", METRICS, "share counts rings without pixels"),
     # the adjoint (gradients of Eq. 15-16)
     ("adjoint.c", "S += 1.0 / mu_ext - s;", "S += 1.0 / mu_ext + s;", ADJ, "sign of the flight score"),
     ("adjoint.c", "pg[0] += A * (R.S[j] + jj * (1.0 / c->mu_s - 1.0 / mu_ext) - R.l[j]);",
