@@ -62,11 +62,12 @@ def test_single_scatter_gradient_closed_form(oracle_mod, table, mu_a):
     assert res["value"] == pytest.approx(float(np.sum(adj * w["image"])), rel=1e-12)
 
 
-def test_replay_matches_walk_functional(oracle_mod, table):
+@pytest.mark.parametrize("beam_radius", [0.0, 1.25])
+def test_replay_matches_walk_functional(oracle_mod, table, beam_radius):
     rng = np.random.default_rng(9)
     adj = rng.uniform(0, 1, (64, 64))
     kw = dict(mu_s=5 / LX - 0.01, mu_a=0.01, table=table, n_photons=20_000, nx=64, nz=64, seed=4,
-              rr_threshold=0.05)
+              rr_threshold=0.05, beam_radius=beam_radius)
     res = oracle_mod.adjoint(adj, 64, **kw)
     w = oracle_mod.walk(**kw)
     assert res["value"] == pytest.approx(float(np.sum(adj * w["image"])), rel=1e-12)

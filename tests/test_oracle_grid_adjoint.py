@@ -22,15 +22,16 @@ def _hg_sr(g, mu):
     return (1 - g * g) / (4 * math.pi * (1 + g * g - 2 * g * mu) ** 1.5)
 
 
-@pytest.mark.parametrize("absorb,mu_a0", [(False, 0.0), (True, 0.0), (True, 0.004)])
-def test_scaling_identity_against_homogeneous_adjoint(oracle_mod, absorb, mu_a0):
+@pytest.mark.parametrize("absorb,mu_a0,beam", [(False, 0.0, 0.0), (True, 0.0, 0.0), (True, 0.004, 0.0),
+                                               (True, 0.004, 2.0)])
+def test_scaling_identity_against_homogeneous_adjoint(oracle_mod, absorb, mu_a0, beam):
     k_ext = 2e-5
     k_sca = 0.85 * k_ext if absorb else k_ext
     rho = 3.0 / LX / k_ext
     dens = np.full((8, 8, 16), rho)
     n, nx, nz = 4000, 16, 16
     adj = np.random.default_rng(2).uniform(0, 1, (nz, nx))
-    common = dict(phase="hg", hg_g=0.8, n_photons=n, nx=nx, nz=nz, seed=5, rr_threshold=1e-2)
+    common = dict(phase="hg", hg_g=0.8, n_photons=n, nx=nx, nz=nz, seed=5, rr_threshold=1e-2, beam_radius=beam)
     g = oracle_mod.grid_adjoint(adj, mu_s=0.0, mu_a=mu_a0,
                                 grid=dict(density=dens, k_ext=k_ext, k_sca=k_sca, block=(4, 2, 2)), **common)
     mu_s, mu_ap = k_sca * rho, (k_ext - k_sca) * rho
@@ -88,12 +89,13 @@ def test_single_scatter_gradient_closed_form(oracle_mod):
     assert np.sum(z ** 2) < z.size + 6 * math.sqrt(2 * z.size)
 
 
-def test_value_is_the_walk_functional(oracle_mod):
+@pytest.mark.parametrize("beam_radius", [0.0, 2.0])
+def test_value_is_the_walk_functional(oracle_mod, beam_radius):
     rng = np.random.default_rng(9)
     dens = 1500.0 * np.exp(0.5 * rng.standard_normal((8, 8, 16)))
     adj = rng.uniform(0, 1, (16, 16))
     kw = dict(phase="hg", hg_g=0.7, mu_s=0.0, mu_a=0.001, n_photons=3000, nx=16, nz=16, seed=4,
-              grid=dict(density=dens, k_ext=5e-5, k_sca=4e-5, block=(4, 2, 2)))
+              beam_radius=beam_radius, grid=dict(density=dens, k_ext=5e-5, k_sca=4e-5, block=(4, 2, 2)))
     r = oracle_mod.grid_adjoint(adj, **kw)
     w = oracle_mod.walk(**kw)
     assert r["value"] == pytest.approx(float(np.sum(adj * w["image"])), rel=1e-12)

@@ -50,6 +50,11 @@ MUTATIONS = [
      TABLE, "bin density"),
     ("table.c", "double target = Z * ((double)i / n_bins);", "double target = Z * ((double)(i - 1) / n_bins);",
      TABLE, "inversion levels shifted by one"),
+    ("table.c", "F[j] += (w[i] / wsum) * G[j] / Z;", "F[j] += (w[i] / wsum) * G[j];", GRID,
+     "mixture of unnormalised components"),
+    ("table.c", "cdf[i + 1] = cdf[i] + 0.5 * h * (F[i] + F[i + 1]);", "cdf[i + 1] = cdf[i] + h * F[i];", PAPER,
+     "paper CDF by rectangles"),
+    ("table.c", "F[i] *= 0.5 * sin(i * h);", "F[i] *= 0.5;", PAPER, "paper CDF without sin(theta)"),
     # Philox4x32-10 and the uniforms
     ("philox.c", "k1 += 0xBB67AE85u;", "k1 += 0xBB67AE84u;", PHILOX, "Weyl constant"),
     ("philox.c", "uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;", "uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k1;",
@@ -78,6 +83,8 @@ MUTATIONS = [
      "table sample without interpolation"),
     ("walk.c", "nbin = table_bin(c->icdf, c->n_bins, muc);", "nbin = table_bin(c->icdf, c->n_bins, -muc);", WALK,
      "camera cosine sign"),
+    ("walk.c", "double rho = c->beam_radius * sqrt(oracle_uniform(o[0]));",
+     "double rho = c->beam_radius * oracle_uniform(o[0]);", WALK, "beam entry radius not uniform over the disc"),
     # delta tracking (heterogeneous media)
     ("walk.c", "const double s = tau / mb;", "const double s = tau * mb;", GRID, "tentative flight length"),
     ("walk.c", "tau -= mb * t;", "tau -= t;", GRID, "optical depth spent in a cell"),
@@ -103,6 +110,10 @@ MUTATIONS = [
     ("metrics.py", "return np.where(ang < 30.0, 0,", "return np.where(ang < 60.0, 0,", METRICS, "forward zone limit"),
     ("metrics.py", "/ max(int(ok.sum()), 1))", "/ n_r)", METRICS, "share counts rings without pixels"),
     # the adjoint (gradients of Eq. 15-16)
+    ("adjoint.c", "double t = fabs(mu - (-1.0 + k * h)) / h;", "double t = fabs(mu - (-1.0 + k * h)) / (2.0 * h);",
+     ADJ, "hat twice as wide"),
+    ("adjoint.c", "s += pdf * hat_integral(n_w, k, a, b);", "s += hat_integral(n_w, k, a, b);", ADJ,
+     "hat integrals without the phase density"),
     ("adjoint.c", "S += 1.0 / mu_ext - s;", "S += 1.0 / mu_ext + s;", ADJ, "sign of the flight score"),
     ("adjoint.c", "pg[0] += A * (R.S[j] + jj * (1.0 / c->mu_s - 1.0 / mu_ext) - R.l[j]);",
      "pg[0] += A * (R.S[j] + jj * (1.0 / c->mu_s - 1.0 / mu_ext));", ADJ, "transport term dropped"),
@@ -112,6 +123,8 @@ MUTATIONS = [
      "double t = oracle_hat(J->n_w, q, R.muc[j]) - J->z[q];", ADJ, "normalisation counted once"),
     ("adjoint.c", "for (int i = 0; i < j; ++i)\n                    t +=", "for (int i = 1; i < j; ++i)\n                    t +=",
      ADJ, "range of the sampled-angle sum"),
+    ("adjoint.c", "r[1] = rho * cos(psi);", "r[1] = -rho * cos(psi);", ADJ, "replayed beam entry point"),
+    ("adjoint.c", "r0[1] = rho * cos(psi);", "r0[1] = 0.0;", GADJ, "first flight starts on the axis"),
     ("adjoint.c", "grad[vi] += B * c->k_ext / mu;", "grad[vi] += B / mu;", GADJ, "collision point term"),
     ("adjoint.c", "grad[vi] -= A[i] * c->k_ext * (top - ri[1]);", "grad[vi] -= A[i] * c->k_ext * (top + ri[1]);",
      GADJ, "camera column inside the collision voxel"),

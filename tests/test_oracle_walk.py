@@ -147,6 +147,25 @@ def test_roulette_is_unbiased(oracle_mod):
         assert abs(m1 - m0) < 4 * math.hypot(s0, s1), (k, m0, m1)
 
 
+def test_finite_beam_enters_uniformly_over_its_disc(oracle_mod):
+    """The top-hat beam: entry points uniform over the disc of radius R at
+    x = 0. The first collision keeps the entry point's y and z (the photon
+    flies along +x), so rho^2 / R^2 must be uniform on [0, 1) and the polar
+    angle uniform on [0, 2 pi)."""
+    R, n = 1.25, 40_000
+    r = oracle_mod.walk(mu_s=0.5, phase="hg", hg_g=0.3, beam_radius=R, lx=1e9, n_photons=n, nx=4, nz=4,
+                        n_trace=n, n_trace_events=1, max_events=1)
+    assert np.all(r["trace"][:, 0, 0] == 0)           # every first event is a collision
+    y, z = r["trace"][:, 0, 2], r["trace"][:, 0, 3]
+    u = (y * y + z * z) / (R * R)
+    assert u.max() < 1.0
+    for q in (0.1, 0.25, 0.5, 0.75, 0.9):             # the uniform CDF of rho^2 / R^2
+        assert abs(np.mean(u < q) - q) < 5 * math.sqrt(q * (1 - q) / n), q
+    ang = np.mod(np.arctan2(z, y), 2 * math.pi) / (2 * math.pi)
+    for q in (0.25, 0.5, 0.75):
+        assert abs(np.mean(ang < q) - q) < 5 * math.sqrt(q * (1 - q) / n), q
+
+
 def test_mean_free_path(oracle_mod):
     mu_ext, n = 0.25, 4000
     big = 1e9
