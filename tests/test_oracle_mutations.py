@@ -85,6 +85,9 @@ MUTATIONS = [
      "camera cosine sign"),
     ("walk.c", "double rho = c->beam_radius * sqrt(oracle_uniform(o[0]));",
      "double rho = c->beam_radius * oracle_uniform(o[0]);", WALK, "beam entry radius not uniform over the disc"),
+    ("walk.c", "double fr = rho / c->r_max * c->n_radial;", "double fr = rho * rho / c->r_max * c->n_radial;",
+     WALK, "radial bin of rho squared"),
+    ("walk.c", "rbin = (int)floor(fr);", "rbin = (int)ceil(fr);", WALK, "radial bin rounded up"),
     # delta tracking (heterogeneous media)
     ("walk.c", "const double s = tau / mb;", "const double s = tau * mb;", GRID, "tentative flight length"),
     ("walk.c", "tau -= mb * t;", "tau -= t;", GRID, "optical depth spent in a cell"),

@@ -166,6 +166,26 @@ def test_finite_beam_enters_uniformly_over_its_disc(oracle_mod):
         assert abs(np.mean(ang < q) - q) < 5 * math.sqrt(q * (1 - q) / n), q
 
 
+@pytest.mark.parametrize("r_max", [2.0, 1.0])
+def test_far_face_radial_profile_of_a_transparent_medium(oracle_mod, r_max):
+    """Without scattering every photon crosses to the far face at its entry
+    point, so the radial profile is the beam disc's share per ring: ring b
+    of n_r on [0, r_max) holds ((b+1)^2 - b^2) (r_max/R)^2 / n_r^2 of the
+    photons, the last ring also everything beyond r_max; the profile sums to
+    the far-face total exactly."""
+    R, n, nr = 2.0, 4_000_000, 16
+    r = oracle_mod.walk(mu_s=1e-12, phase="hg", hg_g=0.0, beam_radius=R, r_max=r_max, n_radial=nr, n_photons=n,
+                        nx=4, nz=4)
+    far = r["totals"][1]
+    assert r["radial"].sum() == far and far >= n - 2
+    b = np.arange(nr)
+    p = ((b + 1) ** 2 - b ** 2) / nr ** 2 * (r_max / R) ** 2
+    p[-1] += 1 - (r_max / R) ** 2
+    z = (r["radial"] - far * p) / np.sqrt(far * p * (1 - p))
+    assert np.max(np.abs(z)) < 5
+    assert np.sum(z ** 2) < nr + 6 * math.sqrt(2 * nr)
+
+
 def test_mean_free_path(oracle_mod):
     mu_ext, n = 0.25, 4000
     big = 1e9
