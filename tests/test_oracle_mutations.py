@@ -88,7 +88,11 @@ MUTATIONS = [
     ("walk.c", "double fr = rho / c->r_max * c->n_radial;", "double fr = rho * rho / c->r_max * c->n_radial;",
      WALK, "radial bin of rho squared"),
     ("walk.c", "rbin = (int)floor(fr);", "rbin = (int)ceil(fr);", WALK, "radial bin rounded up"),
+    ("walk.c", "rec->nee = nee;", "rec->nee = w * psr;", WALK, "traced camera term without its transmittance"),
+    ("walk.c", "rec->pix = pix;", "rec->pix = ix;", WALK, "traced pixel without its row"),
     # delta tracking (heterogeneous media)
+    ("walk.c", "if (mu > *q)\n                        *q = mu;", "if (mu < *q)\n                        *q = mu;", GRID,
+     "majorant from the thinnest voxel"),
     ("walk.c", "const double s = tau / mb;", "const double s = tau * mb;", GRID, "tentative flight length"),
     ("walk.c", "tau -= mb * t;", "tau -= t;", GRID, "optical depth spent in a cell"),
     ("walk.c", "for (int j = iy + 1; j < c->gy; ++j)\n        od +=", "for (int j = iy; j < c->gy; ++j)\n        od +=",
