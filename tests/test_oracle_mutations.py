@@ -71,6 +71,11 @@ MUTATIONS = [
     ("walk.c", "psr = pdf / (2.0 * M_PI);", "psr = pdf / (4.0 * M_PI);", WALK, "table density per steradian"),
     ("walk.c", "return (1.0 - g * g) / (4.0 * M_PI * t * sqrt(t));", "return (1.0 - g * g) / (4.0 * M_PI * t);",
      WALK, "H-G density (Eq. 11)"),
+    ("walk.c", "double q = (1.0 - g * g) / (1.0 - g + 2.0 * g * xi);", "double q = (1.0 - g * g) / (1.0 + g + 2.0 * g * xi);",
+     WALK, "H-G inverse distribution (Eq. 11)"),
+    ("walk.c", "int lo = 0, hi = n; /* icdf", "int lo = 0, hi = n - 1; /* icdf", WALK,
+     "camera density never from the last table bin"),
+    ("walk.c", "double fx = r[0] / c->lx * c->nx;", "double fx = r[0] / c->lz * c->nx;", WALK, "image column scale"),
     ("walk.c", "double fz = (r[2] - lo[2]) / c->lz * c->nz;", "double fz = (r[2] + lo[2]) / c->lz * c->nz;", WALK,
      "image row sign"),
     ("walk.c", "double phi = 2.0 * M_PI * u2;", "double phi = M_PI * u2;", WALK, "azimuth on [0, pi)"),

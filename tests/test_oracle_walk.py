@@ -219,16 +219,19 @@ def test_camera_estimate_matches_analog_count(oracle_mod, mu_a):
 
 def _trace_case(oracle_mod, phase, table):
     n, ev = 300, 32
-    kw = dict(table=table) if phase == "mie" else dict(phase="hg", hg_g=0.8667)
+    kw = dict(table=table) if phase in ("mie", "coarse") else dict(phase="hg", hg_g=0.8667)
     mu_s, mu_a = 10 / LX, 0.02
     r = oracle_mod.walk(mu_s=mu_s, mu_a=mu_a, n_photons=n, nx=64, nz=64, n_trace=n,
                         n_trace_events=ev, seed=7, rr_threshold=1e-3, **kw)
     return r, mu_s, mu_a, n, ev
 
 
-@pytest.mark.parametrize("phase", ["mie", "hg"])
+@pytest.mark.parametrize("phase", ["mie", "hg", "coarse"])
 def test_trace_invariants(oracle_mod, mie_table, phase):
-    r, mu_s, mu_a, n, ev = _trace_case(oracle_mod, phase, mie_table)
+    # "coarse": a 16-bin table of the isotropic function, so that every bin,
+    # the first and the last included, holds many camera directions
+    table = oracle_mod.phase_table(oracle_mod.PHASE_HG, hg_g=0.0, n_bins=16) if phase == "coarse" else mie_table
+    r, mu_s, mu_a, n, ev = _trace_case(oracle_mod, phase, table)
     mu_ext = mu_s + mu_a
     tr = r["trace"]
     ctr = np.zeros((n * ev, 4), dtype=np.uint32)
@@ -261,7 +264,7 @@ def test_trace_invariants(oracle_mod, mie_table, phase):
                     psr = _hg_sr(0.8667, d[1])
                 else:
                     j = int(rec[10])
-                    t = mie_table
+                    t = table
                     assert t["icdf"][j] <= d[1] <= t["icdf"][j + 1]
                     psr = t["pdf"][j] / (2 * math.pi)
                 want = w_after * psr * math.exp(-mu_ext * (LY / 2 - rp[1]))
@@ -274,7 +277,8 @@ def test_trace_invariants(oracle_mod, mie_table, phase):
                     if phase == "hg":
                         mu = _hg_inv(0.8667, u[p, e, 1])
                     else:
-                        mu = np.interp(u[p, e, 1] * 4096, np.arange(4097), mie_table["icdf"])
+                        nb = len(table["icdf"]) - 1
+                        mu = np.interp(u[p, e, 1] * nb, np.arange(nb + 1), table["icdf"])
                     assert float(np.dot(dp, d)) == pytest.approx(mu, abs=1e-12)
                     if w_after < 1e-3:
                         assert rec[7] == pytest.approx(w_after / 0.1, rel=1e-12)
