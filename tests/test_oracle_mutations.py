@@ -102,6 +102,8 @@ MUTATIONS = [
     ("walk.c", "tau -= mb * t;", "tau -= t;", GRID, "optical depth spent in a cell"),
     ("walk.c", "for (int j = iy + 1; j < c->gy; ++j)\n        od +=", "for (int j = iy; j < c->gy; ++j)\n        od +=",
      GRID, "camera column counts its own voxel twice"),
+    ("walk.c", "const double top = (iy == c->gy - 1) ? hi[1] : lo[1] + (iy + 1) * vy;",
+     "const double top = (iy == c->gy - 1) ? hi[1] : lo[1] + iy * vy;", GRID, "top of the collision voxel"),
     ("walk.c", "const double acc = mu_here / mubar;", "const double acc = 0.5 * (1.0 + mu_here / mubar);", GRID,
      "acceptance probability"),
     ("walk.c", "u3 = u3 / acc;  /* uniform", "u3 = u3;  /* uniform", GRID, "roulette number not rescaled"),
@@ -137,6 +139,11 @@ MUTATIONS = [
      ADJ, "range of the sampled-angle sum"),
     ("adjoint.c", "r[1] = rho * cos(psi);", "r[1] = -rho * cos(psi);", ADJ, "replayed beam entry point"),
     ("adjoint.c", "r0[1] = rho * cos(psi);", "r0[1] = 0.0;", GADJ, "first flight starts on the axis"),
+    ("adjoint.c", "m[i] = a[i] + 0.5 * (t0 + t1) * d[i];", "m[i] = a[i] + t0 * d[i];", GADJ,
+     "flight piece given to the voxel at its start"),
+    ("adjoint.c", "coef * (t1 - t0) * len;", "coef * (t1 - t0);", GADJ, "flight pieces without their length"),
+    ("adjoint.c", "for (int j = v[1] + 1; j < c->gy; ++j)", "for (int j = v[1]; j < c->gy; ++j)", GADJ,
+     "camera column counts the collision voxel twice"),
     ("adjoint.c", "grad[vi] += B * c->k_ext / mu;", "grad[vi] += B / mu;", GADJ, "collision point term"),
     ("adjoint.c", "grad[vi] -= A[i] * c->k_ext * (top - ri[1]);", "grad[vi] -= A[i] * c->k_ext * (top + ri[1]);",
      GADJ, "camera column inside the collision voxel"),
