@@ -214,7 +214,21 @@ typedef struct {
 /* Scratch bytes mc_run / mc_trace need for this camera. */
 size_t mc_workspace_bytes(const mc_camera *camera);
 
-/* Run the photon walk on the GPU. Asynchronous on `stream`. */
+/* Run the photon walk on the GPU (Sec. 3.1.3): every photon of the range
+ * enters at x = 0 (on the axis, or uniformly over the beam disc), then
+ * repeats free flight (Eq. 15), escape at the first wall crossed, implicit
+ * capture (Eq. 16), the side camera's next-event estimate, a scattering
+ * angle from the medium's phase function, the rotation and the weight
+ * threshold (roulette with run->rr_survival, or the paper's plain cut with
+ * 0). Tallies go to *tallies in fixed point: the image [nz][nx], the radial
+ * profile of far-face exits, the MC_TOT_* totals. run->accumulate = 0 zeroes
+ * them first (on the stream), 1 adds to them. The error word is only OR-ed.
+ * Returns at once: MC_ERR_ARG (invalid argument, or an image tile that
+ * image_mode 1 cannot hold in shared memory), MC_ERR_NOMEM (workspace too
+ * small) or MC_ERR_CUDA (a launch failed) before anything runs on the
+ * device, MC_OK when queued. Device-side problems appear in the error word
+ * (mc_check). Asynchronous on `stream`; the buffers must stay valid until
+ * the stream reaches this work. */
 mc_status mc_run(const mc_medium *medium, const mc_geometry *geom,
                  const mc_camera *camera, const mc_run_params *run,
                  const mc_tallies *tallies, void *stream);
