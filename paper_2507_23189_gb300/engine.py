@@ -26,14 +26,13 @@ def _stream_handle(stream):
     return C.c_void_p(s.cuda_stream)
 
 
-def _fresh_error(error, stream, accumulate):
-    """A run that starts its tallies afresh starts its error word afresh, on
-    the launch stream; an accumulating run keeps the flags of the tallies it
-    adds to."""
-    if not accumulate:
-        torch = _torch()
-        with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream(error.device)):
-            error.zero_()
+def _clear_error(error, stream):
+    """The error word holds the flags raised since the previous check: a
+    check reads it once the stream has finished and then clears it on that
+    stream, so the runs themselves add no device work for it."""
+    torch = _torch()
+    with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream(error.device)):
+        error.zero_()
 
 
 # --------------------------------------------------------------------- table
@@ -294,13 +293,12 @@ class Engine:
 
     def run(self, medium, n_photons, seed=1, stream=None, **kw):
         """Queue photons on the stream (asynchronous). Without accumulate=True
-        the tallies and the error word start afresh; check() reports the
-        flags of everything run into the tallies since."""
+        the tallies start afresh; check() reports the device flags raised
+        since the previous check."""
         rp = run_params(n_photons, seed, **kw)
         self.image_frac_bits = rp.image_frac_bits
         m, keep = medium.as_c(self.device)
         g, c, t = self.geometry.as_c(), self.camera.as_c(), self._tallies()
-        _fresh_error(self.error, stream, rp.accumulate)
         N.check("mc_run", N.lib().mc_run(C.byref(m), C.byref(g), C.byref(c), C.byref(rp), C.byref(t),
                                          _stream_handle(stream)))
         self._keep = keep
@@ -315,7 +313,6 @@ class Engine:
         m, keep = medium.as_c(self.device)
         buf = torch.empty((n_trace, n_events, N.TRACE_WORDS), dtype=torch.int32, device=self.device)
         g, c, t = self.geometry.as_c(), self.camera.as_c(), self._tallies()
-        _fresh_error(self.error, stream, rp.accumulate)
         N.check("mc_trace", N.lib().mc_trace(C.byref(m), C.byref(g), C.byref(c), C.byref(rp),
                                              C.byref(t), C.c_void_p(buf.data_ptr()), n_trace, n_events,
                                              _stream_handle(stream)))
@@ -360,7 +357,6 @@ class Engine:
         tr = None
         if n_trace:
             tr = torch.empty(n_trace * n_events * N.TRACE_WORDS, dtype=torch.int32, device=self.device)
-        _fresh_error(self.error, stream, rp.accumulate)
         N.check("mc_run_grid", N.lib().mc_run_grid(
             C.byref(g), C.c_void_p(grid.work.data_ptr()), C.byref(m), C.byref(geo), C.byref(c), C.byref(rp),
             C.byref(t), C.c_void_p(tr.data_ptr()) if tr is not None else None, n_trace, n_events,
@@ -389,7 +385,6 @@ class Engine:
         work = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         grad = torch.empty(tuple(grid.density.shape), dtype=torch.float32, device=self.device)
         value = torch.empty(1, dtype=torch.float64, device=self.device)
-        _fresh_error(self.error, stream, False)
         vp = C.c_void_p
         N.check("mc_grid_adjoint", N.lib().mc_grid_adjoint(
             C.byref(g), vp(grid.work.data_ptr()), C.byref(m), C.byref(geo), C.byref(c), C.byref(rp),
@@ -399,8 +394,11 @@ class Engine:
         return value, grad
 
     def check(self, stream=None):
-        """Wait for the stream and raise if a kernel flagged an error."""
-        N.check("mc_check", N.lib().mc_check(C.c_void_p(self.error.data_ptr()), _stream_handle(stream)))
+        """Wait for the stream and raise if a kernel flagged an error since
+        the previous check; the flags are cleared either way."""
+        st = N.lib().mc_check(C.c_void_p(self.error.data_ptr()), _stream_handle(stream))
+        _clear_error(self.error, stream)
+        N.check("mc_check", st)
 
     def check_within(self, timeout_ms, stream=None):
         """check() with a host-side watchdog: True when the stream finished
@@ -410,6 +408,7 @@ class Engine:
                                      float(timeout_ms))
         if st == N.MC_NOT_READY:
             return False
+        _clear_error(self.error, stream)
         N.check("mc_check_within", st)
         return True
 
@@ -465,7 +464,6 @@ class Batch:
             arr[i].d_radial = self.radial[i].data_ptr()
             arr[i].d_totals = self.totals[i].data_ptr()
         g, c = self.geometry.as_c(), self.camera.as_c()
-        _fresh_error(self.error, stream, rp.accumulate)
         N.check("mc_run_batch", N.lib().mc_run_batch(
             n, arr, C.byref(g), C.byref(c), C.byref(rp), int(item_photons),
             C.c_void_p(self.error.data_ptr()), C.c_void_p(self.work.data_ptr()), self.work.numel(),
@@ -474,7 +472,10 @@ class Batch:
         return self
 
     def check(self, stream=None):
-        N.check("mc_check", N.lib().mc_check(C.c_void_p(self.error.data_ptr()), _stream_handle(stream)))
+        """As Engine.check, for the batch's error word."""
+        st = N.lib().mc_check(C.c_void_p(self.error.data_ptr()), _stream_handle(stream))
+        _clear_error(self.error, stream)
+        N.check("mc_check", st)
 
 
 def camera_image(engine, table, mu_s, mu_a, phase_w=None, n_photons=10**6, seed=1, grad_seed=None, **kw):

@@ -28,10 +28,11 @@ def main(out):
     for name, med, geo, cam, kw in cases:
         e = E.Engine(cam, geo)
         e.run(med, 2_000_000, seed=3, **kw)
+        err = int(e.error.cpu().numpy()[0])     # read before check(), which clears it
         e.check()
         r = e.result()
         res[name + "_img"], res[name + "_tot"] = r["raw_image"], r["raw_totals"]
-        res[name + "_rad"], res[name + "_err"] = e.radial.cpu().numpy(), np.array(r["error"])
+        res[name + "_rad"], res[name + "_err"] = e.radial.cpu().numpy(), np.array(err)
     # heterogeneous medium: walk and density gradient
     dens = torch.from_numpy(np.ascontiguousarray(W.rough_grid((16, 16, 64), 4, mean=2000.0),
                                                  dtype=np.float32)).cuda()
@@ -40,19 +41,21 @@ def main(out):
     e = E.Engine(E.Camera(64, 64), geo)
     med = E.Medium(1.0, 0.0, "table", 0.0, tab)
     e.run_grid(g, med, 1_000_000, seed=2)
+    err = int(e.error.cpu().numpy()[0])
     e.check()
     r = e.result()
-    res["grid_img"], res["grid_tot"], res["grid_err"] = r["raw_image"], r["raw_totals"], np.array(r["error"])
+    res["grid_img"], res["grid_tot"], res["grid_err"] = r["raw_image"], r["raw_totals"], np.array(err)
     adj = torch.from_numpy(np.random.default_rng(1).uniform(0, 1, (64, 64)).astype(np.float32))
     val, grad = e.grid_adjoint(g, med, adj, 300_000, seed=4)
+    err = int(e.error.cpu().numpy()[0])
     e.check()
-    res["gadj_val"], res["gadj_grad"], res["gadj_err"] = val.cpu().numpy(), grad.cpu().numpy(), \
-        np.array(int(e.error.cpu().numpy()[0]))
+    res["gadj_val"], res["gadj_grad"], res["gadj_err"] = val.cpu().numpy(), grad.cpu().numpy(), np.array(err)
     # homogeneous adjoint with phase weights
     e = E.Engine(E.Camera(128, 128), E.Geometry())
     gvec = e.adjoint(E.Medium(5 / 45.0, 0.01, "table", 0.0, tab), adj.repeat(2, 2), 1_000_000, n_w=64, seed=5)
+    err = int(e.error.cpu().numpy()[0])
     e.check()
-    res["adj"], res["adj_err"] = gvec.cpu().numpy(), np.array(int(e.error.cpu().numpy()[0]))
+    res["adj"], res["adj_err"] = gvec.cpu().numpy(), np.array(err)
     np.savez(out, **res)
 
 

@@ -49,12 +49,17 @@ def test_run_params_carry_every_field():
     assert (rp.rr_threshold, rp.rr_survival) == (1e-3, 0.0)
 
 
-def test_fresh_error_resets_on_the_launch_stream_only_for_fresh_tallies(monkeypatch):
+def test_check_reports_then_clears_the_flags_on_the_checked_stream(monkeypatch):
+    """Engine.check: mc_check's status is raised as McError, and the error
+    word is cleared afterwards on the stream that was checked (also when it
+    raises), so the next check reports only new flags and no run pays a
+    device operation for it. check_within clears only once the work is done."""
     import contextlib
     import types
 
     import torch
 
+    from paper_2507_23189_gb300 import _native as N
     from paper_2507_23189_gb300 import engine as eng_mod
     log = []
 
@@ -64,25 +69,47 @@ def test_fresh_error_resets_on_the_launch_stream_only_for_fresh_tallies(monkeypa
         yield
         log.append(("exit", s))
 
-    fake = types.SimpleNamespace(cuda=types.SimpleNamespace(
+    fake_torch = types.SimpleNamespace(cuda=types.SimpleNamespace(
         stream=stream_ctx, current_stream=lambda dev=None: ("current", str(dev))))
-    monkeypatch.setattr(eng_mod, "_torch", lambda: fake)
+    monkeypatch.setattr(eng_mod, "_torch", lambda: fake_torch)
+    monkeypatch.setattr(eng_mod, "_stream_handle", lambda s: s)
 
     class Word:
         device = torch.device("cpu")
 
-        def __init__(self):
-            self.v = 0x7
+        def __init__(self, v):
+            self.v = v
+
+        def data_ptr(self):
+            return 1234
 
         def zero_(self):
             log.append(("zero",))
             self.v = 0
 
-    w = Word()
-    eng_mod._fresh_error(w, "s1", True)                # accumulating: flags stay
-    assert w.v == 0x7 and log == []
-    eng_mod._fresh_error(w, "s1", False)               # fresh tallies: zeroed inside the launch stream
-    assert w.v == 0 and log == [("enter", "s1"), ("zero",), ("exit", "s1")]
+    status = {"check": 0, "within": 0}
+    fake_lib = types.SimpleNamespace(
+        mc_check=lambda ptr, st: (log.append(("mc_check", st)), status["check"])[1],
+        mc_check_within=lambda ptr, st, ms: (log.append(("mc_check_within", st)), status["within"])[1])
+    monkeypatch.setattr(N, "lib", lambda: fake_lib)
+
+    e = object.__new__(gpu.Engine)
+    e.error = Word(0)
+    e.check("s1")
+    assert log == [("mc_check", "s1"), ("enter", "s1"), ("zero",), ("exit", "s1")]
+
     log.clear()
-    eng_mod._fresh_error(w, None, 0)                   # no stream given: the device's current stream
-    assert log[0] == ("enter", ("current", "cpu")) and log[1] == ("zero",)
+    e.error = Word(N.EFLAG_EVENTS)
+    status["check"] = -7
+    with pytest.raises(N.McError) as err:
+        e.check(None)
+    assert err.value.status == -7 and e.error.v == 0
+    assert log[1] == ("enter", ("current", "cpu")) and ("zero",) in log
+
+    log.clear()
+    e.error = Word(N.EFLAG_TIMEOUT)
+    status["within"] = N.MC_NOT_READY
+    assert e.check_within(5.0, "s2") is False
+    assert e.error.v == N.EFLAG_TIMEOUT and ("zero",) not in log     # still running: nothing cleared
+    status["within"] = 0
+    assert e.check_within(5.0, "s2") is True and e.error.v == 0
