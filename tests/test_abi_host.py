@@ -92,6 +92,26 @@ def test_table_builder_matches_oracle(eng, oracle_mod, d_um, m):
     assert info["g_table"] == pytest.approx(ot["mean"], abs=1e-12)
 
 
+@pytest.mark.parametrize("d_um,m,n_med,lam,n_bins", [(0.05, complex(1.59, 0.0), 1.33, 532.0, 4096),
+                                                     (3.0, complex(1.5, 0.5), 1.33, 532.0, 1024),
+                                                     (5.0, complex(1.59, 0.0), 1.0, 633.0, 64),
+                                                     (5.0, complex(1.59, 0.0), 1.33, 532.0, 16384)])
+def test_table_builder_matches_oracle_across_sizes_media_and_bins(eng, oracle_mod, d_um, m, n_med, lam, n_bins):
+    """The same two routes for a Rayleigh-sized sphere, a strongly absorbing
+    one, a sphere in air at 633 nm and the smallest and largest tables."""
+    t = eng.PhaseTable(diameter_um=d_um, n_particle=m, n_medium=n_med, wavelength_nm=lam, n_bins=n_bins)
+    x = oracle_mod.size_parameter(d_um, n_med, lam)
+    mr = m / n_med
+    qe, qs, g = oracle_mod.mie_efficiencies(mr, x)
+    assert t.info["x"] == pytest.approx(x, rel=1e-14)
+    assert t.info["qext"] == pytest.approx(qe, rel=1e-10)
+    assert t.info["qsca"] == pytest.approx(qs, rel=1e-10)
+    assert t.info["g"] == pytest.approx(g, abs=1e-10)
+    ot = oracle_mod.phase_table(oracle_mod.PHASE_MIE, mr, x, n_bins=n_bins)
+    np.testing.assert_allclose(t.omu64, ot["omu"], rtol=1e-9, atol=1e-15)
+    np.testing.assert_allclose(t.pdf64, ot["pdf"], rtol=1e-8)
+
+
 def test_packed_table_layout(eng):
     t = eng.PhaseTable()
     b = t.blob
