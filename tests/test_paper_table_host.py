@@ -58,3 +58,14 @@ def test_bad_sizes_rejected(eng_paper):
     for n in (0, 15, 16385):
         with pytest.raises(Exception):
             g.PaperTable(n_theta=n)
+
+
+@pytest.mark.parametrize("n_theta,d_um,m", [(181, 5.0, complex(1.59, 0.0)), (3000, 1.0, complex(1.59, 0.0)),
+                                            (1001, 2.0, complex(1.5, 0.05)), (8000, 10.0, complex(1.59, 0.0))])
+def test_cdf_matches_oracle_across_grids_and_particles(eng_paper, oracle_mod, n_theta, d_um, m):
+    import paper_2507_23189_gb300 as g
+    t = g.PaperTable(diameter_um=d_um, n_particle=m, n_theta=n_theta)
+    x = oracle_mod.size_parameter(d_um, 1.33, 532.0)
+    o = oracle_mod.paper_cdf(oracle_mod.PHASE_MIE, m / 1.33, x, n_theta=n_theta)
+    np.testing.assert_allclose(t.cdf64, o["cdf"], rtol=0, atol=1e-12)
+    assert t.cdf64[0] == 0.0 and t.cdf64[-1] == 1.0 and np.all(np.diff(t.cdf64) >= 0)
