@@ -31,21 +31,49 @@ def test_cdf_matches_oracle(eng_paper, oracle_mod):
 
 
 def test_integer_thresholds_reproduce_the_double_search(eng_paper):
-    b = eng_paper.blob
+    h = _header(eng_paper.blob)
+    assert h["n_theta"] == 3000 and h["top"] == 2048
+    _check_thresholds(eng_paper)
+
+
+@pytest.mark.parametrize("n_theta", [16, 181, 2049, 8000, 16384])
+def test_integer_thresholds_for_other_grids(eng_paper, n_theta):
+    import paper_2507_23189_gb300 as g
+    t = g.PaperTable(n_theta=n_theta)
+    h = _header(t.blob)
+    assert h["n_theta"] == n_theta and h["n_int"] == n_theta - 1
+    # binary lifting over intervals 0 .. n_int - 1 starts at the largest power
+    # of two below n_int, whose steps reach index 2 top - 1 >= n_int - 1
+    top = h["top"]
+    assert top & (top - 1) == 0 and top < h["n_int"] <= 2 * top
+    _check_thresholds(t)
+
+
+def _check_thresholds(table):
+    b = table.blob
     h = _header(b)
     n = h["n_int"]
-    assert h["magic"] == 0x504D434D and h["n_theta"] == 3000 and h["total"] == b.size
-    assert h["top"] == 2048
+    assert h["magic"] == 0x504D434D and h["total"] == b.size
     K = np.frombuffer(b[h["off_k"]:h["off_k"] + 4 * (n + 1)].tobytes(), dtype=np.uint32).astype(np.int64)
     dl = np.frombuffer(b[h["off_dl"]:h["off_dl"] + 4 * n].tobytes(), dtype=np.float32).astype(np.float64)
     ri = np.frombuffer(b[h["off_ri"]:h["off_ri"] + 4 * n].tobytes(), dtype=np.float32).astype(np.float64)
-    cdf = eng_paper.cdf64
+    cdf = table.cdf64
     assert K[0] == 0 and K[n] == 1 << 23 and np.all(np.diff(K) >= 0)
     q = np.concatenate([np.arange(0, 1 << 23, 997), [0, (1 << 23) - 1], K[:n], np.maximum(K[:n] - 1, 0)])
     u = (q + 0.5) * 2.0 ** -23
     want = np.searchsorted(cdf[:n], u, side="right") - 1      # largest i with cdf[i] <= u
     got = np.searchsorted(K[:n], q, side="right") - 1         # largest i with K[i] <= q
     np.testing.assert_array_equal(got, want)
+    # the kernel's binary lifting from the header's starting step finds the same interval
+    lift = np.zeros_like(q)
+    step = h["top"]
+    while step > 0:
+        t = lift + step
+        ok = t < n
+        ok[ok] = K[t[ok]] <= q[ok]
+        lift = np.where(ok, t, lift)
+        step >>= 1
+    np.testing.assert_array_equal(lift, want)
     # the interpolation aids give the fraction (u - cdf_i) / (cdf_{i+1} - cdf_i)
     i = got
     frac = ((q - K[i]) * 2.0 ** -23 + dl[i]) * ri[i]
