@@ -97,3 +97,31 @@ def test_cdf_matches_oracle_across_grids_and_particles(eng_paper, oracle_mod, n_
     o = oracle_mod.paper_cdf(oracle_mod.PHASE_MIE, m / 1.33, x, n_theta=n_theta)
     np.testing.assert_allclose(t.cdf64, o["cdf"], rtol=0, atol=1e-12)
     assert t.cdf64[0] == 0.0 and t.cdf64[-1] == 1.0 and np.all(np.diff(t.cdf64) >= 0)
+
+
+@pytest.mark.parametrize("n_theta", [16, 2049, 3000])
+def test_camera_interval_search_by_lifting(eng_paper, n_theta):
+    """The camera density's interval: the largest i < n_int with omu[i] <=
+    1 - cos(theta_c), found by the same binary lifting over the blob's omu
+    (1 - cos(i pi / n_int) in single precision)."""
+    import paper_2507_23189_gb300 as g
+    t = eng_paper if n_theta == 3000 else g.PaperTable(n_theta=n_theta)
+    b = t.blob
+    h = _header(b)
+    n = h["n_int"]
+    omu = np.frombuffer(b[h["off_omu"]:h["off_omu"] + 4 * n_theta].tobytes(), dtype=np.float32)
+    th = np.arange(n_theta) * np.pi / n
+    np.testing.assert_allclose(omu, 2 * np.sin(th / 2) ** 2, rtol=1e-6, atol=1e-12)
+    rng = np.random.default_rng(n_theta)
+    om = np.concatenate([rng.uniform(0, 2, 20000), omu[:n], np.nextafter(omu[:n], np.float32(-1)), [0.0, 2.0]])
+    om = np.clip(om.astype(np.float32), 0, 2)
+    want = np.maximum(np.searchsorted(omu[:n], om, side="right") - 1, 0)
+    lift = np.zeros(om.size, dtype=np.int64)
+    step = h["top"]
+    while step > 0:
+        tt = lift + step
+        ok = tt < n
+        ok[ok] = omu[tt[ok]] <= om[ok]
+        lift = np.where(ok, tt, lift)
+        step >>= 1
+    np.testing.assert_array_equal(lift, want)
