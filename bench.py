@@ -319,8 +319,8 @@ def plume_leg(E, dev, steps, flush, n_photons=None):
     centred at x = 22.5 mm) of polystyrene spheres with log-normal diameters
     (median 5 um, sigma_ln 0.3, 16 quantile bins, one mixture table), peak
     optical depth 30 along the beam, 512x512 image, 1e9 photons, delta
-    tracking with 8x16x16-voxel majorant cells. Times mc_grid_prepare and
-    mc_run_grid separately."""
+    tracking with majorant cells of 32x256x256 voxels (8 slabs along the
+    beam). Times mc_grid_prepare, mc_run_grid and the density gradient."""
     import numpy as np
     import torch
     from paper_2507_23189_gb300 import workloads as W
