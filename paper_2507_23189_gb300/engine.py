@@ -413,7 +413,9 @@ class Engine:
         return True
 
     def result(self):
-        """Tallies as float64 numpy arrays in weight units (one photon = 1)."""
+        """Tallies as float64 numpy arrays in weight units (one photon = 1),
+        the raw integer image and totals, and the error word (the flags
+        raised since the previous check)."""
         img = self.image.cpu().numpy().astype(np.float64) * 2.0 ** -self.image_frac_bits
         rad = self.radial.cpu().numpy().astype(np.float64) * 2.0 ** -N.WEIGHT_FRAC_BITS
         tot = self.totals.cpu().numpy()
