@@ -90,6 +90,9 @@ MUTATIONS = [
      "camera cosine sign"),
     ("walk.c", "double rho = c->beam_radius * sqrt(oracle_uniform(o[0]));",
      "double rho = c->beam_radius * oracle_uniform(o[0]);", WALK, "beam entry radius not uniform over the disc"),
+    ("walk.c", "uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0xFFFFFFFFu, 0u};",
+     "uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0u, 0u};", WALK,
+     "beam entry drawn from the first flight's numbers"),
     ("walk.c", "double fr = rho / c->r_max * c->n_radial;", "double fr = rho * rho / c->r_max * c->n_radial;",
      WALK, "radial bin of rho squared"),
     ("walk.c", "rbin = (int)floor(fr);", "rbin = (int)ceil(fr);", WALK, "radial bin rounded up"),

@@ -164,6 +164,11 @@ def test_finite_beam_enters_uniformly_over_its_disc(oracle_mod):
     ang = np.mod(np.arctan2(z, y), 2 * math.pi) / (2 * math.pi)
     for q in (0.25, 0.5, 0.75):
         assert abs(np.mean(ang < q) - q) < 5 * math.sqrt(q * (1 - q) / n), q
+    # the entry point is drawn independently of the first flight, whose
+    # length x1 makes exp(-mu_ext x1) uniform on (0, 1)
+    v = np.exp(-0.5 * r["trace"][:, 0, 1])
+    assert abs(np.corrcoef(u, v)[0, 1]) < 5 / math.sqrt(n)
+    assert abs(np.corrcoef(ang, v)[0, 1]) < 5 / math.sqrt(n)
 
 
 @pytest.mark.parametrize("r_max", [2.0, 1.0])
