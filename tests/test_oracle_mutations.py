@@ -140,6 +140,12 @@ MUTATIONS = [
      "double t = oracle_hat(J->n_w, q, R.muc[j]) - J->z[q];", ADJ, "normalisation counted once"),
     ("adjoint.c", "for (int i = 0; i < j; ++i)\n                    t +=", "for (int i = 1; i < j; ++i)\n                    t +=",
      ADJ, "range of the sampled-angle sum"),
+    ("adjoint.c", "{\n        uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0xFFFFFFFFu, 0u}, o[4];",
+     "{\n        uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0u, 0u}, o[4];", ADJ,
+     "replayed beam entry from the first flight's numbers"),
+    ("adjoint.c", "{\n                uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0xFFFFFFFFu, 0u}, o[4];",
+     "{\n                uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0u, 0u}, o[4];", GADJ,
+     "gradient's beam entry from the first flight's numbers"),
     ("adjoint.c", "r[1] = rho * cos(psi);", "r[1] = -rho * cos(psi);", ADJ, "replayed beam entry point"),
     ("adjoint.c", "r0[1] = rho * cos(psi);", "r0[1] = 0.0;", GADJ, "first flight starts on the axis"),
     ("adjoint.c", "m[i] = a[i] + 0.5 * (t0 + t1) * d[i];", "m[i] = a[i] + t0 * d[i];", GADJ,
