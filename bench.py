@@ -190,7 +190,10 @@ def _batch_vs_plain(E, dev, media, nph, steps, warmup, flush):
         tune = dict(item_photons=0, block_size=0, skipped=True)
     else:
         tune = autotune.tune_batch(batch, media, nph)
-    kw = dict(item_photons=tune["item_photons"], block_size=tune["block_size"])
+    # one image scale for the batch and the sequential runs (the batch's own
+    # default: the largest budget's), so their tallies compare bit for bit
+    frac = E.auto_frac_bits(max(nph))
+    kw = dict(item_photons=tune["item_photons"], block_size=tune["block_size"], image_frac_bits=frac)
     stream = torch.cuda.current_stream(dev)
     for _ in range(warmup):
         batch.run(media, nph, 1, 0, **kw)
@@ -206,7 +209,7 @@ def _batch_vs_plain(E, dev, media, nph, steps, warmup, flush):
 
     def plain():
         for e, m, n in zip(engines, media, nph):
-            e.run(m, n, seed=1, stream=stream)
+            e.run(m, n, seed=1, stream=stream, image_frac_bits=frac)
 
     for _ in range(warmup):
         plain()
@@ -551,7 +554,8 @@ def run_engine(args):
             "photons_per_s": ws * N_PHOTONS * args.steps / t_max,
             "steps_per_photon": steps_per_run / N_PHOTONS,
             "e2e": e2e,
-            "gpu_launches": args.steps, "clocks": clk, "roofline": roof}
+            # per step: the walk kernel and the tally sign check after it
+            "gpu_launches": 2 * args.steps, "clocks": clk, "roofline": roof}
     if not args.no_batched and ws == 1:
         line["batched"] = batched_comparison(E, dev, args.steps, args.warmup, flush)
         line["adjoint"] = adjoint_comparison(E, dev, args.steps, flush)

@@ -40,7 +40,8 @@ typedef enum {
     MC_ERR_CUDA = -2,     /* a CUDA runtime call failed                        */
     MC_ERR_NOMEM = -3,    /* workspace too small                               */
     MC_ERR_TIMEOUT = -4,  /* a bounded device wait (table staging) gave up     */
-    MC_ERR_OVERFLOW = -5, /* a fixed-point contribution exceeded 2^62          */
+    MC_ERR_OVERFLOW = -5, /* a fixed-point contribution exceeded 2^62, or a
+                             tally sum reached 2^63 (wrapped)                  */
     MC_ERR_NUMERIC = -6,  /* a non-finite weight or contribution was seen      */
     MC_ERR_EVENTS = -7,   /* at least one photon hit max_events (truncated)    */
     MC_ERR_TABLE = -8,    /* the device table blob failed its header check     */
@@ -51,7 +52,9 @@ typedef enum {
 #define MC_EFLAG_EVENTS   0x1u
 #define MC_EFLAG_TIMEOUT  0x2u
 #define MC_EFLAG_NUMERIC  0x4u
-#define MC_EFLAG_OVERFLOW 0x8u
+#define MC_EFLAG_OVERFLOW 0x8u  /* a contribution above 2^62, or a non-negative tally
+                                    (pixel, radial bin, total) found negative after a
+                                    run: its sum passed 2^63 */
 #define MC_EFLAG_TABLE    0x10u
 #define MC_EFLAG_BOUNDS   0x20u  /* checked build (MC_CHECKED) only: an index fell outside
                                     its array; the access was clamped instead of made */
@@ -155,6 +158,16 @@ typedef struct {
 mc_status mc_medium_from_density(const mie_info *info, double number_density_per_mm3,
                                  double mu_a_medium, mc_medium *out);
 
+/* Eq. 17 solved for the number density: n = tau / (sigma_ext_mm2 length_mm)
+ * gives optical depth tau (extinction by the particles) over a path of
+ * length_mm; mu_s, mu_a of *out then follow as in mc_medium_from_density
+ * (plus mu_a_medium). *number_density_out (may be NULL) receives n in
+ * particles per mm^3. tau >= 0, length_mm > 0 and info->sigma_ext_mm2 > 0,
+ * all finite, else MC_ERR_ARG. */
+mc_status mc_medium_from_optical_depth(const mie_info *info, double tau, double length_mm,
+                                       double mu_a_medium, mc_medium *out,
+                                       double *number_density_out);
+
 typedef struct {
     double lx, ly, lz;      /* cuvette: x in [0,lx] (beam axis),
                                y in [-ly/2,ly/2], z in [-lz/2,lz/2]            */
@@ -170,14 +183,17 @@ typedef struct {
 } mc_camera;
 
 typedef struct {
-    uint64_t n_photons;     /* photons to run                                  */
+    uint64_t n_photons;     /* photons to run, at most 2^31 per call (the
+                               2^-32-unit weight totals stay below 2^63)       */
     uint64_t photon_offset; /* index of the first photon                       */
     uint64_t seed;          /* Philox key                                      */
     double rr_threshold;    /* weight below which roulette is played           */
     double rr_survival;     /* survival probability (0: plain cut)             */
     uint32_t max_events;    /* free flights per photon before truncation       */
     uint32_t max_scatter;   /* 0: unlimited; else end after that many collisions */
-    int image_frac_bits;    /* fixed-point fraction bits of the image (8..48)  */
+    int image_frac_bits;    /* fixed-point fraction bits of the image (8..48),
+                               or 0 with accumulate = 0: mc_auto_frac_bits
+                               (n_photons) (the batch: of its largest budget) */
     int accumulate;         /* 0: zero the tallies first; 1: add to them       */
     /* launch tuning; results do not depend on these (0 = automatic) */
     int block_size;         /* threads per CTA: 0 or a multiple of 32, <= 1024 */
@@ -187,6 +203,15 @@ typedef struct {
                                3 the rows around the beam that fit in shared
                                memory there, the other rows global            */
 } mc_run_params;
+
+/* Image fraction bits for a photon budget: min(32, 54 - ceil(log2 n)), at
+ * least 8 (32 up to 2^22 photons, 27 at 1e8, 24 at 1e9). A pixel's sum then
+ * stays a factor 2^9 below 2^63 even if it collected one weight unit per
+ * photon. After every run a check flags any image pixel, radial bin or
+ * non-negative total that passed 2^63 (MC_EFLAG_OVERFLOW). When tallies
+ * accumulate over several calls, pass the F of the whole budget explicitly
+ * to each call. */
+int mc_auto_frac_bits(uint64_t n_photons);
 
 /* Totals tallied by mc_run, as int64 in the units noted. */
 enum {
@@ -238,13 +263,17 @@ mc_status mc_run(const mc_medium *medium, const mc_geometry *geom,
  * only the buffers it reads and writes). The paper has no counterpart: this is
  * an interface convenience. The scratch the walk needs lives in a fixed
  * MC_STATIC_SCRATCH_BYTES device array inside the library, held by every GPU
- * that loads it until exit; cameras needing more workspace than that are
- * rejected with MC_ERR_NOMEM. The first call on a device looks the array up
- * (cudaGetSymbolAddress), so make it before any stream capture. All calls
- * share the array: consecutive calls are independent (the counter is cleared
- * on the stream first), but calls that overlap on the GPU race and must be
- * serialised by the caller. Allocates nothing. Other arguments and errors as
- * for mc_run. */
+ * that loads it until exit. Every valid camera needs mc_workspace_bytes() =
+ * 256 bytes today, so the MC_ERR_NOMEM rejection of a workspace larger than
+ * the array only guards against future growth of the walk's scratch; an
+ * invalid camera is MC_ERR_ARG. The array's address is looked up
+ * (cudaGetSymbolAddress) by the first call in each CUDA context of a device
+ * and cached with the context's id, so a new context (after cudaDeviceReset,
+ * say) is looked up again; make the first call in a context before any
+ * stream capture. All calls share the array: consecutive calls are
+ * independent (the counter is cleared on the stream first), but calls that
+ * overlap on the GPU race and must be serialised by the caller. Allocates
+ * nothing. Other arguments and errors as for mc_run. */
 #define MC_STATIC_SCRATCH_BYTES 4096
 mc_status mc_run_static(const mc_medium *medium, const mc_geometry *geom,
                         const mc_camera *camera, const mc_run_params *run,

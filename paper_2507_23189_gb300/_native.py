@@ -27,7 +27,8 @@ EXPORTS = ("mc_table_bytes", "mie_table_build", "mc_medium_from_density", "mc_wo
            "mc_adjoint_workspace_bytes", "mc_adjoint", "mc_paper_table_bytes", "mie_paper_table_build",
            "mc_metrics_out_len", "mc_metrics_workspace_bytes", "mc_image_metrics", "mie_mixture_table_build",
            "mc_grid_workspace_bytes", "mc_grid_prepare", "mc_run_grid", "mc_grid_adjoint_workspace_bytes",
-           "mc_grid_adjoint", "mc_check_within", "mc_wait_selftest")
+           "mc_grid_adjoint", "mc_check_within", "mc_wait_selftest", "mc_medium_from_optical_depth",
+           "mc_auto_frac_bits")
 
 
 class McError(RuntimeError):
@@ -103,6 +104,9 @@ def lib():
     if os.environ.get("MC_CHECKED") == "1":
         # the index-checked build (paper_2507_23189_gb300.build.build_checked())
         path = os.path.join(HERE, "_build", "libmcmie_checked.so")
+    elif os.environ.get("MC_STRICT") == "1":
+        # the IEEE-strict build (paper_2507_23189_gb300.build.build_strict())
+        path = os.path.join(HERE, "_build", "libmcmie_strict.so")
     if not os.path.exists(path):
         raise RuntimeError("engine library %s is missing: run paper_2507_23189_gb300.build.build() "
                            "(or __graft_entry__.build()) first" % path)
@@ -115,6 +119,11 @@ def lib():
     L.mie_table_build.argtypes = [P(MieParams), P(MieInfo), vp, P(C.c_double), P(C.c_double)]
     L.mc_medium_from_density.restype = C.c_int
     L.mc_medium_from_density.argtypes = [P(MieInfo), C.c_double, C.c_double, P(Medium)]
+    L.mc_medium_from_optical_depth.restype = C.c_int
+    L.mc_medium_from_optical_depth.argtypes = [P(MieInfo), C.c_double, C.c_double, C.c_double, P(Medium),
+                                               P(C.c_double)]
+    L.mc_auto_frac_bits.restype = C.c_int
+    L.mc_auto_frac_bits.argtypes = [C.c_uint64]
     L.mc_workspace_bytes.restype = C.c_size_t
     L.mc_workspace_bytes.argtypes = [P(Camera)]
     L.mc_run.restype = C.c_int

@@ -16,6 +16,11 @@ LIB = os.path.join(HERE, "_build", "libmcmie.so")
 # time (MC_CHECKED: an out-of-range index sets MC_EFLAG_BOUNDS and is clamped);
 # for tests, built only on request
 LIB_CHECKED = os.path.join(HERE, "_build", "libmcmie_checked.so")
+# the same engine with CUDA's accurate logf / expf / exp2f / sincosf and
+# correctly rounded division and square root in place of the hardware
+# approximations (MC_STRICT), for trace comparisons at the tightest tolerance;
+# built only on request, loaded instead of the normal one when MC_STRICT=1
+LIB_STRICT = os.path.join(HERE, "_build", "libmcmie_strict.so")
 SOURCES = ["walk.cu", "api.cu", "mie_table.cpp", "noalloc.cu", "metrics.cu", "grid.cu"]
 HEADERS = ["engine.h", "table_format.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -66,6 +71,21 @@ def build_checked(force=False, verbose=False):
             raise subprocess.CalledProcessError(proc.returncode, "nvcc")
         os.replace(tmp, lib)
     return LIB_CHECKED
+
+
+def build_strict(force=False, verbose=False):
+    """Compile the IEEE-strict engine (-DMC_STRICT) if missing or stale;
+    return its path. Loaded instead of the normal one when MC_STRICT=1."""
+    me = os.path.abspath(__file__)
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [
+        os.path.join(ROOT, "include", "mcmie.h"), me]
+    job = _compile(LIB_STRICT, SOURCES, deps, force, verbose, ["-DMC_STRICT"])
+    if job is not None:
+        proc, tmp, lib = job
+        if proc.wait() != 0:
+            raise subprocess.CalledProcessError(proc.returncode, "nvcc")
+        os.replace(tmp, lib)
+    return LIB_STRICT
 
 
 def build(force=False, verbose=False, extra=()):

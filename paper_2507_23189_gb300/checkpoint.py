@@ -77,6 +77,10 @@ def run_resumable(engine, medium, n_photons, path, chunk=100_000_000, seed=1, st
     for k in ("photon_offset", "accumulate", "n_photons"):
         if k in run_kw:
             raise ValueError("%s is set by run_resumable" % k)
+    if not run_kw.get("image_frac_bits"):
+        # the chunks accumulate into one image: one F, from the whole budget
+        from .engine import auto_frac_bits
+        run_kw = dict(run_kw, image_frac_bits=auto_frac_bits(n_photons))
     key = config_key(engine, medium, n_photons, seed, run_kw)
     done, n_chunks = 0, 0
     sumsq = np.zeros(tuple(engine.image.shape), dtype=np.float64)
@@ -89,7 +93,7 @@ def run_resumable(engine, medium, n_photons, path, chunk=100_000_000, seed=1, st
         engine.image.zero_()
         engine.radial.zero_()
         engine.totals.zero_()
-    engine.image_frac_bits = int(run_kw.get("image_frac_bits", 32))
+    engine.image_frac_bits = int(run_kw["image_frac_bits"])
     scale = 2.0 ** -engine.image_frac_bits
     prev = engine.image.cpu().numpy().copy()
     chunks = 0
@@ -127,7 +131,9 @@ def run_record(engine, medium, n_photons, seconds, steps=None, **extra):
     """One JSON-serialisable record of a run: configuration, photons,
     photon-steps, wall time and rate, the weight totals of the engine's
     tallies (R, T far, T side, A, roulette, truncated, ballistic; weight
-    units) and the error word."""
+    units) and the error word the engine's last check() read (the flags
+    raised by the runs it covered; check() raises when any is set, so a run
+    recorded after a passing check logs 0)."""
     tot = engine.totals.cpu().numpy()
     w = tot[:7].astype(np.float64) * 2.0 ** -N.WEIGHT_FRAC_BITS
     steps = int(tot[N.TOT_STEPS]) if steps is None else int(steps)
@@ -138,7 +144,7 @@ def run_record(engine, medium, n_photons, seconds, steps=None, **extra):
                photon_steps_per_s=steps / seconds if seconds > 0 else None,
                totals=dict(zip(("reflect", "far", "side", "absorbed", "roulette", "truncated", "ballistic"),
                                map(float, w))),
-               error=int(engine.error.cpu().numpy()[0]))
+               error=int(getattr(engine, "last_error", 0)))
     rec.update(extra)
     return rec
 

@@ -67,11 +67,37 @@ mc_status check_camera(const mc_camera *c)
     return MC_OK;
 }
 
+// Photons one call may run: the weight totals are in 2^-32 units and a
+// photon's exits, absorption and truncation add up to about its unit weight,
+// so 2^31 photons keep every total below 2^63.
+constexpr uint64_t kMaxPhotons = 1ull << 31;
+
+// image_frac_bits 0 (fresh tallies only): the fraction bits for a budget of
+// n photons, min(32, 54 - ceil(log2 n)), at least 8. 54 = 63 - 9 leaves a
+// factor 2^9 between 2^63 and n times one weight unit per photon in one
+// pixel (a pixel's expected sum per photon is far below one weight unit).
+int auto_frac_bits(uint64_t n)
+{
+    int lg = 0;
+    while (lg < 64 && (1ull << lg) < n) ++lg;   // ceil(log2 n) for n >= 1
+    int f = 54 - lg;
+    if (f > 32) f = 32;
+    if (f < 8) f = 8;
+    return f;
+}
+
+int frac_bits_of(const mc_run_params *r, uint64_t n_photons)
+{
+    return r->image_frac_bits ? r->image_frac_bits : auto_frac_bits(n_photons);
+}
+
 mc_status check_run(const mc_run_params *r)
 {
     if (!r || !fin(r->rr_threshold) || r->rr_threshold < 0 || !fin(r->rr_survival) ||
-        r->rr_survival < 0 || r->rr_survival > 1 || r->max_events < 1 || r->image_frac_bits < 8 ||
-        r->image_frac_bits > 48 || (r->accumulate != 0 && r->accumulate != 1) ||
+        r->rr_survival < 0 || r->rr_survival > 1 || r->max_events < 1 ||
+        !((r->image_frac_bits >= 8 && r->image_frac_bits <= 48) ||
+          (r->image_frac_bits == 0 && r->accumulate == 0)) ||
+        r->n_photons > kMaxPhotons || (r->accumulate != 0 && r->accumulate != 1) ||
         r->photon_offset + r->n_photons < r->photon_offset || r->block_size < 0 ||
         r->block_size > 1024 || (r->block_size % 32) != 0 || r->blocks_per_sm < 0 ||
         r->blocks_per_sm > 64 || r->image_mode < 0 || r->image_mode > 3)
@@ -118,8 +144,9 @@ void fill_medium(mcx::MediumArgs &m, const mc_medium *med, uint64_t n_photons, u
     m.totals = reinterpret_cast<unsigned long long *>(totals);
 }
 
+// n_photons: the budget an automatic image_frac_bits is chosen for.
 void fill_common(mcx::CommonArgs &c, const mc_medium *m, const mc_geometry *g, const mc_camera *cam,
-                 const mc_run_params *r, uint32_t *error)
+                 const mc_run_params *r, uint32_t *error, uint64_t n_photons)
 {
     c.phase_kind = m->phase_kind;
     c.table_bytes = (uint32_t)table_bytes_of(m);
@@ -139,7 +166,7 @@ void fill_common(mcx::CommonArgs &c, const mc_medium *m, const mc_geometry *g, c
     c.inv_rr_surv = r->rr_survival > 0 ? (float)(1.0 / r->rr_survival) : 0.0f;
     c.max_events = r->max_events;
     c.max_scatter = r->max_scatter;
-    c.img_scale = std::ldexp(1.0f, r->image_frac_bits);
+    c.img_scale = std::ldexp(1.0f, frac_bits_of(r, n_photons));
     c.error = error;
     c.extra_bytes = 0;
 }
@@ -149,7 +176,7 @@ mcx::WalkArgs make_args(const mc_medium *m, const mc_geometry *g, const mc_camer
 {
     mcx::WalkArgs a;
     std::memset(&a, 0, sizeof a);
-    fill_common(a.c, m, g, c, r, t->d_error);
+    fill_common(a.c, m, g, c, r, t->d_error, r->n_photons);
     fill_medium(a.m, m, r->n_photons, r->photon_offset, r->seed, t->d_image, t->d_radial, t->d_totals);
     a.counter = reinterpret_cast<unsigned long long *>(t->d_work);
     return a;
@@ -207,6 +234,8 @@ mc_status run_common(const mc_medium *m, const mc_geometry *g, const mc_camera *
 }  // namespace
 
 extern "C" {
+
+int mc_auto_frac_bits(uint64_t n_photons) { return auto_frac_bits(n_photons); }
 
 size_t mc_workspace_bytes(const mc_camera *camera)
 {
@@ -339,7 +368,8 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom, 
             (I.medium.phase_kind != MC_PHASE_HG && I.medium.n_bins != inst[0].medium.n_bins))
             return MC_ERR_ARG;   // one phase kind and table size per batch
         if (!I.d_image || !I.d_radial || !I.d_totals || !aligned(I.d_image, 8) || !aligned(I.d_radial, 8) ||
-            !aligned(I.d_totals, 8) || I.photon_offset + I.n_photons < I.photon_offset)
+            !aligned(I.d_totals, 8) || I.photon_offset + I.n_photons < I.photon_offset ||
+            I.n_photons > kMaxPhotons)
             return MC_ERR_ARG;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -369,7 +399,9 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom, 
     mcx::BatchArgs *a = new (std::nothrow) mcx::BatchArgs;
     if (!a) return MC_ERR_NOMEM;
     std::memset(a, 0, sizeof *a);
-    fill_common(a->c, &inst[0].medium, geom, camera, run, d_error);
+    uint64_t n_max = 0;
+    for (int i = 0; i < n; ++i) n_max = inst[i].n_photons > n_max ? inst[i].n_photons : n_max;
+    fill_common(a->c, &inst[0].medium, geom, camera, run, d_error, n_max);
     a->n_media = n;
     a->item_photons = ip;
     a->queue = static_cast<unsigned long long *>(d_work);
@@ -417,7 +449,7 @@ mc_status mc_adjoint(const mc_medium *medium, const mc_geometry *geom, const mc_
     if (run->n_photons == 0) return MC_OK;
     mcx::AdjArgs a;
     std::memset(&a, 0, sizeof a);
-    fill_common(a.c, medium, geom, camera, run, d_error);
+    fill_common(a.c, medium, geom, camera, run, d_error, run->n_photons);
     fill_medium(a.m, medium, run->n_photons, run->photon_offset, run->seed, nullptr, nullptr, nullptr);
     a.adj = d_adj_image;
     a.n_w = n_phase_w;
@@ -517,7 +549,7 @@ void fill_grid(mcx::GridArgs &a, const mc_grid *g, int mx, int my, int mz, const
                uint32_t *d_error, int64_t *image, int64_t *radial, int64_t *totals)
 {
     std::memset(&a, 0, sizeof a);
-    fill_common(a.c, m, geom, camera, run, d_error);
+    fill_common(a.c, m, geom, camera, run, d_error, run->n_photons);
     fill_medium(a.m, m, run->n_photons, run->photon_offset, run->seed, image, radial, totals);
     const unsigned char *w = static_cast<const unsigned char *>(d_grid_work);
     a.cells = reinterpret_cast<const float2 *>(w);

@@ -357,6 +357,22 @@ extern "C" mc_status mc_medium_from_density(const mie_info *info, double nd, dou
     return MC_OK;
 }
 
+// Eq. 17 solved for the number density: OD = n sigma_e L gives n = OD /
+// (sigma_e L), then the coefficients as mc_medium_from_density.
+extern "C" mc_status mc_medium_from_optical_depth(const mie_info *info, double tau, double length_mm,
+                                                  double mu_a_medium, mc_medium *out,
+                                                  double *number_density_out)
+{
+    if (!info || !out || !std::isfinite(tau) || !(tau >= 0.0) || !std::isfinite(length_mm) ||
+        !(length_mm > 0.0) || !std::isfinite(info->sigma_ext_mm2) || !(info->sigma_ext_mm2 > 0.0))
+        return MC_ERR_ARG;
+    const double nd = tau / (info->sigma_ext_mm2 * length_mm);
+    if (!std::isfinite(nd)) return MC_ERR_ARG;
+    const mc_status s = mc_medium_from_density(info, nd, mu_a_medium, out);
+    if (s == MC_OK && number_density_out) *number_density_out = nd;
+    return s;
+}
+
 // A suspension of several particle kinds (the size bins of a polydisperse
 // sample, number fractions f_k) scatters with the mixture of their phase
 // functions weighted by f_k sigma_sca,k (Eq. 14 per kind); each raw

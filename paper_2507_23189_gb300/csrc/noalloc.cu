@@ -13,15 +13,20 @@
 //    MC_STATIC_SCRATCH_BYTES bytes. Every GPU that loads the library holds it
 //    until the process exits. A camera whose workspace would not fit is
 //    rejected with MC_ERR_NOMEM before anything is launched.
-//  * The first call on each device looks the array's device address up with
-//    cudaGetSymbolAddress (with that device current) and caches it; make that
-//    first call before any stream capture.
+//  * The array's device address is looked up with cudaGetSymbolAddress
+//    (with the device current) and cached per device together with the id
+//    of the CUDA context it belongs to. A call in another context of that
+//    device (after cudaDeviceReset, or when a host tears its context down and
+//    builds a new one) finds the id changed and looks the address up again;
+//    only such a look-up may load the library's module on the device, so the
+//    first call in each context should come before any stream capture.
 //  * All calls share the one array, which keeps what the last call left in it.
 //    mc_run clears the counter on the stream before every launch, so
 //    consecutive calls are independent, but calls whose work overlaps on the
 //    GPU (different streams, or different host threads) race on the counter
 //    and must be serialised by the caller.
 //  * Nothing here calls cudaMalloc, cudaFree or an allocating library routine.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -34,20 +39,59 @@ static __device__ __align__(256) unsigned char g_scratch[MC_STATIC_SCRATCH_BYTES
 
 constexpr int kMaxDevices = 64;
 std::mutex g_lock;
-void *g_addr[kMaxDevices] = {};
+struct Cached {
+    unsigned long long ctx_id;   // id of the context the address belongs to
+    void *addr;                  // device address of g_scratch there (null: none yet)
+};
+Cached g_cache[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device (looked up once).
+// The driver's context queries, reached through the runtime (no link to the
+// driver library): current context and its process-unique id.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+bool context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    if (!get_current || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_scratch in the current device's current context.
 mc_status scratch_address(void **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MC_ERR_CUDA;
     std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return MC_ERR_CUDA;
-        g_addr[dev] = p;
+    Cached &c = g_cache[dev];
+    unsigned long long id = 0;
+    if (c.addr && context_id(&id) && c.ctx_id == id) {
+        *out = c.addr;
+        return MC_OK;
     }
-    *out = g_addr[dev];
+    // first call in this context (the look-up also makes the runtime's
+    // context current on this thread if no context is yet)
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return MC_ERR_CUDA;
+    if (!context_id(&id)) return MC_ERR_CUDA;
+    c.addr = p;
+    c.ctx_id = id;
+    *out = p;
     return MC_OK;
 }
 

@@ -79,12 +79,70 @@ __device__ __forceinline__ uint4 philox10(uint4 c, const uint32_t (&rk)[20])
     return c;
 }
 
-// 2^x by the hardware approximation (relative error a few 1e-7).
-__device__ __forceinline__ float ex2_approx(float x)
+// Transcendentals, reciprocals and square roots of the walk. The production
+// build calls the hardware approximations (log2 / ex2 / sin / cos / rsqrt /
+// reciprocal units, errors of a few units in the last place); the IEEE-strict
+// build (MC_STRICT) calls CUDA's accurate logf / expf / exp2f / sincosf and the
+// correctly rounded division and square root instead, so that traces can be
+// compared with a double-precision reference at the tightest tolerance.
+__device__ __forceinline__ float mc_log(float x)
 {
-    float y;
+#ifdef MC_STRICT
+    return logf(x);
+#else
+    return __logf(x);
+#endif
+}
+__device__ __forceinline__ float mc_exp(float x)
+{
+#ifdef MC_STRICT
+    return expf(x);
+#else
+    return __expf(x);
+#endif
+}
+__device__ __forceinline__ float mc_exp2(float x)
+{
+#ifdef MC_STRICT
+    return exp2f(x);
+#else
+    float y;   // the hardware approximation, relative error a few 1e-7
     asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+#endif
+}
+__device__ __forceinline__ void mc_sincos(float x, float *s, float *c)
+{
+#ifdef MC_STRICT
+    sincosf(x, s, c);
+#else
+    __sincosf(x, s, c);
+#endif
+}
+__device__ __forceinline__ float mc_div(float a, float b)
+{
+#ifdef MC_STRICT
+    return a / b;
+#else
+    return __fdividef(a, b);
+#endif
+}
+__device__ __forceinline__ float mc_rsqrt(float x)
+{
+#ifdef MC_STRICT
+    return 1.0f / sqrtf(x);
+#else
+    return rsqrtf(x);
+#endif
+}
+// sqrt(x) for x >= 0 (0 for x <= 0)
+__device__ __forceinline__ float mc_sqrt0(float x)
+{
+#ifdef MC_STRICT
+    return x > 0.0f ? sqrtf(x) : 0.0f;
+#else
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+#endif
 }
 
 // (r >> 9) 2^-23 + 2^-24, exact: the float 1 + (r>>9) 2^-23 minus (1 - 2^-24).
@@ -247,7 +305,7 @@ __device__ __forceinline__ float camera_psr(const MediumArgs &M, const CommonArg
     if (PHASE == MC_PHASE_HG) {
         // Eq. 11 per steradian, K t^(-3/2) with t = (1-g)^2 + 2g(1 - mu)
         const float t = fmaf(M.hg_two_g, 1.0f - dy, M.hg_a2);
-        const float r = rsqrtf(t);
+        const float r = mc_rsqrt(t);
         nb = -1;
         return M.hg_K * (r * r * r);
     }
@@ -256,7 +314,7 @@ __device__ __forceinline__ float camera_psr(const MediumArgs &M, const CommonArg
         const float om = 1.0f - fminf(fmaxf(dy, -1.0f), 1.0f);
         nb = chk(lift_search(S.omu, S.pn, S.ptop, om), S.pn, C.error);
         const float st2 = om * (2.0f - om);
-        return st2 > 0.0f ? S.pdf[nb] * rsqrtf(st2) * INV_2PI : 0.0f;
+        return st2 > 0.0f ? S.pdf[nb] * mc_rsqrt(st2) * INV_2PI : 0.0f;
     }
     nb = chk(table_bin(S.omu, S.guide, C.n_bins, dy), C.n_bins, C.error);
     return S.pdf[nb] * INV_2PI;
@@ -277,7 +335,7 @@ __device__ __forceinline__ float sample_omu(const MediumArgs &M, const CommonArg
 {
     if (PHASE == MC_PHASE_HG) {
         const float D = fmaf(M.hg_two_g, u1, M.hg_one_m_g);
-        return __fdividef(M.hg_A * (1.0f - u1) * fmaf(M.hg_g, u1, 1.0f), D * D);
+        return mc_div(M.hg_A * (1.0f - u1) * fmaf(M.hg_g, u1, 1.0f), D * D);
     }
     if (PHASE == MC_PHASE_PAPER) {
         // bisection of the cumulative distribution on the uniform's integer
@@ -303,21 +361,21 @@ __device__ __forceinline__ void rotate(float &dx, float &dy, float &dz, float om
 {
     const float mu = 1.0f - om;
     const float st2 = om * (2.0f - om);
-    const float st = st2 > 0.0f ? st2 * rsqrtf(st2) : 0.0f;
+    const float st = mc_sqrt0(st2);
     // phi = 2 pi u2 through the hardware sine / cosine, evaluated at
     // phi - pi in [-pi, pi) where they are most accurate
     float sp, cp;
-    __sincosf(fmaf(6.28318530717958647692f, u2, -3.14159265358979323846f), &sp, &cp);
+    mc_sincos(fmaf(6.28318530717958647692f, u2, -3.14159265358979323846f), &sp, &cp);
     sp = -sp;
     cp = -cp;
     const float sg = copysignf(1.0f, dz);
-    const float a = __fdividef(-1.0f, sg + dz);
+    const float a = mc_div(-1.0f, sg + dz);
     const float b = dx * dy * a;
     const float e1x = fmaf(sg * dx * dx, a, 1.0f), e1y = sg * b, e1z = -sg * dx;
     const float e2x = b, e2y = fmaf(dy * dy, a, sg), e2z = -dy;
     const float qx = fmaf(cp, e1x, sp * e2x), qy = fmaf(cp, e1y, sp * e2y), qz = fmaf(cp, e1z, sp * e2z);
     const float nx = fmaf(mu, dx, st * qx), ny = fmaf(mu, dy, st * qy), nz = fmaf(mu, dz, st * qz);
-    const float inv = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+    const float inv = mc_rsqrt(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
     dx = nx * inv; dy = ny * inv; dz = nz * inv;
 }
 
@@ -501,7 +559,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
         ++T.steps;
         const float u0 = u01(rnd.x), u1 = u01(rnd.y), u2 = u01(rnd.z), u3 = u01(rnd.w);
 
-        const float s = -__logf(u0) * M.inv_mu_ext;                 // Eq. 15
+        const float s = -mc_log(u0) * M.inv_mu_ext;                 // Eq. 15
         const float px = fmaf(s, dx, rx), py = fmaf(s, dy, ry), pz = fmaf(s, dz, rz);
         const bool cx = !((px > 0.f) & (px < C.lx));
         const bool cy = !(fabsf(py) < C.hy);
@@ -529,10 +587,10 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
             } else if (face == 0) {
                 T.far += wv;
                 if (ncoll == 0) T.ball += wv;
-                const float t = __fdividef(C.lx - rx, dx);
+                const float t = mc_div(C.lx - rx, dx);
                 ex = C.lx; ey = fmaf(t, dy, ry); ez = fmaf(t, dz, rz);
                 const float r2 = fmaf(ey, ey, ez * ez);
-                const float rho = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+                const float rho = mc_sqrt0(r2);
                 rb = chk(min(__float2int_rd(rho * C.sr), C.n_radial - 1), C.n_radial, C.error);
                 sadd64(&s_rad[rb], wv);
                 status = 2;
@@ -566,7 +624,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
         // camera: next-event estimate toward +y
         int nb, ix, iz;
         const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
-        const float nee = w * psr * ex2_approx(fmaf(cam_a, ry, cam_b));
+        const float nee = w * psr * mc_exp2(fmaf(cam_a, ry, cam_b));
         const int pix = camera_pixel(C, rx, rz, ix, iz);
         const float vf = nee * C.img_scale;
         if (vf < 4.0e18f) {
@@ -768,7 +826,7 @@ __device__ __forceinline__ int grid_flight(const GridArgs &G, const float *s_maj
         const int ax = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
         const float t1 = fmaxf(ax == 0 ? tx : (ax == 1 ? ty : tz), t0);
         if (mb * (t1 - t0) > tau) {
-            const float sl = t0 + __fdividef(tau, mb);
+            const float sl = t0 + mc_div(tau, mb);
             rx = fmaf(sl, dx, rx); ry = fmaf(sl, dy, ry); rz = fmaf(sl, dz, rz);
             return 3;
         }
@@ -880,7 +938,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
 
         // -------- one tentative flight
         float mb = 0.f;
-        const int face = grid_flight(G, s_maj, -__logf(u01(rnd.x)), rx, ry, rz, dx, dy, dz, idx, idy, idz, mb);
+        const int face = grid_flight(G, s_maj, -mc_log(u01(rnd.x)), rx, ry, rz, dx, dy, dz, idx, idy, idz, mb);
         const bool hit = face == 3;
         if (face < 0) {
             // a non-finite direction or more crossings than cells: give up on
@@ -900,7 +958,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
                 T.far += wv;
                 if (ncoll == 0) T.ball += wv;
                 const float r2 = fmaf(ry, ry, rz * rz);
-                const float rho = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+                const float rho = mc_sqrt0(r2);
                 rb = chk(min(__float2int_rd(rho * C.sr), C.n_radial - 1), C.n_radial, C.error);
                 sadd64(&s_rad[rb], wv);
                 status = 2;
@@ -918,12 +976,12 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
         const int iy = min(max(__float2int_rd((ry + C.hy) * G.inv_vy), 0), G.gy - 1);
         const int iz = min(max(__float2int_rd((rz + C.hz) * G.inv_vz), 0), G.gz - 1);
         const float2 cell = __ldg(&G.cells[chk((iz * G.gy + iy) * G.gx + ix, G.gx * G.gy * G.gz, C.error)]);
-        const float acc = __fdividef(cell.x, mb);   // hardware reciprocal: a few ulp
+        const float acc = mc_div(cell.x, mb);   // hardware reciprocal (a few ulp) unless strict
         if (!(u3 < acc)) continue;   // null collision
-        u3 = __fdividef(u3, acc);
+        u3 = mc_div(u3, acc);
         ++ncoll;
         {   // Eq. 16 with the voxel's albedo
-            const float a = G.mu_a > 0.f ? G.ks_over_ke * (1.0f - __fdividef(G.mu_a, cell.x)) : G.ks_over_ke;
+            const float a = G.mu_a > 0.f ? G.ks_over_ke * (1.0f - mc_div(G.mu_a, cell.x)) : G.ks_over_ke;
             const float wn = w * a;
             if (a < 1.0f) T.abs += fix32(w - wn);
             w = wn;
@@ -931,7 +989,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
         int nb, pix_x, pix_z;
         const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
         const float top = (iy == G.gy - 1) ? C.hy : fmaf((float)(iy + 1), G.vy, -C.hy);
-        const float nee = w * psr * __expf(-fmaf(cell.x, top - ry, cell.y));
+        const float nee = w * psr * mc_exp(-fmaf(cell.x, top - ry, cell.y));
         const int pix = camera_pixel(C, rx, rz, pix_x, pix_z);
         const float vf = nee * C.img_scale;
         if (vf < 4.0e18f) {
@@ -950,7 +1008,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
                 alive = false;
             } else {
                 rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
-                idx = __fdividef(1.0f, dx); idy = __fdividef(1.0f, dy); idz = __fdividef(1.0f, dz);
+                idx = mc_div(1.0f, dx); idy = mc_div(1.0f, dy); idz = mc_div(1.0f, dz);
                 if (w < C.rr_thr) {
                     if (u3 < C.rr_surv) {
                         const float wn = w * C.inv_rr_surv;
@@ -970,7 +1028,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
             // one branch for the rare cases, as in walk_loop
             const bool cap = C.max_scatter && ncoll >= C.max_scatter;
             rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
-            idx = __fdividef(1.0f, dx); idy = __fdividef(1.0f, dy); idz = __fdividef(1.0f, dz);
+            idx = mc_div(1.0f, dx); idy = mc_div(1.0f, dy); idz = mc_div(1.0f, dz);
             if (cap | (w < C.rr_thr) | !(w == w)) {
                 if (cap) {
                     sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
@@ -1259,7 +1317,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
             const float u1 = u01(rnd.y), u2 = u01(rnd.z);
             float u3 = u01(rnd.w);
             float mb = 0.f;
-            const int face = grid_flight(G, s_maj, -__logf(u01(rnd.x)), rx, ry, rz, dx, dy, dz, idx, idy, idz, mb);
+            const int face = grid_flight(G, s_maj, -mc_log(u01(rnd.x)), rx, ry, rz, dx, dy, dz, idx, idy, idz, mb);
             if (face < 0) {
                 atomicOr(C.error, MC_EFLAG_NUMERIC);
                 end = true;
@@ -1271,16 +1329,16 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                 const int iz = min(max(__float2int_rd((rz + C.hz) * G.inv_vz), 0), G.gz - 1);
                 const size_t v = chk((iz * G.gy + iy) * G.gx + ix, G.gx * G.gy * G.gz, C.error);
                 const float2 cell = __ldg(&G.cells[v]);
-                const float acc = __fdividef(cell.x, mb);   // hardware reciprocal: a few ulp
+                const float acc = mc_div(cell.x, mb);   // hardware reciprocal (a few ulp) unless strict
                 if (u3 < acc) {
-                    u3 = __fdividef(u3, acc);
+                    u3 = mc_div(u3, acc);
                     ++ncoll;
-                    const float a = G.mu_a > 0.f ? G.ks_over_ke * (1.0f - __fdividef(G.mu_a, cell.x)) : G.ks_over_ke;
+                    const float a = G.mu_a > 0.f ? G.ks_over_ke * (1.0f - mc_div(G.mu_a, cell.x)) : G.ks_over_ke;
                     w = w * a;
                     int nb, pix_x, pix_z;
                     const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
                     const float top = (iy == G.gy - 1) ? C.hy : fmaf((float)(iy + 1), G.vy, -C.hy);
-                    const float nee = w * psr * __expf(-fmaf(cell.x, top - ry, cell.y));
+                    const float nee = w * psr * mc_exp(-fmaf(cell.x, top - ry, cell.y));
                     const int pix = camera_pixel(C, rx, rz, pix_x, pix_z);
                     const float Aj = __ldg(&A.adj[pix]) * nee;
                     if (pass == 1) {
@@ -1289,7 +1347,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                         float gv = -A.k_ext * Aj * (top - ry);
                         if (B != 0.f) {
                             const float dens = cell.x - G.mu_a;   // k_ext n_v
-                            if (dens > 0.f) gv = fmaf(B, __fdividef(A.k_ext, dens), gv);
+                            if (dens > 0.f) gv = fmaf(B, mc_div(A.k_ext, dens), gv);
                             const float coef = -B * A.k_ext;
                             if (ncoll == 1) {
                                 // first flight, along +x from the entry point in this
@@ -1329,7 +1387,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                         end = true;
                     } else {
                         rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
-                        idx = __fdividef(1.0f, dx); idy = __fdividef(1.0f, dy); idz = __fdividef(1.0f, dz);
+                        idx = mc_div(1.0f, dx); idy = mc_div(1.0f, dy); idz = mc_div(1.0f, dz);
                         if (w < C.rr_thr) {
                             if (u3 < C.rr_surv) w = w * C.inv_rr_surv;
                             else end = true;
@@ -1581,7 +1639,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
         const uint4 rnd = philox10(make_uint4(pk0, pk1, ev, 0u), M.rk);
         ++ev;
         const float u0 = u01(rnd.x), u1 = u01(rnd.y), u2 = u01(rnd.z), u3 = u01(rnd.w);
-        const float s = -__logf(u0) * M.inv_mu_ext;
+        const float s = -mc_log(u0) * M.inv_mu_ext;
         const float px = fmaf(s, dx, rx), py = fmaf(s, dy, ry), pz = fmaf(s, dz, rz);
         bool end = !((px > 0.f) & (px < C.lx) & (fabsf(py) < C.hy) & (fabsf(pz) < C.hz));
         if (!end) {
@@ -1592,7 +1650,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
             int nb, ix, iz;
             const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
             const float l = C.hy - ry;
-            const float nee = w * psr * __expf(-M.mu_ext * l);
+            const float nee = w * psr * mc_exp(-M.mu_ext * l);
             const int pix = camera_pixel(C, rx, rz, ix, iz);
             const float Aj = __ldg(&A.adj[pix]) * nee;
             P += Aj;
@@ -1734,6 +1792,49 @@ __global__ void philox_kernel(const uint4 *ctr, uint64_t n, uint32_t k0, uint32_
         out[i] = philox10(ctr[i], k0, k1);
 }
 
+// Tallies whose contributions are all non-negative (image pixels, radial
+// bins, every total but the signed roulette net) can turn negative only by
+// passing 2^63 in fixed point: such a sum has wrapped, and the run is flagged
+// MC_EFLAG_OVERFLOW. Blocks of medium blockIdx.y scan its tallies grid-stride.
+constexpr int SIGN_BLOCK = 256;
+__device__ __forceinline__ void sign_scan(const MediumArgs &M, int npix, int n_radial, uint32_t *err)
+{
+    const long long *img = reinterpret_cast<const long long *>(M.image);
+    bool bad = false;
+    for (int i = blockIdx.x * SIGN_BLOCK + threadIdx.x; i < npix; i += gridDim.x * SIGN_BLOCK)
+        bad |= img[i] < 0;
+    if (blockIdx.x == 0) {
+        const long long *rad = reinterpret_cast<const long long *>(M.radial);
+        for (int i = threadIdx.x; i < n_radial; i += SIGN_BLOCK) bad |= rad[i] < 0;
+        if (threadIdx.x < MC_N_TOTALS && threadIdx.x != MC_TOT_ROULETTE)
+            bad |= reinterpret_cast<const long long *>(M.totals)[threadIdx.x] < 0;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, MC_EFLAG_OVERFLOW);
+}
+
+__global__ void __launch_bounds__(SIGN_BLOCK) sign_check_kernel(const __grid_constant__ WalkArgs A)
+{
+    sign_scan(A.m, A.c.nx * A.c.nz, A.c.n_radial, A.c.error);
+}
+
+__global__ void __launch_bounds__(SIGN_BLOCK) batch_sign_check_kernel(const __grid_constant__ BatchArgs B)
+{
+    sign_scan(B.m[blockIdx.y], B.c.nx * B.c.nz, B.c.n_radial, B.c.error);
+}
+
+unsigned sign_blocks(const CommonArgs &c)
+{
+    const int npix = c.nx * c.nz;
+    const int b = (npix + 4 * SIGN_BLOCK - 1) / (4 * SIGN_BLOCK);
+    return (unsigned)(b < 1 ? 1 : (b > 512 ? 512 : b));
+}
+
+cudaError_t launch_sign_check(const WalkArgs &a, cudaStream_t st)
+{
+    sign_check_kernel<<<sign_blocks(a.c), SIGN_BLOCK, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 // Persistent grid: SMs x CTAs per SM (occupancy, or the caller's choice),
 // capped at what `work_warps` warps of work can use.
 template <class Kern>
@@ -1870,14 +1971,10 @@ cudaError_t launch_grid_adjoint_one(const GridAdjArgs &a, int rows, double *valu
 }
 }  // namespace
 
-cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, cudaStream_t st)
+namespace {
+cudaError_t launch_walk_kernel(const WalkArgs &a, bool trace, const LaunchCfg &cfg, bool smem_img, size_t smem,
+                               cudaStream_t st)
 {
-    WalkArgs a = a0;
-    LaunchCfg cfg = cfg0;
-    bool smem_img = false;
-    size_t smem = 0;
-    cudaError_t e = plan_image(a.c, cfg, &smem_img, &smem);
-    if (e != cudaSuccess) return e;
     switch (a.c.phase_kind * 4 + (smem_img ? 2 : 0) + (trace ? 1 : 0)) {
     case 0: return launch_one<MC_PHASE_TABLE, false, false>(a, cfg, smem, st);
     case 1: return launch_one<MC_PHASE_TABLE, false, true>(a, cfg, smem, st);
@@ -1894,15 +1991,24 @@ cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, c
     default: return cudaErrorInvalidValue;
     }
 }
+}  // namespace
 
-cudaError_t launch_grid(const GridArgs &a0, bool trace, const LaunchCfg &cfg0, cudaStream_t st)
+cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, cudaStream_t st)
 {
-    GridArgs a = a0;
+    WalkArgs a = a0;
     LaunchCfg cfg = cfg0;
     bool smem_img = false;
     size_t smem = 0;
     cudaError_t e = plan_image(a.c, cfg, &smem_img, &smem);
     if (e != cudaSuccess) return e;
+    if ((e = launch_walk_kernel(a, trace, cfg, smem_img, smem, st)) != cudaSuccess) return e;
+    return launch_sign_check(a, st);
+}
+
+namespace {
+cudaError_t launch_grid_kernel(const GridArgs &a, bool trace, const LaunchCfg &cfg, bool smem_img, size_t smem,
+                               cudaStream_t st)
+{
     switch (a.c.phase_kind * 4 + (smem_img ? 2 : 0) + (trace ? 1 : 0)) {
     case 0: return launch_grid_one<MC_PHASE_TABLE, false, false>(a, cfg, smem, st);
     case 1: return launch_grid_one<MC_PHASE_TABLE, false, true>(a, cfg, smem, st);
@@ -1918,6 +2024,23 @@ cudaError_t launch_grid(const GridArgs &a0, bool trace, const LaunchCfg &cfg0, c
     case 11: return launch_grid_one<MC_PHASE_PAPER, true, true>(a, cfg, smem, st);
     default: return cudaErrorInvalidValue;
     }
+}
+}  // namespace
+
+cudaError_t launch_grid(const GridArgs &a0, bool trace, const LaunchCfg &cfg0, cudaStream_t st)
+{
+    GridArgs a = a0;
+    LaunchCfg cfg = cfg0;
+    bool smem_img = false;
+    size_t smem = 0;
+    cudaError_t e = plan_image(a.c, cfg, &smem_img, &smem);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_grid_kernel(a, trace, cfg, smem_img, smem, st)) != cudaSuccess) return e;
+    WalkArgs w;
+    w.c = a.c;
+    w.m = a.m;
+    w.counter = a.counter;
+    return launch_sign_check(w, st);
 }
 
 int grid_adjoint_max_grid()
@@ -1948,14 +2071,17 @@ cudaError_t launch_batch(const BatchArgs &a0, const LaunchCfg &cfg0, cudaStream_
     cudaError_t e = plan_image(a.c, cfg, &smem_img, &smem);
     if (e != cudaSuccess) return e;
     switch (a.c.phase_kind * 2 + (smem_img ? 1 : 0)) {
-    case 0: return launch_batch_one<MC_PHASE_TABLE, false>(a, cfg, smem, st);
-    case 1: return launch_batch_one<MC_PHASE_TABLE, true>(a, cfg, smem, st);
-    case 2: return launch_batch_one<MC_PHASE_HG, false>(a, cfg, smem, st);
-    case 3: return launch_batch_one<MC_PHASE_HG, true>(a, cfg, smem, st);
-    case 4: return launch_batch_one<MC_PHASE_PAPER, false>(a, cfg, smem, st);
-    case 5: return launch_batch_one<MC_PHASE_PAPER, true>(a, cfg, smem, st);
+    case 0: e = launch_batch_one<MC_PHASE_TABLE, false>(a, cfg, smem, st); break;
+    case 1: e = launch_batch_one<MC_PHASE_TABLE, true>(a, cfg, smem, st); break;
+    case 2: e = launch_batch_one<MC_PHASE_HG, false>(a, cfg, smem, st); break;
+    case 3: e = launch_batch_one<MC_PHASE_HG, true>(a, cfg, smem, st); break;
+    case 4: e = launch_batch_one<MC_PHASE_PAPER, false>(a, cfg, smem, st); break;
+    case 5: e = launch_batch_one<MC_PHASE_PAPER, true>(a, cfg, smem, st); break;
     default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
+    batch_sign_check_kernel<<<dim3(sign_blocks(a.c), (unsigned)a.n_media), SIGN_BLOCK, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 int adjoint_max_grid()

@@ -162,9 +162,17 @@ class Medium:
 
     @classmethod
     def from_optical_depth(cls, table, tau, length_mm=45.0, mu_a_medium=0.0, phase="table", hg_g=None):
-        """Number density giving optical depth tau over length_mm (Eq. 17)."""
-        n = tau / (table.info["sigma_ext_mm2"] * length_mm)
-        return cls.from_density(table, n, mu_a_medium, phase, hg_g)
+        """Number density giving optical depth tau over length_mm (Eq. 17,
+        mc_medium_from_optical_depth)."""
+        info = N.MieInfo(**{k: table.info[k] for k, _ in N.MieInfo._fields_})
+        m = N.Medium()
+        nd = C.c_double(0.0)
+        N.check("mc_medium_from_optical_depth", N.lib().mc_medium_from_optical_depth(
+            C.byref(info), float(tau), float(length_mm), float(mu_a_medium), C.byref(m), C.byref(nd)))
+        g = table.info["g"] if hg_g is None else hg_g
+        med = cls(m.mu_s, m.mu_a, phase, g, table)
+        med.number_density = nd.value
+        return med
 
     def as_c(self, device=None):
         m = N.Medium()
@@ -223,8 +231,14 @@ def wait_selftest(tries=4096, device=None, stream=None):
     return N.lib().mc_check(C.c_void_p(err.data_ptr()), _stream_handle(stream))
 
 
+def auto_frac_bits(n_photons):
+    """Image fraction bits the library picks for a photon budget
+    (mc_auto_frac_bits): 32 up to 2^22 photons, 27 at 1e8, 24 at 1e9."""
+    return int(N.lib().mc_auto_frac_bits(int(n_photons)))
+
+
 def run_params(n_photons, seed=1, photon_offset=0, rr_threshold=1e-4, rr_survival=0.1,
-               max_events=1_000_000, max_scatter=0, image_frac_bits=32, accumulate=False,
+               max_events=1_000_000, max_scatter=0, image_frac_bits=0, accumulate=False,
                block_size=0, blocks_per_sm=0, image_mode=0):
     return N.RunParams(int(n_photons), int(photon_offset), int(seed), rr_threshold, rr_survival,
                        int(max_events), int(max_scatter), int(image_frac_bits), int(bool(accumulate)),
@@ -286,6 +300,16 @@ class Engine:
         self.error = torch.zeros(1, dtype=torch.int32, device=dev)
         self.work = torch.zeros(wb, dtype=torch.uint8, device=dev)
         self.image_frac_bits = 32
+        self.last_error = 0
+
+    def _frac_bits(self, n_photons, kw):
+        """kw with an explicit image_frac_bits: the caller's, else the one of
+        the tallies being added to (accumulate), else the budget's own."""
+        f = kw.get("image_frac_bits")
+        if not f:
+            f = self.image_frac_bits if kw.get("accumulate") else auto_frac_bits(n_photons)
+        self.image_frac_bits = int(f)
+        return dict(kw, image_frac_bits=int(f))
 
     def _tallies(self):
         return N.Tallies(self.image.data_ptr(), self.radial.data_ptr(), self.totals.data_ptr(),
@@ -295,8 +319,7 @@ class Engine:
         """Queue photons on the stream (asynchronous). Without accumulate=True
         the tallies start afresh; check() reports the device flags raised
         since the previous check."""
-        rp = run_params(n_photons, seed, **kw)
-        self.image_frac_bits = rp.image_frac_bits
+        rp = run_params(n_photons, seed, **self._frac_bits(n_photons, kw))
         m, keep = medium.as_c(self.device)
         g, c, t = self.geometry.as_c(), self.camera.as_c(), self._tallies()
         N.check("mc_run", N.lib().mc_run(C.byref(m), C.byref(g), C.byref(c), C.byref(rp), C.byref(t),
@@ -308,8 +331,7 @@ class Engine:
         """Run with a per-event trace of the first n_trace photons; returns
         an int32 tensor [n_trace, n_events, 12] (float fields bit-cast)."""
         torch = _torch()
-        rp = run_params(n_photons, seed, **kw)
-        self.image_frac_bits = rp.image_frac_bits
+        rp = run_params(n_photons, seed, **self._frac_bits(n_photons, kw))
         m, keep = medium.as_c(self.device)
         buf = torch.empty((n_trace, n_events, N.TRACE_WORDS), dtype=torch.int32, device=self.device)
         g, c, t = self.geometry.as_c(), self.camera.as_c(), self._tallies()
@@ -349,8 +371,7 @@ class Engine:
         whose phase function is used (its mu_s, mu_a are ignored). With
         n_trace > 0 returns the raw trace of real events (decode_trace)."""
         torch = _torch()
-        rp = run_params(n_photons, seed, **kw)
-        self.image_frac_bits = rp.image_frac_bits
+        rp = run_params(n_photons, seed, **self._frac_bits(n_photons, kw))
         m, keep = phase.as_c(self.device)
         m.mu_s, m.mu_a = 1.0, 0.0
         g, geo, c, t = grid.as_c(), self.geometry.as_c(), self.camera.as_c(), self._tallies()
@@ -395,8 +416,10 @@ class Engine:
 
     def check(self, stream=None):
         """Wait for the stream and raise if a kernel flagged an error since
-        the previous check; the flags are cleared either way."""
+        the previous check; the flags are cleared either way. The word read
+        is kept as last_error (0 when nothing was flagged)."""
         st = N.lib().mc_check(C.c_void_p(self.error.data_ptr()), _stream_handle(stream))
+        self.last_error = int(self.error.cpu().numpy()[0]) & 0xFFFFFFFF
         _clear_error(self.error, stream)
         N.check("mc_check", st)
 
@@ -408,6 +431,7 @@ class Engine:
                                      float(timeout_ms))
         if st == N.MC_NOT_READY:
             return False
+        self.last_error = int(self.error.cpu().numpy()[0]) & 0xFFFFFFFF
         _clear_error(self.error, stream)
         N.check("mc_check_within", st)
         return True
@@ -453,8 +477,11 @@ class Batch:
             raise ValueError("batch holds %d media, got %d" % (self.n, n))
         as_list = lambda v: list(v) if isinstance(v, (list, tuple)) else [v] * n
         nph, sd, off = as_list(n_photons), as_list(seeds), as_list(offsets)
-        rp = run_params(0, 0, **kw)
-        self.image_frac_bits = rp.image_frac_bits
+        f = kw.get("image_frac_bits")
+        if not f:
+            f = self.image_frac_bits if kw.get("accumulate") else auto_frac_bits(max(int(v) for v in nph))
+        self.image_frac_bits = int(f)
+        rp = run_params(0, 0, **dict(kw, image_frac_bits=int(f)))
         arr = (N.Instance * n)()
         keep = []
         for i, med in enumerate(media):

@@ -26,8 +26,10 @@ def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL, nee_slope=None):
     event times that slope. Returns dict(n, matched, flips, bad, worst...)."""
     n, ev = o.shape[0], o.shape[1]
     st_o = o[..., 0].astype(int)
-    worst = dict(pos=0.0, dir=0.0, w=0.0, nee=0.0)
-    bad, flips, checked_events = [], 0, 0
+    # nee_net: the camera term's deviation beyond what the position (and,
+    # with nee_slope, the direction) deviations carry into it
+    worst = dict(pos=0.0, dir=0.0, w=0.0, nee=0.0, nee_net=0.0)
+    bad, causes, flips, checked_events = [], [], 0, 0
     for p in range(n):
         ok = True
         muc, ddir_prev = 0.0, 0.0     # direction before the first collision is +x
@@ -44,6 +46,8 @@ def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL, nee_slope=None):
                     flips += 1
                     break
                 ok = False
+                causes.append((p, e, "discrete (status, pixel, bin, radial) %s vs oracle %s, margin %.3g"
+                               % (disc_g, disc_o, margin)))
                 break
             if so == 6:
                 break
@@ -61,18 +65,21 @@ def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL, nee_slope=None):
             worst["dir"] = max(worst["dir"], ddir)
             worst["w"] = max(worst["w"], dw)
             worst["nee"] = max(worst["nee"], dnee)
+            worst["nee_net"] = max(worst["nee_net"], dnee - (nee_tol - tol))
             if dpos > tol * lx or ddir > tol or dw > tol or dnee > nee_tol:
                 if margin < tol:
                     flips += 1
                     break
                 ok = False
+                causes.append((p, e, "position %.3g mm, direction %.3g, weight %.3g, camera %.3g (allowed %.3g), "
+                               "margin %.3g" % (dpos, ddir, dw, dnee, nee_tol, margin)))
                 break
             if so != 0:
                 break
             muc, ddir_prev = float(rec[5]), ddir
         if not ok:
             bad.append(p)
-    return dict(n=n, matched=n - len(bad), flips=flips, bad=bad[:20], worst=worst,
+    return dict(n=n, matched=n - len(bad), flips=flips, bad=bad[:20], causes=causes, worst=worst,
                 events=checked_events)
 
 
@@ -116,6 +123,11 @@ def gpu_batches(gpu, med, n, batches, camera, geometry, offset=0, seed=1, **kw):
     """Run photons [offset, offset + n) as `batches` separate launches and
     return the summed result plus the batch-means variance of the image sum
     (the engine keeps integer sums only, so its spread comes from batches)."""
+    # one image scale for every batch: the whole budget's (as one launch of
+    # all n photons would use), so the integer sums add up exactly
+    kw = dict(kw)
+    if not kw.get("image_frac_bits"):
+        kw["image_frac_bits"] = gpu.auto_frac_bits(n)
     imgs, tot, steps = [], None, 0
     raw_img = None
     edges = [offset + (n * k) // batches for k in range(batches + 1)]

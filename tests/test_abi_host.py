@@ -174,3 +174,84 @@ def test_peaks_library_exports(eng):
     assert hasattr(L, "mc_peak_run")
     L.mc_peak_run.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     assert L.mc_peak_run(0, 0, 256, 10, None, None, None) == -1   # rejected before any launch
+
+
+def test_static_entry_rejects_an_invalid_camera_before_any_device_call(eng):
+    """mc_run_static sizes its scratch from the camera; an invalid camera has
+    no workspace size and is MC_ERR_ARG, decided on the host."""
+    from paper_2507_23189_gb300 import _native as N
+    import paper_2507_23189_gb300 as E
+    L = N.lib()
+    med = N.Medium()
+    med.mu_s, med.phase_kind, med.hg_g = 0.1, N.PHASE_HG, 0.5
+    geo = E.Geometry().as_c()
+    rp = E.run_params(100)
+    for cam in (N.Camera(0, 64, 128, 7.0), N.Camera(64, 64, 0, 7.0), N.Camera(64, 64, 128, -1.0)):
+        assert L.mc_workspace_bytes(C.byref(cam)) == 0
+        st = L.mc_run_static(C.byref(med), C.byref(geo), C.byref(cam), C.byref(rp),
+                             None, None, None, None, None)
+        assert st == -1, N.STATUS.get(st)
+    # every valid camera's workspace fits the static array with room to spare
+    for nx, nz, nr in ((1, 1, 1), (8192, 8192, 65536)):
+        assert 0 < L.mc_workspace_bytes(C.byref(N.Camera(nx, nz, nr, 7.0))) <= 4096
+
+
+def test_eq17_solved_for_the_number_density_in_c(eng):
+    """mc_medium_from_optical_depth: OD = n sigma_e L (Eq. 17) with the
+    paper's sigma_e = 4.42e-5 mm^2 for the 5 um spheres at 532 nm."""
+    from paper_2507_23189_gb300 import _native as N
+    L = N.lib()
+    info = N.MieInfo(sigma_ext_mm2=4.42e-5, sigma_sca_mm2=4.0e-5, sigma_abs_mm2=0.42e-5)
+    out, nd = N.Medium(), C.c_double(0.0)
+    assert L.mc_medium_from_optical_depth(C.byref(info), 5.0, 45.0, 0.001, C.byref(out), C.byref(nd)) == 0
+    assert nd.value == pytest.approx(5.0 / (4.42e-5 * 45.0), rel=1e-15)
+    assert nd.value == pytest.approx(2513.8260432378, rel=1e-12)
+    assert out.mu_s == pytest.approx(nd.value * 4.0e-5, rel=1e-15)
+    assert out.mu_a == pytest.approx(nd.value * 0.42e-5 + 0.001, rel=1e-15)
+    assert (out.mu_s + out.mu_a - 0.001) * 45.0 == pytest.approx(5.0, rel=1e-14)
+    assert L.mc_medium_from_optical_depth(C.byref(info), 5.0, 45.0, 0.0, C.byref(out), None) == 0
+    for tau, length, sig in ((-1.0, 45.0, 4.42e-5), (5.0, 0.0, 4.42e-5), (float("nan"), 45.0, 4.42e-5),
+                             (5.0, float("inf"), 4.42e-5), (5.0, 45.0, 0.0)):
+        bad = N.MieInfo(sigma_ext_mm2=sig, sigma_sca_mm2=sig)
+        assert L.mc_medium_from_optical_depth(C.byref(bad), tau, length, 0.0, C.byref(out), None) == -1
+    assert L.mc_medium_from_optical_depth(None, 5.0, 45.0, 0.0, C.byref(out), None) == -1
+
+
+def test_auto_image_fraction_bits(eng):
+    """F = min(32, 54 - ceil(log2 n)), at least 8: 24 at 1e9 photons."""
+    L = eng.lib()
+    want = {0: 32, 1: 32, 1 << 22: 32, (1 << 22) + 1: 31, 10 ** 8: 27, 10 ** 9: 24, 1 << 31: 23,
+            1 << 46: 8, 1 << 63: 8}
+    for n, f in want.items():
+        assert L.mc_auto_frac_bits(n) == f, n
+        assert eng.auto_frac_bits(n) == f
+    for n in (3, 1000, 10 ** 6, 5 * 10 ** 7, 3 * 10 ** 9):
+        f = L.mc_auto_frac_bits(n)
+        # n photons at one weight unit each in one pixel stay 2^9 below 2^63
+        assert f == 32 or (n * 2.0 ** f <= 2.0 ** 54 < n * 2.0 ** (f + 1))
+
+
+def test_photon_cap_and_automatic_fraction_bits_are_checked_on_the_host(eng):
+    """More than 2^31 photons in one call (the 2^-32-unit totals could pass
+    2^63), or an automatic F while accumulating (the image being added to
+    has its own F), is MC_ERR_ARG; the controls pass every argument check and
+    stop at the too-small workspace (MC_ERR_NOMEM), before any CUDA call."""
+    from paper_2507_23189_gb300 import _native as N
+    L = N.lib()
+    buf = (C.c_uint64 * 64)()
+    p = C.addressof(buf) + (-C.addressof(buf)) % 16
+    med = N.Medium(0.1, 0.0, N.PHASE_HG, 0.5, None, 0)
+    geo = N.Geometry(45.0, 10.0, 10.0, 0.0)
+    cam = N.Camera(64, 64, 128, 7.0)
+    tal = N.Tallies(p, p, p, p, p, 0)
+
+    def run(n, frac, acc):
+        rp = N.RunParams(n, 0, 1, 1e-4, 0.1, 1000, 0, frac, acc, 0, 0, 0)
+        return L.mc_run(C.byref(med), C.byref(geo), C.byref(cam), C.byref(rp), C.byref(tal), None)
+
+    assert run(1 << 31, 32, 0) == -3
+    assert run((1 << 31) + 1, 32, 0) == -1
+    assert run(1000, 0, 0) == -3
+    assert run(1000, 0, 1) == -1
+    assert run(1000, 32, 1) == -3
+    assert run(1000, 7, 0) == -1 and run(1000, 49, 0) == -1

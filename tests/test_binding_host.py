@@ -87,6 +87,9 @@ def test_check_reports_then_clears_the_flags_on_the_checked_stream(monkeypatch):
             log.append(("zero",))
             self.v = 0
 
+        def cpu(self):
+            return types.SimpleNamespace(numpy=lambda: np.array([self.v], dtype=np.int32))
+
     status = {"check": 0, "within": 0}
     fake_lib = types.SimpleNamespace(
         mc_check=lambda ptr, st: (log.append(("mc_check", st)), status["check"])[1],
@@ -104,6 +107,7 @@ def test_check_reports_then_clears_the_flags_on_the_checked_stream(monkeypatch):
     with pytest.raises(N.McError) as err:
         e.check(None)
     assert err.value.status == -7 and e.error.v == 0
+    assert e.last_error == N.EFLAG_EVENTS          # the word read before it was cleared
     assert log[1] == ("enter", ("current", "cpu")) and ("zero",) in log
 
     log.clear()

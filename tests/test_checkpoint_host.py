@@ -122,3 +122,15 @@ def test_image_sigma_is_the_batch_means_error(gpu_mod, tmp_path):
     one = run_resumable(FakeEngine(gpu_mod), med, n, str(tmp_path / "one.npz"), chunk=n, seed=5)
     assert one["image_sigma"] is None
 
+
+
+def test_run_record_logs_the_word_the_last_check_read(gpu_mod):
+    """The record's error field is the word Engine.check() read before it
+    cleared it (not the cleared device word)."""
+    from paper_2507_23189_gb300.checkpoint import run_record
+    med = gpu_mod.Medium(0.1, 0.0, "hg", 0.8, None)
+    e = FakeEngine(gpu_mod)
+    e.run(med, 100, accumulate=True)
+    assert run_record(e, med, 100, 1.0)["error"] == 0
+    e.last_error = 0x1          # MC_EFLAG_EVENTS seen by the last check
+    assert run_record(e, med, 100, 1.0)["error"] == 1

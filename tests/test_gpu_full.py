@@ -85,10 +85,12 @@ def test_sweep_point(gpu, oracle_mod, ps_table, ps_oracle_table, g_or, tau, phas
 def test_split_ranges_bit_identical(gpu, ps_table):
     med = gpu.Medium(5 / LX, 0.0, "table", 0.0, ps_table)
     cam = gpu.Camera(256, 256, 128, R_MAX)
+    f = gpu.auto_frac_bits(N_FULL)       # the scale one launch of all photons uses
     a = gpu.Engine(cam, gpu.Geometry(LX, LY, LZ))
     a.run(med, N_FULL, seed=1)
+    assert a.image_frac_bits == f == 27
     b = gpu.Engine(cam, gpu.Geometry(LX, LY, LZ))
-    b.run(med, 33_333_333, seed=1)
+    b.run(med, 33_333_333, seed=1, image_frac_bits=f)
     b.run(med, N_FULL - 33_333_333, seed=1, photon_offset=33_333_333, accumulate=True)
     a.check()
     b.check()

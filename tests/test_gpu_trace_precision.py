@@ -1,0 +1,92 @@
+"""The precision contract of the walk: the first 32 events of every photon
+against the double-precision oracle within 1e-5 (positions relative to the
+cuvette length, directions absolutely, weights and camera terms
+relatively), for every optical depth of the sweep, Mie table and H-G.
+
+Two builds run the same 4096-photon traces:
+  * the production library (hardware log / exp / sin / cos / rsqrt /
+    reciprocal approximations, explicit fmaf, no contraction);
+  * the IEEE-strict library (MC_STRICT: CUDA's accurate logf / expf /
+    exp2f / sincosf, correctly rounded division and square root).
+In both, every photon must match: a discrete decision (wall, exit face,
+pixel, table bin, roulette) may differ only where the oracle's branch
+quantity lies within 1e-5 of its threshold, which ends the comparison of
+that photon. Each case prints the worst deviation per field, and the worst
+deviations are asserted below bounds well inside the 1e-5 contract."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from parity import compare_traces
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, os.path.join(ROOT, "tests"))
+import strict_traces as ST   # noqa: E402
+
+# worst deviation per field allowed over all cases, per build: positions
+# (relative to the cuvette length), directions, weights, and the camera term
+# net of the part its position and direction deviations carry into it
+# (nee_net); the measured worst values are in the printed table
+BOUNDS = {"production": dict(pos=5e-6, dir=5e-6, w=1e-6, nee_net=1e-5),
+          "strict": dict(pos=5e-6, dir=5e-6, w=1e-6, nee_net=1e-5)}
+
+
+def _hg_slope(g):
+    """|d log p / d mu| of the H-G density (Eq. 11): 3 g / (1 + g^2 - 2 g mu),
+    which carries a direction deviation into the camera term."""
+    return lambda mu: 3.0 * abs(g) / (1.0 + g * g - 2.0 * g * mu)
+
+
+def _traces(tmp_path, strict):
+    from paper_2507_23189_gb300 import build
+    build.build()
+    if strict:
+        build.build_strict()
+    env = dict(os.environ)
+    env.pop("MC_STRICT", None)
+    env.pop("MC_CHECKED", None)
+    if strict:
+        env["MC_STRICT"] = "1"
+    out = str(tmp_path / ("strict.npz" if strict else "production.npz"))
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "strict_traces.py"), out], env=env,
+                       capture_output=True, text=True, timeout=900)
+    assert p.returncode == 0, p.stderr[-3000:]
+    z = np.load(out)
+    assert str(z["library"]) == ("libmcmie_strict.so" if strict else "libmcmie.so")
+    return z
+
+
+@pytest.mark.parametrize("build_kind", ["production", "strict"])
+def test_first_32_events_every_photon(gpu, oracle_mod, ps_oracle_table, tmp_path, build_kind):
+    z = _traces(tmp_path, build_kind == "strict")
+    x = oracle_mod.size_parameter(5.0, 1.33, 532.0)
+    g_or = oracle_mod.mie_efficiencies(complex(1.59 / 1.33, 0.0), x)[2]
+    worst_all = dict(pos=0.0, dir=0.0, w=0.0, nee=0.0, nee_net=0.0)
+    rows, failed = [], []
+    for name, phase, tau, mu_a, kw in ST.CASES:
+        tr = gpu.decode_trace(z[name])
+        om = dict(phase="mie", table=ps_oracle_table) if phase == "table" else dict(phase="hg", hg_g=g_or)
+        o = oracle_mod.walk(mu_s=tau / ST.LX - mu_a, mu_a=mu_a, n_photons=ST.N_TRACE, nx=64, nz=64, seed=11,
+                            n_trace=ST.N_TRACE, n_trace_events=32, **om, **kw)
+        slope = _hg_slope(g_or) if phase == "hg" else None
+        cmp = compare_traces(tr, o["trace"], mu_ext=tau / ST.LX, nee_slope=slope)
+        w_ = cmp["worst"]
+        rows.append("%-10s %-18s matched %4d/%d flips %3d events %6d  worst pos %.2e dir %.2e w %.2e cam %.2e "
+                    "(net %.2e)" % (build_kind, name, cmp["matched"], cmp["n"], cmp["flips"], cmp["events"],
+                                    w_["pos"], w_["dir"], w_["w"], w_["nee"], w_["nee_net"]))
+        for c in cmp["causes"]:
+            rows.append("    unmatched photon %d event %d: %s" % c)
+        for k in worst_all:
+            worst_all[k] = max(worst_all[k], w_[k])
+        if cmp["matched"] != cmp["n"] or cmp["events"] <= 1.2 * cmp["n"] or cmp["flips"] > 0.002 * cmp["n"]:
+            failed.append(name)
+    print("\n" + "\n".join(rows))
+    print("%s worst over all cases: %s" % (build_kind, {k: "%.2e" % v for k, v in worst_all.items()}))
+    assert not failed, failed
+    for k, b in BOUNDS[build_kind].items():
+        assert worst_all[k] <= b, (k, worst_all[k], b)
