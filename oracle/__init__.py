@@ -66,6 +66,10 @@ def lib():
         L.oracle_hat_integrals.argtypes = [dp, C.c_int, C.c_int, dp]
         L.oracle_adjoint.restype = C.c_int
         L.oracle_adjoint.argtypes = [C.POINTER(WalkCfg), dp, C.c_int, dp, dp, dp]
+        L.oracle_adjoint_weighted.restype = C.c_int
+        L.oracle_adjoint_weighted.argtypes = [C.POINTER(WalkCfg), dp, C.c_int, dp, dp, dp, dp, dp]
+        L.oracle_phase_table_reweighted.restype = C.c_int
+        L.oracle_phase_table_reweighted.argtypes = [dp, C.c_int, C.c_int, dp, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -208,6 +212,21 @@ def phase_table_weighted(m, x, w, n_bins=4096, n_fine=1 << 18):
                 n_fine=int(diag[3]))
 
 
+def phase_table_reweighted(table, w):
+    """The table's own (piecewise-constant) density times h_w = sum_k w_k
+    phi_k, renormalised and inverted at the same number of equal-probability
+    levels: the phase function p_w = p h_w / Z(w) the phase-weight gradients
+    refer to. Returns dict(icdf, omu, pdf, z) with z = Z(w)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    base = np.ascontiguousarray(table["omu"], dtype=np.float64)
+    n = base.size - 1
+    icdf, omu, pdf, z = np.zeros(n + 1), np.zeros(n + 1), np.zeros(n), C.c_double(0.0)
+    if lib().oracle_phase_table_reweighted(_dp(base), n, w.size, _dp(w), _dp(icdf), _dp(omu), _dp(pdf),
+                                           C.byref(z)):
+        raise ValueError("oracle_phase_table_reweighted: bad arguments")
+    return dict(icdf=icdf, omu=omu, pdf=pdf, z=z.value, mean=float(np.mean(1.0 - 0.5 * (omu[:-1] + omu[1:]))))
+
+
 def phase_table_mixture(components, weights, n_bins=4096, n_fine=1 << 18):
     """Table of a phase-function mixture. components: list of ("mie", m, x)
     or ("hg", g); weights: each component's share of the scattering
@@ -271,10 +290,11 @@ def hat(n_w, k, mu):
     return lib().oracle_hat(n_w, k, mu)
 
 
-def adjoint(adj, n_w=64, **walk_kw):
-    """Gradient of sum(adj * image) w.r.t. (mu_s, mu_a, w_0..w_{n_w-1}) at
-    w = 1: dict(grad, grad_sq (per-photon squares), value). Same keywords as
-    walk()."""
+def adjoint(adj, n_w=64, w=None, base_table=None, **walk_kw):
+    """Gradient of sum(adj * image) w.r.t. (mu_s, mu_a, w_0..w_{n_w-1}):
+    dict(grad, grad_sq (per-photon squares), value). Same keywords as walk().
+    At w = 1 (w None) the walk's table is the phase function itself; at other
+    weights walk_kw["table"] is phase_table_reweighted(base_table, w)."""
     cfg, keep = _walk_cfg(**walk_kw)
     a = np.ascontiguousarray(adj, dtype=np.float64).ravel()
     if a.size != cfg.nx * cfg.nz:
@@ -282,7 +302,16 @@ def adjoint(adj, n_w=64, **walk_kw):
     g = np.zeros(2 + n_w)
     g2 = np.zeros(2 + n_w)
     v = C.c_double(0.0)
-    if lib().oracle_adjoint(C.byref(cfg), _dp(a), n_w, _dp(g), _dp(g2), C.byref(v)):
+    if w is None:
+        rc = lib().oracle_adjoint(C.byref(cfg), _dp(a), n_w, _dp(g), _dp(g2), C.byref(v))
+    else:
+        wv = np.ascontiguousarray(w, dtype=np.float64)
+        base = np.ascontiguousarray(base_table["omu"], dtype=np.float64)
+        if wv.size != n_w or base.size != cfg.n_bins + 1:
+            raise ValueError("weights or base table of the wrong size")
+        rc = lib().oracle_adjoint_weighted(C.byref(cfg), _dp(a), n_w, _dp(wv), _dp(base), _dp(g), _dp(g2),
+                                           C.byref(v))
+    if rc:
         raise ValueError("oracle_adjoint: bad arguments")
     return dict(grad=g, grad_sq=g2, value=v.value, n_photons=cfg.n_photons)
 

@@ -14,8 +14,12 @@
  *   flight i:  d/dmu_s = d/dmu_a = 1/mu_ext - s_i
  *   W_j:       d/dmu_s = j (1/mu_s - 1/mu_ext),  d/dmu_a = -j/mu_ext
  *   transport: d/dmu_s = d/dmu_a = -l_j
- *   phase weights at w = 1: d log p_w(mu)/dw_k = phi_k(mu) - Z_k, both for the
- *   sampled angles mu_i (i < j) and for the camera density at mu_c,j.
+ *   phase weights: p_w = p h_w / Z(w), h_w = sum_k w_k phi_k, Z_k = int p phi_k
+ *   over the unweighted table p and Z(w) = sum_k w_k Z_k, so
+ *   d log p_w(mu)/dw_k = phi_k(mu) / h_w(mu) - Z_k / Z(w) (at w = 1:
+ *   phi_k(mu) - Z_k), both for the sampled angles mu_i (i < j) and for the
+ *   camera density at mu_c,j. The walk samples p_w through its table, the
+ *   unweighted table reweighted (oracle_phase_table_reweighted).
  * Flights that leave the cuvette carry no camera term and later terms of
  * the same photon do not depend on them. Each photon's path is simply
  * stored and summed afterwards.
@@ -206,12 +210,21 @@ static void replay(const oracle_walk_cfg *c, uint64_t p, const double *adj, rec_
 
 typedef struct {
     const oracle_walk_cfg *c;
-    const double *adj, *z;
+    const double *adj, *z, *w;   /* z: Z_k / Z(w); w: the weights */
     int n_w;
     uint64_t first, count;
     double *g, *g2;   /* [2 + n_w] */
     double value;
 } ajob_t;
+
+/* h_w(mu) = sum_k w_k phi_k(mu) */
+static double h_w(int n_w, const double *w, double mu)
+{
+    double s = 0.0;
+    for (int k = 0; k < n_w; ++k)
+        s += w[k] * oracle_hat(n_w, k, mu);
+    return s;
+}
 
 static void *adj_worker(void *arg)
 {
@@ -230,9 +243,9 @@ static void *adj_worker(void *arg)
             pg[0] += A * (R.S[j] + jj * (1.0 / c->mu_s - 1.0 / mu_ext) - R.l[j]);
             pg[1] += A * (R.S[j] - jj / mu_ext - R.l[j]);
             for (int q = 0; q < J->n_w; ++q) {
-                double t = oracle_hat(J->n_w, q, R.muc[j]) - jj * J->z[q];
+                double t = oracle_hat(J->n_w, q, R.muc[j]) / h_w(J->n_w, J->w, R.muc[j]) - jj * J->z[q];
                 for (int i = 0; i < j; ++i)
-                    t += oracle_hat(J->n_w, q, R.mus[i]);
+                    t += oracle_hat(J->n_w, q, R.mus[i]) / h_w(J->n_w, J->w, R.mus[i]);
                 pg[2 + q] += A * t;
             }
         }
@@ -249,15 +262,38 @@ static void *adj_worker(void *arg)
 int oracle_adjoint(const oracle_walk_cfg *c, const double *adj, int n_w, double *grad, double *grad_sq,
                    double *value)
 {
+    return oracle_adjoint_weighted(c, adj, n_w, NULL, NULL, grad, grad_sq, value);
+}
+
+int oracle_adjoint_weighted(const oracle_walk_cfg *c, const double *adj, int n_w, const double *w,
+                            const double *base_omu, double *grad, double *grad_sq, double *value)
+{
     if (!c || !adj || !grad || !grad_sq || !value || n_w < 0 || n_w == 1 || !(c->mu_s > 0) || c->mu_a < 0)
         return -1;
     if (n_w > 0 && c->phase_kind != ORACLE_PHASE_MIE)
         return -1;
     if (c->phase_kind == ORACLE_PHASE_MIE && (!c->icdf || !c->omu))
         return -1;
+    if (w && !base_omu)
+        return -1;
     double *z = calloc((size_t)(n_w > 0 ? n_w : 1), sizeof(double));
-    if (n_w > 0)
-        oracle_hat_integrals(c->omu, c->n_bins, n_w, z);
+    double *ws = malloc((size_t)(n_w > 0 ? n_w : 1) * sizeof(double));
+    for (int k = 0; k < n_w; ++k) {
+        ws[k] = w ? w[k] : 1.0;
+        if (!(ws[k] > 0.0)) {
+            free(z); free(ws);
+            return -1;
+        }
+    }
+    if (n_w > 0) {
+        /* Z_k over the unweighted table, then Z_k / Z(w) */
+        oracle_hat_integrals(base_omu ? base_omu : c->omu, c->n_bins, n_w, z);
+        double zw = 0.0;
+        for (int k = 0; k < n_w; ++k)
+            zw += ws[k] * z[k];
+        for (int k = 0; k < n_w; ++k)
+            z[k] /= zw;
+    }
     int T = c->n_threads > 0 ? c->n_threads : 1;
     if ((uint64_t)T > c->n_photons && c->n_photons > 0) T = (int)c->n_photons;
     if (T < 1) T = 1;
@@ -267,6 +303,7 @@ int oracle_adjoint(const oracle_walk_cfg *c, const double *adj, int n_w, double 
         jobs[t].c = c;
         jobs[t].adj = adj;
         jobs[t].z = z;
+        jobs[t].w = ws;
         jobs[t].n_w = n_w;
         jobs[t].first = c->n_photons * (uint64_t)t / (uint64_t)T;
         jobs[t].count = c->n_photons * (uint64_t)(t + 1) / (uint64_t)T - jobs[t].first;
@@ -287,6 +324,7 @@ int oracle_adjoint(const oracle_walk_cfg *c, const double *adj, int n_w, double 
     free(jobs);
     free(th);
     free(z);
+    free(ws);
     return 0;
 }
 

@@ -101,6 +101,16 @@ int oracle_phase_table_weighted(int kind, double m_re, double m_im, double x,
                                 int n_fine, double *icdf, double *omu, double *pdf,
                                 double *diag);
 
+/* The table omu_base[n_bins + 1] (1 - cos theta at the levels, as
+ * oracle_phase_table writes it) reweighted: its own piecewise-constant
+ * density times h_w = sum_k w_k phi_k (n_w >= 2 hats of oracle_hat, every
+ * w_k > 0), renormalised and inverted at the equal-probability levels.
+ * Outputs icdf, omu [n_bins + 1] and pdf [n_bins] as oracle_phase_table
+ * (icdf, pdf may be NULL); *z_out (may be NULL) receives Z(w) = int p h_w.
+ * Returns 0, or -1 on bad arguments. */
+int oracle_phase_table_reweighted(const double *omu_base, int n_bins, int n_w, const double *w,
+                                  double *icdf, double *omu, double *pdf, double *z_out);
+
 /* Table of a mixture of n_comp phase functions (kind[i], m[i], x[i] or
  * hg_g[i]), component i weighted by w[i] >= 0 (its share n_i sigma_sca,i of
  * the scattering coefficient) after each is normalised (Eq. 10). Outputs
@@ -238,6 +248,15 @@ void oracle_hat_integrals(const double *omu, int n_bins, int n_w, double *z);
  * needs the table phase. Returns 0 or -1. */
 int oracle_adjoint(const oracle_walk_cfg *cfg, const double *adj, int n_w, double *grad,
                    double *grad_sq, double *value);
+
+/* oracle_adjoint at phase weights w[n_w] (all > 0; NULL: all 1): the walk's
+ * table (cfg) is the phase function p_w = p h_w / Z(w) as tabulated by
+ * oracle_phase_table_reweighted from the unweighted table base_omu[n_bins+1]
+ * (NULL: cfg's own table, only with w NULL), and the phase-weight scores
+ * are d log p_w / dw_k = phi_k / h_w - Z_k / Z(w), Z_k = int p phi_k over
+ * the unweighted table. */
+int oracle_adjoint_weighted(const oracle_walk_cfg *cfg, const double *adj, int n_w, const double *w,
+                            const double *base_omu, double *grad, double *grad_sq, double *value);
 
 /* Gradient of L = sum_pix adj[pix] image[pix] with respect to the voxel
  * densities of c->density (delta-tracking walk), from the oracle walk's own

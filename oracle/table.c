@@ -295,3 +295,95 @@ int oracle_paper_cdf(int kind, double m_re, double m_im, double x, double hg_g,
     cdf[n] = 1.0;
     return 0;
 }
+
+/*
+ * A tabulated phase function reweighted by hat-function weights: the
+ * phase-table weights that the camera-image gradient is taken with respect
+ * to. The table's own density p (pdf_j = (1/n) / (omu_j - omu_{j+1}) on bin j,
+ * cos theta in [1 - omu_j, 1 - omu_{j+1}]) times h_w(mu) = sum_k w_k phi_k(mu)
+ * is renormalised by Z(w) = int p h_w and inverted at the equal-probability
+ * levels i / n_bins. Steps, in that order:
+ *   1. the mass of each bin: p_j times the integral of h_w over the bin (h_w
+ *      is linear between the hat nodes, so trapezoids piece by piece are
+ *      exact);
+ *   2. the running sum of the masses; its total is Z(w);
+ *   3. for each level, the bin whose running sum brackets i Z(w) / n_bins,
+ *      and inside it the point where the partial mass reaches the level, by
+ *      bisection in 1 - cos theta.
+ */
+static double hw_at(int n_w, const double *w, double mu)
+{
+    /* only the two hats around mu are nonzero */
+    double t = (mu + 1.0) * 0.5 * (n_w - 1);
+    int k = (int)floor(t);
+    if (k < 0) k = 0;
+    if (k > n_w - 2) k = n_w - 2;
+    return w[k] * oracle_hat(n_w, k, mu) + w[k + 1] * oracle_hat(n_w, k + 1, mu);
+}
+
+/* integral of h_w d(mu) over cos theta in [1 - va, 1 - vb], va >= vb given
+ * in 1 - cos theta (the hat nodes sit at 1 - cos theta = 2 - 2k/(n_w - 1)) */
+static double hw_integral(int n_w, const double *w, double va, double vb)
+{
+    const double hh = 2.0 / (n_w - 1);
+    double s = 0.0, hi = va;
+    for (int k = 0; k < n_w; ++k) {
+        double vk = 2.0 - k * hh;
+        if (vk < hi && vk > vb) {
+            s += 0.5 * (hw_at(n_w, w, 1.0 - hi) + hw_at(n_w, w, 1.0 - vk)) * (hi - vk);
+            hi = vk;
+        }
+    }
+    s += 0.5 * (hw_at(n_w, w, 1.0 - hi) + hw_at(n_w, w, 1.0 - vb)) * (hi - vb);
+    return s;
+}
+
+int oracle_phase_table_reweighted(const double *omu_base, int n_bins, int n_w, const double *w,
+                                  double *icdf, double *omu, double *pdf, double *z_out)
+{
+    if (!omu_base || n_bins < 2 || n_w < 2 || !w || !omu)
+        return -1;
+    for (int k = 0; k < n_w; ++k)
+        if (!(w[k] > 0.0) || !isfinite(w[k]))
+            return -1;
+    double *cum = malloc((size_t)(n_bins + 1) * sizeof *cum);
+    double *p = malloc((size_t)n_bins * sizeof *p);
+    if (!cum || !p) {
+        free(cum); free(p);
+        return -1;
+    }
+    cum[0] = 0.0;
+    for (int j = 0; j < n_bins; ++j) {
+        p[j] = (1.0 / n_bins) / (omu_base[j] - omu_base[j + 1]);
+        cum[j + 1] = cum[j] + p[j] * hw_integral(n_w, w, omu_base[j], omu_base[j + 1]);
+    }
+    const double Z = cum[n_bins];
+    omu[0] = 2.0;
+    omu[n_bins] = 0.0;
+    int j = 0;
+    for (int i = 1; i < n_bins; ++i) {
+        double target = ((double)i / n_bins) * Z;   /* level i of the weighted mass */
+        while (j < n_bins - 1 && cum[j + 1] <= target)
+            ++j;
+        double want = target - cum[j];
+        double a = omu_base[j + 1], b = omu_base[j];   /* partial mass from b down to v */
+        for (int it = 0; it < 200; ++it) {
+            double v = 0.5 * (a + b);
+            if (!(v > a && v < b))
+                break;
+            if (p[j] * hw_integral(n_w, w, omu_base[j], v) < want) b = v; else a = v;
+        }
+        omu[i] = 0.5 * (a + b);
+    }
+    for (int i = 0; i < n_bins; ++i) {
+        if (pdf)
+            pdf[i] = (1.0 / n_bins) / (omu[i] - omu[i + 1]);
+    }
+    if (icdf)
+        for (int i = 0; i <= n_bins; ++i)
+            icdf[i] = 1.0 - omu[i];
+    if (z_out)
+        *z_out = Z;
+    free(cum); free(p);
+    return 0;
+}

@@ -23,6 +23,7 @@ GRID = ["test_oracle_grid.py"]
 GADJ = ["test_oracle_grid_adjoint.py"]
 PAPER = ["test_oracle_paper.py"]
 METRICS = ["test_oracle_metrics.py"]
+WEIGHTS = ["test_oracle_phase_weights.py"]
 
 # (file, text, replacement, pin files, the mistake)
 MUTATIONS = [
@@ -136,10 +137,28 @@ MUTATIONS = [
      "pg[0] += A * (R.S[j] + jj * (1.0 / c->mu_s - 1.0 / mu_ext));", ADJ, "transport term dropped"),
     ("adjoint.c", "pg[1] += A * (R.S[j] - jj / mu_ext - R.l[j]);", "pg[1] += A * (R.S[j] + jj / mu_ext - R.l[j]);",
      ADJ, "sign of the albedo term"),
-    ("adjoint.c", "double t = oracle_hat(J->n_w, q, R.muc[j]) - jj * J->z[q];",
-     "double t = oracle_hat(J->n_w, q, R.muc[j]) - J->z[q];", ADJ, "normalisation counted once"),
+    ("adjoint.c", "double t = oracle_hat(J->n_w, q, R.muc[j]) / h_w(J->n_w, J->w, R.muc[j]) - jj * J->z[q];",
+     "double t = oracle_hat(J->n_w, q, R.muc[j]) / h_w(J->n_w, J->w, R.muc[j]) - J->z[q];", ADJ,
+     "normalisation counted once"),
     ("adjoint.c", "for (int i = 0; i < j; ++i)\n                    t +=", "for (int i = 1; i < j; ++i)\n                    t +=",
      ADJ, "range of the sampled-angle sum"),
+    # phase weights at w != 1: the reweighted table and its scores
+    ("table.c", "cum[j + 1] = cum[j] + p[j] * hw_integral(n_w, w, omu_base[j], omu_base[j + 1]);",
+     "cum[j + 1] = cum[j] + hw_integral(n_w, w, omu_base[j], omu_base[j + 1]);", WEIGHTS,
+     "reweighted bin masses without the table density"),
+    ("table.c", "return w[k] * oracle_hat(n_w, k, mu) + w[k + 1] * oracle_hat(n_w, k + 1, mu);",
+     "return w[k] * oracle_hat(n_w, k, mu) + w[k] * oracle_hat(n_w, k + 1, mu);", WEIGHTS,
+     "weight interpolant takes one node's weight"),
+    ("adjoint.c", "double t = oracle_hat(J->n_w, q, R.muc[j]) / h_w(J->n_w, J->w, R.muc[j]) - jj * J->z[q];",
+     "double t = oracle_hat(J->n_w, q, R.muc[j]) - jj * J->z[q];", WEIGHTS,
+     "camera-density score without 1/h_w"),
+    ("adjoint.c", "t += oracle_hat(J->n_w, q, R.mus[i]) / h_w(J->n_w, J->w, R.mus[i]);",
+     "t += oracle_hat(J->n_w, q, R.mus[i]);", WEIGHTS, "sampled-angle score without 1/h_w"),
+    ("adjoint.c", "        for (int k = 0; k < n_w; ++k)\n            z[k] /= zw;\n", "", WEIGHTS,
+     "hat integrals not divided by Z(w)"),
+    ("adjoint.c", "oracle_hat_integrals(base_omu ? base_omu : c->omu, c->n_bins, n_w, z);",
+     "oracle_hat_integrals(c->omu, c->n_bins, n_w, z);", WEIGHTS,
+     "hat integrals of the reweighted table instead of the unweighted one"),
     ("adjoint.c", "{\n        uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0xFFFFFFFFu, 0u}, o[4];",
      "{\n        uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0u, 0u}, o[4];", ADJ,
      "replayed beam entry from the first flight's numbers"),
