@@ -413,12 +413,20 @@ def adjoint_comparison(E, dev, steps, flush):
     t_fwd = timed(lambda: eng.run(med, n, seed=1, stream=stream))
     t_w = timed(lambda: eng.adjoint(med, adj, n, n_w=64, seed=1, stream=stream))
     t_0 = timed(lambda: eng.adjoint(med, adj, n, n_w=0, seed=1, stream=stream))
+    # at phase weights w != 1: the forward pass reweights the table on the
+    # device and walks it; the adjoint does the same and evaluates the scores at w
+    w = (0.5 + torch.rand(64, generator=torch.Generator().manual_seed(2), dtype=torch.float32)).to(dev)
+    t_fwd_w = timed(lambda: eng.run(E.Medium(med.mu_s, med.mu_a, "table", 0.0,
+                                             E.WeightedTable(table, w, dev, stream)), n, seed=1, stream=stream))
+    t_adj_w = timed(lambda: eng.adjoint(med, adj, n, n_w=64, seed=1, stream=stream, phase_w=w))
     eng.check()
     return {"forward_ms": t_fwd, "adjoint_ms": t_w, "adjoint_mu_only_ms": t_0,
             "cost_vs_forward": t_w / t_fwd, "cost_vs_forward_mu_only": t_0 / t_fwd,
+            "at_weights": {"forward_ms": t_fwd_w, "adjoint_ms": t_adj_w, "cost_vs_forward": t_adj_w / t_fwd_w},
             "workload": "tau=5 Mie, 1e7 photons, 128x128 image; gradient w.r.t. mu_s, mu_a and 64 "
                         "phase-table weights (one pass; photons with more than 8 scatterings are replayed once) "
-                        "or mu_s, mu_a only (one pass)"}
+                        "or mu_s, mu_a only (one pass); at_weights: 64 weights in [0.5, 1.5), the table "
+                        "reweighted on the device in both passes"}
 
 
 def run_reference(args):

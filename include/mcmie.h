@@ -299,19 +299,45 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom,
                        uint64_t item_photons, uint32_t *d_error, void *d_work,
                        size_t work_bytes, void *stream);
 
+/* Phase function with hat-function weights w (n_phase_w of them, device
+ * floats, all > 0): p_w(mu) = p(mu) h_w(mu) / Z(w), h_w = sum_k w_k phi_k the
+ * linear interpolant of the weights at the nodes mu_k = -1 + 2k/(n_phase_w -
+ * 1), p the density of base's table (constant on each bin), Z(w) = int p h_w
+ * (Eq. 9-10: the reweighted function is renormalised like the phase
+ * function itself). Writes into d_table (table_bytes >= mc_table_bytes(
+ * base->n_bins), 16-byte aligned, not base's own blob) the equal-probability
+ * table of p_w in the layout of mie_table_build's blob, so that an mc_medium
+ * pointing at it makes mc_run sample p_w and use it as the camera density.
+ * Built by one CTA in double precision, stream-ordered, nothing copied to
+ * the host. Weights that are not all positive and finite (or levels that
+ * single precision cannot hold apart) set MC_EFLAG_NUMERIC in *d_error and
+ * write an invalid header, so a walk using the blob reports MC_ERR_TABLE.
+ * The unweighted table's bin edges are taken in double precision from its
+ * bin densities (every bin holds 1/n_bins), and the new densities from the
+ * new levels in double precision, as mie_table_build does. 2 <= n_phase_w <=
+ * 256; base->phase_kind must be MC_PHASE_TABLE with n_bins <= 8192. The paper
+ * has no phase weights; they parametrise the phase function for fitting. */
+mc_status mc_phase_table_weighted(const mc_medium *base, int n_phase_w, const float *d_phase_w, void *d_table,
+                                  size_t table_bytes, uint32_t *d_error, void *stream);
+
 /* Gradient of L = sum_pix adj[pix] * image[pix] (adj: d_adj_image, float,
  * [nz][nx], in the image's weight units) with respect to mu_s, mu_a and
- * n_phase_w hat-function weights of the phase function, p_w(mu) =
- * p(mu) h_w(mu) / Z(w), h_w = sum_k w_k phi_k, evaluated at w = 1; phi_k has
- * nodes at mu_k = -1 + 2k/(n_phase_w - 1). Likelihood ratios of every
- * sampled flight (Eq. 15) and polar angle plus the direct terms of each
- * camera contribution (Eq. 16 weight, transport, phase density), on the
- * photons mc_run would simulate with the same arguments, replayed from
- * their Philox counters (nothing about the paths is stored). Roulette
- * factors are held fixed. d_out[3 + n_phase_w] receives (L, dL/dmu_s,
- * dL/dmu_a, dL/dw_0, ..) in double precision, reduced in a fixed order.
- * n_phase_w: 0 (no phase weights) or 2..256 (MC_PHASE_TABLE only). One pass
- * per photon; with phase weights, photons with more than 8 collisions are
+ * n_phase_w hat-function weights w of the phase function p_w = p h_w / Z(w)
+ * (see mc_phase_table_weighted), evaluated at the device weights d_phase_w
+ * (all > 0), or at w = 1 when d_phase_w is NULL. medium carries the
+ * unweighted table p; with weights, the walk samples p_w through the table
+ * mc_phase_table_weighted builds (here into d_work), i.e. the photons mc_run
+ * simulates with that table and the same other arguments. Likelihood ratios
+ * of every sampled flight (Eq. 15) and polar angle plus the direct terms of
+ * each camera contribution (Eq. 16 weight, transport, phase density), on
+ * those photons, replayed from their Philox counters (nothing about the
+ * paths is stored): the phase-weight scores are phi_k(mu) / h_w(mu) - Z_k /
+ * Z(w), Z_k = int p phi_k. Roulette factors are held fixed. d_out[3 +
+ * n_phase_w] receives (L, dL/dmu_s, dL/dmu_a, dL/dw_0, ..) in double
+ * precision, reduced in a fixed order. n_phase_w: 0 (no phase weights;
+ * d_phase_w must be NULL) or 2..256 (MC_PHASE_TABLE only; with d_phase_w,
+ * n_bins <= 8192). One pass per
+ * photon; with phase weights, photons with more than 8 collisions are
  * replayed once more. MC_PHASE_PAPER is not supported (MC_ERR_ARG).
  * Requires mu_s > 0.
  * d_work: mc_adjoint_workspace_bytes(n_phase_w) bytes. The paper has no
@@ -319,8 +345,9 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom,
 size_t mc_adjoint_workspace_bytes(int n_phase_w);
 mc_status mc_adjoint(const mc_medium *medium, const mc_geometry *geom,
                      const mc_camera *camera, const mc_run_params *run,
-                     const float *d_adj_image, int n_phase_w, double *d_out,
-                     uint32_t *d_error, void *d_work, size_t work_bytes, void *stream);
+                     const float *d_adj_image, int n_phase_w, const float *d_phase_w,
+                     double *d_out, uint32_t *d_error, void *d_work, size_t work_bytes,
+                     void *stream);
 
 /* ------------------------------------------------------------------------
  * Heterogeneous media: the number density of the particles on a voxel grid

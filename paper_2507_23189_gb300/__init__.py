@@ -7,12 +7,12 @@ CUDA behind the C ABI in include/mcmie.h; this package is its binding.
 """
 from . import _native
 from .engine import (Batch, Camera, Engine, Geometry, Grid, Medium, MixtureTable, PaperTable, PhaseTable,
-                     auto_frac_bits, camera_image, decode_trace, host_workspace_bytes, image_metrics, philox, run_host,
+                     WeightedTable, auto_frac_bits, camera_image, decode_trace, host_workspace_bytes, image_metrics, philox, run_host,
                      run_params, wait_selftest)
 from .checkpoint import append_jsonl, run_record, run_resumable
 
 __all__ = ["Batch", "Camera", "Engine", "Geometry", "Grid", "Medium", "MixtureTable", "PaperTable", "PhaseTable",
-           "auto_frac_bits", "camera_image",
+           "WeightedTable", "auto_frac_bits", "camera_image",
            "decode_trace", "host_workspace_bytes", "image_metrics", "philox", "run_host", "run_params",
            "wait_selftest", "run_resumable", "run_record", "append_jsonl", "lib"]
 

@@ -21,7 +21,7 @@ LIB_CHECKED = os.path.join(HERE, "_build", "libmcmie_checked.so")
 # approximations (MC_STRICT), for trace comparisons at the tightest tolerance;
 # built only on request, loaded instead of the normal one when MC_STRICT=1
 LIB_STRICT = os.path.join(HERE, "_build", "libmcmie_strict.so")
-SOURCES = ["walk.cu", "api.cu", "mie_table.cpp", "noalloc.cu", "metrics.cu", "grid.cu"]
+SOURCES = ["walk.cu", "api.cu", "mie_table.cpp", "noalloc.cu", "metrics.cu", "grid.cu", "phase_weights.cu"]
 HEADERS = ["engine.h", "table_format.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true",

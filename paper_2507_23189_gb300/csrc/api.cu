@@ -426,18 +426,37 @@ size_t mc_adjoint_workspace_bytes(int n_phase_w)
     if (n_phase_w < 0 || n_phase_w == 1 || n_phase_w > 256) return 0;
     const int rows = mcx::adjoint_max_grid();
     if (rows < 1) return 0;
-    return kAlign + up(sizeof(double) * 256) + up(sizeof(double) * (size_t)rows * (3 + n_phase_w));
+    // counter, hat integrals, per-CTA partials, and room for the largest
+    // reweighted table when there are phase weights
+    return kAlign + up(sizeof(double) * 256) + up(sizeof(double) * (size_t)rows * (3 + n_phase_w)) +
+           (n_phase_w > 0 ? up(mc_table_layout(mcx::kMaxWeightedBins, nullptr)) : 0);
+}
+
+mc_status mc_phase_table_weighted(const mc_medium *base, int n_phase_w, const float *d_phase_w, void *d_table,
+                                  size_t table_bytes, uint32_t *d_error, void *stream)
+{
+    if (!base || base->phase_kind != MC_PHASE_TABLE || check_medium(base) != MC_OK ||
+        base->n_bins > mcx::kMaxWeightedBins || n_phase_w < 2 ||
+        n_phase_w > 256 || !d_phase_w || !aligned(d_phase_w, 4) || !d_table || !aligned(d_table, 16) ||
+        !d_error || !aligned(d_error, 4) || d_table == base->d_table)
+        return MC_ERR_ARG;
+    if (table_bytes < mc_table_layout(base->n_bins, nullptr)) return MC_ERR_NOMEM;
+    return cuda_status(mcx::launch_weighted_table(static_cast<const unsigned char *>(base->d_table), base->n_bins,
+                                                  n_phase_w, d_phase_w, static_cast<unsigned char *>(d_table),
+                                                  d_error, static_cast<cudaStream_t>(stream)));
 }
 
 mc_status mc_adjoint(const mc_medium *medium, const mc_geometry *geom, const mc_camera *camera,
-                     const mc_run_params *run, const float *d_adj_image, int n_phase_w, double *d_out,
-                     uint32_t *d_error, void *d_work, size_t work_bytes, void *stream)
+                     const mc_run_params *run, const float *d_adj_image, int n_phase_w,
+                     const float *d_phase_w, double *d_out, uint32_t *d_error, void *d_work,
+                     size_t work_bytes, void *stream)
 {
     mc_status s;
     if ((s = validate_all(medium, geom, camera, run)) != MC_OK) return s;
     if (!d_adj_image || !d_out || !d_error || !d_work || !aligned(d_adj_image, 4) || !aligned(d_out, 8) ||
         !aligned(d_work, 16) || !(medium->mu_s > 0.0) || n_phase_w < 0 || n_phase_w == 1 || n_phase_w > 256 ||
-        (n_phase_w > 0 && medium->phase_kind != MC_PHASE_TABLE) || medium->phase_kind == MC_PHASE_PAPER)
+        (n_phase_w > 0 && medium->phase_kind != MC_PHASE_TABLE) || medium->phase_kind == MC_PHASE_PAPER ||
+        (d_phase_w && (n_phase_w == 0 || !aligned(d_phase_w, 4) || medium->n_bins > mcx::kMaxWeightedBins)))
         return MC_ERR_ARG;
     const size_t need = mc_adjoint_workspace_bytes(n_phase_w);
     if (!need) return MC_ERR_CUDA;
@@ -453,12 +472,24 @@ mc_status mc_adjoint(const mc_medium *medium, const mc_geometry *geom, const mc_
     fill_medium(a.m, medium, run->n_photons, run->photon_offset, run->seed, nullptr, nullptr, nullptr);
     a.adj = d_adj_image;
     a.n_w = n_phase_w;
+    a.w = d_phase_w;
+    a.base_table = a.m.table;
     a.c_s = (float)(1.0 / medium->mu_s - 1.0 / (medium->mu_s + medium->mu_a));
-    a.counter = static_cast<unsigned long long *>(d_work);
-    a.z = reinterpret_cast<double *>(static_cast<unsigned char *>(d_work) + kAlign);
-    a.partials = reinterpret_cast<double *>(static_cast<unsigned char *>(d_work) + kAlign +
-                                            up(sizeof(double) * 256));
-    e = mcx::launch_adjoint(a, mcx::adjoint_max_grid(), d_out, st);
+    unsigned char *wk = static_cast<unsigned char *>(d_work);
+    const int rows = mcx::adjoint_max_grid();
+    a.counter = reinterpret_cast<unsigned long long *>(wk);
+    a.z = reinterpret_cast<double *>(wk + kAlign);
+    a.partials = reinterpret_cast<double *>(wk + kAlign + up(sizeof(double) * 256));
+    if (d_phase_w) {
+        // the walk samples p h_w / Z(w): the table reweighted on the device
+        unsigned char *wt = wk + kAlign + up(sizeof(double) * 256) +
+                            up(sizeof(double) * (size_t)rows * (3 + n_phase_w));
+        if ((e = mcx::launch_weighted_table(a.base_table, medium->n_bins, n_phase_w, d_phase_w, wt, d_error,
+                                            st)) != cudaSuccess)
+            return cuda_status(e);
+        a.m.table = wt;
+    }
+    e = mcx::launch_adjoint(a, rows, d_out, st);
     return cuda_status(e);
 }
 

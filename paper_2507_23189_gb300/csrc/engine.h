@@ -72,11 +72,13 @@ struct BatchArgs {
 // kernel); partials holds one row of 3 + n_w doubles per CTA.
 struct AdjArgs {
     CommonArgs c;
-    MediumArgs m;
+    MediumArgs m;               // m.table: the table the walk samples (reweighted by w if given)
     const float *adj;           // [nz][nx]
     int n_w;                    // phase-weight hats (0: none)
+    const float *w;             // [n_w] phase weights (nullptr: all 1)
+    const unsigned char *base_table;  // the unweighted table (hat integrals Z_k)
     float c_s;                  // 1/mu_s - 1/mu_ext
-    double *z;                  // [n_w] hat integrals of the table (workspace)
+    double *z;                  // [n_w] hat integrals of the unweighted table (workspace)
     double *partials;           // [grid][3 + n_w]
     unsigned long long *counter;
 };
@@ -158,6 +160,16 @@ int adjoint_max_grid();
 
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out,
                           cudaStream_t stream);
+
+// Largest table the device reweighting takes (two double arrays of n_bins + 1
+// entries in shared memory).
+constexpr int kMaxWeightedBins = 8192;
+
+// The equal-probability table of p h_w / Z(w) from the unweighted table blob
+// `base` (n_bins bins) and n_w device weights, into `out` (the same layout);
+// one CTA. Invalid weights set MC_EFLAG_NUMERIC and an invalid header.
+cudaError_t launch_weighted_table(const unsigned char *base, int n_bins, int n_w, const float *w,
+                                  unsigned char *out, uint32_t *err, cudaStream_t stream);
 
 // The bounded mbarrier wait on a phase that cannot complete (self-test).
 cudaError_t launch_wait_selftest(uint32_t *err, uint32_t tries, cudaStream_t stream);

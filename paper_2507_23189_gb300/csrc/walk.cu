@@ -1452,19 +1452,22 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
 
 // ------------------------------------------------------------------ adjoint
 // Gradient of L = sum_pix adj[pix] image[pix] with respect to (mu_s, mu_a)
-// and the hat-function phase weights w_k at w = 1 (p_w = p h_w / Z(w)), by
-// likelihood ratios along replayed paths (the photons, random numbers and
-// single-precision arithmetic of the forward walk). For a camera term
-// A_j = adj[pix_j] c_j at collision j of a photon:
+// and the hat-function phase weights w_k (p_w = p h_w / Z(w), h_w = sum_k
+// w_k phi_k, Z(w) = sum_k w_k Z_k, Z_k = int p phi_k over the unweighted
+// table p), by likelihood ratios along replayed paths (the photons, random
+// numbers and single-precision arithmetic of the forward walk, which samples
+// p_w through its reweighted table). For a camera term A_j = adj[pix_j] c_j
+// at collision j of a photon:
 //   dL/dmu_s += A_j (S_j + j (1/mu_s - 1/mu_ext) - l_j)
 //   dL/dmu_a += A_j (S_j - j/mu_ext - l_j)
-//   dL/dw_k  += A_j (phi_k(mu_c,j) - j Z_k + sum_{i<j} phi_k(mu_i)),
+//   dL/dw_k  += A_j (phi_k(mu_c,j)/h_w(mu_c,j) - j Z_k/Z(w)
+//                    + sum_{i<j} phi_k(mu_i)/h_w(mu_i)),
 // S_j = sum over the flights up to j of (1/mu_ext - s_i) (Eq. 15 score),
-// l_j the distance to the camera face, mu_i the sampled polar cosines,
-// Z_k = int p phi_k. The last sum is rearranged as
-// sum_i phi_k(mu_i) (P_tot - P_i) with P_i = A_1 + .. + A_i, which needs the
-// photon's total P_tot: photons are replayed a second time (same counters)
-// when phase-weight gradients are wanted. Roulette factors are held fixed.
+// l_j the distance to the camera face, mu_i the sampled polar cosines. The
+// last sum is rearranged as sum_i phi_k(mu_i)/h_w(mu_i) (P_tot - P_i) with
+// P_i = A_1 + .. + A_i, which needs the photon's total P_tot: photons with
+// more angles than the kernel keeps are replayed a second time (same
+// counters). Roulette factors are held fixed.
 
 // Hat functions: nodes mu_k = -1 + k h, h = 2/(n_w - 1); the two nonzero
 // weights at mu.
@@ -1527,11 +1530,14 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 }
 
 // Private single-precision accumulators: hat k of thread t at rows[k*B + t]
-// (consecutive threads in consecutive banks; no atomics, fixed order).
-__device__ __forceinline__ void hat_add(float *rows, int nw_stride, int k, float f, float v)
+// (consecutive threads in consecutive banks; no atomics, fixed order). Adds
+// v phi(mu) / h_w(mu) for the two hats around mu (k, fraction f), with the
+// weights sw in shared memory.
+__device__ __forceinline__ void hat_add(float *rows, int nw_stride, const float *sw, int k, float f, float v)
 {
-    rows[k * nw_stride + threadIdx.x] += v * (1.0f - f);
-    rows[(k + 1) * nw_stride + threadIdx.x] += v * f;
+    const float u = mc_div(v, fmaf(f, sw[k + 1] - sw[k], sw[k]));
+    rows[k * nw_stride + threadIdx.x] += u * (1.0f - f);
+    rows[(k + 1) * nw_stride + threadIdx.x] += u * f;
 }
 
 template <int PHASE, bool PHASEW>
@@ -1543,10 +1549,11 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
     const uint32_t tb = (PHASE == MC_PHASE_TABLE && !PHASEW) ? C.table_bytes : 0u;
     const int nw = PHASEW ? A.n_w : 0;
     const int B = blockDim.x, warps = B / 32, warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-    double *s_z = reinterpret_cast<double *>(smem + tb);   // [nw]
+    double *s_z = reinterpret_cast<double *>(smem + tb);   // [nw] Z_k / Z(w)
     double *s_red = s_z + nw;                              // [warps][4]
     unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(s_red + warps * 4);
-    float *rows = reinterpret_cast<float *>(s_bar + 2);    // [nw][B]
+    float *s_w = reinterpret_cast<float *>(s_bar + 2);     // [nw, padded to 4] weights
+    float *rows = s_w + ((nw + 3) & ~3);                   // [nw][B]
     for (int i = threadIdx.x; i < nw * B; i += B) rows[i] = 0.0f;
     if (threadIdx.x == 0) mbar_init(s_bar);
     Smem S = carve<MC_PHASE_HG, false>(smem, C);
@@ -1561,8 +1568,18 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
         }
         if (!bind_table<PHASE>(S, C)) return;
     }
-    if (PHASEW)
-        for (int k = threadIdx.x; k < nw; k += B) s_z[k] = A.z[k];
+    if (PHASEW) {
+        for (int k = threadIdx.x; k < nw; k += B) s_w[k] = A.w ? A.w[k] : 1.0f;
+        __syncthreads();
+        if (threadIdx.x == 0) {   // Z(w) = sum_k w_k Z_k, fixed order
+            double zw = 0.0;
+            for (int k = 0; k < nw; ++k) zw += (double)s_w[k] * A.z[k];
+            s_red[0] = zw;
+        }
+        __syncthreads();
+        const double zw = s_red[0];
+        for (int k = threadIdx.x; k < nw; k += B) s_z[k] = A.z[k] / zw;
+    }
     __syncthreads();
     const float c_s = A.c_s;   // 1/mu_s - 1/mu_ext
 
@@ -1663,7 +1680,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
                 if (PHASEW && Aj != 0.0f) {
                     float f;
                     const int k = chk(hat_pair(nw, dy, f), nw - 1, C.error);
-                    hat_add(rows, B, k, f, Aj);
+                    hat_add(rows, B, s_w, k, f, Aj);
                 }
             }
             if (C.max_scatter && ncoll >= C.max_scatter) {
@@ -1680,7 +1697,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
                         ++cnt;
                     } else {
                         const float coef = Ptot - P;
-                        if (coef != 0.0f) hat_add(rows, B, k, f, coef);
+                        if (coef != 0.0f) hat_add(rows, B, s_w, k, f, coef);
                     }
                 }
                 rotate(dx, dy, dz, om, u2);
@@ -1700,7 +1717,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
                     for (int q = 0; q < ADJ_LIST; ++q) {
                         if (q < cnt) {
                             const float coef = P - lp[q];
-                            if (coef != 0.0f) hat_add(rows, B, lk[q], lf[q], coef);
+                            if (coef != 0.0f) hat_add(rows, B, s_w, lk[q], lf[q], coef);
                         }
                     }
                 } else {
@@ -2100,7 +2117,8 @@ cudaError_t launch_adjoint_one(const AdjArgs &a, int rows, double *out, cudaStre
     const int nw = PHASEW ? a.n_w : 0;
     const int block = PHASEW ? ADJ_BLOCK_W : ADJ_BLOCK;
     const size_t smem = ((PHASE == MC_PHASE_TABLE && !PHASEW) ? a.c.table_bytes : 0) +
-                        sizeof(double) * (nw + (block / 32) * 4) + 16 + sizeof(float) * nw * block;
+                        sizeof(double) * (nw + (block / 32) * 4) + 16 + sizeof(float) * ((nw + 3) & ~3) +
+                        sizeof(float) * nw * block;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, bps = 0;
@@ -2113,7 +2131,7 @@ cudaError_t launch_adjoint_one(const AdjArgs &a, int rows, double *out, cudaStre
     if (cap < grid) grid = cap < 1 ? 1 : cap;
     if (grid > rows) grid = rows;
     if (PHASEW) {
-        hat_integrals_kernel<<<a.n_w, 256, 0, st>>>(a.m.table, a.n_w, a.z);
+        hat_integrals_kernel<<<a.n_w, 256, 0, st>>>(a.base_table, a.n_w, a.z);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     kern<<<(unsigned)grid, block, smem, st>>>(a);

@@ -111,6 +111,43 @@ class MixtureTable(PhaseTable):
         self._dev = {}
 
 
+class WeightedTable:
+    """A phase table reweighted by positive hat-function weights,
+    p_w = p h_w / Z(w), built on the device by mc_phase_table_weighted from
+    `base` (a PhaseTable) and the weights (a CUDA tensor of n_w values,
+    kept as float32; nothing is copied to the host). Use it as a Medium's
+    table: the walk then samples p_w and uses it as the camera density."""
+
+    def __init__(self, base, phase_w, device=None, stream=None):
+        torch = _torch()
+        dev = torch.device(device if device is not None else "cuda")
+        self.base = base
+        self.n_bins = base.n_bins
+        self.info = base.info
+        self.phase_w = phase_w.detach().to(device=dev, dtype=torch.float32).contiguous()
+        L = N.lib()
+        nbytes = L.mc_table_bytes(base.n_bins)
+        self._blob = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.error = torch.zeros(1, dtype=torch.int32, device=dev)
+        m = N.Medium()
+        m.mu_s, m.phase_kind, m.n_bins = 1.0, N.PHASE_TABLE, base.n_bins
+        base_blob = base.device_blob(dev)
+        m.d_table = base_blob.data_ptr()
+        N.check("mc_phase_table_weighted", L.mc_phase_table_weighted(
+            C.byref(m), int(self.phase_w.numel()), C.c_void_p(self.phase_w.data_ptr()),
+            C.c_void_p(self._blob.data_ptr()), nbytes, C.c_void_p(self.error.data_ptr()),
+            _stream_handle(stream)))
+        self._keep = base_blob
+
+    def device_blob(self, device=None):
+        return self._blob
+
+    def check(self, stream=None):
+        """Raise if the weights were rejected (mc_check of the build's word)."""
+        N.check("mc_phase_table_weighted", N.lib().mc_check(C.c_void_p(self.error.data_ptr()),
+                                                            _stream_handle(stream)))
+
+
 class PaperTable:
     """The paper's own sampling table (Sec. 3.1.2, mie_paper_table_build):
     the Mie phase function at n_theta equally spaced angles, its cumulative
@@ -341,14 +378,21 @@ class Engine:
         self._keep = keep
         return buf
 
-    def adjoint(self, medium, adj_image, n_photons, n_w=64, seed=1, stream=None, **kw):
+    def adjoint(self, medium, adj_image, n_photons, n_w=64, seed=1, stream=None, phase_w=None, **kw):
         """(L, dL/dmu_s, dL/dmu_a, dL/dw_0..) for L = sum(adj_image * image)
-        over the photons run(medium, n_photons, seed, **kw) simulates, as a
-        float64 device tensor (mc_adjoint). adj_image: [nz, nx] in weight
+        as a float64 device tensor (mc_adjoint). medium: the unweighted
+        table; phase_w (a tensor of n_w positive weights, or None for w = 1):
+        the gradient at those weights, on the photons run() simulates with
+        WeightedTable(medium.table, phase_w). adj_image: [nz, nx] in weight
         units per image unit."""
         torch = _torch()
         rp = run_params(n_photons, seed, **kw)
         m, keep = medium.as_c(self.device)
+        wdev = None
+        if phase_w is not None:
+            wdev = phase_w.detach().to(device=self.device, dtype=torch.float32).contiguous()
+            if wdev.numel() != n_w:
+                raise ValueError("phase_w must hold n_w weights")
         adj = adj_image.to(device=self.device, dtype=torch.float32).contiguous()
         if tuple(adj.shape) != (self.camera.nz, self.camera.nx):
             raise ValueError("adjoint image must be [nz, nx]")
@@ -361,9 +405,10 @@ class Engine:
         g, c = self.geometry.as_c(), self.camera.as_c()
         N.check("mc_adjoint", N.lib().mc_adjoint(
             C.byref(m), C.byref(g), C.byref(c), C.byref(rp), C.c_void_p(adj.data_ptr()), n_w,
+            C.c_void_p(wdev.data_ptr()) if wdev is not None else None,
             C.c_void_p(out.data_ptr()), C.c_void_p(self.error.data_ptr()),
             C.c_void_p(self._adj_work.data_ptr()), self._adj_work.numel(), _stream_handle(stream)))
-        self._keep = (keep, adj)
+        self._keep = (keep, adj, wdev)
         return out
 
     def run_grid(self, grid, phase, n_photons, seed=1, stream=None, n_trace=0, n_events=32, **kw):
@@ -510,14 +555,16 @@ class Batch:
 def camera_image(engine, table, mu_s, mu_a, phase_w=None, n_photons=10**6, seed=1, grad_seed=None, **kw):
     """Differentiable side-camera image (float64 [nz, nx], weight units).
 
-    mu_s, mu_a: 0-d float64 tensors; phase_w: optional tensor of hat-function
-    phase weights, which must equal 1 (the image is evaluated at w = 1 and
-    only the gradient with respect to w is provided). Forward runs mc_run;
-    backward runs mc_adjoint with grad_output as the adjoint image, on the
-    same photons (grad_seed None: the exact derivative of the sampled image)
-    or on an independent photon set drawn with grad_seed (an unbiased
-    estimate of the derivative of the expected image, uncorrelated with the
-    forward sample; what a loss that is nonlinear in the image needs)."""
+    mu_s, mu_a: 0-d float64 tensors; phase_w: optional tensor of positive
+    hat-function phase weights (the phase function p h_w / Z(w) of
+    mc_phase_table_weighted; None: the table itself). Forward runs mc_run
+    (with the table reweighted on the device when phase_w is given);
+    backward runs mc_adjoint at the same weights with grad_output as the
+    adjoint image, on the same photons (grad_seed None: the exact derivative
+    of the sampled image) or on an independent photon set drawn with
+    grad_seed (an unbiased estimate of the derivative of the expected image,
+    uncorrelated with the forward sample; what a loss that is nonlinear in
+    the image needs)."""
     torch = _torch()
     if phase_w is None:
         phase_w = torch.ones(0, dtype=torch.float64, device=engine.device)
@@ -531,21 +578,27 @@ def _make_camera_image():
     class CameraImageFn(torch.autograd.Function):
         @staticmethod
         def forward(ctx, mu_s, mu_a, phase_w, engine, table, n_photons, seed, kw):
-            if phase_w.numel() and not bool(torch.all(phase_w == 1)):
-                raise ValueError("the image is evaluated at phase weights w = 1")
             seed, grad_seed = seed
             med = Medium(float(mu_s), float(mu_a), "table", 0.0, table)
-            engine.run(med, n_photons, seed=seed, **kw)
+            walk_med, wt = med, None
+            if phase_w.numel():
+                wt = WeightedTable(table, phase_w, engine.device)
+                walk_med = Medium(float(mu_s), float(mu_a), "table", 0.0, wt)
+            engine.run(walk_med, n_photons, seed=seed, **kw)
             engine.check()
+            if wt is not None:
+                wt.check()
             img = engine.image.to(torch.float64) * 2.0 ** -engine.image_frac_bits
             ctx.engine, ctx.med, ctx.n, ctx.seed, ctx.kw = engine, med, n_photons, grad_seed, kw
             ctx.n_w = phase_w.numel()
+            ctx.w = wt.phase_w if wt is not None else None
             ctx.devs = (mu_s.device, mu_a.device, phase_w.device)
             return img
 
         @staticmethod
         def backward(ctx, grad_img):
-            out = ctx.engine.adjoint(ctx.med, grad_img, ctx.n, n_w=ctx.n_w, seed=ctx.seed, **ctx.kw)
+            out = ctx.engine.adjoint(ctx.med, grad_img, ctx.n, n_w=ctx.n_w, seed=ctx.seed, phase_w=ctx.w,
+                                     **ctx.kw)
             ctx.engine.check()
             ds, da, dw = ctx.devs
             gw = out[3:].to(dw) if ctx.n_w else None

@@ -255,3 +255,24 @@ def test_photon_cap_and_automatic_fraction_bits_are_checked_on_the_host(eng):
     assert run(1000, 0, 1) == -1
     assert run(1000, 32, 1) == -3
     assert run(1000, 7, 0) == -1 and run(1000, 49, 0) == -1
+
+
+def test_weighted_table_rejects_bad_arguments_on_the_host(eng):
+    """mc_phase_table_weighted: a table medium, 2..256 weights, an aligned
+    output of at least mc_table_bytes and not the input blob; all decided
+    before any CUDA call."""
+    from paper_2507_23189_gb300 import _native as N
+    L = N.lib()
+    buf = (C.c_uint64 * 64)()
+    p = C.addressof(buf) + (-C.addressof(buf)) % 16
+    tb = L.mc_table_bytes(4096)
+    base = N.Medium(0.1, 0.0, N.PHASE_TABLE, 0.0, p, 4096)
+    q = p + 256
+    for args in ((base, 1, p, q, tb, p), (base, 257, p, q, tb, p), (base, 8, None, q, tb, p),
+                 (base, 8, p, None, tb, p), (base, 8, p, q + 4, tb, p), (base, 8, p, p, tb, p),
+                 (base, 8, p, q, tb, None)):
+        m, nw, w, out, nb, err = args
+        assert L.mc_phase_table_weighted(C.byref(m), nw, w, out, nb, err, None) == -1, args
+    hg = N.Medium(0.1, 0.0, N.PHASE_HG, 0.5, None, 0)
+    assert L.mc_phase_table_weighted(C.byref(hg), 8, p, q, tb, p, None) == -1
+    assert L.mc_phase_table_weighted(C.byref(base), 8, p, q, tb - 16, p, None) == -3
