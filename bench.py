@@ -236,8 +236,43 @@ def _batch_vs_plain(E, dev, media, nph, steps, warmup, flush):
 
     t_batch = timed(g.replay)
     t_plain = timed(plain)
+    # how busy the GPU is during the sequential launches: the sum of the
+    # launches' own durations (events around each) over the wall time
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in engines]
+    busy = []
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        wall0, wall1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        wall0.record(stream)
+        for (a, b), e, m, n in zip(ev, engines, media, nph):
+            a.record(stream)
+            e.run(m, n, seed=1, stream=stream, image_frac_bits=frac)
+            b.record(stream)
+        wall1.record(stream)
+        wall1.synchronize()
+        busy.append(sum(a.elapsed_time(b) for a, b in ev) / wall0.elapsed_time(wall1))
+    busy_frac = float(sum(busy) / len(busy))
+    # the launches' fixed cost (ramp-up, drain tail, table staging, tally
+    # flush): each medium once more at twice its photons (the same first N
+    # photons and N more); 2 t(N) - t(2N) is what one launch spends beyond
+    # its photons' share, the most a single launch over all media can save
+    fixed = []
+    for e, m, n in zip(engines, media, nph):
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        flush.fill_(1)
+        a.record(stream)
+        e.run(m, n, seed=1, stream=stream, image_frac_bits=frac)
+        b.record(stream)
+        e.run(m, 2 * n, seed=1, stream=stream, image_frac_bits=frac)
+        c.record(stream)
+        c.synchronize()
+        fixed.append(2 * a.elapsed_time(b) - b.elapsed_time(c))
+    t_one = 1e3 * t_plain / steps
+    ceiling = t_one / max(t_one * busy_frac - sum(fixed), 1e-9)
     return {"value": steps * steps_per_run / t_batch, "unit": UNIT,
             "plain_sequential": steps * steps_per_run / t_plain, "speedup": t_plain / t_batch,
+            "plain_busy_fraction": busy_frac, "plain_fixed_ms": float(sum(fixed)),
+            "speedup_ceiling": ceiling,
             "ms_batched": 1e3 * t_batch / steps, "ms_plain": 1e3 * t_plain / steps,
             "media": len(media), "photons": int(sum(nph)), "photon_steps": steps_per_run,
             "identical_tallies": same, "tuned": {k: tune[k] for k in ("block_size", "item_photons")}}

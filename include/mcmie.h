@@ -280,14 +280,18 @@ mc_status mc_run_static(const mc_medium *medium, const mc_geometry *geom,
                         int64_t *d_image, int64_t *d_radial, int64_t *d_totals,
                         uint32_t *d_error, void *stream);
 
-/* Many media in one launch (work items: a medium and a chunk of its photons;
- * each CTA takes items from a queue, largest estimated cost first, keeps the
- * medium's table staged in shared memory while consecutive items share it).
- * All instances share geometry, camera and run parameters (run->n_photons,
- * photon_offset and seed are ignored; each instance has its own), and one
- * phase kind and table size. item_photons: photons per work item (0: 2^17).
- * Tallies per instance as for mc_run, bit-identical to running each instance
- * with mc_run. d_work: mc_batch_workspace_bytes(n) bytes. At most 64 media. */
+/* Many media in one launch: every CTA goes through the media in order of
+ * decreasing estimated cost (photons x (1 + optical depth along x)); its warps
+ * take chunks of item_photons photons of the current medium from that
+ * medium's counter (0: 128; else 32 .. 2^20), and when the medium's photons
+ * are all taken the CTA flushes its tallies into the medium's, stages the
+ * next medium's table in shared memory and goes on, so the media follow one
+ * another without launch gaps. All instances share geometry, camera and run
+ * parameters (run->n_photons, photon_offset and seed are ignored; each
+ * instance has its own), and one phase kind and table size. Tallies per
+ * instance as for mc_run, bit-identical to running each instance with
+ * mc_run. d_work: mc_batch_workspace_bytes(n) bytes (one counter per medium,
+ * cleared on the stream by each call). At most 64 media. */
 typedef struct {
     mc_medium medium;
     uint64_t n_photons, photon_offset, seed;

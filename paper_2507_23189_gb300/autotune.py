@@ -1,10 +1,10 @@
 """Launch-shape autotuner for the batched walk.
 
-Times candidate (threads per CTA, photons per work item) pairs on a scaled-
-down copy of the batch (every medium keeps its optical properties, photon
-budgets are divided by `scale`), picks the fastest, and caches the choice in
-a JSON file keyed by GPU name and a hash of the configuration. Results do not
-depend on the choice (integer tallies), only the time does.
+Times candidate (threads per CTA, photons a warp takes per grab) pairs on a
+scaled-down copy of the batch (every medium keeps its optical properties,
+photon budgets are divided by `scale`), picks the fastest, and caches the
+choice in a JSON file keyed by GPU name and a hash of the configuration.
+Results do not depend on the choice (integer tallies), only the time does.
 """
 import hashlib
 import json
@@ -12,7 +12,7 @@ import os
 
 CACHE_ENV = "MCMIE_AUTOTUNE_CACHE"
 BLOCKS = (256, 512, 1024)
-ITEMS = (1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18)
+ITEMS = (32, 64, 128, 256, 512)
 
 
 def cache_path():
@@ -81,8 +81,6 @@ def tune_batch(batch, media, n_photons, seeds=1, scale=8, reps=2, use_cache=True
                 best = dict(block_size=block, item_photons=item, ms=ms)
     if best is None:
         raise RuntimeError("no launchable configuration")
-    # items were sized for 1/scale of the photons: scale back
-    best["item_photons"] = int(best["item_photons"] * scale)
     db[key] = best
     if use_cache:
         _store(db)

@@ -346,7 +346,7 @@ mc_status mc_run_host(const mc_medium *medium, const void *table, const mc_geome
 size_t mc_batch_workspace_bytes(int n_instances)
 {
     if (n_instances < 1 || n_instances > mcx::kMaxBatch) return 0;
-    return kAlign;  // the work-item queue counter
+    return up(sizeof(unsigned long long) * (size_t)n_instances);  // one photon counter per medium
 }
 
 mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom, const mc_camera *camera,
@@ -354,7 +354,7 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom, 
                        size_t work_bytes, void *stream)
 {
     if (n < 1 || n > mcx::kMaxBatch || !inst || !d_error || !d_work || !aligned(d_work, 16) ||
-        !aligned(d_error, 4))
+        !aligned(d_error, 4) || (item_photons != 0 && (item_photons < 32 || item_photons > (1ull << 20))))
         return MC_ERR_ARG;
     if (work_bytes < mc_batch_workspace_bytes(n)) return MC_ERR_NOMEM;
     mc_status s;
@@ -381,7 +381,7 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom, 
                 (e = cudaMemsetAsync(inst[i].d_totals, 0, sizeof(int64_t) * MC_N_TOTALS, st)))
                 return MC_ERR_CUDA;
         }
-    if ((e = cudaMemsetAsync(d_work, 0, sizeof(unsigned long long), st))) return MC_ERR_CUDA;
+    if ((e = cudaMemsetAsync(d_work, 0, sizeof(unsigned long long) * (size_t)n, st))) return MC_ERR_CUDA;
 
     // largest estimated cost first: photons x (1 + optical depth along the beam)
     int order[mcx::kMaxBatch];
@@ -394,24 +394,23 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom, 
         for (int j = i; j > 0 && cost[order[j]] > cost[order[j - 1]]; --j) {
             int t = order[j]; order[j] = order[j - 1]; order[j - 1] = t;
         }
-    unsigned long long ip = item_photons;
-    if (ip == 0) ip = 1ull << 17;
     mcx::BatchArgs *a = new (std::nothrow) mcx::BatchArgs;
     if (!a) return MC_ERR_NOMEM;
     std::memset(a, 0, sizeof *a);
-    uint64_t n_max = 0;
-    for (int i = 0; i < n; ++i) n_max = inst[i].n_photons > n_max ? inst[i].n_photons : n_max;
+    uint64_t n_max = 0, n_all = 0;
+    for (int i = 0; i < n; ++i) {
+        n_max = inst[i].n_photons > n_max ? inst[i].n_photons : n_max;
+        n_all += inst[i].n_photons;
+    }
     fill_common(a->c, &inst[0].medium, geom, camera, run, d_error, n_max);
     a->n_media = n;
-    a->item_photons = ip;
-    a->queue = static_cast<unsigned long long *>(d_work);
-    a->item_begin[0] = 0;
+    a->chunk = item_photons ? (unsigned)item_photons : 128u;
+    a->counters = static_cast<unsigned long long *>(d_work);
     for (int k = 0; k < n; ++k) {
         const mc_instance &I = inst[order[k]];
         fill_medium(a->m[k], &I.medium, I.n_photons, I.photon_offset, I.seed, I.d_image, I.d_radial, I.d_totals);
-        a->item_begin[k + 1] = a->item_begin[k] + (I.n_photons + ip - 1) / ip;
     }
-    if (a->item_begin[n] == 0) {
+    if (n_all == 0) {
         delete a;
         return MC_OK;
     }

@@ -55,16 +55,14 @@ struct WalkArgs {
     unsigned long long *counter;  // photon counter in the caller's workspace
 };
 
-// Many media in one launch: work items (medium, chunk of item_photons
-// photons) are numbered medium by medium in the order of m[]; medium i owns
-// items [item_begin[i], item_begin[i+1]).
+// Many media in one launch, processed in the order of m[]: medium i's photons
+// are taken in warp chunks of `chunk` from counters[i] (caller's workspace).
 constexpr int kMaxBatch = 64;
 struct BatchArgs {
     CommonArgs c;
     int n_media;
-    unsigned long long item_photons;
-    unsigned long long *queue;    // work-item counter in the caller's workspace
-    unsigned long long item_begin[kMaxBatch + 1];
+    unsigned chunk;               // photons a warp takes from a counter at once (>= 32)
+    unsigned long long *counters; // [n_media] photon counters
     MediumArgs m[kMaxBatch];
 };
 

@@ -484,9 +484,10 @@ __device__ void flush(const CommonArgs &C, const MediumArgs &M, const Smem &S, T
 // The photon walk over indices [.., limit) of medium M: every warp refills
 // lanes whose photon ended from chunks of `chunk` indices obtained by
 // grab() (called by lane 0), until the range is exhausted.
-template <int PHASE, bool SMEM_IMAGE, bool TRACE, bool RK, class Grab>
-__device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs &M, const Smem &S,
-                                          unsigned long long limit, unsigned chunk, Grab grab,
+// rk: the Philox round keys of M's seed (M.rk, or a copy of them).
+template <int PHASE, bool SMEM_IMAGE, bool TRACE, class Grab>
+__device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs &M, const uint32_t (&rk)[20],
+                                          const Smem &S, unsigned long long limit, unsigned chunk, Grab grab,
                                           Tally &T)
 {
     const int lane = threadIdx.x & 31;
@@ -553,8 +554,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
 
         // -------- one event
         const uint32_t e_now = ev;
-        const uint4 rnd = RK ? philox10(make_uint4(pk0, pk1, e_now, 0u), M.rk)
-                             : philox10(make_uint4(pk0, pk1, e_now, 0u), M.key0, M.key1);
+        const uint4 rnd = philox10(make_uint4(pk0, pk1, e_now, 0u), rk);
         ++ev;
         ++T.steps;
         const float u0 = u01(rnd.x), u1 = u01(rnd.y), u2 = u01(rnd.z), u3 = u01(rnd.w);
@@ -716,19 +716,21 @@ __global__ void __launch_bounds__(1024) walk_kernel(const __grid_constant__ Walk
     }
     Tally T{0u, 0ll, 0ll, 0ll, 0ll, 0ll};
     unsigned long long *counter = A.counter;
-    walk_loop<PHASE, SMEM_IMAGE, TRACE, true>(A.c, A.m, S, A.m.n_photons, CHUNK,
+    walk_loop<PHASE, SMEM_IMAGE, TRACE>(A.c, A.m, A.m.rk, S, A.m.n_photons, CHUNK,
                                         [counter]() { return atomicAdd(counter, (unsigned long long)CHUNK); },
                                         T);
     flush<SMEM_IMAGE>(A.c, A.m, S, T);
 }
 
-// Many media: each CTA takes work items (medium, chunk of photons) from a
-// global queue; consecutive items of one medium reuse the staged table and
-// the shared-memory tallies, a change of medium flushes them and stages the
-// next table. Within an item the CTA's warps share the photons through a
-// shared-memory counter.
-constexpr unsigned BATCH_CHUNK = 32;
-
+// Many media in one launch: every CTA goes through the media in the order
+// given (largest estimated cost first). Its warps take chunks of the current
+// medium's photons from that medium's global counter, as in the one-medium
+// launch; once the counter is exhausted and the CTA's warps have finished
+// their photons, the CTA flushes its tallies into the medium's, stages the
+// next medium's table and goes on. CTAs flow from one medium into the next
+// without launch gaps, every medium's photons spread over all CTAs at warp-
+// chunk granularity; a CTA skips a medium whose photons were all taken
+// before it arrived.
 template <int PHASE, bool SMEM_IMAGE>
 __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ BatchArgs B)
 {
@@ -737,45 +739,33 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ Bat
     zero_tallies(S, B.c);
     if (threadIdx.x == 0) mbar_init(S.bar);
     __syncthreads();
-    const unsigned long long n_items = B.item_begin[B.n_media];
     Tally T{0u, 0ll, 0ll, 0ll, 0ll, 0ll};
-    int cur = -1;
     uint32_t parity = 0;
-    while (true) {
-        if (threadIdx.x == 0) *S.item = atomicAdd(B.queue, 1ull);
+    const unsigned chunk = B.chunk;
+    for (int m = 0; m < B.n_media; ++m) {
+        const MediumArgs &M = B.m[m];
+        unsigned long long *ctr = B.counters + m;
+        if (threadIdx.x == 0) *S.item = *reinterpret_cast<volatile unsigned long long *>(ctr);
         __syncthreads();
-        const unsigned long long item = *S.item;
-        if (item >= n_items) break;
-        int inst = 0, hi = B.n_media - 1;   // last medium whose first item <= item
-        while (inst < hi) {
-            const int mid = (inst + hi + 1) >> 1;
-            if (B.item_begin[mid] <= item) inst = mid; else hi = mid - 1;
-        }
-        if (inst != cur) {
-            if (cur >= 0) {
-                flush<SMEM_IMAGE>(B.c, B.m[cur], S, T);
-                zero_tallies(S, B.c);
-            }
-            if (PHASE != MC_PHASE_HG) {
-                if (!stage_bulk(S.table, B.m[inst].table, B.c.table_bytes, S.bar, parity, B.c.error))
-                    return;
-                parity ^= 1u;
-                if (!bind_table<PHASE>(S, B.c)) return;
-            }
-            cur = inst;
-        }
-        const MediumArgs &M = B.m[inst];
-        const unsigned long long start = (item - B.item_begin[inst]) * B.item_photons;
-        const unsigned long long end = min(start + B.item_photons, M.n_photons);
-        if (threadIdx.x == 0) *S.pool = start;
+        const bool taken = *S.item >= M.n_photons;
         __syncthreads();
-        unsigned long long *pool = S.pool;
-        walk_loop<PHASE, SMEM_IMAGE, false, false>(
-            B.c, M, S, end, BATCH_CHUNK,
-            [pool]() { return atomicAdd(pool, (unsigned long long)BATCH_CHUNK); }, T);
+        if (taken) continue;
+        if (PHASE != MC_PHASE_HG) {
+            if (!stage_bulk(S.table, M.table, B.c.table_bytes, S.bar, parity, B.c.error)) return;
+            parity ^= 1u;
+            if (!bind_table<PHASE>(S, B.c)) return;
+        }
+        // the medium's round keys, read once (warp-uniform values)
+        uint32_t rk[20];
+#pragma unroll
+        for (int i = 0; i < 20; ++i) rk[i] = M.rk[i];
+        walk_loop<PHASE, SMEM_IMAGE, false>(
+            B.c, M, rk, S, M.n_photons, chunk, [ctr, chunk]() { return atomicAdd(ctr, (unsigned long long)chunk); },
+            T);
+        flush<SMEM_IMAGE>(B.c, M, S, T);
+        zero_tallies(S, B.c);
         __syncthreads();
     }
-    if (cur >= 0) flush<SMEM_IMAGE>(B.c, B.m[cur], S, T);
 }
 
 
@@ -1941,8 +1931,12 @@ cudaError_t launch_batch_one(const BatchArgs &a, const LaunchCfg &cfg, size_t sm
 {
     auto kern = batch_kernel<PHASE, SMEM_IMAGE>;
     unsigned grid = 0;
-    const unsigned long long items = a.item_begin[a.n_media];
-    cudaError_t e = launch_persistent(kern, &a, cfg, smem, items * (cfg.block / 32), &grid);
+    unsigned long long chunks = 0;   // warp chunks of the largest medium: more warps would idle
+    for (int i = 0; i < a.n_media; ++i) {
+        const unsigned long long c = (a.m[i].n_photons + a.chunk - 1) / a.chunk;
+        if (c > chunks) chunks = c;
+    }
+    cudaError_t e = launch_persistent(kern, &a, cfg, smem, chunks, &grid);
     if (e != cudaSuccess) return e;
     kern<<<grid, cfg.block, smem, st>>>(a);
     return cudaGetLastError();

@@ -1,8 +1,8 @@
 """The batched launch's autotuner, host logic on CPU: a stand-in batch whose
-'launches' take a known time per (threads per CTA, photons per item) pair,
-and a stand-in for the CUDA timing calls. It must pick the fastest launchable
-pair, skip pairs that cannot launch, scale the item size back up, and cache
-the choice under a key of the GPU and the configuration."""
+'launches' take a known time per (threads per CTA, photons per warp chunk)
+pair, and a stand-in for the CUDA timing calls. It must pick the fastest
+launchable pair, skip pairs that cannot launch, and cache the choice under a
+key of the GPU and the configuration."""
 import types
 
 import pytest
@@ -27,8 +27,8 @@ class _Event:
 
 
 def _cost(block, item):
-    # fastest at 512 threads and 2^15 photons per item (after scaling by 1/8)
-    return 1.0 + abs(block - 512) / 256.0 + abs(item.bit_length() - 16) * 0.25
+    # fastest at 512 threads and warp chunks of 128 photons
+    return 1.0 + abs(block - 512) / 256.0 + abs(item.bit_length() - 8) * 0.25
 
 
 class _FakeBatch:
@@ -38,7 +38,7 @@ class _FakeBatch:
         self.n, self.camera, self.geometry, self.device = n, camera, geometry, device
 
     def run(self, media, n_photons, seeds, offsets, item_photons=0, block_size=0):
-        if block_size == 256 and item_photons == 1 << 14:
+        if block_size == 256 and item_photons == 32:
             raise RuntimeError("not launchable")
         _FakeBatch.runs.append((block_size, item_photons, tuple(n_photons)))
         _Clock.now += _cost(block_size, item_photons)
@@ -70,11 +70,11 @@ def test_picks_the_fastest_launchable_shape_and_caches_it(tuner):
     batch, media, n = _setup(gpu)
     r = tuner.tune_batch(batch, media, n, scale=8, reps=2)
     assert r["cached"] is False
-    assert r["block_size"] == 512 and r["item_photons"] == 8 * (1 << 15)
-    assert r["ms"] == pytest.approx(_cost(512, 1 << 15))
+    assert r["block_size"] == 512 and r["item_photons"] == 128
+    assert r["ms"] == pytest.approx(_cost(512, 128))
     # every launchable pair ran on the scaled budgets (1 untimed + reps timed), the unlaunchable one never
     shapes = {(b, i) for b, i, _ in _FakeBatch.runs}
-    assert (256, 1 << 14) not in shapes
+    assert (256, 32) not in shapes
     assert len(shapes) == len(tuner.BLOCKS) * len(tuner.ITEMS) - 1
     assert all(p == (100_000, 250_000) for _, _, p in _FakeBatch.runs)
     # the same configuration comes from the cache without running anything
