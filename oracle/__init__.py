@@ -49,6 +49,8 @@ def lib():
                                                  C.c_int, dp, dp, dp, dp]
         L.oracle_grid_adjoint.restype = C.c_int
         L.oracle_grid_adjoint.argtypes = [C.POINTER(WalkCfg), dp, C.c_int, dp, dp]
+        L.oracle_grid_adjoint_nulls.restype = C.c_int
+        L.oracle_grid_adjoint_nulls.argtypes = [C.POINTER(WalkCfg), dp, C.c_int, dp, dp]
         L.oracle_paper_cdf.restype = C.c_int
         L.oracle_paper_cdf.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                        C.c_int, dp]
@@ -104,6 +106,7 @@ class WalkCfg(C.Structure):
         ("gx", C.c_int), ("gy", C.c_int), ("gz", C.c_int),
         ("k_ext", C.c_double), ("k_sca", C.c_double),
         ("bx", C.c_int), ("by", C.c_int), ("bz", C.c_int),
+        ("majorant_scale", C.c_double), ("trace_nulls", C.c_int),
     ]
 
 
@@ -316,16 +319,19 @@ def adjoint(adj, n_w=64, w=None, base_table=None, **walk_kw):
     return dict(grad=g, grad_sq=g2, value=v.value, n_photons=cfg.n_photons)
 
 
-def grid_adjoint(adj, max_events=512, **walk_kw):
+def grid_adjoint(adj, max_events=512, nulls=False, **walk_kw):
     """Gradient of sum(adj * image) w.r.t. the voxel densities of
-    walk_kw["grid"]["density"]: dict(grad [gz, gy, gx], value)."""
+    walk_kw["grid"]["density"]: dict(grad [gz, gy, gx], value). nulls: score
+    the flights' transmission at the null collisions of delta tracking
+    against majorants grid["majorant_scale"] (> 1) times the cell maxima."""
     cfg, keep = _walk_cfg(**walk_kw)
     a = np.ascontiguousarray(adj, dtype=np.float64).ravel()
     if a.size != cfg.nx * cfg.nz or not cfg.density:
         raise ValueError("adjoint image size or grid missing")
     g = np.zeros(cfg.gz * cfg.gy * cfg.gx)
     v = C.c_double(0.0)
-    if lib().oracle_grid_adjoint(C.byref(cfg), _dp(a), max_events, _dp(g), C.byref(v)):
+    fn = lib().oracle_grid_adjoint_nulls if nulls else lib().oracle_grid_adjoint
+    if fn(C.byref(cfg), _dp(a), max_events, _dp(g), C.byref(v)):
         raise ValueError("oracle_grid_adjoint failed (arguments, or a photon with more real events than "
                          "max_events)")
     return dict(grad=g.reshape(cfg.gz, cfg.gy, cfg.gx), value=v.value)
@@ -373,6 +379,7 @@ def _walk_cfg(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,
         cfg.gz, cfg.gy, cfg.gx = dens.shape
         cfg.k_ext, cfg.k_sca = grid["k_ext"], grid["k_sca"]
         cfg.bx, cfg.by, cfg.bz = grid.get("block", (1, 1, 1))
+        cfg.majorant_scale = float(grid.get("majorant_scale", 1.0))
     cfg._keep = keep
     return cfg, keep
 

@@ -405,6 +405,33 @@ static void segment_voxels(const oracle_walk_cfg *c, const double lo[3], const d
     }
 }
 
+/* The point term of a real collision in voxel vi followed by camera terms
+ * B: the flight's density ends in mu_ext there (d log / d n_v = k_ext /
+ * mu_ext) and, with absorption, the albedo k_sca n_v / mu_ext adds 1 / n_v -
+ * k_ext / mu_ext. */
+static void point_term(const oracle_walk_cfg *c, size_t vi, double B, double *grad)
+{
+    const double n_v = c->density[vi];
+    const double mu = c->k_ext * n_v + c->mu_a;
+    grad[vi] += B * c->k_ext / mu;
+    if (c->mu_a > 0.0 && n_v > 0.0)
+        grad[vi] += B * (1.0 / n_v - c->k_ext / mu);
+}
+
+/* Camera term Ai of a collision at height ry in voxel v: -Ai k_ext times the
+ * length of its column up to the camera face inside each voxel it crosses
+ * (the rest of its own voxel, then every voxel above). */
+static void camera_column(const oracle_walk_cfg *c, const double lo[3], const int v[3], double ry, double Ai,
+                          double *grad)
+{
+    const double vy = c->ly / c->gy;
+    const size_t vi = ((size_t)v[2] * c->gy + v[1]) * c->gx + v[0];
+    const double top = (v[1] == c->gy - 1) ? 0.5 * c->ly : lo[1] + (v[1] + 1) * vy;
+    grad[vi] -= Ai * c->k_ext * (top - ry);
+    for (int j = v[1] + 1; j < c->gy; ++j)
+        grad[((size_t)v[2] * c->gy + j) * c->gx + v[0]] -= Ai * c->k_ext * vy;
+}
+
 int oracle_grid_adjoint(const oracle_walk_cfg *c, const double *adj, int max_events, double *grad,
                         double *value)
 {
@@ -412,8 +439,6 @@ int oracle_grid_adjoint(const oracle_walk_cfg *c, const double *adj, int max_eve
         return -1;
     const size_t nv = (size_t)c->gx * c->gy * c->gz;
     const double lo[3] = {0.0, -0.5 * c->ly, -0.5 * c->lz};
-    const double hi1 = 0.5 * c->ly;
-    const double vy = c->ly / c->gy;
     const uint32_t key[2] = {(uint32_t)c->seed, (uint32_t)(c->seed >> 32)};
     const uint64_t batch = 2048;
     oracle_trace_rec *tr = malloc(batch * (size_t)max_events * sizeof *tr);
@@ -479,22 +504,14 @@ int oracle_grid_adjoint(const oracle_walk_cfg *c, const double *adj, int max_eve
                 int v[3];
                 voxel_of(c, lo, ri, v);
                 const size_t vi = ((size_t)v[2] * c->gy + v[1]) * c->gx + v[0];
-                const double n_v = c->density[vi];
-                const double mu = c->k_ext * n_v + c->mu_a;
                 if (B != 0.0) {
                     /* flight: point term and transmission along the flight */
-                    grad[vi] += B * c->k_ext / mu;
-                    if (c->mu_a > 0.0 && n_v > 0.0)
-                        grad[vi] += B * (1.0 / n_v - c->k_ext / mu);
+                    point_term(c, vi, B, grad);
                     segment_voxels(c, lo, prev, ri, -B * c->k_ext, grad, ts, ts_cap);
                 }
                 /* camera term i: its column up to the camera face */
-                if (A[i] != 0.0) {
-                    const double top = (v[1] == c->gy - 1) ? hi1 : lo[1] + (v[1] + 1) * vy;
-                    grad[vi] -= A[i] * c->k_ext * (top - ri[1]);
-                    for (int j = v[1] + 1; j < c->gy; ++j)
-                        grad[((size_t)v[2] * c->gy + j) * c->gx + v[0]] -= A[i] * c->k_ext * vy;
-                }
+                if (A[i] != 0.0)
+                    camera_column(c, lo, v, ri[1], A[i], grad);
                 Pb += A[i];
                 for (int k = 0; k < 3; ++k)
                     prev[k] = ri[k];
@@ -502,6 +519,97 @@ int oracle_grid_adjoint(const oracle_walk_cfg *c, const double *adj, int max_eve
         }
     }
     free(tr); free(A); free(ts);
+    *value = val;
+    return rc;
+}
+
+/* ------------------------------------------------------------------------
+ * The same gradient with the flights' transmission scored at null
+ * collisions. Delta tracking samples tentative collisions from the
+ * majorant's exponential (independent of the densities); each is real with
+ * probability mu_ext / mubar and null otherwise. Along a photon's path the
+ * log-density therefore depends on n_v through log(mu_ext / mubar) at every
+ * real collision in v and log(1 - mu_ext / mubar) at every null collision
+ * in v, whose derivatives are k_ext / mu_ext and -k_ext / (mubar - mu_ext).
+ * With B the camera terms that follow a flight (all of them from its real
+ * collision on), a null collision in that flight adds -B k_ext / (mubar -
+ * mu_ext) at its voxel; the real collision's point term and the camera
+ * columns are those of oracle_grid_adjoint. The paths are the oracle walk's
+ * own with null collisions traced; mubar > mu_ext everywhere needs
+ * majorant_scale > 1.
+ * ------------------------------------------------------------------------ */
+int oracle_grid_adjoint_nulls(const oracle_walk_cfg *c0, const double *adj, int max_events, double *grad,
+                              double *value)
+{
+    if (!c0 || !c0->density || !adj || !grad || !value || max_events < 2 || !(c0->majorant_scale > 1.0))
+        return -1;
+    oracle_walk_cfg cfg = *c0;
+    cfg.trace_nulls = 1;
+    const oracle_walk_cfg *c = &cfg;
+    const size_t nv = (size_t)c->gx * c->gy * c->gz;
+    const double lo[3] = {0.0, -0.5 * c->ly, -0.5 * c->lz};
+    const uint64_t batch = 1024;
+    oracle_trace_rec *tr = malloc(batch * (size_t)max_events * sizeof *tr);
+    if (!tr)
+        return -1;
+    memset(grad, 0, nv * sizeof *grad);
+    double val = 0.0;
+    int rc = 0;
+    for (uint64_t first = 0; first < c->n_photons && rc == 0; first += batch) {
+        const uint64_t cnt = (c->n_photons - first < batch) ? c->n_photons - first : batch;
+        oracle_walk_cfg cb = *c;
+        cb.photon_offset = c->photon_offset + first;
+        cb.n_photons = cnt;
+        oracle_walk_out out;
+        memset(&out, 0, sizeof out);
+        if (oracle_walk(&cb, &out, tr, (int)cnt, max_events)) {
+            rc = -1;
+            break;
+        }
+        for (uint64_t q = 0; q < cnt && rc == 0; ++q) {
+            const oracle_trace_rec *R = tr + q * (size_t)max_events;
+            /* the photon's camera terms, and where its records end */
+            double P = 0.0;
+            int n_rec = -1;
+            for (int e = 0; e < max_events; ++e) {
+                const int st = (int)R[e].status;
+                if (st == 0 || st == 4 || st == 5)
+                    P += adj[(int)R[e].pix] * R[e].nee;
+                if (st == 0 || st == 7)
+                    continue;
+                n_rec = e;   /* the photon ended at record e */
+                break;
+            }
+            if (n_rec < 0) {
+                rc = -1;   /* more events than max_events */
+                break;
+            }
+            val += P;
+            double Pb = 0.0;   /* camera terms before the current flight */
+            for (int e = 0; e <= n_rec; ++e) {
+                const oracle_trace_rec *r = &R[e];
+                const int st = (int)r->status;
+                const double B = P - Pb;
+                if (st == 7) {
+                    if (B != 0.0)
+                        grad[(size_t)r->pix] -= B * c->k_ext / (r->nee - r->w);
+                    continue;
+                }
+                if (!(st == 0 || st == 4 || st == 5))
+                    break;   /* left the cuvette or truncated: no camera term follows */
+                int v[3];
+                voxel_of(c, lo, r->r, v);
+                const size_t vi = ((size_t)v[2] * c->gy + v[1]) * c->gx + v[0];
+                const double A = adj[(int)r->pix] * r->nee;
+                if (B != 0.0)
+                    point_term(c, vi, B, grad);
+                if (A != 0.0)
+                    camera_column(c, lo, v, r->r[1], A, grad);
+                Pb += A;
+            }
+        }
+    }
+    free(tr);
     *value = val;
     return rc;
 }

@@ -176,6 +176,11 @@ typedef struct {
     int gx, gy, gz;
     double k_ext, k_sca;
     int bx, by, bz;
+    /* majorants: the largest mu_ext of each cell times majorant_scale (0 or
+     * 1: the largest itself). trace_nulls != 0: traces of a heterogeneous
+     * walk also record every null collision (status 7, in event order) */
+    double majorant_scale;
+    int trace_nulls;
 } oracle_walk_cfg;
 
 /* Totals, in weight units (one photon carries weight 1). */
@@ -205,7 +210,9 @@ typedef struct {
 /* Per-event trace record, double precision. */
 typedef struct {
     double status;   /* 0 collided, 1 reflect, 2 far, 3 side, 4 roulette kill,
-                        5 truncated (max_scatter), 6 capped (max_events) */
+                        5 truncated (max_scatter), 6 capped (max_events),
+                        7 null collision (trace_nulls; then w holds mu_ext at
+                        the point, nee the majorant, pix the voxel index) */
     double r[3];     /* position after the flight (collision or exit point) */
     double d[3];     /* direction after the event */
     double w;        /* weight after the event */
@@ -264,6 +271,19 @@ int oracle_adjoint_weighted(const oracle_walk_cfg *cfg, const double *adj, int n
  * per photon (real events); -1 if a photon needs more. Roulette held fixed. */
 int oracle_grid_adjoint(const oracle_walk_cfg *c, const double *adj, int max_events, double *grad,
                         double *value);
+
+/* The same gradient with the flights' transmission scored at the null
+ * collisions of delta tracking instead of integrated along each flight:
+ * against majorants mubar = majorant_scale x the cell's largest mu_ext
+ * (c->majorant_scale > 1, so every voxel has mubar > mu_ext), a null
+ * collision at a point of voxel v has probability 1 - mu_ext / mubar, whose
+ * derivative with respect to n_v gives the score -k_ext / (mubar - mu_ext);
+ * it multiplies the camera terms that follow (B of its flight). Real
+ * collisions and camera columns as oracle_grid_adjoint. An unbiased
+ * estimate of the same gradient from paths of the walk with those
+ * majorants. max_events: trace room per photon (null and real events). */
+int oracle_grid_adjoint_nulls(const oracle_walk_cfg *c, const double *adj, int max_events, double *grad,
+                              double *value);
 
 #ifdef __cplusplus
 }

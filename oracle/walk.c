@@ -263,10 +263,12 @@ static void run_photon(const oracle_walk_cfg *c, const double *maj, uint64_t p, 
     }
 
     const int het = c->density != NULL;
+    uint32_t nrec = 0;   /* records written when null collisions are traced too */
     for (uint32_t e = 0;; ++e) {
         /* traces record the real events: every flight, or with delta
-         * tracking every real collision and the exit */
-        const uint32_t ri = het ? n_coll : e;
+         * tracking every real collision and the exit (and, with
+         * trace_nulls, every null collision in between) */
+        const uint32_t ri = het ? (c->trace_nulls ? nrec : n_coll) : e;
         oracle_trace_rec *rec = (tr && ri < (uint32_t)n_tr_ev) ? &tr[ri] : NULL;
         if (e >= c->max_events) {
             pt[ORACLE_T_TRUNC] += w;
@@ -297,8 +299,25 @@ static void run_photon(const oracle_walk_cfg *c, const double *maj, uint64_t p, 
                 mua_here = mu_here - c->k_sca * c->density[((size_t)vz * c->gy + vy) * c->gx + vx];
                 const double acc = mu_here / mubar;
                 margin = min2(margin, fabs(u3 - acc));
-                if (!(u3 < acc))
-                    continue;   /* null collision */
+                if (!(u3 < acc)) {   /* null collision */
+                    if (c->trace_nulls) {
+                        if (rec) {
+                            memset(rec, 0, sizeof *rec);
+                            rec->status = 7;
+                            for (int i = 0; i < 3; ++i) {
+                                rec->r[i] = r[i];
+                                rec->d[i] = d[i];
+                            }
+                            rec->w = mu_here;
+                            rec->nee = mubar;
+                            rec->pix = (double)(((size_t)vz * c->gy + vy) * c->gx + vx);
+                            rec->nee_bin = rec->rad_bin = -1;
+                            rec->margin = margin;
+                        }
+                        nrec++;
+                    }
+                    continue;
+                }
                 u3 = u3 / acc;  /* uniform on [0, 1) given acceptance */
             }
         } else {
@@ -494,6 +513,7 @@ static void run_photon(const oracle_walk_cfg *c, const double *maj, uint64_t p, 
             rec->rad_bin = -1;
             rec->margin = margin;
         }
+        nrec++;
         if (status != 0)
             break;
     }
@@ -569,6 +589,14 @@ int oracle_walk(const oracle_walk_cfg *c, oracle_walk_out *out,
                     if (mu > *q)
                         *q = mu;
                 }
+        if (c->majorant_scale > 0.0 && c->majorant_scale != 1.0) {
+            if (!(c->majorant_scale > 1.0) || !isfinite(c->majorant_scale)) {
+                free(maj);
+                return -1;
+            }
+            for (size_t i = 0; i < (size_t)mx * my * mz; ++i)
+                maj[i] *= c->majorant_scale;
+        }
     } else if (!(c->mu_s + c->mu_a > 0.0)) {
         return -1;
     }

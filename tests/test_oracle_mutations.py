@@ -173,10 +173,19 @@ MUTATIONS = [
     ("adjoint.c", "for (int j = v[1] + 1; j < c->gy; ++j)", "for (int j = v[1]; j < c->gy; ++j)", GADJ,
      "camera column counts the collision voxel twice"),
     ("adjoint.c", "grad[vi] += B * c->k_ext / mu;", "grad[vi] += B / mu;", GADJ, "collision point term"),
-    ("adjoint.c", "grad[vi] -= A[i] * c->k_ext * (top - ri[1]);", "grad[vi] -= A[i] * c->k_ext * (top + ri[1]);",
+    ("adjoint.c", "grad[vi] -= Ai * c->k_ext * (top - ry);", "grad[vi] -= Ai * c->k_ext * (top + ry);",
      GADJ, "camera column inside the collision voxel"),
     ("adjoint.c", "segment_voxels(c, lo, prev, ri, -B * c->k_ext, grad, ts, ts_cap);",
      "segment_voxels(c, lo, prev, ri, B * c->k_ext, grad, ts, ts_cap);", GADJ, "sign of the flight transmission"),
+    # null-collision scores of the density gradient
+    ("adjoint.c", "grad[(size_t)r->pix] -= B * c->k_ext / (r->nee - r->w);",
+     "grad[(size_t)r->pix] += B * c->k_ext / (r->nee - r->w);", GADJ, "sign of the null-collision score"),
+    ("adjoint.c", "grad[(size_t)r->pix] -= B * c->k_ext / (r->nee - r->w);",
+     "grad[(size_t)r->pix] -= B * c->k_ext / r->nee;", GADJ, "null score with the majorant alone"),
+    ("adjoint.c", "grad[(size_t)r->pix] -= B * c->k_ext / (r->nee - r->w);",
+     "grad[(size_t)r->pix] -= P * c->k_ext / (r->nee - r->w);", GADJ,
+     "null score weighted by all the photon's camera terms"),
+    ("walk.c", "maj[i] *= c->majorant_scale;", "maj[i] *= 1.0;", GADJ, "majorant scale ignored"),
 ]
 
 
