@@ -405,10 +405,16 @@ def plume_leg(E, dev, steps, flush, n_photons=None):
     adj = torch.rand((P.nz, P.nx), generator=torch.Generator().manual_seed(1)).to(dev)
     t_fwd_adj = timed(lambda: eng.run_grid(grid, med, n_adj, seed=2, stream=stream), max(1, min(steps, 3)))
     t_adj = timed(lambda: eng.grid_adjoint(grid, med, adj, n_adj, seed=2, stream=stream), max(1, min(steps, 3)))
+    t_null = timed(lambda: eng.grid_adjoint(grid, med, adj, n_adj, seed=2, stream=stream, nulls=NULL_MAJORANT_SCALE),
+                   max(1, min(steps, 3)))
     eng.check()
+    matched = matched_error(eng, grid, med, adj, n_adj, stream, t_adj, t_null)
     return {"prepare_ms": t_prep, "walk_ms": t_walk, "photons_per_s": n / (t_walk * 1e-3),
             "density_gradient": {"photons": n_adj, "forward_ms": t_fwd_adj, "gradient_ms": t_adj,
-                                 "cost_vs_forward": t_adj / t_fwd_adj},
+                                 "cost_vs_forward": t_adj / t_fwd_adj,
+                                 "null_scores": {"majorant_scale": NULL_MAJORANT_SCALE, "gradient_ms": t_null,
+                                                 "cost_vs_forward": t_null / t_fwd_adj},
+                                 "matched_error": matched},
             "tentative_steps_per_s": tentative / (t_walk * 1e-3), "tentative_steps_per_photon": tentative / n,
             "ballistic_fraction": float(res["totals"][6] / n), "expected_ballistic": math.exp(-P.tau_peak),
             "mixture_table_build_s": t_table, "k_ext_mm2": k_ext, "k_sca_mm2": k_sca, "g": tab.info["g"],
@@ -416,6 +422,46 @@ def plume_leg(E, dev, steps, flush, n_photons=None):
             "workload": "256^3 Gaussian plume (sigma 5 mm at x=22.5), 16 log-normal size bins (median 5 um, "
                         "sigma_ln 0.3), peak tau 30 on the beam, %d photons, %dx%d image, cells %s" %
                         (n, P.nx, P.nz, "x".join(map(str, P.block)))}
+
+
+NULL_MAJORANT_SCALE = 1.25
+
+
+def matched_error(eng, grid, med, adj, n, stream, t_exact, t_null, batches=8):
+    """Exact flight lengths against null-collision scores at equal error:
+    each estimator's batch-means variance over `batches` photon batches (the
+    same n photons in all), of 32^3-voxel block sums and of single voxels,
+    times its time per photon; the ratio (nulls / exact) is the cost of the
+    null scores at matched error (< 1: they reach an error sooner)."""
+    import torch
+    nb = n // batches
+
+    def stats(nulls):
+        grads = []
+        for b in range(batches):
+            _, g = eng.grid_adjoint(grid, med, adj, nb, seed=3, photon_offset=b * nb, stream=stream, nulls=nulls)
+            grads.append(g.double())
+        eng.check()
+        G = torch.stack(grads)                       # [batches, gz, gy, gx]
+        gz, gy, gx = G.shape[1:]
+        B = G.reshape(batches, gz // 32, 32, gy // 32, 32, gx // 32, 32).sum(dim=(2, 4, 6)).flatten(1)
+        mean_v, var_v = G.mean(0).flatten(), G.var(0).flatten()
+        return B.mean(0), B.var(0), mean_v, var_v
+
+    bm0, bv0, vm0, vv0 = stats(None)
+    bm1, bv1, vm1, vv1 = stats(NULL_MAJORANT_SCALE)
+    big = bm0.abs() >= bm0.abs().median()            # blocks with at least the median signal
+    a = vm0.abs()
+    thr = torch.kthvalue(a.cpu(), max(1, int(0.9 * a.numel()))).values.item()
+    vsel = (a >= thr) & (a > 0)                      # the 10 % of voxels with the largest gradient
+    ratio_b = float(torch.median(bv1[big] / bv0[big].clamp_min(1e-300)))
+    ratio_v = float(torch.median(vv1[vsel] / vv0[vsel].clamp_min(1e-300)))
+    return {"batches": batches, "photons_per_batch": nb,
+            "variance_ratio_blocks": ratio_b, "variance_ratio_voxels": ratio_v,
+            "cost_at_matched_error_blocks": ratio_b * t_null / t_exact,
+            "cost_at_matched_error_voxels": ratio_v * t_null / t_exact,
+            "note": "median over 32^3 blocks with at least the median |block sum|, and over the 10 % of voxels "
+                    "with the largest |gradient|, of var(nulls) / var(exact), times the time ratio"}
 
 
 def adjoint_comparison(E, dev, steps, flush):

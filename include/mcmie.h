@@ -416,6 +416,26 @@ mc_status mc_grid_adjoint(const mc_grid *grid, const void *d_grid_work, const mc
                           const float *d_adj_image, float *d_grad, double *d_value, uint32_t *d_error,
                           void *d_work, size_t work_bytes, void *stream);
 
+/* mc_grid_adjoint with the flights' transmission scored at the null
+ * collisions of delta tracking instead of integrated along each flight
+ * (same workspace, arguments and outputs). The gradient walk uses majorants
+ * majorant_scale (1 < scale <= 16) times the cell maxima, so every voxel
+ * has mubar > mu_ext; a null collision at a point of voxel v then has
+ * probability 1 - mu_ext / mubar, and its derivative with respect to n_v,
+ * the score -k_ext / (mubar - mu_ext), times the camera terms that follow
+ * its flight is added at v (one atomic per null collision instead of every
+ * voxel the flight crosses). Real collisions and camera columns as in
+ * mc_grid_adjoint. An unbiased estimate of the same gradient, from paths of
+ * the walk with those majorants (so not the photons mc_run_grid runs);
+ * max_events counts their tentative collisions. The paper has no
+ * gradients; this trades the exact flight integrals for cheaper, noisier
+ * per-voxel scores. */
+mc_status mc_grid_adjoint_nulls(const mc_grid *grid, const void *d_grid_work, const mc_medium *phase,
+                                const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
+                                const float *d_adj_image, double majorant_scale, float *d_grad,
+                                double *d_value, uint32_t *d_error, void *d_work, size_t work_bytes,
+                                void *stream);
+
 /* Image comparison (Sec. 3.1.4: every image normalised the same way, here
  * min-max to [0, 1]; Table 3: RMSE and Pearson r over the pixels; Table 4:
  * radial profiles, i.e. means over n_r equal-width rings about the image

@@ -28,7 +28,7 @@ EXPORTS = ("mc_table_bytes", "mie_table_build", "mc_medium_from_density", "mc_wo
            "mc_metrics_out_len", "mc_metrics_workspace_bytes", "mc_image_metrics", "mie_mixture_table_build",
            "mc_grid_workspace_bytes", "mc_grid_prepare", "mc_run_grid", "mc_grid_adjoint_workspace_bytes",
            "mc_grid_adjoint", "mc_check_within", "mc_wait_selftest", "mc_medium_from_optical_depth",
-           "mc_auto_frac_bits", "mc_phase_table_weighted")
+           "mc_auto_frac_bits", "mc_phase_table_weighted", "mc_grid_adjoint_nulls")
 
 
 class McError(RuntimeError):
@@ -156,6 +156,9 @@ def lib():
     L.mc_adjoint.restype = C.c_int
     L.mc_adjoint.argtypes = [P(Medium), P(Geometry), P(Camera), P(RunParams), vp, C.c_int, vp, vp, vp, vp,
                              C.c_size_t, vp]
+    L.mc_grid_adjoint_nulls.restype = C.c_int
+    L.mc_grid_adjoint_nulls.argtypes = [P(Grid), vp, P(Medium), P(Geometry), P(Camera), P(RunParams), vp,
+                                        C.c_double, vp, vp, vp, vp, C.c_size_t, vp]
     L.mc_phase_table_weighted.restype = C.c_int
     L.mc_phase_table_weighted.argtypes = [P(Medium), C.c_int, vp, vp, C.c_size_t, vp, vp]
     L.mc_paper_table_bytes.restype = C.c_size_t

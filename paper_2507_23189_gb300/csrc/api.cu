@@ -682,10 +682,37 @@ size_t mc_grid_adjoint_workspace_bytes(const mc_grid *g)
     return kAlign + 3 * up(sizeof(double) * n) + up(sizeof(double) * (size_t)rows);
 }
 
+namespace {
+mc_status grid_adjoint_common(const mc_grid *g, const void *d_grid_work, const mc_medium *phase,
+                              const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
+                              const float *d_adj_image, float *d_grad, double *d_value, uint32_t *d_error,
+                              void *d_work, size_t work_bytes, void *stream, int nulls, double maj_scale);
+}  // namespace
+
 mc_status mc_grid_adjoint(const mc_grid *g, const void *d_grid_work, const mc_medium *phase,
                           const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
                           const float *d_adj_image, float *d_grad, double *d_value, uint32_t *d_error,
                           void *d_work, size_t work_bytes, void *stream)
+{
+    return grid_adjoint_common(g, d_grid_work, phase, geom, camera, run, d_adj_image, d_grad, d_value, d_error,
+                               d_work, work_bytes, stream, 0, 1.0);
+}
+
+mc_status mc_grid_adjoint_nulls(const mc_grid *g, const void *d_grid_work, const mc_medium *phase,
+                                const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
+                                const float *d_adj_image, double majorant_scale, float *d_grad, double *d_value,
+                                uint32_t *d_error, void *d_work, size_t work_bytes, void *stream)
+{
+    if (!fin(majorant_scale) || !(majorant_scale > 1.0) || majorant_scale > 16.0) return MC_ERR_ARG;
+    return grid_adjoint_common(g, d_grid_work, phase, geom, camera, run, d_adj_image, d_grad, d_value, d_error,
+                               d_work, work_bytes, stream, 1, majorant_scale);
+}
+
+namespace {
+mc_status grid_adjoint_common(const mc_grid *g, const void *d_grid_work, const mc_medium *phase,
+                              const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
+                              const float *d_adj_image, float *d_grad, double *d_value, uint32_t *d_error,
+                              void *d_work, size_t work_bytes, void *stream, int nulls, double maj_scale)
 {
     int mx, my, mz;
     mc_status s;
@@ -714,6 +741,8 @@ mc_status mc_grid_adjoint(const mc_grid *g, const void *d_grid_work, const mc_me
     a.adj = d_adj_image;
     a.grad = d_grad;
     a.k_ext = (float)g->k_ext;
+    a.nulls = nulls;
+    a.maj_scale = (float)maj_scale;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto fail = [](cudaError_t x) { return x != cudaSuccess; };
     if (fail(cudaMemsetAsync(w, 0, kAlign + 3 * nb, st)) ||
@@ -723,3 +752,4 @@ mc_status mc_grid_adjoint(const mc_grid *g, const void *d_grid_work, const mc_me
     if (run->n_photons == 0) return MC_OK;
     return cuda_status(mcx::launch_grid_adjoint(a, mcx::grid_adjoint_max_grid(), d_value, st));
 }
+}  // namespace

@@ -111,6 +111,8 @@ struct GridAdjArgs {
     float *grad;                  // [gz][gy][gx] output (written by the fold)
     float k_ext;
     double *partials;             // [grid] value per CTA
+    int nulls;                    // 1: flight transmission scored at null collisions
+    float maj_scale;              // majorants x this in the walk (nulls: > 1)
 };
 
 struct LaunchCfg {

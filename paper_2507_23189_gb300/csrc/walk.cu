@@ -1203,7 +1203,15 @@ __device__ __forceinline__ void raster_unit(const GridArgs &G, double *grad, con
     }
 }
 
-template <int PHASE>
+// NULLS: the flights' transmission is scored at the null collisions of
+// delta tracking instead of integrated along each flight. Against majorants
+// scaled by maj_scale > 1 (so mubar > mu_ext in every voxel) a null
+// collision has probability 1 - mu_ext / mubar, whose derivative with
+// respect to the voxel's density is the score -k_ext / (mubar - mu_ext); it
+// multiplies the camera terms that follow its flight. One atomic per null
+// collision replaces the rasterised flight; both are unbiased estimates of
+// the same gradient.
+template <int PHASE, bool NULLS>
 __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_constant__ GridAdjArgs A)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1227,6 +1235,10 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
         if (!bind_table<PHASE>(S, C)) return;
     }
     if (!stage_bulk(s_maj, G.maj, C.extra_bytes, s_bar, parity, C.error)) return;
+    if (NULLS) {
+        for (int i = threadIdx.x; i < G.mx * G.my * G.mz; i += blockDim.x) s_maj[i] *= A.maj_scale;
+        __syncthreads();
+    }
 
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
@@ -1320,6 +1332,11 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                 const size_t v = chk((iz * G.gy + iy) * G.gx + ix, G.gx * G.gy * G.gz, C.error);
                 const float2 cell = __ldg(&G.cells[v]);
                 const float acc = mc_div(cell.x, mb);   // hardware reciprocal (a few ulp) unless strict
+                if (NULLS && !(u3 < acc) && pass == 1) {
+                    // null collision: its score times the camera terms after it
+                    const float B = Ptot - P;
+                    if (B != 0.f) atomicAdd(&A.gsum[v], widen(-B * mc_div(A.k_ext, mb - cell.x)));
+                }
                 if (u3 < acc) {
                     u3 = mc_div(u3, acc);
                     ++ncoll;
@@ -1339,7 +1356,9 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                             const float dens = cell.x - G.mu_a;   // k_ext n_v
                             if (dens > 0.f) gv = fmaf(B, mc_div(A.k_ext, dens), gv);
                             const float coef = -B * A.k_ext;
-                            if (ncoll == 1) {
+                            if (NULLS) {
+                                // the flight's transmission was scored at its null collisions
+                            } else if (ncoll == 1) {
                                 // first flight, along +x from the entry point in this
                                 // voxel row: the voxels before ix by the row suffix
                                 gv = fmaf(coef, fmaxf(fmaf(-(float)ix, G.vx, rx), 0.f), gv);
@@ -1404,7 +1423,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
         // partition-axis crossings per lane: the stretches of all flights are
         // numbered in lane order and handed out 32 at a time, each lane
         // finding its flight by a search over the exclusive prefix sums
-        if (__any_sync(FULL, nseg != 0)) {
+        if (!NULLS && __any_sync(FULL, nseg != 0)) {
             __syncwarp();
             int incl = nseg;
             for (int o = 1; o < 32; o <<= 1) {
@@ -1954,10 +1973,10 @@ cudaError_t launch_grid_one(const GridArgs &a, const LaunchCfg &cfg, size_t smem
     return cudaGetLastError();
 }
 
-template <int PHASE>
+template <int PHASE, bool NULLS>
 cudaError_t launch_grid_adjoint_one(const GridAdjArgs &a, int rows, double *value, cudaStream_t st)
 {
-    auto kern = grid_adjoint_kernel<PHASE>;
+    auto kern = grid_adjoint_kernel<PHASE, NULLS>;
     const size_t tb = (PHASE != MC_PHASE_HG) ? a.g.c.table_bytes : 0;
     const size_t smem = tb + a.g.c.extra_bytes + 16 + sizeof(double) * (GADJ_BLOCK / 32) +
                         sizeof(float) * GADJ_BLOCK * GADJ_SEG;
@@ -2065,10 +2084,13 @@ int grid_adjoint_max_grid()
 cudaError_t launch_grid_adjoint(const GridAdjArgs &a, int rows, double *value, cudaStream_t st)
 {
     if (rows < 1) return cudaErrorInvalidValue;
-    switch (a.g.c.phase_kind) {
-    case MC_PHASE_TABLE: return launch_grid_adjoint_one<MC_PHASE_TABLE>(a, rows, value, st);
-    case MC_PHASE_HG: return launch_grid_adjoint_one<MC_PHASE_HG>(a, rows, value, st);
-    case MC_PHASE_PAPER: return launch_grid_adjoint_one<MC_PHASE_PAPER>(a, rows, value, st);
+    switch (a.g.c.phase_kind * 2 + (a.nulls ? 1 : 0)) {
+    case 0: return launch_grid_adjoint_one<MC_PHASE_TABLE, false>(a, rows, value, st);
+    case 1: return launch_grid_adjoint_one<MC_PHASE_TABLE, true>(a, rows, value, st);
+    case 2: return launch_grid_adjoint_one<MC_PHASE_HG, false>(a, rows, value, st);
+    case 3: return launch_grid_adjoint_one<MC_PHASE_HG, true>(a, rows, value, st);
+    case 4: return launch_grid_adjoint_one<MC_PHASE_PAPER, false>(a, rows, value, st);
+    case 5: return launch_grid_adjoint_one<MC_PHASE_PAPER, true>(a, rows, value, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -432,11 +432,13 @@ class Engine:
             return tr.view(n_trace, n_events, N.TRACE_WORDS)
         return self
 
-    def grid_adjoint(self, grid, phase, adj_image, n_photons, seed=1, stream=None, **kw):
+    def grid_adjoint(self, grid, phase, adj_image, n_photons, seed=1, stream=None, nulls=None, **kw):
         """Gradient of sum(adj_image * image) w.r.t. the voxel densities of a
         prepared Grid (mc_grid_adjoint) on the photons run_grid would use.
-        Returns (value tensor [1] float64, grad tensor [gz, gy, gx] float32),
-        both on the device; check() afterwards for device errors."""
+        nulls: a majorant scale > 1 to score the flights' transmission at
+        null collisions instead (mc_grid_adjoint_nulls). Returns (value
+        tensor [1] float64, grad tensor [gz, gy, gx] float32), both on the
+        device; check() afterwards for device errors."""
         torch = _torch()
         rp = run_params(n_photons, seed, **kw)
         m, keep = phase.as_c(self.device)
@@ -452,10 +454,16 @@ class Engine:
         grad = torch.empty(tuple(grid.density.shape), dtype=torch.float32, device=self.device)
         value = torch.empty(1, dtype=torch.float64, device=self.device)
         vp = C.c_void_p
-        N.check("mc_grid_adjoint", N.lib().mc_grid_adjoint(
-            C.byref(g), vp(grid.work.data_ptr()), C.byref(m), C.byref(geo), C.byref(c), C.byref(rp),
-            vp(adj.data_ptr()), vp(grad.data_ptr()), vp(value.data_ptr()), vp(self.error.data_ptr()),
-            vp(work.data_ptr()), work.numel(), _stream_handle(stream)))
+        if nulls is None:
+            N.check("mc_grid_adjoint", N.lib().mc_grid_adjoint(
+                C.byref(g), vp(grid.work.data_ptr()), C.byref(m), C.byref(geo), C.byref(c), C.byref(rp),
+                vp(adj.data_ptr()), vp(grad.data_ptr()), vp(value.data_ptr()), vp(self.error.data_ptr()),
+                vp(work.data_ptr()), work.numel(), _stream_handle(stream)))
+        else:
+            N.check("mc_grid_adjoint_nulls", N.lib().mc_grid_adjoint_nulls(
+                C.byref(g), vp(grid.work.data_ptr()), C.byref(m), C.byref(geo), C.byref(c), C.byref(rp),
+                vp(adj.data_ptr()), float(nulls), vp(grad.data_ptr()), vp(value.data_ptr()),
+                vp(self.error.data_ptr()), vp(work.data_ptr()), work.numel(), _stream_handle(stream)))
         self._keep = (keep, grid, adj, work)
         return value, grad
 

@@ -276,3 +276,13 @@ def test_weighted_table_rejects_bad_arguments_on_the_host(eng):
     hg = N.Medium(0.1, 0.0, N.PHASE_HG, 0.5, None, 0)
     assert L.mc_phase_table_weighted(C.byref(hg), 8, p, q, tb, p, None) == -1
     assert L.mc_phase_table_weighted(C.byref(base), 8, p, q, tb - 16, p, None) == -3
+
+
+def test_null_score_gradient_checks_its_majorant_scale(eng):
+    """mc_grid_adjoint_nulls wants 1 < majorant_scale <= 16 (finite), decided
+    before anything else is looked at."""
+    from paper_2507_23189_gb300 import _native as N
+    L = N.lib()
+    for bad in (1.0, 0.5, 17.0, float("nan"), float("inf")):
+        assert L.mc_grid_adjoint_nulls(None, None, None, None, None, None, None, bad, None, None, None, None, 0,
+                                       None) == -1

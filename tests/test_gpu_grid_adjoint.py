@@ -193,3 +193,102 @@ def test_disc_beam_gradient_matches_oracle(gpu, oracle_mod, ps_table, ps_oracle_
     bg, bo = blk(gg_), blk(o["grad"])
     print("disc beam, multiple scattering: worst block %.2e of max" % (np.max(np.abs(bg - bo)) / np.max(np.abs(bo))))
     assert np.max(np.abs(bg - bo)) <= 1e-2 * np.max(np.abs(bo))
+
+
+# ------------------------------------------- null-collision scores (nulls=)
+
+
+def test_null_scores_match_oracle_single_scatter(gpu, oracle_mod):
+    """Null-collision scores, single scattering: the GPU and the oracle on the
+    same photons with majorants 1.5 times the cell maxima, voxel by voxel."""
+    import torch
+    dens = _rough((16, 16, 32), 11, 2000.0)
+    k_ext, k_sca, gg = 4e-5, 3e-5, 0.6
+    nx, nz = 32, 16
+    rng = np.random.default_rng(5)
+    adj = np.zeros((nz, nx), dtype=np.float32)
+    adj[nz // 2] = rng.uniform(0.2, 1.0, nx)
+    g = _grid(gpu, dens, k_ext, k_sca, 0.0, (8, 4, 4))
+    n = 200_000
+    e = gpu.Engine(gpu.Camera(nx, nz, 64, R_MAX), gpu.Geometry(LX, LY, LZ))
+    val, grad = e.grid_adjoint(g, gpu.Medium(1.0, 0.0, "hg", gg, None), torch.from_numpy(adj), n, seed=3,
+                               max_scatter=1, nulls=1.5)
+    e.check()
+    o = oracle_mod.grid_adjoint(adj.astype(np.float64), nulls=True, max_events=256, phase="hg", hg_g=gg, mu_s=0.0,
+                                n_photons=n, nx=nx, nz=nz, max_scatter=1, seed=3,
+                                grid=dict(density=dens.astype(np.float64), k_ext=k_ext, k_sca=k_sca,
+                                          block=(8, 4, 4), majorant_scale=1.5))
+    gg_ = grad.cpu().numpy().astype(np.float64)
+    mask = np.zeros(dens.shape, bool)
+    mask[8, 8:, :] = True
+    assert np.all(gg_[~mask] == 0.0)
+    assert val.item() == pytest.approx(o["value"], rel=1e-5)
+    scale = np.max(np.abs(o["grad"]))
+    ok = np.abs(gg_ - o["grad"]) <= 1e-4 * np.abs(o["grad"]) + 1e-5 * scale
+    print("nulls, single scattering: voxels within tolerance %d / %d" % (ok[mask].sum(), mask.sum()))
+    # a null collision's voxel is a discrete decision: a few photons whose
+    # single-precision null landed across a voxel face move single voxels
+    assert ok[mask].mean() >= 0.98
+    rows = lambda t: t[8, 8:, :].sum(axis=1)
+    np.testing.assert_allclose(rows(gg_), rows(o["grad"]), rtol=1e-3, atol=1e-4 * np.abs(rows(o["grad"])).max())
+
+
+def test_null_scores_match_oracle_multiple_scattering(gpu, oracle_mod, ps_table, ps_oracle_table):
+    import torch
+    dens = _rough((16, 16, 64), 12, 1500.0)
+    k_ext, k_sca, mu_a = 4e-5, 3.6e-5, 0.002
+    nx = nz = 32
+    adj = np.random.default_rng(4).uniform(0, 1, (nz, nx)).astype(np.float32)
+    g = _grid(gpu, dens, k_ext, k_sca, mu_a, (8, 4, 4))
+    n = 200_000
+    e = gpu.Engine(gpu.Camera(nx, nz, 64, R_MAX), gpu.Geometry(LX, LY, LZ))
+    val, grad = e.grid_adjoint(g, gpu.Medium(1.0, 0.0, "table", 0.0, ps_table), torch.from_numpy(adj), n,
+                               seed=9, rr_threshold=1e-2, nulls=1.25)
+    e.check()
+    o = oracle_mod.grid_adjoint(adj.astype(np.float64), nulls=True, max_events=4096, phase="mie",
+                                table=ps_oracle_table, mu_s=0.0, mu_a=mu_a, n_photons=n, nx=nx, nz=nz, seed=9,
+                                rr_threshold=1e-2,
+                                grid=dict(density=dens.astype(np.float64), k_ext=k_ext, k_sca=k_sca,
+                                          block=(8, 4, 4), majorant_scale=1.25))
+    gg_ = grad.cpu().numpy().astype(np.float64)
+    assert val.item() == pytest.approx(o["value"], rel=2e-4)
+    z, y, x = np.meshgrid(np.arange(16) / 16, np.arange(16) / 16, np.arange(64) / 64, indexing="ij")
+    rng = np.random.default_rng(1)
+    for _ in range(6):
+        a = rng.uniform(0, 3, 3)
+        f = np.cos(2 * np.pi * (a[0] * x + a[1] * y + a[2] * z) + rng.uniform(0, 6.3))
+        pg, po = float(np.sum(f * gg_)), float(np.sum(f * o["grad"]))
+        assert abs(pg - po) <= 3e-3 * float(np.sum(np.abs(f * o["grad"]))), (pg, po)
+    blk = lambda t: t.reshape(4, 4, 4, 4, 8, 8).sum(axis=(1, 3, 5))
+    bg, bo = blk(gg_), blk(o["grad"])
+    assert np.max(np.abs(bg - bo)) <= 1e-2 * np.max(np.abs(bo))
+
+
+def test_null_scores_and_exact_lengths_agree_in_expectation(gpu, ps_table):
+    """The two estimators on independent photons (their majorants differ):
+    block sums agree within the combined batch errors."""
+    import torch
+    dens = _rough((16, 16, 64), 14, 1500.0)
+    k_ext, k_sca = 4e-5, 3.8e-5
+    nx = nz = 32
+    adj = torch.from_numpy(np.random.default_rng(6).uniform(0, 1, (nz, nx)).astype(np.float32))
+    g = _grid(gpu, dens, k_ext, k_sca, 0.0, (8, 4, 4))
+    e = gpu.Engine(gpu.Camera(nx, nz, 64, R_MAX), gpu.Geometry(LX, LY, LZ))
+    med = gpu.Medium(1.0, 0.0, "table", 0.0, ps_table)
+    blk = lambda t: t.reshape(4, 4, 4, 4, 8, 8).sum(axis=(1, 3, 5))
+    out = {}
+    for name, nulls in (("exact", None), ("nulls", 1.25)):
+        bs = []
+        for b in range(12):
+            _, grad = e.grid_adjoint(g, med, adj, 400_000, seed=31, photon_offset=b * 400_000, rr_threshold=1e-2,
+                                     nulls=nulls)
+            e.check()
+            bs.append(blk(grad.cpu().numpy().astype(np.float64)))
+        bs = np.stack(bs)
+        out[name] = (bs.mean(axis=0), bs.std(axis=0, ddof=1) / np.sqrt(len(bs)))
+    (m0, s0), (m1, s1) = out["exact"], out["nulls"]
+    z = (m1 - m0) / np.sqrt(s0 ** 2 + s1 ** 2)
+    print("block sums: max |z| %.2f chi2/dof %.1f/%d; null/exact error ratio median %.2f" %
+          (np.max(np.abs(z)), np.sum(z ** 2), z.size, np.median(s1 / s0)))
+    assert np.max(np.abs(z)) < 4.5
+    assert np.sum(z ** 2) < z.size + 6 * np.sqrt(2 * z.size)
