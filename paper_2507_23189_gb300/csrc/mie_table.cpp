@@ -508,6 +508,18 @@ extern "C" mc_status mie_paper_table_build(const mie_params *P, int n_theta, mie
         }
         om[0] = 0.0f;
         om[n] = 2.0f;
+        // guides: the last interval start at or below each bucket's lower end
+        uint16_t *gq = reinterpret_cast<uint16_t *>(blob + H.off_gq);
+        uint16_t *go = reinterpret_cast<uint16_t *>(blob + H.off_go);
+        const uint32_t qstep = 8388608u / MC_PAPER_GUIDE;
+        int iq = 0, io = 0;
+        for (int b = 0; b <= MC_PAPER_GUIDE; ++b) {
+            while (iq + 1 < n && K[iq + 1] <= (uint32_t)b * qstep) ++iq;
+            gq[b] = (uint16_t)iq;
+            const float edge = (float)b * (2.0f / MC_PAPER_GUIDE);   // exact: b / 2048
+            while (io + 1 < n && om[io + 1] <= edge) ++io;
+            go[b] = (uint16_t)io;
+        }
     }
     return MC_OK;
 }

@@ -68,8 +68,17 @@ static inline size_t mc_table_layout(int n_bins, mc_table_header *h)
 //   off_ri    float ri[n_int]      1 / (cdf_{i+1} - cdf_i)  (0 if empty)
 //   off_omu   float omu[n_theta]   1 - cos(theta_i)
 //   off_pth   float pth[n_int]     (cdf_{i+1} - cdf_i) / dtheta, per radian
+//   off_gq    uint16 gq[G + 1]     gq[b] = largest i < n_int with k[i] <= b 2^23 / G:
+//                                  a sample's interval for an index q lies in
+//                                  [gq[q / (2^23 / G)], gq[q / (2^23 / G) + 1]]
+//   off_go    uint16 go[G + 1]     go[c] = largest i < n_int with omu[i] <= c 2 / G
+//                                  (as floats): the interval of 1 - cos(theta) = om
+//                                  lies in [go[c], go[c + 1]], c = floor(om G / 2)
+// G = MC_PAPER_GUIDE; the guides only narrow the bisection, whose answer is
+// the same as over the whole table.
 #define MC_PAPER_MAGIC 0x504D434Du  // "MCMP"
-#define MC_PAPER_VERSION 1u
+#define MC_PAPER_VERSION 2u
+#define MC_PAPER_GUIDE 4096
 
 struct mc_paper_header {
     uint32_t magic;
@@ -81,7 +90,8 @@ struct mc_paper_header {
     float dtheta;
     int32_t top;            // largest power of two <= n_int - 1
     float g_table;          // mean cosine of the sampled distribution
-    float pad[3];
+    uint32_t off_gq, off_go;
+    float pad;
 };
 static_assert(sizeof(mc_paper_header) == 64, "header must be 64 bytes");
 
@@ -100,6 +110,10 @@ static inline size_t mc_paper_layout(int n_theta, mc_paper_header *h)
     off += mc_pad16(sizeof(float) * (size_t)n_theta);
     const size_t pth = off;
     off += mc_pad16(sizeof(float) * (size_t)n);
+    const size_t gq = off;
+    off += mc_pad16(sizeof(uint16_t) * (size_t)(MC_PAPER_GUIDE + 1));
+    const size_t go = off;
+    off += mc_pad16(sizeof(uint16_t) * (size_t)(MC_PAPER_GUIDE + 1));
     if (h) {
         int top = 1;
         while (2 * top <= n - 1) top *= 2;
@@ -116,7 +130,9 @@ static inline size_t mc_paper_layout(int n_theta, mc_paper_header *h)
         h->dtheta = 0.0f;
         h->top = top;
         h->g_table = 0.0f;
-        for (int i = 0; i < 3; ++i) h->pad[i] = 0.0f;
+        h->off_gq = (uint32_t)gq;
+        h->off_go = (uint32_t)go;
+        h->pad = 0.0f;
     }
     return off;
 }

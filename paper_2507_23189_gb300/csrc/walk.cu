@@ -275,7 +275,8 @@ struct Smem {
     const uint16_t *guide;
     const uint32_t *pk;
     const float *pdl, *pri;
-    int pn, ptop;             // intervals of the paper table, search start
+    const uint16_t *pgq, *pgo; // guides of the paper table's two searches
+    int pn;                   // intervals of the paper table
     float pinv;               // 1 / intervals
 };
 
@@ -283,21 +284,21 @@ struct Smem {
 // Shared by the forward walk and the adjoint replay so both compute the very
 // same single-precision values.
 
-// Phase density per steradian for the camera direction cosine d_y.
-// Largest i in [0, n-1] with a[i] <= v for nondecreasing a: binary lifting
-// from the largest power of two top <= n-1 (a fixed, warp-uniform number of
-// steps, no divergent loop).
+// Largest i in [g[cell], g[cell + 1]] with a[i] <= v, for nondecreasing a
+// and a guide whose bracket is known to hold the answer: the bisection of
+// the whole table narrowed to that bracket (most brackets hold one entry).
 template <class T>
-__device__ __forceinline__ int lift_search(const T *a, int n, int top, T v)
+__device__ __forceinline__ int guided_search(const T *a, const uint16_t *g, int cell, T v)
 {
-    int i = 0;
-    for (int step = top; step > 0; step >>= 1) {
-        const int t = i + step;
-        if (t < n && a[t] <= v) i = t;
+    int lo = g[cell], hi = g[cell + 1];
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a[mid] <= v) lo = mid; else hi = mid - 1;
     }
-    return i;
+    return lo;
 }
 
+// Phase density per steradian for the camera direction cosine d_y.
 template <int PHASE>
 __device__ __forceinline__ float camera_psr(const MediumArgs &M, const CommonArgs &C, const Smem &S,
                                             float dy, int &nb)
@@ -312,7 +313,8 @@ __device__ __forceinline__ float camera_psr(const MediumArgs &M, const CommonArg
     if (PHASE == MC_PHASE_PAPER) {
         // uniform in theta on each interval: density per radian / sin(theta)
         const float om = 1.0f - fminf(fmaxf(dy, -1.0f), 1.0f);
-        nb = chk(lift_search(S.omu, S.pn, S.ptop, om), S.pn, C.error);
+        const int cell = min(__float2int_rd(om * (0.5f * MC_PAPER_GUIDE)), MC_PAPER_GUIDE - 1);   // exact product
+        nb = chk(guided_search(S.omu, S.pgo, cell, om), S.pn, C.error);
         const float st2 = om * (2.0f - om);
         return st2 > 0.0f ? S.pdf[nb] * mc_rsqrt(st2) * INV_2PI : 0.0f;
     }
@@ -325,6 +327,16 @@ __device__ __forceinline__ int camera_pixel(const CommonArgs &C, float rx, float
 {
     ix = min(max(__float2int_rd(rx * C.sx), 0), C.nx - 1);
     iz = min(max(__float2int_rd((rz + C.hz) * C.sz), 0), C.nz - 1);
+    return chk(iz * C.nx + ix, C.nx * C.nz, C.error);
+}
+
+// The same for a collision the caller has tested to lie inside: 0 < rx and
+// |rz| < hz, so both products are >= 0 and only the upper clamp (rounding at
+// the far edge) can act.
+__device__ __forceinline__ int camera_pixel_inside(const CommonArgs &C, float rx, float rz, int &ix, int &iz)
+{
+    ix = min(__float2int_rd(rx * C.sx), C.nx - 1);
+    iz = min(__float2int_rd((rz + C.hz) * C.sz), C.nz - 1);
     return chk(iz * C.nx + ix, C.nx * C.nz, C.error);
 }
 
@@ -342,7 +354,8 @@ __device__ __forceinline__ float sample_omu(const MediumArgs &M, const CommonArg
         // index q (u1 = (q + 1/2) 2^-23 exactly), then linear interpolation
         // in theta: u1 - cdf_i = (q - k_i) 2^-23 + dl_i, fraction = that / w_i
         const int q = __float2int_rd(u1 * 8388608.0f);
-        const int i = chk(lift_search(S.pk, S.pn, S.ptop, (uint32_t)q), S.pn, C.error);
+        const int i = chk(guided_search(S.pk, S.pgq, q / (8388608 / MC_PAPER_GUIDE),
+                                        (uint32_t)q), S.pn, C.error);
         const float fr = fminf(fmaxf(fmaf((float)(q - (int)S.pk[i]), 1.1920928955078125e-7f, S.pdl[i]) *
                                          S.pri[i], 0.0f), 1.0f);
         const float sh = sinpif(0.5f * ((float)i + fr) * S.pinv);   // sin(theta / 2)
@@ -396,7 +409,8 @@ __device__ __forceinline__ Smem carve(unsigned char *smem, const CommonArgs &C)
     S.omu = S.pdf = S.pdl = S.pri = nullptr;
     S.guide = nullptr;
     S.pk = nullptr;
-    S.pn = S.ptop = 0;
+    S.pgq = S.pgo = nullptr;
+    S.pn = 0;
     S.pinv = 0.0f;
     return S;
 }
@@ -414,7 +428,8 @@ __device__ __forceinline__ bool bind_table(Smem &S, const CommonArgs &C)
 {
     if (PHASE == MC_PHASE_PAPER) {
         const mc_paper_header *h = reinterpret_cast<const mc_paper_header *>(S.table);
-        if (h->magic != MC_PAPER_MAGIC || h->n_theta != C.n_bins || h->total_bytes != C.table_bytes) {
+        if (h->magic != MC_PAPER_MAGIC || h->version != MC_PAPER_VERSION || h->n_theta != C.n_bins ||
+            h->total_bytes != C.table_bytes) {
             if (threadIdx.x == 0) atomicOr(C.error, MC_EFLAG_TABLE);
             return false;
         }
@@ -423,8 +438,9 @@ __device__ __forceinline__ bool bind_table(Smem &S, const CommonArgs &C)
         S.pri = reinterpret_cast<const float *>(S.table + h->off_ri);
         S.omu = reinterpret_cast<const float *>(S.table + h->off_omu);
         S.pdf = reinterpret_cast<const float *>(S.table + h->off_pth);
+        S.pgq = reinterpret_cast<const uint16_t *>(S.table + h->off_gq);
+        S.pgo = reinterpret_cast<const uint16_t *>(S.table + h->off_go);
         S.pn = h->n_int;
-        S.ptop = h->top;
         S.pinv = 1.0f / (float)h->n_int;
         return true;
     }
@@ -625,7 +641,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
         int nb, ix, iz;
         const float psr = camera_psr<PHASE>(M, C, S, dy, nb);
         const float nee = w * psr * mc_exp2(fmaf(cam_a, ry, cam_b));
-        const int pix = camera_pixel(C, rx, rz, ix, iz);
+        const int pix = camera_pixel_inside(C, rx, rz, ix, iz);   // 0 < rx < lx, |rz| < hz tested above
         const float vf = nee * C.img_scale;
         if (vf < 4.0e18f) {
             const long long v = __float2ll_rn(vf);

@@ -1,6 +1,8 @@
 """The engine's paper-faithful table (mie_paper_table_build, host code; no
-GPU needed): its cumulative distribution against the oracle's, and the
-integer search thresholds against a double-precision search."""
+GPU needed): its cumulative distribution against the oracle's, the integer
+search thresholds against a double-precision search, and the guides that
+narrow the kernel's two bisections (the answer must be the same as over the
+whole table)."""
 import numpy as np
 import pytest
 
@@ -15,11 +17,32 @@ def eng_paper():
     return g.PaperTable(n_theta=3000)
 
 
+GUIDE = 4096
+
+
 def _header(blob):
     h = np.frombuffer(blob[:64].tobytes(), dtype=np.uint32)
-    return dict(magic=int(h[0]), n_theta=int(h[2]), n_int=int(h[3]), off_k=int(h[4]), off_dl=int(h[5]),
-                off_ri=int(h[6]), off_omu=int(h[7]), off_pth=int(h[8]), total=int(h[9]),
-                top=int(np.frombuffer(blob[44:48].tobytes(), dtype=np.int32)[0]))
+    return dict(magic=int(h[0]), version=int(h[1]), n_theta=int(h[2]), n_int=int(h[3]), off_k=int(h[4]),
+                off_dl=int(h[5]), off_ri=int(h[6]), off_omu=int(h[7]), off_pth=int(h[8]), total=int(h[9]),
+                top=int(np.frombuffer(blob[44:48].tobytes(), dtype=np.int32)[0]), off_gq=int(h[13]),
+                off_go=int(h[14]))
+
+
+def _guide(blob, off):
+    return np.frombuffer(blob[off:off + 2 * (GUIDE + 1)].tobytes(), dtype=np.uint16).astype(np.int64)
+
+
+def _guided_bisection(a, g, cell, v):
+    """The kernel's search: largest i in [g[cell], g[cell + 1]] with a[i] <= v."""
+    lo, hi = g[cell].copy(), g[cell + 1].copy()
+    while np.any(lo < hi):
+        act = lo < hi
+        mid = (lo + hi + 1) >> 1
+        le = np.zeros_like(act)
+        le[act] = a[mid[act]] <= v[act]
+        lo = np.where(act & le, mid, lo)
+        hi = np.where(act & ~le, mid - 1, hi)
+    return lo
 
 
 def test_cdf_matches_oracle(eng_paper, oracle_mod):
@@ -64,16 +87,15 @@ def _check_thresholds(table):
     want = np.searchsorted(cdf[:n], u, side="right") - 1      # largest i with cdf[i] <= u
     got = np.searchsorted(K[:n], q, side="right") - 1         # largest i with K[i] <= q
     np.testing.assert_array_equal(got, want)
-    # the kernel's binary lifting from the header's starting step finds the same interval
-    lift = np.zeros_like(q)
-    step = h["top"]
-    while step > 0:
-        t = lift + step
-        ok = t < n
-        ok[ok] = K[t[ok]] <= q[ok]
-        lift = np.where(ok, t, lift)
-        step >>= 1
-    np.testing.assert_array_equal(lift, want)
+    # the kernel's bisection inside the guide's bracket finds the same interval,
+    # for every one of the 2^23 uniform indices
+    assert h["version"] == 2
+    gq = _guide(b, h["off_gq"])
+    qa = np.arange(1 << 23, dtype=np.int64)
+    want_all = np.searchsorted(K[:n], qa, side="right") - 1
+    cell = qa // ((1 << 23) // GUIDE)
+    assert np.all(gq[cell] <= want_all) and np.all(want_all <= gq[cell + 1])
+    np.testing.assert_array_equal(_guided_bisection(K, gq, cell, qa), want_all)
     # the interpolation aids give the fraction (u - cdf_i) / (cdf_{i+1} - cdf_i)
     i = got
     frac = ((q - K[i]) * 2.0 ** -23 + dl[i]) * ri[i]
@@ -99,11 +121,11 @@ def test_cdf_matches_oracle_across_grids_and_particles(eng_paper, oracle_mod, n_
     assert t.cdf64[0] == 0.0 and t.cdf64[-1] == 1.0 and np.all(np.diff(t.cdf64) >= 0)
 
 
-@pytest.mark.parametrize("n_theta", [16, 2049, 3000])
-def test_camera_interval_search_by_lifting(eng_paper, n_theta):
+@pytest.mark.parametrize("n_theta", [16, 2049, 3000, 16384])
+def test_camera_interval_search_by_guided_bisection(eng_paper, n_theta):
     """The camera density's interval: the largest i < n_int with omu[i] <=
-    1 - cos(theta_c), found by the same binary lifting over the blob's omu
-    (1 - cos(i pi / n_int) in single precision)."""
+    1 - cos(theta_c), found by the kernel's bisection inside the guide's
+    bracket over the blob's omu (1 - cos(i pi / n_int) in single precision)."""
     import paper_2507_23189_gb300 as g
     t = eng_paper if n_theta == 3000 else g.PaperTable(n_theta=n_theta)
     b = t.blob
@@ -115,13 +137,11 @@ def test_camera_interval_search_by_lifting(eng_paper, n_theta):
     rng = np.random.default_rng(n_theta)
     om = np.concatenate([rng.uniform(0, 2, 20000), omu[:n], np.nextafter(omu[:n], np.float32(-1)), [0.0, 2.0]])
     om = np.clip(om.astype(np.float32), 0, 2)
+    edges = (np.arange(GUIDE + 1) * (2.0 / GUIDE)).astype(np.float32)
+    om = np.concatenate([om, edges, np.nextafter(edges, np.float32(-1)), np.nextafter(edges, np.float32(3))])
+    om = np.clip(om, 0, 2).astype(np.float32)
     want = np.maximum(np.searchsorted(omu[:n], om, side="right") - 1, 0)
-    lift = np.zeros(om.size, dtype=np.int64)
-    step = h["top"]
-    while step > 0:
-        tt = lift + step
-        ok = tt < n
-        ok[ok] = omu[tt[ok]] <= om[ok]
-        lift = np.where(ok, tt, lift)
-        step >>= 1
-    np.testing.assert_array_equal(lift, want)
+    go = _guide(b, h["off_go"])
+    cell = np.minimum(np.floor(om * np.float32(GUIDE / 2)).astype(np.int64), GUIDE - 1)   # exact product
+    assert np.all(go[cell] <= want) and np.all(want <= go[cell + 1])
+    np.testing.assert_array_equal(_guided_bisection(omu, go, cell, om), want)
