@@ -62,6 +62,8 @@ def lib():
         L.oracle_walk.restype = C.c_int
         L.oracle_walk.argtypes = [C.POINTER(WalkCfg), C.POINTER(WalkOut),
                                   C.POINTER(TraceRec), C.c_int, C.c_int]
+        L.oracle_walk32_trace.restype = C.c_int
+        L.oracle_walk32_trace.argtypes = [C.POINTER(WalkCfg), C.POINTER(TraceRec), C.c_int, C.c_int]
         L.oracle_hat.restype = C.c_double
         L.oracle_hat.argtypes = [C.c_int, C.c_int, C.c_double]
         L.oracle_hat_integrals.restype = None
@@ -382,6 +384,26 @@ def _walk_cfg(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,
         cfg.majorant_scale = float(grid.get("majorant_scale", 1.0))
     cfg._keep = keep
     return cfg, keep
+
+
+def walk32_trace(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,
+                 lx=45.0, ly=10.0, lz=10.0, beam_radius=0.0,
+                 nx=64, nz=64, n_radial=128, r_max=5.0 * 2 ** 0.5,
+                 n_trace=1000, photon_offset=0, seed=1,
+                 rr_threshold=1e-4, rr_survival=0.1, max_events=1_000_000, max_scatter=0,
+                 n_trace_events=32):
+    """The walk in single precision with explicit fused multiply-adds (the
+    oracle's FP32 mode): traces of the first n_trace_events events of photons
+    photon_offset .. + n_trace - 1, in the record layout of walk()'s trace.
+    Homogeneous medium; phase "mie" (equal-probability table) or "hg"."""
+    cfg, keep = _walk_cfg(mu_s, mu_a, phase, table, hg_g, lx, ly, lz, beam_radius, nx, nz, n_radial,
+                          r_max, n_trace, photon_offset, seed, rr_threshold, rr_survival, max_events,
+                          max_scatter, 0.0, 1, None)
+    trace = (TraceRec * (n_trace * n_trace_events))()
+    rc = lib().oracle_walk32_trace(C.byref(cfg), C.cast(trace, C.POINTER(TraceRec)), n_trace, n_trace_events)
+    if rc:
+        raise ValueError("oracle_walk32_trace: bad arguments")
+    return np.frombuffer(trace, dtype=np.float64).reshape(n_trace, n_trace_events, 13).copy()
 
 
 def walk(mu_s, mu_a=0.0, phase="mie", table=None, hg_g=0.0,

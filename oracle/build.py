@@ -8,7 +8,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["mie.c", "table.c", "philox.c", "walk.c", "adjoint.c"]
+SOURCES = ["mie.c", "table.c", "philox.c", "walk.c", "walk32.c", "adjoint.c"]
 LIB = os.path.join(HERE, "_build", "liboracle.so")
 
 

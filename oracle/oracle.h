@@ -21,6 +21,8 @@
  *             next-event estimate for the 90-degree side camera (Sec. 4.3);
  *             optionally through a voxel density grid by delta tracking
  *             (the complex media the paper leaves to future work, Sec. 6).
+ *   walk32.c  the homogeneous walk again in IEEE single precision with
+ *             explicit fused multiply-adds (the FP32 mode), traces only.
  *
  * Parity status: every function here is pinned by the -m "not gpu" tests
  * (closed forms, invariants, an independent 50-digit evaluation of Eq. 7-8,
@@ -231,6 +233,15 @@ typedef struct {
  * Returns 0, or -1 on bad arguments. */
 int oracle_walk(const oracle_walk_cfg *cfg, oracle_walk_out *out,
                 oracle_trace_rec *trace, int n_trace, int n_trace_events);
+
+/* ---------------------------------------------------------- walk32.c */
+
+/* The same walk in IEEE single precision with explicit fused multiply-adds
+ * (the oracle's FP32 mode): homogeneous medium, table or H-G phase, the
+ * first n_trace_events events of photons photon_offset .. + n_trace - 1
+ * recorded as by oracle_walk (no tallies). Returns 0 or -1. */
+int oracle_walk32_trace(const oracle_walk_cfg *cfg, oracle_trace_rec *trace, int n_trace,
+                        int n_trace_events);
 
 /* ---------------------------------------------------------- adjoint.c */
 

@@ -12,7 +12,12 @@ In both, every photon must match: a discrete decision (wall, exit face,
 pixel, table bin, roulette) may differ only where the oracle's branch
 quantity lies within 1e-5 of its threshold, which ends the comparison of
 that photon. Each case prints the worst deviation per field, and the worst
-deviations are asserted below bounds well inside the 1e-5 contract."""
+deviations are asserted below bounds well inside the 1e-5 contract.
+
+The same traces of both builds are also compared with the oracle's
+single-precision mode (oracle/walk32.c: IEEE single precision with explicit
+fmaf, the C library's logf / expf / sincosf / sqrtf), the comparison the
+contract names for IEEE-strict builds on both sides."""
 import os
 import subprocess
 import sys
@@ -42,7 +47,12 @@ def _hg_slope(g):
     return lambda mu: 3.0 * abs(g) / (1.0 + g * g - 2.0 * g * mu)
 
 
+_CACHE = {}
+
+
 def _traces(tmp_path, strict):
+    if strict in _CACHE:
+        return _CACHE[strict]
     from paper_2507_23189_gb300 import build
     build.build()
     if strict:
@@ -56,8 +66,9 @@ def _traces(tmp_path, strict):
     p = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "strict_traces.py"), out], env=env,
                        capture_output=True, text=True, timeout=900)
     assert p.returncode == 0, p.stderr[-3000:]
-    z = np.load(out)
+    z = dict(np.load(out))
     assert str(z["library"]) == ("libmcmie_strict.so" if strict else "libmcmie.so")
+    _CACHE[strict] = z
     return z
 
 
@@ -89,4 +100,42 @@ def test_first_32_events_every_photon(gpu, oracle_mod, ps_oracle_table, tmp_path
     print("%s worst over all cases: %s" % (build_kind, {k: "%.2e" % v for k, v in worst_all.items()}))
     assert not failed, failed
     for k, b in BOUNDS[build_kind].items():
+        assert worst_all[k] <= b, (k, worst_all[k], b)
+
+
+# worst deviation per field against the single-precision oracle, per build
+BOUNDS32 = {"production": dict(pos=5e-6, dir=2e-6, w=1e-7, nee_net=1.5e-6),
+            "strict": dict(pos=5e-6, dir=2e-6, w=1e-7, nee_net=1.5e-6)}
+
+
+@pytest.mark.parametrize("build_kind", ["strict", "production"])
+def test_first_32_events_against_the_single_precision_oracle(gpu, oracle_mod, ps_oracle_table, tmp_path,
+                                                             build_kind):
+    z = _traces(tmp_path, build_kind == "strict")
+    x = oracle_mod.size_parameter(5.0, 1.33, 532.0)
+    g_or = oracle_mod.mie_efficiencies(complex(1.59 / 1.33, 0.0), x)[2]
+    worst_all = dict(pos=0.0, dir=0.0, w=0.0, nee=0.0, nee_net=0.0)
+    rows, failed = [], []
+    for name, phase, tau, mu_a, kw in ST.CASES:
+        tr = gpu.decode_trace(z[name])
+        om = dict(phase="mie", table=ps_oracle_table) if phase == "table" else dict(phase="hg", hg_g=g_or)
+        t32 = oracle_mod.walk32_trace(mu_s=tau / ST.LX - mu_a, mu_a=mu_a, nx=64, nz=64, seed=11,
+                                      n_trace=ST.N_TRACE, n_trace_events=32, **om, **kw)
+        slope = _hg_slope(g_or) if phase == "hg" else None
+        cmp = compare_traces(tr, t32, mu_ext=tau / ST.LX, nee_slope=slope)
+        w_ = cmp["worst"]
+        rows.append("%-10s %-18s vs FP32 oracle: matched %4d/%d flips %3d events %6d  worst pos %.2e dir %.2e "
+                    "w %.2e cam %.2e (net %.2e)" % (build_kind, name, cmp["matched"], cmp["n"], cmp["flips"],
+                                                    cmp["events"], w_["pos"], w_["dir"], w_["w"], w_["nee"],
+                                                    w_["nee_net"]))
+        for c in cmp["causes"]:
+            rows.append("    unmatched photon %d event %d: %s" % c)
+        for k in worst_all:
+            worst_all[k] = max(worst_all[k], w_[k])
+        if cmp["matched"] != cmp["n"] or cmp["events"] <= 1.2 * cmp["n"] or cmp["flips"] > 0.002 * cmp["n"]:
+            failed.append(name)
+    print("\n" + "\n".join(rows))
+    print("%s vs FP32 oracle, worst over all cases: %s" % (build_kind, {k: "%.2e" % v for k, v in worst_all.items()}))
+    assert not failed, failed
+    for k, b in BOUNDS32[build_kind].items():
         assert worst_all[k] <= b, (k, worst_all[k], b)

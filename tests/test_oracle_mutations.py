@@ -24,6 +24,7 @@ GADJ = ["test_oracle_grid_adjoint.py"]
 PAPER = ["test_oracle_paper.py"]
 METRICS = ["test_oracle_metrics.py"]
 WEIGHTS = ["test_oracle_phase_weights.py"]
+W32 = ["test_oracle_walk32.py"]
 
 # (file, text, replacement, pin files, the mistake)
 MUTATIONS = [
@@ -186,6 +187,24 @@ MUTATIONS = [
      "grad[(size_t)r->pix] -= P * c->k_ext / (r->nee - r->w);", GADJ,
      "null score weighted by all the photon's camera terms"),
     ("walk.c", "maj[i] *= c->majorant_scale;", "maj[i] *= 1.0;", GADJ, "majorant scale ignored"),
+    # the single-precision mode
+    ("walk32.c", "const float s = -logf(u0) / mu_ext;", "const float s = -logf(u0) * mu_ext;", W32,
+     "FP32 free path times mu_ext"),
+    ("walk32.c", "const float albedo = (float)(c->mu_s / (c->mu_s + c->mu_a));",
+     "const float albedo = (float)(c->mu_a / (c->mu_s + c->mu_a));", W32, "FP32 albedo from the absorption"),
+    ("walk32.c", "om = 2.0f * (1.0f - g) * (1.0f - g) * (1.0f - u1) * fmaf(g, u1, 1.0f) / (D * D);",
+     "om = 2.0f * (1.0f - g) * (1.0f - g) * fmaf(g, u1, 1.0f) / (D * D);", W32, "FP32 H-G inverse without (1 - xi)"),
+    ("walk32.c", "om = fmaf(f, omu[i + 1] - omu[i], omu[i]);", "om = fmaf(f, omu[i + 1] - omu[i], omu[i + 1]);", W32,
+     "FP32 table interpolation from the wrong level"),
+    ("walk32.c", "const float e2[3] = {b, fmaf(d[1] * d[1], a, sg), -d[1]};",
+     "const float e2[3] = {b, fmaf(d[1] * d[1], a, sg), d[1]};", W32, "FP32 sign in the Duff basis"),
+    ("walk32.c", "sincosf(2.0f * PI_F * u2, &sp, &cp);", "sincosf(PI_F * u2, &sp, &cp);", W32,
+     "FP32 azimuth over half the circle"),
+    ("walk32.c", "expf(-mu_ext * (hy - r[1]))", "expf(-mu_ext * (hy + r[1]))", W32,
+     "FP32 camera path length from the wrong face"),
+    ("walk32.c", "psr = pdf[nbin] / (2.0f * PI_F);", "psr = pdf[nbin + 1] / (2.0f * PI_F);", W32,
+     "FP32 camera density of the next bin"),
+    ("walk32.c", "w = w / surv;", "w = w * surv;", W32, "FP32 roulette survivor weight"),
 ]
 
 
@@ -205,7 +224,8 @@ def _pins(root, files, basetemp):
 
 
 def _compiles(root):
-    src = [os.path.join(root, "oracle", s) for s in ("mie.c", "table.c", "philox.c", "walk.c", "adjoint.c")]
+    src = [os.path.join(root, "oracle", s) for s in ("mie.c", "table.c", "philox.c", "walk.c", "walk32.c",
+                                                      "adjoint.c")]
     p = subprocess.run(["gcc", "-std=c11", "-D_GNU_SOURCE", "-fsyntax-only", "-Wall"] + src,
                        capture_output=True, text=True)
     return p.returncode == 0, p.stderr[-800:]
