@@ -141,14 +141,37 @@ def job_rate(t_local_s, steps_local, ws, device):
     return total / t_max, t_max, total
 
 
+# Arm core part numbers (MIDR part field of implementer 0x41) that /proc/cpuinfo reports
+ARM_PARTS = {0xd0c: "Neoverse-N1", 0xd40: "Neoverse-V1", 0xd49: "Neoverse-N2", 0xd4f: "Neoverse-V2",
+             0xd8e: "Neoverse-N3", 0xd84: "Neoverse-V3"}
+
+
 def _cpu_model():
-    try:
-        for ln in open("/proc/cpuinfo"):
-            if ln.lower().startswith(("model name", "cpu model")):
-                return ln.split(":", 1)[1].strip()
-    except OSError:
-        pass
+    """The host CPU's model: lscpu's model name, else /proc/cpuinfo's (x86),
+    else the Arm part number it lists, else the machine architecture."""
     import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name:"):
+                return "%s %s" % (platform.machine(), ln.split(":", 1)[1].strip())
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        impl = part = None
+        for ln in open("/proc/cpuinfo"):
+            low = ln.lower()
+            if low.startswith(("model name", "cpu model")):
+                return ln.split(":", 1)[1].strip()
+            if low.startswith("cpu implementer"):
+                impl = int(ln.split(":", 1)[1], 0)
+            if low.startswith("cpu part"):
+                part = int(ln.split(":", 1)[1], 0)
+        if impl == 0x41 and part is not None:
+            return "%s %s" % (platform.machine(), ARM_PARTS.get(part, "Arm part 0x%x" % part))
+    except (OSError, ValueError):
+        pass
     return platform.machine()
 
 

@@ -4,9 +4,10 @@
 // the unweighted table (constant (1/n) / (omu_j - omu_{j+1}) per unit cos
 // theta on bin j, omu = 1 - cos theta at the levels j / n), h_w the linear
 // interpolant of the weights w_k at the hat nodes mu_k = -1 + 2k/(n_w - 1)
-// (h_w = sum_k w_k phi_k), Z(w) = int p h_w. One CTA writes the packed blob of
-// p_w's equal-probability table in the layout of table_format.h, so the walk,
-// the camera density and the adjoint use it like any table:
+// (h_w = sum_k w_k phi_k), Z(w) = int p h_w. One cluster of CTAs writes the
+// packed blob of p_w's equal-probability table in the layout of
+// table_format.h, so the walk, the camera density and the adjoint use it like
+// any table:
 //   1. each bin's mass p_j int h_w (h_w is linear between hat nodes, so
 //      trapezoids piece by piece are exact), in double precision;
 //   2. their running sum (a fixed-order block scan), Z(w) its total;
@@ -18,6 +19,7 @@
 // Weights must be positive and finite; otherwise (or if single precision
 // cannot hold the levels apart) the blob gets an invalid header, so a walk
 // using it stops with MC_EFLAG_TABLE, and MC_EFLAG_NUMERIC is set.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,7 +29,10 @@
 namespace mcx {
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int WT_BLOCK = 1024;
+constexpr int WT_CLUSTER = 8;   // CTAs of the one cluster (a portable cluster size)
 constexpr unsigned FULL = 0xffffffffu;
 
 // h_w at cos theta = mu: the two hats around mu
@@ -132,27 +137,38 @@ __device__ __forceinline__ double level_of(int i, int n, double Z, const double 
     return v;
 }
 
-// X: the layout of an n-bin blob, which the caller sized shared memory and
-// the output for (the base blob's header must agree).
-// Dynamic shared memory: double ve[n + 1], cum[n + 1], red[32].
+// X: the layout of an n-bin blob (the base blob's header must agree). One
+// cluster of WT_CLUSTER CTAs: CTA r owns bins [r c, r c + c), c = ceil(n /
+// WT_CLUSTER), and computes their widths, masses and levels, the part that
+// costs double-precision arithmetic; the per-bin values are exchanged through
+// distributed shared memory, and every CTA runs the same fixed-order scans
+// over the whole table (cheap additions), so all see identical edges and
+// running masses. Dynamic shared memory: double ve[n + 1], cum[n + 1],
+// mine[c + 1], red[32], part[2].
 __global__ void __launch_bounds__(WT_BLOCK) weighted_table_kernel(const unsigned char *base, mc_table_header X,
                                                                   int n_w, const float *w, unsigned char *out,
                                                                   uint32_t *err)
 {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank(), nr = (int)cluster.num_blocks();
     const int n = X.n_bins;
+    const int c = (n + nr - 1) / nr;
+    const int r0 = min(rank * c, n), r1 = min(r0 + c, n);
     extern __shared__ __align__(16) double sh[];
     const mc_table_header *hb = reinterpret_cast<const mc_table_header *>(base);
     mc_table_header *ho = reinterpret_cast<mc_table_header *>(out);
     double *ve = sh;
-    double *cum = sh + n + 1;
-    double *red = cum + n + 1;
+    double *cum = ve + n + 1;
+    double *mine = cum + n + 1;
+    double *red = mine + c + 1;
+    double *part = red + 32;   // [0]: this CTA's share of the mean, [1]: its failure flag
     bool bad = false;
     for (int k = threadIdx.x; k < n_w; k += blockDim.x) bad |= !(w[k] > 0.0f) || !isfinite(w[k]);
     if (hb->magic != MC_TABLE_MAGIC || hb->n_bins != n || hb->n_guide != X.n_guide || hb->off_omu != X.off_omu ||
         hb->off_pdf != X.off_pdf || hb->off_guide != X.off_guide || hb->total_bytes != X.total_bytes)
         bad = true;
-    if (__syncthreads_or(bad)) {
-        if (threadIdx.x == 0) {
+    if (__syncthreads_or(bad)) {   // the same inputs in every CTA: all leave here together
+        if (rank == 0 && threadIdx.x == 0) {
             atomicOr(err, MC_EFLAG_NUMERIC);
             ho->magic = 0u;    // walks using this blob stop with MC_EFLAG_TABLE
         }
@@ -164,64 +180,96 @@ __global__ void __launch_bounds__(WT_BLOCK) weighted_table_kernel(const unsigned
     uint16_t *og = reinterpret_cast<uint16_t *>(out + hb->off_guide);
     const double inv_n = 1.0 / n;
     const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+    // every CTA's value of bin j, into a full local array
+    auto gather = [&](double *dst, int shift) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const double *src = cluster.map_shared_rank(mine, j / c);
+            dst[j + shift] = src[j % c];
+        }
+    };
 
     // 0. the unweighted table's edges in double precision from its bin
     // densities (each bin holds 1/n): widths (1/n) / pdf_j summed from the
     // forward end, omu = 0, so every edge keeps the densities' relative
     // precision. Thread t owns the t-th run of bins counted from that end.
+    for (int j = r0 + threadIdx.x; j < r1; j += blockDim.x) mine[j - r0] = inv_n / (double)bpdf[j];
+    cluster.sync();
+    gather(ve, 0);
+    __syncthreads();
     {
         const int jhi = max(n - (int)threadIdx.x * per, 0), jlo = max(jhi - per, 0);
         double own = 0.0;
         for (int j = jhi - 1; j >= jlo; --j) {
-            own += inv_n / (double)bpdf[j];
+            own += ve[j];
             ve[j] = own;   // local suffix sum for now
         }
         const double before = block_exclusive(own, red);
         for (int j = jlo; j < jhi; ++j) ve[j] += before;
         if (threadIdx.x == 0) ve[n] = 0.0;
-        __syncthreads();
     }
+    cluster.sync();   // every CTA has read the widths: mine is free again
 
-    // 1-2. bin masses p_j int h_w and their running sum (thread t owns the
-    // t-th run of bins from mu = -1)
-    const int j0 = min((int)threadIdx.x * per, n), j1 = min(j0 + per, n);
+    // 1-2. bin masses p_j int h_w (this CTA's bins) and their running sum
+    // (over the whole table; thread t owns the t-th run of bins from mu = -1)
+    for (int j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
+        double m = 0.0;
+        for_pieces(w, n_w, ve[j], ve[j + 1], [&](double a, double b, double ha, double hbv) {
+            m += 0.5 * (ha + hbv) * (a - b);
+            return true;
+        });
+        mine[j - r0] = (double)bpdf[j] * m;
+    }
+    cluster.sync();
+    gather(cum, 1);
+    __syncthreads();
     {
+        const int j0 = min((int)threadIdx.x * per, n), j1 = min(j0 + per, n);
         double own = 0.0;
         for (int j = j0; j < j1; ++j) {
-            double m = 0.0;
-            for_pieces(w, n_w, ve[j], ve[j + 1], [&](double a, double b, double ha, double hbv) {
-                m += 0.5 * (ha + hbv) * (a - b);
-                return true;
-            });
-            own += (double)bpdf[j] * m;
+            own += cum[j + 1];
             cum[j + 1] = own;   // local running sum for now
         }
         const double before = block_exclusive(own, red);
         for (int j = j0; j < j1; ++j) cum[j + 1] += before;
         if (threadIdx.x == 0) cum[0] = 0.0;
-        __syncthreads();
     }
+    cluster.sync();   // every CTA has read the masses: mine is free again
     const double Z = cum[n];
 
-    // 3-4. levels, densities of the bins between them (from the double
-    // levels, as the host builder does) and the mean
+    // 3-4. this CTA's levels r0 .. r1 (one solve each), the densities of its
+    // bins from the double levels (as the host builder does), its share of
+    // the mean
+    for (int i = r0 + threadIdx.x; i <= r1; i += blockDim.x) mine[i - r0] = level_of(i, n, Z, cum, ve, bpdf, w, n_w);
+    __syncthreads();
     double msum = 0.0;
-    if (j0 < j1) {
-        double vj = level_of(j0, n, Z, cum, ve, bpdf, w, n_w);
-        for (int j = j0; j < j1; ++j) {
-            const double vn = level_of(j + 1, n, Z, cum, ve, bpdf, w, n_w);
-            oo[j] = j == 0 ? 2.0f : (float)vj;
-            const double width = vj - vn;
-            if (!(width > 0.0)) bad = true;
-            op[j] = (float)(inv_n / width);
-            msum += 1.0 - 0.5 * (vj + vn);
-            vj = vn;
-        }
-        if (j1 == n) oo[n] = 0.0f;
+    for (int j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
+        const double vj = mine[j - r0], vn = mine[j + 1 - r0];
+        oo[j] = j == 0 ? 2.0f : (float)vj;
+        const double width = vj - vn;
+        if (!(width > 0.0)) bad = true;
+        op[j] = (float)(inv_n / width);
+        msum += 1.0 - 0.5 * (vj + vn);
     }
-    const double mean = block_sum(msum, red) * inv_n;
-    if (__syncthreads_or(bad)) {
-        if (threadIdx.x == 0) {
+    if (r1 == n && threadIdx.x == 0) oo[n] = 0.0f;
+    const double share = block_sum(msum, red);
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        part[0] = share;
+        part[1] = bad ? 1.0 : 0.0;
+    }
+    __threadfence();   // the levels in global memory, before the guide reads them
+    cluster.sync();
+    double mean = 0.0;
+    bool any_bad = false;
+    for (int q = 0; q < nr; ++q) {   // fixed order
+        const double *pq = cluster.map_shared_rank(part, q);
+        mean += pq[0];
+        any_bad |= pq[1] != 0.0;
+    }
+    mean *= inv_n;
+    cluster.sync();   // no CTA leaves while others read its shares
+    if (any_bad) {
+        if (rank == 0 && threadIdx.x == 0) {
             atomicOr(err, MC_EFLAG_NUMERIC);
             ho->magic = 0u;
         }
@@ -230,8 +278,9 @@ __global__ void __launch_bounds__(WT_BLOCK) weighted_table_kernel(const unsigned
 
     // guide[c]: bin of the smallest float m with cell(m) >= c, where the
     // walk's lookup takes cell(m) = floor(fl(m + 1) (n_guide / 2)) and bin(m)
-    // = the largest j with omu[j] >= fl(1 - m)
+    // = the largest j with omu[j] >= fl(1 - m); this CTA's share of the cells
     const int G = hb->n_guide;
+    const int gc = (G + 1 + nr - 1) / nr, g0 = min(rank * gc, G + 1), g1 = min(g0 + gc, G + 1);
     const float half_g = 0.5f * (float)G;
     auto cell_of = [&](float m) { return (int)floorf((m + 1.0f) * half_g); };
     auto bin_of = [&](float m) {
@@ -250,23 +299,23 @@ __global__ void __launch_bounds__(WT_BLOCK) weighted_table_kernel(const unsigned
     auto float_of = [](uint32_t k) {
         return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
     };
-    for (int c = threadIdx.x; c <= G; c += blockDim.x) {
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
         float m;
-        if (c == 0) {
+        if (g == 0) {
             m = -1.0f;
-        } else if (c == G) {
+        } else if (g == G) {
             m = 1.0f;
         } else {
             uint32_t lo = key_of(-1.0f), hi = key_of(1.0f);
             while (lo < hi) {
                 const uint32_t mid = lo + (hi - lo) / 2;
-                if (cell_of(float_of(mid)) >= c) hi = mid; else lo = mid + 1;
+                if (cell_of(float_of(mid)) >= g) hi = mid; else lo = mid + 1;
             }
             m = float_of(lo);
         }
-        og[c] = (uint16_t)bin_of(m);
+        og[g] = (uint16_t)bin_of(m);
     }
-    if (threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
         mc_table_header h = *hb;
         h.g_table = (float)mean;
         *ho = h;
@@ -275,7 +324,11 @@ __global__ void __launch_bounds__(WT_BLOCK) weighted_table_kernel(const unsigned
 
 }  // namespace
 
-size_t weighted_table_smem(int n_bins) { return sizeof(double) * (2 * ((size_t)n_bins + 1) + 32); }
+size_t weighted_table_smem(int n_bins)
+{
+    const size_t c = ((size_t)n_bins + WT_CLUSTER - 1) / WT_CLUSTER;
+    return sizeof(double) * (2 * ((size_t)n_bins + 1) + (c + 1) + 32 + 2);
+}
 
 cudaError_t launch_weighted_table(const unsigned char *base, int n_bins, int n_w, const float *w,
                                   unsigned char *out, uint32_t *err, cudaStream_t st)
@@ -286,8 +339,19 @@ cudaError_t launch_weighted_table(const unsigned char *base, int n_bins, int n_w
     cudaError_t e = cudaFuncSetAttribute(weighted_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    weighted_table_kernel<<<1, WT_BLOCK, smem, st>>>(base, X, n_w, w, out, err);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(WT_CLUSTER);
+    cfg.blockDim = dim3(WT_BLOCK);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = WT_CLUSTER;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, weighted_table_kernel, base, X, n_w, w, out, err);
 }
 
 }  // namespace mcx
