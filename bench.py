@@ -42,6 +42,7 @@ SEED = 1
 # flight on this workload, from ncu (smsp__thread_inst_executed.sum / steps);
 # DRAM bytes per launch from the same capture (None when stale).
 THREAD_INST_PER_STEP = 239.8          # ncu, 1e7-photon launch of this workload
+BATCH_THREAD_INST_PER_STEP = 245.4    # ncu, one batch_kernel launch over the 64 media (1024 threads, chunks of 128)
 DRAM_BYTES_PER_LAUNCH = 596736        # same capture; fixed per launch (L2-resident tallies)
 LANES_PER_SM = 128
 SMEM_WAVEFRONTS_PER_STEP = 0.650       # same capture: shared-memory wavefronts (128 B each) per photon-step
@@ -212,7 +213,9 @@ def _batch_vs_plain(E, dev, media, nph, steps, warmup, flush):
     if globals().get("NO_TUNE"):
         tune = dict(item_photons=0, block_size=0, skipped=True)
     else:
-        tune = autotune.tune_batch(batch, media, nph)
+        # at the full photon budgets: the best shape at a fraction of them is
+        # not the best here (the launch-shape differences are below 1 %)
+        tune = autotune.tune_batch(batch, media, nph, scale=1)
     # one image scale for the batch and the sequential runs (the batch's own
     # default: the largest budget's), so their tallies compare bit for bit
     frac = E.auto_frac_bits(max(nph))
@@ -690,6 +693,14 @@ def run_engine(args):
             "gpu_launches": 2 * args.steps, "clocks": clk, "roofline": roof}
     if not args.no_batched and ws == 1:
         line["batched"] = batched_comparison(E, dev, args.steps, args.warmup, flush)
+        # the same walk loop over the 64 media (optical depths 0.5-20): its
+        # place on the issue roofline, from its own instruction count
+        ach_b = BATCH_THREAD_INST_PER_STEP * line["batched"]["value"] / 1e12
+        line["batched"]["roofline"] = {
+            "bound": "alu", "achieved": ach_b, "peak": peak, "unit": "Tinst/s", "frac": ach_b / peak,
+            "per_unit": "%g thread-instructions per photon-step (ncu, batch_kernel on this workload), "
+                        "peak = %d SMs x %d lanes x %.0f MHz" % (BATCH_THREAD_INST_PER_STEP, sms, LANES_PER_SM,
+                                                                 sm_max)}
         line["adjoint"] = adjoint_comparison(E, dev, args.steps, flush)
         line["paper_mode"] = paper_comparison(E, dev, args.steps, flush)
         line["plume"] = plume_leg(E, dev, args.steps, flush)

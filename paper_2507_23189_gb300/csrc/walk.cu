@@ -759,7 +759,9 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ Bat
     uint32_t parity = 0;
     const unsigned chunk = B.chunk;
     for (int m = 0; m < B.n_media; ++m) {
-        const MediumArgs &M = B.m[m];
+        // this medium's arguments, copied once: read through the dynamically
+        // indexed kernel parameter, every use in the walk would be a load
+        const MediumArgs M = B.m[m];
         unsigned long long *ctr = B.counters + m;
         if (threadIdx.x == 0) *S.item = *reinterpret_cast<volatile unsigned long long *>(ctr);
         __syncthreads();
