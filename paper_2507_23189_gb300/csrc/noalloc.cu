@@ -45,8 +45,8 @@ struct Cached {
 };
 Cached g_cache[kMaxDevices] = {};
 
-// The driver's context queries, reached through the runtime (no link to the
-// driver library): current context and its process-unique id.
+// The CUDA driver API's context queries, reached through the runtime (no
+// link to libcuda): current context and its process-unique id.
 typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
 typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
 
