@@ -408,8 +408,9 @@ mc_status mc_run_grid(const mc_grid *grid, const void *d_grid_work, const mc_med
  * summed by double-precision atomics and rounded once; the sums' last bits
  * depend on scheduling); *d_value = L
  * (double, fixed order).
- * d_work: mc_grid_adjoint_workspace_bytes(grid) bytes. The paper has no
- * gradients; this serves fitting the density of a heterogeneous medium. */
+ * d_work: mc_grid_adjoint_workspace_bytes(grid) bytes (three
+ * double-precision voxel arrays). The paper has no gradients; this serves
+ * fitting the density of a heterogeneous medium. */
 size_t mc_grid_adjoint_workspace_bytes(const mc_grid *grid);
 mc_status mc_grid_adjoint(const mc_grid *grid, const void *d_grid_work, const mc_medium *phase,
                           const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
@@ -418,7 +419,12 @@ mc_status mc_grid_adjoint(const mc_grid *grid, const void *d_grid_work, const mc
 
 /* mc_grid_adjoint with the flights' transmission scored at the null
  * collisions of delta tracking instead of integrated along each flight
- * (same workspace, arguments and outputs). The gradient walk uses majorants
+ * (same arguments and outputs; d_work: mc_grid_adjoint_nulls_workspace_bytes
+ * (grid) bytes, sixteen double-precision voxel arrays: eight copies each of
+ * the voxel sum and the column sources, over which the CTAs spread their
+ * atomics, since many CTAs adding to the same voxels near the beam at once
+ * serialise in L2; the copies are summed before the fold, so the result is
+ * that of one sum). The gradient walk uses majorants
  * majorant_scale (1 < scale <= 16) times the cell maxima, so every voxel
  * has mubar > mu_ext; a null collision at a point of voxel v then has
  * probability 1 - mu_ext / mubar, and its derivative with respect to n_v,
@@ -430,6 +436,7 @@ mc_status mc_grid_adjoint(const mc_grid *grid, const void *d_grid_work, const mc
  * max_events counts their tentative collisions. The paper has no
  * gradients; this trades the exact flight integrals for cheaper, noisier
  * per-voxel scores. */
+size_t mc_grid_adjoint_nulls_workspace_bytes(const mc_grid *grid);
 mc_status mc_grid_adjoint_nulls(const mc_grid *grid, const void *d_grid_work, const mc_medium *phase,
                                 const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,
                                 const float *d_adj_image, double majorant_scale, float *d_grad,

@@ -27,6 +27,7 @@ EXPORTS = ("mc_table_bytes", "mie_table_build", "mc_medium_from_density", "mc_wo
            "mc_adjoint_workspace_bytes", "mc_adjoint", "mc_paper_table_bytes", "mie_paper_table_build",
            "mc_metrics_out_len", "mc_metrics_workspace_bytes", "mc_image_metrics", "mie_mixture_table_build",
            "mc_grid_workspace_bytes", "mc_grid_prepare", "mc_run_grid", "mc_grid_adjoint_workspace_bytes",
+           "mc_grid_adjoint_nulls_workspace_bytes",
            "mc_grid_adjoint", "mc_check_within", "mc_wait_selftest", "mc_medium_from_optical_depth",
            "mc_auto_frac_bits", "mc_phase_table_weighted", "mc_grid_adjoint_nulls")
 
@@ -183,6 +184,8 @@ def lib():
                               C.c_int, C.c_int, vp]
     L.mc_grid_adjoint_workspace_bytes.restype = C.c_size_t
     L.mc_grid_adjoint_workspace_bytes.argtypes = [P(Grid)]
+    L.mc_grid_adjoint_nulls_workspace_bytes.restype = C.c_size_t
+    L.mc_grid_adjoint_nulls_workspace_bytes.argtypes = [P(Grid)]
     L.mc_grid_adjoint.restype = C.c_int
     L.mc_grid_adjoint.argtypes = [P(Grid), vp, P(Medium), P(Geometry), P(Camera), P(RunParams), vp, vp, vp, vp,
                                   vp, C.c_size_t, vp]

@@ -679,7 +679,19 @@ size_t mc_grid_adjoint_workspace_bytes(const mc_grid *g)
     const int rows = mcx::grid_adjoint_max_grid();
     if (rows < 1) return 0;
     const size_t n = (size_t)g->gx * g->gy * g->gz;
+    // voxel sum, column sources, first-flight row entries
     return kAlign + 3 * up(sizeof(double) * n) + up(sizeof(double) * (size_t)rows);
+}
+
+size_t mc_grid_adjoint_nulls_workspace_bytes(const mc_grid *g)
+{
+    int mx, my, mz;
+    if (!grid_dims(g, &mx, &my, &mz)) return 0;
+    const int rows = mcx::grid_adjoint_max_grid();
+    if (rows < 1) return 0;
+    const size_t n = (size_t)g->gx * g->gy * g->gz;
+    // kNullCopies copies each of the voxel sum and the column sources
+    return kAlign + 2 * (size_t)mcx::kNullCopies * up(sizeof(double) * n) + up(sizeof(double) * (size_t)rows);
 }
 
 namespace {
@@ -724,7 +736,7 @@ mc_status grid_adjoint_common(const mc_grid *g, const void *d_grid_work, const m
     m.mu_s = 1.0;
     m.mu_a = 0.0;
     if ((s = validate_all(&m, geom, camera, run)) != MC_OK) return s;
-    const size_t need = mc_grid_adjoint_workspace_bytes(g);
+    const size_t need = nulls ? mc_grid_adjoint_nulls_workspace_bytes(g) : mc_grid_adjoint_workspace_bytes(g);
     if (!need) return MC_ERR_CUDA;
     if (work_bytes < need) return MC_ERR_NOMEM;
     const size_t n = (size_t)g->gx * g->gy * g->gz;
@@ -733,11 +745,16 @@ mc_status grid_adjoint_common(const mc_grid *g, const void *d_grid_work, const m
     std::memset(&a, 0, sizeof a);
     fill_grid(a.g, g, mx, my, mz, d_grid_work, &m, geom, camera, run, d_error, nullptr, nullptr, nullptr);
     const size_t nb = up(sizeof(double) * n);
+    // exact: s1, ex, gsum; null scores: kNullCopies copies of s1, then of gsum
+    const size_t copies = nulls ? (size_t)mcx::kNullCopies : 1;
+    const size_t arrays = nulls ? 2 * copies : 3;
     a.g.counter = reinterpret_cast<unsigned long long *>(w);
-    a.gsum = reinterpret_cast<double *>(w + kAlign);
-    a.s1 = reinterpret_cast<double *>(w + kAlign + nb);
-    a.ex = reinterpret_cast<double *>(w + kAlign + 2 * nb);
-    a.partials = reinterpret_cast<double *>(w + kAlign + 3 * nb);
+    a.s1 = reinterpret_cast<double *>(w + kAlign);
+    a.ex = nulls ? nullptr : reinterpret_cast<double *>(w + kAlign + nb);
+    a.gsum = reinterpret_cast<double *>(w + kAlign + (nulls ? copies : 2) * nb);
+    a.rep = nb / sizeof(double);
+    a.copies = (int)copies;
+    a.partials = reinterpret_cast<double *>(w + kAlign + arrays * nb);
     a.adj = d_adj_image;
     a.grad = d_grad;
     a.k_ext = (float)g->k_ext;
@@ -745,7 +762,7 @@ mc_status grid_adjoint_common(const mc_grid *g, const void *d_grid_work, const m
     a.maj_scale = (float)maj_scale;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto fail = [](cudaError_t x) { return x != cudaSuccess; };
-    if (fail(cudaMemsetAsync(w, 0, kAlign + 3 * nb, st)) ||
+    if (fail(cudaMemsetAsync(w, 0, kAlign + arrays * nb, st)) ||
         fail(cudaMemsetAsync(d_grad, 0, sizeof(float) * n, st)) ||
         fail(cudaMemsetAsync(d_value, 0, sizeof(double), st)))
         return MC_ERR_CUDA;

@@ -106,8 +106,12 @@ struct GridAdjArgs {
     GridArgs g;
     const float *adj;             // [nz][nx]
     // [gz][gy][gx] double-precision atomic sums: point, flight and own-voxel
-    // column terms; column sources above a collision; first-flight row suffix
+    // column terms; column sources above a collision; first-flight row suffix.
+    // gsum and s1 have `copies` copies each, rep elements apart: CTA b adds
+    // into copy b % copies (null scores: spreads the atomics on hot voxels)
     double *gsum, *s1, *ex;
+    size_t rep;
+    int copies;
     float *grad;                  // [gz][gy][gx] output (written by the fold)
     float k_ext;
     double *partials;             // [grid] value per CTA
@@ -147,10 +151,15 @@ cudaError_t launch_grid_prepare(const float *density, int gx, int gy, int gz, in
 cudaError_t launch_grid_adjoint(const GridAdjArgs &a, int partial_rows, double *value, cudaStream_t stream);
 
 // grad[v] = gsum[v] + vx * (sum of ex after v in its row along x)
-//           - k_ext vy * (sum of s1 below v in its column along y); gsum is
-// updated in place by the row sums.
-cudaError_t launch_gradient_fold(double *gsum, const double *s1, const double *ex, float *grad, int gx, int gy,
-                                 int gz, double k_ext, double vx, double vy, cudaStream_t stream);
+//           - k_ext vy * (sum of s1 below v in its column along y), gsum and
+// s1 each the sum of its `copies` copies (rep elements apart; summed into
+// the first), gsum updated in place by the row sums; ex null: no row terms.
+cudaError_t launch_gradient_fold(double *gsum, double *s1, size_t rep, int copies, const double *ex,
+                                 float *grad, int gx, int gy, int gz, double k_ext, double vx, double vy,
+                                 cudaStream_t stream);
+
+// Copies of the voxel sums the null-score gradient spreads its atomics over.
+constexpr int kNullCopies = 8;
 
 // CTAs the grid adjoint may use on the current device (for workspace sizing).
 int grid_adjoint_max_grid();

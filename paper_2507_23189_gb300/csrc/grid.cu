@@ -112,13 +112,33 @@ __global__ void fold_kernel(const double *__restrict__ gsum, const double *__res
 
 }  // namespace
 
-cudaError_t launch_gradient_fold(double *gsum, const double *s1, const double *ex, float *grad, int gx, int gy,
-                                 int gz, double k_ext, double vx, double vy, cudaStream_t st)
+namespace {
+// a[i] += a[i + c rep] for c = 1 .. copies - 1, in that order
+__global__ void combine_kernel(double *__restrict__ a, size_t rep, int copies, size_t n)
 {
-    const long long rows = (long long)gy * gz;
-    row_suffix_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(gsum, ex, gx, rows, vx);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double t = a[i];
+        for (int c = 1; c < copies; ++c) t += a[i + (size_t)c * rep];
+        a[i] = t;
+    }
+}
+}  // namespace
+
+cudaError_t launch_gradient_fold(double *gsum, double *s1, size_t rep, int copies, const double *ex,
+                                 float *grad, int gx, int gy, int gz, double k_ext, double vx, double vy,
+                                 cudaStream_t st)
+{
+    cudaError_t e;
+    if (copies > 1) {
+        combine_kernel<<<1024, 256, 0, st>>>(gsum, rep, copies, (size_t)gx * gy * gz);
+        combine_kernel<<<1024, 256, 0, st>>>(s1, rep, copies, (size_t)gx * gy * gz);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (ex) {
+        const long long rows = (long long)gy * gz;
+        row_suffix_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(gsum, ex, gx, rows, vx);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const long long cols = (long long)gx * gz;
     fold_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(gsum, s1, grad, gx, gy, gz, k_ext * vy);
     return cudaGetLastError();

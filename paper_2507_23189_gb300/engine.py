@@ -447,9 +447,10 @@ class Engine:
         if tuple(adj.shape) != (self.camera.nz, self.camera.nx):
             raise ValueError("adjoint image must be [nz, nx]")
         g, geo, c = grid.as_c(), self.geometry.as_c(), self.camera.as_c()
-        nbytes = N.lib().mc_grid_adjoint_workspace_bytes(C.byref(g))
+        size_fn = "mc_grid_adjoint_workspace_bytes" if nulls is None else "mc_grid_adjoint_nulls_workspace_bytes"
+        nbytes = getattr(N.lib(), size_fn)(C.byref(g))
         if nbytes == 0:
-            raise N.McError("mc_grid_adjoint_workspace_bytes", -1)
+            raise N.McError(size_fn, -1)
         work = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         grad = torch.empty(tuple(grid.density.shape), dtype=torch.float32, device=self.device)
         value = torch.empty(1, dtype=torch.float64, device=self.device)
