@@ -420,11 +420,11 @@ mc_status mc_grid_adjoint(const mc_grid *grid, const void *d_grid_work, const mc
 /* mc_grid_adjoint with the flights' transmission scored at the null
  * collisions of delta tracking instead of integrated along each flight
  * (same arguments and outputs; d_work: mc_grid_adjoint_nulls_workspace_bytes
- * (grid) bytes, sixteen double-precision voxel arrays: eight copies each of
- * the voxel sum and the column sources, over which the CTAs spread their
- * atomics, since many CTAs adding to the same voxels near the beam at once
- * serialise in L2; the copies are summed before the fold, so the result is
- * that of one sum). The gradient walk uses majorants
+ * (grid) bytes: the voxel sum and the column sources, and eight copies of
+ * both over the central 32 x 32 voxels of y and z (all x) around the beam
+ * axis, over which the CTAs spread their atomics, since many CTAs adding to
+ * the same voxels there at once serialise in L2; the copies are summed into
+ * the voxels before the fold). The gradient walk uses majorants
  * majorant_scale (1 < scale <= 16) times the cell maxima, so every voxel
  * has mubar > mu_ext; a null collision at a point of voxel v then has
  * probability 1 - mu_ext / mubar, and its derivative with respect to n_v,

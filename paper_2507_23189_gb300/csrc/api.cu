@@ -683,6 +683,14 @@ size_t mc_grid_adjoint_workspace_bytes(const mc_grid *g)
     return kAlign + 3 * up(sizeof(double) * n) + up(sizeof(double) * (size_t)rows);
 }
 
+// Voxels in the null-score gradient's box around the beam axis: all x, the
+// central min(kNullBox, gy, gz) voxels along y and z.
+static size_t null_box(const mc_grid *g)
+{
+    const size_t bw = (size_t)std::min(mcx::kNullBox, std::min(g->gy, g->gz));
+    return (size_t)g->gx * bw * bw;
+}
+
 size_t mc_grid_adjoint_nulls_workspace_bytes(const mc_grid *g)
 {
     int mx, my, mz;
@@ -690,8 +698,10 @@ size_t mc_grid_adjoint_nulls_workspace_bytes(const mc_grid *g)
     const int rows = mcx::grid_adjoint_max_grid();
     if (rows < 1) return 0;
     const size_t n = (size_t)g->gx * g->gy * g->gz;
-    // kNullCopies copies each of the voxel sum and the column sources
-    return kAlign + 2 * (size_t)mcx::kNullCopies * up(sizeof(double) * n) + up(sizeof(double) * (size_t)rows);
+    // the voxel sum and the column sources, and kNullCopies copies of each
+    // over the box around the beam axis
+    return kAlign + 2 * up(sizeof(double) * n) + 2 * (size_t)mcx::kNullCopies * up(sizeof(double) * null_box(g)) +
+           up(sizeof(double) * (size_t)rows);
 }
 
 namespace {
@@ -745,16 +755,24 @@ mc_status grid_adjoint_common(const mc_grid *g, const void *d_grid_work, const m
     std::memset(&a, 0, sizeof a);
     fill_grid(a.g, g, mx, my, mz, d_grid_work, &m, geom, camera, run, d_error, nullptr, nullptr, nullptr);
     const size_t nb = up(sizeof(double) * n);
-    // exact: s1, ex, gsum; null scores: kNullCopies copies of s1, then of gsum
-    const size_t copies = nulls ? (size_t)mcx::kNullCopies : 1;
-    const size_t arrays = nulls ? 2 * copies : 3;
+    // exact: s1, ex, gsum; null scores: s1, gsum, then the box copies of s1
+    // and of gsum
+    const int bw = std::min(mcx::kNullBox, std::min(g->gy, g->gz));
+    const size_t bb = up(sizeof(double) * null_box(g));
+    const size_t region = nulls ? 2 * nb + 2 * (size_t)mcx::kNullCopies * bb : 3 * nb;
     a.g.counter = reinterpret_cast<unsigned long long *>(w);
     a.s1 = reinterpret_cast<double *>(w + kAlign);
     a.ex = nulls ? nullptr : reinterpret_cast<double *>(w + kAlign + nb);
-    a.gsum = reinterpret_cast<double *>(w + kAlign + (nulls ? copies : 2) * nb);
-    a.rep = nb / sizeof(double);
-    a.copies = (int)copies;
-    a.partials = reinterpret_cast<double *>(w + kAlign + arrays * nb);
+    a.gsum = reinterpret_cast<double *>(w + kAlign + (nulls ? 1 : 2) * nb);
+    a.bs1 = nulls ? reinterpret_cast<double *>(w + kAlign + 2 * nb) : nullptr;
+    a.bgs = nulls ? reinterpret_cast<double *>(w + kAlign + 2 * nb + mcx::kNullCopies * bb) : nullptr;
+    a.copies = nulls ? mcx::kNullCopies : 1;
+    a.bw = nulls ? bw : 0;
+    a.by0 = g->gy / 2 - bw / 2;   // centred on the beam axis (y = z = 0)
+    a.bz0 = g->gz / 2 - bw / 2;
+    a.nbox = null_box(g);
+    a.bstride = bb / sizeof(double);
+    a.partials = reinterpret_cast<double *>(w + kAlign + region);
     a.adj = d_adj_image;
     a.grad = d_grad;
     a.k_ext = (float)g->k_ext;
@@ -762,7 +780,7 @@ mc_status grid_adjoint_common(const mc_grid *g, const void *d_grid_work, const m
     a.maj_scale = (float)maj_scale;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto fail = [](cudaError_t x) { return x != cudaSuccess; };
-    if (fail(cudaMemsetAsync(w, 0, kAlign + arrays * nb, st)) ||
+    if (fail(cudaMemsetAsync(w, 0, kAlign + region, st)) ||
         fail(cudaMemsetAsync(d_grad, 0, sizeof(float) * n, st)) ||
         fail(cudaMemsetAsync(d_value, 0, sizeof(double), st)))
         return MC_ERR_CUDA;

@@ -107,11 +107,14 @@ struct GridAdjArgs {
     const float *adj;             // [nz][nx]
     // [gz][gy][gx] double-precision atomic sums: point, flight and own-voxel
     // column terms; column sources above a collision; first-flight row suffix.
-    // gsum and s1 have `copies` copies each, rep elements apart: CTA b adds
-    // into copy b % copies (null scores: spreads the atomics on hot voxels)
+    // With null scores, the voxels of the box iy in [by0, by0 + bw), iz in
+    // [bz0, bz0 + bw) around the beam axis (where many CTAs add at once) are
+    // summed instead in `copies` copies of the box, bstride elements apart,
+    // CTA b adding into copy b % copies: bgs for gsum, bs1 for s1
     double *gsum, *s1, *ex;
-    size_t rep;
-    int copies;
+    double *bgs, *bs1;
+    int copies, by0, bz0, bw;
+    size_t nbox, bstride;
     float *grad;                  // [gz][gy][gx] output (written by the fold)
     float k_ext;
     double *partials;             // [grid] value per CTA
@@ -151,15 +154,21 @@ cudaError_t launch_grid_prepare(const float *density, int gx, int gy, int gz, in
 cudaError_t launch_grid_adjoint(const GridAdjArgs &a, int partial_rows, double *value, cudaStream_t stream);
 
 // grad[v] = gsum[v] + vx * (sum of ex after v in its row along x)
-//           - k_ext vy * (sum of s1 below v in its column along y), gsum and
-// s1 each the sum of its `copies` copies (rep elements apart; summed into
-// the first), gsum updated in place by the row sums; ex null: no row terms.
-cudaError_t launch_gradient_fold(double *gsum, double *s1, size_t rep, int copies, const double *ex,
-                                 float *grad, int gx, int gy, int gz, double k_ext, double vx, double vy,
-                                 cudaStream_t stream);
+//           - k_ext vy * (sum of s1 below v in its column along y); gsum is
+// updated in place by the row sums; ex null: no row terms.
+cudaError_t launch_gradient_fold(double *gsum, const double *s1, const double *ex, float *grad, int gx, int gy,
+                                 int gz, double k_ext, double vx, double vy, cudaStream_t stream);
 
-// Copies of the voxel sums the null-score gradient spreads its atomics over.
+// gsum[v] += sum over the copies of bgs at v's box element, s1 likewise
+// (copies bstride elements apart, summed in copy order).
+cudaError_t launch_box_merge(double *gsum, double *s1, const double *bgs, const double *bs1, int copies,
+                             size_t nbox, size_t bstride, int gx, int gy, int by0, int bz0, int bw,
+                             cudaStream_t stream);
+
+// The null-score gradient's copies of the voxel sums near the beam axis: how
+// many, and the box's width in voxels along y and z (at most the grid's).
 constexpr int kNullCopies = 8;
+constexpr int kNullBox = 32;
 
 // CTAs the grid adjoint may use on the current device (for workspace sizing).
 int grid_adjoint_max_grid();

@@ -113,27 +113,39 @@ __global__ void fold_kernel(const double *__restrict__ gsum, const double *__res
 }  // namespace
 
 namespace {
-// a[i] += a[i + c rep] for c = 1 .. copies - 1, in that order
-__global__ void combine_kernel(double *__restrict__ a, size_t rep, int copies, size_t n)
+// One thread per box element (ix fastest): its copies summed in copy order
+// into the voxel's own sums.
+__global__ void box_merge_kernel(double *__restrict__ gsum, double *__restrict__ s1, const double *__restrict__ bgs,
+                                 const double *__restrict__ bs1, int copies, size_t nbox, size_t bstride, int gx,
+                                 int gy, int by0, int bz0, int bw)
 {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        double t = a[i];
-        for (int c = 1; c < copies; ++c) t += a[i + (size_t)c * rep];
-        a[i] = t;
+    for (size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x; b < nbox; b += (size_t)gridDim.x * blockDim.x) {
+        double tg = 0.0, ts = 0.0;
+        for (int c = 0; c < copies; ++c) {
+            tg += bgs[(size_t)c * bstride + b];
+            ts += bs1[(size_t)c * bstride + b];
+        }
+        const int ix = (int)(b % (size_t)gx);
+        const size_t r = b / (size_t)gx;
+        const int iy = by0 + (int)(r % (size_t)bw), iz = bz0 + (int)(r / (size_t)bw);
+        const size_t v = ((size_t)iz * gy + iy) * gx + ix;
+        gsum[v] += tg;
+        s1[v] += ts;
     }
 }
 }  // namespace
 
-cudaError_t launch_gradient_fold(double *gsum, double *s1, size_t rep, int copies, const double *ex,
-                                 float *grad, int gx, int gy, int gz, double k_ext, double vx, double vy,
-                                 cudaStream_t st)
+cudaError_t launch_box_merge(double *gsum, double *s1, const double *bgs, const double *bs1, int copies,
+                             size_t nbox, size_t bstride, int gx, int gy, int by0, int bz0, int bw, cudaStream_t st)
+{
+    box_merge_kernel<<<1024, 256, 0, st>>>(gsum, s1, bgs, bs1, copies, nbox, bstride, gx, gy, by0, bz0, bw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gradient_fold(double *gsum, const double *s1, const double *ex, float *grad, int gx, int gy,
+                                 int gz, double k_ext, double vx, double vy, cudaStream_t st)
 {
     cudaError_t e;
-    if (copies > 1) {
-        combine_kernel<<<1024, 256, 0, st>>>(gsum, rep, copies, (size_t)gx * gy * gz);
-        combine_kernel<<<1024, 256, 0, st>>>(s1, rep, copies, (size_t)gx * gy * gz);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
     if (ex) {
         const long long rows = (long long)gy * gz;
         row_suffix_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(gsum, ex, gx, rows, vx);

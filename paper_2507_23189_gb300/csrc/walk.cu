@@ -1261,10 +1261,17 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
     const float INF = __int_as_float(0x7f800000);
-    // this CTA's copy of the voxel sum: many CTAs adding to the same hot
-    // voxels at once (near the beam) serialise in L2, copies spread them
-    const size_t cp = (size_t)(blockIdx.x % (unsigned)A.copies) * A.rep;
-    double *gs = A.gsum + cp, *s1c = A.s1 + cp;
+    // null scores: inside the box around the beam axis, this CTA's copy of
+    // the voxel sums (many CTAs adding to the same voxels there at once
+    // serialise in L2; the copies spread them)
+    const size_t cpb = (size_t)(blockIdx.x % (unsigned)A.copies) * A.bstride;
+    double *gs = A.gsum, *s1c = A.s1, *bgs = A.bgs + cpb, *bs1 = A.bs1 + cpb;
+    auto slot = [&](double *main, double *box, int ix, int iy, int iz, size_t v) -> double * {
+        const unsigned by = (unsigned)(iy - A.by0), bz = (unsigned)(iz - A.bz0);
+        if (NULLS && by < (unsigned)A.bw && bz < (unsigned)A.bw)
+            return box + ((size_t)bz * A.bw + by) * G.gx + ix;
+        return main + v;
+    };
     unsigned long long pool_next = 0, pool_end = 0;
     bool alive = false, done = false;
     int pass = 0;
@@ -1357,7 +1364,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                 if (NULLS && !(u3 < acc) && pass == 1) {
                     // null collision: its score times the camera terms after it
                     const float B = Ptot - P;
-                    if (B != 0.f) atomicAdd(&gs[v], widen(-B * mc_div(A.k_ext, mb - cell.x)));
+                    if (B != 0.f) atomicAdd(slot(gs, bgs, ix, iy, iz, v), widen(-B * mc_div(A.k_ext, mb - cell.x)));
                 }
                 if (u3 < acc) {
                     u3 = mc_div(u3, acc);
@@ -1409,8 +1416,8 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                                 nseg = A0.n + 1;
                             }
                         }
-                        if (gv != 0.f) atomicAdd(&gs[v], widen(gv));
-                        if (Aj != 0.f) atomicAdd(&s1c[v], widen(Aj));
+                        if (gv != 0.f) atomicAdd(slot(gs, bgs, ix, iy, iz, v), widen(gv));
+                        if (Aj != 0.f) atomicAdd(slot(s1c, bs1, ix, iy, iz, v), widen(Aj));
                     }
                     P += Aj;
                     px = rx; py = ry; pz = rz;
@@ -2015,8 +2022,13 @@ cudaError_t launch_grid_adjoint_one(const GridAdjArgs &a, int rows, double *valu
     if (grid > rows) grid = rows;
     kern<<<(unsigned)grid, GADJ_BLOCK, smem, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = launch_gradient_fold(a.gsum, a.s1, a.rep, a.copies, NULLS ? nullptr : a.ex, a.grad, a.g.gx, a.g.gy,
-                             a.g.gz, (double)a.k_ext, (double)a.g.vx, (double)a.g.vy, st);
+    if (NULLS) {
+        e = launch_box_merge(a.gsum, a.s1, a.bgs, a.bs1, a.copies, a.nbox, a.bstride, a.g.gx, a.g.gy, a.by0, a.bz0,
+                             a.bw, st);
+        if (e != cudaSuccess) return e;
+    }
+    e = launch_gradient_fold(a.gsum, a.s1, NULLS ? nullptr : a.ex, a.grad, a.g.gx, a.g.gy, a.g.gz, (double)a.k_ext,
+                             (double)a.g.vx, (double)a.g.vy, st);
     if (e != cudaSuccess) return e;
     adjoint_reduce<<<1, RED_BLOCK, 0, st>>>(a.partials, (int)grid, 1, value);
     return cudaGetLastError();
