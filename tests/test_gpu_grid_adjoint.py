@@ -264,6 +264,41 @@ def test_null_scores_match_oracle_multiple_scattering(gpu, oracle_mod, ps_table,
     assert np.max(np.abs(bg - bo)) <= 1e-2 * np.max(np.abs(bo))
 
 
+def test_null_scores_match_oracle_with_a_partial_beam_box(gpu, oracle_mod, ps_table, ps_oracle_table):
+    """A grid wider than the null-score kernel's box of copies around the beam
+    axis (64 x 64 voxels across, the box the central 32 x 32): the voxels
+    summed through the copies and those summed directly, against the oracle on
+    the same photons, through block sums inside and outside the box."""
+    import torch
+    dens = _rough((64, 64, 32), 15, 1500.0)
+    k_ext, k_sca = 4e-5, 3.8e-5
+    nx = nz = 32
+    adj = np.random.default_rng(8).uniform(0, 1, (nz, nx)).astype(np.float32)
+    g = _grid(gpu, dens, k_ext, k_sca, 0.0, (8, 8, 8))
+    n = 100_000
+    e = gpu.Engine(gpu.Camera(nx, nz, 64, R_MAX), gpu.Geometry(LX, LY, LZ))
+    val, grad = e.grid_adjoint(g, gpu.Medium(1.0, 0.0, "table", 0.0, ps_table), torch.from_numpy(adj), n,
+                               seed=13, rr_threshold=1e-2, nulls=1.25)
+    e.check()
+    o = oracle_mod.grid_adjoint(adj.astype(np.float64), nulls=True, max_events=4096, phase="mie",
+                                table=ps_oracle_table, mu_s=0.0, n_photons=n, nx=nx, nz=nz, seed=13,
+                                rr_threshold=1e-2,
+                                grid=dict(density=dens.astype(np.float64), k_ext=k_ext, k_sca=k_sca,
+                                          block=(8, 8, 8), majorant_scale=1.25))
+    gg_ = grad.cpu().numpy().astype(np.float64)
+    assert val.item() == pytest.approx(o["value"], rel=2e-4)
+    # 8^3-voxel blocks; the box covers blocks 2..5 along y and z
+    blk = lambda t: t.reshape(8, 8, 8, 8, 4, 8).sum(axis=(1, 3, 5))
+    bg, bo = blk(gg_), blk(o["grad"])
+    inside = np.zeros(bg.shape, bool)
+    inside[2:6, 2:6, :] = True
+    scale = np.max(np.abs(bo))
+    print("partial box: worst block inside %.2e, outside %.2e of max" %
+          (np.max(np.abs(bg - bo)[inside]) / scale, np.max(np.abs(bg - bo)[~inside]) / scale))
+    assert np.max(np.abs(bo[inside])) > 0 and np.max(np.abs(bo[~inside])) > 0
+    assert np.max(np.abs(bg - bo)) <= 1e-3 * scale
+
+
 def test_null_scores_and_exact_lengths_agree_in_expectation(gpu, ps_table):
     """The two estimators on independent photons (their majorants differ):
     block sums agree within the combined batch errors."""
