@@ -181,6 +181,13 @@ typedef struct {
     int n_radial;           /* far-face (x = lx) radial profile bins           */
     double r_max;           /* radial profile range [0, r_max)                 */
 } mc_camera;
+/* Limits: nx, nz in [1, 8192], n_radial in [1, 65536]. The kernels sum the
+ * radial profile (8 bytes a bin) and the totals in shared memory next to the
+ * phase table (a 4096-bin table takes 41 KB, the largest, 16384 bins, 164 KB;
+ * the grid walks add 4 bytes per majorant cell): a combination that does not
+ * fit in one CTA's shared memory (227 KB on GB300) is refused with
+ * MC_ERR_ARG before anything runs. The image needs no room there: the rows
+ * that do not fit are summed in global memory. */
 
 typedef struct {
     uint64_t n_photons;     /* photons to run, at most 2^31 per call (the
@@ -248,8 +255,9 @@ size_t mc_workspace_bytes(const mc_camera *camera);
  * 0). Tallies go to *tallies in fixed point: the image [nz][nx], the radial
  * profile of far-face exits, the MC_TOT_* totals. run->accumulate = 0 zeroes
  * them first (on the stream), 1 adds to them. The error word is only OR-ed.
- * Returns at once: MC_ERR_ARG (invalid argument, or an image tile that
- * image_mode 1 cannot hold in shared memory), MC_ERR_NOMEM (workspace too
+ * Returns at once: MC_ERR_ARG (invalid argument, a phase table and radial
+ * profile too large for shared memory together (see mc_camera), or an image
+ * tile that image_mode 1 cannot hold there), MC_ERR_NOMEM (workspace too
  * small) or MC_ERR_CUDA (a launch failed) before anything runs on the
  * device, MC_OK when queued. Device-side problems appear in the error word
  * (mc_check). Asynchronous on `stream`; the buffers must stay valid until
@@ -409,8 +417,12 @@ mc_status mc_run_grid(const mc_grid *grid, const void *d_grid_work, const mc_med
  * depend on scheduling); *d_value = L
  * (double, fixed order).
  * d_work: mc_grid_adjoint_workspace_bytes(grid) bytes (three
- * double-precision voxel arrays). The paper has no gradients; this serves
- * fitting the density of a heterogeneous medium. */
+ * double-precision voxel arrays). The kernel holds the phase table, the
+ * majorant cells and 12 KB of per-warp flight queues in shared memory: a
+ * table and cell count that do not fit there (the largest table with the
+ * most cells does not) are refused with MC_ERR_ARG before anything runs.
+ * The paper has no gradients; this serves fitting the density of a
+ * heterogeneous medium. */
 size_t mc_grid_adjoint_workspace_bytes(const mc_grid *grid);
 mc_status mc_grid_adjoint(const mc_grid *grid, const void *d_grid_work, const mc_medium *phase,
                           const mc_geometry *geom, const mc_camera *camera, const mc_run_params *run,

@@ -211,7 +211,13 @@ mc_status run_common(const mc_medium *m, const mc_geometry *g, const mc_camera *
     mc_status s;
     if ((s = validate_all(m, g, c, r)) != MC_OK) return s;
     if ((s = check_tallies(t, c)) != MC_OK) return s;
-    cudaError_t e;
+    mcx::WalkArgs a = make_args(m, g, c, r, t);
+    a.c.trace = trace;
+    a.c.n_trace = n_trace;
+    a.c.n_trace_events = n_events;
+    // refused before anything is queued when the shared-memory plan does not fit
+    cudaError_t e = mcx::check_plan(a.c, launch_cfg(r));
+    if (e != cudaSuccess) return e == cudaErrorInvalidValue ? MC_ERR_ARG : MC_ERR_CUDA;
     if (!r->accumulate) {
         if ((e = cudaMemsetAsync(t->d_image, 0, sizeof(int64_t) * (size_t)c->nx * c->nz, st)))
             return cuda_status(e);
@@ -222,12 +228,7 @@ mc_status run_common(const mc_medium *m, const mc_geometry *g, const mc_camera *
     }
     if ((e = cudaMemsetAsync(t->d_work, 0, sizeof(unsigned long long), st))) return cuda_status(e);
     if (r->n_photons == 0) return MC_OK;
-    mcx::WalkArgs a = make_args(m, g, c, r, t);
-    a.c.trace = trace;
-    a.c.n_trace = n_trace;
-    a.c.n_trace_events = n_events;
     e = mcx::launch_walk(a, trace != nullptr, launch_cfg(r), st);
-    if (e == cudaErrorInvalidValue) return MC_ERR_ARG;  // requested image tile does not fit
     return cuda_status(e);
 }
 
@@ -374,6 +375,13 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom, 
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
+    {   // refused before anything is queued when the shared-memory plan does not fit
+        mcx::CommonArgs c;
+        std::memset(&c, 0, sizeof c);
+        fill_common(c, &inst[0].medium, geom, camera, run, d_error, 1);
+        if ((e = mcx::check_plan(c, launch_cfg(run))) != cudaSuccess)
+            return e == cudaErrorInvalidValue ? MC_ERR_ARG : MC_ERR_CUDA;
+    }
     if (!run->accumulate)
         for (int i = 0; i < n; ++i) {
             if ((e = cudaMemsetAsync(inst[i].d_image, 0, sizeof(int64_t) * (size_t)camera->nx * camera->nz, st)) ||
@@ -416,7 +424,6 @@ mc_status mc_run_batch(int n, const mc_instance *inst, const mc_geometry *geom, 
     }
     e = mcx::launch_batch(*a, launch_cfg(run), st);
     delete a;
-    if (e == cudaErrorInvalidValue) return MC_ERR_ARG;
     return cuda_status(e);
 }
 
@@ -657,6 +664,9 @@ mc_status mc_run_grid(const mc_grid *g, const void *d_grid_work, const mc_medium
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t npix = (size_t)camera->nx * camera->nz;
     auto fail = [](cudaError_t x) { return x != cudaSuccess; };
+    // refused before anything is queued when the shared-memory plan does not fit
+    const cudaError_t pe = mcx::check_plan(a.c, launch_cfg(run));
+    if (pe != cudaSuccess) return pe == cudaErrorInvalidValue ? MC_ERR_ARG : MC_ERR_CUDA;
     if (fail(cudaMemsetAsync(tallies->d_work, 0, sizeof(unsigned long long), st))) return MC_ERR_CUDA;
     if (!run->accumulate) {
         if (fail(cudaMemsetAsync(tallies->d_image, 0, sizeof(int64_t) * npix, st)) ||
@@ -667,9 +677,7 @@ mc_status mc_run_grid(const mc_grid *g, const void *d_grid_work, const mc_medium
     if (d_trace && fail(cudaMemsetAsync(d_trace, 0xFF, sizeof(int32_t) * 12 * (size_t)n_trace * n_events, st)))
         return MC_ERR_CUDA;
     if (run->n_photons == 0) return MC_OK;
-    const cudaError_t e = mcx::launch_grid(a, d_trace != nullptr, launch_cfg(run), st);
-    if (e == cudaErrorInvalidValue) return MC_ERR_ARG;  // the shared-memory plan does not fit
-    return cuda_status(e);
+    return cuda_status(mcx::launch_grid(a, d_trace != nullptr, launch_cfg(run), st));
 }
 
 size_t mc_grid_adjoint_workspace_bytes(const mc_grid *g)
@@ -780,6 +788,9 @@ mc_status grid_adjoint_common(const mc_grid *g, const void *d_grid_work, const m
     a.maj_scale = (float)maj_scale;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto fail = [](cudaError_t x) { return x != cudaSuccess; };
+    // refused before anything is queued when the table and cells do not fit
+    const cudaError_t pe = mcx::grid_adjoint_check(a);
+    if (pe != cudaSuccess) return pe == cudaErrorInvalidValue ? MC_ERR_ARG : MC_ERR_CUDA;
     if (fail(cudaMemsetAsync(w, 0, kAlign + region, st)) ||
         fail(cudaMemsetAsync(d_grad, 0, sizeof(float) * n, st)) ||
         fail(cudaMemsetAsync(d_value, 0, sizeof(double), st)))

@@ -133,6 +133,11 @@ struct LaunchCfg {
 // Launch the walk (or its trace variant) on `stream`. Returns cudaSuccess or
 // the launch error.
 cudaError_t launch_walk(const WalkArgs &a, bool trace, const LaunchCfg &cfg, cudaStream_t stream);
+// The shared-memory plan of a walk, batch or grid launch without launching
+// anything: cudaErrorInvalidValue when the table, the majorant cells, the
+// radial profile and the totals (with the image tile image_mode 1 asks for)
+// do not fit in one CTA's shared memory.
+cudaError_t check_plan(const CommonArgs &c, const LaunchCfg &cfg);
 
 // Launch the batched walk (phase fixed by c.phase_kind) on `stream`.
 cudaError_t launch_batch(const BatchArgs &a, const LaunchCfg &cfg, cudaStream_t stream);
@@ -152,6 +157,9 @@ cudaError_t launch_grid_prepare(const float *density, int gx, int gy, int gz, in
 
 // Launch the density-gradient replay, the column fold and the value reduction.
 cudaError_t launch_grid_adjoint(const GridAdjArgs &a, int partial_rows, double *value, cudaStream_t stream);
+// cudaErrorInvalidValue when the gradient kernel's table, majorant cells and
+// flight queues do not fit in one CTA's shared memory (nothing launched).
+cudaError_t grid_adjoint_check(const GridAdjArgs &a);
 
 // grad[v] = gsum[v] + vx * (sum of ex after v in its row along x)
 //           - k_ext vy * (sum of s1 below v in its column along y); gsum is

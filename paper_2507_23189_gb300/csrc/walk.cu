@@ -2002,13 +2002,17 @@ cudaError_t launch_grid_one(const GridArgs &a, const LaunchCfg &cfg, size_t smem
     return cudaGetLastError();
 }
 
+size_t grid_adjoint_smem(const GridAdjArgs &a)
+{
+    const size_t tb = (a.g.c.phase_kind != MC_PHASE_HG) ? a.g.c.table_bytes : 0;
+    return tb + a.g.c.extra_bytes + 16 + sizeof(double) * (GADJ_BLOCK / 32) + sizeof(float) * GADJ_BLOCK * GADJ_SEG;
+}
+
 template <int PHASE, bool NULLS>
 cudaError_t launch_grid_adjoint_one(const GridAdjArgs &a, int rows, double *value, cudaStream_t st)
 {
     auto kern = grid_adjoint_kernel<PHASE, NULLS>;
-    const size_t tb = (PHASE != MC_PHASE_HG) ? a.g.c.table_bytes : 0;
-    const size_t smem = tb + a.g.c.extra_bytes + 16 + sizeof(double) * (GADJ_BLOCK / 32) +
-                        sizeof(float) * GADJ_BLOCK * GADJ_SEG;
+    const size_t smem = grid_adjoint_smem(a);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, bps = 0;
@@ -2069,6 +2073,15 @@ cudaError_t launch_walk(const WalkArgs &a0, bool trace, const LaunchCfg &cfg0, c
     return launch_sign_check(a, st);
 }
 
+cudaError_t check_plan(const CommonArgs &c0, const LaunchCfg &cfg0)
+{
+    CommonArgs c = c0;
+    LaunchCfg cfg = cfg0;
+    bool smem_img = false;
+    size_t smem = 0;
+    return plan_image(c, cfg, &smem_img, &smem);
+}
+
 namespace {
 cudaError_t launch_grid_kernel(const GridArgs &a, bool trace, const LaunchCfg &cfg, bool smem_img, size_t smem,
                                cudaStream_t st)
@@ -2105,6 +2118,16 @@ cudaError_t launch_grid(const GridArgs &a0, bool trace, const LaunchCfg &cfg0, c
     w.m = a.m;
     w.counter = a.counter;
     return launch_sign_check(w, st);
+}
+
+cudaError_t grid_adjoint_check(const GridAdjArgs &a)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return e;
+    return grid_adjoint_smem(a) <= (size_t)optin ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 int grid_adjoint_max_grid()
