@@ -9,7 +9,9 @@ images are not used.
   sweep       tau in {1, 2, 5, 10, 20}, Mie and H-G, 1e8 photons,
               256x256 image + 128-bin radial profile (headline: tau = 5, Mie)
   batched     64 media: d log-uniform in [1, 10] um, tau uniform in [0.5, 20],
-              photon budgets log-uniform in [1e6, 1e8], 128x128 images
+              photon budgets log-uniform in [1e6, 1e8], 128x128 images; the
+              list is recorded in batched_media.json (python -m
+              paper_2507_23189_gb300.workloads --write-batched)
   adjoint     tau = 5, Mie, 1e7 photons, 128x128; target at 0.9 mu_s0, mu_a = 0.01
   plume       256^3 voxel grid over the cuvette: a Gaussian plume (sigma 5 mm,
               centred at x = 22.5 mm on the beam axis) of polystyrene spheres
@@ -17,6 +19,7 @@ images are not used.
               equal-number quantile bins; peak optical depth 30 along the
               beam; 1e9 photons, 512x512 image
 """
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -70,6 +73,26 @@ def batched(n=64, seed=2026):
                  diameter_um=float(d[i])) for i in range(n)]
 
 
+BATCHED_RECORD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "batched_media.json")
+
+
+def batched_record(cases=None):
+    """The 64 media as a JSON-ready dict (the list the batched workload runs)."""
+    cases = batched() if cases is None else cases
+    return {"generator": "numpy.random.Philox(2026): 64 draws each of ln d ~ U[ln 1, ln 10] (um), "
+                         "tau ~ U[0.5, 20], ln N ~ U[ln 1e6, ln 1e8] (N truncated to an integer), in that order",
+            "image": [128, 128], "photon_seed": 1,
+            "media": [{"name": c.name, "diameter_um": c.diameter_um, "tau": c.tau, "n_photons": c.n_photons}
+                      for c in cases]}
+
+
+def write_batched_record(path=BATCHED_RECORD):
+    import json
+    with open(path, "w") as f:
+        json.dump(batched_record(), f, indent=1)
+        f.write("\n")
+
+
 def adjoint():
     return Case("adjoint-tau5-mie", 5.0, "mie", 10_000_000, 128, 128,
                 extra=dict(mu_s_factor=0.9, mu_a=0.01))
@@ -119,3 +142,12 @@ def rough_grid(shape, seed, mean=1.0, spread=0.6):
     """Seeded log-normal voxel field (a test input without structure)."""
     rng = np.random.Generator(np.random.Philox(seed))
     return (mean * np.exp(spread * rng.standard_normal(shape))).astype(np.float32)
+
+
+if __name__ == "__main__":
+    import sys
+    if sys.argv[1:] == ["--write-batched"]:
+        write_batched_record()
+        print(BATCHED_RECORD)
+    else:
+        raise SystemExit("usage: python -m paper_2507_23189_gb300.workloads --write-batched")

@@ -34,6 +34,17 @@ def test_batched_media_are_deterministic_and_in_range():
     assert [c.tau for c in W.batched(seed=7)] != [c.tau for c in a]
 
 
+def test_batched_media_match_their_record():
+    """The generated list equals the committed record bit for bit (a change of
+    numpy's Philox stream, or of the recipe, shows up here)."""
+    import json
+    with open(W.BATCHED_RECORD) as f:
+        rec = json.load(f)
+    assert rec == json.loads(json.dumps(W.batched_record()))
+    assert [(m["diameter_um"], m["tau"], m["n_photons"]) for m in rec["media"]] == \
+        [(c.diameter_um, c.tau, c.n_photons) for c in W.batched()]
+
+
 def test_size_bins_are_log_normal_quantile_centres():
     from scipy.stats import norm
     d, f = W.size_bins(5.0, 0.3, 16)
