@@ -63,8 +63,10 @@ def headline(n_photons=100_000_000):
     return Case("sweep-tau5-mie", 5.0, "mie", n_photons, 256, 256)
 
 
-def batched(n=64, seed=2026):
-    """Instance parameters from numpy's Philox (a 64-bit counter-based stream)."""
+def batched_draw(n=64, seed=2026):
+    """Instance parameters from numpy's Philox (a 64-bit counter-based stream).
+    The uniforms are the same on every platform; numpy's exp and log may not
+    be, in the last bit."""
     rng = np.random.Generator(np.random.Philox(seed))
     d = np.exp(rng.uniform(np.log(1.0), np.log(10.0), n))
     tau = rng.uniform(0.5, 20.0, n)
@@ -73,12 +75,25 @@ def batched(n=64, seed=2026):
                  diameter_um=float(d[i])) for i in range(n)]
 
 
+def batched(n=64, seed=2026):
+    """The batched media. The default 64 (seed 2026) are the recorded list in
+    batched_media.json, so every machine runs exactly the same media; other
+    arguments draw afresh (batched_draw)."""
+    if (n, seed) == (64, 2026) and os.path.exists(BATCHED_RECORD):
+        import json
+        with open(BATCHED_RECORD) as f:
+            rec = json.load(f)
+        return [Case(m["name"], float(m["tau"]), "mie", int(m["n_photons"]), rec["image"][0], rec["image"][1],
+                     seed=int(rec["photon_seed"]), diameter_um=float(m["diameter_um"])) for m in rec["media"]]
+    return batched_draw(n, seed)
+
+
 BATCHED_RECORD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "batched_media.json")
 
 
 def batched_record(cases=None):
-    """The 64 media as a JSON-ready dict (the list the batched workload runs)."""
-    cases = batched() if cases is None else cases
+    """The 64 media as a JSON-ready dict (by default a fresh draw)."""
+    cases = batched_draw() if cases is None else cases
     return {"generator": "numpy.random.Philox(2026): 64 draws each of ln d ~ U[ln 1, ln 10] (um), "
                          "tau ~ U[0.5, 20], ln N ~ U[ln 1e6, ln 1e8] (N truncated to an integer), in that order",
             "image": [128, 128], "photon_seed": 1,

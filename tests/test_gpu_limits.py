@@ -13,7 +13,7 @@ oracle on the same photons:
     weight exact, the radial profile summing exactly to the far-face total
     and, in groups of bins, within 3 sigma of the oracle's;
   * a radial profile too large to share the CTA's shared memory with the
-    table, and the largest table with the most majorant cells in the
+    table (one run or a batch), and the largest table with the most majorant cells in the
     density gradient's kernel, are refused on the host before anything
     runs (the tallies keep their contents); that table and grid with a
     128-bin profile fit a grid walk, whose traces follow the oracle's.
@@ -164,3 +164,15 @@ def test_largest_table_with_most_majorant_cells(gpu, oracle_mod):
     wide.check()
     assert int(eng.image[0, 0].item()) == 5 and int(wide.image[0, 0].item()) == 5
     assert eng.last_error == 0 and wide.last_error == 0
+
+
+def test_batch_with_profile_too_large_for_shared_memory_is_refused(gpu, ps_table):
+    from paper_2507_23189_gb300 import _native as N
+    b = gpu.Batch(2, gpu.Camera(64, 64, 65536, R_MAX), gpu.Geometry(LX, LY, LZ))
+    b.image.fill_(5)
+    med = gpu.Medium(TAU / LX, 0.0, "table", 0.0, ps_table)
+    with pytest.raises(N.McError) as ex:
+        b.run([med, med], [1000, 2000], [1, 2])
+    assert ex.value.status == -1
+    b.check()
+    assert int(b.image.min().item()) == 5 and int(b.image.max().item()) == 5
