@@ -43,7 +43,7 @@ SEED = 1
 # DRAM bytes per launch from the same capture (None when stale).
 THREAD_INST_PER_STEP = 239.8          # ncu, 1e7-photon launch of this workload
 BATCH_THREAD_INST_PER_STEP = 245.4    # ncu, one batch_kernel launch over the 64 media (1024 threads, chunks of 128)
-DRAM_BYTES_PER_LAUNCH = 596736        # same capture; fixed per launch (L2-resident tallies)
+DRAM_BYTES_PER_LAUNCH = 597248        # ncu, a 1e8-photon launch of this workload (table + tallies, L2-resident)
 LANES_PER_SM = 128
 SMEM_WAVEFRONTS_PER_STEP = 0.650       # same capture: shared-memory wavefronts (128 B each) per photon-step
 SMEM_BYTES_PER_CLK_SM = 128
