@@ -318,6 +318,11 @@ mc_status mc_run_host(const mc_medium *medium, const void *table, const mc_geome
     p += up(sizeof(uint32_t));
     t.d_work = p;
     t.work_bytes = mc_workspace_bytes(camera);
+    {   // refused before any copy is queued when the shared-memory plan does not fit
+        const mcx::WalkArgs a = make_args(&m, geom, camera, run, &t);
+        const cudaError_t pe = mcx::check_plan(a.c, launch_cfg(run));
+        if (pe != cudaSuccess) return pe == cudaErrorInvalidValue ? MC_ERR_ARG : MC_ERR_CUDA;
+    }
     auto fail = [](cudaError_t x) { return x != cudaSuccess; };
     if (tb && fail(cudaMemcpyAsync(d_table, table, tb, cudaMemcpyHostToDevice, st))) return MC_ERR_CUDA;
     if (fail(cudaMemsetAsync(t.d_error, 0, sizeof(uint32_t), st))) return MC_ERR_CUDA;

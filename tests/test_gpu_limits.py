@@ -13,7 +13,7 @@ oracle on the same photons:
     weight exact, the radial profile summing exactly to the far-face total
     and, in groups of bins, within 3 sigma of the oracle's;
   * a radial profile too large to share the CTA's shared memory with the
-    table (one run or a batch), and the largest table with the most majorant cells in the
+    table (one run, a batch, or the host-buffer entry point), and the largest table with the most majorant cells in the
     density gradient's kernel, are refused on the host before anything
     runs (the tallies keep their contents); that table and grid with a
     128-bin profile fit a grid walk, whose traces follow the oracle's.
@@ -176,3 +176,16 @@ def test_batch_with_profile_too_large_for_shared_memory_is_refused(gpu, ps_table
     assert ex.value.status == -1
     b.check()
     assert int(b.image.min().item()) == 5 and int(b.image.max().item()) == 5
+
+
+def test_host_buffer_entry_point_refuses_before_copying(gpu, ps_table):
+    import torch
+    from paper_2507_23189_gb300 import _native as N
+    med = gpu.Medium(TAU / LX, 0.0, "table", 0.0, ps_table)
+    cam, geo = gpu.Camera(64, 64, 65536, R_MAX), gpu.Geometry(LX, LY, LZ)
+    work = torch.empty(gpu.host_workspace_bytes(med, cam), dtype=torch.uint8, device="cuda")
+    image = np.full((64, 64), 5, dtype=np.int64)
+    with pytest.raises(N.McError) as ex:
+        gpu.run_host(med, geo, cam, 1000, work, image=image)
+    assert ex.value.status == -1
+    assert np.all(image == 5)
