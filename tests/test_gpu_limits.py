@@ -1,8 +1,10 @@
 """The CUDA path at the edges of the sizes the C ABI accepts, against the
 oracle on the same photons:
   * the smallest and largest equal-probability phase tables (64 and 16384
-    bins, Sec. 3.1.2), each built by the engine and, independently, by the
-    oracle: the first 32 events of 4096 photons under the trace rule;
+    bins, Sec. 3.1.2), and the paper's bisection table with 16 angles and
+    with 10240 (the most that fit shared memory; 16384 are refused), each
+    built by the engine and, independently, by the oracle: the first 32
+    events of 4096 photons under the trace rule;
   * a single-pixel camera, a 8192-pixel-wide camera four rows high and a
     four-pixel-wide one 8192 rows high (8192 is the largest side), with
     radial profiles of 1, 16384 and 7 bins (16384 bins next to the 4096-bin
@@ -189,3 +191,39 @@ def test_host_buffer_entry_point_refuses_before_copying(gpu, ps_table):
         gpu.run_host(med, geo, cam, 1000, work, image=image)
     assert ex.value.status == -1
     assert np.all(image == 5)
+
+
+def _paper_slope(mu):
+    # the paper table's camera density ~ 1 / sin(theta_c) inside an interval
+    return abs(mu) / max(1.0 - mu * mu, 1e-300)
+
+
+@pytest.mark.parametrize("n_theta", [16, 10240])
+def test_paper_table_size_extremes_follow_the_oracle(gpu, oracle_mod, n_theta):
+    """The paper's bisection table (Sec. 3.1.2) with the fewest angles and with
+    the most that fit shared memory beside the tallies (10240: 221 KB)."""
+    t = gpu.PaperTable(n_theta=n_theta)
+    x = oracle_mod.size_parameter(5.0, 1.33, 532.0)
+    ot = oracle_mod.paper_cdf(oracle_mod.PHASE_MIE, complex(1.59 / 1.33, 0.0), x, n_theta=n_theta)
+    n = 4096
+    eng = gpu.Engine(gpu.Camera(64, 64, 128, R_MAX), gpu.Geometry(LX, LY, LZ))
+    tr = gpu.decode_trace(eng.trace(gpu.Medium(TAU / LX, 0.0, "paper", 0.0, t), n, n, 32, seed=17))
+    eng.check()
+    o = oracle_mod.walk(mu_s=TAU / LX, phase="paper", table=ot, n_photons=n, nx=64, nz=64, seed=17, n_trace=n,
+                        n_trace_events=32)
+    cmp = compare_traces(tr, o["trace"], TAU / LX, nee_slope=_paper_slope)
+    print("paper", n_theta, "matched %d/%d flips %d events %d" % (cmp["matched"], n, cmp["flips"], cmp["events"]))
+    assert cmp["matched"] >= 0.999 * n, cmp["causes"][:5]
+    assert cmp["events"] > 1.5 * n
+
+
+def test_paper_table_too_large_for_shared_memory_is_refused(gpu):
+    from paper_2507_23189_gb300 import _native as N
+    t = gpu.PaperTable(n_theta=16384)                 # 344 KB
+    eng = gpu.Engine(gpu.Camera(64, 64, 128, R_MAX), gpu.Geometry(LX, LY, LZ))
+    eng.image.fill_(5)
+    with pytest.raises(N.McError) as ex:
+        eng.run(gpu.Medium(TAU / LX, 0.0, "paper", 0.0, t), 1000, seed=1)
+    assert ex.value.status == -1
+    eng.check()
+    assert int(eng.image[0, 0].item()) == 5
