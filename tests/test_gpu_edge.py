@@ -1,7 +1,8 @@
 """Edge cases and invariances of the CUDA path: empty and ragged ranges,
 64-bit photon indices, launch-shape independence, truncation flags, finite
-beams, error reporting, and the host-buffer entry point."""
+beams, error reporting, the host-buffer entry point, and a pure absorber."""
 import ctypes as C
+import math
 
 import numpy as np
 import pytest
@@ -218,3 +219,26 @@ def test_multi_wall_exits_in_a_cube_match_oracle(gpu, oracle_mod):
     for k in range(3):                     # reflected, far face, side faces
         assert g[k] == pytest.approx(o[k], rel=1e-4, abs=2.0)
     assert g[1] > 0.1 * n and g[2] > 0.3 * n and g[0] > 0.1 * n
+
+
+@pytest.mark.parametrize("phase", ["table", "hg"])
+def test_pure_absorber_matches_oracle(gpu, oracle_mod, ps_table, ps_oracle_table, phase):
+    """mu_s = 0 (albedo 0): every collision captures the whole weight (Eq. 16),
+    so the far face sees only ballistic photons, the other faces and the
+    camera nothing, and absorption takes the rest; a zero-weight photon goes
+    on until roulette ends it, step for step as in the oracle."""
+    n, tau = 100_000, 2.0
+    e = _eng(gpu, 16, 16)
+    e.run(gpu.Medium(0.0, tau / LX, phase, 0.5, ps_table), n, seed=4)
+    e.check()
+    r = e.result()
+    om = dict(phase="mie", table=ps_oracle_table) if phase == "table" else dict(phase="hg", hg_g=0.5)
+    o = oracle_mod.walk(mu_s=0.0, mu_a=tau / LX, n_photons=n, nx=16, nz=16, seed=4, **om)
+    raw = r["raw_totals"]
+    assert raw[0] == 0 and raw[2] == 0 and raw[1] == raw[6]
+    assert raw[1] + raw[3] == n << 32                  # exact: ballistic exits plus whole captures
+    assert not r["raw_image"].any() and o["image"].sum() == 0.0
+    assert abs(raw[1] / 2 ** 32 - o["totals"][6]) <= 1
+    assert abs(r["steps"] - o["steps"]) <= 2
+    p = math.exp(-tau)
+    assert abs(raw[1] / 2 ** 32 / n - p) < 5 * math.sqrt(p * (1 - p) / n)
