@@ -200,19 +200,23 @@ static void photon32(const oracle_walk_cfg *c, const float *omu, const float *pd
         if (c->max_scatter && n_coll >= c->max_scatter) {
             status = 5;
         } else {
-            /* polar angle as 1 - cos(theta) */
-            float om;
+            /* polar angle as om = 1 - cos(theta) and op = 1 + cos(theta) */
+            float om, op;
             if (c->phase_kind == ORACLE_PHASE_HG) {
                 const float D = fmaf(2.0f * g, u1, 1.0f - g);
                 om = 2.0f * (1.0f - g) * (1.0f - g) * (1.0f - u1) * fmaf(g, u1, 1.0f) / (D * D);
+                /* the inverse of Eq. 11 written for 1 + cos(theta) too, so that
+                   an angle near pi does not lose 1 + cos(theta) in 2 - om */
+                op = 2.0f * (1.0f + g) * (1.0f + g) * u1 * fmaf(g, u1, 1.0f - g) / (D * D);
             } else {
                 const float t = u1 * (float)c->n_bins;
                 const int i = (int)t;
                 const float f = t - (float)i;
                 om = fmaf(f, omu[i + 1] - omu[i], omu[i]);
+                op = 2.0f - om;
             }
-            const float mu = 1.0f - om;
-            const float st = sqrtf(fmaxf(om * (2.0f - om), 0.0f));
+            const float mu = om <= op ? 1.0f - om : op - 1.0f;
+            const float st = sqrtf(fmaxf(om * op, 0.0f));
             float sp, cp;
             sincosf(2.0f * PI_F * u2, &sp, &cp);
             /* Duff et al. basis around d */

@@ -128,6 +128,7 @@ void fill_medium(mcx::MediumArgs &m, const mc_medium *med, uint64_t n_photons, u
     m.hg_one_m_g = (float)(1.0 - gg);
     m.hg_two_g = (float)(2.0 * gg);
     m.hg_A = (float)(2.0 * (1.0 - gg) * (1.0 - gg));
+    m.hg_B = (float)(2.0 * (1.0 + gg) * (1.0 + gg));
     m.hg_a2 = (float)((1.0 - gg) * (1.0 - gg));
     m.hg_K = (float)((1.0 - gg * gg) / (4.0 * kPi));
     m.table = (med->phase_kind != MC_PHASE_HG) ? static_cast<const unsigned char *>(med->d_table) : nullptr;

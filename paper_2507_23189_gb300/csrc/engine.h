@@ -13,7 +13,8 @@ struct MediumArgs {
     float albedo;               // 1 - mu_a/mu_ext (Eq. 16 factor)
     float absorb_frac;          // mu_a/mu_ext
     float hg_g, hg_one_m_g, hg_two_g;
-    float hg_A;                 // 2 (1-g)^2        (sampling)
+    float hg_A;                 // 2 (1-g)^2        (sampling 1 - cos)
+    float hg_B;                 // 2 (1+g)^2        (sampling 1 + cos)
     float hg_a2;                // (1-g)^2           (density)
     float hg_K;                 // (1-g^2) / (4 pi)  (density per sr)
     const unsigned char *table; // packed blob in global memory (table_format.h)

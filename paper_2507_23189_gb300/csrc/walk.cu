@@ -368,12 +368,18 @@ __device__ __forceinline__ float sample_omu(const MediumArgs &M, const CommonArg
     return fmaf(f, o1 - o0, o0);
 }
 
+// 1 + cos(theta) of the H-G angle that sample_omu draws from the same u1:
+// Eq. 11 inverted as 2 (1+g)^2 u1 (1 - g + g u1) / (1 - g + 2 g u1)^2.
+__device__ __forceinline__ float hg_opu(const MediumArgs &M, float u1)
+{
+    const float D = fmaf(M.hg_two_g, u1, M.hg_one_m_g);
+    return mc_div(M.hg_B * u1 * fmaf(M.hg_g, u1, M.hg_one_m_g), D * D);
+}
+
 // d <- mu d + sin(theta) (cos phi e1 + sin phi e2), (e1, e2) the orthonormal
 // basis of Duff et al. (2017) around d, phi = 2 pi u2; renormalised.
-__device__ __forceinline__ void rotate(float &dx, float &dy, float &dz, float om, float u2)
+__device__ __forceinline__ void rotate_cs(float &dx, float &dy, float &dz, float mu, float st2, float u2)
 {
-    const float mu = 1.0f - om;
-    const float st2 = om * (2.0f - om);
     const float st = mc_sqrt0(st2);
     // phi = 2 pi u2 through the hardware sine / cosine, evaluated at
     // phi - pi in [-pi, pi) where they are most accurate
@@ -390,6 +396,32 @@ __device__ __forceinline__ void rotate(float &dx, float &dy, float &dz, float om
     const float nx = fmaf(mu, dx, st * qx), ny = fmaf(mu, dy, st * qy), nz = fmaf(mu, dz, st * qz);
     const float inv = mc_rsqrt(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
     dx = nx * inv; dy = ny * inv; dz = nz * inv;
+}
+
+// New direction at polar angle theta given as om = 1 - cos(theta).
+__device__ __forceinline__ void rotate(float &dx, float &dy, float &dz, float om, float u2)
+{
+    rotate_cs(dx, dy, dz, 1.0f - om, om * (2.0f - om), u2);
+}
+
+// The same given om = 1 - cos(theta) and op = 1 + cos(theta), each from its
+// own closed form: cos(theta) from the smaller of the two and sin^2 = om op,
+// so a direction near theta = pi keeps its accuracy (2 - om, formed from a
+// rounded om close to 2, would not).
+__device__ __forceinline__ void rotate_hg(float &dx, float &dy, float &dz, float om, float op, float u2)
+{
+    rotate_cs(dx, dy, dz, om <= op ? 1.0f - om : op - 1.0f, om * op, u2);
+}
+
+// Scattering: draw the polar angle with u1 and turn the direction (azimuth
+// from u2).
+template <int PHASE>
+__device__ __forceinline__ void scatter(const MediumArgs &M, const CommonArgs &C, const Smem &S, float u1, float u2,
+                                        float &dx, float &dy, float &dz)
+{
+    const float om = sample_omu<PHASE>(M, C, S, u1);
+    if (PHASE == MC_PHASE_HG) rotate_hg(dx, dy, dz, om, hg_opu(M, u1), u2);
+    else rotate(dx, dy, dz, om, u2);
 }
 
 template <int PHASE, bool SMEM_IMAGE>
@@ -659,7 +691,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
                 status = 5;
                 alive = false;
             } else {
-                rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
+                scatter<PHASE>(M, C, S, u1, u2, dx, dy, dz);
                 // weight threshold / roulette (Sec. 3.1.3)
                 if (w < C.rr_thr) {
                     if (u3 < C.rr_surv) {
@@ -687,7 +719,7 @@ __device__ __forceinline__ void walk_loop(const CommonArgs &C, const MediumArgs 
             // direction is computed for every photon (a photon truncated by
             // max_scatter ends here and never uses it)
             const bool cap = C.max_scatter && ncoll >= C.max_scatter;
-            rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
+            scatter<PHASE>(M, C, S, u1, u2, dx, dy, dz);
             if (cap | (w < C.rr_thr) | (ev >= C.max_events) | !(w == w)) {
                 if (cap) {
                     sadd64(&s_tot[MC_TOT_TRUNC], fix32(w));
@@ -1015,7 +1047,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
                 status = 5;
                 alive = false;
             } else {
-                rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
+                scatter<PHASE>(M, C, S, u1, u2, dx, dy, dz);
                 idx = mc_div(1.0f, dx); idy = mc_div(1.0f, dy); idz = mc_div(1.0f, dz);
                 if (w < C.rr_thr) {
                     if (u3 < C.rr_surv) {
@@ -1035,7 +1067,7 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
         } else {
             // one branch for the rare cases, as in walk_loop
             const bool cap = C.max_scatter && ncoll >= C.max_scatter;
-            rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
+            scatter<PHASE>(M, C, S, u1, u2, dx, dy, dz);
             idx = mc_div(1.0f, dx); idy = mc_div(1.0f, dy); idz = mc_div(1.0f, dz);
             if (cap | (w < C.rr_thr) | !(w == w)) {
                 if (cap) {
@@ -1424,7 +1456,7 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                     if (C.max_scatter && ncoll >= C.max_scatter) {
                         end = true;
                     } else {
-                        rotate(dx, dy, dz, sample_omu<PHASE>(M, C, S, u1), u2);
+                        scatter<PHASE>(M, C, S, u1, u2, dx, dy, dz);
                         idx = mc_div(1.0f, dx); idy = mc_div(1.0f, dy); idz = mc_div(1.0f, dz);
                         if (w < C.rr_thr) {
                             if (u3 < C.rr_surv) w = w * C.inv_rr_surv;
@@ -1738,7 +1770,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK) adjoint_kernel(const __grid_constan
                         if (coef != 0.0f) hat_add(rows, B, s_w, k, f, coef);
                     }
                 }
-                rotate(dx, dy, dz, om, u2);
+                if (PHASE == MC_PHASE_HG) rotate_hg(dx, dy, dz, om, hg_opu(M, u1), u2);
+                else rotate(dx, dy, dz, om, u2);
                 if (w < C.rr_thr) {
                     if (u3 < C.rr_surv) w = w * C.inv_rr_surv;
                     else end = true;

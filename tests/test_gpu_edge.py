@@ -242,3 +242,22 @@ def test_pure_absorber_matches_oracle(gpu, oracle_mod, ps_table, ps_oracle_table
     assert abs(r["steps"] - o["steps"]) <= 2
     p = math.exp(-tau)
     assert abs(raw[1] / 2 ** 32 / n - p) < 5 * math.sqrt(p * (1 - p) / n)
+
+
+@pytest.mark.parametrize("g", [-0.9, 0.0, 0.99])
+def test_hg_extreme_anisotropy_traces_match_oracle(gpu, oracle_mod, g):
+    """Eq. 11 sampled and scored at strong back-scattering, isotropy and
+    strong forward scattering (where 1 - g = 0.01 sets the scale of both the
+    sampled 1 - cos(theta) and the camera density's peak)."""
+    n, tau = 4096, 5.0
+    e = _eng(gpu)
+    tr = gpu.decode_trace(e.trace(gpu.Medium(tau / LX, 0.0, "hg", g), n, n, 32, seed=6))
+    e.check()
+    o = oracle_mod.walk(mu_s=tau / LX, phase="hg", hg_g=g, n_photons=n, nx=64, nz=64, seed=6, n_trace=n,
+                        n_trace_events=32)
+    slope = lambda mu: 3.0 * abs(g) / (1.0 + g * g - 2.0 * g * mu)
+    cmp = compare_traces(tr, o["trace"], tau / LX, nee_slope=slope)
+    print("g", g, "matched %d/%d flips %d events %d worst %s" %
+          (cmp["matched"], n, cmp["flips"], cmp["events"], {k: "%.2e" % v for k, v in cmp["worst"].items()}))
+    assert cmp["matched"] >= 0.999 * n, cmp["causes"][:5]
+    assert cmp["events"] > 1.5 * n

@@ -194,6 +194,11 @@ MUTATIONS = [
      "const float albedo = (float)(c->mu_a / (c->mu_s + c->mu_a));", W32, "FP32 albedo from the absorption"),
     ("walk32.c", "om = 2.0f * (1.0f - g) * (1.0f - g) * (1.0f - u1) * fmaf(g, u1, 1.0f) / (D * D);",
      "om = 2.0f * (1.0f - g) * (1.0f - g) * fmaf(g, u1, 1.0f) / (D * D);", W32, "FP32 H-G inverse without (1 - xi)"),
+    ("walk32.c", "op = 2.0f * (1.0f + g) * (1.0f + g) * u1 * fmaf(g, u1, 1.0f - g) / (D * D);",
+     "op = 2.0f * (1.0f + g) * (1.0f + g) * (1.0f - u1) * fmaf(g, u1, 1.0f - g) / (D * D);", W32,
+     "FP32 H-G 1 + cos(theta)"),
+    ("walk32.c", "op = 2.0f * (1.0f + g) * (1.0f + g) * u1 * fmaf(g, u1, 1.0f - g) / (D * D);",
+     "op = 2.0f - om;", W32, "FP32 H-G 1 + cos(theta) from 2 - om (its accuracy lost near pi)"),
     ("walk32.c", "om = fmaf(f, omu[i + 1] - omu[i], omu[i]);", "om = fmaf(f, omu[i + 1] - omu[i], omu[i + 1]);", W32,
      "FP32 table interpolation from the wrong level"),
     ("walk32.c", "const float e2[3] = {b, fmaf(d[1] * d[1], a, sg), -d[1]};",

@@ -3,8 +3,9 @@ fused multiply-adds): the walk of Sec. 3.1.3 restated in IEEE single
 precision. It is pinned by
   * the double-precision oracle (itself pinned by closed forms): every
     photon's first 32 events agree within single-precision accuracy under
-    the trace rule of tests/parity.py, for the Mie table and H-G, with
-    absorption and roulette, with a finite beam;
+    the trace rule of tests/parity.py, for the Mie table and H-G (the Mie
+    table's g, strong back-scattering g = -0.9 and strong forward
+    scattering g = 0.99), with absorption and roulette, with a finite beam;
   * Beer-Lambert: the share of photons whose first flight leaves through
     the far face is exp(-tau);
   * implicit capture (Eq. 16): after k collisions the weight is the albedo
@@ -36,20 +37,24 @@ def _g(oracle_mod):
 
 
 CASES = [("mie", 5.0, 0.0, {}), ("mie", 20.0, 0.08, dict(rr_threshold=0.02)), ("hg", 5.0, 0.0, {}),
-         ("hg", 1.0, 0.005, dict(beam_radius=1.25)), ("mie", 2.0, 0.0, dict(beam_radius=1.25))]
+         ("hg", 1.0, 0.005, dict(beam_radius=1.25)), ("mie", 2.0, 0.0, dict(beam_radius=1.25)),
+         ("hg", 5.0, 0.0, dict(hg_g=-0.9)), ("hg", 5.0, 0.0, dict(hg_g=0.99))]
 
 
 @pytest.mark.parametrize("phase,tau,mu_a,kw", CASES)
 def test_single_precision_walk_follows_the_double_precision_walk(oracle_mod, ps_oracle_table, phase, tau,
                                                                   mu_a, kw):
     n = 1024
-    om = dict(phase="mie", table=ps_oracle_table) if phase == "mie" else dict(phase="hg", hg_g=_g(oracle_mod))
+    kw = dict(kw)
+    g = kw.pop("hg_g", None)
+    if phase == "hg" and g is None:
+        g = _g(oracle_mod)
+    om = dict(phase="mie", table=ps_oracle_table) if phase == "mie" else dict(phase="hg", hg_g=g)
     args = dict(mu_s=tau / LX - mu_a, mu_a=mu_a, nx=64, nz=64, seed=11, **om, **kw)
     t64 = oracle_mod.walk(n_photons=n, n_trace=n, n_trace_events=32, **args)["trace"]
     t32 = oracle_mod.walk32_trace(n_trace=n, n_trace_events=32, **args)
     slope = None
     if phase == "hg":
-        g = _g(oracle_mod)
         slope = lambda mu: 3.0 * abs(g) / (1.0 + g * g - 2.0 * g * mu)
     cmp = compare_traces(_as_engine(t32), t64, mu_ext=tau / LX, nee_slope=slope)
     print(phase, tau, mu_a, kw, "matched %d/%d flips %d events %d worst %s" %
