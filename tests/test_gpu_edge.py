@@ -1,6 +1,7 @@
 """Edge cases and invariances of the CUDA path: empty and ragged ranges,
 64-bit photon indices, launch-shape independence, truncation flags, finite
-beams, error reporting, the host-buffer entry point, and a pure absorber."""
+beams, error reporting, the host-buffer entry point, a pure absorber, H-G at
+extreme anisotropy, extreme optical depths and a thin-plate geometry."""
 import ctypes as C
 import math
 
@@ -261,3 +262,24 @@ def test_hg_extreme_anisotropy_traces_match_oracle(gpu, oracle_mod, g):
           (cmp["matched"], n, cmp["flips"], cmp["events"], {k: "%.2e" % v for k, v in cmp["worst"].items()}))
     assert cmp["matched"] >= 0.999 * n, cmp["causes"][:5]
     assert cmp["events"] > 1.5 * n
+
+
+@pytest.mark.parametrize("tau,geom,beam", [(0.01, (45.0, 10.0, 10.0), 0.0), (100.0, (45.0, 10.0, 10.0), 0.0),
+                                           (5.0, (2.0, 50.0, 0.5), 0.2)])
+def test_extreme_depth_and_geometry_traces_match_oracle(gpu, oracle_mod, ps_table, ps_oracle_table, tau, geom, beam):
+    """A nearly transparent cuvette (tau = 0.01: almost every photon ballistic),
+    a very thick one (tau = 100: steps of 0.45 mm, positions summed over many
+    of them) and a thin plate 2 x 50 x 0.5 mm crossed by a 0.2 mm beam (most
+    photons leave through the nearby z faces)."""
+    n = 4096
+    lx, ly, lz = geom
+    e = gpu.Engine(gpu.Camera(64, 64, 128, R_MAX), gpu.Geometry(lx, ly, lz, beam))
+    tr = gpu.decode_trace(e.trace(gpu.Medium(tau / lx, 0.0, "table", 0.0, ps_table), n, n, 32, seed=12))
+    e.check()
+    o = oracle_mod.walk(mu_s=tau / lx, table=ps_oracle_table, lx=lx, ly=ly, lz=lz, beam_radius=beam, n_photons=n,
+                        nx=64, nz=64, seed=12, n_trace=n, n_trace_events=32)
+    cmp = compare_traces(tr, o["trace"], tau / lx, lx=lx)
+    print("tau", tau, geom, "matched %d/%d flips %d events %d worst %s" %
+          (cmp["matched"], n, cmp["flips"], cmp["events"], {k: "%.2e" % v for k, v in cmp["worst"].items()}))
+    assert cmp["matched"] >= 0.999 * n, cmp["causes"][:5]
+    assert cmp["events"] >= n
