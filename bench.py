@@ -59,6 +59,9 @@ def _workload_config():
     }
 
 
+LOAD_WINDOW_S = 0.6   # untimed steps under the clock sampler before the timed ones
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -83,6 +86,12 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_first(self, timeout_s):
+        """Wait (at most timeout_s) until nvidia-smi has printed a reading."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -624,8 +633,18 @@ def run_engine(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
+    # the clocks are read under this load: the sampler's first reading comes
+    # a moment after it starts, so the readings taken while the GPU idled are
+    # dropped, the same steps run untimed for LOAD_WINDOW_S, and sampling
+    # goes on through the timed steps
     clocks.start()
-    time.sleep(0.3)
+    clocks.wait_first(2.0)
+    clocks.lines.clear()
+    t_load = time.perf_counter()
+    while time.perf_counter() - t_load < LOAD_WINDOW_S:
+        step()
+        torch.cuda.synchronize(dev)
+    barrier()
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         starts[i].record(stream)
@@ -633,6 +652,9 @@ def run_engine(args):
         ends[i].record(stream)
     barrier()
     clk = clocks.stop()
+    if clk is not None:
+        clk["window"] = ("%.1f s of the same steps, untimed, then the %d timed steps" %
+                         (LOAD_WINDOW_S, args.steps))
     eng.check()
     assert eng.result()["steps"] == steps_per_run
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
