@@ -43,6 +43,9 @@ SEED = 1
 # DRAM bytes per launch from the same capture (None when stale).
 THREAD_INST_PER_STEP = 239.8          # ncu, 1e7-photon launch of this workload
 BATCH_THREAD_INST_PER_STEP = 245.4    # ncu, one batch_kernel launch over the 64 media (1024 threads, chunks of 128)
+ADJ_W_THREAD_INST_PER_STEP = 344.8    # ncu, adjoint_kernel with 64 phase weights, per forward photon-step (tau 5, 1e7)
+ADJ_MU_THREAD_INST_PER_STEP = 250.7   # ncu, adjoint_kernel for mu_s, mu_a only, per forward photon-step
+GRID_THREAD_INST_PER_TENTATIVE = 361.0  # ncu, grid_kernel on the plume (cells 32x256x256), per tentative collision
 DRAM_BYTES_PER_LAUNCH = 597248        # ncu, a 1e8-photon launch of this workload (table + tallies, L2-resident)
 LANES_PER_SM = 128
 SMEM_WAVEFRONTS_PER_STEP = 0.650       # same capture: shared-memory wavefronts (128 B each) per photon-step
@@ -547,6 +550,8 @@ def adjoint_comparison(E, dev, steps, flush):
         return tot / steps
 
     t_fwd = timed(lambda: eng.run(med, n, seed=1, stream=stream))
+    eng.check()
+    fwd_steps = eng.result()["steps"]
     t_w = timed(lambda: eng.adjoint(med, adj, n, n_w=64, seed=1, stream=stream))
     t_0 = timed(lambda: eng.adjoint(med, adj, n, n_w=0, seed=1, stream=stream))
     # at phase weights w != 1: the forward pass reweights the table on the
@@ -556,7 +561,7 @@ def adjoint_comparison(E, dev, steps, flush):
                                              E.WeightedTable(table, w, dev, stream)), n, seed=1, stream=stream))
     t_adj_w = timed(lambda: eng.adjoint(med, adj, n, n_w=64, seed=1, stream=stream, phase_w=w))
     eng.check()
-    return {"forward_ms": t_fwd, "adjoint_ms": t_w, "adjoint_mu_only_ms": t_0,
+    return {"forward_ms": t_fwd, "forward_steps": fwd_steps, "adjoint_ms": t_w, "adjoint_mu_only_ms": t_0,
             "cost_vs_forward": t_w / t_fwd, "cost_vs_forward_mu_only": t_0 / t_fwd,
             "at_weights": {"forward_ms": t_fwd_w, "adjoint_ms": t_adj_w, "cost_vs_forward": t_adj_w / t_fwd_w},
             "workload": "tau=5 Mie, 1e7 photons, 128x128 image; gradient w.r.t. mu_s, mu_a and 64 "
@@ -726,6 +731,23 @@ def run_engine(args):
         line["adjoint"] = adjoint_comparison(E, dev, args.steps, flush)
         line["paper_mode"] = paper_comparison(E, dev, args.steps, flush)
         line["plume"] = plume_leg(E, dev, args.steps, flush)
+
+        def alu_roof(per_unit, units_per_s, what):
+            ach = per_unit * units_per_s / 1e12
+            return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tinst/s", "frac": ach / peak,
+                    "per_unit": "%g thread-instructions per %s (ncu), peak = %d SMs x %d lanes x %.0f MHz"
+                                % (per_unit, what, sms, LANES_PER_SM, sm_max)}
+        # the adjoint kernels and the plume's delta-tracking walk on the same
+        # issue roofline, from their own instruction counts
+        a = line["adjoint"]
+        a["roofline"] = alu_roof(ADJ_W_THREAD_INST_PER_STEP, a["forward_steps"] / (a["adjoint_ms"] * 1e-3),
+                                 "forward photon-step (adjoint_kernel with 64 phase weights)")
+        a["roofline_mu_only"] = alu_roof(ADJ_MU_THREAD_INST_PER_STEP,
+                                         a["forward_steps"] / (a["adjoint_mu_only_ms"] * 1e-3),
+                                         "forward photon-step (adjoint_kernel, mu_s and mu_a only)")
+        pl = line["plume"]
+        pl["roofline"] = alu_roof(GRID_THREAD_INST_PER_TENTATIVE, pl["tentative_steps_per_s"],
+                                  "tentative collision (grid_kernel)")
     if not args.no_peaks:
         from paper_2507_23189_gb300 import peaks
         pk = peaks.measure(dev)
