@@ -83,6 +83,14 @@ def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL, nee_slope=None):
                 events=checked_events)
 
 
+def report_unmatched(cmp, label=""):
+    """Print every photon that compare_traces did not match, with its cause
+    (photon, event, what differed and the oracle's margin), so a tolerated
+    mismatch is always on record in the test output."""
+    for p, e, why in cmp["causes"]:
+        print("unmatched%s: photon %d event %d: %s" % ((" " + label) if label else "", p, e, why))
+
+
 def chi2_sf(x, k):
     """Survival function of the chi-square distribution (Wilson-Hilferty
     approximation for large k, exact series otherwise via scipy if present)."""

@@ -8,7 +8,7 @@ import math
 import numpy as np
 import pytest
 
-from parity import compare_traces
+from parity import compare_traces, report_unmatched
 
 pytestmark = pytest.mark.gpu
 
@@ -142,6 +142,7 @@ def test_finite_beam_matches_oracle(gpu, oracle_mod, ps_table, ps_oracle_table):
     o = oracle_mod.walk(mu_s=5 / LX, table=ps_oracle_table, n_photons=n, nx=64, nz=64, seed=8,
                         beam_radius=1.25, n_trace=n, n_trace_events=32)
     cmp = compare_traces(tr, o["trace"], 5 / LX)
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n, cmp
 
 
@@ -208,6 +209,7 @@ def test_multi_wall_exits_in_a_cube_match_oracle(gpu, oracle_mod):
     o = oracle_mod.walk(mu_s=0.2, phase="hg", hg_g=0.0, lx=10.0, ly=10.0, lz=10.0, n_photons=n, nx=32, nz=32,
                         seed=12, n_trace=n, n_trace_events=32)
     cmp = compare_traces(tr, o["trace"], 0.2, lx=10.0)
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n, cmp
     n = 1_000_000
     e = gpu.Engine(gpu.Camera(32, 32, 128, R_MAX), geom)
@@ -260,6 +262,7 @@ def test_hg_extreme_anisotropy_traces_match_oracle(gpu, oracle_mod, g):
     cmp = compare_traces(tr, o["trace"], tau / LX, nee_slope=slope)
     print("g", g, "matched %d/%d flips %d events %d worst %s" %
           (cmp["matched"], n, cmp["flips"], cmp["events"], {k: "%.2e" % v for k, v in cmp["worst"].items()}))
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n, cmp["causes"][:5]
     assert cmp["events"] > 1.5 * n
 
@@ -281,5 +284,6 @@ def test_extreme_depth_and_geometry_traces_match_oracle(gpu, oracle_mod, ps_tabl
     cmp = compare_traces(tr, o["trace"], tau / lx, lx=lx)
     print("tau", tau, geom, "matched %d/%d flips %d events %d worst %s" %
           (cmp["matched"], n, cmp["flips"], cmp["events"], {k: "%.2e" % v for k, v in cmp["worst"].items()}))
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n, cmp["causes"][:5]
     assert cmp["events"] >= n

@@ -21,7 +21,7 @@ import math
 import numpy as np
 import pytest
 
-from parity import compare_traces, oracle_var, tally_agreement
+from parity import compare_traces, oracle_var, tally_agreement, report_unmatched
 
 pytestmark = pytest.mark.gpu
 
@@ -114,6 +114,7 @@ def test_batched_smallest_and_largest_particle_traces(gpu, oracle_mod, batched_r
         cmp = compare_traces(tr, o["trace"], mu_ext=c.tau / LX)
         print("medium %d d=%.3f um tau=%.2f: %d/%d matched, flips %d, worst %s, events %d" %
               (i, c.diameter_um, c.tau, cmp["matched"], n, cmp["flips"], cmp["worst"], cmp["events"]))
+        report_unmatched(cmp)
         assert cmp["matched"] >= 0.999 * n, cmp["bad"]
         assert cmp["events"] > 1.2 * n
 

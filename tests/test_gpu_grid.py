@@ -8,7 +8,7 @@ import math
 import numpy as np
 import pytest
 
-from parity import compare_traces, gpu_batches, oracle_var, tally_agreement
+from parity import compare_traces, gpu_batches, oracle_var, tally_agreement, report_unmatched
 
 pytestmark = pytest.mark.gpu
 
@@ -74,6 +74,7 @@ def test_trace_parity_grid(gpu, oracle_mod, ps_table, ps_oracle_table, phase, bl
     cmp = compare_traces(tr, o["trace"], mu_ext=mu_max)
     print(phase, block, cmp["matched"], "/", n, "flips", cmp["flips"], "worst", cmp["worst"], "events",
           cmp["events"])
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n, cmp["bad"]
     assert cmp["events"] > 2 * n
 

@@ -6,7 +6,7 @@ import math
 import numpy as np
 import pytest
 
-from parity import compare_traces
+from parity import compare_traces, report_unmatched
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +46,7 @@ def test_one_voxel_grid_traces_match_homogeneous_oracle(gpu, oracle_mod, ps_tabl
                         nx=64, nz=64, seed=17, n_trace=n, n_trace_events=32, rr_threshold=0.02)
     cmp = compare_traces(tr, o["trace"], mu_ext=k_ext * rho32)
     print(cmp["matched"], "/", n, "flips", cmp["flips"], "worst", cmp["worst"])
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n
     assert np.any(o["trace"][..., 0] == 4)        # roulette fired
 
@@ -71,6 +72,7 @@ def test_disc_beam_with_paper_table_in_a_grid(gpu, oracle_mod):
     slope = lambda mu: abs(mu) / max(1.0 - mu * mu, 1e-300)
     cmp = compare_traces(tr, o["trace"], mu_ext=k_ext * float(dens.max()), nee_slope=slope)
     print(cmp["matched"], "/", n, "flips", cmp["flips"], "worst", cmp["worst"])
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n
     assert cmp["events"] > 2 * n
 

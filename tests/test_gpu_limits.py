@@ -23,7 +23,7 @@ oracle on the same photons:
 import numpy as np
 import pytest
 
-from parity import compare_traces
+from parity import compare_traces, report_unmatched
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +46,7 @@ def test_table_size_extremes_follow_the_oracle(gpu, oracle_mod, n_bins):
     cmp = compare_traces(tr, o["trace"], TAU / LX)
     print(n_bins, "matched %d/%d flips %d events %d worst %s" %
           (cmp["matched"], n, cmp["flips"], cmp["events"], {k: "%.2e" % v for k, v in cmp["worst"].items()}))
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n, cmp["causes"][:5]
     assert cmp["events"] > 1.5 * n
 
@@ -70,6 +71,7 @@ def test_camera_and_profile_extremes_match_oracle(gpu, oracle_mod, ps_table, ps_
                          n_trace_events=32, **cam)
     cmp = compare_traces(tr, ot["trace"], TAU / LX)
     print(nx, nz, n_radial, "traces matched %d/%d flips %d" % (cmp["matched"], nt, cmp["flips"]))
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * nt, cmp["causes"][:5]
 
     n = 200_000
@@ -148,6 +150,7 @@ def test_largest_table_with_most_majorant_cells(gpu, oracle_mod):
     cmp = compare_traces(tr, o["trace"], mu_ext=k_ext * float(dens.max()))
     print("grid, 16384 bins, 16384 cells: matched %d/%d flips %d events %d" %
           (cmp["matched"], n, cmp["flips"], cmp["events"]))
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n, cmp["causes"][:5]
     assert cmp["events"] > 2 * n
 
@@ -213,6 +216,7 @@ def test_paper_table_size_extremes_follow_the_oracle(gpu, oracle_mod, n_theta):
                         n_trace_events=32)
     cmp = compare_traces(tr, o["trace"], TAU / LX, nee_slope=_paper_slope)
     print("paper", n_theta, "matched %d/%d flips %d events %d" % (cmp["matched"], n, cmp["flips"], cmp["events"]))
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n, cmp["causes"][:5]
     assert cmp["events"] > 1.5 * n
 

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import metrics as OM
-from parity import compare_traces, gpu_batches, oracle_var, tally_agreement
+from parity import compare_traces, gpu_batches, oracle_var, tally_agreement, report_unmatched
 
 pytestmark = pytest.mark.gpu
 
@@ -57,6 +57,7 @@ def test_trace_parity_paper_mode(gpu, oracle_mod, paper_tables, tau, mu_a, kw):
     cmp = compare_traces(tr, o["trace"], mu_ext=tau / LX, lx=LX, nee_slope=_slope)
     print(tau, mu_a, cmp["matched"], "/", n, "flips", cmp["flips"], "worst", cmp["worst"], "events",
           cmp["events"])
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n, cmp["bad"]
     assert cmp["events"] > 1.5 * n
     if kw.get("rr_survival", 0.1) == 0.0 and mu_a > 0:

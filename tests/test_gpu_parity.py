@@ -10,7 +10,7 @@ import math
 import numpy as np
 import pytest
 
-from parity import compare_traces, gpu_batches, oracle_var, tally_agreement
+from parity import compare_traces, gpu_batches, oracle_var, tally_agreement, report_unmatched
 
 pytestmark = pytest.mark.gpu
 
@@ -58,6 +58,7 @@ def test_trace_parity_first_32_events(gpu, oracle_mod, ps_table, ps_oracle_table
     cmp = compare_traces(tr, ores["trace"], mu_ext=tau / LX)
     print(phase, tau, mu_a, cmp["matched"], "/", cmp["n"], "flips", cmp["flips"], "worst", cmp["worst"],
           "events", cmp["events"])
+    report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n, cmp["bad"]
     assert cmp["events"] > 1.5 * n
     if kw:

@@ -7,7 +7,7 @@ ones."""
 import numpy as np
 import pytest
 
-from parity import TOL, compare_traces, oracle_var, tally_agreement
+from parity import TOL, compare_traces, oracle_var, report_unmatched, tally_agreement
 
 LX = 45.0
 
@@ -104,3 +104,15 @@ def test_oracle_var_is_n_times_the_sample_variance():
     x = rng.exponential(1.0, (n, 3, 4)) * (rng.uniform(size=(n, 3, 4)) < 0.3)   # per-photon contributions
     res = dict(n_photons=n, image=x.sum(axis=0), image_sq=(x * x).sum(axis=0))
     np.testing.assert_allclose(oracle_var(res), n * x.var(axis=0, ddof=1), rtol=1e-10)
+
+
+def test_every_unmatched_photon_is_reported_with_its_cause(traced, capsys):
+    o, mu_ext = traced
+    p = _collision(o)
+    g = _as_engine(o)
+    g["d"][p][1, 1] += 3.0 * TOL
+    c = compare_traces(g, o, mu_ext)
+    report_unmatched(c, "case")
+    out = capsys.readouterr().out.strip().splitlines()
+    assert c["matched"] == c["n"] - 1 and len(out) == 1
+    assert out[0].startswith("unmatched case: photon %d event 1: position" % p) and "direction" in out[0]
