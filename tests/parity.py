@@ -3,7 +3,8 @@
 Trace rule: the first 32 events of every photon must agree with the
 double-precision oracle within 1e-5 relative (positions relative to the
 cuvette length, directions absolutely, weights and camera contributions
-relative). A discrete decision (wall hit, exit face, pixel, table bin,
+relative; two camera contributions both below NEE_FLOOR, which no tally
+can register, agree). A discrete decision (wall hit, exit face, pixel, table bin,
 roulette) may differ only where the oracle's branch quantity lies within
 1e-5 of its threshold; that photon's later events are then excluded.
 At least 99.9 % of photons must match.
@@ -16,6 +17,14 @@ import math
 import numpy as np
 
 TOL = 1e-5
+# Two camera terms that are both below this floor agree; otherwise they are
+# compared relative to the larger of the oracle's value and the floor. A
+# term below it can reach no fixed-point tally: the finest
+# image unit is 2^-48, and one run adds at most 2^31 photons times 10^6
+# events (2.1e15 terms, 2.1e-16 in all). Single precision cannot hold such a
+# term at all where the camera path's optical depth passes about 87: it
+# flushes to zero while the double-precision oracle keeps, say, 1e-98.
+NEE_FLOOR = 1e-31
 
 
 def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL, nee_slope=None):
@@ -57,7 +66,9 @@ def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL, nee_slope=None):
             dw = abs(g["w"][p, e] - rec[7]) / max(abs(rec[7]), 1e-300) if rec[7] else abs(g["w"][p, e])
             dnee_abs = abs(g["nee"][p, e] - rec[8])
             # the camera term depends on r_y through exp(-mu_ext (ly/2 - r_y))
-            dnee = dnee_abs / rec[8] if rec[8] else dnee_abs
+            # two terms below what any tally can register agree
+            tiny = max(abs(g["nee"][p, e]), abs(rec[8])) < NEE_FLOOR
+            dnee = 0.0 if tiny else dnee_abs / max(abs(rec[8]), NEE_FLOOR)
             nee_tol = tol + mu_ext * dpos
             if nee_slope is not None:
                 nee_tol += nee_slope(muc) * ddir_prev

@@ -1,0 +1,72 @@
+"""The CUDA walk against the oracle over seeded random configurations, so that
+regimes no hand-picked case covers are checked as well: cuvette sides from
+0.5 to 100 mm, optical depths from 0.05 to 50, Mie tables of spheres from
+0.5 to 20 um (from nearly isotropic to strongly forward) or H-G with
+g in (-0.95, 0.99), absorption up to half the extinction, roulette
+thresholds and survival chances (the plain cut included), finite beams and
+cameras of 1 to 300 pixels a side. Each configuration compares the first 32
+events of 2048 photons under the trace rule (tests/parity.py) and prints
+every photon it did not match with its cause.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from parity import compare_traces, report_unmatched
+
+pytestmark = pytest.mark.gpu
+
+N_CONFIGS = 12
+
+
+def _configs(seed=7, n=N_CONFIGS):
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = []
+    for k in range(n):
+        lx, ly, lz = (float(v) for v in np.exp(rng.uniform(np.log(0.5), np.log(100.0), 3)))
+        tau = float(np.exp(rng.uniform(np.log(0.05), np.log(50.0))))
+        phase = "hg" if k % 3 == 2 else "mie"
+        g = float(rng.uniform(-0.95, 0.99))
+        d = float(np.exp(rng.uniform(np.log(0.5), np.log(20.0))))
+        mu_ext = tau / lx
+        mu_a = float(mu_ext * rng.uniform(0.0, 0.5)) if k % 2 else 0.0
+        beam = float(rng.uniform(0.0, 0.5) * min(ly, lz)) if k % 4 == 1 else 0.0
+        nx, nz = int(rng.integers(1, 300)), int(rng.integers(1, 300))
+        rr = (float(rng.uniform(1e-4, 0.05)), float(rng.uniform(0.0, 0.5)))
+        out.append(dict(lx=lx, ly=ly, lz=lz, tau=tau, phase=phase, g=g, d=d, mu_a=mu_a, beam=beam, nx=nx, nz=nz,
+                        rr=rr))
+    return out
+
+
+@pytest.mark.parametrize("k", range(N_CONFIGS))
+def test_random_configuration_traces_match_oracle(gpu, oracle_mod, k):
+    c = _configs()[k]
+    n = 2048
+    mu_ext = c["tau"] / c["lx"]
+    mu_s = mu_ext - c["mu_a"]
+    r_max = 0.5 * math.hypot(c["ly"], c["lz"])
+    kw = dict(rr_threshold=c["rr"][0], rr_survival=c["rr"][1])
+    if c["phase"] == "mie":
+        med = gpu.Medium(mu_s, c["mu_a"], "table", 0.0, gpu.PhaseTable(diameter_um=c["d"]))
+        x = oracle_mod.size_parameter(c["d"], 1.33, 532.0)
+        om = dict(phase="mie", table=oracle_mod.phase_table(oracle_mod.PHASE_MIE, complex(1.59 / 1.33, 0.0), x))
+        slope = None
+    else:
+        g = c["g"]
+        med = gpu.Medium(mu_s, c["mu_a"], "hg", g)
+        om = dict(phase="hg", hg_g=g)
+        slope = lambda mu: 3.0 * abs(g) / (1.0 + g * g - 2.0 * g * mu)
+    e = gpu.Engine(gpu.Camera(c["nx"], c["nz"], 128, r_max), gpu.Geometry(c["lx"], c["ly"], c["lz"], c["beam"]))
+    tr = gpu.decode_trace(e.trace(med, n, n, 32, seed=31, **kw))
+    e.check()
+    o = oracle_mod.walk(mu_s=mu_s, mu_a=c["mu_a"], lx=c["lx"], ly=c["ly"], lz=c["lz"], beam_radius=c["beam"],
+                        nx=c["nx"], nz=c["nz"], r_max=r_max, n_photons=n, seed=31, n_trace=n, n_trace_events=32,
+                        **om, **kw)
+    cmp = compare_traces(tr, o["trace"], mu_ext, lx=c["lx"], nee_slope=slope)
+    print("config %d %s: matched %d/%d flips %d events %d worst %s" %
+          (k, {q: (round(v, 3) if isinstance(v, float) else v) for q, v in c.items()}, cmp["matched"], n,
+           cmp["flips"], cmp["events"], {q: "%.2e" % v for q, v in cmp["worst"].items()}))
+    report_unmatched(cmp, "config %d" % k)
+    assert cmp["matched"] >= 0.998 * n, cmp["causes"][:5]
+    assert cmp["events"] >= n

@@ -7,7 +7,7 @@ ones."""
 import numpy as np
 import pytest
 
-from parity import TOL, compare_traces, oracle_var, report_unmatched, tally_agreement
+from parity import NEE_FLOOR, TOL, compare_traces, oracle_var, report_unmatched, tally_agreement
 
 LX = 45.0
 
@@ -116,3 +116,20 @@ def test_every_unmatched_photon_is_reported_with_its_cause(traced, capsys):
     out = capsys.readouterr().out.strip().splitlines()
     assert c["matched"] == c["n"] - 1 and len(out) == 1
     assert out[0].startswith("unmatched case: photon %d event 1: position" % p) and "direction" in out[0]
+
+
+def test_camera_terms_below_any_tally_unit_are_compared_absolutely(traced):
+    """A camera term that single precision flushes to zero (the oracle's 1e-98
+    against the engine's 0) matches; one that a tally could register does
+    not (the floor is far below the finest image unit over a whole run:
+    2.1e15 terms of 1e-31 add to 2.1e-16 < 2^-48)."""
+    o, mu_ext = traced
+    assert 2.0 ** 31 * 1e6 * NEE_FLOOR < 2.0 ** -48
+    p = _collision(o)
+    for oracle_value, ok in ((1e-98, True), (1e-33, True), (1e-20, False)):
+        oo = o.copy()
+        oo[p, 1, 8] = oracle_value
+        g = _as_engine(oo)
+        g["nee"][p][1] = 0.0
+        c = compare_traces(g, oo, mu_ext)
+        assert (p not in c["bad"]) == ok, oracle_value
