@@ -27,12 +27,17 @@ TOL = 1e-5
 NEE_FLOOR = 1e-31
 
 
-def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL, nee_slope=None):
+def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL, nee_slope=None, hy=None):
     """g: decode_trace() dict of the GPU trace; o: oracle trace array
     [n, ev, 13]. nee_slope(mu_c): |d log p_sr / d mu_c| of a camera density
     that varies continuously with the direction (the paper's table); the
     camera term then also carries the direction difference of the previous
-    event times that slope. Returns dict(n, matched, flips, bad, worst...)."""
+    event times that slope. hy (half the cuvette's height along the camera
+    axis): the camera term's transmittance exp(-D) in single precision
+    carries a relative error of about D 2^-23 (D, its argument and the fused
+    multiply-add forming it are each rounded), so with hy given the term is
+    also allowed 2^-22 D, D bounded by mu_ext (hy - r_y) with mu_ext the
+    largest extinction. Returns dict(n, matched, flips, bad, worst...)."""
     n, ev = o.shape[0], o.shape[1]
     st_o = o[..., 0].astype(int)
     # nee_net: the camera term's deviation beyond what the position (and,
@@ -72,6 +77,8 @@ def compare_traces(g, o, mu_ext, lx=45.0, tol=TOL, nee_slope=None):
             nee_tol = tol + mu_ext * dpos
             if nee_slope is not None:
                 nee_tol += nee_slope(muc) * ddir_prev
+            if hy is not None:
+                nee_tol += 2.0 ** -22 * mu_ext * max(hy - rec[2], 0.0)
             worst["pos"] = max(worst["pos"], dpos / lx)
             worst["dir"] = max(worst["dir"], ddir)
             worst["w"] = max(worst["w"], dw)

@@ -63,10 +63,79 @@ def test_random_configuration_traces_match_oracle(gpu, oracle_mod, k):
     o = oracle_mod.walk(mu_s=mu_s, mu_a=c["mu_a"], lx=c["lx"], ly=c["ly"], lz=c["lz"], beam_radius=c["beam"],
                         nx=c["nx"], nz=c["nz"], r_max=r_max, n_photons=n, seed=31, n_trace=n, n_trace_events=32,
                         **om, **kw)
-    cmp = compare_traces(tr, o["trace"], mu_ext, lx=c["lx"], nee_slope=slope)
+    cmp = compare_traces(tr, o["trace"], mu_ext, lx=c["lx"], nee_slope=slope, hy=0.5 * c["ly"])
     print("config %d %s: matched %d/%d flips %d events %d worst %s" %
           (k, {q: (round(v, 3) if isinstance(v, float) else v) for q, v in c.items()}, cmp["matched"], n,
            cmp["flips"], cmp["events"], {q: "%.2e" % v for q, v in cmp["worst"].items()}))
     report_unmatched(cmp, "config %d" % k)
     assert cmp["matched"] >= 0.998 * n, cmp["causes"][:5]
     assert cmp["events"] >= n
+
+
+N_GRID_CONFIGS = 8
+
+
+def _grid_configs(seed=11, n=N_GRID_CONFIGS):
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = []
+    for k in range(n):
+        lx, ly, lz = (float(v) for v in np.exp(rng.uniform(np.log(1.0), np.log(60.0), 3)))
+        gx, gy, gz = (int(v) for v in rng.integers(4, 41, 3))
+        bx, by, bz = (int(rng.integers(1, v + 1)) for v in (gx, gy, gz))
+        while ((gx + bx - 1) // bx) * ((gy + by - 1) // by) * ((gz + bz - 1) // bz) > 16384:
+            bx += 1
+        tau = float(np.exp(rng.uniform(np.log(0.1), np.log(20.0))))   # mean extinction times lx
+        phase = "hg" if k % 2 else "mie"
+        g = float(rng.uniform(-0.9, 0.95))
+        d = float(np.exp(rng.uniform(np.log(0.5), np.log(15.0))))
+        k_ext = 4e-5
+        albedo = float(rng.uniform(0.6, 1.0))
+        mu_a = float(tau / lx * rng.uniform(0.0, 0.2)) if k % 3 == 0 else 0.0
+        spread = float(rng.uniform(0.0, 1.2))
+        out.append(dict(lx=lx, ly=ly, lz=lz, shape=(gz, gy, gx), block=(bx, by, bz), tau=tau, phase=phase, g=g, d=d,
+                        k_ext=k_ext, k_sca=k_ext * albedo, mu_a=mu_a, spread=spread, seed=100 + k,
+                        rr=(float(rng.uniform(1e-4, 0.05)), float(rng.uniform(0.0, 0.5)))))
+    return out
+
+
+@pytest.mark.parametrize("k", range(N_GRID_CONFIGS))
+def test_random_grid_configuration_traces_match_oracle(gpu, oracle_mod, k):
+    """Delta tracking over seeded random grids: 4 to 40 voxels a side, majorant
+    cells from one voxel to the whole grid, log-normal densities of random
+    spread scaled to optical depths 0.1 to 20 along lx, particle albedo 0.6 to
+    1 and background absorption, the Mie table or H-G."""
+    import torch
+    from paper_2507_23189_gb300 import workloads as W
+    c = _grid_configs()[k]
+    n = 2048
+    rough = W.rough_grid(c["shape"], c["seed"], mean=1.0, spread=c["spread"])
+    dens = (rough * (c["tau"] / (c["k_ext"] * c["lx"] * float(rough.mean())))).astype(np.float32)
+    geo = gpu.Geometry(c["lx"], c["ly"], c["lz"])
+    grid = gpu.Grid(torch.from_numpy(dens).cuda(), c["k_ext"], c["k_sca"], c["mu_a"], c["block"]).prepare(geo)
+    kw = dict(rr_threshold=c["rr"][0], rr_survival=c["rr"][1])
+    if c["phase"] == "mie":
+        med = gpu.Medium(1.0, 0.0, "table", 0.0, gpu.PhaseTable(diameter_um=c["d"]))
+        x = oracle_mod.size_parameter(c["d"], 1.33, 532.0)
+        om = dict(phase="mie", table=oracle_mod.phase_table(oracle_mod.PHASE_MIE, complex(1.59 / 1.33, 0.0), x))
+        slope = None
+    else:
+        g = c["g"]
+        med = gpu.Medium(1.0, 0.0, "hg", g)
+        om = dict(phase="hg", hg_g=g)
+        slope = lambda mu: 3.0 * abs(g) / (1.0 + g * g - 2.0 * g * mu)
+    r_max = 0.5 * math.hypot(c["ly"], c["lz"])
+    e = gpu.Engine(gpu.Camera(64, 64, 128, r_max), geo)
+    tr = gpu.decode_trace(e.run_grid(grid, med, n, seed=37, n_trace=n, n_events=32, **kw))
+    e.check()
+    o = oracle_mod.walk(mu_s=0.0, mu_a=c["mu_a"], lx=c["lx"], ly=c["ly"], lz=c["lz"], nx=64, nz=64, r_max=r_max,
+                        n_photons=n, seed=37, n_trace=n, n_trace_events=32,
+                        grid=dict(density=dens.astype(np.float64), k_ext=c["k_ext"], k_sca=c["k_sca"],
+                                  block=c["block"]), **om, **kw)
+    cmp = compare_traces(tr, o["trace"], c["k_ext"] * float(dens.max()) + c["mu_a"], lx=c["lx"], nee_slope=slope,
+                         hy=0.5 * c["ly"])
+    print("grid config %d %s: matched %d/%d flips %d events %d worst %s" %
+          (k, {q: (round(v, 3) if isinstance(v, float) else v) for q, v in c.items()}, cmp["matched"], n,
+           cmp["flips"], cmp["events"], {q: "%.2e" % v for q, v in cmp["worst"].items()}))
+    report_unmatched(cmp, "grid config %d" % k)
+    assert cmp["matched"] >= 0.998 * n, cmp["causes"][:5]
+    assert cmp["events"] >= 0.5 * n     # thin media: many photons leave before any real event

@@ -133,3 +133,18 @@ def test_camera_terms_below_any_tally_unit_are_compared_absolutely(traced):
         g["nee"][p][1] = 0.0
         c = compare_traces(g, oo, mu_ext)
         assert (p not in c["bad"]) == ok, oracle_value
+
+
+def test_camera_allowance_for_a_deep_transmittance(traced):
+    """With the half-height given, a camera term may also differ by 2^-22 times
+    the bound mu_ext (hy - r_y) on its transmittance's optical depth: a 3e-5
+    difference passes where that bound is 200, and fails without it."""
+    o, mu_ext = traced
+    p = _collision(o)
+    hy = o[p, 1, 2] + 200.0 / mu_ext
+    g = _as_engine(o)
+    g["nee"][p][1] = o[p, 1, 8] * (1.0 + 3e-5)
+    assert p in compare_traces(g, o, mu_ext)["bad"]
+    assert p not in compare_traces(g, o, mu_ext, hy=hy)["bad"]
+    g["nee"][p][1] = o[p, 1, 8] * (1.0 + 1e-4)
+    assert p in compare_traces(g, o, mu_ext, hy=hy)["bad"]
