@@ -6,7 +6,9 @@ g in (-0.95, 0.99), absorption up to half the extinction, roulette
 thresholds and survival chances (the plain cut included), finite beams and
 cameras of 1 to 300 pixels a side. Each configuration compares the first 32
 events of 2048 photons under the trace rule (tests/parity.py) and prints
-every photon it did not match with its cause.
+every photon it did not match with its cause. Random grids check delta
+tracking the same way, and random media and cameras check the adjoint's
+gradient against the oracle's on the same photons.
 """
 import math
 
@@ -139,3 +141,61 @@ def test_random_grid_configuration_traces_match_oracle(gpu, oracle_mod, k):
     report_unmatched(cmp, "grid config %d" % k)
     assert cmp["matched"] >= 0.998 * n, cmp["causes"][:5]
     assert cmp["events"] >= 0.5 * n     # thin media: many photons leave before any real event
+
+
+N_ADJ_CONFIGS = 6
+
+
+def _adjoint_configs(seed=13, n=N_ADJ_CONFIGS):
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = []
+    for k in range(n):
+        lx, ly, lz = (float(v) for v in np.exp(rng.uniform(np.log(2.0), np.log(60.0), 3)))
+        tau = float(np.exp(rng.uniform(np.log(0.3), np.log(15.0))))
+        phase = "hg" if k % 3 == 2 else "mie"
+        g = float(rng.uniform(-0.8, 0.95))
+        d = float(np.exp(rng.uniform(np.log(0.5), np.log(15.0))))
+        mu_a = float(tau / lx * rng.uniform(0.0, 0.3)) if k % 2 else 0.0
+        nx, nz = int(rng.integers(4, 96)), int(rng.integers(4, 96))
+        out.append(dict(lx=lx, ly=ly, lz=lz, tau=tau, phase=phase, g=g, d=d, mu_a=mu_a, nx=nx, nz=nz,
+                        rr=(float(rng.uniform(1e-4, 0.05)), float(rng.uniform(0.05, 0.5)))))
+    return out
+
+
+@pytest.mark.parametrize("k", range(N_ADJ_CONFIGS))
+def test_random_configuration_adjoint_matches_oracle(gpu, oracle_mod, k):
+    """The adjoint (mc_adjoint: d/d(mu_s, mu_a) and, with the Mie table, 64
+    phase weights) on seeded random cuvettes, media and cameras against the
+    oracle's gradient on the same photons: the value to 1e-4 and every
+    component within 0.05 sigma + 1e-4 relative, as in the adjoint's own
+    parity test."""
+    import torch
+    c = _adjoint_configs()[k]
+    n = 30_000
+    mu_ext = c["tau"] / c["lx"]
+    mu_s = mu_ext - c["mu_a"]
+    r_max = 0.5 * math.hypot(c["ly"], c["lz"])
+    kw = dict(rr_threshold=c["rr"][0], rr_survival=c["rr"][1])
+    adj = np.random.default_rng(100 + k).uniform(0.0, 1.0, (c["nz"], c["nx"])).astype(np.float32)
+    e = gpu.Engine(gpu.Camera(c["nx"], c["nz"], 128, r_max), gpu.Geometry(c["lx"], c["ly"], c["lz"]))
+    if c["phase"] == "mie":
+        n_w = 64
+        med = gpu.Medium(mu_s, c["mu_a"], "table", 0.0, gpu.PhaseTable(diameter_um=c["d"]))
+        x = oracle_mod.size_parameter(c["d"], 1.33, 532.0)
+        om = dict(phase="mie", table=oracle_mod.phase_table(oracle_mod.PHASE_MIE, complex(1.59 / 1.33, 0.0), x))
+    else:
+        n_w = 0
+        med = gpu.Medium(mu_s, c["mu_a"], "hg", c["g"])
+        om = dict(phase="hg", hg_g=c["g"])
+    out = e.adjoint(med, torch.from_numpy(adj), n, n_w=n_w, seed=9, **kw).cpu().numpy()
+    e.check()
+    o = oracle_mod.adjoint(adj.astype(np.float64), n_w, mu_s=mu_s, mu_a=c["mu_a"], lx=c["lx"], ly=c["ly"],
+                           lz=c["lz"], nx=c["nx"], nz=c["nz"], r_max=r_max, n_photons=n, seed=9, **om, **kw)
+    g, g2 = o["grad"], o["grad_sq"]
+    sig = np.sqrt(np.maximum(g2 - g ** 2 / n, 0))
+    d = np.abs(out[1:] - g)
+    print("adjoint config %d %s: value %.6g vs %.6g, max |diff|/sigma %.3g" %
+          (k, {q: (round(v, 3) if isinstance(v, float) else v) for q, v in c.items()}, out[0], o["value"],
+           float(np.max(d / np.maximum(sig, 1e-300)))))
+    assert out[0] == pytest.approx(o["value"], rel=1e-4, abs=1e-9)
+    assert np.all(d <= 0.05 * sig + 1e-4 * np.abs(g) + 1e-9)
