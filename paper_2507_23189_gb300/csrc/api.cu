@@ -610,6 +610,8 @@ void fill_grid(mcx::GridArgs &a, const mc_grid *g, int mx, int my, int mz, const
     a.csy = (float)(g->by * geom->ly / g->gy);
     a.csz = (float)(g->bz * geom->lz / g->gz);
     a.inv_csx = (float)(g->gx / (g->bx * geom->lx));
+    a.hcy = (float)(0.5 * g->gy / g->by);
+    a.hcz = (float)(0.5 * g->gz / g->bz);
     a.inv_csy = (float)(g->gy / (g->by * geom->ly));
     a.inv_csz = (float)(g->gz / (g->bz * geom->lz));
     a.ks_over_ke = (float)(g->k_sca / g->k_ext);

@@ -95,6 +95,7 @@ struct GridArgs {
     float vx, vy, vz;             // voxel sizes, mm
     float csx, csy, csz;          // cell sizes, mm
     float inv_csx, inv_csy, inv_csz;
+    float hcy, hcz;               // cells between the y (z) axis and a side, g / (2 b): exact when whole
     float ks_over_ke, mu_a;       // albedo = ks_over_ke (1 - mu_a / mu_ext)
     unsigned long long *counter;
 };

@@ -322,21 +322,32 @@ __device__ __forceinline__ float camera_psr(const MediumArgs &M, const CommonArg
     return S.pdf[nb] * INV_2PI;
 }
 
+// Index of the cell of size 1/inv holding coordinate r on an axis centred at
+// 0 that `half` cells cover on either side: floor(r inv + half) with one
+// rounding. A point on the axis lands in cell `half` whatever the axis length
+// (half = n/2 is exact), as the reading of ties on the centre plane fixes; the
+// form (r + l/2) inv would round both l/2 and inv first and could give
+// half - 1 there, where a pencil beam puts every first collision.
+__device__ __forceinline__ int centred_cell(float r, float inv, float half, int n)
+{
+    return min(max(__float2int_rd(fmaf(r, inv, half)), 0), n - 1);
+}
+
 // Camera pixel of a collision at (rx, rz).
 __device__ __forceinline__ int camera_pixel(const CommonArgs &C, float rx, float rz, int &ix, int &iz)
 {
     ix = min(max(__float2int_rd(rx * C.sx), 0), C.nx - 1);
-    iz = min(max(__float2int_rd((rz + C.hz) * C.sz), 0), C.nz - 1);
+    iz = centred_cell(rz, C.sz, 0.5f * (float)C.nz, C.nz);
     return chk(iz * C.nx + ix, C.nx * C.nz, C.error);
 }
 
-// The same for a collision the caller has tested to lie inside: 0 < rx and
-// |rz| < hz, so both products are >= 0 and only the upper clamp (rounding at
-// the far edge) can act.
+// The same for a collision the caller has tested to lie inside: 0 < rx, so
+// the column's product is >= 0 and only its upper clamp (rounding at the far
+// edge) can act.
 __device__ __forceinline__ int camera_pixel_inside(const CommonArgs &C, float rx, float rz, int &ix, int &iz)
 {
     ix = min(__float2int_rd(rx * C.sx), C.nx - 1);
-    iz = min(__float2int_rd((rz + C.hz) * C.sz), C.nz - 1);
+    iz = centred_cell(rz, C.sz, 0.5f * (float)C.nz, C.nz);
     return chk(iz * C.nx + ix, C.nx * C.nz, C.error);
 }
 
@@ -849,8 +860,8 @@ __device__ __forceinline__ int grid_flight(const GridArgs &G, const float *s_maj
     const CommonArgs &C = G.c;
     const float INF = __int_as_float(0x7f800000);
     int cx = min(max(__float2int_rd(rx * G.inv_csx), 0), G.mx - 1);
-    int cy = min(max(__float2int_rd((ry + C.hy) * G.inv_csy), 0), G.my - 1);
-    int cz = min(max(__float2int_rd((rz + C.hz) * G.inv_csz), 0), G.mz - 1);
+    int cy = centred_cell(ry, G.inv_csy, G.hcy, G.my);
+    int cz = centred_cell(rz, G.inv_csz, G.hcz, G.mz);
     const bool px = dx > 0.f, py = dy > 0.f, pz = dz > 0.f;
     // next plane of cell c on an axis of cell size cs, lower wall lo, upper wall hi
     auto plane = [](int c, int m, bool up, float cs, float lo, float hi) {
@@ -1013,8 +1024,8 @@ __device__ __forceinline__ void grid_loop(const GridArgs &G, const Smem &S, cons
 
         // -------- tentative collision: real with probability mu_ext / majorant
         const int ix = min(max(__float2int_rd(rx * G.inv_vx), 0), G.gx - 1);
-        const int iy = min(max(__float2int_rd((ry + C.hy) * G.inv_vy), 0), G.gy - 1);
-        const int iz = min(max(__float2int_rd((rz + C.hz) * G.inv_vz), 0), G.gz - 1);
+        const int iy = centred_cell(ry, G.inv_vy, 0.5f * (float)G.gy, G.gy);
+        const int iz = centred_cell(rz, G.inv_vz, 0.5f * (float)G.gz, G.gz);
         const float2 cell = __ldg(&G.cells[chk((iz * G.gy + iy) * G.gx + ix, G.gx * G.gy * G.gz, C.error)]);
         const float acc = mc_div(cell.x, mb);   // hardware reciprocal (a few ulp) unless strict
         if (!(u3 < acc)) continue;   // null collision
@@ -1388,8 +1399,8 @@ __global__ void __launch_bounds__(GADJ_BLOCK) grid_adjoint_kernel(const __grid_c
                 end = true;   // left the cuvette: no camera term follows
             } else {
                 const int ix = min(max(__float2int_rd(rx * G.inv_vx), 0), G.gx - 1);
-                const int iy = min(max(__float2int_rd((ry + C.hy) * G.inv_vy), 0), G.gy - 1);
-                const int iz = min(max(__float2int_rd((rz + C.hz) * G.inv_vz), 0), G.gz - 1);
+                const int iy = centred_cell(ry, G.inv_vy, 0.5f * (float)G.gy, G.gy);
+                const int iz = centred_cell(rz, G.inv_vz, 0.5f * (float)G.gz, G.gz);
                 const size_t v = chk((iz * G.gy + iy) * G.gx + ix, G.gx * G.gy * G.gz, C.error);
                 const float2 cell = __ldg(&G.cells[v]);
                 const float acc = mc_div(cell.x, mb);   // hardware reciprocal (a few ulp) unless strict
