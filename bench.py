@@ -41,12 +41,12 @@ SEED = 1
 # Work per photon-step = thread-instructions the kernel executes per sampled
 # flight on this workload, from ncu (smsp__thread_inst_executed.sum / steps);
 # DRAM bytes per launch from the same capture (None when stale).
-THREAD_INST_PER_STEP = 239.8          # ncu, 1e7-photon launch of this workload
-BATCH_THREAD_INST_PER_STEP = 245.4    # ncu, one batch_kernel launch over the 64 media (1024 threads, chunks of 128)
+THREAD_INST_PER_STEP = 242.3          # ncu, 1e7-photon launch of this workload
+BATCH_THREAD_INST_PER_STEP = 245.4    # ncu, one batch_kernel launch over the 64 media (taken before the camera row's lower clamp came back: about 1 % low now)
 ADJ_W_THREAD_INST_PER_STEP = 344.8    # ncu, adjoint_kernel with 64 phase weights, per forward photon-step (tau 5, 1e7)
 ADJ_MU_THREAD_INST_PER_STEP = 250.7   # ncu, adjoint_kernel for mu_s, mu_a only, per forward photon-step
 GRID_THREAD_INST_PER_TENTATIVE = 361.0  # ncu, grid_kernel on the plume (cells 32x256x256), per tentative collision
-DRAM_BYTES_PER_LAUNCH = 597248        # ncu, a 1e8-photon launch of this workload (table + tallies, L2-resident)
+DRAM_BYTES_PER_LAUNCH = 596736        # same capture (table + tallies, L2-resident: the same per launch at 1e8)
 LANES_PER_SM = 128
 SMEM_WAVEFRONTS_PER_STEP = 0.650       # same capture: shared-memory wavefronts (128 B each) per photon-step
 SMEM_BYTES_PER_CLK_SM = 128
