@@ -287,3 +287,16 @@ def test_extreme_depth_and_geometry_traces_match_oracle(gpu, oracle_mod, ps_tabl
     report_unmatched(cmp)
     assert cmp["matched"] >= 0.999 * n, cmp["causes"][:5]
     assert cmp["events"] >= n
+
+
+@pytest.mark.parametrize("lz,nz", [(5.6997014, 24), (10.0, 64), (4.2667066, 30), (0.964, 2)])
+def test_first_collisions_on_the_axis_fall_in_row_nz_over_2(gpu, lz, nz):
+    """A pencil beam's first collisions lie on z = 0, the edge between rows
+    nz/2 - 1 and nz/2, and belong to row nz/2 whatever the cuvette height
+    (5.6997 mm with 24 rows once sent them to row 11); with max_scatter = 1
+    only first collisions add camera terms."""
+    e = gpu.Engine(gpu.Camera(8, nz, 16, R_MAX), gpu.Geometry(20.0, 8.0, lz))
+    e.run(gpu.Medium(0.1, 0.0, "hg", 0.3), 2000, seed=3, max_scatter=1)
+    e.check()
+    rows = e.result()["raw_image"].sum(axis=1)
+    assert rows[nz // 2] > 0 and rows.sum() == rows[nz // 2]

@@ -338,3 +338,15 @@ def test_walk_rejects_bad_arguments(oracle_mod, mie_table):
         oracle_mod.walk(mu_s=0.1, phase="hg", hg_g=1.5)
     with pytest.raises(ValueError):
         oracle_mod.walk(mu_s=0.1, table=mie_table, nx=0)
+
+
+@pytest.mark.parametrize("lz,nz", [(5.6997014, 24), (10.0, 64), (4.2667066, 30), (0.964, 2)])
+def test_first_collisions_on_the_axis_fall_in_row_nz_over_2(oracle_mod, lz, nz):
+    """The pixel-tie reading: a pencil beam's first collisions lie on z = 0,
+    the edge between rows nz/2 - 1 and nz/2, and belong to row nz/2 for every
+    cuvette height (with max_scatter = 1 only first collisions add camera
+    terms)."""
+    r = oracle_mod.walk(mu_s=0.1, phase="hg", hg_g=0.3, lx=20.0, ly=8.0, lz=lz, nx=8, nz=nz, n_photons=2000,
+                        seed=3, max_scatter=1)
+    rows = r["image"].sum(axis=1)
+    assert rows[nz // 2] > 0 and rows.sum() == rows[nz // 2]
