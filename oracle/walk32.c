@@ -187,7 +187,9 @@ static void photon32(const oracle_walk_cfg *c, const float *omu, const float *pd
         }
         const float nee = w * psr * expf(-mu_ext * (hy - r[1]));
         const double fx = (double)r[0] / c->lx * c->nx;
-        const double fz = ((double)r[2] + hz) / c->lz * c->nz;
+        /* rows measured from the axis: z = 0 is exactly row nz / 2 (the
+           pixel-tie reading); hz, the float half-height, would round it */
+        const double fz = (double)r[2] / c->lz * c->nz + 0.5 * c->nz;
         int ix = (int)floor(fx), iz = (int)floor(fz);
         if (ix > c->nx - 1) ix = c->nx - 1;
         if (iz > c->nz - 1) iz = c->nz - 1;

@@ -210,6 +210,9 @@ MUTATIONS = [
     ("walk32.c", "psr = pdf[nbin] / (2.0f * PI_F);", "psr = pdf[nbin + 1] / (2.0f * PI_F);", W32,
      "FP32 camera density of the next bin"),
     ("walk32.c", "w = w / surv;", "w = w * surv;", W32, "FP32 roulette survivor weight"),
+    ("walk32.c", "const double fz = (double)r[2] / c->lz * c->nz + 0.5 * c->nz;",
+     "const double fz = ((double)r[2] + hz) / c->lz * c->nz;", W32,
+     "FP32 camera row from the float half-height (z = 0 off row nz/2)"),
 ]
 
 

@@ -106,3 +106,64 @@ def test_hg_polar_angle_is_the_inverse_distribution(oracle_mod):
             d_prev = d
             checked += 1
     assert checked > 2 * n
+
+
+def _random_configs(seed=7, n=8):
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = []
+    for k in range(n):
+        lx, ly, lz = (float(v) for v in np.exp(rng.uniform(np.log(0.5), np.log(100.0), 3)))
+        tau = float(np.exp(rng.uniform(np.log(0.05), np.log(30.0))))
+        g = float(rng.uniform(-0.95, 0.99))
+        d = float(np.exp(rng.uniform(np.log(0.5), np.log(15.0))))
+        mu_a = float(tau / lx * rng.uniform(0.0, 0.5)) if k % 2 else 0.0
+        beam = float(rng.uniform(0.0, 0.5) * min(ly, lz)) if k % 4 == 1 else 0.0
+        out.append(dict(lx=lx, ly=ly, lz=lz, tau=tau, phase="hg" if k % 3 == 2 else "mie", g=g, d=d, mu_a=mu_a,
+                        beam=beam, nx=int(rng.integers(1, 200)), nz=int(rng.integers(1, 200)),
+                        rr=(float(rng.uniform(1e-4, 0.05)), float(rng.uniform(0.0, 0.5)))))
+    return out
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_single_precision_walk_follows_the_double_precision_walk_in_random_set_ups(oracle_mod, k):
+    """The FP32 mode against the FP64 walk over seeded random cuvettes, optical
+    depths, particles (Mie tables) or H-G anisotropies, absorption, roulette,
+    beams and cameras: the precision the engine's strict build is compared
+    with holds outside the hand-picked cases too (the trace rule, with the
+    camera transmittance's rounding allowance)."""
+    c = _random_configs()[k]
+    n = 1024
+    mu_ext = c["tau"] / c["lx"]
+    if c["phase"] == "mie":
+        x = oracle_mod.size_parameter(c["d"], 1.33, 532.0)
+        om = dict(phase="mie", table=oracle_mod.phase_table(oracle_mod.PHASE_MIE, complex(1.59 / 1.33, 0.0), x))
+        slope = None
+    else:
+        g = c["g"]
+        om = dict(phase="hg", hg_g=g)
+        slope = lambda mu: 3.0 * abs(g) / (1.0 + g * g - 2.0 * g * mu)
+    args = dict(mu_s=mu_ext - c["mu_a"], mu_a=c["mu_a"], lx=c["lx"], ly=c["ly"], lz=c["lz"], beam_radius=c["beam"],
+                nx=c["nx"], nz=c["nz"], r_max=0.5 * math.hypot(c["ly"], c["lz"]), seed=23,
+                rr_threshold=c["rr"][0], rr_survival=c["rr"][1], **om)
+    t64 = oracle_mod.walk(n_photons=n, n_trace=n, n_trace_events=32, **args)["trace"]
+    t32 = oracle_mod.walk32_trace(n_trace=n, n_trace_events=32, **args)
+    cmp = compare_traces(_as_engine(t32), t64, mu_ext=mu_ext, lx=c["lx"], nee_slope=slope, hy=0.5 * c["ly"])
+    print(k, c["phase"], round(c["tau"], 3), "matched %d/%d flips %d worst %s" %
+          (cmp["matched"], n, cmp["flips"], {q: "%.2e" % v for q, v in cmp["worst"].items()}))
+    for p, e, why in cmp["causes"]:
+        print("  unmatched photon %d event %d: %s" % (p, e, why))
+    assert cmp["matched"] >= 0.998 * n, cmp["causes"][:5]
+    assert cmp["flips"] <= 0.01 * n      # no systematic tie decided differently
+
+
+@pytest.mark.parametrize("lz,nz", [(21.034007022851252, 42), (5.6997014, 24), (10.0, 64)])
+def test_first_collisions_on_the_axis_fall_in_row_nz_over_2(oracle_mod, lz, nz):
+    """The pixel-tie reading in single precision: a pencil beam's first
+    collision lies on z = 0 and belongs to row nz/2 for any cuvette height."""
+    t32 = oracle_mod.walk32_trace(mu_s=0.1, phase="hg", hg_g=0.3, lx=20.0, ly=8.0, lz=lz, nx=8, nz=nz, n_trace=500,
+                                  n_trace_events=2, seed=3)
+    first = t32[:, 0, :]
+    coll = first[:, 0] == 0
+    assert coll.sum() > 100
+    assert np.all(first[coll, 3] == 0.0)
+    assert np.all(first[coll, 9].astype(int) // 8 == nz // 2)
