@@ -92,13 +92,18 @@ def test_table_builder_matches_oracle(eng, oracle_mod, d_um, m):
     assert info["g_table"] == pytest.approx(ot["mean"], abs=1e-12)
 
 
-@pytest.mark.parametrize("d_um,m,n_med,lam,n_bins", [(0.05, complex(1.59, 0.0), 1.33, 532.0, 4096),
-                                                     (3.0, complex(1.5, 0.5), 1.33, 532.0, 1024),
-                                                     (5.0, complex(1.59, 0.0), 1.0, 633.0, 64),
-                                                     (5.0, complex(1.59, 0.0), 1.33, 532.0, 16384)])
-def test_table_builder_matches_oracle_across_sizes_media_and_bins(eng, oracle_mod, d_um, m, n_med, lam, n_bins):
+@pytest.mark.parametrize("d_um,m,n_med,lam,n_bins,rtol", [(0.05, complex(1.59, 0.0), 1.33, 532.0, 4096, 1e-9),
+                                                          (3.0, complex(1.5, 0.5), 1.33, 532.0, 1024, 1e-9),
+                                                          (5.0, complex(1.59, 0.0), 1.0, 633.0, 64, 1e-9),
+                                                          (5.0, complex(1.59, 0.0), 1.33, 532.0, 16384, 1e-9),
+                                                          (2.0, complex(2.5, 0.001), 1.33, 532.0, 4096, 1e-9),
+                                                          (30.0, complex(1.59, 0.0), 1.33, 532.0, 4096, 1e-8)])
+def test_table_builder_matches_oracle_across_sizes_media_and_bins(eng, oracle_mod, d_um, m, n_med, lam, n_bins,
+                                                                    rtol):
     """The same two routes for a Rayleigh-sized sphere, a strongly absorbing
-    one, a sphere in air at 633 nm and the smallest and largest tables."""
+    one, a sphere in air at 633 nm, the smallest and largest tables, a
+    high-index sphere and a 30 um one (x = 236, where the forward peak is
+    1/x wide and the two quadratures differ by a few 1e-9)."""
     t = eng.PhaseTable(diameter_um=d_um, n_particle=m, n_medium=n_med, wavelength_nm=lam, n_bins=n_bins)
     x = oracle_mod.size_parameter(d_um, n_med, lam)
     mr = m / n_med
@@ -108,8 +113,8 @@ def test_table_builder_matches_oracle_across_sizes_media_and_bins(eng, oracle_mo
     assert t.info["qsca"] == pytest.approx(qs, rel=1e-10)
     assert t.info["g"] == pytest.approx(g, abs=1e-10)
     ot = oracle_mod.phase_table(oracle_mod.PHASE_MIE, mr, x, n_bins=n_bins)
-    np.testing.assert_allclose(t.omu64, ot["omu"], rtol=1e-9, atol=1e-15)
-    np.testing.assert_allclose(t.pdf64, ot["pdf"], rtol=1e-8)
+    np.testing.assert_allclose(t.omu64, ot["omu"], rtol=rtol, atol=1e-15)
+    np.testing.assert_allclose(t.pdf64, ot["pdf"], rtol=10 * rtol)
 
 
 def test_packed_table_layout(eng):
