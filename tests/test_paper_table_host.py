@@ -111,7 +111,8 @@ def test_bad_sizes_rejected(eng_paper):
 
 
 @pytest.mark.parametrize("n_theta,d_um,m", [(181, 5.0, complex(1.59, 0.0)), (3000, 1.0, complex(1.59, 0.0)),
-                                            (1001, 2.0, complex(1.5, 0.05)), (8000, 10.0, complex(1.59, 0.0))])
+                                            (1001, 2.0, complex(1.5, 0.05)), (8000, 10.0, complex(1.59, 0.0)),
+                                            (3000, 30.0, complex(1.59, 0.0)), (3000, 2.0, complex(2.5, 0.001))])
 def test_cdf_matches_oracle_across_grids_and_particles(eng_paper, oracle_mod, n_theta, d_um, m):
     import paper_2507_23189_gb300 as g
     t = g.PaperTable(diameter_um=d_um, n_particle=m, n_theta=n_theta)
